@@ -1,0 +1,145 @@
+"""ctypes binding of liboracle.so (FP64 CPU oracle, test infrastructure only)."""
+from __future__ import annotations
+
+import ctypes as C
+import dataclasses
+import os
+import subprocess
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB = os.path.join(HERE, "liboracle.so")
+SRC = [os.path.join(HERE, f) for f in ("tpc_oracle.cpp", "mlp_oracle.cpp") if os.path.exists(os.path.join(HERE, f))]
+
+
+def build_oracle(force: bool = False) -> str:
+    """Compile the oracle with g++ (-O2, no fast-math) if missing or stale."""
+    deps = SRC + [os.path.join(HERE, "tpc_oracle.h")]
+    if not force and os.path.exists(LIB) and all(os.path.getmtime(LIB) >= os.path.getmtime(s) for s in deps):
+        return LIB
+    tmp = LIB + f".tmp{os.getpid()}"
+    cmd = ["g++", "-O2", "-std=c++17", "-fPIC", "-shared", "-fno-fast-math", "-ffp-contract=off",
+           "-o", tmp] + SRC
+    subprocess.check_call(cmd, cwd=HERE)
+    os.replace(tmp, LIB)
+    return LIB
+
+
+class _Cfg(C.Structure):
+    _fields_ = [("n_rows", C.c_int), ("x_min", C.c_double), ("x_max", C.c_double),
+                ("half_angle_deg", C.c_double), ("bz_tesla", C.c_double),
+                ("sigma_y", C.c_double), ("sigma_z", C.c_double), ("brute", C.c_int)]
+
+
+@dataclasses.dataclass
+class OracleConfig:
+    n_rows: int = 152
+    x_min: float = 85.0
+    x_max: float = 246.0
+    half_angle_deg: float = 10.0
+    bz_tesla: float = 0.5
+    sigma_y: float = 0.1
+    sigma_z: float = 0.1
+    brute: bool = False
+
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        build_oracle()
+        lib = C.CDLL(LIB)
+        lib.orc_run.restype = C.c_int
+        lib.orc_run.argtypes = [C.POINTER(_Cfg), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_uint64,
+                                C.c_void_p, C.c_uint32, C.c_void_p, C.POINTER(C.c_void_p)]
+        lib.orc_free.argtypes = [C.c_void_p]
+        lib.orc_get.restype = C.c_int64
+        lib.orc_get.argtypes = [C.c_void_p, C.c_char_p, C.c_void_p, C.c_int64]
+        lib.orc_propagate.restype = C.c_int
+        lib.orc_propagate.argtypes = [C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_void_p]
+        lib.orc_fit_hits.restype = C.c_int
+        lib.orc_fit_hits.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                     C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.orc_chi2.restype = C.c_double
+        lib.orc_chi2.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
+        _lib = lib
+    return _lib
+
+
+_DT = {"sorted_qy": np.int32, "sorted_qz": np.int32, "sorted_id": np.int32, "rows": np.int32,
+       "first": np.int32, "up_raw": np.int32, "dn_raw": np.int32, "up": np.int32, "dn": np.int32,
+       "starts": np.int32, "trk_f": np.float64, "trk_i": np.int64, "trk_ids": np.int32,
+       "tl_n": np.int32, "tl_hits": np.int32, "tl_meta": np.int32}
+
+
+def _p(a):
+    return a.ctypes.data_as(C.c_void_p) if a is not None else None
+
+
+def run(cl, cfg: OracleConfig = None, what=None) -> dict:
+    """Run every step on a synth.Clusters-like object; returns the requested arrays."""
+    lib = _load()
+    cfg = cfg or OracleConfig()
+    c = _Cfg(cfg.n_rows, cfg.x_min, cfg.x_max, cfg.half_angle_deg, cfg.bz_tesla, cfg.sigma_y, cfg.sigma_z,
+             int(cfg.brute))
+    x = np.ascontiguousarray(cl.x, np.float32)
+    y = np.ascontiguousarray(cl.y, np.float32)
+    z = np.ascontiguousarray(cl.z, np.float32)
+    row = np.ascontiguousarray(cl.row, np.int32)
+    off = np.ascontiguousarray(cl.item_off, np.uint64)
+    core = None if getattr(cl, "item_core", None) is None else np.ascontiguousarray(cl.item_core, np.int32)
+    h = C.c_void_p()
+    st = lib.orc_run(C.byref(c), _p(x), _p(y), _p(z), _p(row), x.shape[0], _p(off), off.shape[0] - 1,
+                     _p(core), C.byref(h))
+    if st != 0:
+        raise ValueError(f"oracle rejected the input (status {st})")
+    out = {"status": st}
+    try:
+        for k in (what or _DT.keys()):
+            n = lib.orc_get(h, k.encode(), None, 0)
+            a = np.empty(n, dtype=_DT[k])
+            lib.orc_get(h, k.encode(), _p(a), n)
+            out[k] = a
+    finally:
+        lib.orc_free(h)
+    if "trk_f" in out:
+        out["trk_f"] = out["trk_f"].reshape(-1, 24)
+    if "trk_i" in out:
+        out["trk_i"] = out["trk_i"].reshape(-1, 4)
+    if "tl_meta" in out:
+        out["tl_meta"] = out["tl_meta"].reshape(-1, 2)
+    if "rows" in out:
+        out["rows"] = out["rows"].reshape(-1, 7)
+    return out
+
+
+def propagate(p, x1, x2, bz=0.5):
+    lib = _load()
+    p = np.ascontiguousarray(p, np.float64)
+    q = np.empty(5)
+    F = np.empty((5, 5))
+    ok = lib.orc_propagate(_p(p), x1, x2, bz, _p(q), _p(F))
+    return (q, F) if ok else None
+
+
+def fit_hits(x, y, z, p0, C0, sigma_y=0.1, sigma_z=0.1, bz=0.5):
+    lib = _load()
+    x, y, z = (np.ascontiguousarray(a, np.float64) for a in (x, y, z))
+    p0 = np.ascontiguousarray(p0, np.float64)
+    C0 = np.ascontiguousarray(C0, np.float64)
+    p = np.empty(5)
+    Cm = np.empty((5, 5))
+    chi2 = np.empty(1)
+    ok = lib.orc_fit_hits(x.shape[0], _p(x), _p(y), _p(z), _p(p0), _p(C0), sigma_y, sigma_z, bz, _p(p), _p(Cm),
+                          _p(chi2))
+    return (p, Cm, float(chi2[0])) if ok else None
+
+
+def chi2(p, Cm, my, mz, vy=0.01, vz=0.01):
+    lib = _load()
+    p = np.ascontiguousarray(p, np.float64)
+    Cm = np.ascontiguousarray(Cm, np.float64)
+    return float(lib.orc_chi2(_p(p), _p(Cm), my, mz, vy, vz))

@@ -1,0 +1,484 @@
+"""Pins of the FP64 oracle against things other than itself (CPU only).
+
+Each test ties one oracle function to an independent fact: a hand-derived
+fixture, brute force over all candidates, the Lorentz-force ODE, finite
+differences, the closed-form least-squares solution of a linear special case,
+exact (noise-free) helices, and the chi2 / pull statistics of smeared ones.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import OracleConfig
+from paper_1910_12214_b300 import synth
+import trackeval
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+Q = 1024.0
+
+
+class _Cl:
+    def __init__(self, x, y, z, row, item_off):
+        self.x = np.asarray(x, np.float32)
+        self.y = np.asarray(y, np.float32)
+        self.z = np.asarray(z, np.float32)
+        self.row = np.asarray(row, np.int32)
+        self.item_off = np.asarray(item_off, np.uint64)
+        self.item_core = None
+
+
+# ------------------------------------------------------------------ golden fixture
+def test_golden_tiny_links():
+    g = json.load(open(os.path.join(HERE, "golden", "tiny_links.json")))
+    hits = g["hits"]
+    n_rows = g["rows"]
+    x_max = 85.0 + 4 * 161.0 / 151.0
+    cfg = OracleConfig(n_rows=n_rows, x_min=85.0, x_max=x_max)
+    cl = _Cl([0] * len(hits), [h["y"] for h in hits], [h["z"] for h in hits], [h["row"] for h in hits],
+             [0, len(hits)])
+    r = oracle.run(cl, cfg)
+    e = g["expect"]
+    assert r["sorted_id"].tolist() == e["sorted_id"]
+    assert r["rows"][:, 1:].tolist() == e["rows_n_ymin_zmin_shift_ny_nz"]
+    flat = [v for row in e["first"] for v in row]
+    assert r["first"].tolist() == flat
+    for k in ("up_raw", "dn_raw", "up", "dn", "starts"):
+        assert r[k].tolist() == e[k], k
+
+
+# ------------------------------------------------------------------ binning
+def _check_binning(cl, r, n_rows):
+    rows = r["rows"]
+    first = r["first"]
+    qy, qz, ids = r["sorted_qy"], r["sorted_qz"], r["sorted_id"]
+    n = cl.x.shape[0]
+    assert np.array_equal(np.sort(ids), np.arange(n))
+    assert rows[:, 1].sum() == n
+    # quantisation: exact power-of-two scale, round half to even
+    assert np.array_equal(qy, np.rint(cl.y[ids].astype(np.float64) * Q).astype(np.int64))
+    assert np.array_equal(qz, np.rint(cl.z[ids].astype(np.float64) * Q).astype(np.int64))
+    fo = 0
+    item_off = cl.item_off.astype(np.int64)
+    for k in range(rows.shape[0]):
+        item, r_ = divmod(k, n_rows)
+        pos0, cnt, ymin, zmin, s, ny, nz = (int(v) for v in rows[k])
+        nb = ny * nz
+        f = first[fo:fo + nb + 1]
+        fo += nb + 1
+        assert f[0] == 0 and f[-1] == cnt and np.all(np.diff(f) >= 0)
+        if k % n_rows == 0:
+            assert pos0 == item_off[item]
+        if cnt == 0:
+            assert nb == 0
+            continue
+        sl = slice(pos0, pos0 + cnt)
+        assert np.all(cl.row[ids[sl]] == r_)
+        y, z = qy[sl].astype(np.int64), qz[sl].astype(np.int64)
+        assert y.min() == ymin and z.min() == zmin
+        Ly, Lz = y.max() - ymin + 1, z.max() - zmin + 1
+        assert ny == ((y.max() - ymin) >> s) + 1 and nz == ((z.max() - zmin) >> s) + 1
+        # bin-size rule: smallest s >= 10 with n*4^s >= Ly*Lz and ny*nz <= 2n+2
+        def ok(t):
+            return cnt * 4 ** t >= Ly * Lz and (((y.max() - ymin) >> t) + 1) * (((z.max() - zmin) >> t) + 1) <= 2 * cnt + 2
+        assert ok(s) and (s == 10 or not ok(s - 1))
+        b = ((y - ymin) >> s) * nz + ((z - zmin) >> s)
+        # canonical order (bin, id) and the bin ranges of first[]
+        order = np.lexsort((ids[sl], b))
+        assert np.array_equal(order, np.arange(cnt))
+        for j in range(nb):
+            assert np.all(b[f[j]:f[j + 1]] == j)
+    assert fo == first.shape[0]
+
+
+def test_binning_invariants_config1():
+    cl = synth.make_config1()
+    r = oracle.run(cl)
+    _check_binning(cl, r, 152)
+
+
+def test_binning_invariants_multi_item_with_empty_items():
+    cl = synth.make_batched(seed=3, n_events=2, mult=(5, 40))
+    sizes = np.diff(cl.item_off.astype(np.int64))
+    assert (sizes == 0).any()  # empty items are part of the case
+    r = oracle.run(cl)
+    _check_binning(cl, r, 152)
+
+
+def test_binning_and_links_independent_of_input_order():
+    cl = synth.make_config1(seed=4)
+    r1 = oracle.run(cl)
+    perm = np.random.default_rng(0).permutation(cl.x.shape[0])
+    cl2 = _Cl(cl.x[perm], cl.y[perm], cl.z[perm], cl.row[perm], cl.item_off)
+    r2 = oracle.run(cl2)
+    assert np.array_equal(r1["rows"][:, 1:], r2["rows"][:, 1:])
+    assert np.array_equal(r1["first"], r2["first"])
+    # ids of run 2 map back through perm; same hits, same per-bin multisets
+    back = perm[r2["sorted_id"]]
+    assert np.array_equal(np.sort(back), np.sort(r1["sorted_id"]))
+    # links are geometric, independent of the ids except for exact ties
+    up1 = r1["up"]
+    up2 = np.full_like(up1, -1)
+    m = r2["up"] >= 0
+    up2[perm[np.nonzero(m)[0]]] = perm[r2["up"][m]]
+    assert np.mean(up1 == up2) > 0.999
+
+
+# ------------------------------------------------------------------ links: brute force
+def _brute_links(qx, rowv, qy, qz):
+    """All triples, straight from the definition (no grid, no window pre-filter)."""
+    n = rowv.shape[0]
+    n_rows = qx.shape[0]
+    up_raw = np.full(n, -1)
+    dn_raw = np.full(n, -1)
+    for h in range(n):
+        r = rowv[h]
+        if r == 0 or r == n_rows - 1:
+            continue
+        dxu = int(qx[r + 1] - qx[r])
+        dxd = int(qx[r] - qx[r - 1])
+        best = None
+        for u in range(n):
+            if rowv[u] != r + 1 or abs(qy[u] - qy[h]) > dxu * 11 // 4 or abs(qz[u] - qz[h]) > dxu * 11 // 10:
+                continue
+            for d in range(n):
+                if rowv[d] != r - 1 or abs(qy[d] - qy[h]) > dxd * 11 // 4 or abs(qz[d] - qz[h]) > dxd * 11 // 10:
+                    continue
+                dY = (int(qy[u]) - int(qy[h])) * dxd - (int(qy[h]) - int(qy[d])) * dxu
+                dZ = (int(qz[u]) - int(qz[h])) * dxd - (int(qz[h]) - int(qz[d])) * dxu
+                m = dY * dY + dZ * dZ
+                if m > ((dxu + dxd) * 512) ** 2:
+                    continue
+                key = (m, u, d)
+                if best is None or key < best:
+                    best = key
+        if best is not None:
+            up_raw[h], dn_raw[h] = best[1], best[2]
+    up = np.array([u if u >= 0 and dn_raw[u] == h else -1 for h, u in enumerate(up_raw)])
+    dn = np.array([d if d >= 0 and up_raw[d] == h else -1 for h, d in enumerate(dn_raw)])
+    starts = [h for h in range(n) if up[h] >= 0 and dn[h] < 0 and up[up[h]] >= 0]
+    return up_raw, dn_raw, up, dn, starts
+
+
+@pytest.mark.parametrize("seed", range(60))
+def test_links_match_brute_force_tiny_sectors(seed):
+    rng = np.random.default_rng(1000 + seed)
+    n_rows = int(rng.integers(3, 9))
+    x_max = 85.0 + (n_rows - 1) * 161.0 / 151.0
+    cfg = OracleConfig(n_rows=n_rows, x_min=85.0, x_max=x_max)
+    rows, ys, zs = [], [], []
+    # a few straight-ish tracks plus clutter in a 6x6 cm box: many candidates per window
+    for _ in range(int(rng.integers(1, 4))):
+        y0, z0, ty, tz = rng.uniform(-2, 2), rng.uniform(-2, 2), rng.uniform(-1, 1), rng.uniform(-0.8, 0.8)
+        for r in range(n_rows):
+            if rng.uniform() < 0.9:
+                rows.append(r)
+                ys.append(y0 + ty * r * 1.0662 + rng.normal(0, 0.1))
+                zs.append(z0 + tz * r * 1.0662 + rng.normal(0, 0.1))
+    for r in range(n_rows):
+        k = int(rng.integers(0, 9))
+        rows += [r] * k
+        ys += list(rng.uniform(-3, 3, k))
+        zs += list(rng.uniform(-3, 3, k))
+    n = len(rows)
+    perm = rng.permutation(n)
+    rows, ys, zs = np.array(rows)[perm], np.array(ys)[perm], np.array(zs)[perm]
+    cl = _Cl(np.zeros(n), ys, zs, rows, [0, n])
+    r = oracle.run(cl, cfg)
+    qx = np.rint((85.0 + np.arange(n_rows) * ((x_max - 85.0) / (n_rows - 1))) * Q).astype(np.int64)
+    qy = np.rint(cl.y.astype(np.float64) * Q).astype(np.int64)
+    qz = np.rint(cl.z.astype(np.float64) * Q).astype(np.int64)
+    up_raw, dn_raw, up, dn, starts = _brute_links(qx, cl.row, qy, qz)
+    assert r["up_raw"].tolist() == up_raw.tolist()
+    assert r["dn_raw"].tolist() == dn_raw.tolist()
+    assert r["up"].tolist() == up.tolist()
+    assert r["dn"].tolist() == dn.tolist()
+    # starts: same set; canonical order is (row, bin, id)
+    assert sorted(r["starts"].tolist()) == sorted(starts)
+    # brute-force search mode of the oracle itself gives the same links
+    rb = oracle.run(cl, OracleConfig(n_rows=n_rows, x_min=85.0, x_max=x_max, brute=True), what=["up", "dn"])
+    assert np.array_equal(rb["up"], r["up"]) and np.array_equal(rb["dn"], r["dn"])
+
+
+@pytest.mark.parametrize("seed", range(40))
+def test_links_match_brute_force_on_lattice_with_ties(seed):
+    """Hits on a coarse lattice of quanta so that equal metrics (exact ties) are common;
+    the tie-break (smaller id_u, then smaller id_d) decides."""
+    rng = np.random.default_rng(5000 + seed)
+    n_rows = int(rng.integers(3, 7))
+    x_max = 85.0 + (n_rows - 1) * 161.0 / 151.0
+    cfg = OracleConfig(n_rows=n_rows, x_min=85.0, x_max=x_max)
+    rows, ys, zs = [], [], []
+    for r in range(n_rows):
+        k = int(rng.integers(2, 10))
+        rows += [r] * k
+        ys += list(rng.integers(-3, 4, k) * 256 / Q)
+        zs += list(rng.integers(-2, 3, k) * 256 / Q)
+    n = len(rows)
+    perm = rng.permutation(n)
+    rows, ys, zs = np.array(rows)[perm], np.array(ys)[perm], np.array(zs)[perm]
+    cl = _Cl(np.zeros(n), ys, zs, rows, [0, n])
+    r = oracle.run(cl, cfg)
+    qx = np.rint((85.0 + np.arange(n_rows) * ((x_max - 85.0) / (n_rows - 1))) * Q).astype(np.int64)
+    qy = np.rint(cl.y.astype(np.float64) * Q).astype(np.int64)
+    qz = np.rint(cl.z.astype(np.float64) * Q).astype(np.int64)
+    up_raw, dn_raw, up, dn, starts = _brute_links(qx, cl.row, qy, qz)
+    assert r["up_raw"].tolist() == up_raw.tolist()
+    assert r["dn_raw"].tolist() == dn_raw.tolist()
+    assert sorted(r["starts"].tolist()) == sorted(starts)
+
+
+def test_links_follow_straight_noise_free_tracks():
+    """kappa = 0, well separated straight tracks: every inner link is the true neighbour, m = 0."""
+    rng = np.random.default_rng(7)
+    n_tr = 30
+    rows, ys, zs, lab = [], [], [], []
+    for t in range(n_tr):
+        y0, z0 = -40 + t * 2.7, -100 + 7.0 * t
+        ty, tz = rng.uniform(-0.3, 0.3), rng.uniform(-0.5, 0.5)
+        for r in range(152):
+            xr = (85.0 + r * (161.0 / 151.0)) - 85.0
+            rows.append(r)
+            # place hits exactly on quanta so the line is exact in integers
+            ys.append(np.round((y0 + ty * xr) * Q) / Q)
+            zs.append(np.round((z0 + tz * xr) * Q) / Q)
+            lab.append(t)
+    n = len(rows)
+    cl = _Cl(np.zeros(n), ys, zs, rows, [0, n])
+    r = oracle.run(cl)
+    lab = np.array(lab)
+    rows = np.array(rows)
+    inner = (rows >= 1) & (rows <= 150)
+    assert np.all(r["up_raw"][inner] >= 0)
+    assert np.all(lab[r["up_raw"][inner]] == lab[inner])
+    assert np.all(rows[r["up_raw"][inner]] == rows[inner] + 1)
+    assert np.all(lab[r["dn_raw"][inner]] == lab[inner])
+    # every track is exactly one chain from row 1 to row 150 -> one start hit per track
+    assert r["starts"].shape[0] == n_tr
+    assert np.all(rows[r["starts"]] == 1)
+
+
+# ------------------------------------------------------------------ track model
+C_LIGHT = 0.299792458e-2
+
+
+def _rk4(p, x1, x2, bz=0.5, h=1e-3):
+    """Integrate the Lorentz force dt/ds = (q c B / p) t x z_hat in FP64 (independent of the
+    closed-form helix step)."""
+    y, z, snp, tgl, qpt = p
+    t = np.array([math.sqrt(1 - snp * snp), snp, tgl]) / math.sqrt(1 + tgl * tgl)
+    k = C_LIGHT * bz * qpt / math.sqrt(1 + tgl * tgl)  # q/p = (q/pT) / sqrt(1+tgl^2)
+
+    def f(st):
+        tt = st[3:]
+        return np.array([tt[0], tt[1], tt[2], k * tt[1], -k * tt[0], 0.0])
+
+    def step(st, ds):
+        k1 = f(st)
+        k2 = f(st + 0.5 * ds * k1)
+        k3 = f(st + 0.5 * ds * k2)
+        k4 = f(st + ds * k3)
+        return st + ds / 6 * (k1 + 2 * k2 + 2 * k3 + k4)
+
+    st = np.array([x1, y, z, *t])
+    sgn = 1.0 if x2 >= x1 else -1.0
+    while abs((x2 - st[0]) / st[3]) > h:
+        st = step(st, sgn * h)
+    for _ in range(4):
+        st = step(st, (x2 - st[0]) / st[3])
+    tt = st[3:]
+    return np.array([st[1], st[2], tt[1] / math.hypot(tt[0], tt[1]), tgl, qpt])
+
+
+@pytest.mark.parametrize("i", range(5))
+def test_propagation_matches_rk4_lorentz_force(i):
+    rng = np.random.default_rng(50 + i)
+    p = np.array([rng.uniform(-5, 5), rng.uniform(-50, 50), rng.uniform(-0.6, 0.6), rng.uniform(-1, 1),
+                  rng.choice([-1, 1]) * rng.uniform(0.1, 8)])
+    x1 = rng.uniform(85, 200)
+    x2 = x1 + rng.uniform(-8, 8)
+    q, _ = oracle.propagate(p, x1, x2)
+    assert np.max(np.abs(q - _rk4(p, x1, x2))) < 1e-9
+
+
+@pytest.mark.parametrize("i", range(8))
+def test_jacobian_matches_finite_differences(i):
+    rng = np.random.default_rng(80 + i)
+    p = np.array([rng.uniform(-5, 5), rng.uniform(-50, 50), rng.uniform(-0.8, 0.8), rng.uniform(-1, 1),
+                  rng.choice([-1, 1]) * rng.uniform(0.05, 10)])
+    x1 = rng.uniform(85, 240)
+    x2 = x1 + rng.choice([-1, 1]) * rng.uniform(0.5, 20)
+    out = oracle.propagate(p, x1, x2)
+    if out is None:
+        pytest.skip("step leaves the valid region")
+    _, F = out
+    J = np.zeros((5, 5))
+    for j in range(5):
+        e = np.zeros(5)
+        e[j] = 1e-6 * max(1.0, abs(p[j]))
+        J[:, j] = (oracle.propagate(p + e, x1, x2)[0] - oracle.propagate(p - e, x1, x2)[0]) / (2 * e[j])
+    assert np.max(np.abs(J - F) / np.maximum(1e-3, np.abs(F))) < 1e-5
+
+
+def test_kalman_straight_line_equals_weighted_least_squares():
+    """sinphi = 0 and q/pT = 0 with zero prior variance: the model is linear
+    (y constant, z = z0 + tgl*(x - x0)), so the filter equals the closed-form
+    Bayesian weighted least squares with the same prior."""
+    rng = np.random.default_rng(3)
+    n = 40
+    x = 85.0 + np.arange(n) * 1.0662
+    y = 1.5 + rng.normal(0, 0.1, n)
+    z = 20.0 + 0.4 * (x - x[0]) + rng.normal(0, 0.1, n)
+    p0 = np.array([1.0, 19.0, 0.0, 0.3, 0.0])
+    C0 = np.diag([4.0, 9.0, 0.0, 0.25, 0.0])
+    p, Cm, chi2 = oracle.fit_hits(x, y, z, p0, C0)
+    s2 = 0.01
+    # y: scalar Gaussian product
+    vy = 1.0 / (1.0 / C0[0, 0] + n / s2)
+    my = vy * (p0[0] / C0[0, 0] + y.sum() / s2)
+    # (z at the last x, tgl): normal equations with the prior, parametrised at x[-1]
+    A = np.stack([np.ones(n), x - x[-1]], axis=1)
+    P0 = np.array([[C0[1, 1], 0], [0, C0[3, 3]]])
+    m0 = np.array([p0[1] + p0[3] * (x[-1] - x[0]), p0[3]])
+    # prior expressed at x[-1]: z_last = z0 + tgl*(x_last-x0)
+    Tm = np.array([[1.0, x[-1] - x[0]], [0.0, 1.0]])
+    P0l = Tm @ P0 @ Tm.T
+    Inf = np.linalg.inv(P0l) + A.T @ A / s2
+    cov = np.linalg.inv(Inf)
+    mz = cov @ (np.linalg.inv(P0l) @ m0 + A.T @ z / s2)
+    assert abs(p[0] - my) < 1e-10 and abs(Cm[0, 0] - vy) < 1e-12
+    assert np.allclose([p[1], p[3]], mz, atol=1e-10, rtol=0)
+    assert np.allclose([[Cm[1, 1], Cm[1, 3]], [Cm[3, 1], Cm[3, 3]]], cov, atol=1e-12, rtol=1e-9)
+    assert p[2] == 0.0 and p[4] == 0.0
+    # chi2 of a sequential filter = the batch objective at the optimum (prior term included)
+    ry = y - my
+    rz = z - A @ mz
+    batch = ((my - p0[0]) ** 2 / C0[0, 0] + (mz - m0) @ np.linalg.inv(P0l) @ (mz - m0)
+             + (ry @ ry + rz @ rz) / s2)
+    assert abs(chi2 - batch) < 1e-8 * batch
+
+
+def test_chi2_matches_linear_solve_with_correlated_covariance():
+    """chi2 = r^T S^-1 r with S = H C H^T + V, checked against a generic linear solve
+    for covariances with a strong y-z correlation."""
+    rng = np.random.default_rng(11)
+    for _ in range(50):
+        A = rng.normal(size=(5, 5))
+        Cm = A @ A.T + 0.1 * np.eye(5)
+        p = rng.normal(size=5)
+        my, mz = rng.normal(size=2)
+        S = Cm[:2, :2] + np.diag([0.01, 0.02])
+        res = np.array([my - p[0], mz - p[1]])
+        assert abs(oracle.chi2(p, Cm, my, mz, 0.01, 0.02) - res @ np.linalg.solve(S, res)) < 1e-9
+
+
+def _pulls(cl, r):
+    f = r["trk_f"]
+    ti = r["trk_i"]
+    ids = r["trk_ids"]
+    qx = np.rint(synth.Geometry().row_x() * Q) / Q
+    out = []
+    for k in range(f.shape[0]):
+        s = ids[ti[k, 1]:ti[k, 1] + ti[k, 2]]
+        lab = np.bincount(cl.mc[s][cl.mc[s] >= 0]).argmax()
+        row_ref = int(np.argmin(np.abs(qx - f[k, 0])))
+        cand = np.nonzero((cl.mc == lab) & (cl.row == row_ref))[0]
+        if cand.shape[0] != 1:
+            continue
+        cov = f[k, 6:21]
+        diag = np.array([cov[0], cov[2], cov[5], cov[9], cov[14]])
+        out.append((f[k, 1:6] - cl.truth[cand[0]]) / np.sqrt(diag))
+    return np.array(out)
+
+
+def test_noise_free_helices_reproduce_truth():
+    """sigma = 0 (coordinates only quantised to 2^-10 cm): parameters equal the exact
+    helix to the quantisation scale (pulls ~ (Q/sqrt(12))/0.1 = 0.003), chi2 ~ 0."""
+    cl = synth.make_config1(noise_frac=0.0, sigma_y=0.0, sigma_z=0.0)
+    r = oracle.run(cl)
+    P = _pulls(cl, r)
+    assert P.shape[0] >= 190
+    assert np.abs(P).max() < 0.05
+    f = r["trk_f"]
+    assert np.max(f[:, 21] / f[:, 22]) < 1e-4
+
+
+def test_smeared_helices_chi2_and_pulls():
+    """sigma = 0.1 cm: <chi2/ndf> ~ 1 and pulls ~ N(0,1) (after a 5-sigma outlier cut
+    that removes tracks with a confused hit)."""
+    allp, chi, ndf = [], 0.0, 0.0
+    for seed in range(1, 6):
+        cl = synth.make_config1(seed=seed, noise_frac=0.0)
+        r = oracle.run(cl)
+        allp.append(_pulls(cl, r))
+        chi += r["trk_f"][:, 21].sum()
+        ndf += r["trk_f"][:, 22].sum()
+    P = np.concatenate(allp)
+    assert 0.97 <= chi / ndf <= 1.03
+    good = np.all(np.abs(P) < 5, axis=1)
+    assert good.mean() > 0.99
+    P = P[good]
+    assert np.all(np.abs(P.mean(0)) < 0.1)
+    assert np.all((P.std(0) > 0.9) & (P.std(0) < 1.1))
+
+
+# ------------------------------------------------------------------ selection
+def test_selection_matches_brute_force():
+    cl = synth.make_config2(seed=2, n_tracks=1500)
+    r = oracle.run(cl)
+    tl_n, meta, hits = r["tl_n"], r["tl_meta"], r["tl_hits"]
+    lists, o = [], 0
+    for t in range(tl_n.shape[0]):
+        lists.append(hits[o:o + tl_n[t]].tolist())
+        o += tl_n[t]
+    best = {}
+    for t, hl in enumerate(lists):
+        if tl_n[t] == 0:
+            continue
+        key = (int(tl_n[t]), -int(meta[t, 1]))
+        for h in hl:
+            if h not in best or key > best[h]:
+                best[h] = key
+    exp_tracks, exp_ids = [], []
+    for t, hl in enumerate(lists):
+        if tl_n[t] == 0:
+            continue
+        key = (int(tl_n[t]), -int(meta[t, 1]))
+        own = [h for h in reversed(hl) if best[h] == key]
+        if len(own) >= 10:
+            exp_tracks.append((int(meta[t, 0]), int(meta[t, 1]), len(own)))
+            exp_ids += own
+    got = [(int(a), int(d), int(c)) for a, b, c, d in r["trk_i"]]
+    assert got == exp_tracks
+    assert r["trk_ids"].tolist() == exp_ids
+
+
+def test_chi2_search_independent_of_grid():
+    """The best-chi2 pick over the grid window equals the pick over the whole row."""
+    cl = synth.make_config1(seed=2)
+    a = oracle.run(cl, what=["trk_ids", "trk_f"])
+    b = oracle.run(cl, OracleConfig(brute=True), what=["trk_ids", "trk_f"])
+    assert np.array_equal(a["trk_ids"], b["trk_ids"])
+    assert np.array_equal(a["trk_f"], b["trk_f"])
+
+
+def test_end_to_end_noise_free_high_pt():
+    cl = synth.make_config1(noise_frac=0.0, sigma_y=0.0, sigma_z=0.0, pt_range=(1.0, 10.0))
+    r = oracle.run(cl)
+    e = trackeval.efficiency(cl, r["trk_i"], r["trk_ids"])
+    assert e["eff"] == 1.0 and e["fake_rate"] == 0.0
+
+
+def test_rejects_bad_input():
+    cl = synth.make_config1()
+    bad = _Cl(cl.x, cl.y, cl.z, cl.row.copy(), cl.item_off)
+    bad.row[5] = 152
+    with pytest.raises(ValueError):
+        oracle.run(bad)
+    bad = _Cl(cl.x, cl.y.copy(), cl.z, cl.row, cl.item_off)
+    bad.y[3] = np.nan
+    with pytest.raises(ValueError):
+        oracle.run(bad)
