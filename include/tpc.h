@@ -1,0 +1,162 @@
+/*
+ * tpc.h -- C ABI of libtpc.so, a B300-native (sm_103a) TPC sector tracker.
+ *
+ * The library performs the hot path of the TPC reconstruction described in
+ * D. Rohr, "Global Track Reconstruction and Data Compression Strategy in ALICE
+ * for LHC Run 3" (arXiv:1910.12214): cellular-automaton track finding followed
+ * by a Kalman fit (Sec. 3, derived from the Run 2 HLT tracker), under continuous
+ * read-out with no a-priori vertex (Abstract).  Clusters produced by the cluster
+ * finder go in (Sec. 4, step 1); tracks and their cluster attachment come out
+ * (Sec. 4: the compression steps consume the cluster-to-track attachment, and an
+ * ambiguous cluster is given to one track only).
+ *
+ * Conventions
+ *  - Every call returns a tpc_status; the library never aborts or throws.
+ *  - A failed call leaves the context usable, except TPC_ERR_CUDA after a
+ *    sticky CUDA context error.
+ *  - Units: cm, GeV/c, Tesla.  Cluster ids in the output are the caller's
+ *    original input indices (0-based, over the whole tpc_clusters batch).
+ *  - One context per host thread; a context is not thread-safe.
+ *  - Device work runs on the context's stream; tpc_track() is asynchronous and
+ *    errors detected on the device (bad input values, capacity) are returned by
+ *    the next tpc_get_tracks() or tpc_sync().
+ */
+#ifndef TPC_H
+#define TPC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct tpc_ctx tpc_ctx;
+
+typedef enum {
+  TPC_OK = 0,
+  TPC_ERR_INVALID_ARG = 1, /* a NULL pointer, an out-of-range size or an inconsistent CSR */
+  TPC_ERR_STATE = 2,       /* call out of order (e.g. tpc_track before tpc_load_clusters) */
+  TPC_ERR_CUDA = 3,        /* a CUDA runtime error; see tpc_last_error() */
+  TPC_ERR_OOM = 4,         /* the allocator returned NULL */
+  TPC_ERR_CAPACITY = 5,    /* an output buffer or an internal limit is too small */
+  TPC_ERR_TIMEOUT = 6,     /* a bounded device wait gave up */
+  TPC_ERR_BAD_INPUT = 7    /* a cluster has a row out of range or a non-finite coordinate */
+} tpc_status;
+
+typedef enum { TPC_MODE_PLAIN = 0, TPC_MODE_BATCHED = 1 } tpc_mode;
+typedef enum { TPC_CORR_NONE = 0, TPC_CORR_GRID = 1, TPC_CORR_MLP = 2 } tpc_corr;
+
+/* Optional device-memory allocator (e.g. a framework's caching allocator).
+ * alloc(bytes, user) returns a device pointer aligned to >= 256 bytes or NULL;
+ * free(ptr, user) releases it.  NULL allocator = cudaMallocAsync on the stream. */
+typedef struct {
+  void* (*alloc)(size_t bytes, void* user);
+  void (*free)(void* ptr, void* user);
+  void* user;
+} tpc_allocator;
+
+typedef struct {
+  int device;                 /* CUDA device ordinal */
+  void* stream;               /* cudaStream_t to run on; NULL = a library-owned stream */
+  float bz_tesla;             /* solenoid field, e.g. 0.5 */
+  int n_rows;                 /* pad rows per sector, 3..256 (152 for the ALICE TPC) */
+  float row_x_min, row_x_max; /* radii of the first and last pad row [cm] (85, 246) */
+  float sector_half_angle_deg;/* sector half opening angle (10) */
+  float sigma_y, sigma_z;     /* cluster resolution used by the Kalman filter [cm] (0.1) */
+  tpc_mode mode;              /* PLAIN: one launch per step; BATCHED: persistent kernel */
+  tpc_corr correction;        /* space-point correction applied at load (NONE for now) */
+  uint64_t max_clusters;      /* initial reservation (0 = grow on demand) */
+  uint32_t max_items;         /* initial reservation (0 = grow on demand) */
+  const tpc_allocator* allocator; /* NULL = cudaMallocAsync */
+  int profile;                /* 1 = record per-step CUDA events for tpc_stage_times */
+} tpc_config;
+
+/* Cluster batch, SoA, grouped by work item (event, sector[, time slice]).
+ * Item k owns clusters [item_off[k], item_off[k+1]); item_off[0] = 0 and
+ * item_off[n_items] = n.  x is the pad-row radius (only checked to be finite: the
+ * row index defines the position along x); y, z are sector-local [cm]; row is the
+ * pad-row index 0..n_rows-1.  x, y, z, row are host pointers (copied during the
+ * call) or, with on_device = 1, device pointers borrowed until tpc_track() has
+ * completed.  item_off, item_sector, item_event and item_core are host arrays.
+ * item_core (nullable) holds [n_items][2] z ranges [lo, hi) in units of 2^-10 cm:
+ * a track is reported only if its innermost cluster's z lies in its item's range
+ * (time-frame slices with overlap report each track once). */
+typedef struct {
+  const float* x;
+  const float* y;
+  const float* z;
+  const int32_t* row;
+  uint64_t n;
+  const uint64_t* item_off;
+  uint32_t n_items;
+  const uint32_t* item_sector; /* nullable: sector id copied into the tracks */
+  const uint32_t* item_event;  /* nullable: event id copied into the tracks */
+  const int32_t* item_core;    /* nullable */
+  int on_device;
+} tpc_clusters;
+
+/* One track: Kalman state at the innermost cluster, x_ref = that pad row's radius
+ * (sector-local); (y, z, sinphi, tanlambda, q/pT); cov = lower triangle of the 5x5
+ * covariance, row by row ((0,0),(1,0),(1,1),(2,0),...,(4,4)).  The track's cluster
+ * ids are cluster_ids[first_cluster .. first_cluster + n_clusters), innermost first. */
+typedef struct {
+  float x_ref, y, z, snp, tgl, qpt;
+  float cov[15];
+  float chi2;
+  int32_t ndf;
+  uint32_t item, sector, event, first_cluster, n_clusters;
+} tpc_track_t;
+
+/* Creates a context on cfg->device.  *out receives the context or NULL. */
+tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out);
+
+/* Loads one batch of clusters (copied to the device if on_device = 0) and
+ * resets the previous output.  Grows the device buffers if needed. */
+tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* cl);
+
+/* Runs every step of the tracker on the loaded batch: quantisation, per-row
+ * grids, neighbour links, mutual cleaning, start hits, Kalman tracklets,
+ * shared-cluster resolution and output compaction.  Asynchronous. */
+tpc_status tpc_track(tpc_ctx* ctx);
+
+/* Waits for the stream and returns a device-side error if one was flagged. */
+tpc_status tpc_sync(tpc_ctx* ctx);
+
+/* Waits for the stream and copies the tracks and their cluster ids to the
+ * caller's host buffers.  *n_trk and *n_ids always receive the required sizes;
+ * if trk_cap or id_cap is too small nothing is copied and TPC_ERR_CAPACITY is
+ * returned.  trk / cluster_ids may be NULL with zero capacity (size query). */
+tpc_status tpc_get_tracks(tpc_ctx* ctx, tpc_track_t* trk, uint64_t trk_cap, uint32_t* cluster_ids,
+                          uint64_t id_cap, uint64_t* n_trk, uint64_t* n_ids);
+
+/* Device pointers of the last output (valid until the next load), for callers
+ * that keep the tracks on the GPU.  Any argument may be NULL. */
+tpc_status tpc_device_tracks(tpc_ctx* ctx, const tpc_track_t** trk, const uint32_t** cluster_ids,
+                             const uint64_t** d_counts);
+
+/* Per-step device times of the last tpc_track() in microseconds (needs
+ * cfg.profile = 1): us[i] for the steps named by tpc_stage_name(i). */
+tpc_status tpc_stage_times(tpc_ctx* ctx, float* us, int n, int* n_stages);
+const char* tpc_stage_name(int i);
+
+/* Intermediate results of the last tpc_track() in a canonical host layout, for
+ * parity tests.  stage: 0 sorted (qy,qz,id) int32 x3 per cluster; 1 row records
+ * int32 x7 (pos0,n,ymin,zmin,shift,ny,nz) per (item,row); 2 bin starts relative
+ * to pos0, nbins+1 per (item,row); 3..6 raw up, raw down, clean up, clean down
+ * links as original ids indexed by original id (-1 = none); 7 start hits
+ * (original ids, canonical order); 8 hits per tracklet (0 = dropped);
+ * 9 tracklet hit lists (original ids, outermost first).  Copies up to cap int32
+ * values into host_buf and sets *n to the full count. */
+tpc_status tpc_debug_dump(tpc_ctx* ctx, int stage, int32_t* host_buf, uint64_t cap, uint64_t* n);
+
+/* Frees every device buffer and the context. */
+void tpc_destroy(tpc_ctx* ctx);
+
+/* Text of the last error of this context (never NULL). */
+const char* tpc_last_error(const tpc_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* TPC_H */

@@ -1,0 +1,486 @@
+// C ABI of libtpc (include/tpc.h): context, device buffers, launches, copies.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "tpc.h"
+#include "tpc_internal.cuh"
+
+struct tpc_ctx {
+  tpc_config cfg{};
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  bool has_alloc = false;
+  tpc_allocator alloc{};
+  DevParams par{};
+  LaunchCfg lc{};
+  std::string err;
+  // capacity of the current allocation
+  long long capN = -1, capI = -1, capChunks = -1;
+  std::vector<void*> blocks;
+  Buffers b{};
+  // buffers owned by the context (b.x.. may point at borrowed device input instead)
+  float *own_x = nullptr, *own_y = nullptr, *own_z = nullptr;
+  int* own_row = nullptr;
+  int* own_core = nullptr;
+  uint32_t *own_sec = nullptr, *own_ev = nullptr;
+  // host-side copy bookkeeping
+  std::vector<Chunk> chunks;
+  bool loaded = false, tracked = false;
+  bool input_on_device = false;
+  cudaEvent_t ev[TPC_N_STAGES + 1] = {};
+  bool have_events = false;
+};
+
+namespace {
+
+tpc_status fail(tpc_ctx* c, tpc_status s, const std::string& msg) {
+  if (c) c->err = msg;
+  return s;
+}
+
+tpc_status cuda_fail(tpc_ctx* c, cudaError_t e, const char* where) {
+  return fail(c, TPC_ERR_CUDA, std::string(where) + ": " + cudaGetErrorString(e));
+}
+
+void* dev_alloc(tpc_ctx* c, size_t bytes) {
+  if (bytes == 0) bytes = 256;
+  bytes = (bytes + 255) & ~size_t(255);
+  void* p = nullptr;
+  if (c->has_alloc) {
+    p = c->alloc.alloc(bytes, c->alloc.user);
+  } else if (cudaMallocAsync(&p, bytes, c->stream) != cudaSuccess) {
+    cudaGetLastError();
+    p = nullptr;
+  }
+  if (p) c->blocks.push_back(p);
+  return p;
+}
+
+void free_all(tpc_ctx* c) {
+  if (!c->blocks.empty()) cudaStreamSynchronize(c->stream);
+  for (void* p : c->blocks) {
+    if (c->has_alloc)
+      c->alloc.free(p, c->alloc.user);
+    else
+      cudaFreeAsync(p, c->stream);
+  }
+  c->blocks.clear();
+  c->capN = c->capI = c->capChunks = -1;
+}
+
+// Allocates every buffer for N clusters, I items and n_chunks CTAs of the
+// cluster-parallel kernels.  Sizes per cluster (bytes): inputs 16, temporaries
+// 12, grouped 12, sorted 16, bins <= 8, links 20 + 4, tracklets (N/3 starts)
+// 4 + 112/3 + 4*n_rows/3, ownership 8 + 16/3, output 112/3 + 4.
+tpc_status reserve(tpc_ctx* c, long long N, long long I, long long n_chunks) {
+  if (N <= c->capN && I <= c->capI && n_chunks <= c->capChunks) return TPC_OK;
+  free_all(c);
+  N = std::max<long long>(N, c->capN < 0 ? 0 : c->capN);
+  N = std::max<long long>(N, 1);
+  I = std::max<long long>(I, 1);
+  n_chunks = std::max<long long>(n_chunks, 1);
+  const int NR = c->cfg.n_rows;
+  const long long M = I * NR;
+  const long long Tcap = N / 3 + 1;
+  Buffers& b = c->b;
+  bool ok = true;
+  auto A = [&](size_t bytes) -> void* {
+    void* p = dev_alloc(c, bytes);
+    ok &= p != nullptr;
+    return p;
+  };
+  c->own_x = (float*)A(4 * N);
+  c->own_y = (float*)A(4 * N);
+  c->own_z = (float*)A(4 * N);
+  c->own_row = (int*)A(4 * N);
+  b.item_off = (const uint64_t*)A(8 * (I + 1));
+  c->own_core = (int*)A(8 * I);
+  c->own_sec = (uint32_t*)A(4 * I);
+  c->own_ev = (uint32_t*)A(4 * I);
+  b.chunks = (const Chunk*)A(sizeof(Chunk) * n_chunks);
+  b.cl_key = (int*)A(4 * N);
+  b.cl_q = (int2*)A(8 * N);
+  b.rs_cnt = (int*)A(4 * M);
+  b.rs_min = (int*)A(16 * M);
+  b.row_fill = (int*)A(4 * M);
+  b.rows = (RowInfo*)A(sizeof(RowInfo) * M);
+  b.g_q = (int2*)A(8 * N);
+  b.g_id = (int*)A(4 * N);
+  b.s_q = (int2*)A(8 * N);
+  b.s_id = (int*)A(4 * N);
+  b.s_key = (int*)A(4 * N);
+  b.first = (int*)A(4 * (2 * N + 3 * M + 1));
+  b.up_raw = (int*)A(4 * N);
+  b.dn_raw = (int*)A(4 * N);
+  b.up = (int*)A(4 * N);
+  b.dn = (int*)A(4 * N);
+  b.flags = (int*)A(4 * N);
+  b.start_ex = (int*)A(4 * (N + 1));
+  b.starts = (int*)A(4 * Tcap);
+  b.tl = (TrackletRec*)A(sizeof(TrackletRec) * Tcap);
+  b.tl_hits = (int*)A(4 * (size_t)Tcap * NR);
+  b.hit_key = (unsigned long long*)A(8 * N);
+  b.tl_cnt = (unsigned long long*)A(8 * Tcap);
+  b.tl_ex = (unsigned long long*)A(8 * (Tcap + 1));
+  b.trk = A(sizeof(tpc_track_t) * Tcap);
+  b.trk_ids = (uint32_t*)A(4 * N);
+  b.counts = (unsigned long long*)A(8 * 4);
+  b.err = (unsigned int*)A(16);
+  b.scan_tmp = (unsigned long long*)A(8 * 1040);
+  b.T_cap = (int)Tcap;
+  if (!ok) {
+    free_all(c);
+    return fail(c, TPC_ERR_OOM, "device allocation failed");
+  }
+  c->capN = N;
+  c->capI = I;
+  c->capChunks = n_chunks;
+  return TPC_OK;
+}
+
+}  // namespace
+
+extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
+  if (!out) return TPC_ERR_INVALID_ARG;
+  *out = nullptr;
+  if (!cfg) return TPC_ERR_INVALID_ARG;
+  if (cfg->n_rows < 3 || cfg->n_rows > TPC_MAX_ROWS || !(cfg->row_x_max > cfg->row_x_min) ||
+      !(cfg->row_x_min > 0.f) || !(cfg->sector_half_angle_deg > 0.f) || !(cfg->sector_half_angle_deg < 60.f) ||
+      !(cfg->sigma_y > 0.f) || !(cfg->sigma_z > 0.f) || !std::isfinite(cfg->bz_tesla) ||
+      (cfg->mode != TPC_MODE_PLAIN && cfg->mode != TPC_MODE_BATCHED) || cfg->correction != TPC_CORR_NONE)
+    return TPC_ERR_INVALID_ARG;
+  if (cfg->allocator && (!cfg->allocator->alloc || !cfg->allocator->free)) return TPC_ERR_INVALID_ARG;
+  tpc_ctx* c = new tpc_ctx();
+  c->cfg = *cfg;
+  cudaError_t e = cudaSetDevice(cfg->device);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    return TPC_ERR_CUDA;
+  }
+  if (cfg->stream) {
+    c->stream = (cudaStream_t)cfg->stream;
+  } else {
+    if (cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking) != cudaSuccess) {
+      cudaGetLastError();
+      delete c;
+      return TPC_ERR_CUDA;
+    }
+    c->own_stream = true;
+  }
+  if (cfg->allocator) {
+    c->alloc = *cfg->allocator;
+    c->has_alloc = true;
+  }
+  // geometry table: rows at x_min + r*(x_max-x_min)/(n_rows-1), quantised to 2^-10 cm
+  DevParams& p = c->par;
+  p.n_rows = cfg->n_rows;
+  const double x0 = cfg->row_x_min, x1 = cfg->row_x_max;
+  for (int r = 0; r < cfg->n_rows; ++r) {
+    const double xr = x0 + r * ((x1 - x0) / (cfg->n_rows - 1));
+    p.qx[r] = (int)std::nearbyint(xr * 1024.0);
+    p.x[r] = (float)(p.qx[r] / 1024.0);
+  }
+  p.tan_half = (float)std::tan(cfg->sector_half_angle_deg * M_PI / 180.0);
+  p.vy = cfg->sigma_y * cfg->sigma_y;
+  p.vz = cfg->sigma_z * cfg->sigma_z;
+  p.kB = (float)(0.299792458e-2 * cfg->bz_tesla);
+  c->b.par = p;
+  int dev = cfg->device, sms = 148;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  LaunchCfg& L = c->lc;
+  L.n_rows = cfg->n_rows;
+  L.num_sms = sms;
+  L.sort_smem = 32 * 1024;
+  L.link_smem = 32 * 1024;
+  L.grid_scan = std::min(1024, 2 * sms);
+  L.block_tl = 128;
+  L.grid_tl = sms * 8;
+  if ((e = tpc_configure_kernels(L.sort_smem, L.link_smem)) != cudaSuccess) {
+    cudaGetLastError();
+    if (c->own_stream) cudaStreamDestroy(c->stream);
+    delete c;
+    return TPC_ERR_CUDA;
+  }
+  if (cfg->profile) {
+    for (int i = 0; i <= TPC_N_STAGES; ++i) cudaEventCreate(&c->ev[i]);
+    c->have_events = true;
+  }
+  if (cfg->max_clusters || cfg->max_items) {
+    tpc_status s = reserve(c, (long long)cfg->max_clusters, (long long)std::max<uint32_t>(1, cfg->max_items),
+                           (long long)cfg->max_clusters / 1024 + std::max<uint32_t>(1, cfg->max_items) + 1);
+    if (s != TPC_OK) {
+      tpc_destroy(c);
+      return s;
+    }
+  }
+  *out = c;
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
+  if (!c || !cl) return TPC_ERR_INVALID_ARG;
+  if (cl->n_items == 0 || !cl->item_off) return fail(c, TPC_ERR_INVALID_ARG, "need at least one item and item_off");
+  if (cl->n > 0 && (!cl->x || !cl->y || !cl->z || !cl->row)) return fail(c, TPC_ERR_INVALID_ARG, "null cluster array");
+  if (cl->n >= (1ull << 31) / 3) return fail(c, TPC_ERR_CAPACITY, "at most 715827882 clusters per batch");
+  if (cl->item_off[0] != 0 || cl->item_off[cl->n_items] != cl->n)
+    return fail(c, TPC_ERR_INVALID_ARG, "item_off must start at 0 and end at n");
+  for (uint32_t i = 0; i < cl->n_items; ++i)
+    if (cl->item_off[i + 1] < cl->item_off[i]) return fail(c, TPC_ERR_INVALID_ARG, "item_off not monotone");
+  if ((unsigned long long)cl->n_items * c->cfg.n_rows >= (1ull << 31) / 4)
+    return fail(c, TPC_ERR_CAPACITY, "too many items");
+  if (cl->item_core)
+    for (uint32_t i = 0; i < cl->n_items; ++i)
+      if (cl->item_core[2 * i] > cl->item_core[2 * i + 1]) return fail(c, TPC_ERR_INVALID_ARG, "item_core lo > hi");
+  cudaError_t e = cudaSetDevice(c->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  // work table of the cluster-parallel kernels: chunks of <= 1024 clusters, one item each
+  c->chunks.clear();
+  for (uint32_t i = 0; i < cl->n_items; ++i)
+    for (uint64_t a = cl->item_off[i]; a < cl->item_off[i + 1]; a += 1024)
+      c->chunks.push_back({(int)i, (int)a, (int)std::min<uint64_t>(a + 1024, cl->item_off[i + 1])});
+  if (c->chunks.empty()) c->chunks.push_back({0, 0, 0});
+  tpc_status s = reserve(c, (long long)cl->n, cl->n_items, (long long)c->chunks.size());
+  if (s != TPC_OK) return s;
+  Buffers& b = c->b;
+  b.N = (int)cl->n;
+  b.I = (int)cl->n_items;
+  b.n_chunks = (int)c->chunks.size();
+  const size_t n = cl->n;
+  // cluster arrays: device pointers are borrowed, host arrays copied into our buffers
+  if (cl->on_device) {
+    c->input_on_device = true;
+    c->b.x = cl->x;
+    c->b.y = cl->y;
+    c->b.z = cl->z;
+    c->b.row = cl->row;
+  } else {
+    c->b.x = c->own_x;
+    c->b.y = c->own_y;
+    c->b.z = c->own_z;
+    c->b.row = c->own_row;
+    c->input_on_device = false;
+    if (n) {
+      if ((e = cudaMemcpyAsync((void*)b.x, cl->x, 4 * n, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+          (e = cudaMemcpyAsync((void*)b.y, cl->y, 4 * n, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+          (e = cudaMemcpyAsync((void*)b.z, cl->z, 4 * n, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+          (e = cudaMemcpyAsync((void*)b.row, cl->row, 4 * n, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "cluster upload");
+    }
+  }
+  const size_t I = cl->n_items;
+  e = cudaMemcpyAsync((void*)b.item_off, cl->item_off, 8 * (I + 1), cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync((void*)b.chunks, c->chunks.data(), sizeof(Chunk) * c->chunks.size(), cudaMemcpyHostToDevice,
+                        c->stream);
+  // item metadata: optional arrays become null device pointers when absent
+  const int* core_dev = c->own_core;
+  const uint32_t* sec_dev = c->own_sec;
+  const uint32_t* ev_dev = c->own_ev;
+  b.item_core = cl->item_core ? core_dev : nullptr;
+  b.item_sector = cl->item_sector ? sec_dev : nullptr;
+  b.item_event = cl->item_event ? ev_dev : nullptr;
+  if (e == cudaSuccess && cl->item_core)
+    e = cudaMemcpyAsync((void*)core_dev, cl->item_core, 8 * I, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && cl->item_sector)
+    e = cudaMemcpyAsync((void*)sec_dev, cl->item_sector, 4 * I, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess && cl->item_event)
+    e = cudaMemcpyAsync((void*)ev_dev, cl->item_event, 4 * I, cudaMemcpyHostToDevice, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.err, 0, 16, c->stream);
+  if (e == cudaSuccess) e = cudaMemsetAsync(b.counts, 0, 32, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "metadata upload");
+  // host arrays must stay valid only during the call
+  if (!cl->on_device && (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
+  c->loaded = true;
+  c->tracked = false;
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_track(tpc_ctx* c) {
+  if (!c) return TPC_ERR_INVALID_ARG;
+  if (!c->loaded) return fail(c, TPC_ERR_STATE, "tpc_track before tpc_load_clusters");
+  cudaError_t e = cudaSetDevice(c->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  if (c->b.N == 0) {
+    c->tracked = true;
+    return TPC_OK;  // counts were zeroed at load
+  }
+  e = tpc_launch_plain(c->b, c->lc, c->stream, c->have_events ? c->ev : nullptr);
+  if (e != cudaSuccess) return cuda_fail(c, e, "launch");
+  c->tracked = true;
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_sync(tpc_ctx* c) {
+  if (!c) return TPC_ERR_INVALID_ARG;
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+  if (!c->loaded) return TPC_OK;
+  unsigned int err = 0;
+  e = cudaMemcpy(&err, c->b.err, 4, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "error word");
+  if (err & TPC_DERR_BAD_INPUT) return fail(c, TPC_ERR_BAD_INPUT, "a cluster has a bad row or a non-finite value");
+  if (err & TPC_DERR_ROW_CAP) return fail(c, TPC_ERR_CAPACITY, "row too large");
+  if (err & TPC_DERR_TIMEOUT) return fail(c, TPC_ERR_TIMEOUT, "device wait timed out");
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_get_tracks(tpc_ctx* c, tpc_track_t* trk, uint64_t trk_cap, uint32_t* ids, uint64_t id_cap,
+                                     uint64_t* n_trk, uint64_t* n_ids) {
+  if (!c) return TPC_ERR_INVALID_ARG;
+  if (!c->tracked) return fail(c, TPC_ERR_STATE, "tpc_get_tracks before tpc_track");
+  tpc_status s = tpc_sync(c);
+  if (s != TPC_OK) return s;
+  unsigned long long cnt[4] = {0, 0, 0, 0};
+  cudaError_t e = cudaMemcpy(cnt, c->b.counts, 32, cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_fail(c, e, "counts");
+  if (n_trk) *n_trk = cnt[0];
+  if (n_ids) *n_ids = cnt[1];
+  if (cnt[0] > trk_cap || cnt[1] > id_cap) return fail(c, TPC_ERR_CAPACITY, "output buffers too small");
+  if ((cnt[0] && !trk) || (cnt[1] && !ids)) return fail(c, TPC_ERR_INVALID_ARG, "null output buffer");
+  if (cnt[0] && (e = cudaMemcpy(trk, c->b.trk, sizeof(tpc_track_t) * cnt[0], cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(c, e, "track copy");
+  if (cnt[1] && (e = cudaMemcpy(ids, c->b.trk_ids, 4 * cnt[1], cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(c, e, "id copy");
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_device_tracks(tpc_ctx* c, const tpc_track_t** trk, const uint32_t** ids,
+                                        const uint64_t** counts) {
+  if (!c) return TPC_ERR_INVALID_ARG;
+  if (!c->loaded) return fail(c, TPC_ERR_STATE, "nothing loaded");
+  if (trk) *trk = (const tpc_track_t*)c->b.trk;
+  if (ids) *ids = c->b.trk_ids;
+  if (counts) *counts = (const uint64_t*)c->b.counts;
+  return TPC_OK;
+}
+
+static const char* kStageNames[TPC_N_STAGES] = {"quantise+row_stats", "row_setup",   "group_scatter",
+                                                "row_sort",           "links",       "clean+starts",
+                                                "tracklets",          "selection",   "output"};
+
+extern "C" const char* tpc_stage_name(int i) { return (i >= 0 && i < TPC_N_STAGES) ? kStageNames[i] : ""; }
+
+extern "C" tpc_status tpc_stage_times(tpc_ctx* c, float* us, int n, int* n_stages) {
+  if (!c) return TPC_ERR_INVALID_ARG;
+  if (n_stages) *n_stages = TPC_N_STAGES;
+  if (!c->have_events) return fail(c, TPC_ERR_STATE, "context created without profile = 1");
+  if (!c->tracked) return fail(c, TPC_ERR_STATE, "no tpc_track yet");
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "stream");
+  for (int i = 0; i < TPC_N_STAGES && i < n; ++i) {
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) != cudaSuccess) {
+      cudaGetLastError();
+      ms = 0.f;
+    }
+    us[i] = ms * 1000.f;
+  }
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_debug_dump(tpc_ctx* c, int stage, int32_t* buf, uint64_t cap, uint64_t* n_out) {
+  if (!c || !n_out) return TPC_ERR_INVALID_ARG;
+  if (!c->tracked) return fail(c, TPC_ERR_STATE, "no tpc_track yet");
+  tpc_status st = tpc_sync(c);
+  if (st != TPC_OK && st != TPC_ERR_BAD_INPUT) return st;
+  const Buffers& b = c->b;
+  const size_t N = b.N, NR = c->cfg.n_rows, M = (size_t)b.I * NR;
+  auto D2H = [&](std::vector<int>& v, const void* src, size_t n) {
+    v.resize(n);
+    return n ? cudaMemcpy(v.data(), src, 4 * n, cudaMemcpyDeviceToHost) : cudaSuccess;
+  };
+  std::vector<int> out, sid, tmp;
+  cudaError_t e = D2H(sid, b.s_id, N);
+  if (e != cudaSuccess) return cuda_fail(c, e, "dump");
+  std::vector<RowInfo> rows(M);
+  if (M && (e = cudaMemcpy(rows.data(), b.rows, sizeof(RowInfo) * M, cudaMemcpyDeviceToHost)) != cudaSuccess)
+    return cuda_fail(c, e, "dump");
+  int T = 0;
+  if ((e = cudaMemcpy(&T, b.start_ex + N, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(c, e, "dump");
+  switch (stage) {
+    case 0: {
+      std::vector<int> q;
+      if ((e = D2H(q, b.s_q, 2 * N)) != cudaSuccess) return cuda_fail(c, e, "dump");
+      out.resize(3 * N);
+      for (size_t i = 0; i < N; ++i) {
+        out[3 * i] = q[2 * i];
+        out[3 * i + 1] = q[2 * i + 1];
+        out[3 * i + 2] = sid[i];
+      }
+      break;
+    }
+    case 1:
+      for (const RowInfo& r : rows) {
+        const int v[7] = {r.pos0, r.n, r.ymin, r.zmin, r.shift, r.ny, r.nz};
+        out.insert(out.end(), v, v + 7);
+      }
+      break;
+    case 2: {
+      if ((e = D2H(tmp, b.first, 2 * N + 3 * M + 1)) != cudaSuccess) return cuda_fail(c, e, "dump");
+      for (const RowInfo& r : rows) {
+        const int nb = r.n > 0 ? r.ny * r.nz : 0;
+        for (int j = 0; j <= nb; ++j) out.push_back(tmp[r.bin0 + j] - r.pos0);
+      }
+      break;
+    }
+    case 3:
+    case 4:
+    case 5:
+    case 6: {
+      const int* src = stage == 3 ? b.up_raw : stage == 4 ? b.dn_raw : stage == 5 ? b.up : b.dn;
+      if ((e = D2H(tmp, src, N)) != cudaSuccess) return cuda_fail(c, e, "dump");
+      out.assign(N, -1);
+      for (size_t p = 0; p < N; ++p)
+        if (sid[p] >= 0 && (size_t)sid[p] < N) out[sid[p]] = (tmp[p] >= 0 && (size_t)tmp[p] < N) ? sid[tmp[p]] : -1;
+      break;
+    }
+    case 7: {
+      if ((e = D2H(tmp, b.starts, T)) != cudaSuccess) return cuda_fail(c, e, "dump");
+      for (int t = 0; t < T; ++t) out.push_back(sid[tmp[t]]);
+      break;
+    }
+    case 8:
+    case 9: {
+      std::vector<TrackletRec> tl(T);
+      if (T && (e = cudaMemcpy(tl.data(), b.tl, sizeof(TrackletRec) * T, cudaMemcpyDeviceToHost)) != cudaSuccess)
+        return cuda_fail(c, e, "dump");
+      if (stage == 8) {
+        for (int t = 0; t < T; ++t) out.push_back(tl[t].n);
+      } else {
+        if ((e = D2H(tmp, b.tl_hits, (size_t)T * NR)) != cudaSuccess) return cuda_fail(c, e, "dump");
+        for (int t = 0; t < T; ++t)
+          for (int k = 0; k < tl[t].n; ++k) out.push_back(sid[tmp[(size_t)t * NR + k]]);
+      }
+      break;
+    }
+    default:
+      return fail(c, TPC_ERR_INVALID_ARG, "unknown stage");
+  }
+  *n_out = out.size();
+  if (buf && cap) std::memcpy(buf, out.data(), 4 * std::min<size_t>(cap, out.size()));
+  if (cap < out.size()) return fail(c, TPC_ERR_CAPACITY, "dump buffer too small");
+  return TPC_OK;
+}
+
+extern "C" void tpc_destroy(tpc_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->cfg.device);
+  free_all(c);
+  if (c->have_events)
+    for (int i = 0; i <= TPC_N_STAGES; ++i) cudaEventDestroy(c->ev[i]);
+  if (c->own_stream) {
+    cudaStreamSynchronize(c->stream);
+    cudaStreamDestroy(c->stream);
+  }
+  cudaGetLastError();
+  delete c;
+}
+
+extern "C" const char* tpc_last_error(const tpc_ctx* c) { return c ? c->err.c_str() : "null context"; }

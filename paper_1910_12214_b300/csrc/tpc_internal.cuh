@@ -1,0 +1,119 @@
+// Internal device structures of libtpc (not part of the ABI).
+#pragma once
+#include <cstdint>
+
+#include <cuda_runtime.h>
+
+#define TPC_MAX_ROWS 256
+#define TPC_MAX_ROW_HITS 8192   // hits per (item,row) grid handled in shared memory
+#define TPC_QSCALE 1024.0f      // quanta per cm (Q = 2^-10 cm)
+
+// device error bits (OR-ed into a device word, read on the host)
+#define TPC_DERR_BAD_INPUT 1u
+#define TPC_DERR_ROW_CAP 2u
+#define TPC_DERR_TIMEOUT 4u
+
+// One (item, pad row) of the binning grid: 32 bytes, one load.
+struct RowInfo {
+  int pos0;   // first sorted position of the row (absolute)
+  int n;      // hits in the row
+  int ymin, zmin;
+  int shift;  // bin edge = 2^shift quanta
+  int ny, nz; // grid dimensions; nbins = ny*nz (0 for an empty row)
+  int bin0;   // index of the row's first entry in first[] (nbins+1 entries)
+};
+
+// Per tracklet result of the Kalman pass (the hit list lives in a separate
+// fixed-stride array of n_rows positions per tracklet).
+struct TrackletRec {
+  float p[5];   // y, z - z_base*Q, sinphi, tanlambda, q/pT at the innermost hit
+  float C[15];  // lower triangle
+  float chi2, x_ref;
+  int n;        // hits of the inward pass (0 = dropped)
+  int z_base;   // z origin of the state in quanta (start hit)
+  int z_in;     // z of the innermost hit in quanta
+  int item, local;
+  int pad;
+};
+
+struct DevParams {
+  int n_rows;
+  float tan_half;   // tan(sector half angle)
+  float vy, vz;     // measurement variances
+  float kB;         // curvature per unit q/pT [1/cm]
+  int qx[TPC_MAX_ROWS];
+  float x[TPC_MAX_ROWS];  // qx * Q
+};
+
+// Work table entry for cluster-parallel kernels: a CTA handles clusters
+// [begin, end) of one item.
+struct Chunk {
+  int item;
+  int begin;
+  int end;
+};
+
+struct Buffers {
+  DevParams par;  // geometry and filter constants (kernel argument, no global state)
+  // inputs (device)
+  const float *x, *y, *z;
+  const int* row;
+  const uint64_t* item_off;   // [I+1]
+  const int* item_core;       // [I][2] or null
+  const uint32_t* item_sector;
+  const uint32_t* item_event;
+  const Chunk* chunks;
+  int n_chunks;
+  int N, I;
+  // per cluster temporaries
+  int* cl_key;    // item*NR+row or -1
+  int2* cl_q;     // quantised (qy,qz)
+  // per (item,row)
+  int* rs_cnt;    // [I*NR]
+  int* rs_min;    // [4][I*NR]: ymin, -ymax, zmin, -zmax
+  int* row_fill;  // [I*NR]
+  RowInfo* rows;  // [I*NR]
+  // grouped (row-major, unsorted) and sorted hits
+  int2* g_q;
+  int* g_id;
+  int2* s_q;
+  int* s_id;
+  int* s_key;     // item*NR+row per sorted position
+  int* first;     // bins
+  // links
+  int* up_raw;
+  int* dn_raw;
+  int* up;
+  int* dn;
+  int* flags;     // start flags -> scan
+  int* start_ex;  // exclusive scan of flags [N+1]
+  int* starts;    // [T_cap]
+  // tracklets
+  int T_cap;
+  TrackletRec* tl;
+  int* tl_hits;   // [T_cap * NR]
+  unsigned long long* hit_key;  // [N]
+  unsigned long long* tl_cnt;   // packed (1<<32 | owned) per tracklet
+  unsigned long long* tl_ex;    // exclusive scan [T_cap+1]
+  // outputs
+  void* trk;      // tpc_track_t [T_cap]
+  uint32_t* trk_ids;  // [N]
+  unsigned long long* counts;  // [0] n_trk, [1] n_ids, [2] n_tracklets
+  unsigned int* err;
+  unsigned long long* scan_tmp;  // block sums
+};
+
+#define TPC_N_STAGES 9
+
+struct LaunchCfg {
+  int n_rows;
+  int num_sms;
+  int sort_smem;  // dynamic shared memory of k_row_sort
+  int link_smem;  // dynamic shared memory of k_links (two staged rows)
+  int grid_scan;  // blocks of the reduce-then-scan (<= 1024)
+  int grid_tl;    // blocks of k_tracklets
+  int block_tl;   // threads per block of k_tracklets
+};
+
+cudaError_t tpc_configure_kernels(int sort_smem, int link_smem);
+cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);

@@ -1,0 +1,1005 @@
+// CUDA kernels of the TPC sector tracker (sm_103a).
+//
+// Steps (one kernel each in plain mode; see tpc_capi.cu for the launch order):
+//   k_row_stats      quantise y,z to Q = 2^-10 cm, validate, per-(item,row) count
+//                    and extents (global atomics)
+//   k_row_setup      bin size, grid dims, row and bin offsets (block scans)
+//   k_group_scatter  counting sort of clusters into row-contiguous order
+//   k_row_sort       per row: bin histogram, scan, scatter, in-bin sort by id
+//                    (canonical order row, bin, original id) and first[] starts
+//   k_links          per hit of an inner row: best (up, down) pair (integer metric)
+//   k_clean_start    mutual-link cleaning and start-hit flags
+//   k_scan_*         device-wide exclusive scans (reduce-then-scan, fixed grid)
+//   k_tracklets      FP32 Kalman tracklet per start hit (chain fit, outward
+//                    extension, inward refit with hit re-picking)
+//   k_select_max/own shared-cluster resolution by 64-bit atomicMax keys
+//   k_output         track and cluster-id compaction
+//
+// The method follows the paper's TPC tracking (Sec. 3: cellular-automaton track
+// finding derived from the Run 2 HLT tracker, followed by a Kalman fit) under
+// the conditions of the Abstract (continuous read-out, no vertex constraint).
+// All discrete decisions before the fit are exact integer arithmetic on
+// quantised coordinates, so the result does not depend on thread order
+// (the ordering and rounding effects discussed in Sec. 3).
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "tpc.h"
+#include "tpc_internal.cuh"
+
+
+namespace {
+
+constexpr float CHI2_CUT = 16.0f;
+constexpr float WIN_MIN = 0.5f;
+constexpr int MAX_MISS = 5;
+constexpr float SIN_MAX = 0.93969262f;  // sin 70 deg: steeper segments are not fitted (Sec. 4)
+constexpr float SNP_LIMIT = 0.9999f;
+constexpr int MIN_HITS = 10;
+constexpr int SHIFT_MIN = 10;
+constexpr long long LINK_D = 512;       // 0.5 cm chord deviation
+
+__device__ __forceinline__ int warp_incl_scan(int v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_incl_scan64(unsigned long long v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned long long t = __shfl_up_sync(0xffffffffu, v, o);
+    if (lane >= o) v += t;
+  }
+  return v;
+}
+
+// Exclusive scan over the block; sm needs 33 ints.  All threads must call it.
+__device__ __forceinline__ int block_excl_scan(int v, int* sm, int* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  const int inc = warp_incl_scan(v);
+  if (lane == 31) sm[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const int s = lane < nw ? sm[lane] : 0;
+    const int si = warp_incl_scan(s);
+    if (lane < nw) sm[lane] = si - s;
+    if (lane == 31) sm[32] = si;
+  }
+  __syncthreads();
+  const int r = sm[w] + inc - v;
+  *total = sm[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long long v, unsigned long long* sm,
+                                                                unsigned long long* total) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nw = (blockDim.x + 31) >> 5;
+  const unsigned long long inc = warp_incl_scan64(v);
+  if (lane == 31) sm[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    const unsigned long long s = lane < nw ? sm[lane] : 0ull;
+    const unsigned long long si = warp_incl_scan64(s);
+    if (lane < nw) sm[lane] = si - s;
+    if (lane == 31) sm[32] = si;
+  }
+  __syncthreads();
+  const unsigned long long r = sm[w] + inc - v;
+  *total = sm[32];
+  __syncthreads();
+  return r;
+}
+
+}  // namespace
+
+// ============================================================================ S1
+// Quantise and validate; per-(item,row) count and extents.  rs_min holds four
+// planes: ymin, -ymax, zmin, -zmax (all atomicMin, initialised to 0x7F7F7F7F).
+__global__ void __launch_bounds__(256) k_row_stats(const __grid_constant__ Buffers b) {
+  const DevParams& P = b.par;
+  const Chunk ch = b.chunks[blockIdx.x];
+  const int NR = P.n_rows;
+  const int M = b.I * NR;
+  for (int i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) {
+    const float xv = b.x[i], yv = b.y[i], zv = b.z[i];
+    const int r = b.row[i];
+    const bool ok = r >= 0 && r < NR && fabsf(xv) < INFINITY && fabsf(yv) <= 1e6f && fabsf(zv) <= 1e6f;
+    if (!ok) {
+      atomicOr(b.err, TPC_DERR_BAD_INPUT);
+      b.cl_key[i] = -1;
+      continue;
+    }
+    // y*1024 is exact in FP32; round half to even
+    const int qy = __float2int_rn(yv * TPC_QSCALE);
+    const int qz = __float2int_rn(zv * TPC_QSCALE);
+    const int k = ch.item * NR + r;
+    b.cl_key[i] = k;
+    b.cl_q[i] = make_int2(qy, qz);
+    atomicAdd(&b.rs_cnt[k], 1);
+    atomicMin(&b.rs_min[k], qy);
+    atomicMin(&b.rs_min[M + k], -qy);
+    atomicMin(&b.rs_min[2 * M + k], qz);
+    atomicMin(&b.rs_min[3 * M + k], -qz);
+  }
+}
+
+// ============================================================================ S2a
+// Per row: bin edge 2^s quanta with s the smallest s >= 10 such that
+// n*4^s >= Ly*Lz (about one hit per bin) and ny*nz <= 2n+2 (bounded grid).
+// Row and bin offsets inside the item come from block scans; the item's bin
+// space starts at 2*item_off + 3*n_rows*item (closed form of the bound).
+__global__ void __launch_bounds__(256) k_row_setup(const __grid_constant__ Buffers b) {
+  const DevParams& P = b.par;
+  __shared__ int sm[33];
+  const int item = blockIdx.x, NR = P.n_rows, M = b.I * NR;
+  const int r = threadIdx.x;
+  int n = 0, ymin = 0, zmin = 0, s = SHIFT_MIN, ny = 0, nz = 0;
+  if (r < NR) {
+    const int k = item * NR + r;
+    n = b.rs_cnt[k];
+    if (n > 0) {
+      ymin = b.rs_min[k];
+      const int ymax = -b.rs_min[M + k];
+      zmin = b.rs_min[2 * M + k];
+      const int zmax = -b.rs_min[3 * M + k];
+      const long long dy = (long long)ymax - ymin, dz = (long long)zmax - zmin;
+      const long long area = (dy + 1) * (dz + 1);
+      const long long need = (area + n - 1) / n;  // n*4^s >= area  <=>  4^s >= ceil(area/n)
+      for (;; ++s) {
+        const long long nyy = (dy >> s) + 1, nzz = (dz >> s) + 1;
+        const bool dense = (2 * s >= 63) || ((1ll << (2 * s)) >= need);
+        if (dense && nyy * nzz <= 2ll * n + 2) {
+          ny = (int)nyy;
+          nz = (int)nzz;
+          break;
+        }
+      }
+    }
+  }
+  const int nb = n > 0 ? ny * nz : 0;
+  int tot;
+  const int pos_ex = block_excl_scan(n, sm, &tot);
+  const int bin_ex = block_excl_scan(r < NR ? nb + 1 : 0, sm, &tot);
+  if (r < NR) {
+    const long long off = (long long)b.item_off[item];
+    RowInfo ri;
+    ri.pos0 = (int)off + pos_ex;
+    ri.n = n;
+    ri.ymin = ymin;
+    ri.zmin = zmin;
+    ri.shift = s;
+    ri.ny = ny;
+    ri.nz = nz;
+    ri.bin0 = (int)(2 * off) + 3 * NR * item + bin_ex;
+    b.rows[item * NR + r] = ri;
+  }
+}
+
+// ============================================================================ S2b
+// Counting sort into row-contiguous order (order inside a row is arbitrary here;
+// k_row_sort makes it canonical).
+__global__ void __launch_bounds__(256) k_group_scatter(const __grid_constant__ Buffers b) {
+  const Chunk ch = b.chunks[blockIdx.x];
+  for (int i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) {
+    const int k = b.cl_key[i];
+    if (k < 0) continue;
+    const int slot = atomicAdd(&b.row_fill[k], 1);
+    const int gp = b.rows[k].pos0 + slot;
+    b.g_q[gp] = b.cl_q[i];
+    b.g_id[gp] = i;
+  }
+}
+
+// ============================================================================ S2c
+// One CTA per (item,row).  Rows that fit the dynamic shared-memory budget are
+// sorted in shared memory; larger rows use the same code on global scratch
+// (tq/tid/tslot) with the row's own first[] entries as the histogram.
+__global__ void __launch_bounds__(128) k_row_sort(const __grid_constant__ Buffers b, int smem_bytes, int2* tq, int* tid_buf, int* tslot) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int sm[33];
+  const int k = blockIdx.x;
+  const RowInfo ri = b.rows[k];
+  const int n = ri.n;
+  if (n == 0) {
+    if (threadIdx.x == 0) b.first[ri.bin0] = ri.pos0;
+    return;
+  }
+  const int nb = ri.ny * ri.nz;
+  const long long need = 12ll * n + 4ll * n + 4ll * (nb + 1);
+  int2* q2;
+  int* id2;
+  int* slot;
+  int* hist;
+  if (need <= smem_bytes) {
+    q2 = reinterpret_cast<int2*>(smem_raw);
+    id2 = reinterpret_cast<int*>(q2 + n);
+    slot = id2 + n;
+    hist = slot + n;
+  } else {
+    q2 = tq + ri.pos0;
+    id2 = tid_buf + ri.pos0;
+    slot = tslot + ri.pos0;
+    hist = b.first + ri.bin0;
+  }
+  for (int j = threadIdx.x; j <= nb; j += blockDim.x) hist[j] = 0;
+  __syncthreads();
+  const int s = ri.shift;
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int2 q = b.g_q[ri.pos0 + j];
+    const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
+    slot[j] = atomicAdd(&hist[bin], 1);
+  }
+  __syncthreads();
+  // exclusive scan of hist[0..nb] in place, chunk by chunk
+  int carry = 0;
+  for (int base = 0; base <= nb; base += blockDim.x) {
+    const int j = base + threadIdx.x;
+    const int v = j <= nb ? hist[j] : 0;
+    int tot;
+    const int ex = block_excl_scan(v, sm, &tot);
+    if (j <= nb) hist[j] = carry + ex;
+    carry += tot;
+    __syncthreads();
+  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    const int2 q = b.g_q[ri.pos0 + j];
+    const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
+    const int p = hist[bin] + slot[j];
+    q2[p] = q;
+    id2[p] = b.g_id[ri.pos0 + j];
+  }
+  __syncthreads();
+  // canonical order inside a bin: original id (insertion sort; bins hold a few hits)
+  for (int bin = threadIdx.x; bin < nb; bin += blockDim.x) {
+    const int a = hist[bin], e = hist[bin + 1];
+    for (int i = a + 1; i < e; ++i) {
+      const int2 qv = q2[i];
+      const int iv = id2[i];
+      int j = i - 1;
+      while (j >= a && id2[j] > iv) {
+        q2[j + 1] = q2[j];
+        id2[j + 1] = id2[j];
+        --j;
+      }
+      q2[j + 1] = qv;
+      id2[j + 1] = iv;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+    b.s_q[ri.pos0 + j] = q2[j];
+    b.s_id[ri.pos0 + j] = id2[j];
+    b.s_key[ri.pos0 + j] = k;
+  }
+  if (hist != b.first + ri.bin0) {
+    for (int j = threadIdx.x; j <= nb; j += blockDim.x) b.first[ri.bin0 + j] = ri.pos0 + hist[j];
+  } else {
+    __syncthreads();
+    for (int j = threadIdx.x; j <= nb; j += blockDim.x) b.first[ri.bin0 + j] += ri.pos0;
+  }
+}
+
+// ============================================================================ S3
+namespace {
+struct RowView {  // a row's hits and bin starts, staged in shared memory or global
+  const int2* q;     // indexed by position - pos0
+  const int* id;
+  const int* first;  // absolute positions, nbins+1
+  RowInfo ri;
+};
+
+__device__ __forceinline__ void stage_row(RowView& v, const Buffers& b, const RowInfo& ri, unsigned char* sm,
+                                          int budget) {
+  v.ri = ri;
+  const int nb = ri.n > 0 ? ri.ny * ri.nz : 0;
+  const long long need = 12ll * ri.n + 4ll * (nb + 1);
+  if (ri.n > 0 && need <= budget) {
+    int2* q = reinterpret_cast<int2*>(sm);
+    int* id = reinterpret_cast<int*>(q + ri.n);
+    int* f = id + ri.n;
+    for (int j = threadIdx.x; j < ri.n; j += blockDim.x) {
+      q[j] = b.s_q[ri.pos0 + j];
+      id[j] = b.s_id[ri.pos0 + j];
+    }
+    for (int j = threadIdx.x; j <= nb; j += blockDim.x) f[j] = b.first[ri.bin0 + j];
+    v.q = q;
+    v.id = id;
+    v.first = f;
+  } else {
+    v.q = b.s_q + ri.pos0;
+    v.id = b.s_id + ri.pos0;
+    v.first = b.first + ri.bin0;
+  }
+}
+
+// bin range of [lo, hi] along one axis; empty if hi < lo
+__device__ __forceinline__ void bin_range(long long lo, long long hi, int vmin, int shift, int nbin, int* a,
+                                          int* e) {
+  if (hi < vmin || nbin == 0) {
+    *a = 0;
+    *e = -1;
+    return;
+  }
+  const long long vmax = (long long)vmin + ((long long)nbin << shift) - 1;
+  if (lo > vmax) {
+    *a = 0;
+    *e = -1;
+    return;
+  }
+  *a = lo <= vmin ? 0 : (int)((lo - vmin) >> shift);
+  const long long t = (hi - vmin) >> shift;
+  *e = t < nbin - 1 ? (int)t : nbin - 1;
+}
+}  // namespace
+
+// One CTA per (item,row): for every hit h of an inner row, the pair (u on r+1,
+// d on r-1) inside the windows |dqy| <= 11*dqx/4, |dqz| <= 11*dqx/10 that
+// minimises m = dY^2 + dZ^2, dY = (qy_u-qy_h)*dx_dn - (qy_h-qy_d)*dx_up (int64),
+// accepted if m <= ((dx_up+dx_dn)*512)^2; ties: smaller id_u, then smaller id_d.
+// Rows 0 and n_rows-1 get no links (targets only).
+__global__ void __launch_bounds__(128) k_links(const __grid_constant__ Buffers b, int smem_bytes) {
+  const DevParams& P = b.par;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int k = blockIdx.x;
+  const int NR = P.n_rows;
+  const int r = k % NR;
+  const RowInfo rh = b.rows[k];
+  if (rh.n == 0) return;
+  if (r == 0 || r == NR - 1) {
+    for (int j = threadIdx.x; j < rh.n; j += blockDim.x) {
+      b.up_raw[rh.pos0 + j] = -1;
+      b.dn_raw[rh.pos0 + j] = -1;
+    }
+    return;
+  }
+  RowView U, D;
+  stage_row(U, b, b.rows[k + 1], smem_raw, smem_bytes / 2);
+  stage_row(D, b, b.rows[k - 1], smem_raw + smem_bytes / 2, smem_bytes / 2);
+  __syncthreads();
+  const long long dxu = P.qx[r + 1] - P.qx[r];
+  const long long dxd = P.qx[r] - P.qx[r - 1];
+  const long long wyu = dxu * 11 / 4, wzu = dxu * 11 / 10;
+  const long long wyd = dxd * 11 / 4, wzd = dxd * 11 / 10;
+  const long long cut = (dxu + dxd) * LINK_D;
+  const long long cut2 = cut * cut;
+  for (int j = threadIdx.x; j < rh.n; j += blockDim.x) {
+    const int pos = rh.pos0 + j;
+    const int2 qh = b.s_q[pos];
+    const long long yh = qh.x, zh = qh.y;
+    long long best = -1;
+    int bu = -1, bd = -1, bid_u = 0, bid_d = 0;
+    int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
+    bin_range(yh - wyu, yh + wyu, U.ri.ymin, U.ri.shift, U.ri.ny, &uy0, &uy1);
+    bin_range(zh - wzu, zh + wzu, U.ri.zmin, U.ri.shift, U.ri.nz, &uz0, &uz1);
+    bin_range(yh - wyd, yh + wyd, D.ri.ymin, D.ri.shift, D.ri.ny, &dy0, &dy1);
+    bin_range(zh - wzd, zh + wzd, D.ri.zmin, D.ri.shift, D.ri.nz, &dz0, &dz1);
+    for (int iy = uy0; iy <= uy1; ++iy)
+      for (int iz = uz0; iz <= uz1; ++iz) {
+        const int bu_ = iy * U.ri.nz + iz;
+        for (int pu = U.first[bu_]; pu < U.first[bu_ + 1]; ++pu) {
+          const int2 qu = U.q[pu - U.ri.pos0];
+          const long long ey = qu.x - yh, ez = qu.y - zh;
+          if (ey > wyu || -ey > wyu || ez > wzu || -ez > wzu) continue;
+          const int idu = U.id[pu - U.ri.pos0];
+          for (int jy = dy0; jy <= dy1; ++jy)
+            for (int jz = dz0; jz <= dz1; ++jz) {
+              const int bd_ = jy * D.ri.nz + jz;
+              for (int pd = D.first[bd_]; pd < D.first[bd_ + 1]; ++pd) {
+                const int2 qd = D.q[pd - D.ri.pos0];
+                const long long fy = yh - qd.x, fz = zh - qd.y;
+                if (fy > wyd || -fy > wyd || fz > wzd || -fz > wzd) continue;
+                const long long dY = ey * dxd - fy * dxu;
+                const long long dZ = ez * dxd - fz * dxu;
+                const long long m = dY * dY + dZ * dZ;
+                if (m > cut2) continue;
+                const int idd = D.id[pd - D.ri.pos0];
+                bool better = best < 0 || m < best;
+                if (!better && m == best) better = idu < bid_u || (idu == bid_u && idd < bid_d);
+                if (better) {
+                  best = m;
+                  bu = pu;
+                  bd = pd;
+                  bid_u = idu;
+                  bid_d = idd;
+                }
+              }
+            }
+        }
+      }
+    b.up_raw[pos] = bu;
+    b.dn_raw[pos] = bd;
+  }
+}
+
+// ============================================================================ S4+S5
+// Mutual links only (reads the raw arrays only); start hit = clean up link, no
+// clean down link, chain of >= 3 hits.
+__global__ void __launch_bounds__(256) k_clean_start(const __grid_constant__ Buffers b) {
+  for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < b.N; pos += gridDim.x * blockDim.x) {
+    const int u = b.up_raw[pos], d = b.dn_raw[pos];
+    const int cu = (u >= 0 && b.dn_raw[u] == pos) ? u : -1;
+    const int cd = (d >= 0 && b.up_raw[d] == pos) ? d : -1;
+    b.up[pos] = cu;
+    b.dn[pos] = cd;
+    int start = 0;
+    if (cu >= 0 && cd < 0) {
+      const int u2 = b.up_raw[cu];
+      start = (u2 >= 0 && b.dn_raw[u2] == cu) ? 1 : 0;
+    }
+    b.flags[pos] = start;
+  }
+}
+
+// ============================================================================ scans
+// Reduce-then-scan over n values (n from the host or from a device word) with a
+// fixed grid: block g owns a contiguous range; bsum gets per-block totals.
+template <typename T>
+__global__ void __launch_bounds__(256) k_scan_reduce(const T* in, const int* n_dev, long long n_host, T* bsum) {
+  const long long n = n_dev ? (long long)*n_dev : n_host;
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long a = blockIdx.x * per, e = a + per < n ? a + per : n;
+  T s = 0;
+  for (long long i = a + threadIdx.x; i < e; i += blockDim.x) s += in[i];
+  __shared__ T red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = red[0];
+}
+
+template <typename T>
+__global__ void __launch_bounds__(1024) k_scan_bsums(T* bsum, int nb) {
+  // nb <= 1024: one element per thread; exclusive, total in bsum[nb]
+  __shared__ T sm[1024];
+  const int t = threadIdx.x;
+  sm[t] = t < nb ? bsum[t] : 0;
+  __syncthreads();
+  for (int o = 1; o < 1024; o <<= 1) {
+    const T v = t >= o ? sm[t - o] : 0;
+    __syncthreads();
+    sm[t] += v;
+    __syncthreads();
+  }
+  if (t < nb) bsum[t] = t ? sm[t - 1] : 0;
+  if (t == nb - 1) bsum[nb] = sm[t];
+}
+
+__global__ void __launch_bounds__(256) k_scan_final_i32(const int* in, int* out, const int* n_dev, long long n_host,
+                                                        const unsigned long long* bsum) {
+  __shared__ int sm[33];
+  const long long n = n_dev ? (long long)*n_dev : n_host;
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long a = blockIdx.x * per, e = a + per < n ? a + per : n;
+  int carry = (int)bsum[blockIdx.x];
+  for (long long base = a; base < e; base += blockDim.x) {
+    const long long i = base + threadIdx.x;
+    const int v = i < e ? in[i] : 0;
+    int tot;
+    const int ex = block_excl_scan(v, sm, &tot);
+    if (i < e) out[i] = carry + ex;
+    carry += tot;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = (int)bsum[gridDim.x];
+}
+
+__global__ void __launch_bounds__(256) k_scan_final_u64(const unsigned long long* in, unsigned long long* out,
+                                                        const int* n_dev, long long n_host,
+                                                        const unsigned long long* bsum) {
+  __shared__ unsigned long long sm[33];
+  const long long n = n_dev ? (long long)*n_dev : n_host;
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long a = blockIdx.x * per, e = a + per < n ? a + per : n;
+  unsigned long long carry = bsum[blockIdx.x];
+  for (long long base = a; base < e; base += blockDim.x) {
+    const long long i = base + threadIdx.x;
+    const unsigned long long v = i < e ? in[i] : 0ull;
+    unsigned long long tot;
+    const unsigned long long ex = block_excl_scan64(v, sm, &tot);
+    if (i < e) out[i] = carry + ex;
+    carry += tot;
+  }
+  if (blockIdx.x == gridDim.x - 1 && threadIdx.x == 0) out[n] = bsum[gridDim.x];
+}
+
+// int flags summed into 64-bit block sums
+__global__ void __launch_bounds__(256) k_scan_reduce_i32(const int* in, long long n, unsigned long long* bsum) {
+  const long long per = (n + gridDim.x - 1) / gridDim.x;
+  const long long a = blockIdx.x * per, e = a + per < n ? a + per : n;
+  unsigned long long s = 0;
+  for (long long i = a + threadIdx.x; i < e; i += blockDim.x) s += (unsigned long long)in[i];
+  __shared__ unsigned long long red[256];
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int o = 128; o > 0; o >>= 1) {
+    if (threadIdx.x < o) red[threadIdx.x] += red[threadIdx.x + o];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) bsum[blockIdx.x] = red[0];
+}
+
+template __global__ void k_scan_reduce<unsigned long long>(const unsigned long long*, const int*, long long,
+                                                           unsigned long long*);
+template __global__ void k_scan_bsums<unsigned long long>(unsigned long long*, int);
+
+__global__ void __launch_bounds__(256) k_starts(const __grid_constant__ Buffers b) {
+  for (int pos = blockIdx.x * blockDim.x + threadIdx.x; pos < b.N; pos += gridDim.x * blockDim.x)
+    if (b.flags[pos]) b.starts[b.start_ex[pos]] = pos;
+}
+
+// ============================================================================ S6
+namespace {
+// packed lower triangle index
+__device__ __forceinline__ constexpr int ix(int i, int j) { return i * (i + 1) / 2 + j; }
+
+__device__ __forceinline__ float asin_over_u(float u) {
+  if (fabsf(u) < 0.1f) {
+    const float u2 = u * u;
+    return 1.0f + u2 * (1.0f / 6.0f + u2 * (3.0f / 40.0f + u2 * (5.0f / 112.0f)));
+  }
+  return asinf(u) / u;
+}
+
+__device__ __forceinline__ float d_asin_over_u(float u) {
+  if (fabsf(u) < 0.1f) {
+    const float u2 = u * u;
+    return u * (1.0f / 3.0f + u2 * (3.0f / 10.0f + u2 * (15.0f / 56.0f + u2 * (35.0f / 144.0f))));
+  }
+  return (u / sqrtf(1.0f - u * u) - asinf(u)) / (u * u);
+}
+
+// Helix step of (y, z, sinphi, tanlambda, q/pT) and covariance transport C <- F C F^T.
+// F differs from the identity in F02, F04, F12, F13, F14, F24 only.
+__device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float* C, float x1, float x2) {
+  const float kB = P.kB;
+  const float dx = x2 - x1;
+  const float s1 = p[2];
+  const float kappa = kB * p[4];
+  const float s2 = s1 - kappa * dx;
+  if (!(fabsf(s1) < SNP_LIMIT) || !(fabsf(s2) < SNP_LIMIT)) return false;
+  const float c1 = sqrtf((1.0f - s1) * (1.0f + s1));
+  const float c2 = sqrtf((1.0f - s2) * (1.0f + s2));
+  const float T = (s1 + s2) / (c1 + c2);
+  const float w = sqrtf(1.0f + T * T);
+  const float adx = fabsf(dx);
+  const float u = 0.5f * kappa * adx * w;
+  if (!(fabsf(u) < 1.0f)) return false;
+  const float f = asin_over_u(u);
+  const float fp = d_asin_over_u(u);
+  const float ell = dx * w * f;
+  const float num = 1.0f + c1 * c2 + s1 * s2;
+  const float cc = c1 + c2;
+  const float den = cc * cc;
+  const float A1 = num / (c1 * den), A2 = num / (c2 * den);
+  const float dT_ds = A1 + A2;
+  const float dT_dq = -A2 * kB * dx;
+  const float dg_dT = (T / w) * (f + u * fp);
+  const float dg_dk = 0.5f * w * w * adx * fp;
+  const float tgl = p[3];
+  const float a = dx * dT_ds;                          // F02
+  const float bq = dx * dT_dq;                         // F04
+  const float c = tgl * dx * dg_dT * dT_ds;            // F12
+  const float d = ell;                                 // F13
+  const float e = tgl * dx * (dg_dT * dT_dq + dg_dk * kB);  // F14
+  const float g = -kB * dx;                            // F24
+  p[0] += dx * T;
+  p[1] += tgl * ell;
+  p[2] = s2;
+  // full symmetric copy
+  float M[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      M[i][j] = C[ix(i, j)];
+      M[j][i] = C[ix(i, j)];
+    }
+  // v_j = C F_j^T for the three non-trivial rows of F
+  float v0[5], v1[5], v2[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    v0[i] = M[i][0] + a * M[i][2] + bq * M[i][4];
+    v1[i] = M[i][1] + c * M[i][2] + d * M[i][3] + e * M[i][4];
+    v2[i] = M[i][2] + g * M[i][4];
+  }
+  C[ix(0, 0)] = v0[0] + a * v0[2] + bq * v0[4];
+  C[ix(1, 0)] = v0[1] + c * v0[2] + d * v0[3] + e * v0[4];
+  C[ix(1, 1)] = v1[1] + c * v1[2] + d * v1[3] + e * v1[4];
+  C[ix(2, 0)] = v0[2] + g * v0[4];
+  C[ix(2, 1)] = v1[2] + g * v1[4];
+  C[ix(2, 2)] = v2[2] + g * v2[4];
+  C[ix(3, 0)] = v0[3];
+  C[ix(3, 1)] = v1[3];
+  C[ix(3, 2)] = v2[3];
+  C[ix(4, 0)] = v0[4];
+  C[ix(4, 1)] = v1[4];
+  C[ix(4, 2)] = v2[4];
+  // (3,3), (4,3), (4,4) unchanged
+  return true;
+}
+
+// Kalman update with H = [I2 0]; residuals (r0, r1); returns the chi2 increment.
+__device__ __forceinline__ float kf_update(const DevParams& P, float* p, float* C, float r0, float r1) {
+  const float S00 = C[ix(0, 0)] + P.vy, S01 = C[ix(1, 0)], S11 = C[ix(1, 1)] + P.vz;
+  const float det = S00 * S11 - S01 * S01;
+  const float I00 = S11 / det, I01 = -S01 / det, I11 = S00 / det;
+  // columns 0 and 1 of the symmetric covariance
+  float c0[5], c1[5], K0[5], K1[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) c0[i] = C[ix(i, 0)];
+  c1[0] = C[ix(1, 0)];
+#pragma unroll
+  for (int i = 1; i < 5; ++i) c1[i] = C[ix(i, 1)];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    K0[i] = c0[i] * I00 + c1[i] * I01;
+    K1[i] = c0[i] * I01 + c1[i] * I11;
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) p[i] += K0[i] * r0 + K1[i] * r1;
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) C[ix(i, j)] -= K0[i] * c0[j] + K1[i] * c1[j];
+  return r0 * (I00 * r0 + I01 * r1) + r1 * (I01 * r0 + I11 * r1);
+}
+
+__device__ __forceinline__ bool cov_ok(const float* C) {
+  bool ok = true;
+#pragma unroll
+  for (int i = 0; i < 15; ++i) ok &= fabsf(C[i]) < INFINITY;
+  ok &= C[ix(0, 0)] > 0.f && C[ix(1, 1)] > 0.f && C[ix(2, 2)] > 0.f && C[ix(3, 3)] > 0.f && C[ix(4, 4)] > 0.f;
+  return ok;
+}
+
+__device__ __forceinline__ void set_c0(const DevParams& P, float* C) {
+#pragma unroll
+  for (int i = 0; i < 15; ++i) C[i] = 0.f;
+  C[ix(0, 0)] = P.vy;
+  C[ix(1, 1)] = P.vz;
+  C[ix(2, 2)] = 1.0f;
+  C[ix(3, 3)] = 1.0f;
+  C[ix(4, 4)] = 100.0f;
+}
+
+// Best hit of row r for the predicted state: smallest chi2 <= 16, ties to the
+// smaller original id.  The search box (max(0.5 cm, 4 sigma) plus 2 quanta)
+// contains every hit with chi2 <= 16, so the box never changes the result.
+__device__ __forceinline__ int pick_hit(const Buffers& b, int item, int r, const float* p, const float* C, int z_base,
+                                        float* chi2_out) {
+  const DevParams& P = b.par;
+  const RowInfo ri = b.rows[item * P.n_rows + r];
+  if (ri.n == 0) return -1;
+  const float S00 = C[ix(0, 0)] + P.vy, S01 = C[ix(1, 0)], S11 = C[ix(1, 1)] + P.vz;
+  const float det = S00 * S11 - S01 * S01;
+  const float wy = fmaxf(WIN_MIN, 4.0f * sqrtf(S00));
+  const float wz = fmaxf(WIN_MIN, 4.0f * sqrtf(S11));
+  const float lim = 1.0e9f;
+  const long long ylo = (long long)floorf(fmaxf(-lim, (p[0] - wy) * TPC_QSCALE)) - 2;
+  const long long yhi = (long long)ceilf(fminf(lim, (p[0] + wy) * TPC_QSCALE)) + 2;
+  const long long zlo = (long long)floorf(fmaxf(-lim, (p[1] - wz) * TPC_QSCALE)) - 2 + z_base;
+  const long long zhi = (long long)ceilf(fminf(lim, (p[1] + wz) * TPC_QSCALE)) + 2 + z_base;
+  int iy0, iy1, iz0, iz1;
+  bin_range(ylo, yhi, ri.ymin, ri.shift, ri.ny, &iy0, &iy1);
+  bin_range(zlo, zhi, ri.zmin, ri.shift, ri.nz, &iz0, &iz1);
+  const float Q = 1.0f / TPC_QSCALE;
+  int best = -1, bid = 0;
+  float bchi = 0.f;
+  for (int iy = iy0; iy <= iy1; ++iy)
+    for (int iz = iz0; iz <= iz1; ++iz) {
+      const int bb = ri.bin0 + iy * ri.nz + iz;
+      const int a = b.first[bb], e = b.first[bb + 1];
+      for (int h = a; h < e; ++h) {
+        const int2 q = b.s_q[h];
+        const float dy = (float)q.x * Q - p[0];
+        const float dz = (float)(q.y - z_base) * Q - p[1];
+        const float chi2 = (S11 * dy * dy - 2.0f * S01 * dy * dz + S00 * dz * dz) / det;
+        if (!(chi2 <= CHI2_CUT)) continue;
+        const int id = b.s_id[h];
+        if (best < 0 || chi2 < bchi || (chi2 == bchi && id < bid)) {
+          best = h;
+          bid = id;
+          bchi = chi2;
+        }
+      }
+    }
+  *chi2_out = bchi;
+  return best;
+}
+}  // namespace
+
+// One thread per tracklet (grid-stride over the device count of start hits):
+//  (i)   circle through the first, middle and last chain hits -> initial state;
+//        Kalman fit along the chain (chain hits accepted without a chi2 test);
+//  (ii)  outward extension: best hit with chi2 <= 16, 5 consecutive misses end it;
+//  (iii) fresh inward fit from the outermost hit (its y, z; outward sinphi,
+//        tanlambda, q/pT; initial covariance), re-picking hits down to row 0.
+// Guards end a pass: |sinphi| >= sin 70 deg, |y| > x tan(half angle), invalid
+// step.  A non-finite or non-positive covariance diagonal drops the tracklet.
+// z is carried relative to the start hit (z_base) so that FP32 keeps its
+// precision for time-frame z' of thousands of cm.
+__global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Buffers b) {
+  const DevParams& P = b.par;
+  const int T = b.start_ex[b.N];
+  const int NR = P.n_rows;
+  const float Q = 1.0f / TPC_QSCALE;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    TrackletRec rec;
+    rec.n = 0;
+    const int start = b.starts[t];
+    const int key = b.s_key[start];
+    const int item = key / NR;
+    const int r0 = key - item * NR;
+    rec.item = item;
+    rec.local = t - b.start_ex[b.item_off[item]];
+    int* hl = b.tl_hits + (size_t)t * NR;
+    int L = 0;
+    for (int h = start; h >= 0 && L < NR; h = b.up[h]) hl[L++] = h;
+    const int z_base = b.s_q[start].y;
+    rec.z_base = z_base;
+    const int2 qa = b.s_q[hl[0]], qm = b.s_q[hl[L / 2]], qc = b.s_q[hl[L - 1]];
+    const float x1 = P.x[r0], x2 = P.x[r0 + L / 2], x3 = P.x[r0 + L - 1];
+    const float y1 = qa.x * Q, y2 = qm.x * Q, y3 = qc.x * Q;
+    const float z3 = (float)(qc.y - z_base) * Q;
+    const float dx13 = x3 - x1, dy13 = y3 - y1;
+    const float d13 = sqrtf(dx13 * dx13 + dy13 * dy13);
+    const float d12 = sqrtf((x2 - x1) * (x2 - x1) + (y2 - y1) * (y2 - y1));
+    const float d23 = sqrtf((x3 - x2) * (x3 - x2) + (y3 - y2) * (y3 - y2));
+    const float cross = (x2 - x1) * (y3 - y1) - (y2 - y1) * (x3 - x1);
+    const float kappa = -2.0f * cross / (d12 * d23 * d13);
+    const float u = fminf(1.0f, fmaxf(-1.0f, 0.5f * kappa * d13));
+    const float phi1 = atan2f(dy13, dx13) + asinf(u);
+    const float arc = d13 * asin_over_u(u);
+    float p[5] = {y1, 0.0f, sinf(phi1), z3 / arc, kappa / P.kB};
+    float C[15];
+    set_c0(P, C);
+    float x = x1;
+    int out_row = r0, out_hit = start;
+    float out_p[5] = {p[0], p[1], p[2], p[3], p[4]};
+    bool alive = true, dead = false;
+    // (i) chain
+    for (int i = 1; i < L; ++i) {
+      const int r = r0 + i;
+      if (!kf_propagate(P, p, C, x, P.x[r])) { alive = false; break; }
+      x = P.x[r];
+      if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) { alive = false; break; }
+      const int h = hl[i];
+      const int2 q = b.s_q[h];
+      kf_update(P, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
+      if (!cov_ok(C)) { dead = true; break; }
+      out_row = r;
+      out_hit = h;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) out_p[m] = p[m];
+    }
+    // (ii) outward extension
+    if (alive && !dead) {
+      int misses = 0;
+      for (int r = out_row + 1; r < NR && misses < MAX_MISS; ++r) {
+        if (!kf_propagate(P, p, C, x, P.x[r])) break;
+        x = P.x[r];
+        if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) break;
+        float chi2;
+        const int h = pick_hit(b, item, r, p, C, z_base, &chi2);
+        if (h < 0) { ++misses; continue; }
+        const int2 q = b.s_q[h];
+        kf_update(P, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
+        if (!cov_ok(C)) { dead = true; break; }
+        misses = 0;
+        out_row = r;
+        out_hit = h;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) out_p[m] = p[m];
+      }
+    }
+    if (!dead) {
+      // (iii) inward refit from the outermost hit
+      const int2 qo = b.s_q[out_hit];
+      float q5[5] = {qo.x * Q, (float)(qo.y - z_base) * Q, out_p[2], out_p[3], out_p[4]};
+      set_c0(P, C);
+      x = P.x[out_row];
+      hl[0] = out_hit;
+      int n = 1;
+      float chi2sum = 0.f;
+      float in_p[5], in_C[15], in_x = x;
+      int in_hit = out_hit;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) in_p[m] = q5[m];
+#pragma unroll
+      for (int m = 0; m < 15; ++m) in_C[m] = C[m];
+      int misses = 0;
+      for (int r = out_row - 1; r >= 0 && misses < MAX_MISS; --r) {
+        if (!kf_propagate(P, q5, C, x, P.x[r])) break;
+        x = P.x[r];
+        if (!(fabsf(q5[2]) < SIN_MAX) || fabsf(q5[0]) > x * P.tan_half) break;
+        float chi2;
+        const int h = pick_hit(b, item, r, q5, C, z_base, &chi2);
+        if (h < 0) { ++misses; continue; }
+        const int2 q = b.s_q[h];
+        chi2sum += kf_update(P, q5, C, q.x * Q - q5[0], (float)(q.y - z_base) * Q - q5[1]);
+        if (!cov_ok(C)) { dead = true; break; }
+        misses = 0;
+        hl[n++] = h;
+        in_hit = h;
+        in_x = x;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) in_p[m] = q5[m];
+#pragma unroll
+        for (int m = 0; m < 15; ++m) in_C[m] = C[m];
+      }
+      if (!dead && n >= MIN_HITS) {
+        rec.n = n;
+#pragma unroll
+        for (int m = 0; m < 5; ++m) rec.p[m] = in_p[m];
+#pragma unroll
+        for (int m = 0; m < 15; ++m) rec.C[m] = in_C[m];
+        rec.chi2 = chi2sum;
+        rec.x_ref = in_x;
+        rec.z_in = b.s_q[in_hit].y;
+      }
+    }
+    b.tl[t] = rec;
+  }
+}
+
+// ============================================================================ S7
+__device__ __forceinline__ unsigned long long tl_key(const TrackletRec& r) {
+  return ((unsigned long long)(unsigned)r.n << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)r.local);
+}
+
+// Each hit goes to the tracklet with the largest key (more hits, then smaller
+// item-local id): one 64-bit atomicMax per (tracklet, hit).  Order-independent.
+__global__ void __launch_bounds__(256) k_select_max(const __grid_constant__ Buffers b) {
+  const DevParams& P = b.par;
+  const int T = b.start_ex[b.N];
+  const int NR = P.n_rows;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    const TrackletRec& r = b.tl[t];
+    const int n = r.n;
+    if (n < MIN_HITS) continue;
+    const unsigned long long key = tl_key(r);
+    const int* hl = b.tl_hits + (size_t)t * NR;
+    for (int k = 0; k < n; ++k) atomicMax(&b.hit_key[hl[k]], key);
+  }
+}
+
+// A tracklet keeps the hits it owns and is a track if it owns >= 10; with
+// time-frame slices only tracks whose innermost hit lies in the item's core.
+__global__ void __launch_bounds__(256) k_select_own(const __grid_constant__ Buffers b) {
+  const DevParams& P = b.par;
+  const int T = b.start_ex[b.N];
+  const int NR = P.n_rows;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    const TrackletRec& r = b.tl[t];
+    unsigned long long out = 0;
+    if (r.n >= MIN_HITS) {
+      const unsigned long long key = tl_key(r);
+      const int* hl = b.tl_hits + (size_t)t * NR;
+      int own = 0;
+      for (int k = 0; k < r.n; ++k) own += b.hit_key[hl[k]] == key;
+      bool keep = own >= MIN_HITS;
+      if (keep && b.item_core) keep = r.z_in >= b.item_core[2 * r.item] && r.z_in < b.item_core[2 * r.item + 1];
+      if (keep) out = (1ull << 32) | (unsigned long long)own;
+    }
+    b.tl_cnt[t] = out;
+  }
+}
+
+// ============================================================================ S8
+__global__ void __launch_bounds__(256) k_output(const __grid_constant__ Buffers b) {
+  const DevParams& P = b.par;
+  const int T = b.start_ex[b.N];
+  const int NR = P.n_rows;
+  tpc_track_t* trk = reinterpret_cast<tpc_track_t*>(b.trk);
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    if (b.tl_cnt[t] == 0) continue;
+    const TrackletRec& r = b.tl[t];
+    const unsigned long long ex = b.tl_ex[t];
+    const unsigned ti = (unsigned)(ex >> 32);
+    unsigned io = (unsigned)(ex & 0xFFFFFFFFull);
+    tpc_track_t o;
+    o.x_ref = r.x_ref;
+    o.y = r.p[0];
+    o.z = r.p[1] + (float)r.z_base * (1.0f / TPC_QSCALE);
+    o.snp = r.p[2];
+    o.tgl = r.p[3];
+    o.qpt = r.p[4];
+#pragma unroll
+    for (int m = 0; m < 15; ++m) o.cov[m] = r.C[m];
+    o.chi2 = r.chi2;
+    o.ndf = 2 * r.n - 5;
+    o.item = r.item;
+    o.sector = b.item_sector ? b.item_sector[r.item] : 0u;
+    o.event = b.item_event ? b.item_event[r.item] : 0u;
+    o.first_cluster = io;
+    o.n_clusters = (unsigned)(b.tl_cnt[t] & 0xFFFFFFFFull);
+    trk[ti] = o;
+    const unsigned long long key = tl_key(r);
+    const int* hl = b.tl_hits + (size_t)t * NR;
+    for (int k = r.n - 1; k >= 0; --k)  // innermost first
+      if (b.hit_key[hl[k]] == key) b.trk_ids[io++] = (uint32_t)b.s_id[hl[k]];
+  }
+}
+
+__global__ void k_counts(const __grid_constant__ Buffers b) {
+  const int T = b.start_ex[b.N];
+  const unsigned long long tot = b.tl_ex[T];
+  b.counts[0] = tot >> 32;
+  b.counts[1] = tot & 0xFFFFFFFFull;
+  b.counts[2] = (unsigned long long)T;
+}
+
+// ============================================================================ host launchers
+cudaError_t tpc_configure_kernels(int sort_smem, int link_smem) {
+  cudaError_t e = cudaFuncSetAttribute(k_row_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, sort_smem);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(k_links, cudaFuncAttributeMaxDynamicSharedMemorySize, link_smem);
+}
+
+static void scan_i32(const int* in, int* out, long long n, unsigned long long* bsum, int G, cudaStream_t s) {
+  k_scan_reduce_i32<<<G, 256, 0, s>>>(in, n, bsum);
+  k_scan_bsums<unsigned long long><<<1, 1024, 0, s>>>(bsum, G);
+  k_scan_final_i32<<<G, 256, 0, s>>>(in, out, nullptr, n, bsum);
+}
+
+static void scan_u64_dev(const unsigned long long* in, unsigned long long* out, const int* n_dev,
+                         unsigned long long* bsum, int G, cudaStream_t s) {
+  k_scan_reduce<unsigned long long><<<G, 256, 0, s>>>(in, n_dev, 0, bsum);
+  k_scan_bsums<unsigned long long><<<1, 1024, 0, s>>>(bsum, G);
+  k_scan_final_u64<<<G, 256, 0, s>>>(in, out, n_dev, 0, bsum);
+}
+
+// Plain mode: one launch per step over all items.  ev (nullable) receives
+// TPC_N_STAGES+1 events around the steps.
+cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev) {
+  const int NR = c.n_rows;
+  const int M = b.I * NR;
+  auto mark = [&](int i) {
+    if (ev) cudaEventRecord(ev[i], s);
+  };
+  mark(0);
+  cudaMemsetAsync(b.rs_cnt, 0, sizeof(int) * M, s);
+  cudaMemsetAsync(b.rs_min, 0x7F, sizeof(int) * 4 * (size_t)M, s);
+  cudaMemsetAsync(b.row_fill, 0, sizeof(int) * M, s);
+  cudaMemsetAsync(b.hit_key, 0, sizeof(unsigned long long) * (size_t)b.N, s);
+  k_row_stats<<<b.n_chunks, 256, 0, s>>>(b);
+  mark(1);
+  k_row_setup<<<b.I, 256, 0, s>>>(b);
+  mark(2);
+  k_group_scatter<<<b.n_chunks, 256, 0, s>>>(b);
+  mark(3);
+  k_row_sort<<<M, 128, c.sort_smem, s>>>(b, c.sort_smem, b.cl_q, b.cl_key, b.up_raw);
+  mark(4);
+  // positions left unwritten by rejected clusters must read as "no link"
+  cudaMemsetAsync(b.up_raw, 0xFF, sizeof(int) * (size_t)b.N, s);
+  cudaMemsetAsync(b.dn_raw, 0xFF, sizeof(int) * (size_t)b.N, s);
+  k_links<<<M, 128, c.link_smem, s>>>(b, c.link_smem);
+  mark(5);
+  const int gN = (int)((b.N + 255) / 256) < c.num_sms * 8 ? (int)((b.N + 255) / 256) : c.num_sms * 8;
+  k_clean_start<<<gN > 0 ? gN : 1, 256, 0, s>>>(b);
+  scan_i32(b.flags, b.start_ex, b.N, b.scan_tmp, c.grid_scan, s);
+  k_starts<<<gN > 0 ? gN : 1, 256, 0, s>>>(b);
+  mark(6);
+  k_tracklets<<<c.grid_tl, c.block_tl, 0, s>>>(b);
+  mark(7);
+  k_select_max<<<c.num_sms * 4, 256, 0, s>>>(b);
+  k_select_own<<<c.num_sms * 4, 256, 0, s>>>(b);
+  scan_u64_dev(b.tl_cnt, b.tl_ex, b.start_ex + b.N, b.scan_tmp, c.grid_scan, s);
+  mark(8);
+  k_output<<<c.num_sms * 4, 256, 0, s>>>(b);
+  k_counts<<<1, 1, 0, s>>>(b);
+  mark(9);
+  return cudaGetLastError();
+}

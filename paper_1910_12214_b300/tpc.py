@@ -1,0 +1,235 @@
+"""Thin ctypes binding of libtpc.so (include/tpc.h).  Argument marshalling only:
+every step of the tracker runs in the library's CUDA kernels.  torch supplies
+device memory (its caching allocator, through the allocator callback) and the
+stream.  There is no CPU fallback: without the built library this module fails
+to import."""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libtpc.so")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build it with `python -m paper_1910_12214_b300.build` "
+                      "(nvcc, sm_103a); there is no CPU fallback")
+
+_lib = C.CDLL(LIB_PATH)
+
+TPC_OK = 0
+STATUS = {0: "TPC_OK", 1: "TPC_ERR_INVALID_ARG", 2: "TPC_ERR_STATE", 3: "TPC_ERR_CUDA", 4: "TPC_ERR_OOM",
+          5: "TPC_ERR_CAPACITY", 6: "TPC_ERR_TIMEOUT", 7: "TPC_ERR_BAD_INPUT"}
+MODE = {"plain": 0, "batched": 1}
+CORR = {"none": 0, "grid": 1, "mlp": 2}
+
+ALLOC_FN = C.CFUNCTYPE(C.c_void_p, C.c_size_t, C.c_void_p)
+FREE_FN = C.CFUNCTYPE(None, C.c_void_p, C.c_void_p)
+
+
+class tpc_allocator(C.Structure):
+    _fields_ = [("alloc", ALLOC_FN), ("free", FREE_FN), ("user", C.c_void_p)]
+
+
+class tpc_config(C.Structure):
+    _fields_ = [("device", C.c_int), ("stream", C.c_void_p), ("bz_tesla", C.c_float), ("n_rows", C.c_int),
+                ("row_x_min", C.c_float), ("row_x_max", C.c_float), ("sector_half_angle_deg", C.c_float),
+                ("sigma_y", C.c_float), ("sigma_z", C.c_float), ("mode", C.c_int), ("correction", C.c_int),
+                ("max_clusters", C.c_uint64), ("max_items", C.c_uint32), ("allocator", C.POINTER(tpc_allocator)),
+                ("profile", C.c_int)]
+
+
+class tpc_clusters(C.Structure):
+    _fields_ = [("x", C.c_void_p), ("y", C.c_void_p), ("z", C.c_void_p), ("row", C.c_void_p), ("n", C.c_uint64),
+                ("item_off", C.c_void_p), ("n_items", C.c_uint32), ("item_sector", C.c_void_p),
+                ("item_event", C.c_void_p), ("item_core", C.c_void_p), ("on_device", C.c_int)]
+
+
+TRACK_DTYPE = np.dtype([("x_ref", "<f4"), ("y", "<f4"), ("z", "<f4"), ("snp", "<f4"), ("tgl", "<f4"),
+                        ("qpt", "<f4"), ("cov", "<f4", (15,)), ("chi2", "<f4"), ("ndf", "<i4"), ("item", "<u4"),
+                        ("sector", "<u4"), ("event", "<u4"), ("first_cluster", "<u4"), ("n_clusters", "<u4")])
+assert TRACK_DTYPE.itemsize == 112
+
+_P = C.c_void_p
+_sig = {
+    "tpc_init": ([C.POINTER(tpc_config), C.POINTER(_P)], C.c_int),
+    "tpc_load_clusters": ([_P, C.POINTER(tpc_clusters)], C.c_int),
+    "tpc_track": ([_P], C.c_int),
+    "tpc_sync": ([_P], C.c_int),
+    "tpc_get_tracks": ([_P, _P, C.c_uint64, _P, C.c_uint64, C.POINTER(C.c_uint64), C.POINTER(C.c_uint64)], C.c_int),
+    "tpc_device_tracks": ([_P, C.POINTER(_P), C.POINTER(_P), C.POINTER(_P)], C.c_int),
+    "tpc_stage_times": ([_P, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)], C.c_int),
+    "tpc_stage_name": ([C.c_int], C.c_char_p),
+    "tpc_debug_dump": ([_P, C.c_int, _P, C.c_uint64, C.POINTER(C.c_uint64)], C.c_int),
+    "tpc_destroy": ([_P], None),
+    "tpc_last_error": ([_P], C.c_char_p),
+}
+for _name, (_a, _r) in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _a
+    _f.restype = _r
+
+EXPORTED = sorted(_sig)
+
+
+class TpcError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+def _torch_allocator(device):
+    import torch
+
+    def alloc(nbytes, user):
+        try:
+            return torch.cuda.caching_allocator_alloc(int(nbytes), device, torch.cuda.current_stream(device))
+        except Exception:
+            return None
+
+    def free(ptr, user):
+        torch.cuda.caching_allocator_delete(ptr)
+
+    fa, ff = ALLOC_FN(alloc), FREE_FN(free)
+    return tpc_allocator(fa, ff, None), (fa, ff)
+
+
+def _ptr(a):
+    """Host numpy array -> address; torch tensor -> data_ptr (device or host)."""
+    if a is None:
+        return None
+    if hasattr(a, "data_ptr"):
+        return a.data_ptr()
+    return a.ctypes.data
+
+
+class Tracker:
+    """One tpc_ctx.  Cluster input may be numpy (host) or CUDA torch tensors (device)."""
+
+    def __init__(self, device: int = 0, stream=None, n_rows: int = 152, row_x_min: float = 85.0,
+                 row_x_max: float = 246.0, half_angle_deg: float = 10.0, bz_tesla: float = 0.5,
+                 sigma_y: float = 0.1, sigma_z: float = 0.1, mode: str = "plain", correction: str = "none",
+                 max_clusters: int = 0, max_items: int = 0, torch_allocator: bool = True, profile: bool = False):
+        self._keep = []
+        alloc_ptr = None
+        if torch_allocator:
+            al, keep = _torch_allocator(device)
+            self._alloc = al
+            self._keep.append(keep)
+            alloc_ptr = C.pointer(self._alloc)
+        if stream is None:
+            import torch
+            stream = torch.cuda.current_stream(device)
+        sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        self.cfg = tpc_config(device, sptr, bz_tesla, n_rows, row_x_min, row_x_max, half_angle_deg, sigma_y, sigma_z,
+                              MODE[mode], CORR[correction], max_clusters, max_items, alloc_ptr, int(profile))
+        self.n_rows = n_rows
+        h = _P()
+        st = _lib.tpc_init(C.byref(self.cfg), C.byref(h))
+        if st != TPC_OK:
+            raise TpcError(st, "tpc_init failed")
+        self._h = h
+        self._loaded = None
+
+    def _check(self, st):
+        if st != TPC_OK:
+            raise TpcError(st, _lib.tpc_last_error(self._h).decode())
+
+    def load(self, cl, on_device: bool = None):
+        """cl: object with x, y, z, row (numpy or torch), item_off, optional item_sector,
+        item_event, item_core (host numpy)."""
+        if on_device is None:
+            on_device = hasattr(cl.x, "is_cuda") and cl.x.is_cuda
+        keep = []
+
+        def host(a, dt):
+            if a is None:
+                return None
+            a = np.ascontiguousarray(a, dtype=dt)
+            keep.append(a)
+            return a
+
+        if on_device:
+            x, y, z, row = cl.x, cl.y, cl.z, cl.row
+            n = int(x.shape[0])
+        else:
+            x, y, z = (host(a, np.float32) for a in (cl.x, cl.y, cl.z))
+            row = host(cl.row, np.int32)
+            n = int(x.shape[0])
+        off = host(cl.item_off, np.uint64)
+        sec = host(getattr(cl, "item_sector", None), np.uint32)
+        ev = host(getattr(cl, "item_event", None), np.uint32)
+        core = host(getattr(cl, "item_core", None), np.int32)
+        c = tpc_clusters(_ptr(x), _ptr(y), _ptr(z), _ptr(row), n, _ptr(off), int(off.shape[0] - 1), _ptr(sec),
+                         _ptr(ev), _ptr(core), int(bool(on_device)))
+        self._check(_lib.tpc_load_clusters(self._h, C.byref(c)))
+        self._loaded = (cl, keep) if on_device else None
+        return self
+
+    def track(self):
+        self._check(_lib.tpc_track(self._h))
+        return self
+
+    def sync(self):
+        self._check(_lib.tpc_sync(self._h))
+
+    def counts(self):
+        nt, ni = C.c_uint64(), C.c_uint64()
+        st = _lib.tpc_get_tracks(self._h, None, 0, None, 0, C.byref(nt), C.byref(ni))
+        if st not in (TPC_OK, 5):
+            self._check(st)
+        return int(nt.value), int(ni.value)
+
+    def get_tracks(self):
+        nt, ni = self.counts()
+        trk = np.zeros(nt, dtype=TRACK_DTYPE)
+        ids = np.zeros(ni, dtype=np.uint32)
+        a, b = C.c_uint64(), C.c_uint64()
+        self._check(_lib.tpc_get_tracks(self._h, _ptr(trk) if nt else None, nt, _ptr(ids) if ni else None, ni,
+                                        C.byref(a), C.byref(b)))
+        return trk, ids
+
+    def device_tracks(self):
+        t, i, cnt = _P(), _P(), _P()
+        self._check(_lib.tpc_device_tracks(self._h, C.byref(t), C.byref(i), C.byref(cnt)))
+        return t.value, i.value, cnt.value
+
+    def stage_times(self):
+        us = (C.c_float * 32)()
+        n = C.c_int()
+        self._check(_lib.tpc_stage_times(self._h, us, 32, C.byref(n)))
+        return {_lib.tpc_stage_name(i).decode(): float(us[i]) for i in range(n.value)}
+
+    def debug_dump(self, stage: int) -> np.ndarray:
+        n = C.c_uint64()
+        st = _lib.tpc_debug_dump(self._h, stage, None, 0, C.byref(n))
+        if st not in (TPC_OK, 5):
+            self._check(st)
+        buf = np.zeros(int(n.value), dtype=np.int32)
+        self._check(_lib.tpc_debug_dump(self._h, stage, _ptr(buf) if n.value else None, n.value, C.byref(n)))
+        return buf
+
+    def close(self):
+        if getattr(self, "_h", None):
+            _lib.tpc_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *a):
+        self.close()
+
+
+def tracks_to_trk_i(trk: np.ndarray) -> np.ndarray:
+    """(item, first_cluster, n_clusters, index) rows, the layout of the evaluation helpers."""
+    return np.stack([trk["item"].astype(np.int64), trk["first_cluster"].astype(np.int64),
+                     trk["n_clusters"].astype(np.int64), np.arange(trk.shape[0])], axis=1)
