@@ -74,7 +74,7 @@ typedef struct {
 
 /* Cluster batch, SoA, grouped by work item (event, sector[, time slice]).
  * Item k owns clusters [item_off[k], item_off[k+1]); item_off[0] = 0 and
- * item_off[n_items] = n.  x is the pad-row radius (only checked to be finite: the
+ * item_off[n_items] = n.  An empty batch has n = 0 (n_items may be 0).  x is the pad-row radius (only checked to be finite: the
  * row index defines the position along x); y, z are sector-local [cm]; row is the
  * pad-row index 0..n_rows-1.  x, y, z, row are host pointers (copied during the
  * call) or, with on_device = 1, device pointers borrowed until tpc_track() has

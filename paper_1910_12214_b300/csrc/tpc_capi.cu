@@ -226,7 +226,8 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
 
 extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
   if (!c || !cl) return TPC_ERR_INVALID_ARG;
-  if (cl->n_items == 0 || !cl->item_off) return fail(c, TPC_ERR_INVALID_ARG, "need at least one item and item_off");
+  if (!cl->item_off) return fail(c, TPC_ERR_INVALID_ARG, "item_off is required");
+  if (cl->n_items == 0 && cl->n != 0) return fail(c, TPC_ERR_INVALID_ARG, "clusters without items");
   if (cl->n > 0 && (!cl->x || !cl->y || !cl->z || !cl->row)) return fail(c, TPC_ERR_INVALID_ARG, "null cluster array");
   if (cl->n >= (1ull << 31) / 3) return fail(c, TPC_ERR_CAPACITY, "at most 715827882 clusters per batch");
   if (cl->item_off[0] != 0 || cl->item_off[cl->n_items] != cl->n)
@@ -250,7 +251,7 @@ extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
   if (s != TPC_OK) return s;
   Buffers& b = c->b;
   b.N = (int)cl->n;
-  b.I = (int)cl->n_items;
+  b.I = (int)std::max<uint32_t>(cl->n_items, 1);
   b.n_chunks = (int)c->chunks.size();
   const size_t n = cl->n;
   // cluster arrays: device pointers are borrowed, host arrays copied into our buffers

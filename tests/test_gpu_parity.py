@@ -36,9 +36,20 @@ def test_config1_stages_bit_exact_and_tracks(seed):
     assert r["ok"], r
 
 
+def _with_empty_items(cl):
+    """Insert empty items at the front, in the middle and at the end."""
+    off = cl.item_off.astype(np.int64)
+    mid = off.shape[0] // 2
+    off = np.concatenate([[0], off[:mid], [off[mid - 1]], off[mid:], [off[-1]]]).astype(np.uint64)
+    sec = np.concatenate([[7], cl.item_sector[:mid - 1], [9], cl.item_sector[mid - 1:], [11]]).astype(np.uint32)
+    ev = np.concatenate([[70], cl.item_event[:mid - 1], [90], cl.item_event[mid - 1:], [110]]).astype(np.uint32)
+    cl.item_off, cl.item_sector, cl.item_event = off, sec, ev
+    return cl
+
+
 def test_multi_item_uneven_with_empty_items():
-    cl = synth.make_batched(seed=5, n_events=4, mult=(3, 600))
-    assert (np.diff(cl.item_off.astype(np.int64)) == 0).any()
+    cl = _with_empty_items(synth.make_batched(seed=5, n_events=4, mult=(3, 600)))
+    assert (np.diff(cl.item_off.astype(np.int64)) == 0).sum() >= 3
     ref = oracle.run(cl)
     trk, ids, d = run_gpu(cl)
     compare_stages(d, ref)
@@ -98,6 +109,9 @@ def test_empty_batch_and_single_hit():
         t.load(_Cl([], [], [], [], [0])).track()
         trk, ids = t.get_tracks()
         assert trk.shape[0] == 0 and ids.shape[0] == 0
+        t.load(_Cl([], [], [], [], [0, 0, 0])).track()  # two empty items
+        trk, ids = t.get_tracks()
+        assert trk.shape[0] == 0 and ids.shape[0] == 0
         t.load(_Cl([100.0], [1.0], [2.0], [14], [0, 1])).track()
         trk, ids = t.get_tracks()
         assert trk.shape[0] == 0
@@ -142,6 +156,7 @@ def test_deterministic_and_device_input_equal_host_input():
     trk2, ids2, _ = run_gpu(cl)
     assert trk1.tobytes() == trk2.tobytes() and np.array_equal(ids1, ids2)
     dev = _Cl(cl.x, cl.y, cl.z, cl.row, cl.item_off)
+    dev.item_sector, dev.item_event = cl.item_sector, cl.item_event
     dev.x, dev.y, dev.z = (torch.from_numpy(a).cuda() for a in (cl.x, cl.y, cl.z))
     dev.row = torch.from_numpy(cl.row).cuda()
     with tpc.Tracker() as t:
@@ -150,16 +165,24 @@ def test_deterministic_and_device_input_equal_host_input():
     assert trk1.tobytes() == trk3.tobytes() and np.array_equal(ids1, ids3)
 
 
-def test_input_order_does_not_change_tracks():
+def test_input_order_only_moves_id_tie_breaks():
+    """Original ids break ties (equal metrics, equal chi2, equal hit counts), so a
+    permuted input may resolve a few duplicates differently; the CUDA path must
+    still match the oracle on the permuted input exactly as on the original."""
     cl = synth.make_config1(seed=6)
     trk1, ids1, _ = run_gpu(cl)
     perm = np.random.default_rng(1).permutation(cl.x.shape[0])
     c2 = _Cl(cl.x[perm], cl.y[perm], cl.z[perm], cl.row[perm], cl.item_off)
-    trk2, ids2, _ = run_gpu(c2)
+    c2.mc = cl.mc[perm]
+    trk2, ids2, d2 = run_gpu(c2)
+    ref2 = oracle.run(c2)
+    compare_stages(d2, ref2)
+    r = compare_tracks(c2, trk2, ids2, ref2)
+    assert r["ok"], r
     a = sorted(tuple(sorted(ids1[f:f + n])) for f, n in zip(trk1["first_cluster"], trk1["n_clusters"]))
     b = sorted(tuple(sorted(perm[ids2[f:f + n]])) for f, n in zip(trk2["first_cluster"], trk2["n_clusters"]))
     same = len(set(a) & set(b)) / max(1, len(a))
-    assert same > 0.99
+    assert same > 0.95
 
 
 def test_stage_times_profile():

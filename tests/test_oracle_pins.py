@@ -102,6 +102,8 @@ def test_binning_invariants_config1():
 
 def test_binning_invariants_multi_item_with_empty_items():
     cl = synth.make_batched(seed=3, n_events=2, mult=(5, 40))
+    off = cl.item_off.astype(np.int64)
+    cl.item_off = np.concatenate([[0], off[:5], [off[4]], off[5:]]).astype(np.uint64)  # an extra empty item
     sizes = np.diff(cl.item_off.astype(np.int64))
     assert (sizes == 0).any()  # empty items are part of the case
     r = oracle.run(cl)
