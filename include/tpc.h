@@ -146,9 +146,35 @@ const char* tpc_stage_name(int i);
  * to pos0, nbins+1 per (item,row); 3..6 raw up, raw down, clean up, clean down
  * links as original ids indexed by original id (-1 = none); 7 start hits
  * (original ids, canonical order); 8 hits per tracklet (0 = dropped);
- * 9 tracklet hit lists (original ids, outermost first).  Copies up to cap int32
+ * 9 tracklet hit lists (original ids, outermost first); 10 tracklet index
+ * (canonical order) of every output track.  Copies up to cap int32
  * values into host_buf and sets *n to the full count. */
 tpc_status tpc_debug_dump(tpc_ctx* ctx, int stage, int32_t* host_buf, uint64_t cap, uint64_t* n);
+
+/* Launch shapes of the kernels (no effect on results: every shape gives the
+ * same output bit for bit).  tracklet_lanes: lanes that share one tracklet
+ * (1, 2, 4, 8, 16 or 32; they split the hit search of every row);
+ * tracklet_block: threads per block of the tracklet kernel (32, 64, 96
+ * or 128); tracklet_blocks_per_sm: grid = this x SM count; sort_smem,
+ * link_smem: dynamic shared memory [bytes] of the per-row sort and neighbour
+ * kernels (rows that do not fit use global memory).  0 keeps a field. */
+typedef struct {
+  int tracklet_lanes;
+  int tracklet_block;
+  int tracklet_blocks_per_sm;
+  int sort_smem;
+  int link_rows;
+} tpc_tuning;
+
+tpc_status tpc_set_tuning(tpc_ctx* ctx, const tpc_tuning* t);
+tpc_status tpc_get_tuning(tpc_ctx* ctx, tpc_tuning* t);
+
+/* Autotuner: runs tpc_track() on the loaded batch for every candidate shape
+ * (lane groups x block sizes x shared-memory budgets), times each with CUDA
+ * events (median of `iters` runs), keeps the fastest in the context and
+ * returns it in *best (nullable) with its time in *best_us (nullable).  The
+ * last run leaves the batch tracked with the chosen shape. */
+tpc_status tpc_autotune(tpc_ctx* ctx, int iters, tpc_tuning* best, float* best_us);
 
 /* Frees every device buffer and the context. */
 void tpc_destroy(tpc_ctx* ctx);

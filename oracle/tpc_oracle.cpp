@@ -39,6 +39,7 @@ const double SIN_MAX = 0.93969262078590838; // sin(70 deg)
 const int MIN_HITS = 10;                 // minimum tracklet / track size
 const double SNP_LIMIT = 0.9999;         // propagation validity
 const double C0_DIAG_ANGLE = 1.0, C0_DIAG_QPT = 100.0;
+const double INFLATE = 100.0;            // covariance inflation of the inward refit
 
 struct Row {  // one (item, pad row) of the binning grid
   int pos0 = 0, n = 0, ymin = 0, zmin = 0, shift = SHIFT_MIN, ny = 0, nz = 0;
@@ -328,8 +329,9 @@ void binning(orc_result* R, const std::vector<int>& qy_in, const std::vector<int
 
 // ---------------------------------------------------------------- neighbours
 // For every hit h on an inner row (1..n_rows-2): the pair (u on r+1, d on r-1),
-// each inside the window |dqy| <= 2.75*dqx, |dqz| <= 1.1*dqx, whose chord passes
-// closest to h: minimise m = dY^2 + dZ^2 with
+// each inside the window |dqy| <= 2.75*dqx, |dqz| <= 3.2*dqx, whose chord passes
+// closest to h (2.75 = tan 70 deg; 3.2 > sinh(0.9)/cos 70 deg, the steepest z slope
+// per unit x of a fitted segment): minimise m = dY^2 + dZ^2 with
 //   dY = (qy_u - qy_h)*dx_dn - (qy_h - qy_d)*dx_up  (dx in quanta, exact int64),
 // accept if m <= ((dx_up + dx_dn) * D)^2; ties by smaller id_u, then smaller id_d.
 void neighbours(orc_result* R) {
@@ -343,8 +345,8 @@ void neighbours(orc_result* R) {
       const Row& rw = c.row(it, r);
       const int64_t dx_up = R->row_qx[r + 1] - R->row_qx[r];
       const int64_t dx_dn = R->row_qx[r] - R->row_qx[r - 1];
-      const int64_t wy_u = dx_up * 11 / 4, wz_u = dx_up * 11 / 10;
-      const int64_t wy_d = dx_dn * 11 / 4, wz_d = dx_dn * 11 / 10;
+      const int64_t wy_u = dx_up * 11 / 4, wz_u = dx_up * 16 / 5;
+      const int64_t wy_d = dx_dn * 11 / 4, wz_d = dx_dn * 16 / 5;
       const int64_t cut = (dx_up + dx_dn) * LINK_D;
       const int64_t cut2 = cut * cut;
       for (int h = rw.pos0; h < rw.pos0 + rw.n; ++h) {
@@ -435,9 +437,9 @@ int row_of_pos(const orc_result* R, int item, int pos) {
 //        (chain hits are accepted without a chi2 test);
 //  (ii)  extension to outer rows: predict, take the best hit with chi2 <= 16,
 //        stop after 5 consecutive misses;
-//  (iii) a fresh fit from the outermost hit towards the inner rows, with the
-//        outer direction and curvature as starting values and the initial
-//        covariance, re-picking hits as in (ii).
+//  (iii) a refit from the outermost hit towards the inner rows, with the
+//        outer direction and curvature as starting values and their variances
+//        inflated 100-fold, re-picking hits as in (ii).
 // The tracklet is the set of hits of (iii); its parameters are those at the
 // innermost hit.  Guards end a pass: |sinphi| >= sin 70 deg, |y| > x tan(half
 // angle) (the track leaves the sector), an invalid propagation.  A non-finite or
@@ -472,7 +474,7 @@ void build_tracklet(Ctx& c, int start, Tracklet& T) {
   set_c0(C, c.vy, c.vz);
   double x = x1;
   int out_hit = chain[0], out_row = chain_row[0];
-  double out_p[5];
+  double out_p[5], out_var[3] = {C[2][2], C[3][3], C[4][4]};
   std::memcpy(out_p, p, sizeof(p));
   bool alive = true;
   for (size_t i = 1; i < chain.size(); ++i) {
@@ -485,6 +487,9 @@ void build_tracklet(Ctx& c, int start, Tracklet& T) {
     out_hit = chain[i];
     out_row = r;
     std::memcpy(out_p, p, sizeof(p));
+    out_var[0] = C[2][2];
+    out_var[1] = C[3][3];
+    out_var[2] = C[4][4];
   }
   // (ii) extension outwards
   if (alive) {
@@ -502,11 +507,20 @@ void build_tracklet(Ctx& c, int start, Tracklet& T) {
       out_hit = h;
       out_row = r;
       std::memcpy(out_p, p, sizeof(p));
+      out_var[0] = C[2][2];
+      out_var[1] = C[3][3];
+      out_var[2] = C[4][4];
     }
   }
-  // (iii) fresh fit inwards from the outermost hit
+  // (iii) refit inwards from the outermost hit: its measured y, z; the outward
+  // direction and curvature with their variances inflated 100-fold (at most the
+  // initial ones), so that the refit is well conditioned and the outward fit
+  // enters with 1% of its weight.
   double q[5] = {c.hy(out_hit), c.hz(out_hit), out_p[2], out_p[3], out_p[4]};
   set_c0(C, c.vy, c.vz);
+  C[2][2] = std::min(C0_DIAG_ANGLE, INFLATE * out_var[0]);
+  C[3][3] = std::min(C0_DIAG_ANGLE, INFLATE * out_var[1]);
+  C[4][4] = std::min(C0_DIAG_QPT, INFLATE * out_var[2]);
   x = X(out_row);
   T.hits.assign(1, out_hit);
   T.chi2 = 0.0;

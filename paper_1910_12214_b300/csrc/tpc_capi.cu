@@ -112,9 +112,7 @@ tpc_status reserve(tpc_ctx* c, long long N, long long I, long long n_chunks) {
   b.rows = (RowInfo*)A(sizeof(RowInfo) * M);
   b.g_q = (int2*)A(8 * N);
   b.g_id = (int*)A(4 * N);
-  b.s_q = (int2*)A(8 * N);
-  b.s_id = (int*)A(4 * N);
-  b.s_key = (int*)A(4 * N);
+  b.s_hit = (int4*)A(16 * N);
   b.first = (int*)A(4 * (2 * N + 3 * M + 1));
   b.up_raw = (int*)A(4 * N);
   b.dn_raw = (int*)A(4 * N);
@@ -130,6 +128,7 @@ tpc_status reserve(tpc_ctx* c, long long N, long long I, long long n_chunks) {
   b.tl_ex = (unsigned long long*)A(8 * (Tcap + 1));
   b.trk = A(sizeof(tpc_track_t) * Tcap);
   b.trk_ids = (uint32_t*)A(4 * N);
+  b.trk_tl = (int*)A(4 * Tcap);
   b.counts = (unsigned long long*)A(8 * 4);
   b.err = (unsigned int*)A(16);
   b.scan_tmp = (unsigned long long*)A(8 * 1040);
@@ -197,11 +196,13 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
   LaunchCfg& L = c->lc;
   L.n_rows = cfg->n_rows;
   L.num_sms = sms;
-  L.sort_smem = 32 * 1024;
-  L.link_smem = 32 * 1024;
+  L.sort_smem = 12 * 1024;
+  L.link_smem = 0;
+  L.link_rows = 0;
   L.grid_scan = std::min(1024, 2 * sms);
   L.block_tl = 128;
-  L.grid_tl = sms * 8;
+  L.grid_tl = sms * 16;
+  L.tl_group = 1;
   if ((e = tpc_configure_kernels(L.sort_smem, L.link_smem)) != cudaSuccess) {
     cudaGetLastError();
     if (c->own_stream) cudaStreamDestroy(c->stream);
@@ -397,9 +398,10 @@ extern "C" tpc_status tpc_debug_dump(tpc_ctx* c, int stage, int32_t* buf, uint64
     v.resize(n);
     return n ? cudaMemcpy(v.data(), src, 4 * n, cudaMemcpyDeviceToHost) : cudaSuccess;
   };
-  std::vector<int> out, sid, tmp;
-  cudaError_t e = D2H(sid, b.s_id, N);
+  std::vector<int> out, sid(N), tmp, hit;
+  cudaError_t e = D2H(hit, b.s_hit, 4 * N);
   if (e != cudaSuccess) return cuda_fail(c, e, "dump");
+  for (size_t i = 0; i < N; ++i) sid[i] = hit[4 * i + 2];
   std::vector<RowInfo> rows(M);
   if (M && (e = cudaMemcpy(rows.data(), b.rows, sizeof(RowInfo) * M, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(c, e, "dump");
@@ -407,13 +409,11 @@ extern "C" tpc_status tpc_debug_dump(tpc_ctx* c, int stage, int32_t* buf, uint64
   if ((e = cudaMemcpy(&T, b.start_ex + N, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(c, e, "dump");
   switch (stage) {
     case 0: {
-      std::vector<int> q;
-      if ((e = D2H(q, b.s_q, 2 * N)) != cudaSuccess) return cuda_fail(c, e, "dump");
       out.resize(3 * N);
       for (size_t i = 0; i < N; ++i) {
-        out[3 * i] = q[2 * i];
-        out[3 * i + 1] = q[2 * i + 1];
-        out[3 * i + 2] = sid[i];
+        out[3 * i] = hit[4 * i];
+        out[3 * i + 1] = hit[4 * i + 1];
+        out[3 * i + 2] = hit[4 * i + 2];
       }
       break;
     }
@@ -461,6 +461,12 @@ extern "C" tpc_status tpc_debug_dump(tpc_ctx* c, int stage, int32_t* buf, uint64
       }
       break;
     }
+    case 10: {
+      unsigned long long cnt[4] = {0, 0, 0, 0};
+      if ((e = cudaMemcpy(cnt, b.counts, 32, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(c, e, "dump");
+      if ((e = D2H(out, b.trk_tl, cnt[0])) != cudaSuccess) return cuda_fail(c, e, "dump");
+      break;
+    }
     default:
       return fail(c, TPC_ERR_INVALID_ARG, "unknown stage");
   }
@@ -468,6 +474,127 @@ extern "C" tpc_status tpc_debug_dump(tpc_ctx* c, int stage, int32_t* buf, uint64
   if (buf && cap) std::memcpy(buf, out.data(), 4 * std::min<size_t>(cap, out.size()));
   if (cap < out.size()) return fail(c, TPC_ERR_CAPACITY, "dump buffer too small");
   return TPC_OK;
+}
+
+namespace {
+tpc_status apply_tuning(tpc_ctx* c, const tpc_tuning& t) {
+  LaunchCfg L = c->lc;
+  if (t.tracklet_lanes) {
+    if (t.tracklet_lanes != 1 && t.tracklet_lanes != 2 && t.tracklet_lanes != 4 && t.tracklet_lanes != 8 &&
+        t.tracklet_lanes != 16 && t.tracklet_lanes != 32)
+      return fail(c, TPC_ERR_INVALID_ARG, "tracklet_lanes must be 1, 2, 4, 8, 16 or 32");
+    L.tl_group = t.tracklet_lanes;
+  }
+  if (t.tracklet_block) {
+    if (t.tracklet_block % 32 || t.tracklet_block > 128 || t.tracklet_block < 32)
+      return fail(c, TPC_ERR_INVALID_ARG, "tracklet_block must be a multiple of 32, at most 128");
+    L.block_tl = t.tracklet_block;
+  }
+  if (t.tracklet_blocks_per_sm) {
+    if (t.tracklet_blocks_per_sm < 1 || t.tracklet_blocks_per_sm > 64)
+      return fail(c, TPC_ERR_INVALID_ARG, "tracklet_blocks_per_sm out of range");
+    L.grid_tl = t.tracklet_blocks_per_sm * L.num_sms;
+  }
+  if (t.sort_smem) {
+    if (t.sort_smem < 1024 || t.sort_smem > 200 * 1024) return fail(c, TPC_ERR_INVALID_ARG, "sort_smem out of range");
+    L.sort_smem = t.sort_smem & ~15;
+  }
+  if (t.link_rows) {
+    if (t.link_rows < -1 || t.link_rows > TPC_MAX_ROWS) return fail(c, TPC_ERR_INVALID_ARG, "link_rows out of range");
+    L.link_rows = t.link_rows < 0 ? 0 : t.link_rows;
+  }
+  cudaError_t e = tpc_configure_kernels(L.sort_smem, L.link_smem);
+  if (e != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
+  c->lc = L;
+  return TPC_OK;
+}
+}  // namespace
+
+extern "C" tpc_status tpc_set_tuning(tpc_ctx* c, const tpc_tuning* t) {
+  if (!c || !t) return TPC_ERR_INVALID_ARG;
+  cudaError_t e = cudaSetDevice(c->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  return apply_tuning(c, *t);
+}
+
+extern "C" tpc_status tpc_get_tuning(tpc_ctx* c, tpc_tuning* t) {
+  if (!c || !t) return TPC_ERR_INVALID_ARG;
+  t->tracklet_lanes = c->lc.tl_group;
+  t->tracklet_block = c->lc.block_tl;
+  t->tracklet_blocks_per_sm = c->lc.grid_tl / std::max(1, c->lc.num_sms);
+  t->sort_smem = c->lc.sort_smem;
+  t->link_rows = c->lc.link_rows ? c->lc.link_rows : -1;
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_autotune(tpc_ctx* c, int iters, tpc_tuning* best_out, float* best_us) {
+  if (!c || iters < 1) return TPC_ERR_INVALID_ARG;
+  if (!c->loaded) return fail(c, TPC_ERR_STATE, "tpc_autotune before tpc_load_clusters");
+  cudaError_t e = cudaSetDevice(c->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  std::vector<tpc_tuning> cand;
+  for (int lanes : {1, 2, 4, 8, 16, 32})
+    for (int blk : {32, 64, 128})
+      for (int per_sm : {8, 16, 32}) cand.push_back({lanes, blk, per_sm, 0, 0});
+  for (int sm : {6 * 1024, 12 * 1024, 24 * 1024})
+    for (int lr : {-1, 4, 16, 152}) cand.push_back({0, 0, 0, sm, lr});
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  tpc_tuning best{};
+  tpc_get_tuning(c, &best);
+  float best_t = 1e30f;
+  const LaunchCfg saved = c->lc;
+  auto time_cfg = [&](const tpc_tuning& t, float* us) -> tpc_status {
+    tpc_status s = apply_tuning(c, t);
+    if (s != TPC_OK) return s;
+    std::vector<float> ts;
+    for (int k = 0; k < iters + 1; ++k) {
+      cudaEventRecord(e0, c->stream);
+      s = tpc_track(c);
+      if (s != TPC_OK) return s;
+      cudaEventRecord(e1, c->stream);
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return cuda_fail(c, e, "autotune");
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (k) ts.push_back(ms * 1000.f);  // first run warms up
+    }
+    std::sort(ts.begin(), ts.end());
+    *us = ts[ts.size() / 2];
+    return TPC_OK;
+  };
+  tpc_status st = TPC_OK;
+  // lane groups, blocks and grids first (shared memory at its current value), then shared memory
+  for (const tpc_tuning& t0 : cand) {
+    tpc_tuning t = t0;
+    if (!t.tracklet_lanes) {
+      t.tracklet_lanes = best.tracklet_lanes;
+      t.tracklet_block = best.tracklet_block;
+      t.tracklet_blocks_per_sm = best.tracklet_blocks_per_sm;
+    } else {
+      t.sort_smem = best.sort_smem;
+      t.link_rows = best.link_rows;
+    }
+    float us = 0.f;
+    st = time_cfg(t, &us);
+    if (st != TPC_OK) break;
+    if (us < best_t) {
+      best_t = us;
+      best = t;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  if (st != TPC_OK) {
+    c->lc = saved;
+    tpc_configure_kernels(saved.sort_smem, saved.link_smem);
+    return st;
+  }
+  apply_tuning(c, best);
+  st = tpc_track(c);
+  if (best_out) *best_out = best;
+  if (best_us) *best_us = best_t;
+  return st;
 }
 
 extern "C" void tpc_destroy(tpc_ctx* c) {

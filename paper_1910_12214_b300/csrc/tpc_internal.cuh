@@ -76,9 +76,7 @@ struct Buffers {
   // grouped (row-major, unsorted) and sorted hits
   int2* g_q;
   int* g_id;
-  int2* s_q;
-  int* s_id;
-  int* s_key;     // item*NR+row per sorted position
+  int4* s_hit;    // sorted hits: (qy, qz, original id, item*NR+row)
   int* first;     // bins
   // links
   int* up_raw;
@@ -98,6 +96,7 @@ struct Buffers {
   // outputs
   void* trk;      // tpc_track_t [T_cap]
   uint32_t* trk_ids;  // [N]
+  int* trk_tl;        // tracklet index of every track [T_cap]
   unsigned long long* counts;  // [0] n_trk, [1] n_ids, [2] n_tracklets
   unsigned int* err;
   unsigned long long* scan_tmp;  // block sums
@@ -109,10 +108,12 @@ struct LaunchCfg {
   int n_rows;
   int num_sms;
   int sort_smem;  // dynamic shared memory of k_row_sort
-  int link_smem;  // dynamic shared memory of k_links (two staged rows)
+  int link_smem;  // unused (kept for the ABI's tuning struct)
+  int link_rows;  // rows per CTA of k_links (0 = derived from the batch size)
   int grid_scan;  // blocks of the reduce-then-scan (<= 1024)
   int grid_tl;    // blocks of k_tracklets
   int block_tl;   // threads per block of k_tracklets
+  int tl_group;   // lanes per tracklet (1, 2, 4, 8, 16, 32)
 };
 
 cudaError_t tpc_configure_kernels(int sort_smem, int link_smem);

@@ -23,6 +23,7 @@
 // (the ordering and rounding effects discussed in Sec. 3).
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
 
 #include "tpc.h"
@@ -39,6 +40,9 @@ constexpr float SNP_LIMIT = 0.9999f;
 constexpr int MIN_HITS = 10;
 constexpr int SHIFT_MIN = 10;
 constexpr long long LINK_D = 512;       // 0.5 cm chord deviation
+constexpr float INFLATE = 100.0f;       // covariance inflation of the inward refit
+constexpr int LINK_THREADS = 128;
+constexpr int LINK_MAXC = 24;           // window candidates per side and hit
 
 __device__ __forceinline__ int warp_incl_scan(int v) {
   const int lane = threadIdx.x & 31;
@@ -103,13 +107,21 @@ __device__ __forceinline__ unsigned long long block_excl_scan64(unsigned long lo
 }  // namespace
 
 // ============================================================================ S1
-// Quantise and validate; per-(item,row) count and extents.  rs_min holds four
-// planes: ymin, -ymax, zmin, -zmax (all atomicMin, initialised to 0x7F7F7F7F).
+// Quantise and validate; per-(item,row) count and extents.  A CTA handles one
+// chunk of one item and aggregates in shared memory first (one global atomic
+// per row and statistic per CTA).  rs_min holds four planes: ymin, -ymax, zmin,
+// -zmax (atomicMin, initialised to 0x7F7F7F7F).
 __global__ void __launch_bounds__(256) k_row_stats(const __grid_constant__ Buffers b) {
   const DevParams& P = b.par;
+  __shared__ int s_cnt[TPC_MAX_ROWS], s_min[4][TPC_MAX_ROWS];
   const Chunk ch = b.chunks[blockIdx.x];
   const int NR = P.n_rows;
   const int M = b.I * NR;
+  for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+    s_cnt[r] = 0;
+    s_min[0][r] = s_min[1][r] = s_min[2][r] = s_min[3][r] = 0x7F7F7F7F;
+  }
+  __syncthreads();
   for (int i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) {
     const float xv = b.x[i], yv = b.y[i], zv = b.z[i];
     const int r = b.row[i];
@@ -122,14 +134,21 @@ __global__ void __launch_bounds__(256) k_row_stats(const __grid_constant__ Buffe
     // y*1024 is exact in FP32; round half to even
     const int qy = __float2int_rn(yv * TPC_QSCALE);
     const int qz = __float2int_rn(zv * TPC_QSCALE);
-    const int k = ch.item * NR + r;
-    b.cl_key[i] = k;
+    b.cl_key[i] = ch.item * NR + r;
     b.cl_q[i] = make_int2(qy, qz);
-    atomicAdd(&b.rs_cnt[k], 1);
-    atomicMin(&b.rs_min[k], qy);
-    atomicMin(&b.rs_min[M + k], -qy);
-    atomicMin(&b.rs_min[2 * M + k], qz);
-    atomicMin(&b.rs_min[3 * M + k], -qz);
+    atomicAdd(&s_cnt[r], 1);
+    atomicMin(&s_min[0][r], qy);
+    atomicMin(&s_min[1][r], -qy);
+    atomicMin(&s_min[2][r], qz);
+    atomicMin(&s_min[3][r], -qz);
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+    if (s_cnt[r] == 0) continue;
+    const int k = ch.item * NR + r;
+    atomicAdd(&b.rs_cnt[k], s_cnt[r]);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) atomicMin(&b.rs_min[j * M + k], s_min[j][r]);
   }
 }
 
@@ -187,14 +206,35 @@ __global__ void __launch_bounds__(256) k_row_setup(const __grid_constant__ Buffe
 
 // ============================================================================ S2b
 // Counting sort into row-contiguous order (order inside a row is arbitrary here;
-// k_row_sort makes it canonical).
+// k_row_sort makes it canonical).  The CTA counts its chunk per row in shared
+// memory, reserves one contiguous range per row with a single global atomic, and
+// places clusters at local slots inside it.
 __global__ void __launch_bounds__(256) k_group_scatter(const __grid_constant__ Buffers b) {
+  const DevParams& P = b.par;
+  __shared__ int s_cnt[TPC_MAX_ROWS], s_base[TPC_MAX_ROWS];
   const Chunk ch = b.chunks[blockIdx.x];
-  for (int i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) {
-    const int k = b.cl_key[i];
-    if (k < 0) continue;
-    const int slot = atomicAdd(&b.row_fill[k], 1);
-    const int gp = b.rows[k].pos0 + slot;
+  const int NR = P.n_rows;
+  for (int r = threadIdx.x; r < NR; r += blockDim.x) s_cnt[r] = 0;
+  __syncthreads();
+  constexpr int PER = 1024 / 256;  // chunks hold <= 1024 clusters
+  int key[PER], slot[PER];
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    const int i = ch.begin + threadIdx.x + u * 256;
+    key[u] = i < ch.end ? b.cl_key[i] : -1;
+    slot[u] = key[u] >= 0 ? atomicAdd(&s_cnt[key[u] - ch.item * NR], 1) : 0;
+  }
+  __syncthreads();
+  for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+    const int k = ch.item * NR + r;
+    s_base[r] = s_cnt[r] ? b.rows[k].pos0 + atomicAdd(&b.row_fill[k], s_cnt[r]) : 0;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int u = 0; u < PER; ++u) {
+    if (key[u] < 0) continue;
+    const int i = ch.begin + threadIdx.x + u * 256;
+    const int gp = s_base[key[u] - ch.item * NR] + slot[u];
     b.g_q[gp] = b.cl_q[i];
     b.g_id[gp] = i;
   }
@@ -276,11 +316,7 @@ __global__ void __launch_bounds__(128) k_row_sort(const __grid_constant__ Buffer
     }
   }
   __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
-    b.s_q[ri.pos0 + j] = q2[j];
-    b.s_id[ri.pos0 + j] = id2[j];
-    b.s_key[ri.pos0 + j] = k;
-  }
+  for (int j = threadIdx.x; j < n; j += blockDim.x) b.s_hit[ri.pos0 + j] = make_int4(q2[j].x, q2[j].y, id2[j], k);
   if (hist != b.first + ri.bin0) {
     for (int j = threadIdx.x; j <= nb; j += blockDim.x) b.first[ri.bin0 + j] = ri.pos0 + hist[j];
   } else {
@@ -291,37 +327,6 @@ __global__ void __launch_bounds__(128) k_row_sort(const __grid_constant__ Buffer
 
 // ============================================================================ S3
 namespace {
-struct RowView {  // a row's hits and bin starts, staged in shared memory or global
-  const int2* q;     // indexed by position - pos0
-  const int* id;
-  const int* first;  // absolute positions, nbins+1
-  RowInfo ri;
-};
-
-__device__ __forceinline__ void stage_row(RowView& v, const Buffers& b, const RowInfo& ri, unsigned char* sm,
-                                          int budget) {
-  v.ri = ri;
-  const int nb = ri.n > 0 ? ri.ny * ri.nz : 0;
-  const long long need = 12ll * ri.n + 4ll * (nb + 1);
-  if (ri.n > 0 && need <= budget) {
-    int2* q = reinterpret_cast<int2*>(sm);
-    int* id = reinterpret_cast<int*>(q + ri.n);
-    int* f = id + ri.n;
-    for (int j = threadIdx.x; j < ri.n; j += blockDim.x) {
-      q[j] = b.s_q[ri.pos0 + j];
-      id[j] = b.s_id[ri.pos0 + j];
-    }
-    for (int j = threadIdx.x; j <= nb; j += blockDim.x) f[j] = b.first[ri.bin0 + j];
-    v.q = q;
-    v.id = id;
-    v.first = f;
-  } else {
-    v.q = b.s_q + ri.pos0;
-    v.id = b.s_id + ri.pos0;
-    v.first = b.first + ri.bin0;
-  }
-}
-
 // bin range of [lo, hi] along one axis; empty if hi < lo
 __device__ __forceinline__ void bin_range(long long lo, long long hi, int vmin, int shift, int nbin, int* a,
                                           int* e) {
@@ -342,80 +347,135 @@ __device__ __forceinline__ void bin_range(long long lo, long long hi, int vmin, 
 }
 }  // namespace
 
-// One CTA per (item,row): for every hit h of an inner row, the pair (u on r+1,
-// d on r-1) inside the windows |dqy| <= 11*dqx/4, |dqz| <= 11*dqx/10 that
-// minimises m = dY^2 + dZ^2, dY = (qy_u-qy_h)*dx_dn - (qy_h-qy_d)*dx_up (int64),
-// accepted if m <= ((dx_up+dx_dn)*512)^2; ties: smaller id_u, then smaller id_d.
-// Rows 0 and n_rows-1 get no links (targets only).
-__global__ void __launch_bounds__(128) k_links(const __grid_constant__ Buffers b, int smem_bytes) {
+// One CTA per block of `rows_per_cta` consecutive rows of one item (their hits
+// are contiguous in sorted order, so the threads take a flat range of them).
+// For every hit h of an inner row: the pair (u on r+1, d on r-1) inside the
+// windows |dqy| <= 11*dqx/4, |dqz| <= 16*dqx/5 that minimises m = dY^2 + dZ^2,
+// dY = (qy_u-qy_h)*dx_dn - (qy_h-qy_d)*dx_up (int64), accepted if
+// m <= ((dx_up+dx_dn)*512)^2; ties: smaller id_u, then smaller id_d.  Rows 0 and
+// n_rows-1 get no links (targets only).  Neighbour rows are read through L1.
+__global__ void __launch_bounds__(LINK_THREADS) k_links(const __grid_constant__ Buffers b, int rows_per_cta) {
   const DevParams& P = b.par;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int k = blockIdx.x;
+  __shared__ RowInfo s_rows[TPC_MAX_ROWS + 2];
+  __shared__ int s_cu[LINK_MAXC][LINK_THREADS], s_cd[LINK_MAXC][LINK_THREADS];
   const int NR = P.n_rows;
-  const int r = k % NR;
-  const RowInfo rh = b.rows[k];
-  if (rh.n == 0) return;
-  if (r == 0 || r == NR - 1) {
-    for (int j = threadIdx.x; j < rh.n; j += blockDim.x) {
-      b.up_raw[rh.pos0 + j] = -1;
-      b.dn_raw[rh.pos0 + j] = -1;
-    }
-    return;
-  }
-  RowView U, D;
-  stage_row(U, b, b.rows[k + 1], smem_raw, smem_bytes / 2);
-  stage_row(D, b, b.rows[k - 1], smem_raw + smem_bytes / 2, smem_bytes / 2);
+  const int nrb = (NR + rows_per_cta - 1) / rows_per_cta;
+  const int item = blockIdx.x / nrb;
+  const int r_begin = (blockIdx.x - item * nrb) * rows_per_cta;
+  const int r_end = min(NR, r_begin + rows_per_cta);
+  const int lo = max(0, r_begin - 1), hi = min(NR - 1, r_end);
+  for (int r = lo + threadIdx.x; r <= hi; r += blockDim.x) s_rows[r - lo] = b.rows[item * NR + r];
   __syncthreads();
-  const long long dxu = P.qx[r + 1] - P.qx[r];
-  const long long dxd = P.qx[r] - P.qx[r - 1];
-  const long long wyu = dxu * 11 / 4, wzu = dxu * 11 / 10;
-  const long long wyd = dxd * 11 / 4, wzd = dxd * 11 / 10;
-  const long long cut = (dxu + dxd) * LINK_D;
-  const long long cut2 = cut * cut;
-  for (int j = threadIdx.x; j < rh.n; j += blockDim.x) {
-    const int pos = rh.pos0 + j;
-    const int2 qh = b.s_q[pos];
+  const int p_begin = s_rows[r_begin - lo].pos0;
+  const int p_end = s_rows[r_end - 1 - lo].pos0 + s_rows[r_end - 1 - lo].n;
+  const int t = threadIdx.x;
+  for (int pos = p_begin + t; pos < p_end; pos += blockDim.x) {
+    const int4 qh = b.s_hit[pos];
+    const int r = qh.w - item * NR;
+    if (r == 0 || r == NR - 1) {
+      b.up_raw[pos] = -1;
+      b.dn_raw[pos] = -1;
+      continue;
+    }
+    const RowInfo U = s_rows[r + 1 - lo], D = s_rows[r - 1 - lo];
+    const long long dxu = P.qx[r + 1] - P.qx[r];
+    const long long dxd = P.qx[r] - P.qx[r - 1];
+    const long long wyu = dxu * 11 / 4, wzu = dxu * 16 / 5;
+    const long long wyd = dxd * 11 / 4, wzd = dxd * 16 / 5;
+    const long long cut = (dxu + dxd) * LINK_D;
+    const long long cut2 = cut * cut;
     const long long yh = qh.x, zh = qh.y;
+    // candidates of each side: hits inside the window, from one contiguous hit
+    // range per y-bin row (the z-bins of a y-bin row are adjacent)
+    int nu = 0, nd = 0;
+    bool ovf = false;
+    {
+      int y0, y1, z0, z1;
+      bin_range(yh - wyu, yh + wyu, U.ymin, U.shift, U.ny, &y0, &y1);
+      bin_range(zh - wzu, zh + wzu, U.zmin, U.shift, U.nz, &z0, &z1);
+      if (z1 >= z0)
+        for (int iy = y0; iy <= y1; ++iy) {
+          const int b0 = U.bin0 + iy * U.nz + z0;
+          const int e_ = b.first[b0 + z1 - z0 + 1];
+          for (int pu = b.first[b0]; pu < e_; ++pu) {
+            const int4 q = b.s_hit[pu];
+            const long long ey = q.x - yh, ez = q.y - zh;
+            if (ey > wyu || -ey > wyu || ez > wzu || -ez > wzu) continue;
+            if (nu < LINK_MAXC) s_cu[nu++][t] = pu; else ovf = true;
+          }
+        }
+    }
+    {
+      int y0, y1, z0, z1;
+      bin_range(yh - wyd, yh + wyd, D.ymin, D.shift, D.ny, &y0, &y1);
+      bin_range(zh - wzd, zh + wzd, D.zmin, D.shift, D.nz, &z0, &z1);
+      if (z1 >= z0 && nu > 0)
+        for (int iy = y0; iy <= y1; ++iy) {
+          const int b0 = D.bin0 + iy * D.nz + z0;
+          const int e_ = b.first[b0 + z1 - z0 + 1];
+          for (int pd = b.first[b0]; pd < e_; ++pd) {
+            const int4 q = b.s_hit[pd];
+            const long long fy = yh - q.x, fz = zh - q.y;
+            if (fy > wyd || -fy > wyd || fz > wzd || -fz > wzd) continue;
+            if (nd < LINK_MAXC) s_cd[nd++][t] = pd; else ovf = true;
+          }
+        }
+    }
     long long best = -1;
     int bu = -1, bd = -1, bid_u = 0, bid_d = 0;
-    int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
-    bin_range(yh - wyu, yh + wyu, U.ri.ymin, U.ri.shift, U.ri.ny, &uy0, &uy1);
-    bin_range(zh - wzu, zh + wzu, U.ri.zmin, U.ri.shift, U.ri.nz, &uz0, &uz1);
-    bin_range(yh - wyd, yh + wyd, D.ri.ymin, D.ri.shift, D.ri.ny, &dy0, &dy1);
-    bin_range(zh - wzd, zh + wzd, D.ri.zmin, D.ri.shift, D.ri.nz, &dz0, &dz1);
-    for (int iy = uy0; iy <= uy1; ++iy)
-      for (int iz = uz0; iz <= uz1; ++iz) {
-        const int bu_ = iy * U.ri.nz + iz;
-        for (int pu = U.first[bu_]; pu < U.first[bu_ + 1]; ++pu) {
-          const int2 qu = U.q[pu - U.ri.pos0];
-          const long long ey = qu.x - yh, ez = qu.y - zh;
-          if (ey > wyu || -ey > wyu || ez > wzu || -ez > wzu) continue;
-          const int idu = U.id[pu - U.ri.pos0];
-          for (int jy = dy0; jy <= dy1; ++jy)
-            for (int jz = dz0; jz <= dz1; ++jz) {
-              const int bd_ = jy * D.ri.nz + jz;
-              for (int pd = D.first[bd_]; pd < D.first[bd_ + 1]; ++pd) {
-                const int2 qd = D.q[pd - D.ri.pos0];
-                const long long fy = yh - qd.x, fz = zh - qd.y;
-                if (fy > wyd || -fy > wyd || fz > wzd || -fz > wzd) continue;
-                const long long dY = ey * dxd - fy * dxu;
-                const long long dZ = ez * dxd - fz * dxu;
-                const long long m = dY * dY + dZ * dZ;
-                if (m > cut2) continue;
-                const int idd = D.id[pd - D.ri.pos0];
-                bool better = best < 0 || m < best;
-                if (!better && m == best) better = idu < bid_u || (idu == bid_u && idd < bid_d);
-                if (better) {
-                  best = m;
-                  bu = pu;
-                  bd = pd;
-                  bid_u = idu;
-                  bid_d = idd;
-                }
-              }
-            }
+    auto pair = [&](int pu, const int4& qu, int pd, const int4& qd) {
+      const long long ey = qu.x - yh, ez = qu.y - zh;
+      const long long fy = yh - qd.x, fz = zh - qd.y;
+      const long long dY = ey * dxd - fy * dxu;
+      const long long dZ = ez * dxd - fz * dxu;
+      const long long m = dY * dY + dZ * dZ;
+      if (m > cut2) return;
+      bool better = best < 0 || m < best;
+      if (!better && m == best) better = qu.z < bid_u || (qu.z == bid_u && qd.z < bid_d);
+      if (better) {
+        best = m;
+        bu = pu;
+        bd = pd;
+        bid_u = qu.z;
+        bid_d = qd.z;
+      }
+    };
+    if (!ovf) {
+      for (int iu = 0; iu < nu; ++iu) {
+        const int pu = s_cu[iu][t];
+        const int4 qu = b.s_hit[pu];
+        for (int id = 0; id < nd; ++id) {
+          const int pd = s_cd[id][t];
+          pair(pu, qu, pd, b.s_hit[pd]);
         }
       }
+    } else {
+      // more candidates than the lists hold (very dense rows): direct enumeration
+      int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
+      bin_range(yh - wyu, yh + wyu, U.ymin, U.shift, U.ny, &uy0, &uy1);
+      bin_range(zh - wzu, zh + wzu, U.zmin, U.shift, U.nz, &uz0, &uz1);
+      bin_range(yh - wyd, yh + wyd, D.ymin, D.shift, D.ny, &dy0, &dy1);
+      bin_range(zh - wzd, zh + wzd, D.zmin, D.shift, D.nz, &dz0, &dz1);
+      for (int iy = uy0; iy <= uy1; ++iy) {
+        const int bu0 = U.bin0 + iy * U.nz + uz0;
+        const int ue = b.first[bu0 + uz1 - uz0 + 1];
+        for (int pu = b.first[bu0]; pu < ue; ++pu) {
+          const int4 qu = b.s_hit[pu];
+          const long long ey = qu.x - yh, ez = qu.y - zh;
+          if (ey > wyu || -ey > wyu || ez > wzu || -ez > wzu) continue;
+          for (int jy = dy0; jy <= dy1; ++jy) {
+            const int bd0 = D.bin0 + jy * D.nz + dz0;
+            const int de = b.first[bd0 + dz1 - dz0 + 1];
+            for (int pd = b.first[bd0]; pd < de; ++pd) {
+              const int4 qd = b.s_hit[pd];
+              const long long fy = yh - qd.x, fz = zh - qd.y;
+              if (fy > wyd || -fy > wyd || fz > wzd || -fz > wzd) continue;
+              pair(pu, qu, pd, qd);
+            }
+          }
+        }
+      }
+    }
     b.up_raw[pos] = bu;
     b.dn_raw[pos] = bd;
   }
@@ -571,7 +631,10 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float
   if (!(fabsf(s1) < SNP_LIMIT) || !(fabsf(s2) < SNP_LIMIT)) return false;
   const float c1 = sqrtf((1.0f - s1) * (1.0f + s1));
   const float c2 = sqrtf((1.0f - s2) * (1.0f + s2));
-  const float T = (s1 + s2) / (c1 + c2);
+  // fast reciprocals (2 ulp): the Jacobian only feeds the covariance
+  const float cc = c1 + c2;
+  const float inv_cc = __fdividef(1.0f, cc);
+  const float T = (s1 + s2) * inv_cc;
   const float w = sqrtf(1.0f + T * T);
   const float adx = fabsf(dx);
   const float u = 0.5f * kappa * adx * w;
@@ -579,13 +642,11 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float
   const float f = asin_over_u(u);
   const float fp = d_asin_over_u(u);
   const float ell = dx * w * f;
-  const float num = 1.0f + c1 * c2 + s1 * s2;
-  const float cc = c1 + c2;
-  const float den = cc * cc;
-  const float A1 = num / (c1 * den), A2 = num / (c2 * den);
+  const float A = (1.0f + c1 * c2 + s1 * s2) * inv_cc * inv_cc;
+  const float A1 = __fdividef(A, c1), A2 = __fdividef(A, c2);
   const float dT_ds = A1 + A2;
   const float dT_dq = -A2 * kB * dx;
-  const float dg_dT = (T / w) * (f + u * fp);
+  const float dg_dT = __fdividef(T, w) * (f + u * fp);
   const float dg_dk = 0.5f * w * w * adx * fp;
   const float tgl = p[3];
   const float a = dx * dT_ds;                          // F02
@@ -633,8 +694,8 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float
 // Kalman update with H = [I2 0]; residuals (r0, r1); returns the chi2 increment.
 __device__ __forceinline__ float kf_update(const DevParams& P, float* p, float* C, float r0, float r1) {
   const float S00 = C[ix(0, 0)] + P.vy, S01 = C[ix(1, 0)], S11 = C[ix(1, 1)] + P.vz;
-  const float det = S00 * S11 - S01 * S01;
-  const float I00 = S11 / det, I01 = -S01 / det, I11 = S00 / det;
+  const float inv_det = 1.0f / (S00 * S11 - S01 * S01);
+  const float I00 = S11 * inv_det, I01 = -S01 * inv_det, I11 = S00 * inv_det;
   // columns 0 and 1 of the symmetric covariance
   float c0[5], c1[5], K0[5], K1[5];
 #pragma unroll
@@ -674,82 +735,178 @@ __device__ __forceinline__ void set_c0(const DevParams& P, float* C) {
   C[ix(4, 4)] = 100.0f;
 }
 
-// Best hit of row r for the predicted state: smallest chi2 <= 16, ties to the
-// smaller original id.  The search box (max(0.5 cm, 4 sigma) plus 2 quanta)
-// contains every hit with chi2 <= 16, so the box never changes the result.
-__device__ __forceinline__ int pick_hit(const Buffers& b, int item, int r, const float* p, const float* C, int z_base,
-                                        float* chi2_out) {
+// Group helpers: a tracklet is handled by a group of G consecutive lanes
+// (G = 1, 2, 4, 8, 16 or 32).  All lanes of a group hold the same state and take
+// the same branches; they split the chain loads and the hit search of a row.
+template <int G>
+struct Grp {
+  int gl;        // lane inside the group
+  unsigned mask; // lanes of the group
+  __device__ __forceinline__ Grp() {
+    const int lane = threadIdx.x & 31;
+    gl = lane & (G - 1);
+    mask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+  }
+  template <class T>
+  __device__ __forceinline__ T shfl(T v, int src) const {
+    if constexpr (G == 1) return v;
+    else return __shfl_sync(mask, v, src, G);
+  }
+  __device__ __forceinline__ int incl_scan(int v) const {
+#pragma unroll
+    for (int o = 1; o < G; o <<= 1) {
+      const int t = __shfl_up_sync(mask, v, o, G);
+      if (gl >= o) v += t;
+    }
+    return v;
+  }
+  __device__ __forceinline__ unsigned long long min64(unsigned long long v) const {
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) {
+      const unsigned long long w = __shfl_xor_sync(mask, v, o, G);
+      v = w < v ? w : v;
+    }
+    return v;
+  }
+  __device__ __forceinline__ void sync() const {
+    if constexpr (G > 1) __syncwarp(mask);
+  }
+};
+
+// Best hit of row r for the predicted state: the smallest chi2 <= 16, ties to
+// the smaller original id (a 64-bit key of the chi2 bit pattern and the id,
+// minimised over the group).  The search box (max(0.5 cm, 4 sigma) plus 2
+// quanta) contains every hit with chi2 <= 16, so the box never changes the
+// result.  Every lane of the group returns the same position.
+template <int G>
+__device__ __forceinline__ int pick_hit(const Buffers& b, const Grp<G>& g, int item, int r, const float* p,
+                                        const float* C, int z_base) {
   const DevParams& P = b.par;
   const RowInfo ri = b.rows[item * P.n_rows + r];
   if (ri.n == 0) return -1;
   const float S00 = C[ix(0, 0)] + P.vy, S01 = C[ix(1, 0)], S11 = C[ix(1, 1)] + P.vz;
-  const float det = S00 * S11 - S01 * S01;
+  const float inv_det = 1.0f / (S00 * S11 - S01 * S01);
   const float wy = fmaxf(WIN_MIN, 4.0f * sqrtf(S00));
   const float wz = fmaxf(WIN_MIN, 4.0f * sqrtf(S11));
+  // 32-bit conversions (values clamped to +-1e9): 64-bit ones run on the FP64 pipe
   const float lim = 1.0e9f;
-  const long long ylo = (long long)floorf(fmaxf(-lim, (p[0] - wy) * TPC_QSCALE)) - 2;
-  const long long yhi = (long long)ceilf(fminf(lim, (p[0] + wy) * TPC_QSCALE)) + 2;
-  const long long zlo = (long long)floorf(fmaxf(-lim, (p[1] - wz) * TPC_QSCALE)) - 2 + z_base;
-  const long long zhi = (long long)ceilf(fminf(lim, (p[1] + wz) * TPC_QSCALE)) + 2 + z_base;
+  const long long ylo = (long long)(int)floorf(fmaxf(-lim, (p[0] - wy) * TPC_QSCALE)) - 2;
+  const long long yhi = (long long)(int)ceilf(fminf(lim, (p[0] + wy) * TPC_QSCALE)) + 2;
+  const long long zlo = (long long)(int)floorf(fmaxf(-lim, (p[1] - wz) * TPC_QSCALE)) - 2 + z_base;
+  const long long zhi = (long long)(int)ceilf(fminf(lim, (p[1] + wz) * TPC_QSCALE)) + 2 + z_base;
   int iy0, iy1, iz0, iz1;
   bin_range(ylo, yhi, ri.ymin, ri.shift, ri.ny, &iy0, &iy1);
   bin_range(zlo, zhi, ri.zmin, ri.shift, ri.nz, &iz0, &iz1);
+  if (iy1 < iy0 || iz1 < iz0) return -1;
+  // the bins (iy, iz0..iz1) of one y-bin row are contiguous: one hit range each
+  const int nyb = iy1 - iy0 + 1;
+  const int span = iz1 - iz0 + 1;
   const float Q = 1.0f / TPC_QSCALE;
-  int best = -1, bid = 0;
-  float bchi = 0.f;
-  for (int iy = iy0; iy <= iy1; ++iy)
-    for (int iz = iz0; iz <= iz1; ++iz) {
-      const int bb = ri.bin0 + iy * ri.nz + iz;
-      const int a = b.first[bb], e = b.first[bb + 1];
-      for (int h = a; h < e; ++h) {
-        const int2 q = b.s_q[h];
-        const float dy = (float)q.x * Q - p[0];
-        const float dz = (float)(q.y - z_base) * Q - p[1];
-        const float chi2 = (S11 * dy * dy - 2.0f * S01 * dy * dz + S00 * dz * dz) / det;
-        if (!(chi2 <= CHI2_CUT)) continue;
-        const int id = b.s_id[h];
-        if (best < 0 || chi2 < bchi || (chi2 == bchi && id < bid)) {
-          best = h;
-          bid = id;
-          bchi = chi2;
-        }
+  unsigned long long best = ~0ull;
+  int best_pos = -1;
+  auto consider = [&](int h) {
+    const int4 q = b.s_hit[h];
+    const float dy = (float)q.x * Q - p[0];
+    const float dz = (float)(q.y - z_base) * Q - p[1];
+    const float chi2 = fmaxf(0.0f, (S11 * dy * dy - 2.0f * S01 * dy * dz + S00 * dz * dz) * inv_det);
+    if (chi2 <= CHI2_CUT) {
+      const unsigned long long key = ((unsigned long long)__float_as_uint(chi2) << 32) | (unsigned)q.z;
+      if (key < best) {
+        best = key;
+        best_pos = h;
       }
     }
-  *chi2_out = bchi;
-  return best;
+  };
+  if constexpr (G == 1) {
+    for (int iy = iy0; iy <= iy1; ++iy) {
+      const int b0 = ri.bin0 + iy * ri.nz + iz0;
+      const int a = b.first[b0], e = b.first[b0 + span];
+      int h = a;
+      for (; h + 1 < e; h += 2) {  // two loads in flight
+        consider(h);
+        consider(h + 1);
+      }
+      if (h < e) consider(h);
+    }
+    return best_pos;
+  } else {
+  for (int base = 0; base < nyb; base += G) {  // group-uniform loop
+    // one y-bin row per lane: its hit range [a, a + cnt)
+    const int j = base + g.gl;
+    int a = 0, cnt = 0;
+    if (j < nyb) {
+      const int b0 = ri.bin0 + (iy0 + j) * ri.nz + iz0;
+      a = b.first[b0];
+      cnt = b.first[b0 + span] - a;
+    }
+    const int inc = g.incl_scan(cnt);
+    const int ex = inc - cnt;
+    const int total = g.shfl(inc, G - 1);
+    for (int kk = 0; kk < total; kk += G) {  // group-uniform loop
+      const int k = kk + g.gl;
+      // lane holding candidate k: the first lane whose inclusive count exceeds k
+      int lo = 0;
+      int hi = G - 1;
+#pragma unroll
+      for (int step = 1; step < G; step <<= 1) {
+        const int mid = (lo + hi) >> 1;
+        const int v = g.shfl(inc, mid);
+        if (v > k) hi = mid; else lo = mid + 1;
+      }
+      const int a_src = g.shfl(a, lo);
+      const int ex_src = g.shfl(ex, lo);
+      if (k < total) consider(a_src + (k - ex_src));
+    }
+  }
+  {
+    const unsigned long long gbest = g.min64(best);
+    if (gbest == ~0ull) return -1;
+    const unsigned who = __ballot_sync(g.mask, best == gbest) & g.mask;
+    const int src = (__ffs(who) - 1) & (G - 1);
+    return g.shfl(best_pos, src);
+  }
+  }
 }
 }  // namespace
 
-// One thread per tracklet (grid-stride over the device count of start hits):
+// One group of G lanes per tracklet (grid-stride over the device count of start
+// hits).  All lanes of a group run the same Kalman arithmetic on the same values;
+// the lanes split the chain loads and the hit search of every row.
 //  (i)   circle through the first, middle and last chain hits -> initial state;
 //        Kalman fit along the chain (chain hits accepted without a chi2 test);
 //  (ii)  outward extension: best hit with chi2 <= 16, 5 consecutive misses end it;
-//  (iii) fresh inward fit from the outermost hit (its y, z; outward sinphi,
-//        tanlambda, q/pT; initial covariance), re-picking hits down to row 0.
+//  (iii) inward refit from the outermost hit (its y, z; outward sinphi,
+//        tanlambda, q/pT with variances inflated 100-fold), re-picking hits
+//        down to row 0.
 // Guards end a pass: |sinphi| >= sin 70 deg, |y| > x tan(half angle), invalid
 // step.  A non-finite or non-positive covariance diagonal drops the tracklet.
 // z is carried relative to the start hit (z_base) so that FP32 keeps its
 // precision for time-frame z' of thousands of cm.
+template <int G>
 __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Buffers b) {
   const DevParams& P = b.par;
+  const Grp<G> g;
   const int T = b.start_ex[b.N];
   const int NR = P.n_rows;
   const float Q = 1.0f / TPC_QSCALE;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
-    TrackletRec rec;
-    rec.n = 0;
+  const int grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int ngrp = (gridDim.x * blockDim.x) / G;
+  for (int t = grp; t < T; t += ngrp) {
     const int start = b.starts[t];
-    const int key = b.s_key[start];
+    const int4 hs = b.s_hit[start];
+    const int key = hs.w;
     const int item = key / NR;
     const int r0 = key - item * NR;
-    rec.item = item;
-    rec.local = t - b.start_ex[b.item_off[item]];
+    const int z_base = hs.y;
     int* hl = b.tl_hits + (size_t)t * NR;
+    // chain walk (pointer chasing; every lane of the group loads the same address)
     int L = 0;
-    for (int h = start; h >= 0 && L < NR; h = b.up[h]) hl[L++] = h;
-    const int z_base = b.s_q[start].y;
-    rec.z_base = z_base;
-    const int2 qa = b.s_q[hl[0]], qm = b.s_q[hl[L / 2]], qc = b.s_q[hl[L - 1]];
+    for (int h = start; h >= 0 && L < NR; h = b.up[h]) {
+      if (g.gl == 0) hl[L] = h;
+      ++L;
+    }
+    g.sync();
+    const int4 qa = b.s_hit[hl[0]], qm = b.s_hit[hl[L / 2]], qc = b.s_hit[hl[L - 1]];
     const float x1 = P.x[r0], x2 = P.x[r0 + L / 2], x3 = P.x[r0 + L - 1];
     const float y1 = qa.x * Q, y2 = qm.x * Q, y3 = qc.x * Q;
     const float z3 = (float)(qc.y - z_base) * Q;
@@ -768,21 +925,35 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Buffe
     float x = x1;
     int out_row = r0, out_hit = start;
     float out_p[5] = {p[0], p[1], p[2], p[3], p[4]};
+    float ov2 = C[ix(2, 2)], ov3 = C[ix(3, 3)], ov4 = C[ix(4, 4)];
     bool alive = true, dead = false;
-    // (i) chain
-    for (int i = 1; i < L; ++i) {
-      const int r = r0 + i;
-      if (!kf_propagate(P, p, C, x, P.x[r])) { alive = false; break; }
-      x = P.x[r];
-      if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) { alive = false; break; }
-      const int h = hl[i];
-      const int2 q = b.s_q[h];
-      kf_update(P, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
-      if (!cov_ok(C)) { dead = true; break; }
-      out_row = r;
-      out_hit = h;
+    // (i) chain: the lanes prefetch G chain hits at a time, broadcast in order
+    for (int c0 = 1; c0 < L && alive && !dead; c0 += G) {
+      int hpos = 0;
+      int4 mine = make_int4(0, 0, 0, 0);
+      if (c0 + g.gl < L) {
+        hpos = hl[c0 + g.gl];
+        mine = b.s_hit[hpos];
+      }
+      const int cend = min(L, c0 + G);
+      for (int i = c0; i < cend; ++i) {
+        const int qx_ = g.shfl(mine.x, i - c0);
+        const int qy_ = g.shfl(mine.y, i - c0);
+        const int hp = g.shfl(hpos, i - c0);
+        const int r = r0 + i;
+        if (!kf_propagate(P, p, C, x, P.x[r])) { alive = false; break; }
+        x = P.x[r];
+        if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) { alive = false; break; }
+        kf_update(P, p, C, qx_ * Q - p[0], (float)(qy_ - z_base) * Q - p[1]);
+        if (!cov_ok(C)) { dead = true; break; }
+        out_row = r;
+        out_hit = hp;
 #pragma unroll
-      for (int m = 0; m < 5; ++m) out_p[m] = p[m];
+        for (int m = 0; m < 5; ++m) out_p[m] = p[m];
+        ov2 = C[ix(2, 2)];
+        ov3 = C[ix(3, 3)];
+        ov4 = C[ix(4, 4)];
+      }
     }
     // (ii) outward extension
     if (alive && !dead) {
@@ -791,10 +962,9 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Buffe
         if (!kf_propagate(P, p, C, x, P.x[r])) break;
         x = P.x[r];
         if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) break;
-        float chi2;
-        const int h = pick_hit(b, item, r, p, C, z_base, &chi2);
+        const int h = pick_hit<G>(b, g, item, r, p, C, z_base);
         if (h < 0) { ++misses; continue; }
-        const int2 q = b.s_q[h];
+        const int4 q = b.s_hit[h];
         kf_update(P, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
         if (!cov_ok(C)) { dead = true; break; }
         misses = 0;
@@ -802,19 +972,31 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Buffe
         out_hit = h;
 #pragma unroll
         for (int m = 0; m < 5; ++m) out_p[m] = p[m];
+        ov2 = C[ix(2, 2)];
+        ov3 = C[ix(3, 3)];
+        ov4 = C[ix(4, 4)];
       }
     }
+    int n = 0;
+    float chi2sum = 0.f, in_x = x;
+    float in_p[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, in_C[15];
+#pragma unroll
+    for (int m = 0; m < 15; ++m) in_C[m] = 0.f;
+    int in_hit = out_hit;
     if (!dead) {
-      // (iii) inward refit from the outermost hit
-      const int2 qo = b.s_q[out_hit];
+      // (iii) inward refit from the outermost hit: its y, z; the outward direction
+      // and curvature with variances inflated 100-fold (capped at the initial ones)
+      const int4 qo = b.s_hit[out_hit];
       float q5[5] = {qo.x * Q, (float)(qo.y - z_base) * Q, out_p[2], out_p[3], out_p[4]};
       set_c0(P, C);
+      C[ix(2, 2)] = fminf(1.0f, INFLATE * ov2);
+      C[ix(3, 3)] = fminf(1.0f, INFLATE * ov3);
+      C[ix(4, 4)] = fminf(100.0f, INFLATE * ov4);
       x = P.x[out_row];
-      hl[0] = out_hit;
-      int n = 1;
-      float chi2sum = 0.f;
-      float in_p[5], in_C[15], in_x = x;
-      int in_hit = out_hit;
+      g.sync();
+      if (g.gl == 0) hl[0] = out_hit;
+      n = 1;
+      in_x = x;
 #pragma unroll
       for (int m = 0; m < 5; ++m) in_p[m] = q5[m];
 #pragma unroll
@@ -824,14 +1006,14 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Buffe
         if (!kf_propagate(P, q5, C, x, P.x[r])) break;
         x = P.x[r];
         if (!(fabsf(q5[2]) < SIN_MAX) || fabsf(q5[0]) > x * P.tan_half) break;
-        float chi2;
-        const int h = pick_hit(b, item, r, q5, C, z_base, &chi2);
+        const int h = pick_hit<G>(b, g, item, r, q5, C, z_base);
         if (h < 0) { ++misses; continue; }
-        const int2 q = b.s_q[h];
+        const int4 q = b.s_hit[h];
         chi2sum += kf_update(P, q5, C, q.x * Q - q5[0], (float)(q.y - z_base) * Q - q5[1]);
         if (!cov_ok(C)) { dead = true; break; }
         misses = 0;
-        hl[n++] = h;
+        if (g.gl == 0) hl[n] = h;
+        ++n;
         in_hit = h;
         in_x = x;
 #pragma unroll
@@ -839,97 +1021,142 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Buffe
 #pragma unroll
         for (int m = 0; m < 15; ++m) in_C[m] = C[m];
       }
-      if (!dead && n >= MIN_HITS) {
-        rec.n = n;
-#pragma unroll
-        for (int m = 0; m < 5; ++m) rec.p[m] = in_p[m];
-#pragma unroll
-        for (int m = 0; m < 15; ++m) rec.C[m] = in_C[m];
-        rec.chi2 = chi2sum;
-        rec.x_ref = in_x;
-        rec.z_in = b.s_q[in_hit].y;
-      }
     }
-    b.tl[t] = rec;
+    if (dead || n < MIN_HITS) n = 0;
+    // the 112-byte record, fields split over the lanes of the group
+    float* rf = reinterpret_cast<float*>(b.tl + t);
+    int* ri_ = reinterpret_cast<int*>(b.tl + t);
+    const int local = t - b.start_ex[b.item_off[item]];
+    const int z_in = n ? b.s_hit[in_hit].y : 0;
+    for (int fld = g.gl; fld < 27; fld += G) {
+      float fv = 0.f;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) fv = (fld == m) ? in_p[m] : fv;
+#pragma unroll
+      for (int m = 0; m < 15; ++m) fv = (fld == 5 + m) ? in_C[m] : fv;
+      if (fld < 20) rf[fld] = fv;
+      else if (fld == 20) rf[20] = chi2sum;
+      else if (fld == 21) rf[21] = in_x;
+      else if (fld == 22) ri_[22] = n;
+      else if (fld == 23) ri_[23] = z_base;
+      else if (fld == 24) ri_[24] = z_in;
+      else if (fld == 25) ri_[25] = item;
+      else ri_[26] = local;
+    }
+    g.sync();
   }
 }
 
+cudaError_t tpc_launch_tracklets(const Buffers& b, int group, int grid, int block, cudaStream_t s) {
+  switch (group) {
+    case 1: k_tracklets<1><<<grid, block, 0, s>>>(b); break;
+    case 2: k_tracklets<2><<<grid, block, 0, s>>>(b); break;
+    case 4: k_tracklets<4><<<grid, block, 0, s>>>(b); break;
+    case 8: k_tracklets<8><<<grid, block, 0, s>>>(b); break;
+    case 16: k_tracklets<16><<<grid, block, 0, s>>>(b); break;
+    default: k_tracklets<32><<<grid, block, 0, s>>>(b); break;
+  }
+  return cudaGetLastError();
+}
+
 // ============================================================================ S7
-__device__ __forceinline__ unsigned long long tl_key(const TrackletRec& r) {
-  return ((unsigned long long)(unsigned)r.n << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)r.local);
+__device__ __forceinline__ unsigned long long tl_key(int n, int local) {
+  return ((unsigned long long)(unsigned)n << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)local);
 }
 
 // Each hit goes to the tracklet with the largest key (more hits, then smaller
-// item-local id): one 64-bit atomicMax per (tracklet, hit).  Order-independent.
+// item-local id): one 64-bit atomicMax per (tracklet, hit); a warp per tracklet.
 __global__ void __launch_bounds__(256) k_select_max(const __grid_constant__ Buffers b) {
-  const DevParams& P = b.par;
   const int T = b.start_ex[b.N];
-  const int NR = P.n_rows;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
-    const TrackletRec& r = b.tl[t];
-    const int n = r.n;
+  const int NR = b.par.n_rows;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = warp; t < T; t += nwarps) {
+    const int n = b.tl[t].n;
     if (n < MIN_HITS) continue;
-    const unsigned long long key = tl_key(r);
+    const unsigned long long key = tl_key(n, b.tl[t].local);
     const int* hl = b.tl_hits + (size_t)t * NR;
-    for (int k = 0; k < n; ++k) atomicMax(&b.hit_key[hl[k]], key);
+    for (int k = lane; k < n; k += 32) atomicMax(&b.hit_key[hl[k]], key);
   }
 }
 
 // A tracklet keeps the hits it owns and is a track if it owns >= 10; with
 // time-frame slices only tracks whose innermost hit lies in the item's core.
 __global__ void __launch_bounds__(256) k_select_own(const __grid_constant__ Buffers b) {
-  const DevParams& P = b.par;
   const int T = b.start_ex[b.N];
-  const int NR = P.n_rows;
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+  const int NR = b.par.n_rows;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = warp; t < T; t += nwarps) {
     const TrackletRec& r = b.tl[t];
+    const int n = r.n;
     unsigned long long out = 0;
-    if (r.n >= MIN_HITS) {
-      const unsigned long long key = tl_key(r);
+    if (n >= MIN_HITS) {
+      const unsigned long long key = tl_key(n, r.local);
       const int* hl = b.tl_hits + (size_t)t * NR;
       int own = 0;
-      for (int k = 0; k < r.n; ++k) own += b.hit_key[hl[k]] == key;
+      for (int k = lane; k < n; k += 32) own += b.hit_key[hl[k]] == key;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) own += __shfl_xor_sync(0xffffffffu, own, o);
       bool keep = own >= MIN_HITS;
       if (keep && b.item_core) keep = r.z_in >= b.item_core[2 * r.item] && r.z_in < b.item_core[2 * r.item + 1];
       if (keep) out = (1ull << 32) | (unsigned long long)own;
     }
-    b.tl_cnt[t] = out;
+    if (lane == 0) b.tl_cnt[t] = out;
   }
 }
 
 // ============================================================================ S8
+// Track records and owned cluster ids (innermost first), a warp per tracklet.
 __global__ void __launch_bounds__(256) k_output(const __grid_constant__ Buffers b) {
-  const DevParams& P = b.par;
   const int T = b.start_ex[b.N];
-  const int NR = P.n_rows;
+  const int NR = b.par.n_rows;
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
   tpc_track_t* trk = reinterpret_cast<tpc_track_t*>(b.trk);
-  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
-    if (b.tl_cnt[t] == 0) continue;
+  for (int t = warp; t < T; t += nwarps) {
+    const unsigned long long cnt = b.tl_cnt[t];
+    if (cnt == 0) continue;
     const TrackletRec& r = b.tl[t];
     const unsigned long long ex = b.tl_ex[t];
     const unsigned ti = (unsigned)(ex >> 32);
-    unsigned io = (unsigned)(ex & 0xFFFFFFFFull);
-    tpc_track_t o;
-    o.x_ref = r.x_ref;
-    o.y = r.p[0];
-    o.z = r.p[1] + (float)r.z_base * (1.0f / TPC_QSCALE);
-    o.snp = r.p[2];
-    o.tgl = r.p[3];
-    o.qpt = r.p[4];
+    const unsigned io = (unsigned)(ex & 0xFFFFFFFFull);
+    if (lane == 0) {
+      tpc_track_t o;
+      o.x_ref = r.x_ref;
+      o.y = r.p[0];
+      o.z = r.p[1] + (float)r.z_base * (1.0f / TPC_QSCALE);
+      o.snp = r.p[2];
+      o.tgl = r.p[3];
+      o.qpt = r.p[4];
 #pragma unroll
-    for (int m = 0; m < 15; ++m) o.cov[m] = r.C[m];
-    o.chi2 = r.chi2;
-    o.ndf = 2 * r.n - 5;
-    o.item = r.item;
-    o.sector = b.item_sector ? b.item_sector[r.item] : 0u;
-    o.event = b.item_event ? b.item_event[r.item] : 0u;
-    o.first_cluster = io;
-    o.n_clusters = (unsigned)(b.tl_cnt[t] & 0xFFFFFFFFull);
-    trk[ti] = o;
-    const unsigned long long key = tl_key(r);
+      for (int m = 0; m < 15; ++m) o.cov[m] = r.C[m];
+      o.chi2 = r.chi2;
+      o.ndf = 2 * r.n - 5;
+      o.item = r.item;
+      o.sector = b.item_sector ? b.item_sector[r.item] : 0u;
+      o.event = b.item_event ? b.item_event[r.item] : 0u;
+      o.first_cluster = io;
+      o.n_clusters = (unsigned)(cnt & 0xFFFFFFFFull);
+      trk[ti] = o;
+      b.trk_tl[ti] = t;
+    }
+    const unsigned long long key = tl_key(r.n, r.local);
     const int* hl = b.tl_hits + (size_t)t * NR;
-    for (int k = r.n - 1; k >= 0; --k)  // innermost first
-      if (b.hit_key[hl[k]] == key) b.trk_ids[io++] = (uint32_t)b.s_id[hl[k]];
+    // innermost first: walk the hit list backwards, compact owned hits in order
+    unsigned done = 0;
+    for (int base = 0; base < r.n; base += 32) {
+      const int k = r.n - 1 - (base + lane);
+      int h = -1;
+      bool own = false;
+      if (k >= 0) {
+        h = hl[k];
+        own = b.hit_key[h] == key;
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, own);
+      if (own) b.trk_ids[io + done + __popc(bal & ((1u << lane) - 1))] = (uint32_t)b.s_hit[h].z;
+      done += __popc(bal);
+    }
   }
 }
 
@@ -943,9 +1170,8 @@ __global__ void k_counts(const __grid_constant__ Buffers b) {
 
 // ============================================================================ host launchers
 cudaError_t tpc_configure_kernels(int sort_smem, int link_smem) {
-  cudaError_t e = cudaFuncSetAttribute(k_row_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, sort_smem);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(k_links, cudaFuncAttributeMaxDynamicSharedMemorySize, link_smem);
+  (void)link_smem;
+  return cudaFuncSetAttribute(k_row_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, sort_smem);
 }
 
 static void scan_i32(const int* in, int* out, long long n, unsigned long long* bsum, int G, cudaStream_t s) {
@@ -985,14 +1211,23 @@ cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t 
   // positions left unwritten by rejected clusters must read as "no link"
   cudaMemsetAsync(b.up_raw, 0xFF, sizeof(int) * (size_t)b.N, s);
   cudaMemsetAsync(b.dn_raw, 0xFF, sizeof(int) * (size_t)b.N, s);
-  k_links<<<M, 128, c.link_smem, s>>>(b, c.link_smem);
+  {
+    // default: about 8 CTAs per SM
+    int rpc = c.link_rows;
+    if (rpc <= 0) {
+      const long long want = (long long)c.num_sms * 8;
+      rpc = (int)std::min<long long>(NR, std::max<long long>(1, ((long long)b.I * NR + want - 1) / want));
+    }
+    const int nrb = (NR + rpc - 1) / rpc;
+    k_links<<<b.I * nrb, LINK_THREADS, 0, s>>>(b, rpc);
+  }
   mark(5);
   const int gN = (int)((b.N + 255) / 256) < c.num_sms * 8 ? (int)((b.N + 255) / 256) : c.num_sms * 8;
   k_clean_start<<<gN > 0 ? gN : 1, 256, 0, s>>>(b);
   scan_i32(b.flags, b.start_ex, b.N, b.scan_tmp, c.grid_scan, s);
   k_starts<<<gN > 0 ? gN : 1, 256, 0, s>>>(b);
   mark(6);
-  k_tracklets<<<c.grid_tl, c.block_tl, 0, s>>>(b);
+  tpc_launch_tracklets(b, c.tl_group, c.grid_tl, c.block_tl, s);
   mark(7);
   k_select_max<<<c.num_sms * 4, 256, 0, s>>>(b);
   k_select_own<<<c.num_sms * 4, 256, 0, s>>>(b);

@@ -47,6 +47,11 @@ class tpc_clusters(C.Structure):
                 ("item_event", C.c_void_p), ("item_core", C.c_void_p), ("on_device", C.c_int)]
 
 
+class tpc_tuning(C.Structure):
+    _fields_ = [("tracklet_lanes", C.c_int), ("tracklet_block", C.c_int), ("tracklet_blocks_per_sm", C.c_int),
+                ("sort_smem", C.c_int), ("link_rows", C.c_int)]
+
+
 TRACK_DTYPE = np.dtype([("x_ref", "<f4"), ("y", "<f4"), ("z", "<f4"), ("snp", "<f4"), ("tgl", "<f4"),
                         ("qpt", "<f4"), ("cov", "<f4", (15,)), ("chi2", "<f4"), ("ndf", "<i4"), ("item", "<u4"),
                         ("sector", "<u4"), ("event", "<u4"), ("first_cluster", "<u4"), ("n_clusters", "<u4")])
@@ -63,6 +68,9 @@ _sig = {
     "tpc_stage_times": ([_P, C.POINTER(C.c_float), C.c_int, C.POINTER(C.c_int)], C.c_int),
     "tpc_stage_name": ([C.c_int], C.c_char_p),
     "tpc_debug_dump": ([_P, C.c_int, _P, C.c_uint64, C.POINTER(C.c_uint64)], C.c_int),
+    "tpc_set_tuning": ([_P, C.POINTER(tpc_tuning)], C.c_int),
+    "tpc_get_tuning": ([_P, C.POINTER(tpc_tuning)], C.c_int),
+    "tpc_autotune": ([_P, C.c_int, C.POINTER(tpc_tuning), C.POINTER(C.c_float)], C.c_int),
     "tpc_destroy": ([_P], None),
     "tpc_last_error": ([_P], C.c_char_p),
 }
@@ -123,6 +131,8 @@ class Tracker:
             import torch
             stream = torch.cuda.current_stream(device)
         sptr = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        if not sptr:
+            sptr = 1  # cudaStreamLegacy: torch's default stream (a NULL handle would mean a library stream)
         self.cfg = tpc_config(device, sptr, bz_tesla, n_rows, row_x_min, row_x_max, half_angle_deg, sigma_y, sigma_z,
                               MODE[mode], CORR[correction], max_clusters, max_items, alloc_ptr, int(profile))
         self.n_rows = n_rows
@@ -210,6 +220,21 @@ class Tracker:
         buf = np.zeros(int(n.value), dtype=np.int32)
         self._check(_lib.tpc_debug_dump(self._h, stage, _ptr(buf) if n.value else None, n.value, C.byref(n)))
         return buf
+
+    def set_tuning(self, **kw):
+        t = tpc_tuning(**kw)
+        self._check(_lib.tpc_set_tuning(self._h, C.byref(t)))
+
+    def get_tuning(self) -> dict:
+        t = tpc_tuning()
+        self._check(_lib.tpc_get_tuning(self._h, C.byref(t)))
+        return {f: getattr(t, f) for f, _ in tpc_tuning._fields_}
+
+    def autotune(self, iters: int = 3):
+        t = tpc_tuning()
+        us = C.c_float()
+        self._check(_lib.tpc_autotune(self._h, iters, C.byref(t), C.byref(us)))
+        return {f: getattr(t, f) for f, _ in tpc_tuning._fields_}, float(us.value)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -41,7 +41,11 @@ def compare_tracks(cl, trk, ids, ref, min_match=0.995, min_param=0.995):
     frac = len(pairs) / max(1, n_ref)
     good = 0
     worst = 0.0
+    same_sets = same_good = 0
+    bad_params = np.zeros(5, int)
+    worst_same = 0.0
     for i, j in pairs.items():
+        same = np.array_equal(ref_sets[i][1], gpu_sets[j][1])
         fr = ref["trk_f"][i]
         pg = np.array([trk["y"][j], trk["z"][j], trk["snp"][j], trk["tgl"][j], trk["qpt"][j]], np.float64)
         if abs(float(trk["x_ref"][j]) - fr[0]) > 1e-4:
@@ -51,7 +55,17 @@ def compare_tracks(cl, trk, ids, ref, min_match=0.995, min_param=0.995):
             pg = out[0]
         rel = np.abs(pg - fr[1:6]) / np.maximum(np.abs(fr[1:6]), FLOORS)
         worst = max(worst, float(rel.max()))
-        good += bool(np.all(rel <= 1e-3))
+        ok = bool(np.all(rel <= 1e-3))
+        good += ok
+        bad_params += rel > 1e-3
+        if same:
+            same_sets += 1
+            same_good += ok
+            worst_same = max(worst_same, float(rel.max()))
     pfrac = good / max(1, len(pairs))
-    return dict(n_ref=n_ref, n_gpu=len(gpu_sets), matched=frac, param_ok=pfrac, worst_rel=worst,
+    res = dict(n_ref=n_ref, n_gpu=len(gpu_sets), matched=frac, param_ok=pfrac, worst_rel=worst,
+                identical_sets=same_sets / max(1, len(pairs)), param_ok_identical=same_good / max(1, same_sets),
+                worst_rel_identical=worst_same, bad_by_param=bad_params.tolist(),
                 ok=frac >= min_match and pfrac >= min_param)
+    print("PARITY", res)
+    return res

@@ -193,3 +193,42 @@ def test_stage_times_profile():
         t.sync()
         st = t.stage_times()
     assert len(st) == 9 and all(v >= 0 for v in st.values())
+
+
+def test_every_launch_shape_gives_identical_output():
+    """Lane groups, block sizes and shared-memory budgets change only the speed."""
+    from paper_1910_12214_b300 import tpc
+    cl = synth.make_config2(seed=4, n_tracks=1500)
+    outs = []
+    with tpc.Tracker() as t:
+        t.load(cl)
+        for lanes, blk, sm, lr in [(1, 32, 4096, 1), (2, 64, 12288, 3), (4, 128, 2048, 152), (8, 64, 24576, 7),
+                                   (16, 128, 12288, -1), (32, 128, 12288, 40)]:
+            t.set_tuning(tracklet_lanes=lanes, tracklet_block=blk, tracklet_blocks_per_sm=8, sort_smem=sm,
+                         link_rows=lr)
+            t.track()
+            trk, ids = t.get_tracks()
+            outs.append((trk.tobytes(), ids.tobytes(), t.debug_dump(9).tobytes()))
+        best, us = t.autotune(iters=1)
+        trk, ids = t.get_tracks()
+        outs.append((trk.tobytes(), ids.tobytes(), t.debug_dump(9).tobytes()))
+    assert all(o == outs[0] for o in outs)
+    assert us > 0 and best["tracklet_lanes"] in (1, 2, 4, 8, 16, 32)
+
+
+def test_dense_rows_take_the_direct_neighbour_enumeration():
+    """More than 24 window candidates on one side of a hit: the neighbour search
+    falls back to enumerating the bins directly; links stay bit-exact."""
+    rng = np.random.default_rng(12)
+    n_rows = 6
+    x_max = 85.0 + 5 * 161.0 / 151.0
+    rows, ys, zs = [], [], []
+    for r in range(n_rows):
+        k = 60
+        rows += [r] * k
+        ys += list(rng.uniform(-1.5, 1.5, k))
+        zs += list(rng.uniform(-1.5, 1.5, k))
+    c = _Cl(np.zeros(len(rows)), ys, zs, rows, [0, len(rows)])
+    ref = oracle.run(c, oracle.OracleConfig(n_rows=n_rows, x_max=x_max))
+    trk, ids, d = run_gpu(c, n_rows=n_rows, row_x_max=x_max)
+    compare_stages(d, ref)

@@ -144,10 +144,10 @@ def _brute_links(qx, rowv, qy, qz):
         dxd = int(qx[r] - qx[r - 1])
         best = None
         for u in range(n):
-            if rowv[u] != r + 1 or abs(qy[u] - qy[h]) > dxu * 11 // 4 or abs(qz[u] - qz[h]) > dxu * 11 // 10:
+            if rowv[u] != r + 1 or abs(qy[u] - qy[h]) > dxu * 11 // 4 or abs(qz[u] - qz[h]) > dxu * 16 // 5:
                 continue
             for d in range(n):
-                if rowv[d] != r - 1 or abs(qy[d] - qy[h]) > dxd * 11 // 4 or abs(qz[d] - qz[h]) > dxd * 11 // 10:
+                if rowv[d] != r - 1 or abs(qy[d] - qy[h]) > dxd * 11 // 4 or abs(qz[d] - qz[h]) > dxd * 16 // 5:
                     continue
                 dY = (int(qy[u]) - int(qy[h])) * dxd - (int(qy[h]) - int(qy[d])) * dxu
                 dZ = (int(qz[u]) - int(qz[h])) * dxd - (int(qz[h]) - int(qz[d])) * dxu
