@@ -176,6 +176,34 @@ tpc_status tpc_get_tuning(tpc_ctx* ctx, tpc_tuning* t);
  * last run leaves the batch tracked with the chosen shape. */
 tpc_status tpc_autotune(tpc_ctx* ctx, int iters, tpc_tuning* best, float* best_us);
 
+/* Binning of ONE sector without any device allocation.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate GPU
+ * memory while they run (a real-time loop with a memory budget fixed at start,
+ * a plug-in inside a framework that owns all device memory, or code that must
+ * avoid cudaMalloc/cudaFree because they synchronise the device).  It needs no
+ * context: the caller passes device pointers for the inputs (y, z, row: n
+ * values each) and the outputs, and the work runs on `stream` (NULL = legacy
+ * default stream) on the current device.  The call waits for its stream before
+ * returning (it reads an error word).
+ *   sorted:    n x 4 int32: (qy, qz, original index, row) in canonical order
+ *              (row, bin, index); qy = rint(y * 1024), qz = rint(z * 1024);
+ *   rows_out:  n_rows x 8 int32: (pos0, n, ymin, zmin, shift, ny, nz, bin0);
+ *   first_out: 2n + 3 n_rows + 1 int32: first sorted position of every bin,
+ *              nbins + 1 entries per row starting at its bin0.
+ * The temporary storage lives in one fixed device array per GPU inside the
+ * library (16 bytes per cluster, TPC_NOALLOC_MAX_CLUSTERS clusters; held by
+ * every GPU that loads the library until the process exits).  Larger inputs
+ * are rejected with TPC_ERR_CAPACITY before any GPU work; n_rows must be
+ * 1..256.  The first call on a device looks up that array's device address,
+ * so make the first call on each device before any stream capture.  Every
+ * call uses the same array and it keeps the previous call's contents; calls
+ * that overlap on the GPU (other streams, other host threads) race on it, so
+ * run them one after another.  Returns TPC_ERR_BAD_INPUT if a row is out of
+ * range or a coordinate is not finite (such clusters are left out). */
+#define TPC_NOALLOC_MAX_CLUSTERS 65536
+tpc_status tpc_bin_sector_noalloc(const float* y, const float* z, const int32_t* row, uint32_t n, int n_rows,
+                                  int32_t* sorted, int32_t* rows_out, int32_t* first_out, void* stream);
+
 /* Frees every device buffer and the context. */
 void tpc_destroy(tpc_ctx* ctx);
 

@@ -71,6 +71,7 @@ _sig = {
     "tpc_set_tuning": ([_P, C.POINTER(tpc_tuning)], C.c_int),
     "tpc_get_tuning": ([_P, C.POINTER(tpc_tuning)], C.c_int),
     "tpc_autotune": ([_P, C.c_int, C.POINTER(tpc_tuning), C.POINTER(C.c_float)], C.c_int),
+    "tpc_bin_sector_noalloc": ([_P, _P, _P, C.c_uint32, C.c_int, _P, _P, _P, _P], C.c_int),
     "tpc_destroy": ([_P], None),
     "tpc_last_error": ([_P], C.c_char_p),
 }
@@ -80,6 +81,7 @@ for _name, (_a, _r) in _sig.items():
     _f.restype = _r
 
 EXPORTED = sorted(_sig)
+NOALLOC_MAX_CLUSTERS = 65536
 
 
 class TpcError(RuntimeError):
