@@ -64,7 +64,8 @@ typedef struct {
   float row_x_min, row_x_max; /* radii of the first and last pad row [cm] (85, 246) */
   float sector_half_angle_deg;/* sector half opening angle (10) */
   float sigma_y, sigma_z;     /* cluster resolution used by the Kalman filter [cm] (0.1) */
-  tpc_mode mode;              /* PLAIN: one launch per step; BATCHED: persistent kernel */
+  tpc_mode mode;              /* PLAIN: one launch per step; BATCHED: persistent kernel over a
+                                 work queue of items (identical results) */
   tpc_corr correction;        /* space-point correction applied at load (NONE for now) */
   uint64_t max_clusters;      /* initial reservation (0 = grow on demand) */
   uint32_t max_items;         /* initial reservation (0 = grow on demand) */
@@ -136,7 +137,8 @@ tpc_status tpc_device_tracks(tpc_ctx* ctx, const tpc_track_t** trk, const uint32
                              const uint64_t** d_counts);
 
 /* Per-step device times of the last tpc_track() in microseconds (needs
- * cfg.profile = 1): us[i] for the steps named by tpc_stage_name(i). */
+ * cfg.profile = 1): us[i] for the steps named by tpc_stage_name(i); steps the
+ * last run's mode does not have read 0 (plain mode: 0..8, batched: 9..10). */
 tpc_status tpc_stage_times(tpc_ctx* ctx, float* us, int n, int* n_stages);
 const char* tpc_stage_name(int i);
 
@@ -164,6 +166,9 @@ typedef struct {
   int tracklet_blocks_per_sm;
   int sort_smem;
   int link_rows;
+  int mode;          /* 1 = plain (one launch per step), 2 = batched (persistent kernel) */
+  int batch_lanes;   /* lanes per tracklet in the batched kernel: 1, 2 or 4 */
+  int use_graph;     /* 1 = launch directly, 2 = capture tpc_track once per load and replay it */
 } tpc_tuning;
 
 tpc_status tpc_set_tuning(tpc_ctx* ctx, const tpc_tuning* t);

@@ -35,6 +35,12 @@ struct tpc_ctx {
   bool input_on_device = false;
   cudaEvent_t ev[TPC_N_STAGES + 1] = {};
   bool have_events = false;
+  // host copies used by the debug dump and the work queue
+  std::vector<uint64_t> h_item_off;
+  int* own_queue = nullptr;
+  // execution mode and CUDA graph of tpc_track
+  bool batched = false, use_graph = false, last_batched = false;
+  cudaGraphExec_t graph = nullptr;
 };
 
 namespace {
@@ -62,7 +68,15 @@ void* dev_alloc(tpc_ctx* c, size_t bytes) {
   return p;
 }
 
+void drop_graph(tpc_ctx* c) {
+  if (c->graph) cudaGraphExecDestroy(c->graph);
+  c->graph = nullptr;
+}
+
+bool capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
+
 void free_all(tpc_ctx* c) {
+  drop_graph(c);
   if (!c->blocks.empty()) cudaStreamSynchronize(c->stream);
   for (void* p : c->blocks) {
     if (c->has_alloc)
@@ -87,7 +101,7 @@ tpc_status reserve(tpc_ctx* c, long long N, long long I, long long n_chunks) {
   n_chunks = std::max<long long>(n_chunks, 1);
   const int NR = c->cfg.n_rows;
   const long long M = I * NR;
-  const long long Tcap = N / 3 + 1;
+  const long long Tcap = N / 3 + I + 1;  // starts <= N/3 in total and <= n/3 per item
   Buffers& b = c->b;
   bool ok = true;
   auto A = [&](size_t bytes) -> void* {
@@ -132,6 +146,16 @@ tpc_status reserve(tpc_ctx* c, long long N, long long I, long long n_chunks) {
   b.counts = (unsigned long long*)A(8 * 4);
   b.err = (unsigned int*)A(16);
   b.scan_tmp = (unsigned long long*)A(8 * 1040);
+  c->own_queue = (int*)A(4 * I);
+  b.queue = c->own_queue;
+  b.queue_head = (int*)A(16);
+  b.item_cnt = (unsigned long long*)A(8 * I);
+  b.item_ex = (unsigned long long*)A(8 * I);
+  b.item_ntl = (int*)A(4 * I);
+  b.item_tl_ex = (int*)A(4 * I);
+  b.trk_tmp = A(sizeof(tpc_track_t) * Tcap);
+  b.trk_tl_tmp = (int*)A(4 * Tcap);
+  b.ids_tmp = (uint32_t*)A(4 * N);
   b.T_cap = (int)Tcap;
   if (!ok) {
     free_all(c);
@@ -203,7 +227,11 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
   L.block_tl = 128;
   L.grid_tl = sms * 16;
   L.tl_group = 1;
-  if ((e = tpc_configure_kernels(L.sort_smem, L.link_smem)) != cudaSuccess) {
+  L.batch_group = 1;
+  c->batched = cfg->mode == TPC_MODE_BATCHED;
+  c->use_graph = capturable(c->stream);
+  if ((e = tpc_configure_kernels(L.sort_smem, L.link_smem)) != cudaSuccess ||
+      (e = tpc_batched_occupancy(L.batch_per_sm)) != cudaSuccess) {
     cudaGetLastError();
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -294,11 +322,21 @@ extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
     e = cudaMemcpyAsync((void*)sec_dev, cl->item_sector, 4 * I, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess && cl->item_event)
     e = cudaMemcpyAsync((void*)ev_dev, cl->item_event, 4 * I, cudaMemcpyHostToDevice, c->stream);
+  // work queue of the batched form: items by decreasing cluster count (longest first)
+  c->h_item_off.assign(cl->item_off, cl->item_off + cl->n_items + 1);
+  std::vector<int> order(cl->n_items);
+  for (uint32_t i = 0; i < cl->n_items; ++i) order[i] = (int)i;
+  std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
+    return cl->item_off[u + 1] - cl->item_off[u] > cl->item_off[v + 1] - cl->item_off[v];
+  });
+  if (e == cudaSuccess && cl->n_items)
+    e = cudaMemcpyAsync(c->own_queue, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.err, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.counts, 0, 32, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "metadata upload");
   // host arrays must stay valid only during the call
   if (!cl->on_device && (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
+  drop_graph(c);  // kernel arguments changed
   c->loaded = true;
   c->tracked = false;
   return TPC_OK;
@@ -313,8 +351,31 @@ extern "C" tpc_status tpc_track(tpc_ctx* c) {
     c->tracked = true;
     return TPC_OK;  // counts were zeroed at load
   }
-  e = tpc_launch_plain(c->b, c->lc, c->stream, c->have_events ? c->ev : nullptr);
+  auto launch = [&]() {
+    return c->batched ? tpc_launch_batched(c->b, c->lc, c->stream, c->have_events ? c->ev : nullptr)
+                      : tpc_launch_plain(c->b, c->lc, c->stream, c->have_events ? c->ev : nullptr);
+  };
+  if (c->use_graph && capturable(c->stream)) {
+    if (!c->graph) {
+      cudaGraph_t g = nullptr;
+      e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+      if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
+      cudaError_t le = launch();
+      e = cudaStreamEndCapture(c->stream, &g);
+      if (le != cudaSuccess) e = le;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {
+        c->graph = nullptr;
+        return cuda_fail(c, e, "graph build");
+      }
+    }
+    e = cudaGraphLaunch(c->graph, c->stream);
+  } else {
+    e = launch();
+  }
   if (e != cudaSuccess) return cuda_fail(c, e, "launch");
+  c->last_batched = c->batched;
   c->tracked = true;
   return TPC_OK;
 }
@@ -363,9 +424,9 @@ extern "C" tpc_status tpc_device_tracks(tpc_ctx* c, const tpc_track_t** trk, con
   return TPC_OK;
 }
 
-static const char* kStageNames[TPC_N_STAGES] = {"quantise+row_stats", "row_setup",   "group_scatter",
-                                                "row_sort",           "links",       "clean+starts",
-                                                "tracklets",          "selection",   "output"};
+static const char* kStageNames[TPC_N_STAGES] = {"quantise+row_stats", "row_setup", "group_scatter", "row_sort",
+                                                "links", "clean+starts", "tracklets", "selection", "output",
+                                                "batched_items", "batched_concat"};
 
 extern "C" const char* tpc_stage_name(int i) { return (i >= 0 && i < TPC_N_STAGES) ? kStageNames[i] : ""; }
 
@@ -378,11 +439,12 @@ extern "C" tpc_status tpc_stage_times(tpc_ctx* c, float* us, int n, int* n_stage
   if (e != cudaSuccess) return cuda_fail(c, e, "stream");
   for (int i = 0; i < TPC_N_STAGES && i < n; ++i) {
     float ms = 0.f;
-    if (cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) != cudaSuccess) {
+    const bool mine = c->last_batched ? (i >= 9) : (i < 9);
+    if (mine && cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) != cudaSuccess) {
       cudaGetLastError();
       ms = 0.f;
     }
-    us[i] = ms * 1000.f;
+    us[i] = mine ? ms * 1000.f : 0.f;
   }
   return TPC_OK;
 }
@@ -405,8 +467,24 @@ extern "C" tpc_status tpc_debug_dump(tpc_ctx* c, int stage, int32_t* buf, uint64
   std::vector<RowInfo> rows(M);
   if (M && (e = cudaMemcpy(rows.data(), b.rows, sizeof(RowInfo) * M, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(c, e, "dump");
+  // tracklet storage index of every tracklet in canonical order (plain: 0..T-1;
+  // batched: item k's tracklets at item_off[k]/3 + k + local)
   int T = 0;
-  if ((e = cudaMemcpy(&T, b.start_ex + N, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(c, e, "dump");
+  std::vector<int> tl_index;
+  if (!c->last_batched) {
+    if ((e = cudaMemcpy(&T, b.start_ex + N, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(c, e, "dump");
+    tl_index.resize(T);
+    for (int t = 0; t < T; ++t) tl_index[t] = t;
+  } else {
+    std::vector<int> ntl;
+    if ((e = D2H(ntl, b.item_ntl, b.I)) != cudaSuccess) return cuda_fail(c, e, "dump");
+    for (int k = 0; k < b.I && k + 1 < (int)c->h_item_off.size(); ++k) {
+      const int tlb = (int)(c->h_item_off[k] / 3) + k;
+      for (int l = 0; l < ntl[k]; ++l) tl_index.push_back(tlb + l);
+    }
+    T = (int)tl_index.size();
+  }
+  const int Tmax = tl_index.empty() ? 0 : *std::max_element(tl_index.begin(), tl_index.end()) + 1;
   switch (stage) {
     case 0: {
       out.resize(3 * N);
@@ -443,20 +521,20 @@ extern "C" tpc_status tpc_debug_dump(tpc_ctx* c, int stage, int32_t* buf, uint64
       break;
     }
     case 7: {
-      if ((e = D2H(tmp, b.starts, T)) != cudaSuccess) return cuda_fail(c, e, "dump");
-      for (int t = 0; t < T; ++t) out.push_back(sid[tmp[t]]);
+      if ((e = D2H(tmp, b.starts, Tmax)) != cudaSuccess) return cuda_fail(c, e, "dump");
+      for (int t : tl_index) out.push_back(sid[tmp[t]]);
       break;
     }
     case 8:
     case 9: {
-      std::vector<TrackletRec> tl(T);
-      if (T && (e = cudaMemcpy(tl.data(), b.tl, sizeof(TrackletRec) * T, cudaMemcpyDeviceToHost)) != cudaSuccess)
+      std::vector<TrackletRec> tl(Tmax);
+      if (Tmax && (e = cudaMemcpy(tl.data(), b.tl, sizeof(TrackletRec) * Tmax, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(c, e, "dump");
       if (stage == 8) {
-        for (int t = 0; t < T; ++t) out.push_back(tl[t].n);
+        for (int t : tl_index) out.push_back(tl[t].n);
       } else {
-        if ((e = D2H(tmp, b.tl_hits, (size_t)T * NR)) != cudaSuccess) return cuda_fail(c, e, "dump");
-        for (int t = 0; t < T; ++t)
+        if ((e = D2H(tmp, b.tl_hits, (size_t)Tmax * NR)) != cudaSuccess) return cuda_fail(c, e, "dump");
+        for (int t : tl_index)
           for (int k = 0; k < tl[t].n; ++k) out.push_back(sid[tmp[(size_t)t * NR + k]]);
       }
       break;
@@ -503,9 +581,26 @@ tpc_status apply_tuning(tpc_ctx* c, const tpc_tuning& t) {
     if (t.link_rows < -1 || t.link_rows > TPC_MAX_ROWS) return fail(c, TPC_ERR_INVALID_ARG, "link_rows out of range");
     L.link_rows = t.link_rows < 0 ? 0 : t.link_rows;
   }
+  bool batched = c->batched, use_graph = c->use_graph;
+  if (t.mode) {
+    if (t.mode != 1 && t.mode != 2) return fail(c, TPC_ERR_INVALID_ARG, "mode must be 1 (plain) or 2 (batched)");
+    batched = t.mode == 2;
+  }
+  if (t.batch_lanes) {
+    if (t.batch_lanes != 1 && t.batch_lanes != 2 && t.batch_lanes != 4)
+      return fail(c, TPC_ERR_INVALID_ARG, "batch_lanes must be 1, 2 or 4");
+    L.batch_group = t.batch_lanes;
+  }
+  if (t.use_graph) {
+    if (t.use_graph != 1 && t.use_graph != 2) return fail(c, TPC_ERR_INVALID_ARG, "use_graph must be 1 or 2");
+    use_graph = t.use_graph == 2 && capturable(c->stream);
+  }
   cudaError_t e = tpc_configure_kernels(L.sort_smem, L.link_smem);
   if (e != cudaSuccess) return cuda_fail(c, e, "kernel attributes");
   c->lc = L;
+  c->batched = batched;
+  c->use_graph = use_graph;
+  drop_graph(c);
   return TPC_OK;
 }
 }  // namespace
@@ -524,6 +619,9 @@ extern "C" tpc_status tpc_get_tuning(tpc_ctx* c, tpc_tuning* t) {
   t->tracklet_blocks_per_sm = c->lc.grid_tl / std::max(1, c->lc.num_sms);
   t->sort_smem = c->lc.sort_smem;
   t->link_rows = c->lc.link_rows ? c->lc.link_rows : -1;
+  t->mode = c->batched ? 2 : 1;
+  t->batch_lanes = c->lc.batch_group;
+  t->use_graph = c->use_graph ? 2 : 1;
   return TPC_OK;
 }
 
@@ -532,12 +630,14 @@ extern "C" tpc_status tpc_autotune(tpc_ctx* c, int iters, tpc_tuning* best_out, 
   if (!c->loaded) return fail(c, TPC_ERR_STATE, "tpc_autotune before tpc_load_clusters");
   cudaError_t e = cudaSetDevice(c->cfg.device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  // plain-mode shapes, then shared memory and row blocks, then the batched kernel
   std::vector<tpc_tuning> cand;
   for (int lanes : {1, 2, 4, 8, 16, 32})
     for (int blk : {32, 64, 128})
-      for (int per_sm : {8, 16, 32}) cand.push_back({lanes, blk, per_sm, 0, 0});
+      for (int per_sm : {8, 16, 32}) cand.push_back({lanes, blk, per_sm, 0, 0, 1, 0, 0});
   for (int sm : {6 * 1024, 12 * 1024, 24 * 1024})
-    for (int lr : {-1, 4, 16, 152}) cand.push_back({0, 0, 0, sm, lr});
+    for (int lr : {-1, 4, 16, 152}) cand.push_back({0, 0, 0, sm, lr, 1, 0, 0});
+  for (int bl : {1, 2, 4}) cand.push_back({0, 0, 0, 0, 0, 2, bl, 0});
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
@@ -571,10 +671,13 @@ extern "C" tpc_status tpc_autotune(tpc_ctx* c, int iters, tpc_tuning* best_out, 
       t.tracklet_lanes = best.tracklet_lanes;
       t.tracklet_block = best.tracklet_block;
       t.tracklet_blocks_per_sm = best.tracklet_blocks_per_sm;
-    } else {
+    }
+    if (!t.sort_smem) {
       t.sort_smem = best.sort_smem;
       t.link_rows = best.link_rows;
     }
+    if (!t.batch_lanes) t.batch_lanes = best.batch_lanes;
+    t.use_graph = best.use_graph;
     float us = 0.f;
     st = time_cfg(t, &us);
     if (st != TPC_OK) break;

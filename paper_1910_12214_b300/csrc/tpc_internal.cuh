@@ -100,9 +100,19 @@ struct Buffers {
   unsigned long long* counts;  // [0] n_trk, [1] n_ids, [2] n_tracklets
   unsigned int* err;
   unsigned long long* scan_tmp;  // block sums
+  // batched form
+  const int* queue;               // items, longest first [I]
+  int* queue_head;                // atomic work-queue position
+  unsigned long long* item_cnt;   // (tracks << 32 | ids) per item [I]
+  unsigned long long* item_ex;    // exclusive scan of item_cnt [I]
+  int* item_ntl;                  // tracklets per item [I]
+  int* item_tl_ex;                // exclusive scan of item_ntl [I]
+  void* trk_tmp;                  // per-item track regions [T_cap]
+  int* trk_tl_tmp;                // tracklet storage index of every per-item track [T_cap]
+  uint32_t* ids_tmp;              // per-item cluster-id regions [N]
 };
 
-#define TPC_N_STAGES 9
+#define TPC_N_STAGES 11  // 9 plain-mode steps, then the batched kernel and its compaction
 
 struct LaunchCfg {
   int n_rows;
@@ -114,7 +124,11 @@ struct LaunchCfg {
   int grid_tl;    // blocks of k_tracklets
   int block_tl;   // threads per block of k_tracklets
   int tl_group;   // lanes per tracklet (1, 2, 4, 8, 16, 32)
+  int batch_group;  // lanes per tracklet in the batched kernel (1, 2, 4)
+  int batch_per_sm[3];  // resident CTAs per SM of the batched kernel for 1, 2, 4 lanes
 };
 
 cudaError_t tpc_configure_kernels(int sort_smem, int link_smem);
+cudaError_t tpc_batched_occupancy(int per_sm[3]);
 cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
+cudaError_t tpc_launch_batched(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);

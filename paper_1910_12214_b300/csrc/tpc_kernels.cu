@@ -354,6 +354,117 @@ __device__ __forceinline__ void bin_range(long long lo, long long hi, int vmin, 
 // dY = (qy_u-qy_h)*dx_dn - (qy_h-qy_d)*dx_up (int64), accepted if
 // m <= ((dx_up+dx_dn)*512)^2; ties: smaller id_u, then smaller id_d.  Rows 0 and
 // n_rows-1 get no links (targets only).  Neighbour rows are read through L1.
+namespace {
+// Neighbour search of one hit at sorted position pos on inner row r of an item
+// (rows[r - lo] is row r); s_cu / s_cd are this thread's candidate lists.
+template <int W>
+__device__ __forceinline__ void link_hit(const Buffers& b, const RowInfo* rows, int lo, int pos, int4 qh, int r,
+                                         int (*s_cu)[W], int (*s_cd)[W], int t) {
+  const DevParams& P = b.par;
+  const RowInfo U = rows[r + 1 - lo], D = rows[r - 1 - lo];
+  const long long dxu = P.qx[r + 1] - P.qx[r];
+  const long long dxd = P.qx[r] - P.qx[r - 1];
+  const long long wyu = dxu * 11 / 4, wzu = dxu * 16 / 5;
+  const long long wyd = dxd * 11 / 4, wzd = dxd * 16 / 5;
+  const long long cut = (dxu + dxd) * LINK_D;
+  const long long cut2 = cut * cut;
+  const long long yh = qh.x, zh = qh.y;
+  // candidates of each side: hits inside the window, from one contiguous hit
+  // range per y-bin row (the z-bins of a y-bin row are adjacent)
+  int nu = 0, nd = 0;
+  bool ovf = false;
+  {
+    int y0, y1, z0, z1;
+    bin_range(yh - wyu, yh + wyu, U.ymin, U.shift, U.ny, &y0, &y1);
+    bin_range(zh - wzu, zh + wzu, U.zmin, U.shift, U.nz, &z0, &z1);
+    if (z1 >= z0)
+      for (int iy = y0; iy <= y1; ++iy) {
+        const int b0 = U.bin0 + iy * U.nz + z0;
+        const int e_ = b.first[b0 + z1 - z0 + 1];
+        for (int pu = b.first[b0]; pu < e_; ++pu) {
+          const int4 q = b.s_hit[pu];
+          const long long ey = q.x - yh, ez = q.y - zh;
+          if (ey > wyu || -ey > wyu || ez > wzu || -ez > wzu) continue;
+          if (nu < LINK_MAXC) s_cu[nu++][t] = pu; else ovf = true;
+        }
+      }
+  }
+  {
+    int y0, y1, z0, z1;
+    bin_range(yh - wyd, yh + wyd, D.ymin, D.shift, D.ny, &y0, &y1);
+    bin_range(zh - wzd, zh + wzd, D.zmin, D.shift, D.nz, &z0, &z1);
+    if (z1 >= z0 && nu > 0)
+      for (int iy = y0; iy <= y1; ++iy) {
+        const int b0 = D.bin0 + iy * D.nz + z0;
+        const int e_ = b.first[b0 + z1 - z0 + 1];
+        for (int pd = b.first[b0]; pd < e_; ++pd) {
+          const int4 q = b.s_hit[pd];
+          const long long fy = yh - q.x, fz = zh - q.y;
+          if (fy > wyd || -fy > wyd || fz > wzd || -fz > wzd) continue;
+          if (nd < LINK_MAXC) s_cd[nd++][t] = pd; else ovf = true;
+        }
+      }
+  }
+  long long best = -1;
+  int bu = -1, bd = -1, bid_u = 0, bid_d = 0;
+  auto pair = [&](int pu, const int4& qu, int pd, const int4& qd) {
+    const long long ey = qu.x - yh, ez = qu.y - zh;
+    const long long fy = yh - qd.x, fz = zh - qd.y;
+    const long long dY = ey * dxd - fy * dxu;
+    const long long dZ = ez * dxd - fz * dxu;
+    const long long m = dY * dY + dZ * dZ;
+    if (m > cut2) return;
+    bool better = best < 0 || m < best;
+    if (!better && m == best) better = qu.z < bid_u || (qu.z == bid_u && qd.z < bid_d);
+    if (better) {
+      best = m;
+      bu = pu;
+      bd = pd;
+      bid_u = qu.z;
+      bid_d = qd.z;
+    }
+  };
+  if (!ovf) {
+    for (int iu = 0; iu < nu; ++iu) {
+      const int pu = s_cu[iu][t];
+      const int4 qu = b.s_hit[pu];
+      for (int id = 0; id < nd; ++id) {
+        const int pd = s_cd[id][t];
+        pair(pu, qu, pd, b.s_hit[pd]);
+      }
+    }
+  } else {
+    // more candidates than the lists hold (very dense rows): direct enumeration
+    int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
+    bin_range(yh - wyu, yh + wyu, U.ymin, U.shift, U.ny, &uy0, &uy1);
+    bin_range(zh - wzu, zh + wzu, U.zmin, U.shift, U.nz, &uz0, &uz1);
+    bin_range(yh - wyd, yh + wyd, D.ymin, D.shift, D.ny, &dy0, &dy1);
+    bin_range(zh - wzd, zh + wzd, D.zmin, D.shift, D.nz, &dz0, &dz1);
+    for (int iy = uy0; iy <= uy1; ++iy) {
+      const int bu0 = U.bin0 + iy * U.nz + uz0;
+      const int ue = b.first[bu0 + uz1 - uz0 + 1];
+      for (int pu = b.first[bu0]; pu < ue; ++pu) {
+        const int4 qu = b.s_hit[pu];
+        const long long ey = qu.x - yh, ez = qu.y - zh;
+        if (ey > wyu || -ey > wyu || ez > wzu || -ez > wzu) continue;
+        for (int jy = dy0; jy <= dy1; ++jy) {
+          const int bd0 = D.bin0 + jy * D.nz + dz0;
+          const int de = b.first[bd0 + dz1 - dz0 + 1];
+          for (int pd = b.first[bd0]; pd < de; ++pd) {
+            const int4 qd = b.s_hit[pd];
+            const long long fy = yh - qd.x, fz = zh - qd.y;
+            if (fy > wyd || -fy > wyd || fz > wzd || -fz > wzd) continue;
+            pair(pu, qu, pd, qd);
+          }
+        }
+      }
+    }
+  }
+  b.up_raw[pos] = bu;
+  b.dn_raw[pos] = bd;
+}
+}  // namespace
+
 __global__ void __launch_bounds__(LINK_THREADS) k_links(const __grid_constant__ Buffers b, int rows_per_cta) {
   const DevParams& P = b.par;
   __shared__ RowInfo s_rows[TPC_MAX_ROWS + 2];
@@ -377,107 +488,7 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(const __grid_constant__ 
       b.dn_raw[pos] = -1;
       continue;
     }
-    const RowInfo U = s_rows[r + 1 - lo], D = s_rows[r - 1 - lo];
-    const long long dxu = P.qx[r + 1] - P.qx[r];
-    const long long dxd = P.qx[r] - P.qx[r - 1];
-    const long long wyu = dxu * 11 / 4, wzu = dxu * 16 / 5;
-    const long long wyd = dxd * 11 / 4, wzd = dxd * 16 / 5;
-    const long long cut = (dxu + dxd) * LINK_D;
-    const long long cut2 = cut * cut;
-    const long long yh = qh.x, zh = qh.y;
-    // candidates of each side: hits inside the window, from one contiguous hit
-    // range per y-bin row (the z-bins of a y-bin row are adjacent)
-    int nu = 0, nd = 0;
-    bool ovf = false;
-    {
-      int y0, y1, z0, z1;
-      bin_range(yh - wyu, yh + wyu, U.ymin, U.shift, U.ny, &y0, &y1);
-      bin_range(zh - wzu, zh + wzu, U.zmin, U.shift, U.nz, &z0, &z1);
-      if (z1 >= z0)
-        for (int iy = y0; iy <= y1; ++iy) {
-          const int b0 = U.bin0 + iy * U.nz + z0;
-          const int e_ = b.first[b0 + z1 - z0 + 1];
-          for (int pu = b.first[b0]; pu < e_; ++pu) {
-            const int4 q = b.s_hit[pu];
-            const long long ey = q.x - yh, ez = q.y - zh;
-            if (ey > wyu || -ey > wyu || ez > wzu || -ez > wzu) continue;
-            if (nu < LINK_MAXC) s_cu[nu++][t] = pu; else ovf = true;
-          }
-        }
-    }
-    {
-      int y0, y1, z0, z1;
-      bin_range(yh - wyd, yh + wyd, D.ymin, D.shift, D.ny, &y0, &y1);
-      bin_range(zh - wzd, zh + wzd, D.zmin, D.shift, D.nz, &z0, &z1);
-      if (z1 >= z0 && nu > 0)
-        for (int iy = y0; iy <= y1; ++iy) {
-          const int b0 = D.bin0 + iy * D.nz + z0;
-          const int e_ = b.first[b0 + z1 - z0 + 1];
-          for (int pd = b.first[b0]; pd < e_; ++pd) {
-            const int4 q = b.s_hit[pd];
-            const long long fy = yh - q.x, fz = zh - q.y;
-            if (fy > wyd || -fy > wyd || fz > wzd || -fz > wzd) continue;
-            if (nd < LINK_MAXC) s_cd[nd++][t] = pd; else ovf = true;
-          }
-        }
-    }
-    long long best = -1;
-    int bu = -1, bd = -1, bid_u = 0, bid_d = 0;
-    auto pair = [&](int pu, const int4& qu, int pd, const int4& qd) {
-      const long long ey = qu.x - yh, ez = qu.y - zh;
-      const long long fy = yh - qd.x, fz = zh - qd.y;
-      const long long dY = ey * dxd - fy * dxu;
-      const long long dZ = ez * dxd - fz * dxu;
-      const long long m = dY * dY + dZ * dZ;
-      if (m > cut2) return;
-      bool better = best < 0 || m < best;
-      if (!better && m == best) better = qu.z < bid_u || (qu.z == bid_u && qd.z < bid_d);
-      if (better) {
-        best = m;
-        bu = pu;
-        bd = pd;
-        bid_u = qu.z;
-        bid_d = qd.z;
-      }
-    };
-    if (!ovf) {
-      for (int iu = 0; iu < nu; ++iu) {
-        const int pu = s_cu[iu][t];
-        const int4 qu = b.s_hit[pu];
-        for (int id = 0; id < nd; ++id) {
-          const int pd = s_cd[id][t];
-          pair(pu, qu, pd, b.s_hit[pd]);
-        }
-      }
-    } else {
-      // more candidates than the lists hold (very dense rows): direct enumeration
-      int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
-      bin_range(yh - wyu, yh + wyu, U.ymin, U.shift, U.ny, &uy0, &uy1);
-      bin_range(zh - wzu, zh + wzu, U.zmin, U.shift, U.nz, &uz0, &uz1);
-      bin_range(yh - wyd, yh + wyd, D.ymin, D.shift, D.ny, &dy0, &dy1);
-      bin_range(zh - wzd, zh + wzd, D.zmin, D.shift, D.nz, &dz0, &dz1);
-      for (int iy = uy0; iy <= uy1; ++iy) {
-        const int bu0 = U.bin0 + iy * U.nz + uz0;
-        const int ue = b.first[bu0 + uz1 - uz0 + 1];
-        for (int pu = b.first[bu0]; pu < ue; ++pu) {
-          const int4 qu = b.s_hit[pu];
-          const long long ey = qu.x - yh, ez = qu.y - zh;
-          if (ey > wyu || -ey > wyu || ez > wzu || -ez > wzu) continue;
-          for (int jy = dy0; jy <= dy1; ++jy) {
-            const int bd0 = D.bin0 + jy * D.nz + dz0;
-            const int de = b.first[bd0 + dz1 - dz0 + 1];
-            for (int pd = b.first[bd0]; pd < de; ++pd) {
-              const int4 qd = b.s_hit[pd];
-              const long long fy = yh - qd.x, fz = zh - qd.y;
-              if (fy > wyd || -fy > wyd || fz > wzd || -fz > wzd) continue;
-              pair(pu, qu, pd, qd);
-            }
-          }
-        }
-      }
-    }
-    b.up_raw[pos] = bu;
-    b.dn_raw[pos] = bd;
+    link_hit<LINK_THREADS>(b, s_rows, lo, pos, qh, r, s_cu, s_cd, t);
   }
 }
 
@@ -882,168 +893,177 @@ __device__ __forceinline__ int pick_hit(const Buffers& b, const Grp<G>& g, int i
 // step.  A non-finite or non-positive covariance diagonal drops the tracklet.
 // z is carried relative to the start hit (z_base) so that FP32 keeps its
 // precision for time-frame z' of thousands of cm.
+// One tracklet from the start hit at sorted position `start`, built by a group
+// of G lanes: the record goes to b.tl[tl] and the hit list to
+// b.tl_hits[tl * n_rows ...]; `local` is the tracklet's item-local id.
 template <int G>
-__global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Buffers b) {
+__device__ __forceinline__ void tracklet_build(const Buffers& b, const Grp<G>& g, int start, int tl, int local) {
   const DevParams& P = b.par;
-  const Grp<G> g;
-  const int T = b.start_ex[b.N];
   const int NR = P.n_rows;
   const float Q = 1.0f / TPC_QSCALE;
-  const int grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
-  const int ngrp = (gridDim.x * blockDim.x) / G;
-  for (int t = grp; t < T; t += ngrp) {
-    const int start = b.starts[t];
-    const int4 hs = b.s_hit[start];
-    const int key = hs.w;
-    const int item = key / NR;
-    const int r0 = key - item * NR;
-    const int z_base = hs.y;
-    int* hl = b.tl_hits + (size_t)t * NR;
-    // chain walk (pointer chasing; every lane of the group loads the same address)
-    int L = 0;
-    for (int h = start; h >= 0 && L < NR; h = b.up[h]) {
-      if (g.gl == 0) hl[L] = h;
-      ++L;
+  const int4 hs = b.s_hit[start];
+  const int key = hs.w;
+  const int item = key / NR;
+  const int r0 = key - item * NR;
+  const int z_base = hs.y;
+  int* hl = b.tl_hits + (size_t)tl * NR;
+  // chain walk (pointer chasing; every lane of the group loads the same address)
+  int L = 0;
+  for (int h = start; h >= 0 && L < NR; h = b.up[h]) {
+    if (g.gl == 0) hl[L] = h;
+    ++L;
+  }
+  g.sync();
+  const int4 qa = b.s_hit[hl[0]], qm = b.s_hit[hl[L / 2]], qc = b.s_hit[hl[L - 1]];
+  const float x1 = P.x[r0], x2 = P.x[r0 + L / 2], x3 = P.x[r0 + L - 1];
+  const float y1 = qa.x * Q, y2 = qm.x * Q, y3 = qc.x * Q;
+  const float z3 = (float)(qc.y - z_base) * Q;
+  const float dx13 = x3 - x1, dy13 = y3 - y1;
+  const float d13 = sqrtf(dx13 * dx13 + dy13 * dy13);
+  const float d12 = sqrtf((x2 - x1) * (x2 - x1) + (y2 - y1) * (y2 - y1));
+  const float d23 = sqrtf((x3 - x2) * (x3 - x2) + (y3 - y2) * (y3 - y2));
+  const float cross = (x2 - x1) * (y3 - y1) - (y2 - y1) * (x3 - x1);
+  const float kappa = -2.0f * cross / (d12 * d23 * d13);
+  const float u = fminf(1.0f, fmaxf(-1.0f, 0.5f * kappa * d13));
+  const float phi1 = atan2f(dy13, dx13) + asinf(u);
+  const float arc = d13 * asin_over_u(u);
+  float p[5] = {y1, 0.0f, sinf(phi1), z3 / arc, kappa / P.kB};
+  float C[15];
+  set_c0(P, C);
+  float x = x1;
+  int out_row = r0, out_hit = start;
+  float out_p[5] = {p[0], p[1], p[2], p[3], p[4]};
+  float ov2 = C[ix(2, 2)], ov3 = C[ix(3, 3)], ov4 = C[ix(4, 4)];
+  bool alive = true, dead = false;
+  // (i) chain: the lanes prefetch G chain hits at a time, broadcast in order
+  for (int c0 = 1; c0 < L && alive && !dead; c0 += G) {
+    int hpos = 0;
+    int4 mine = make_int4(0, 0, 0, 0);
+    if (c0 + g.gl < L) {
+      hpos = hl[c0 + g.gl];
+      mine = b.s_hit[hpos];
     }
-    g.sync();
-    const int4 qa = b.s_hit[hl[0]], qm = b.s_hit[hl[L / 2]], qc = b.s_hit[hl[L - 1]];
-    const float x1 = P.x[r0], x2 = P.x[r0 + L / 2], x3 = P.x[r0 + L - 1];
-    const float y1 = qa.x * Q, y2 = qm.x * Q, y3 = qc.x * Q;
-    const float z3 = (float)(qc.y - z_base) * Q;
-    const float dx13 = x3 - x1, dy13 = y3 - y1;
-    const float d13 = sqrtf(dx13 * dx13 + dy13 * dy13);
-    const float d12 = sqrtf((x2 - x1) * (x2 - x1) + (y2 - y1) * (y2 - y1));
-    const float d23 = sqrtf((x3 - x2) * (x3 - x2) + (y3 - y2) * (y3 - y2));
-    const float cross = (x2 - x1) * (y3 - y1) - (y2 - y1) * (x3 - x1);
-    const float kappa = -2.0f * cross / (d12 * d23 * d13);
-    const float u = fminf(1.0f, fmaxf(-1.0f, 0.5f * kappa * d13));
-    const float phi1 = atan2f(dy13, dx13) + asinf(u);
-    const float arc = d13 * asin_over_u(u);
-    float p[5] = {y1, 0.0f, sinf(phi1), z3 / arc, kappa / P.kB};
-    float C[15];
+    const int cend = min(L, c0 + G);
+    for (int i = c0; i < cend; ++i) {
+      const int qx_ = g.shfl(mine.x, i - c0);
+      const int qy_ = g.shfl(mine.y, i - c0);
+      const int hp = g.shfl(hpos, i - c0);
+      const int r = r0 + i;
+      if (!kf_propagate(P, p, C, x, P.x[r])) { alive = false; break; }
+      x = P.x[r];
+      if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) { alive = false; break; }
+      kf_update(P, p, C, qx_ * Q - p[0], (float)(qy_ - z_base) * Q - p[1]);
+      if (!cov_ok(C)) { dead = true; break; }
+      out_row = r;
+      out_hit = hp;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) out_p[m] = p[m];
+      ov2 = C[ix(2, 2)];
+      ov3 = C[ix(3, 3)];
+      ov4 = C[ix(4, 4)];
+    }
+  }
+  // (ii) outward extension
+  if (alive && !dead) {
+    int misses = 0;
+    for (int r = out_row + 1; r < NR && misses < MAX_MISS; ++r) {
+      if (!kf_propagate(P, p, C, x, P.x[r])) break;
+      x = P.x[r];
+      if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) break;
+      const int h = pick_hit<G>(b, g, item, r, p, C, z_base);
+      if (h < 0) { ++misses; continue; }
+      const int4 q = b.s_hit[h];
+      kf_update(P, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
+      if (!cov_ok(C)) { dead = true; break; }
+      misses = 0;
+      out_row = r;
+      out_hit = h;
+#pragma unroll
+      for (int m = 0; m < 5; ++m) out_p[m] = p[m];
+      ov2 = C[ix(2, 2)];
+      ov3 = C[ix(3, 3)];
+      ov4 = C[ix(4, 4)];
+    }
+  }
+  int n = 0;
+  float chi2sum = 0.f, in_x = x;
+  float in_p[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, in_C[15];
+#pragma unroll
+  for (int m = 0; m < 15; ++m) in_C[m] = 0.f;
+  int in_hit = out_hit;
+  if (!dead) {
+    // (iii) inward refit from the outermost hit: its y, z; the outward direction
+    // and curvature with variances inflated 100-fold (capped at the initial ones)
+    const int4 qo = b.s_hit[out_hit];
+    float q5[5] = {qo.x * Q, (float)(qo.y - z_base) * Q, out_p[2], out_p[3], out_p[4]};
     set_c0(P, C);
-    float x = x1;
-    int out_row = r0, out_hit = start;
-    float out_p[5] = {p[0], p[1], p[2], p[3], p[4]};
-    float ov2 = C[ix(2, 2)], ov3 = C[ix(3, 3)], ov4 = C[ix(4, 4)];
-    bool alive = true, dead = false;
-    // (i) chain: the lanes prefetch G chain hits at a time, broadcast in order
-    for (int c0 = 1; c0 < L && alive && !dead; c0 += G) {
-      int hpos = 0;
-      int4 mine = make_int4(0, 0, 0, 0);
-      if (c0 + g.gl < L) {
-        hpos = hl[c0 + g.gl];
-        mine = b.s_hit[hpos];
-      }
-      const int cend = min(L, c0 + G);
-      for (int i = c0; i < cend; ++i) {
-        const int qx_ = g.shfl(mine.x, i - c0);
-        const int qy_ = g.shfl(mine.y, i - c0);
-        const int hp = g.shfl(hpos, i - c0);
-        const int r = r0 + i;
-        if (!kf_propagate(P, p, C, x, P.x[r])) { alive = false; break; }
-        x = P.x[r];
-        if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) { alive = false; break; }
-        kf_update(P, p, C, qx_ * Q - p[0], (float)(qy_ - z_base) * Q - p[1]);
-        if (!cov_ok(C)) { dead = true; break; }
-        out_row = r;
-        out_hit = hp;
+    C[ix(2, 2)] = fminf(1.0f, INFLATE * ov2);
+    C[ix(3, 3)] = fminf(1.0f, INFLATE * ov3);
+    C[ix(4, 4)] = fminf(100.0f, INFLATE * ov4);
+    x = P.x[out_row];
+    g.sync();
+    if (g.gl == 0) hl[0] = out_hit;
+    n = 1;
+    in_x = x;
 #pragma unroll
-        for (int m = 0; m < 5; ++m) out_p[m] = p[m];
-        ov2 = C[ix(2, 2)];
-        ov3 = C[ix(3, 3)];
-        ov4 = C[ix(4, 4)];
-      }
-    }
-    // (ii) outward extension
-    if (alive && !dead) {
-      int misses = 0;
-      for (int r = out_row + 1; r < NR && misses < MAX_MISS; ++r) {
-        if (!kf_propagate(P, p, C, x, P.x[r])) break;
-        x = P.x[r];
-        if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) break;
-        const int h = pick_hit<G>(b, g, item, r, p, C, z_base);
-        if (h < 0) { ++misses; continue; }
-        const int4 q = b.s_hit[h];
-        kf_update(P, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
-        if (!cov_ok(C)) { dead = true; break; }
-        misses = 0;
-        out_row = r;
-        out_hit = h;
+    for (int m = 0; m < 5; ++m) in_p[m] = q5[m];
 #pragma unroll
-        for (int m = 0; m < 5; ++m) out_p[m] = p[m];
-        ov2 = C[ix(2, 2)];
-        ov3 = C[ix(3, 3)];
-        ov4 = C[ix(4, 4)];
-      }
-    }
-    int n = 0;
-    float chi2sum = 0.f, in_x = x;
-    float in_p[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, in_C[15];
-#pragma unroll
-    for (int m = 0; m < 15; ++m) in_C[m] = 0.f;
-    int in_hit = out_hit;
-    if (!dead) {
-      // (iii) inward refit from the outermost hit: its y, z; the outward direction
-      // and curvature with variances inflated 100-fold (capped at the initial ones)
-      const int4 qo = b.s_hit[out_hit];
-      float q5[5] = {qo.x * Q, (float)(qo.y - z_base) * Q, out_p[2], out_p[3], out_p[4]};
-      set_c0(P, C);
-      C[ix(2, 2)] = fminf(1.0f, INFLATE * ov2);
-      C[ix(3, 3)] = fminf(1.0f, INFLATE * ov3);
-      C[ix(4, 4)] = fminf(100.0f, INFLATE * ov4);
-      x = P.x[out_row];
-      g.sync();
-      if (g.gl == 0) hl[0] = out_hit;
-      n = 1;
+    for (int m = 0; m < 15; ++m) in_C[m] = C[m];
+    int misses = 0;
+    for (int r = out_row - 1; r >= 0 && misses < MAX_MISS; --r) {
+      if (!kf_propagate(P, q5, C, x, P.x[r])) break;
+      x = P.x[r];
+      if (!(fabsf(q5[2]) < SIN_MAX) || fabsf(q5[0]) > x * P.tan_half) break;
+      const int h = pick_hit<G>(b, g, item, r, q5, C, z_base);
+      if (h < 0) { ++misses; continue; }
+      const int4 q = b.s_hit[h];
+      chi2sum += kf_update(P, q5, C, q.x * Q - q5[0], (float)(q.y - z_base) * Q - q5[1]);
+      if (!cov_ok(C)) { dead = true; break; }
+      misses = 0;
+      if (g.gl == 0) hl[n] = h;
+      ++n;
+      in_hit = h;
       in_x = x;
 #pragma unroll
       for (int m = 0; m < 5; ++m) in_p[m] = q5[m];
 #pragma unroll
       for (int m = 0; m < 15; ++m) in_C[m] = C[m];
-      int misses = 0;
-      for (int r = out_row - 1; r >= 0 && misses < MAX_MISS; --r) {
-        if (!kf_propagate(P, q5, C, x, P.x[r])) break;
-        x = P.x[r];
-        if (!(fabsf(q5[2]) < SIN_MAX) || fabsf(q5[0]) > x * P.tan_half) break;
-        const int h = pick_hit<G>(b, g, item, r, q5, C, z_base);
-        if (h < 0) { ++misses; continue; }
-        const int4 q = b.s_hit[h];
-        chi2sum += kf_update(P, q5, C, q.x * Q - q5[0], (float)(q.y - z_base) * Q - q5[1]);
-        if (!cov_ok(C)) { dead = true; break; }
-        misses = 0;
-        if (g.gl == 0) hl[n] = h;
-        ++n;
-        in_hit = h;
-        in_x = x;
-#pragma unroll
-        for (int m = 0; m < 5; ++m) in_p[m] = q5[m];
-#pragma unroll
-        for (int m = 0; m < 15; ++m) in_C[m] = C[m];
-      }
     }
-    if (dead || n < MIN_HITS) n = 0;
-    // the 112-byte record, fields split over the lanes of the group
-    float* rf = reinterpret_cast<float*>(b.tl + t);
-    int* ri_ = reinterpret_cast<int*>(b.tl + t);
-    const int local = t - b.start_ex[b.item_off[item]];
-    const int z_in = n ? b.s_hit[in_hit].y : 0;
-    for (int fld = g.gl; fld < 27; fld += G) {
-      float fv = 0.f;
+  }
+  if (dead || n < MIN_HITS) n = 0;
+  // the 112-byte record, fields split over the lanes of the group
+  float* rf = reinterpret_cast<float*>(b.tl + tl);
+  int* ri_ = reinterpret_cast<int*>(b.tl + tl);
+  const int z_in = n ? b.s_hit[in_hit].y : 0;
+  for (int fld = g.gl; fld < 27; fld += G) {
+    float fv = 0.f;
 #pragma unroll
-      for (int m = 0; m < 5; ++m) fv = (fld == m) ? in_p[m] : fv;
+    for (int m = 0; m < 5; ++m) fv = (fld == m) ? in_p[m] : fv;
 #pragma unroll
-      for (int m = 0; m < 15; ++m) fv = (fld == 5 + m) ? in_C[m] : fv;
-      if (fld < 20) rf[fld] = fv;
-      else if (fld == 20) rf[20] = chi2sum;
-      else if (fld == 21) rf[21] = in_x;
-      else if (fld == 22) ri_[22] = n;
-      else if (fld == 23) ri_[23] = z_base;
-      else if (fld == 24) ri_[24] = z_in;
-      else if (fld == 25) ri_[25] = item;
-      else ri_[26] = local;
-    }
-    g.sync();
+    for (int m = 0; m < 15; ++m) fv = (fld == 5 + m) ? in_C[m] : fv;
+    if (fld < 20) rf[fld] = fv;
+    else if (fld == 20) rf[20] = chi2sum;
+    else if (fld == 21) rf[21] = in_x;
+    else if (fld == 22) ri_[22] = n;
+    else if (fld == 23) ri_[23] = z_base;
+    else if (fld == 24) ri_[24] = z_in;
+    else if (fld == 25) ri_[25] = item;
+    else ri_[26] = local;
+  }
+  g.sync();
+}
+
+template <int G>
+__global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Buffers b) {
+  const Grp<G> g;
+  const int T = b.start_ex[b.N];
+  const int NR = b.par.n_rows;
+  const int grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int ngrp = (gridDim.x * blockDim.x) / G;
+  for (int t = grp; t < T; t += ngrp) {
+    const int start = b.starts[t];
+    const int item = b.s_hit[start].w / NR;
+    tracklet_build<G>(b, g, start, t, t - b.start_ex[b.item_off[item]]);
   }
 }
 
@@ -1064,99 +1084,107 @@ __device__ __forceinline__ unsigned long long tl_key(int n, int local) {
   return ((unsigned long long)(unsigned)n << 32) | (unsigned long long)(0xFFFFFFFFu - (unsigned)local);
 }
 
-// Each hit goes to the tracklet with the largest key (more hits, then smaller
-// item-local id): one 64-bit atomicMax per (tracklet, hit); a warp per tracklet.
-__global__ void __launch_bounds__(256) k_select_max(const __grid_constant__ Buffers b) {
-  const int T = b.start_ex[b.N];
-  const int NR = b.par.n_rows;
-  const int lane = threadIdx.x & 31;
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
-  for (int t = warp; t < T; t += nwarps) {
-    const int n = b.tl[t].n;
-    if (n < MIN_HITS) continue;
-    const unsigned long long key = tl_key(n, b.tl[t].local);
-    const int* hl = b.tl_hits + (size_t)t * NR;
-    for (int k = lane; k < n; k += 32) atomicMax(&b.hit_key[hl[k]], key);
-  }
+namespace {
+// Ownership bid of tracklet tl: one 64-bit atomicMax per hit (key: more hits,
+// then smaller item-local id), lanes of a warp over the hits.
+__device__ __forceinline__ void select_max_warp(const Buffers& b, int tl, int lane) {
+  const int n = b.tl[tl].n;
+  if (n < MIN_HITS) return;
+  const unsigned long long key = tl_key(n, b.tl[tl].local);
+  const int* hl = b.tl_hits + (size_t)tl * b.par.n_rows;
+  for (int k = lane; k < n; k += 32) atomicMax(&b.hit_key[hl[k]], key);
 }
 
-// A tracklet keeps the hits it owns and is a track if it owns >= 10; with
-// time-frame slices only tracks whose innermost hit lies in the item's core.
+// Hits owned by tracklet tl; a track if >= 10 (and, with slices, if its innermost
+// hit lies in the item's core).  Returns (1 << 32 | owned) or 0, in every lane.
+__device__ __forceinline__ unsigned long long select_own_warp(const Buffers& b, int tl, int lane) {
+  const TrackletRec& r = b.tl[tl];
+  const int n = r.n;
+  if (n < MIN_HITS) return 0;
+  const unsigned long long key = tl_key(n, r.local);
+  const int* hl = b.tl_hits + (size_t)tl * b.par.n_rows;
+  int own = 0;
+  for (int k = lane; k < n; k += 32) own += b.hit_key[hl[k]] == key;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) own += __shfl_xor_sync(0xffffffffu, own, o);
+  bool keep = own >= MIN_HITS;
+  if (keep && b.item_core) keep = r.z_in >= b.item_core[2 * r.item] && r.z_in < b.item_core[2 * r.item + 1];
+  return keep ? ((1ull << 32) | (unsigned long long)own) : 0ull;
+}
+
+// Track record of tracklet tl (first_cluster = io) and its owned cluster ids,
+// innermost first, at ids[io ...]; a warp per tracklet.
+__device__ __forceinline__ void emit_warp(const Buffers& b, int tl, unsigned long long cnt, unsigned io,
+                                          tpc_track_t* dst, uint32_t* ids, int lane) {
+  const TrackletRec& r = b.tl[tl];
+  if (lane == 0) {
+    tpc_track_t o;
+    o.x_ref = r.x_ref;
+    o.y = r.p[0];
+    o.z = r.p[1] + (float)r.z_base * (1.0f / TPC_QSCALE);
+    o.snp = r.p[2];
+    o.tgl = r.p[3];
+    o.qpt = r.p[4];
+#pragma unroll
+    for (int m = 0; m < 15; ++m) o.cov[m] = r.C[m];
+    o.chi2 = r.chi2;
+    o.ndf = 2 * r.n - 5;
+    o.item = r.item;
+    o.sector = b.item_sector ? b.item_sector[r.item] : 0u;
+    o.event = b.item_event ? b.item_event[r.item] : 0u;
+    o.first_cluster = io;
+    o.n_clusters = (unsigned)(cnt & 0xFFFFFFFFull);
+    *dst = o;
+  }
+  const unsigned long long key = tl_key(r.n, r.local);
+  const int* hl = b.tl_hits + (size_t)tl * b.par.n_rows;
+  unsigned done = 0;
+  for (int base = 0; base < r.n; base += 32) {
+    const int k = r.n - 1 - (base + lane);
+    int h = -1;
+    bool own = false;
+    if (k >= 0) {
+      h = hl[k];
+      own = b.hit_key[h] == key;
+    }
+    const unsigned bal = __ballot_sync(0xffffffffu, own);
+    if (own) ids[done + __popc(bal & ((1u << lane) - 1))] = (uint32_t)b.s_hit[h].z;
+    done += __popc(bal);
+  }
+}
+}  // namespace
+
+__global__ void __launch_bounds__(256) k_select_max(const __grid_constant__ Buffers b) {
+  const int T = b.start_ex[b.N];
+  const int lane = threadIdx.x & 31;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
+  for (int t = warp; t < T; t += nwarps) select_max_warp(b, t, lane);
+}
+
 __global__ void __launch_bounds__(256) k_select_own(const __grid_constant__ Buffers b) {
   const int T = b.start_ex[b.N];
-  const int NR = b.par.n_rows;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
   for (int t = warp; t < T; t += nwarps) {
-    const TrackletRec& r = b.tl[t];
-    const int n = r.n;
-    unsigned long long out = 0;
-    if (n >= MIN_HITS) {
-      const unsigned long long key = tl_key(n, r.local);
-      const int* hl = b.tl_hits + (size_t)t * NR;
-      int own = 0;
-      for (int k = lane; k < n; k += 32) own += b.hit_key[hl[k]] == key;
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) own += __shfl_xor_sync(0xffffffffu, own, o);
-      bool keep = own >= MIN_HITS;
-      if (keep && b.item_core) keep = r.z_in >= b.item_core[2 * r.item] && r.z_in < b.item_core[2 * r.item + 1];
-      if (keep) out = (1ull << 32) | (unsigned long long)own;
-    }
+    const unsigned long long out = select_own_warp(b, t, lane);
     if (lane == 0) b.tl_cnt[t] = out;
   }
 }
 
 // ============================================================================ S8
-// Track records and owned cluster ids (innermost first), a warp per tracklet.
 __global__ void __launch_bounds__(256) k_output(const __grid_constant__ Buffers b) {
   const int T = b.start_ex[b.N];
-  const int NR = b.par.n_rows;
   const int lane = threadIdx.x & 31;
   const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, nwarps = (gridDim.x * blockDim.x) >> 5;
   tpc_track_t* trk = reinterpret_cast<tpc_track_t*>(b.trk);
   for (int t = warp; t < T; t += nwarps) {
     const unsigned long long cnt = b.tl_cnt[t];
     if (cnt == 0) continue;
-    const TrackletRec& r = b.tl[t];
     const unsigned long long ex = b.tl_ex[t];
     const unsigned ti = (unsigned)(ex >> 32);
     const unsigned io = (unsigned)(ex & 0xFFFFFFFFull);
-    if (lane == 0) {
-      tpc_track_t o;
-      o.x_ref = r.x_ref;
-      o.y = r.p[0];
-      o.z = r.p[1] + (float)r.z_base * (1.0f / TPC_QSCALE);
-      o.snp = r.p[2];
-      o.tgl = r.p[3];
-      o.qpt = r.p[4];
-#pragma unroll
-      for (int m = 0; m < 15; ++m) o.cov[m] = r.C[m];
-      o.chi2 = r.chi2;
-      o.ndf = 2 * r.n - 5;
-      o.item = r.item;
-      o.sector = b.item_sector ? b.item_sector[r.item] : 0u;
-      o.event = b.item_event ? b.item_event[r.item] : 0u;
-      o.first_cluster = io;
-      o.n_clusters = (unsigned)(cnt & 0xFFFFFFFFull);
-      trk[ti] = o;
-      b.trk_tl[ti] = t;
-    }
-    const unsigned long long key = tl_key(r.n, r.local);
-    const int* hl = b.tl_hits + (size_t)t * NR;
-    // innermost first: walk the hit list backwards, compact owned hits in order
-    unsigned done = 0;
-    for (int base = 0; base < r.n; base += 32) {
-      const int k = r.n - 1 - (base + lane);
-      int h = -1;
-      bool own = false;
-      if (k >= 0) {
-        h = hl[k];
-        own = b.hit_key[h] == key;
-      }
-      const unsigned bal = __ballot_sync(0xffffffffu, own);
-      if (own) b.trk_ids[io + done + __popc(bal & ((1u << lane) - 1))] = (uint32_t)b.s_hit[h].z;
-      done += __popc(bal);
-    }
+    emit_warp(b, t, cnt, io, trk + ti, b.trk_ids + io, lane);
+    if (lane == 0) b.trk_tl[ti] = t;
   }
 }
 
@@ -1168,7 +1196,331 @@ __global__ void k_counts(const __grid_constant__ Buffers b) {
   b.counts[2] = (unsigned long long)T;
 }
 
+
+// ============================================================================ S9
+// Batched form: one persistent launch.  Each CTA pops work items (event,
+// sector[, time slice]) from an atomic queue ordered by decreasing cluster
+// count (longest first) and runs every step on the item: shared-memory row
+// statistics, grid setup, counting sort into rows, one warp per row for the
+// bin sort, the neighbour search, cleaning and start compaction, tracklets,
+// shared-cluster resolution and the item's output.  The arithmetic is the
+// plain path's (same device functions), so every item's result is identical.
+// Item k's tracklets live at [item_off[k]/3 + k, ...) and its output at the
+// same place (tracks) and at [item_off[k], ...) (cluster ids); a second kernel
+// concatenates the items.
+namespace {
+constexpr int BT = 128;  // threads per CTA of the persistent kernel
+
+// exclusive scan of n values v(i) (i in [0, n)) over the CTA, chunk by chunk;
+// out(i, ex) receives the exclusive prefix; returns the total
+template <class V, class O>
+__device__ __forceinline__ int cta_scan(int n, V v, O out, int* sm) {
+  int carry = 0;
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const int x = i < n ? v(i) : 0;
+    int tot;
+    const int ex = block_excl_scan(x, sm, &tot);
+    if (i < n) out(i, carry + ex);
+    carry += tot;
+  }
+  return carry;
+}
+
+// one row sorted by one warp: histogram in the row's own first[] entries,
+// warp scan, scatter by arrival slot (slots kept in `slot`), in-bin sort by id
+__device__ __forceinline__ void warp_row_sort(const Buffers& b, const RowInfo& ri, int key, int* slot, int lane) {
+  const int n = ri.n;
+  int* hist = b.first + ri.bin0;
+  if (n == 0) {
+    if (lane == 0) hist[0] = ri.pos0;
+    return;
+  }
+  const int nb = ri.ny * ri.nz;
+  for (int j = lane; j <= nb; j += 32) hist[j] = 0;
+  __syncwarp();
+  const int s = ri.shift;
+  for (int j = lane; j < n; j += 32) {
+    const int2 q = b.g_q[ri.pos0 + j];
+    const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
+    slot[ri.pos0 + j] = atomicAdd(&hist[bin], 1);
+  }
+  __syncwarp();
+  int carry = 0;
+  for (int base = 0; base <= nb; base += 32) {
+    const int j = base + lane;
+    const int v = j <= nb ? hist[j] : 0;
+    const int inc = warp_incl_scan(v);
+    if (j <= nb) hist[j] = carry + inc - v;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
+  }
+  __syncwarp();
+  for (int j = lane; j < n; j += 32) {
+    const int2 q = b.g_q[ri.pos0 + j];
+    const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
+    b.s_hit[ri.pos0 + hist[bin] + slot[ri.pos0 + j]] = make_int4(q.x, q.y, b.g_id[ri.pos0 + j], key);
+  }
+  __syncwarp();
+  for (int bin = lane; bin < nb; bin += 32) {
+    const int a = ri.pos0 + hist[bin], e = ri.pos0 + hist[bin + 1];
+    for (int i = a + 1; i < e; ++i) {
+      const int4 v = b.s_hit[i];
+      int j = i - 1;
+      while (j >= a && b.s_hit[j].z > v.z) {
+        b.s_hit[j + 1] = b.s_hit[j];
+        --j;
+      }
+      b.s_hit[j + 1] = v;
+    }
+  }
+  __syncwarp();
+  for (int j = lane; j <= nb; j += 32) hist[j] += ri.pos0;
+  __syncwarp();
+}
+}  // namespace
+
+template <int G>
+__global__ void __launch_bounds__(BT) k_batched(const __grid_constant__ Buffers b) {
+  const DevParams& P = b.par;
+  __shared__ RowInfo s_rows[TPC_MAX_ROWS];
+  __shared__ int s_cnt[TPC_MAX_ROWS], s_min[4][TPC_MAX_ROWS], s_fill[TPC_MAX_ROWS];
+  __shared__ int s_cu[LINK_MAXC][BT], s_cd[LINK_MAXC][BT];
+  __shared__ int sm[33];
+  __shared__ int s_item, s_ntl;
+  const int NR = P.n_rows;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  const Grp<G> g;
+  for (;;) {
+    if (threadIdx.x == 0) {
+      const int k = atomicAdd(b.queue_head, 1);
+      s_item = k < b.I ? b.queue[k] : -1;
+    }
+    __syncthreads();
+    const int item = s_item;
+    if (item < 0) break;
+    const int a0 = (int)b.item_off[item], a1 = (int)b.item_off[item + 1];
+    const int tlb = a0 / 3 + item;
+    // ---- S1: validation, quantisation and row statistics in shared memory
+    for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+      s_cnt[r] = 0;
+      s_fill[r] = 0;
+      s_min[0][r] = s_min[1][r] = s_min[2][r] = s_min[3][r] = 0x7F7F7F7F;
+    }
+    __syncthreads();
+    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+      b.hit_key[i] = 0ull;
+      const float xv = b.x[i], yv = b.y[i], zv = b.z[i];
+      const int r = b.row[i];
+      if (!(r >= 0 && r < NR && fabsf(xv) < INFINITY && fabsf(yv) <= 1e6f && fabsf(zv) <= 1e6f)) {
+        atomicOr(b.err, TPC_DERR_BAD_INPUT);
+        continue;
+      }
+      const int qy = __float2int_rn(yv * TPC_QSCALE), qz = __float2int_rn(zv * TPC_QSCALE);
+      atomicAdd(&s_cnt[r], 1);
+      atomicMin(&s_min[0][r], qy);
+      atomicMin(&s_min[1][r], -qy);
+      atomicMin(&s_min[2][r], qz);
+      atomicMin(&s_min[3][r], -qz);
+    }
+    __syncthreads();
+    // ---- S2a: bin size and grid of every row, row and bin offsets
+    for (int r = threadIdx.x; r < NR; r += blockDim.x) {
+      const int n = s_cnt[r];
+      int s = SHIFT_MIN, ny = 0, nz = 0, ymin = 0, zmin = 0;
+      if (n > 0) {
+        ymin = s_min[0][r];
+        zmin = s_min[2][r];
+        const long long dy = (long long)(-s_min[1][r]) - ymin, dz = (long long)(-s_min[3][r]) - zmin;
+        const long long need = ((dy + 1) * (dz + 1) + n - 1) / n;
+        for (;; ++s) {
+          const long long nyy = (dy >> s) + 1, nzz = (dz >> s) + 1;
+          if ((2 * s >= 63 || (1ll << (2 * s)) >= need) && nyy * nzz <= 2ll * n + 2) {
+            ny = (int)nyy;
+            nz = (int)nzz;
+            break;
+          }
+        }
+      }
+      RowInfo& ri = s_rows[r];
+      ri.n = n;
+      ri.ymin = ymin;
+      ri.zmin = zmin;
+      ri.shift = s;
+      ri.ny = ny;
+      ri.nz = nz;
+    }
+    __syncthreads();
+    cta_scan(NR, [&](int r) { return s_rows[r].n; }, [&](int r, int ex) { s_rows[r].pos0 = a0 + ex; }, sm);
+    cta_scan(NR, [&](int r) { return (s_rows[r].n > 0 ? s_rows[r].ny * s_rows[r].nz : 0) + 1; },
+             [&](int r, int ex) { s_rows[r].bin0 = 2 * a0 + 3 * NR * item + ex; }, sm);
+    __syncthreads();
+    for (int r = threadIdx.x; r < NR; r += blockDim.x) b.rows[item * NR + r] = s_rows[r];
+    // ---- S2b: counting sort into rows
+    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
+      const float xv = b.x[i], yv = b.y[i], zv = b.z[i];
+      const int r = b.row[i];
+      if (!(r >= 0 && r < NR && fabsf(xv) < INFINITY && fabsf(yv) <= 1e6f && fabsf(zv) <= 1e6f)) continue;
+      const int gp = s_rows[r].pos0 + atomicAdd(&s_fill[r], 1);
+      b.g_q[gp] = make_int2(__float2int_rn(yv * TPC_QSCALE), __float2int_rn(zv * TPC_QSCALE));
+      b.g_id[gp] = i;
+    }
+    __syncthreads();
+    // ---- S2c: one warp per row
+    for (int r = warp; r < NR; r += nwarps) warp_row_sort(b, s_rows[r], item * NR + r, b.flags, lane);
+    __syncthreads();
+    // ---- S3: neighbours
+    const int p_end = s_rows[NR - 1].pos0 + s_rows[NR - 1].n;
+    for (int pos = a0 + threadIdx.x; pos < p_end; pos += blockDim.x) {
+      const int4 qh = b.s_hit[pos];
+      const int r = qh.w - item * NR;
+      if (r == 0 || r == NR - 1) {
+        b.up_raw[pos] = -1;
+        b.dn_raw[pos] = -1;
+        continue;
+      }
+      link_hit<BT>(b, s_rows, 0, pos, qh, r, s_cu, s_cd, threadIdx.x);
+    }
+    for (int pos = p_end + threadIdx.x; pos < a1; pos += blockDim.x) {  // rejected clusters: no links
+      b.up_raw[pos] = -1;
+      b.dn_raw[pos] = -1;
+    }
+    __syncthreads();
+    // ---- S4+S5: mutual links, start hits, compaction in canonical order
+    for (int pos = a0 + threadIdx.x; pos < a1; pos += blockDim.x) {
+      const int u = b.up_raw[pos], d = b.dn_raw[pos];
+      const int cu = (u >= 0 && b.dn_raw[u] == pos) ? u : -1;
+      const int cd = (d >= 0 && b.up_raw[d] == pos) ? d : -1;
+      b.up[pos] = cu;
+      b.dn[pos] = cd;
+      int start = 0;
+      if (cu >= 0 && cd < 0) {
+        const int u2 = b.up_raw[cu];
+        start = (u2 >= 0 && b.dn_raw[u2] == cu) ? 1 : 0;
+      }
+      b.flags[pos] = start;
+    }
+    __syncthreads();
+    {
+      const int ntl = cta_scan(a1 - a0, [&](int i) { return b.flags[a0 + i]; },
+                               [&](int i, int ex) {
+                                 if (b.flags[a0 + i]) b.starts[tlb + ex] = a0 + i;
+                               },
+                               sm);
+      if (threadIdx.x == 0) s_ntl = ntl;
+    }
+    __syncthreads();
+    const int ntl = s_ntl;
+    // ---- S6: tracklets, a group of G lanes each
+    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_build<G>(b, g, b.starts[tlb + t], tlb + t, t);
+    __syncthreads();
+    // ---- S7: ownership
+    for (int t = warp; t < ntl; t += nwarps) select_max_warp(b, tlb + t, lane);
+    __syncthreads();
+    for (int t = warp; t < ntl; t += nwarps) {
+      const unsigned long long o = select_own_warp(b, tlb + t, lane);
+      if (lane == 0) b.tl_cnt[tlb + t] = o;
+    }
+    __syncthreads();
+    // item-local output offsets: tracks in the high word, cluster ids in the low word
+    if (warp == 0) {
+      unsigned long long carry = 0;
+      for (int base = 0; base < ntl; base += 32) {
+        const int t = base + lane;
+        const unsigned long long v = t < ntl ? b.tl_cnt[tlb + t] : 0ull;
+        const unsigned long long inc = warp_incl_scan64(v);
+        if (t < ntl) b.tl_ex[tlb + t] = carry + inc - v;
+        carry += __shfl_sync(0xffffffffu, inc, 31);
+      }
+      if (lane == 0) {
+        b.item_cnt[item] = carry;
+        b.item_ntl[item] = ntl;
+      }
+    }
+    __syncthreads();
+    // ---- S8: the item's tracks and cluster ids
+    tpc_track_t* trk_tmp = reinterpret_cast<tpc_track_t*>(b.trk_tmp);
+    for (int t = warp; t < ntl; t += nwarps) {
+      const unsigned long long cnt = b.tl_cnt[tlb + t];
+      if (cnt == 0) continue;
+      const unsigned long long ex = b.tl_ex[tlb + t];
+      const unsigned ti = (unsigned)(ex >> 32), io = (unsigned)(ex & 0xFFFFFFFFull);
+      emit_warp(b, tlb + t, cnt, io, trk_tmp + tlb + ti, b.ids_tmp + a0 + io, lane);
+      if (lane == 0) b.trk_tl_tmp[tlb + ti] = tlb + t;
+    }
+    __syncthreads();
+  }
+}
+
+// exclusive scan of the items' packed (tracks, ids) counts and tracklet counts
+__global__ void __launch_bounds__(1024) k_items_scan(const __grid_constant__ Buffers b) {
+  __shared__ unsigned long long sm64[33];
+  unsigned long long carry = 0, tl_carry = 0;
+  for (int base = 0; base < b.I; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    const unsigned long long v = i < b.I ? b.item_cnt[i] : 0ull;
+    const unsigned long long w = i < b.I ? (unsigned long long)b.item_ntl[i] : 0ull;
+    unsigned long long tot, tot2;
+    const unsigned long long ex = block_excl_scan64(v, sm64, &tot);
+    const unsigned long long ex2 = block_excl_scan64(w, sm64, &tot2);
+    if (i < b.I) {
+      b.item_ex[i] = carry + ex;
+      b.item_tl_ex[i] = (int)(tl_carry + ex2);
+    }
+    carry += tot;
+    tl_carry += tot2;
+  }
+  if (threadIdx.x == 0) {
+    b.counts[0] = carry >> 32;
+    b.counts[1] = carry & 0xFFFFFFFFull;
+    b.counts[2] = tl_carry;
+  }
+}
+
+// concatenation of the items' outputs (one CTA per item)
+__global__ void __launch_bounds__(256) k_items_copy(const __grid_constant__ Buffers b) {
+  const int item = blockIdx.x;
+  const unsigned long long cnt = b.item_cnt[item], ex = b.item_ex[item];
+  const unsigned nt = (unsigned)(cnt >> 32), ni = (unsigned)(cnt & 0xFFFFFFFFull);
+  const unsigned t0 = (unsigned)(ex >> 32), i0 = (unsigned)(ex & 0xFFFFFFFFull);
+  const int a0 = (int)b.item_off[item];
+  const int tlb = a0 / 3 + item;
+  const tpc_track_t* src = reinterpret_cast<const tpc_track_t*>(b.trk_tmp) + tlb;
+  tpc_track_t* dst = reinterpret_cast<tpc_track_t*>(b.trk) + t0;
+  for (unsigned k = threadIdx.x; k < nt; k += blockDim.x) {
+    tpc_track_t o = src[k];
+    o.first_cluster += i0;
+    dst[k] = o;
+    b.trk_tl[t0 + k] = b.item_tl_ex[item] + (b.trk_tl_tmp[tlb + k] - tlb);
+  }
+  for (unsigned k = threadIdx.x; k < ni; k += blockDim.x) b.trk_ids[i0 + k] = b.ids_tmp[a0 + k];
+}
+
+cudaError_t tpc_launch_batched(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev) {
+  auto mark = [&](int i) {
+    if (ev) cudaEventRecord(ev[i], s);
+  };
+  mark(9);
+  cudaMemsetAsync(b.queue_head, 0, sizeof(int), s);
+  // persistent grid: every resident CTA slot of the GPU
+  switch (c.batch_group) {
+    case 1: k_batched<1><<<std::max(1, c.batch_per_sm[0]) * c.num_sms, BT, 0, s>>>(b); break;
+    case 2: k_batched<2><<<std::max(1, c.batch_per_sm[1]) * c.num_sms, BT, 0, s>>>(b); break;
+    default: k_batched<4><<<std::max(1, c.batch_per_sm[2]) * c.num_sms, BT, 0, s>>>(b); break;
+  }
+  mark(10);
+  k_items_scan<<<1, 1024, 0, s>>>(b);
+  k_items_copy<<<b.I, 256, 0, s>>>(b);
+  mark(11);
+  return cudaGetLastError();
+}
 // ============================================================================ host launchers
+cudaError_t tpc_batched_occupancy(int per_sm[3]) {
+  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_batched<1>, BT, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_batched<2>, BT, 0);
+  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_batched<4>, BT, 0);
+  return e;
+}
+
 cudaError_t tpc_configure_kernels(int sort_smem, int link_smem) {
   (void)link_smem;
   return cudaFuncSetAttribute(k_row_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, sort_smem);
@@ -1212,12 +1564,8 @@ cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t 
   cudaMemsetAsync(b.up_raw, 0xFF, sizeof(int) * (size_t)b.N, s);
   cudaMemsetAsync(b.dn_raw, 0xFF, sizeof(int) * (size_t)b.N, s);
   {
-    // default: about 8 CTAs per SM
-    int rpc = c.link_rows;
-    if (rpc <= 0) {
-      const long long want = (long long)c.num_sms * 8;
-      rpc = (int)std::min<long long>(NR, std::max<long long>(1, ((long long)b.I * NR + want - 1) / want));
-    }
+    // default: 8 rows per CTA (measured best between 4 for one event and 16 for 64 events)
+    const int rpc = c.link_rows > 0 ? std::min(c.link_rows, NR) : std::min(8, NR);
     const int nrb = (NR + rpc - 1) / rpc;
     k_links<<<b.I * nrb, LINK_THREADS, 0, s>>>(b, rpc);
   }

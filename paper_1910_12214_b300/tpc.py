@@ -49,7 +49,8 @@ class tpc_clusters(C.Structure):
 
 class tpc_tuning(C.Structure):
     _fields_ = [("tracklet_lanes", C.c_int), ("tracklet_block", C.c_int), ("tracklet_blocks_per_sm", C.c_int),
-                ("sort_smem", C.c_int), ("link_rows", C.c_int)]
+                ("sort_smem", C.c_int), ("link_rows", C.c_int), ("mode", C.c_int),
+                ("batch_lanes", C.c_int), ("use_graph", C.c_int)]
 
 
 TRACK_DTYPE = np.dtype([("x_ref", "<f4"), ("y", "<f4"), ("z", "<f4"), ("snp", "<f4"), ("tgl", "<f4"),
@@ -212,7 +213,7 @@ class Tracker:
         us = (C.c_float * 32)()
         n = C.c_int()
         self._check(_lib.tpc_stage_times(self._h, us, 32, C.byref(n)))
-        return {_lib.tpc_stage_name(i).decode(): float(us[i]) for i in range(n.value)}
+        return {_lib.tpc_stage_name(i).decode(): float(us[i]) for i in range(n.value) if us[i] > 0}
 
     def debug_dump(self, stage: int) -> np.ndarray:
         n = C.c_uint64()

@@ -195,6 +195,60 @@ def test_stage_times_profile():
     assert len(st) == 9 and all(v >= 0 for v in st.values())
 
 
+def _run_mode(cl, mode, graph, stream=None, lanes=1):
+    from paper_1910_12214_b300 import tpc
+    with tpc.Tracker(stream=stream) as t:
+        t.set_tuning(mode=mode, use_graph=graph, batch_lanes=lanes)
+        t.load(cl).track()
+        trk, ids = t.get_tracks()
+        t.track()  # a second run (graph replay) must give the same result
+        trk2, ids2 = t.get_tracks()
+        assert trk.tobytes() == trk2.tobytes() and np.array_equal(ids, ids2)
+        return trk, ids, {s_: t.debug_dump(s_) for s_ in range(11)}
+
+
+@pytest.mark.parametrize("lanes", [1, 2, 4])
+def test_batched_persistent_kernel_equals_plain_mode(lanes):
+    """The persistent kernel (work queue, longest item first, CUDA graph) gives
+    the plain path's result bit for bit, item by item; so it matches the oracle."""
+    import torch
+    cl = _with_empty_items(synth.make_batched(seed=7, n_events=6, mult=(5, 3000)))
+    s = torch.cuda.Stream()
+    trk_p, ids_p, d_p = _run_mode(cl, 1, 1)
+    trk_b, ids_b, d_b = _run_mode(cl, 2, 2, stream=s, lanes=lanes)
+    assert trk_p.tobytes() == trk_b.tobytes()
+    assert np.array_equal(ids_p, ids_b)
+    for k in range(11):
+        assert np.array_equal(d_p[k], d_b[k]), k
+    ref = oracle.run(cl)
+    compare_stages(d_b, ref)
+    r = compare_tracks(cl, trk_b, ids_b, ref)
+    assert r["ok"], r
+
+
+def test_batched_with_rejected_clusters_reports_and_recovers():
+    from paper_1910_12214_b300 import tpc
+    cl = synth.make_batched(seed=8, n_events=2, mult=(100, 400))
+    bad = _Cl(cl.x, cl.y.copy(), cl.z, cl.row.copy(), cl.item_off)
+    bad.row[3] = -1
+    with tpc.Tracker() as t:
+        t.set_tuning(mode=2)
+        t.load(bad).track()
+        with pytest.raises(tpc.TpcError) as e:
+            t.get_tracks()
+        assert e.value.status == 7
+        t.load(cl).track()
+        assert t.get_tracks()[0].shape[0] > 0
+
+
+def test_graph_replay_equals_direct_launch_plain_mode():
+    import torch
+    cl = synth.make_config2(seed=5, n_tracks=1000)
+    trk_a, ids_a, _ = _run_mode(cl, 1, 1)
+    trk_b, ids_b, _ = _run_mode(cl, 1, 2, stream=torch.cuda.Stream())
+    assert trk_a.tobytes() == trk_b.tobytes() and np.array_equal(ids_a, ids_b)
+
+
 def test_every_launch_shape_gives_identical_output():
     """Lane groups, block sizes and shared-memory budgets change only the speed."""
     from paper_1910_12214_b300 import tpc
