@@ -66,7 +66,7 @@ typedef struct {
   float sigma_y, sigma_z;     /* cluster resolution used by the Kalman filter [cm] (0.1) */
   tpc_mode mode;              /* PLAIN: one launch per step; BATCHED: persistent kernel over a
                                  work queue of items (identical results) */
-  tpc_corr correction;        /* space-point correction applied at load (NONE for now) */
+  tpc_corr correction;        /* space-point correction applied by tpc_track (see tpc_set_correction) */
   uint64_t max_clusters;      /* initial reservation (0 = grow on demand) */
   uint32_t max_items;         /* initial reservation (0 = grow on demand) */
   const tpc_allocator* allocator; /* NULL = cudaMallocAsync */
@@ -149,9 +149,28 @@ const char* tpc_stage_name(int i);
  * links as original ids indexed by original id (-1 = none); 7 start hits
  * (original ids, canonical order); 8 hits per tracklet (0 = dropped);
  * 9 tracklet hit lists (original ids, outermost first); 10 tracklet index
- * (canonical order) of every output track.  Copies up to cap int32
+ * (canonical order) of every output track; 11 corrected (y, z) of every
+ * input cluster as float32 bit patterns (the input when no correction is on).  Copies up to cap int32
  * values into host_buf and sets *n to the full count. */
 tpc_status tpc_debug_dump(tpc_ctx* ctx, int stage, int32_t* host_buf, uint64_t cap, uint64_t* n);
+
+/* Space-point correction by per-sector grids (location-dependent calibration,
+ * the paper's Abstract; online calibration, Sec. 3).  grid: host float32
+ * [n_sectors][nx][ny][nz][3] of (dx, dy, dz) shifts such that corrected =
+ * measured + shift, at nodes spanning (x, v = y / (x tan(half angle)), z) in
+ * the measured (distorted) space; bounds: host float32 [n_sectors][6] =
+ * (x0, x1, v0, v1, z0, z1).  A cluster is corrected by trilinear interpolation
+ * at its pad row's radius with coordinates clamped to the grid; the pad row
+ * fixes x, so only dy and dz are applied.  Items use the grid of their
+ * item_sector (0 when item_sector is NULL).  The grid is copied and kept until
+ * replaced or the context is destroyed. */
+tpc_status tpc_set_grid_correction(tpc_ctx* ctx, const float* grid, const float* bounds, uint32_t n_sectors, int nx,
+                                   int ny, int nz);
+
+/* Selects the correction applied by tpc_track(): TPC_CORR_NONE, TPC_CORR_GRID
+ * (needs tpc_set_grid_correction) or TPC_CORR_MLP (needs a trained or loaded
+ * network). */
+tpc_status tpc_set_correction(tpc_ctx* ctx, tpc_corr mode);
 
 /* Launch shapes of the kernels (no effect on results: every shape gives the
  * same output bit for bit).  tracklet_lanes: lanes that share one tracklet

@@ -10,7 +10,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
-SRC = [os.path.join(HERE, f) for f in ("tpc_oracle.cpp", "mlp_oracle.cpp") if os.path.exists(os.path.join(HERE, f))]
+SRC = [os.path.join(HERE, f) for f in ("tpc_oracle.cpp", "corr_oracle.cpp", "mlp_oracle.cpp")
+       if os.path.exists(os.path.join(HERE, f))]
 
 
 def build_oracle(force: bool = False) -> str:
@@ -63,6 +64,9 @@ def _load():
         lib.orc_fit_hits.restype = C.c_int
         lib.orc_fit_hits.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                                      C.c_double, C.c_double, C.c_double, C.c_void_p, C.c_void_p, C.c_void_p]
+        lib.orc_trilinear.restype = None
+        lib.orc_trilinear.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
+                                      C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
         lib.orc_chi2.restype = C.c_double
         lib.orc_chi2.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         _lib = lib
@@ -143,3 +147,30 @@ def chi2(p, Cm, my, mz, vy=0.01, vz=0.01):
     p = np.ascontiguousarray(p, np.float64)
     Cm = np.ascontiguousarray(Cm, np.float64)
     return float(lib.orc_chi2(_p(p), _p(Cm), my, mz, vy, vz))
+
+
+def trilinear(grid, bounds, sector, x, y, z, tan_half=None):
+    """(dy, dz) of the per-sector grid at points (x = pad-row radius), FP64."""
+    import math
+    lib = _load()
+    tan_half = math.tan(math.radians(10.0)) if tan_half is None else tan_half
+    grid = np.ascontiguousarray(grid, np.float32)
+    bounds = np.ascontiguousarray(bounds, np.float32)
+    S, nx, ny, nz, _ = grid.shape
+    sector = np.ascontiguousarray(sector, np.int32)
+    x, y, z = (np.ascontiguousarray(a, np.float64) for a in (x, y, z))
+    n = x.shape[0]
+    dy, dz = np.empty(n), np.empty(n)
+    lib.orc_trilinear(_p(grid), _p(bounds), nx, ny, nz, tan_half, n, _p(sector), _p(x), _p(y), _p(z), _p(dy), _p(dz))
+    return dy, dz
+
+
+def correct_clusters(cl, grid, bounds, n_rows=152, x_min=85.0, x_max=246.0):
+    """Corrected cluster y, z (float32) with the grid read at the quantised pad-row x."""
+    xr = np.rint((x_min + np.arange(n_rows) * ((x_max - x_min) / (n_rows - 1))) * 1024.0) / 1024.0
+    sec = np.repeat(cl.item_sector.astype(np.int64), np.diff(cl.item_off.astype(np.int64)))
+    x = xr[cl.row]
+    y = cl.y.astype(np.float64)
+    z = cl.z.astype(np.float64)
+    dy, dz = trilinear(grid, bounds, sec, x, y, z)
+    return (y + dy).astype(np.float32), (z + dz).astype(np.float32)

@@ -14,7 +14,8 @@
  *   orc_fit_hits     : pinned (straight-line weighted least squares; noise-free helices)
  *   orc_run tracklets: pinned statistically (chi2/ndf ~ 1, pulls N(0,1)), brute search
  *   orc_run selection: pinned (brute force max-key per hit)
- *   orc_trilinear, orc_mlp_*: see their own comments.
+ *   orc_trilinear    : pinned (linear fields exact, node values, exact inverse of the field)
+ *   orc_mlp_*        : see mlp_oracle.cpp.
  */
 #ifndef TPC_ORACLE_H
 #define TPC_ORACLE_H
@@ -66,6 +67,13 @@ int orc_propagate(const double* p_in, double x1, double x2, double bz_tesla, dou
 int orc_fit_hits(int n, const double* x, const double* y, const double* z, const double* p0,
                  const double* C0, double sigma_y, double sigma_z, double bz_tesla,
                  double* p_out, double* C_out, double* chi2_out);
+
+/* Trilinear read of per-sector correction grids (corr_oracle.cpp): grid float32
+ * [S][nx][ny][nz][3] over (x, v = y / (x tan_half), z), bounds [S][6]; returns
+ * the (dy, dz) components (the pad row fixes x). */
+void orc_trilinear(const float* grid, const float* bounds, int nx, int ny, int nz, double tan_half, int n,
+                   const int32_t* sector, const double* x, const double* y, const double* z, double* out_dy,
+                   double* out_dz);
 
 /* chi2 of measurement (my,mz) against state p with covariance C (row-major 5x5)
  * and measurement variances vy, vz: the hit-selection criterion. */

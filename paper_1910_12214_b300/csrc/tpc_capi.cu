@@ -41,6 +41,12 @@ struct tpc_ctx {
   // execution mode and CUDA graph of tpc_track
   bool batched = false, use_graph = false, last_batched = false;
   cudaGraphExec_t graph = nullptr;
+  // space-point correction: mode and model buffers (kept across batch loads)
+  tpc_corr corr = TPC_CORR_NONE;
+  std::vector<void*> persist;
+  void* grid_dev = nullptr;
+  void* grid_bounds_dev = nullptr;
+  int grid_n[3] = {0, 0, 0}, grid_sectors = 0;
 };
 
 namespace {
@@ -74,6 +80,30 @@ void drop_graph(tpc_ctx* c) {
 }
 
 bool capturable(cudaStream_t s) { return s != nullptr && s != cudaStreamLegacy && s != cudaStreamPerThread; }
+
+void* persist_alloc(tpc_ctx* c, size_t bytes) {
+  const size_t before = c->blocks.size();
+  void* p = dev_alloc(c, bytes);
+  if (p) {  // move it from the batch list to the persistent list
+    c->blocks.resize(before);
+    c->persist.push_back(p);
+  }
+  return p;
+}
+
+void persist_free(tpc_ctx* c, void* p) {
+  if (!p) return;
+  cudaStreamSynchronize(c->stream);
+  for (size_t i = 0; i < c->persist.size(); ++i)
+    if (c->persist[i] == p) {
+      if (c->has_alloc)
+        c->alloc.free(p, c->alloc.user);
+      else
+        cudaFreeAsync(p, c->stream);
+      c->persist.erase(c->persist.begin() + i);
+      return;
+    }
+}
 
 void free_all(tpc_ctx* c) {
   drop_graph(c);
@@ -156,6 +186,8 @@ tpc_status reserve(tpc_ctx* c, long long N, long long I, long long n_chunks) {
   b.trk_tmp = A(sizeof(tpc_track_t) * Tcap);
   b.trk_tl_tmp = (int*)A(4 * Tcap);
   b.ids_tmp = (uint32_t*)A(4 * N);
+  b.cy = (float*)A(4 * N);
+  b.cz = (float*)A(4 * N);
   b.T_cap = (int)Tcap;
   if (!ok) {
     free_all(c);
@@ -176,7 +208,8 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
   if (cfg->n_rows < 3 || cfg->n_rows > TPC_MAX_ROWS || !(cfg->row_x_max > cfg->row_x_min) ||
       !(cfg->row_x_min > 0.f) || !(cfg->sector_half_angle_deg > 0.f) || !(cfg->sector_half_angle_deg < 60.f) ||
       !(cfg->sigma_y > 0.f) || !(cfg->sigma_z > 0.f) || !std::isfinite(cfg->bz_tesla) ||
-      (cfg->mode != TPC_MODE_PLAIN && cfg->mode != TPC_MODE_BATCHED) || cfg->correction != TPC_CORR_NONE)
+      (cfg->mode != TPC_MODE_PLAIN && cfg->mode != TPC_MODE_BATCHED) ||
+      (cfg->correction != TPC_CORR_NONE && cfg->correction != TPC_CORR_GRID && cfg->correction != TPC_CORR_MLP))
     return TPC_ERR_INVALID_ARG;
   if (cfg->allocator && (!cfg->allocator->alloc || !cfg->allocator->free)) return TPC_ERR_INVALID_ARG;
   tpc_ctx* c = new tpc_ctx();
@@ -229,6 +262,7 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
   L.tl_group = 1;
   L.batch_group = 1;
   c->batched = cfg->mode == TPC_MODE_BATCHED;
+  c->corr = cfg->correction;
   c->use_graph = capturable(c->stream);
   if ((e = tpc_configure_kernels(L.sort_smem, L.link_smem)) != cudaSuccess ||
       (e = tpc_batched_occupancy(L.batch_per_sm)) != cudaSuccess) {
@@ -351,9 +385,22 @@ extern "C" tpc_status tpc_track(tpc_ctx* c) {
     c->tracked = true;
     return TPC_OK;  // counts were zeroed at load
   }
+  if (c->corr == TPC_CORR_GRID && !c->grid_dev)
+    return fail(c, TPC_ERR_STATE, "grid correction selected but no grid set (tpc_set_grid_correction)");
+  if (c->corr == TPC_CORR_MLP && !c->b.mlp)
+    return fail(c, TPC_ERR_STATE, "MLP correction selected but no trained or loaded network");
+  Buffers tb = c->b;  // tracking reads corrected coordinates when a correction is on
+  if (c->corr != TPC_CORR_NONE) {
+    tb.y = c->b.cy;
+    tb.z = c->b.cz;
+  }
   auto launch = [&]() {
-    return c->batched ? tpc_launch_batched(c->b, c->lc, c->stream, c->have_events ? c->ev : nullptr)
-                      : tpc_launch_plain(c->b, c->lc, c->stream, c->have_events ? c->ev : nullptr);
+    cudaError_t ce = cudaSuccess;
+    if (c->corr == TPC_CORR_GRID) ce = tpc_launch_grid_correction(c->b, c->stream);
+    if (c->corr == TPC_CORR_MLP) ce = tpc_launch_mlp_correction(c->b, c->stream);
+    if (ce != cudaSuccess) return ce;
+    return c->batched ? tpc_launch_batched(tb, c->lc, c->stream, c->have_events ? c->ev : nullptr)
+                      : tpc_launch_plain(tb, c->lc, c->stream, c->have_events ? c->ev : nullptr);
   };
   if (c->use_graph && capturable(c->stream)) {
     if (!c->graph) {
@@ -539,6 +586,18 @@ extern "C" tpc_status tpc_debug_dump(tpc_ctx* c, int stage, int32_t* buf, uint64
       }
       break;
     }
+    case 11: {  // corrected (y, z) per input cluster as float bits (input coordinates when no correction)
+      const float* ys = c->corr != TPC_CORR_NONE ? b.cy : b.y;
+      const float* zs = c->corr != TPC_CORR_NONE ? b.cz : b.z;
+      std::vector<int> yy, zz;
+      if ((e = D2H(yy, ys, N)) != cudaSuccess || (e = D2H(zz, zs, N)) != cudaSuccess) return cuda_fail(c, e, "dump");
+      out.resize(2 * N);
+      for (size_t i = 0; i < N; ++i) {
+        out[2 * i] = yy[i];
+        out[2 * i + 1] = zz[i];
+      }
+      break;
+    }
     case 10: {
       unsigned long long cnt[4] = {0, 0, 0, 0};
       if ((e = cudaMemcpy(cnt, b.counts, 32, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(c, e, "dump");
@@ -700,10 +759,61 @@ extern "C" tpc_status tpc_autotune(tpc_ctx* c, int iters, tpc_tuning* best_out, 
   return st;
 }
 
+extern "C" tpc_status tpc_set_grid_correction(tpc_ctx* c, const float* grid, const float* bounds, uint32_t n_sectors,
+                                              int nx, int ny, int nz) {
+  if (!c || !grid || !bounds || n_sectors == 0 || nx < 2 || ny < 2 || nz < 2 || nx > 1024 || ny > 1024 || nz > 1024)
+    return TPC_ERR_INVALID_ARG;
+  for (uint32_t s_ = 0; s_ < n_sectors; ++s_) {
+    const float* B = bounds + 6 * s_;
+    if (!(B[1] > B[0]) || !(B[3] > B[2]) || !(B[5] > B[4]) || !(B[0] > 0.f))
+      return fail(c, TPC_ERR_INVALID_ARG, "grid bounds must be increasing, x0 > 0");
+  }
+  cudaError_t e = cudaSetDevice(c->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  const size_t nodes = (size_t)n_sectors * nx * ny * nz;
+  std::vector<float> packed(2 * nodes);
+  for (size_t k = 0; k < nodes; ++k) {  // keep (dy, dz): the pad row fixes x
+    packed[2 * k] = grid[3 * k + 1];
+    packed[2 * k + 1] = grid[3 * k + 2];
+  }
+  persist_free(c, c->grid_dev);
+  persist_free(c, c->grid_bounds_dev);
+  c->grid_dev = persist_alloc(c, 8 * nodes);
+  c->grid_bounds_dev = persist_alloc(c, 24 * (size_t)n_sectors);
+  if (!c->grid_dev || !c->grid_bounds_dev) {
+    persist_free(c, c->grid_dev);
+    persist_free(c, c->grid_bounds_dev);
+    c->grid_dev = c->grid_bounds_dev = nullptr;
+    return fail(c, TPC_ERR_OOM, "grid allocation failed");
+  }
+  if ((e = cudaMemcpyAsync(c->grid_dev, packed.data(), 8 * nodes, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->grid_bounds_dev, bounds, 24 * (size_t)n_sectors, cudaMemcpyHostToDevice, c->stream)) !=
+          cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "grid upload");
+  c->b.grid = (const float2*)c->grid_dev;
+  c->b.grid_bounds = (const float*)c->grid_bounds_dev;
+  c->b.grid_nx = nx;
+  c->b.grid_ny = ny;
+  c->b.grid_nz = nz;
+  c->b.grid_sectors = (int)n_sectors;
+  drop_graph(c);
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_set_correction(tpc_ctx* c, tpc_corr mode) {
+  if (!c) return TPC_ERR_INVALID_ARG;
+  if (mode != TPC_CORR_NONE && mode != TPC_CORR_GRID && mode != TPC_CORR_MLP) return TPC_ERR_INVALID_ARG;
+  c->corr = mode;
+  drop_graph(c);
+  return TPC_OK;
+}
+
 extern "C" void tpc_destroy(tpc_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->cfg.device);
   free_all(c);
+  while (!c->persist.empty()) persist_free(c, c->persist.back());
   if (c->have_events)
     for (int i = 0; i <= TPC_N_STAGES; ++i) cudaEventDestroy(c->ev[i]);
   if (c->own_stream) {

@@ -107,6 +107,14 @@ struct Buffers {
   unsigned long long* item_ex;    // exclusive scan of item_cnt [I]
   int* item_ntl;                  // tracklets per item [I]
   int* item_tl_ex;                // exclusive scan of item_ntl [I]
+  // space-point correction (applied before binning when enabled)
+  const float2* grid;             // per-sector (dy, dz) nodes [S][nx][ny][nz]
+  const float* grid_bounds;       // [S][6]: x0, x1, v0, v1, z0, z1 (v = y / (x tan_half))
+  int grid_nx, grid_ny, grid_nz, grid_sectors;
+  const void* mlp;                // per-sector BF16 networks (tpc_mlp.cu), null = none
+  int mlp_sectors;
+  float* cy;                      // corrected y, z [N]
+  float* cz;
   void* trk_tmp;                  // per-item track regions [T_cap]
   int* trk_tl_tmp;                // tracklet storage index of every per-item track [T_cap]
   uint32_t* ids_tmp;              // per-item cluster-id regions [N]
@@ -132,3 +140,5 @@ cudaError_t tpc_configure_kernels(int sort_smem, int link_smem);
 cudaError_t tpc_batched_occupancy(int per_sm[3]);
 cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t tpc_launch_batched(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
+cudaError_t tpc_launch_grid_correction(const Buffers& b, cudaStream_t s);
+cudaError_t tpc_launch_mlp_correction(const Buffers& b, cudaStream_t s);

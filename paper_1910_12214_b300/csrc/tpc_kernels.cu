@@ -1513,6 +1513,68 @@ cudaError_t tpc_launch_batched(const Buffers& b, const LaunchCfg& c, cudaStream_
   mark(11);
   return cudaGetLastError();
 }
+
+// ============================================================================ S11
+// Space-point correction by a per-sector grid (location-dependent calibration,
+// Abstract; online calibration, Sec. 3): trilinear interpolation of (dy, dz)
+// nodes over (x, v = y / (x tan_half), z), coordinates clamped to the grid, at
+// the pad row's radius (the row fixes x).  Writes corrected y, z.
+__global__ void __launch_bounds__(256) k_correct_grid(const __grid_constant__ Buffers b) {
+  const DevParams& P = b.par;
+  const Chunk ch = b.chunks[blockIdx.x];
+  const int sector = b.item_sector ? (int)b.item_sector[ch.item] : 0;
+  if (sector >= b.grid_sectors) {
+    if (threadIdx.x == 0 && ch.end > ch.begin) atomicOr(b.err, TPC_DERR_BAD_INPUT);
+    return;
+  }
+  const float* B = b.grid_bounds + 6 * sector;
+  const float bx0 = B[0], sx = (b.grid_nx - 1) / (B[1] - B[0]);
+  const float bv0 = B[2], sv = (b.grid_ny - 1) / (B[3] - B[2]);
+  const float bz0 = B[4], sz = (b.grid_nz - 1) / (B[5] - B[4]);
+  const float2* G = b.grid + (size_t)sector * b.grid_nx * b.grid_ny * b.grid_nz;
+  for (int i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) {
+    const int r = b.row[i];
+    const float y = b.y[i], z = b.z[i];
+    if (r < 0 || r >= P.n_rows) {  // rejected later by validation
+      b.cy[i] = y;
+      b.cz[i] = z;
+      continue;
+    }
+    const float x = P.x[r];
+    const float v = y / (x * P.tan_half);
+    float u[3] = {(x - bx0) * sx, (v - bv0) * sv, (z - bz0) * sz};
+    const int dims[3] = {b.grid_nx, b.grid_ny, b.grid_nz};
+    int lo[3];
+    float f[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+      const float t = fminf(fmaxf(u[a], 0.0f), (float)(dims[a] - 1));  // NaN stays NaN, caught later
+      int k = (int)floorf(t);
+      k = min(max(k, 0), dims[a] - 2);
+      lo[a] = k;
+      f[a] = t - k;
+    }
+    const size_t sy_ = b.grid_nz, sx_ = (size_t)b.grid_ny * b.grid_nz;
+    const float2* g0 = G + lo[0] * sx_ + lo[1] * sy_ + lo[2];
+    float2 c[8];
+#pragma unroll
+    for (int k = 0; k < 8; ++k) c[k] = g0[(k >> 2) * sx_ + ((k >> 1) & 1) * sy_ + (k & 1)];
+    float dy = 0.f, dz = 0.f;
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      const float w = ((k >> 2) ? f[0] : 1.f - f[0]) * (((k >> 1) & 1) ? f[1] : 1.f - f[1]) * ((k & 1) ? f[2] : 1.f - f[2]);
+      dy += w * c[k].x;
+      dz += w * c[k].y;
+    }
+    b.cy[i] = y + dy;
+    b.cz[i] = z + dz;
+  }
+}
+
+cudaError_t tpc_launch_grid_correction(const Buffers& b, cudaStream_t s) {
+  k_correct_grid<<<b.n_chunks, 256, 0, s>>>(b);
+  return cudaGetLastError();
+}
 // ============================================================================ host launchers
 cudaError_t tpc_batched_occupancy(int per_sm[3]) {
   cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_batched<1>, BT, 0);

@@ -360,3 +360,136 @@ def slice_frame(frame: Clusters, core_cm: float = 1000.0, overlap_cm: float = 30
                    n_physical=frame.n_physical)
     out.src_index = np.concatenate(ids)
     return out
+
+
+# ---------------------------------------------------------------- distortions
+@dataclasses.dataclass
+class Distortion:
+    """Per-sector smooth space-charge distortion of the measured (y, z).
+
+    d_s(x, y, z) = sum_k A_k exp(-|p - c_k|^2 / (2 w_k^2)), k < 32, with (y, z)
+    components (the pad row fixes x, so a radial shift is not measurable on it);
+    centres uniform in the sector volume, widths uniform in [30, 80] cm,
+    amplitudes in the unit disc, the field rescaled so that max |d| = max_d on a
+    probe grid.  Measured = true + d(true).
+    """
+    centres: np.ndarray   # [S, K, 3]
+    widths: np.ndarray    # [S, K]
+    amps: np.ndarray      # [S, K, 2]
+    z_side: np.ndarray    # [S] +1 (z >= 0) or -1; 0 = both sides (single-sector config)
+    geom: Geometry
+
+    def field(self, s: int, x, y, z):
+        c, w, a = self.centres[s], self.widths[s], self.amps[s]
+        d2 = ((x[..., None] - c[:, 0]) ** 2 + (y[..., None] - c[:, 1]) ** 2 + (z[..., None] - c[:, 2]) ** 2)
+        g = np.exp(-d2 / (2.0 * w ** 2))
+        return g @ a[:, 0], g @ a[:, 1]
+
+    def field_jac(self, s: int, x, y, z):
+        """Field and its derivatives d(dy, dz)/d(y, z)."""
+        c, w, a = self.centres[s], self.widths[s], self.amps[s]
+        ry, rz = y[..., None] - c[:, 1], z[..., None] - c[:, 2]
+        g = np.exp(-((x[..., None] - c[:, 0]) ** 2 + ry * ry + rz * rz) / (2.0 * w ** 2))
+        gy, gz = -g * ry / w ** 2, -g * rz / w ** 2
+        return g @ a[:, 0], g @ a[:, 1], gy @ a[:, 0], gz @ a[:, 0], gy @ a[:, 1], gz @ a[:, 1]
+
+    def invert(self, s: int, x, ym, zm, tol: float = 1e-10, max_iter: int = 50):
+        """True (y, z) with measured = true + d(true): Newton's method on the 2x2
+        system (the field gradient is well below 1, so the root is unique)."""
+        yt, zt = np.array(ym, np.float64, copy=True), np.array(zm, np.float64, copy=True)
+        for _ in range(max_iter):
+            dy, dz, dyy, dyz, dzy, dzz = self.field_jac(s, x, yt, zt)
+            fy, fz = yt + dy - ym, zt + dz - zm
+            a11, a12, a21, a22 = 1.0 + dyy, dyz, dzy, 1.0 + dzz
+            det = a11 * a22 - a12 * a21
+            sy = (a22 * fy - a12 * fz) / det
+            sz = (a11 * fz - a21 * fy) / det
+            yt -= sy
+            zt -= sz
+            if max(np.abs(sy).max(initial=0.0), np.abs(sz).max(initial=0.0)) < tol:
+                break
+        return yt, zt
+
+    def z_range(self, s: int):
+        zm = self.geom.z_max
+        return {1: (0.0, zm), -1: (-zm, 0.0), 0: (-zm, zm)}[int(self.z_side[s])]
+
+
+def make_distortion(seed: int = 1, n_sectors: int = 36, n_gauss: int = 32, max_d: float = 10.0,
+                    geom: Geometry = None, single_sector: bool = False) -> Distortion:
+    geom = geom or Geometry()
+    rng = rng_for(seed, stream=5)
+    tan_h = math.tan(math.radians(geom.half_angle_deg))
+    side = np.zeros(n_sectors) if single_sector else np.where(np.arange(n_sectors) < n_sectors // 2, 1.0, -1.0)
+    cen = np.zeros((n_sectors, n_gauss, 3))
+    wid = rng.uniform(30.0, 80.0, (n_sectors, n_gauss))
+    amp = np.zeros((n_sectors, n_gauss, 2))
+    for s in range(n_sectors):
+        x = rng.uniform(geom.x_min, geom.x_max, n_gauss)
+        cen[s, :, 0] = x
+        cen[s, :, 1] = rng.uniform(-1.0, 1.0, n_gauss) * x * tan_h
+        lo, hi = {1: (0.0, geom.z_max), -1: (-geom.z_max, 0.0), 0: (-geom.z_max, geom.z_max)}[int(side[s])]
+        cen[s, :, 2] = rng.uniform(lo, hi, n_gauss)
+        r = np.sqrt(rng.uniform(0.0, 1.0, n_gauss))
+        ph = rng.uniform(0.0, 2.0 * math.pi, n_gauss)
+        amp[s, :, 0] = r * np.cos(ph)
+        amp[s, :, 1] = r * np.sin(ph)
+    d = Distortion(cen, wid, amp, side, geom)
+    # rescale each sector so that max |d| = max_d over a probe grid of its volume
+    for s in range(n_sectors):
+        lo, hi = d.z_range(s)
+        xs = np.linspace(geom.x_min, geom.x_max, 24)
+        vs = np.linspace(-1.0, 1.0, 24)
+        zs = np.linspace(lo, hi, 48)
+        X, V, Z = np.meshgrid(xs, vs, zs, indexing="ij")
+        dy, dz = d.field(s, X, V * X * tan_h, Z)
+        m = max(np.abs(dy).max(), np.abs(dz).max())
+        d.amps[s] *= max_d / m
+    return d
+
+
+def distort(cl: Clusters, dist: Distortion) -> Clusters:
+    """Measured clusters: y, z shifted by the field at the true position (x, row kept)."""
+    out = dataclasses.replace(cl)
+    y = cl.y.astype(np.float64).copy()
+    z = cl.z.astype(np.float64).copy()
+    x = cl.x.astype(np.float64)
+    sec = np.repeat(cl.item_sector.astype(np.int64), np.diff(cl.item_off.astype(np.int64)))
+    for s in np.unique(sec):
+        m = sec == s
+        dy, dz = dist.field(int(s), x[m], y[m], z[m])
+        y[m] += dy
+        z[m] += dz
+    out.y = y.astype(np.float32)
+    out.z = z.astype(np.float32)
+    return out
+
+
+def correction_grid(dist: Distortion, n: int = 64, margin: float = 12.0, tol: float = 1e-9):
+    """Per sector n^3 grid over the distorted volume (x, v = y / (x tan), z) with
+    margins; node value = (0, dy, dz) such that true = measured + value, found by
+    Newton's method on measured = true + d(true) to tol (FP64).
+    Returns grid float32 [S, n, n, n, 3] (axes x, v, z) and bounds float32
+    [S, 6] = (x0, x1, v0, v1, z0, z1)."""
+    g = dist.geom
+    tan_h = math.tan(math.radians(g.half_angle_deg))
+    S = dist.centres.shape[0]
+    grid = np.zeros((S, n, n, n, 3), np.float32)
+    bounds = np.zeros((S, 6), np.float32)
+    for s in range(S):
+        lo, hi = dist.z_range(s)
+        x0, x1 = g.x_min - margin, g.x_max + margin
+        v0, v1 = -1.3, 1.3
+        z0, z1 = lo - margin, hi + margin
+        bounds[s] = (x0, x1, v0, v1, z0, z1)
+        X, V, Z = np.meshgrid(np.linspace(x0, x1, n), np.linspace(v0, v1, n), np.linspace(z0, z1, n), indexing="ij")
+        ym = V * X * tan_h
+        yt, zt = dist.invert(s, X, ym, Z, tol=tol)
+        grid[s, ..., 1] = (yt - ym).astype(np.float32)
+        grid[s, ..., 2] = (zt - Z).astype(np.float32)
+    return grid, bounds
+
+
+def exact_correction(dist: Distortion, sector: int, x, ym, zm, tol: float = 1e-10):
+    """True (y, z) of measured points (FP64 inversion of the field)."""
+    return dist.invert(sector, np.asarray(x, np.float64), np.asarray(ym, np.float64), np.asarray(zm, np.float64), tol)

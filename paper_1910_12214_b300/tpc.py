@@ -72,6 +72,8 @@ _sig = {
     "tpc_set_tuning": ([_P, C.POINTER(tpc_tuning)], C.c_int),
     "tpc_get_tuning": ([_P, C.POINTER(tpc_tuning)], C.c_int),
     "tpc_autotune": ([_P, C.c_int, C.POINTER(tpc_tuning), C.POINTER(C.c_float)], C.c_int),
+    "tpc_set_grid_correction": ([_P, _P, _P, C.c_uint32, C.c_int, C.c_int, C.c_int], C.c_int),
+    "tpc_set_correction": ([_P, C.c_int], C.c_int),
     "tpc_bin_sector_noalloc": ([_P, _P, _P, C.c_uint32, C.c_int, _P, _P, _P, _P], C.c_int),
     "tpc_destroy": ([_P], None),
     "tpc_last_error": ([_P], C.c_char_p),
@@ -238,6 +240,21 @@ class Tracker:
         us = C.c_float()
         self._check(_lib.tpc_autotune(self._h, iters, C.byref(t), C.byref(us)))
         return {f: getattr(t, f) for f, _ in tpc_tuning._fields_}, float(us.value)
+
+    def set_grid_correction(self, grid, bounds):
+        grid = np.ascontiguousarray(grid, np.float32)
+        bounds = np.ascontiguousarray(bounds, np.float32)
+        S, nx, ny, nz, k = grid.shape
+        assert k == 3 and bounds.shape == (S, 6)
+        self._check(_lib.tpc_set_grid_correction(self._h, _ptr(grid), _ptr(bounds), S, nx, ny, nz))
+
+    def set_correction(self, mode: str):
+        self._check(_lib.tpc_set_correction(self._h, CORR[mode]))
+
+    def corrected(self):
+        """Corrected (y, z) of the last tpc_track() (debug stage 11)."""
+        d = self.debug_dump(11).view(np.float32).reshape(-1, 2)
+        return d[:, 0].copy(), d[:, 1].copy()
 
     def close(self):
         if getattr(self, "_h", None):
