@@ -172,6 +172,39 @@ tpc_status tpc_set_grid_correction(tpc_ctx* ctx, const float* grid, const float*
  * network). */
 tpc_status tpc_set_correction(tpc_ctx* ctx, tpc_corr mode);
 
+/* Learned surrogate of the grid correction: per sector a 3 -> 64 -> 64 -> 3
+ * network with SiLU activations, BF16 operands and FP32 sums, whose output x
+ * 10 cm is the (dx, dy, dz) correction (dy, dz applied; the pad row fixes x).
+ * Inputs are the measured (x, v = y / (x tan), z) normalised to [-1, 1]^3 by
+ * the grid's bounds.  Parameters per sector (float32, 4611): W1[64][3], b1[64],
+ * W2[64][64] (out, in), b2[64], W3[3][64], b3[3].
+ *
+ * tpc_surrogate_train: trains on samples drawn uniformly in each sector's grid
+ * box with targets read from the grid (tpc_set_grid_correction must have been
+ * called): MSE, Adam (beta 0.9, 0.999), learning rate lr (0 = 3e-2) with a
+ * cosine decay over n_samples / 1024 steps of 1024 samples per sector, Xavier-uniform
+ * initial weights; samples and initial weights come from a counter-based
+ * generator (splitmix64) keyed by seed.  max_steps > 0 stops after that many
+ * steps; a later call with the same seed resumes (a call after the last step
+ * starts afresh).  The residual |network - grid| of (dy, dz) in cm over
+ * held-out points is returned in *max_resid_cm and *rms_resid_cm (nullable).
+ * tpc_surrogate_eval: the same residual over n_points per sector.
+ * tpc_surrogate_params / set_params: a sector's FP32 master parameters (n >=
+ * 4611 floats).  tpc_surrogate_grad: dL/dparams and the loss of the current
+ * parameters on the training batch (seed, step) of `batch` samples (a multiple
+ * of 128, at most 1024), without updating anything.  save / load: parameters,
+ * Adam state, step and input bounds in a binary checkpoint; resuming a run
+ * from a checkpoint gives the same parameters bit for bit. */
+tpc_status tpc_surrogate_train(tpc_ctx* ctx, uint64_t n_samples, uint64_t seed, int max_steps, float lr,
+                               float* max_resid_cm, float* rms_resid_cm);
+tpc_status tpc_surrogate_eval(tpc_ctx* ctx, uint64_t n_points, float* max_resid_cm, float* rms_resid_cm);
+tpc_status tpc_surrogate_params(tpc_ctx* ctx, int sector, float* out, int n);
+tpc_status tpc_surrogate_set_params(tpc_ctx* ctx, int sector, const float* in, int n);
+tpc_status tpc_surrogate_grad(tpc_ctx* ctx, int sector, uint64_t seed, uint64_t step, int batch, float* grad, int n,
+                              float* loss);
+tpc_status tpc_surrogate_save(tpc_ctx* ctx, const char* path);
+tpc_status tpc_surrogate_load(tpc_ctx* ctx, const char* path);
+
 /* Launch shapes of the kernels (no effect on results: every shape gives the
  * same output bit for bit).  tracklet_lanes: lanes that share one tracklet
  * (1, 2, 4, 8, 16 or 32; they split the hit search of every row);

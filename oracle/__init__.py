@@ -3,4 +3,5 @@
 Only tests/, __graft_entry__.smoke() and bench.py's CPU-baseline leg may import
 this package.  The product path (paper_1910_12214_b300) never does.
 """
-from .oracle import (OracleConfig, build_oracle, chi2, correct_clusters, fit_hits, propagate, run, trilinear)  # noqa: F401
+from .oracle import (MLP_NP, OracleConfig, adam, bf16, build_oracle, chi2, correct_clusters, counter_uniform, fit_hits,
+                     mlp_batch, mlp_forward, mlp_grad, mlp_init, propagate, run, trilinear)  # noqa: F401

@@ -67,6 +67,23 @@ def _load():
         lib.orc_trilinear.restype = None
         lib.orc_trilinear.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int, C.c_double, C.c_int,
                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p]
+        if hasattr(lib, "orc_mlp_forward"):
+            lib.orc_counter_uniform.restype = C.c_double
+            lib.orc_counter_uniform.argtypes = [C.c_uint64, C.c_uint64, C.c_uint64, C.c_uint64]
+            lib.orc_bf16.restype = C.c_float
+            lib.orc_bf16.argtypes = [C.c_float]
+            lib.orc_mlp_forward.restype = None
+            lib.orc_mlp_forward.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_int, C.c_void_p]
+            lib.orc_mlp_grad.restype = C.c_double
+            lib.orc_mlp_grad.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p]
+            lib.orc_adam.restype = None
+            lib.orc_adam.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_int, C.c_int,
+                                     C.c_double, C.c_double, C.c_double, C.c_double]
+            lib.orc_mlp_init.restype = None
+            lib.orc_mlp_init.argtypes = [C.c_uint64, C.c_int, C.c_void_p]
+            lib.orc_mlp_batch.restype = None
+            lib.orc_mlp_batch.argtypes = [C.c_uint64, C.c_int, C.c_uint64, C.c_int, C.c_void_p, C.c_int, C.c_int,
+                                          C.c_int, C.c_void_p, C.c_void_p]
         lib.orc_chi2.restype = C.c_double
         lib.orc_chi2.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         _lib = lib
@@ -174,3 +191,55 @@ def correct_clusters(cl, grid, bounds, n_rows=152, x_min=85.0, x_max=246.0):
     z = cl.z.astype(np.float64)
     dy, dz = trilinear(grid, bounds, sec, x, y, z)
     return (y + dy).astype(np.float32), (z + dz).astype(np.float32)
+
+
+MLP_NP = 4611
+
+
+def counter_uniform(seed, a, b, k):
+    return _load().orc_counter_uniform(seed, a, b, k)
+
+
+def mlp_forward(P, inputs, exact=False):
+    lib = _load()
+    P = np.ascontiguousarray(P, np.float32)
+    x = np.ascontiguousarray(inputs, np.float64).reshape(-1, 3)
+    out = np.empty_like(x)
+    lib.orc_mlp_forward(_p(P), x.shape[0], _p(x), int(exact), _p(out))
+    return out
+
+
+def mlp_grad(P, inputs, targets, exact=False):
+    lib = _load()
+    P = np.ascontiguousarray(P, np.float32)
+    x = np.ascontiguousarray(inputs, np.float64).reshape(-1, 3)
+    t = np.ascontiguousarray(targets, np.float64).reshape(-1, 3)
+    g = np.empty(MLP_NP)
+    loss = lib.orc_mlp_grad(_p(P), x.shape[0], _p(x), _p(t), int(exact), _p(g))
+    return g, loss
+
+
+def adam(w, m, v, g, t, T, lr=1e-3, b1=0.9, b2=0.999, eps=1e-8):
+    lib = _load()
+    w, m, v = (np.ascontiguousarray(a, np.float64).copy() for a in (w, m, v))
+    g = np.ascontiguousarray(g, np.float64)
+    lib.orc_adam(_p(w), _p(m), _p(v), _p(g), w.shape[0], t, T, lr, b1, b2, eps)
+    return w, m, v
+
+
+def mlp_init(seed, sector):
+    P = np.empty(MLP_NP, np.float32)
+    _load().orc_mlp_init(seed, sector, _p(P))
+    return P
+
+
+def mlp_batch(seed, sector, step, n, grid_sector):
+    g = np.ascontiguousarray(grid_sector, np.float32)
+    nx, ny, nz, _ = g.shape
+    x, t = np.empty((n, 3)), np.empty((n, 3))
+    _load().orc_mlp_batch(seed, sector, step, n, _p(g), nx, ny, nz, _p(x), _p(t))
+    return x, t
+
+
+def bf16(v):
+    return _load().orc_bf16(float(v))

@@ -47,6 +47,14 @@ struct tpc_ctx {
   void* grid_dev = nullptr;
   void* grid_bounds_dev = nullptr;
   int grid_n[3] = {0, 0, 0}, grid_sectors = 0;
+  // MLP surrogate state (master weights, Adam moments, inference copies)
+  int mlp_S = 0, mlp_batch = 1024;
+  uint64_t mlp_seed = 0, mlp_step = 0, mlp_T = 0;
+  float mlp_lr = 3e-2f;
+  float *mlp_master = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_partial = nullptr, *mlp_loss = nullptr;
+  float* mlp_bounds = nullptr;
+  void* mlp_infer = nullptr;
+  std::vector<float> mlp_bounds_host;
 };
 
 namespace {
@@ -779,6 +787,7 @@ extern "C" tpc_status tpc_set_grid_correction(tpc_ctx* c, const float* grid, con
   persist_free(c, c->grid_dev);
   persist_free(c, c->grid_bounds_dev);
   c->grid_dev = persist_alloc(c, 8 * nodes);
+  c->mlp_bounds_host.assign(bounds, bounds + 6 * (size_t)n_sectors);
   c->grid_bounds_dev = persist_alloc(c, 24 * (size_t)n_sectors);
   if (!c->grid_dev || !c->grid_bounds_dev) {
     persist_free(c, c->grid_dev);
@@ -807,6 +816,240 @@ extern "C" tpc_status tpc_set_correction(tpc_ctx* c, tpc_corr mode) {
   c->corr = mode;
   drop_graph(c);
   return TPC_OK;
+}
+
+
+// ---------------------------------------------------------------- MLP surrogate
+namespace {
+const uint32_t kMlpMagic = 0x31504C4D;  // "MLP1"
+
+tpc_status mlp_alloc(tpc_ctx* c, int S) {
+  if (c->mlp_master && c->mlp_S == S) return TPC_OK;
+  for (void* p : {(void*)c->mlp_master, (void*)c->mlp_m, (void*)c->mlp_v, (void*)c->mlp_partial,
+                  (void*)c->mlp_loss, (void*)c->mlp_bounds, c->mlp_infer})
+    persist_free(c, p);
+  const size_t np = (size_t)S * tpc_mlp_stride();
+  const int nblk = c->mlp_batch / 128;
+  c->mlp_master = (float*)persist_alloc(c, 4 * np);
+  c->mlp_m = (float*)persist_alloc(c, 4 * np);
+  c->mlp_v = (float*)persist_alloc(c, 4 * np);
+  c->mlp_partial = (float*)persist_alloc(c, 4 * np * nblk);
+  c->mlp_loss = (float*)persist_alloc(c, 4 * (size_t)S * nblk);
+  c->mlp_bounds = (float*)persist_alloc(c, 24 * (size_t)S);
+  c->mlp_infer = persist_alloc(c, tpc_mlp_infer_bytes() * S);
+  if (!c->mlp_master || !c->mlp_m || !c->mlp_v || !c->mlp_partial || !c->mlp_loss || !c->mlp_bounds ||
+      !c->mlp_infer) {
+    c->mlp_master = nullptr;
+    return fail(c, TPC_ERR_OOM, "surrogate allocation failed");
+  }
+  c->mlp_S = S;
+  c->b.mlp = nullptr;
+  return TPC_OK;
+}
+
+tpc_status mlp_publish(tpc_ctx* c) {
+  cudaError_t e = tpc_mlp_prepare(c->mlp_master, c->mlp_bounds, c->mlp_infer, c->mlp_S, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "surrogate prepare");
+  c->b.mlp = c->mlp_infer;
+  c->b.mlp_sectors = c->mlp_S;
+  drop_graph(c);
+  return TPC_OK;
+}
+
+tpc_status mlp_eval(tpc_ctx* c, uint64_t n_points, float* max_resid, float* rms_resid) {
+  const int nblk = (int)std::max<uint64_t>(1, (n_points + 127) / 128);
+  float* out = (float*)dev_alloc(c, 8 * (size_t)c->mlp_S * nblk);
+  if (!out) return fail(c, TPC_ERR_OOM, "evaluation buffer");
+  cudaError_t e = tpc_mlp_eval(c->mlp_master, (const float2*)c->grid_dev, c->b.grid_nx, c->b.grid_ny, c->b.grid_nz,
+                               c->mlp_S, nblk, c->mlp_seed, out, c->stream);
+  std::vector<float> h(2 * (size_t)c->mlp_S * nblk);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(h.data(), out, 4 * h.size(), cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  // return the scratch block to the allocator (it is the last one of the batch list)
+  c->blocks.pop_back();
+  if (c->has_alloc)
+    c->alloc.free(out, c->alloc.user);
+  else
+    cudaFreeAsync(out, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "surrogate evaluation");
+  double mx = 0.0, ss = 0.0;
+  for (size_t k = 0; k < h.size() / 2; ++k) {
+    mx = std::max(mx, (double)h[2 * k]);
+    ss += h[2 * k + 1];
+  }
+  if (max_resid) *max_resid = (float)mx;
+  if (rms_resid) *rms_resid = (float)std::sqrt(ss / (128.0 * nblk * c->mlp_S));
+  return TPC_OK;
+}
+}  // namespace
+
+extern "C" tpc_status tpc_surrogate_train(tpc_ctx* c, uint64_t n_samples, uint64_t seed, int max_steps, float lr,
+                                          float* max_resid_cm, float* rms_resid_cm) {
+  if (!c || n_samples == 0 || lr < 0.f || !(lr < 1.f)) return TPC_ERR_INVALID_ARG;
+  if (!c->grid_dev) return fail(c, TPC_ERR_STATE, "the surrogate learns the grid correction: set a grid first");
+  cudaError_t e = cudaSetDevice(c->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  const int S = c->b.grid_sectors;
+  const bool fresh = !c->mlp_master || c->mlp_S != S || c->mlp_seed != seed || c->mlp_step >= c->mlp_T;
+  if (fresh) {
+    tpc_status st = mlp_alloc(c, S);
+    if (st != TPC_OK) return st;
+    c->mlp_seed = seed;
+    c->mlp_step = 0;
+    c->mlp_T = std::max<uint64_t>(1, n_samples / (uint64_t)c->mlp_batch);
+    c->mlp_lr = lr > 0.f ? lr : 3e-2f;
+    if ((e = tpc_mlp_init(c->mlp_master, c->mlp_m, c->mlp_v, S, seed, c->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(c->mlp_bounds, c->mlp_bounds_host.data(), 24 * (size_t)S, cudaMemcpyHostToDevice,
+                             c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "surrogate init");
+  }
+  const uint64_t end = max_steps > 0 ? std::min<uint64_t>(c->mlp_T, c->mlp_step + (uint64_t)max_steps) : c->mlp_T;
+  for (uint64_t t = c->mlp_step; t < end; ++t) {
+    const double lr_t = c->mlp_lr * 0.5 * (1.0 + std::cos(M_PI * (double)t / (double)c->mlp_T));
+    const double c1 = 1.0 - std::pow(0.9, (double)(t + 1)), c2 = 1.0 - std::pow(0.999, (double)(t + 1));
+    e = tpc_mlp_step(c->mlp_master, c->mlp_m, c->mlp_v, c->mlp_partial, c->mlp_loss, (const float2*)c->grid_dev,
+                     c->b.grid_nx, c->b.grid_ny, c->b.grid_nz, S, c->mlp_batch, seed, t, (float)lr_t, (float)c1,
+                     (float)c2, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "surrogate step");
+  }
+  c->mlp_step = end;
+  tpc_status st = mlp_publish(c);
+  if (st != TPC_OK) return st;
+  float mx = 0.f, rms = 0.f;
+  st = mlp_eval(c, 8192, &mx, &rms);
+  if (st != TPC_OK) return st;
+  if (max_resid_cm) *max_resid_cm = mx;
+  if (rms_resid_cm) *rms_resid_cm = rms;
+  if (!std::isfinite(rms)) return fail(c, TPC_ERR_BAD_INPUT, "training diverged (non-finite residual): lower lr");
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_surrogate_eval(tpc_ctx* c, uint64_t n_points, float* max_resid_cm, float* rms_resid_cm) {
+  if (!c || n_points == 0) return TPC_ERR_INVALID_ARG;
+  if (!c->mlp_master || !c->grid_dev) return fail(c, TPC_ERR_STATE, "needs a trained surrogate and its grid");
+  return mlp_eval(c, n_points, max_resid_cm, rms_resid_cm);
+}
+
+extern "C" tpc_status tpc_surrogate_params(tpc_ctx* c, int sector, float* out, int n) {
+  if (!c || !out || n < tpc_mlp_nparams()) return TPC_ERR_INVALID_ARG;
+  if (!c->mlp_master || sector < 0 || sector >= c->mlp_S) return fail(c, TPC_ERR_STATE, "no surrogate for sector");
+  cudaError_t e = cudaMemcpyAsync(out, c->mlp_master + (size_t)sector * tpc_mlp_stride(), 4 * tpc_mlp_nparams(),
+                                  cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  return e == cudaSuccess ? TPC_OK : cuda_fail(c, e, "surrogate params");
+}
+
+extern "C" tpc_status tpc_surrogate_set_params(tpc_ctx* c, int sector, const float* in, int n) {
+  if (!c || !in || n < tpc_mlp_nparams()) return TPC_ERR_INVALID_ARG;
+  if (!c->grid_dev) return fail(c, TPC_ERR_STATE, "set a grid first (it fixes the sectors and input bounds)");
+  const int S = c->b.grid_sectors;
+  if (sector < 0 || sector >= S) return TPC_ERR_INVALID_ARG;
+  if (!c->mlp_master || c->mlp_S != S) {
+    tpc_status st = mlp_alloc(c, S);
+    if (st != TPC_OK) return st;
+    cudaError_t e = tpc_mlp_init(c->mlp_master, c->mlp_m, c->mlp_v, S, 0, c->stream);
+    if (e == cudaSuccess)
+      e = cudaMemcpyAsync(c->mlp_bounds, c->mlp_bounds_host.data(), 24 * (size_t)S, cudaMemcpyHostToDevice, c->stream);
+    if (e != cudaSuccess) return cuda_fail(c, e, "surrogate init");
+    c->mlp_step = c->mlp_T = 0;
+  }
+  cudaError_t e = cudaMemcpyAsync(c->mlp_master + (size_t)sector * tpc_mlp_stride(), in, 4 * tpc_mlp_nparams(),
+                                  cudaMemcpyHostToDevice, c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "surrogate params");
+  return mlp_publish(c);
+}
+
+extern "C" tpc_status tpc_surrogate_grad(tpc_ctx* c, int sector, uint64_t seed, uint64_t step, int batch, float* grad,
+                                         int n, float* loss) {
+  if (!c || !grad || n < tpc_mlp_nparams() || batch < 128 || batch % 128 || batch > c->mlp_batch)
+    return TPC_ERR_INVALID_ARG;
+  if (!c->mlp_master || !c->grid_dev || sector < 0 || sector >= c->mlp_S)
+    return fail(c, TPC_ERR_STATE, "needs surrogate parameters and the grid");
+  cudaError_t e = tpc_mlp_grad_only(c->mlp_master, c->mlp_partial, c->mlp_loss, (const float2*)c->grid_dev,
+                                    c->b.grid_nx, c->b.grid_ny, c->b.grid_nz, c->mlp_S, batch, seed, step, c->stream);
+  const int nblk = batch / 128, np = tpc_mlp_nparams(), stride = tpc_mlp_stride();
+  std::vector<float> part((size_t)nblk * stride), lv(nblk);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(part.data(), c->mlp_partial + (size_t)sector * nblk * stride, 4 * part.size(),
+                        cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(lv.data(), c->mlp_loss + (size_t)sector * nblk, 4 * lv.size(), cudaMemcpyDeviceToHost,
+                        c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "surrogate gradient");
+  for (int p = 0; p < np; ++p) {
+    double g = 0.0;
+    for (int k = 0; k < nblk; ++k) g += part[(size_t)k * stride + p];
+    grad[p] = (float)g;
+  }
+  if (loss) {
+    double l = 0.0;
+    for (int k = 0; k < nblk; ++k) l += lv[k];
+    *loss = (float)(l / batch);
+  }
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_surrogate_save(tpc_ctx* c, const char* path) {
+  if (!c || !path) return TPC_ERR_INVALID_ARG;
+  if (!c->mlp_master) return fail(c, TPC_ERR_STATE, "no surrogate to save");
+  const size_t np = (size_t)c->mlp_S * tpc_mlp_stride();
+  std::vector<float> w(np), m(np), v(np), bnd(6 * (size_t)c->mlp_S);
+  cudaError_t e = cudaMemcpyAsync(w.data(), c->mlp_master, 4 * np, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(m.data(), c->mlp_m, 4 * np, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(v.data(), c->mlp_v, 4 * np, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(bnd.data(), c->mlp_bounds, 24 * (size_t)c->mlp_S, cudaMemcpyDeviceToHost, c->stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "surrogate save");
+  FILE* f = std::fopen(path, "wb");
+  if (!f) return fail(c, TPC_ERR_INVALID_ARG, std::string("cannot write ") + path);
+  const uint64_t hdr[8] = {kMlpMagic, (uint64_t)c->mlp_S, (uint64_t)tpc_mlp_stride(), c->mlp_seed, c->mlp_step,
+                           c->mlp_T, (uint64_t)c->mlp_batch, 0};
+  bool ok = std::fwrite(hdr, sizeof(hdr), 1, f) == 1 && std::fwrite(&c->mlp_lr, 4, 1, f) == 1 &&
+            std::fwrite(bnd.data(), 4, bnd.size(), f) == bnd.size() && std::fwrite(w.data(), 4, np, f) == np &&
+            std::fwrite(m.data(), 4, np, f) == np && std::fwrite(v.data(), 4, np, f) == np;
+  ok &= std::fclose(f) == 0;
+  return ok ? TPC_OK : fail(c, TPC_ERR_INVALID_ARG, "surrogate write failed");
+}
+
+extern "C" tpc_status tpc_surrogate_load(tpc_ctx* c, const char* path) {
+  if (!c || !path) return TPC_ERR_INVALID_ARG;
+  FILE* f = std::fopen(path, "rb");
+  if (!f) return fail(c, TPC_ERR_INVALID_ARG, std::string("cannot read ") + path);
+  uint64_t hdr[8];
+  float lr = 0.f;
+  bool ok = std::fread(hdr, sizeof(hdr), 1, f) == 1 && hdr[0] == kMlpMagic && hdr[2] == (uint64_t)tpc_mlp_stride() &&
+            hdr[1] > 0 && hdr[1] < 4096 && hdr[6] >= 128 && hdr[6] % 128 == 0 && hdr[6] <= (1u << 20) &&
+            std::fread(&lr, 4, 1, f) == 1;
+  if (!ok) {
+    std::fclose(f);
+    return fail(c, TPC_ERR_INVALID_ARG, "not a surrogate checkpoint");
+  }
+  const int S = (int)hdr[1];
+  const size_t np = (size_t)S * tpc_mlp_stride();
+  std::vector<float> w(np), m(np), v(np), bnd(6 * (size_t)S);
+  ok = std::fread(bnd.data(), 4, bnd.size(), f) == bnd.size() && std::fread(w.data(), 4, np, f) == np &&
+       std::fread(m.data(), 4, np, f) == np && std::fread(v.data(), 4, np, f) == np;
+  std::fclose(f);
+  if (!ok) return fail(c, TPC_ERR_INVALID_ARG, "truncated surrogate checkpoint");
+  cudaError_t e = cudaSetDevice(c->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  c->mlp_batch = (int)hdr[6];
+  if (c->mlp_S != S) c->mlp_master = nullptr;
+  tpc_status st = mlp_alloc(c, S);
+  if (st != TPC_OK) return st;
+  c->mlp_seed = hdr[3];
+  c->mlp_step = hdr[4];
+  c->mlp_T = hdr[5];
+  c->mlp_lr = lr;
+  if ((e = cudaMemcpyAsync(c->mlp_master, w.data(), 4 * np, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->mlp_m, m.data(), 4 * np, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->mlp_v, v.data(), 4 * np, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(c->mlp_bounds, bnd.data(), 24 * (size_t)S, cudaMemcpyHostToDevice, c->stream)) !=
+          cudaSuccess)
+    return cuda_fail(c, e, "surrogate upload");
+  return mlp_publish(c);
 }
 
 extern "C" void tpc_destroy(tpc_ctx* c) {

@@ -142,3 +142,17 @@ cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t 
 cudaError_t tpc_launch_batched(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t tpc_launch_grid_correction(const Buffers& b, cudaStream_t s);
 cudaError_t tpc_launch_mlp_correction(const Buffers& b, cudaStream_t s);
+
+// MLP surrogate (tpc_mlp.cu)
+size_t tpc_mlp_infer_bytes();
+int tpc_mlp_nparams();
+int tpc_mlp_stride();
+cudaError_t tpc_mlp_init(float* master, float* m, float* v, int S, uint64_t seed, cudaStream_t s);
+cudaError_t tpc_mlp_step(float* master, float* m, float* v, float* partial, float* loss, const float2* grid, int nx,
+                         int ny, int nz, int S, int batch, uint64_t seed, uint64_t step, float lr_t, float c1, float c2,
+                         cudaStream_t s);
+cudaError_t tpc_mlp_grad_only(const float* master, float* partial, float* loss, const float2* grid, int nx, int ny,
+                              int nz, int S, int batch, uint64_t seed, uint64_t step, cudaStream_t s);
+cudaError_t tpc_mlp_eval(const float* master, const float2* grid, int nx, int ny, int nz, int S, int nblk,
+                         uint64_t seed, float* out, cudaStream_t s);
+cudaError_t tpc_mlp_prepare(const float* master, const float* bounds, void* infer, int S, cudaStream_t s);

@@ -1,12 +1,523 @@
-// BF16 MLP surrogate of the space-point correction (placeholder until the
-// network kernels are in place).
+// BF16 MLP surrogate of the space-point correction: training, evaluation and
+// inference kernels.
+//
+// The paper asks for a location-dependent calibration of the cluster positions
+// during the online reconstruction (Abstract; online calibration, Sec. 3).  The
+// plain method is a per-sector trilinear grid (k_correct_grid).  This file
+// replaces the grid by a small network per sector, trained on samples of that
+// grid: 3 -> 64 -> 64 -> 3 with SiLU, inputs the measured position normalised to
+// [-1, 1]^3 by the grid's bounds, output the correction / 10 cm.  Operands
+// (inputs, weights, activations) are BF16 (round to nearest even), sums FP32.
+//
+//  - k_mlp_grad: forward and backward of one training batch, one CTA per 128
+//    samples of a sector, FP32 arithmetic on BF16-rounded operands; per-CTA
+//    gradient partials (fixed summation order, so training is deterministic).
+//  - k_mlp_adam: sums the partials in a fixed order and takes an Adam step
+//    (cosine learning rate) on the FP32 master weights.
+//  - k_correct_mlp: inference inside tracking.  A warp handles 16 clusters: the
+//    64x64 layer runs on the tensor cores (mma.sync m16n8k16, BF16 inputs, FP32
+//    accumulators); the 3-wide layers on the FMA pipes.
+//
+// Training samples and initial weights come from a counter-based generator
+// (splitmix64, Steele, Lea and Flood 2014) keyed by (seed, sector, step, index).
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
 
 #include "tpc.h"
 #include "tpc_internal.cuh"
 
+namespace {
+
+constexpr int H = 64;
+constexpr int OW1 = 0, OB1 = 192, OW2 = 256, OB2 = 4352, OW3 = 4416, OB3 = 4608, NP = 4611;
+constexpr int NPP = 4616;     // padded parameter stride per sector
+constexpr int TB = 128;       // samples per training CTA
+constexpr float OUT_SCALE = 10.0f;
+constexpr int WS = 516;       // per-warp slots: 192 gW3, 3 gb3, 64 gb2, 192 gW1, 64 gb1, loss
+
+__device__ __forceinline__ uint64_t sm64(uint64_t x) {
+  uint64_t z = x + 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+
+// uniform in [0, 1) with 24 bits: exact in FP32
+__device__ __forceinline__ float counter_uniform(uint64_t seed, uint64_t a, uint64_t b, uint64_t k) {
+  return (float)(sm64(sm64(sm64(seed + a) + b) + k) >> 40) * (1.0f / 16777216.0f);
+}
+
+__device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
+__device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
+__device__ __forceinline__ float dsilu(float z) {
+  const float s = 1.0f / (1.0f + expf(-z));
+  return s * (1.0f + z * (1.0f - s));
+}
+
+// trilinear (dy, dz) of a sector grid at index-space coordinates t (clamped)
+__device__ __forceinline__ float2 grid_at(const float2* G, int nx, int ny, int nz, float tx, float ty, float tz) {
+  const float t[3] = {tx, ty, tz};
+  const int dims[3] = {nx, ny, nz};
+  int lo[3];
+  float f[3];
+#pragma unroll
+  for (int a = 0; a < 3; ++a) {
+    const float u = fminf(fmaxf(t[a], 0.0f), (float)(dims[a] - 1));
+    int k = (int)floorf(u);
+    k = min(max(k, 0), dims[a] - 2);
+    lo[a] = k;
+    f[a] = u - k;
+  }
+  const size_t sy = nz, sx = (size_t)ny * nz;
+  const float2* g0 = G + lo[0] * sx + lo[1] * sy + lo[2];
+  float dy = 0.f, dz = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    const float2 c = g0[(k >> 2) * sx + ((k >> 1) & 1) * sy + (k & 1)];
+    const float w = ((k >> 2) ? f[0] : 1.f - f[0]) * (((k >> 1) & 1) ? f[1] : 1.f - f[1]) * ((k & 1) ? f[2] : 1.f - f[2]);
+    dy += w * c.x;
+    dz += w * c.y;
+  }
+  return make_float2(dy, dz);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------- training
+struct MlpTrain {
+  const float* master;  // [S][NPP]
+  float* partial;       // [S][nblk][NPP]
+  float* loss;          // [S][nblk]
+  const float2* grid;   // [S][nx][ny][nz]
+  int nx, ny, nz;
+  uint64_t seed, step;
+  int batch;            // samples per sector and step (multiple of TB)
+};
+
+__global__ void __launch_bounds__(TB) k_mlp_grad(const __grid_constant__ MlpTrain a) {
+  extern __shared__ float smem[];
+  float* W = smem;                 // rounded weights and FP32 biases [NPP]
+  float* A1 = W + NPP;             // [H][TB] first hidden activations (BF16 values)
+  float* Z2 = A1 + H * TB;         // [H][TB] second pre-activations, then their gradients
+  float* WP = Z2 + H * TB;         // [4 warps][WS] per-warp gradient sums
+  const int s = blockIdx.y, blk = blockIdx.x, t = threadIdx.x;
+  const int lane = t & 31, warp = t >> 5;
+  const float* M = a.master + (size_t)s * NPP;
+  for (int p = t; p < NP; p += TB) {
+    const bool bias = (p >= OB1 && p < OW2) || (p >= OB2 && p < OW3) || p >= OB3;
+    W[p] = bias ? M[p] : bf(M[p]);
+  }
+  __syncthreads();
+  // sample and target
+  const uint64_t k = (uint64_t)blk * TB + t;
+  float in[3], u[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    u[c] = counter_uniform(a.seed, (uint64_t)s, a.step, 3ull * k + c);
+    in[c] = bf(2.0f * u[c] - 1.0f);
+  }
+  const float2* G = a.grid + (size_t)s * a.nx * a.ny * a.nz;
+  const float2 tg = grid_at(G, a.nx, a.ny, a.nz, u[0] * (a.nx - 1), u[1] * (a.ny - 1), u[2] * (a.nz - 1));
+  const float tgt[3] = {0.0f, tg.x / OUT_SCALE, tg.y / OUT_SCALE};
+  // forward
+  for (int j = 0; j < H; ++j) {
+    const float z1 = W[OB1 + j] + W[OW1 + 3 * j] * in[0] + W[OW1 + 3 * j + 1] * in[1] + W[OW1 + 3 * j + 2] * in[2];
+    A1[j * TB + t] = bf(silu(z1));
+  }
+  float o[3] = {W[OB3], W[OB3 + 1], W[OB3 + 2]};
+  for (int j = 0; j < H; ++j) {
+    float z2 = W[OB2 + j];
+    const float* w2 = W + OW2 + H * j;
+    for (int i = 0; i < H; ++i) z2 += w2[i] * A1[i * TB + t];
+    Z2[j * TB + t] = z2;
+    const float a2 = bf(silu(z2));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[c] += W[OW3 + H * c + j] * a2;
+  }
+  float go[3], l = 0.f;
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float r = o[c] - tgt[c];
+    l += r * r;
+    go[c] = 2.0f * r / (float)a.batch;
+  }
+  // backward through layer 3: per-warp sums of the 3-wide gradients
+  auto wsum = [&](float v) {
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
+    return v;
+  };
+  float* wp = WP + warp * WS;  // 192 gW3 | 3 gb3 | 64 gb2 | 192 gW1 | 64 gb1 | loss
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    const float v = wsum(go[c]);
+    if (lane == 0) wp[192 + c] = v;
+  }
+  {
+    const float lv = wsum(l);
+    if (lane == 0) wp[515] = lv;
+  }
+  for (int j = 0; j < H; ++j) {
+    const float z2 = Z2[j * TB + t];
+    const float a2 = bf(silu(z2));
+    float ga2 = 0.f;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      ga2 += W[OW3 + H * c + j] * go[c];
+      const float v = wsum(go[c] * a2);
+      if (lane == 0) wp[H * c + j] = v;
+    }
+    const float gz2 = ga2 * dsilu(z2);
+    Z2[j * TB + t] = gz2;
+    const float v = wsum(gz2);
+    if (lane == 0) wp[195 + j] = v;
+  }
+  __syncthreads();
+  float* P = a.partial + ((size_t)s * gridDim.x + blk) * NPP;
+  // gW2[j][i] = sum over samples of gz2[j] a1[i]
+  for (int e = t; e < H * H; e += TB) {
+    const int j = e / H, i = e % H;
+    const float* gz = Z2 + j * TB;
+    const float* a1 = A1 + i * TB;
+    float acc = 0.f;
+    for (int b = 0; b < TB; ++b) acc += gz[b] * a1[b];
+    P[OW2 + e] = acc;
+  }
+  // layer 1
+  for (int i = 0; i < H; ++i) {
+    float ga1 = 0.f;
+    for (int j = 0; j < H; ++j) ga1 += W[OW2 + H * j + i] * Z2[j * TB + t];
+    const float z1 = W[OB1 + i] + W[OW1 + 3 * i] * in[0] + W[OW1 + 3 * i + 1] * in[1] + W[OW1 + 3 * i + 2] * in[2];
+    const float gz1 = ga1 * dsilu(z1);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const float v = wsum(gz1 * in[c]);
+      if (lane == 0) wp[259 + 3 * i + c] = v;
+    }
+    const float v = wsum(gz1);
+    if (lane == 0) wp[451 + i] = v;
+  }
+  __syncthreads();
+  // fixed-order sum of the four warps
+  for (int q = t; q < WS; q += TB) {
+    const float v = ((WP[q] + WP[WS + q]) + WP[2 * WS + q]) + WP[3 * WS + q];
+    if (q < 192) P[OW3 + q] = v;
+    else if (q < 195) P[OB3 + q - 192] = v;
+    else if (q < 259) P[OB2 + q - 195] = v;
+    else if (q < 451) P[OW1 + q - 259] = v;
+    else if (q < 515) P[OB1 + q - 451] = v;
+    else a.loss[(size_t)s * gridDim.x + blk] = v;
+  }
+}
+
+struct MlpAdam {
+  float* master;
+  float* m;
+  float* v;
+  const float* partial;
+  int nblk;
+  float lr_t, b1, b2, c1, c2, eps;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+};
+
+__global__ void __launch_bounds__(256) k_mlp_adam(const __grid_constant__ MlpAdam a) {
+  const int s = blockIdx.x;
+  for (int p = threadIdx.x; p < NP; p += blockDim.x) {
+    float g = 0.f;
+    for (int k = 0; k < a.nblk; ++k) g += a.partial[((size_t)s * a.nblk + k) * NPP + p];
+    const size_t q = (size_t)s * NPP + p;
+    const float m = a.b1 * a.m[q] + (1.0f - a.b1) * g;
+    const float v = a.b2 * a.v[q] + (1.0f - a.b2) * g * g;
+    a.m[q] = m;
+    a.v[q] = v;
+    a.master[q] -= a.lr_t * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
+  }
+}
+
+// Xavier-uniform initial weights (stream b = 0x5EED00000000, index = parameter)
+__global__ void k_mlp_init(float* master, float* m, float* v, uint64_t seed) {
+  const int s = blockIdx.x;
+  for (int p = threadIdx.x; p < NPP; p += blockDim.x) {
+    float lim = 0.f;
+    if (p < OB1) lim = sqrtf(6.0f / (3 + H));
+    else if (p >= OW2 && p < OB2) lim = sqrtf(6.0f / (H + H));
+    else if (p >= OW3 && p < OB3) lim = sqrtf(6.0f / (H + 3));
+    const size_t q = (size_t)s * NPP + p;
+    master[q] = (p < NP && lim > 0.f)
+                    ? (2.0f * counter_uniform(seed, (uint64_t)s, 0x5EED00000000ull, (uint64_t)p) - 1.0f) * lim
+                    : 0.f;
+    m[q] = 0.f;
+    v[q] = 0.f;
+  }
+}
+
+// residual |network - grid| (dy, dz) in cm at held-out points
+struct MlpEval {
+  const float* master;
+  const float2* grid;
+  int nx, ny, nz;
+  uint64_t seed;
+  float* out;  // [S][nblk][2]: max, sum of squares
+};
+
+__global__ void __launch_bounds__(TB) k_mlp_eval(const __grid_constant__ MlpEval a) {
+  __shared__ float W[NPP];
+  __shared__ float red[2][TB];
+  const int s = blockIdx.y, blk = blockIdx.x, t = threadIdx.x;
+  const float* M = a.master + (size_t)s * NPP;
+  for (int p = t; p < NP; p += TB) {
+    const bool bias = (p >= OB1 && p < OW2) || (p >= OB2 && p < OW3) || p >= OB3;
+    W[p] = bias ? M[p] : bf(M[p]);
+  }
+  __syncthreads();
+  float u[3], in[3];
+#pragma unroll
+  for (int c = 0; c < 3; ++c) {
+    u[c] = counter_uniform(a.seed, (uint64_t)s, 0xE7A100000000ull + blk, 3ull * t + c);
+    in[c] = bf(2.0f * u[c] - 1.0f);
+  }
+  float a1[H];
+#pragma unroll
+  for (int j = 0; j < H; ++j)
+    a1[j] = bf(silu(W[OB1 + j] + W[OW1 + 3 * j] * in[0] + W[OW1 + 3 * j + 1] * in[1] + W[OW1 + 3 * j + 2] * in[2]));
+  float o[3] = {W[OB3], W[OB3 + 1], W[OB3 + 2]};
+  for (int j = 0; j < H; ++j) {
+    float z2 = W[OB2 + j];
+#pragma unroll
+    for (int i = 0; i < H; ++i) z2 += W[OW2 + H * j + i] * a1[i];
+    const float a2 = bf(silu(z2));
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[c] += W[OW3 + H * c + j] * a2;
+  }
+  const float2* G = a.grid + (size_t)s * a.nx * a.ny * a.nz;
+  const float2 tg = grid_at(G, a.nx, a.ny, a.nz, u[0] * (a.nx - 1), u[1] * (a.ny - 1), u[2] * (a.nz - 1));
+  const float r = hypotf(OUT_SCALE * o[1] - tg.x, OUT_SCALE * o[2] - tg.y);
+  red[0][t] = r;
+  red[1][t] = r * r;
+  __syncthreads();
+  for (int off = TB / 2; off > 0; off >>= 1) {
+    if (t < off) {
+      red[0][t] = fmaxf(red[0][t], red[0][t + off]);
+      red[1][t] += red[1][t + off];
+    }
+    __syncthreads();
+  }
+  if (t == 0) {
+    a.out[((size_t)s * gridDim.x + blk) * 2] = red[0][0];
+    a.out[((size_t)s * gridDim.x + blk) * 2 + 1] = red[1][0];
+  }
+}
+
+// ---------------------------------------------------------------------------- inference
+// Per-sector inference copy: W2 in BF16 with padded rows (conflict-free
+// fragment loads), the other parameters as floats (weights BF16-rounded).
+constexpr int W2S = 72;  // padded row stride of W2 in BF16 elements
+struct __align__(16) MlpInfer {
+  __nv_bfloat16 w2[H * W2S];
+  float w1[192], b1[64], b2[64], w3[192], b3[4];
+  float bounds[8];
+};
+static_assert(sizeof(MlpInfer) % 16 == 0, "16-byte copies");
+
+__global__ void k_mlp_prepare(const float* master, const float* bounds, MlpInfer* inf) {
+  const int s = blockIdx.x;
+  const float* M = master + (size_t)s * NPP;
+  MlpInfer& I = inf[s];
+  for (int p = threadIdx.x; p < H * W2S; p += blockDim.x) {
+    const int j = p / W2S, i = p % W2S;
+    I.w2[p] = __float2bfloat16_rn(i < H ? M[OW2 + H * j + i] : 0.0f);
+  }
+  for (int p = threadIdx.x; p < 192; p += blockDim.x) {
+    I.w1[p] = bf(M[OW1 + p]);
+    I.w3[p] = bf(M[OW3 + p]);
+  }
+  for (int p = threadIdx.x; p < 64; p += blockDim.x) {
+    I.b1[p] = M[OB1 + p];
+    I.b2[p] = M[OB2 + p];
+  }
+  if (threadIdx.x < 3) I.b3[threadIdx.x] = M[OB3 + threadIdx.x];
+  if (threadIdx.x < 6) I.bounds[threadIdx.x] = bounds[6 * s + threadIdx.x];
+}
+
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+// One CTA per cluster chunk (one item): the sector's network in shared memory;
+// each warp takes 16 clusters at a time.  Fragment layout of m16n8k16 (lane =
+// 4 g + q): A rows g and g+8, columns 2q, 2q+1 and +8; B column g, rows 2q, 2q+1
+// and +8; accumulators rows g and g+8, columns 2q, 2q+1.
+__global__ void __launch_bounds__(128) k_correct_mlp(const __grid_constant__ Buffers b) {
+  __shared__ __align__(16) MlpInfer S;
+  const DevParams& P = b.par;
+  const Chunk ch = b.chunks[blockIdx.x];
+  const int sector = b.item_sector ? (int)b.item_sector[ch.item] : 0;
+  if (sector >= b.mlp_sectors) {
+    if (threadIdx.x == 0 && ch.end > ch.begin) atomicOr(b.err, TPC_DERR_BAD_INPUT);
+    return;
+  }
+  {
+    const int4* src = reinterpret_cast<const int4*>(reinterpret_cast<const MlpInfer*>(b.mlp) + sector);
+    int4* dst = reinterpret_cast<int4*>(&S);
+    for (int p = threadIdx.x; p < (int)(sizeof(MlpInfer) / 16); p += blockDim.x) dst[p] = src[p];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int g = lane >> 2, q = lane & 3;
+  const float sx = 2.0f / (S.bounds[1] - S.bounds[0]), sv = 2.0f / (S.bounds[3] - S.bounds[2]);
+  const float sz = 2.0f / (S.bounds[5] - S.bounds[4]);
+  for (int base = ch.begin + warp * 16; base < ch.end; base += 64) {
+    // normalised inputs of the two rows this lane touches
+    float in[2][3];
+    int idx[2];
+    bool ok[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = base + g + 8 * h;
+      idx[h] = i;
+      ok[h] = i < ch.end;
+      float x = 0.f, y = 0.f, z = 0.f;
+      if (ok[h]) {
+        const int r = b.row[i];
+        ok[h] = r >= 0 && r < P.n_rows;
+        if (ok[h]) {
+          x = P.x[r];
+          y = b.y[i];
+          z = b.z[i];
+        }
+      }
+      const float v = y / (x > 0.f ? x * P.tan_half : 1.0f);
+      in[h][0] = bf((x - S.bounds[0]) * sx - 1.0f);
+      in[h][1] = bf((v - S.bounds[2]) * sv - 1.0f);
+      in[h][2] = bf((z - S.bounds[4]) * sz - 1.0f);
+    }
+    // layer 1 straight into the A fragments of the four k-steps
+    uint32_t A[4][4];
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) {
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int c0 = 16 * ks + 2 * q + 8 * half;
+        float h1[2][2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            const int c = c0 + e;
+            const float z1 = S.b1[c] + S.w1[3 * c] * in[h][0] + S.w1[3 * c + 1] * in[h][1] + S.w1[3 * c + 2] * in[h][2];
+            h1[h][e] = silu(z1);
+          }
+        A[ks][2 * half] = pack_bf2(h1[0][0], h1[0][1]);      // row g
+        A[ks][2 * half + 1] = pack_bf2(h1[1][0], h1[1][1]);  // row g + 8
+      }
+    }
+    // layer 2 on the tensor cores, layer 3 on the fly
+    float o[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+      const __nv_bfloat16* wrow = S.w2 + (8 * nt + g) * W2S;
+#pragma unroll
+      for (int ks = 0; ks < 4; ++ks) {
+        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow + 16 * ks + 2 * q);
+        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + 16 * ks + 2 * q + 8);
+        mma_bf16(d, A[ks], b0, b1);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int col = 8 * nt + 2 * q + (e & 1);
+        const int h = e >> 1;
+        const float a2 = bf(silu(d[e] + S.b2[col]));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) o[h][c] += S.w3[64 * c + col] * a2;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h)
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        o[h][c] += __shfl_xor_sync(0xffffffffu, o[h][c], 1);
+        o[h][c] += __shfl_xor_sync(0xffffffffu, o[h][c], 2);
+      }
+    if (q == 0) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int i = idx[h];
+        if (i >= ch.end) continue;
+        if (ok[h]) {
+          b.cy[i] = b.y[i] + OUT_SCALE * (o[h][1] + S.b3[1]);
+          b.cz[i] = b.z[i] + OUT_SCALE * (o[h][2] + S.b3[2]);
+        } else {
+          b.cy[i] = b.y[i];
+          b.cz[i] = b.z[i];
+        }
+      }
+    }
+  }
+}
+
 cudaError_t tpc_launch_mlp_correction(const Buffers& b, cudaStream_t s) {
-  (void)b;
-  (void)s;
-  return cudaErrorNotSupported;
+  k_correct_mlp<<<b.n_chunks, 128, 0, s>>>(b);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------------------- host side
+size_t tpc_mlp_infer_bytes() { return sizeof(MlpInfer); }
+int tpc_mlp_nparams() { return NP; }
+int tpc_mlp_stride() { return NPP; }
+
+cudaError_t tpc_mlp_init(float* master, float* m, float* v, int S, uint64_t seed, cudaStream_t s) {
+  k_mlp_init<<<S, 256, 0, s>>>(master, m, v, seed);
+  return cudaGetLastError();
+}
+
+cudaError_t tpc_mlp_step(float* master, float* m, float* v, float* partial, float* loss, const float2* grid, int nx,
+                         int ny, int nz, int S, int batch, uint64_t seed, uint64_t step, float lr_t, float c1, float c2,
+                         cudaStream_t s) {
+  static bool attr = false;
+  const size_t smem = sizeof(float) * (NPP + 2 * H * TB + 4 * WS);
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  MlpTrain a{master, partial, loss, grid, nx, ny, nz, seed, step, batch};
+  const int nblk = batch / TB;
+  k_mlp_grad<<<dim3(nblk, S), TB, smem, s>>>(a);
+  MlpAdam ad{master, m, v, partial, nblk, lr_t, 0.9f, 0.999f, c1, c2, 1e-8f};
+  k_mlp_adam<<<S, 256, 0, s>>>(ad);
+  return cudaGetLastError();
+}
+
+cudaError_t tpc_mlp_grad_only(const float* master, float* partial, float* loss, const float2* grid, int nx, int ny,
+                              int nz, int S, int batch, uint64_t seed, uint64_t step, cudaStream_t s) {
+  const size_t smem = sizeof(float) * (NPP + 2 * H * TB + 4 * WS);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  MlpTrain a{master, partial, loss, grid, nx, ny, nz, seed, step, batch};
+  k_mlp_grad<<<dim3(batch / TB, S), TB, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t tpc_mlp_eval(const float* master, const float2* grid, int nx, int ny, int nz, int S, int nblk,
+                         uint64_t seed, float* out, cudaStream_t s) {
+  MlpEval a{master, grid, nx, ny, nz, seed, out};
+  k_mlp_eval<<<dim3(nblk, S), TB, 0, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t tpc_mlp_prepare(const float* master, const float* bounds, void* infer, int S, cudaStream_t s) {
+  k_mlp_prepare<<<S, 256, 0, s>>>(master, bounds, reinterpret_cast<MlpInfer*>(infer));
+  return cudaGetLastError();
 }

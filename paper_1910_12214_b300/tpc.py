@@ -74,6 +74,14 @@ _sig = {
     "tpc_autotune": ([_P, C.c_int, C.POINTER(tpc_tuning), C.POINTER(C.c_float)], C.c_int),
     "tpc_set_grid_correction": ([_P, _P, _P, C.c_uint32, C.c_int, C.c_int, C.c_int], C.c_int),
     "tpc_set_correction": ([_P, C.c_int], C.c_int),
+    "tpc_surrogate_train": ([_P, C.c_uint64, C.c_uint64, C.c_int, C.c_float, C.POINTER(C.c_float),
+                             C.POINTER(C.c_float)], C.c_int),
+    "tpc_surrogate_eval": ([_P, C.c_uint64, C.POINTER(C.c_float), C.POINTER(C.c_float)], C.c_int),
+    "tpc_surrogate_params": ([_P, C.c_int, _P, C.c_int], C.c_int),
+    "tpc_surrogate_set_params": ([_P, C.c_int, _P, C.c_int], C.c_int),
+    "tpc_surrogate_grad": ([_P, C.c_int, C.c_uint64, C.c_uint64, C.c_int, _P, C.c_int, C.POINTER(C.c_float)], C.c_int),
+    "tpc_surrogate_save": ([_P, C.c_char_p], C.c_int),
+    "tpc_surrogate_load": ([_P, C.c_char_p], C.c_int),
     "tpc_bin_sector_noalloc": ([_P, _P, _P, C.c_uint32, C.c_int, _P, _P, _P, _P], C.c_int),
     "tpc_destroy": ([_P], None),
     "tpc_last_error": ([_P], C.c_char_p),
@@ -255,6 +263,39 @@ class Tracker:
         """Corrected (y, z) of the last tpc_track() (debug stage 11)."""
         d = self.debug_dump(11).view(np.float32).reshape(-1, 2)
         return d[:, 0].copy(), d[:, 1].copy()
+
+    MLP_NP = 4611
+
+    def surrogate_train(self, n_samples, seed=1, max_steps=0, lr=0.0):
+        mx, rms = C.c_float(), C.c_float()
+        self._check(_lib.tpc_surrogate_train(self._h, n_samples, seed, max_steps, lr, C.byref(mx), C.byref(rms)))
+        return float(mx.value), float(rms.value)
+
+    def surrogate_eval(self, n_points=65536):
+        mx, rms = C.c_float(), C.c_float()
+        self._check(_lib.tpc_surrogate_eval(self._h, n_points, C.byref(mx), C.byref(rms)))
+        return float(mx.value), float(rms.value)
+
+    def surrogate_params(self, sector=0):
+        out = np.zeros(self.MLP_NP, np.float32)
+        self._check(_lib.tpc_surrogate_params(self._h, sector, _ptr(out), out.shape[0]))
+        return out
+
+    def surrogate_set_params(self, sector, params):
+        p = np.ascontiguousarray(params, np.float32)
+        self._check(_lib.tpc_surrogate_set_params(self._h, sector, _ptr(p), p.shape[0]))
+
+    def surrogate_grad(self, sector, seed, step, batch):
+        g = np.zeros(self.MLP_NP, np.float32)
+        loss = C.c_float()
+        self._check(_lib.tpc_surrogate_grad(self._h, sector, seed, step, batch, _ptr(g), g.shape[0], C.byref(loss)))
+        return g, float(loss.value)
+
+    def surrogate_save(self, path):
+        self._check(_lib.tpc_surrogate_save(self._h, str(path).encode()))
+
+    def surrogate_load(self, path):
+        self._check(_lib.tpc_surrogate_load(self._h, str(path).encode()))
 
     def close(self):
         if getattr(self, "_h", None):
