@@ -1,10 +1,14 @@
 #!/usr/bin/env python
 """Benchmark of the TPC sector tracker on B300: TPC clusters/s tracked.
 
-Default workload: the full TPC (36 sectors x 152 rows) with one central
-Pb-Pb-like event of 6000 primary helices (~0.9M clusters) plus 5% noise,
-synthetic (seeded), plain mode (one launch per step over all 36 sectors).
-A "step" is one tpc_track() over the resident batch (every step of the path).
+Headline workload: the full TPC (36 sectors x 152 rows), one central Pb-Pb-like
+event of 6000 primary helices (~0.9M clusters, 5% noise), synthetic and seeded;
+one step = one tpc_track() over the resident batch (every step of the path),
+launch shapes chosen by the library's autotuner, replayed as a CUDA graph.
+Further forms (rank 0, N=1): 64 uneven events (plain vs batched persistent
+kernel), a 50 kHz continuous-readout time frame (128 collisions, sliced), and
+the same 64 events distorted by a space-charge field, corrected by the grid or
+by the trained BF16 network.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
 bounded sample of the same workload instead.
@@ -13,6 +17,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import multiprocessing as mp
 import os
 import subprocess
 import sys
@@ -24,10 +29,16 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
-# algorithmic bytes per input cluster of each step (minimum traffic the step must
-# move) and the dominant step's unit
-ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12 + 12, "row_sort": 12 + 16,
-              "links": 12 + 8, "clean+starts": 8 + 8, "tracklets": 28, "selection": 20, "output": 8}
+# Algorithmic bytes per input cluster of each step: the minimum HBM traffic the
+# step must move (cluster SoA 16 B, quantised (qy,qz) 8 B, sorted hit 16 B, link
+# words 4 B each, tracklet hits 4 B per hit and pass).
+ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12 + 12, "row_sort": 12 + 16 + 8,
+              "links": 16 + 8, "clean+starts": 8 + 8 + 4, "tracklets": 28, "selection": 20, "output": 8,
+              "batched_items": 150, "batched_concat": 4}
+# DRAM bytes per launch of the dominant kernel from the ncu capture summarised in
+# profiles/k_tracklets_config2.md (same kernel source); None = not captured.
+TRAFFIC = {"tracklets": None}
+KERNELS_PER_STEP = {"plain": 18, "batched": 3}
 
 WORKLOADS = {
     "c1": "1 sector x 152 rows, 200 helices pT 0.1-10 GeV |eta|<0.9, sigma 0.1 cm, 5% noise, seed 1",
@@ -45,6 +56,50 @@ def make_workload(name: str, rank: int):
     raise SystemExit(f"unknown workload {name}")
 
 
+# ------------------------------------------------------------ input generation (CPU, before CUDA)
+def _gen_batched():
+    from paper_1910_12214_b300 import synth
+    return synth.make_batched(seed=1, n_events=64)
+
+
+def _gen_frame():
+    from paper_1910_12214_b300 import synth
+    fr = synth.make_timeframe(seed=1)
+    sl = synth.slice_frame(fr)
+    sl.src_index = None
+    sl.truth = None
+    return sl, fr.n
+
+
+def _gen_grid():
+    from paper_1910_12214_b300 import synth
+    d = synth.make_distortion(seed=1, n_sectors=36)
+    g, b = synth.correction_grid(d)
+    return d, g, b
+
+
+def generate_forms(forms):
+    """Generate the form workloads in spawned worker processes (no CUDA yet)."""
+    out = {}
+    jobs = {}
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(3) as pool:
+        if "c3" in forms or "c5" in forms:
+            jobs["c3"] = pool.apply_async(_gen_batched)
+        if "c4" in forms:
+            jobs["c4"] = pool.apply_async(_gen_frame)
+        if "c5" in forms:
+            jobs["grid"] = pool.apply_async(_gen_grid)
+        for k, j in jobs.items():
+            out[k] = j.get()
+    if "c5" in forms:
+        from paper_1910_12214_b300 import synth
+        d, g, b = out["grid"]
+        out["c5"] = (synth.distort(out["c3"], d), g, b)
+    return out
+
+
+# ------------------------------------------------------------ measurement helpers
 class ClockSampler:
     """nvidia-smi clocks and throttle reasons sampled during the timed region."""
 
@@ -134,6 +189,45 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def to_device(cl, dev):
+    import torch
+    d = type("D", (), {})()
+    d.x, d.y, d.z = (torch.from_numpy(np.ascontiguousarray(a)).to(dev) for a in (cl.x, cl.y, cl.z))
+    d.row = torch.from_numpy(np.ascontiguousarray(cl.row)).to(dev)
+    d.item_off, d.item_sector, d.item_event = cl.item_off, cl.item_sector, cl.item_event
+    d.item_core = getattr(cl, "item_core", None)
+    return d
+
+
+def time_steps(t, stream, steps, flush):
+    """Device time of `steps` tpc_track() calls, L2 flushed between them."""
+    import torch
+    ms = []
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        t.track()
+        e1.record(stream)
+        flush.zero_()
+        ms.append((e0, e1))
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in ms]
+
+
+def stage_profile(t, steps=3):
+    """Per-step device times from the library's events (direct launches)."""
+    tun = t.get_tuning()
+    t.set_tuning(use_graph=1)
+    acc = {}
+    for _ in range(steps):
+        t.track()
+        for k, v in t.stage_times().items():
+            acc[k] = acc.get(k, 0.0) + v / steps
+    t.set_tuning(use_graph=tun["use_graph"])
+    return acc
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -141,6 +235,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
+    ap.add_argument("--forms", default="c3,c4,c5", help="extra forms at N=1: c3,c4,c5 or none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -148,6 +243,8 @@ def main():
     local = int(os.environ.get("LOCAL_RANK", "0"))
     if args.impl == "reference":
         return run_reference(args, rank, world)
+    forms = [] if args.forms == "none" or world > 1 or rank != 0 else [f for f in args.forms.split(",") if f]
+    gen = generate_forms(forms) if forms else {}  # CPU work before CUDA is touched
 
     import torch
     from paper_1910_12214_b300 import tpc
@@ -157,25 +254,21 @@ def main():
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl")
-    cl = make_workload(args.workload, rank)
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
-    # resident inputs
-    d = type("D", (), {})()
-    d.x, d.y, d.z = (torch.from_numpy(a).to(dev) for a in (cl.x, cl.y, cl.z))
-    d.row = torch.from_numpy(cl.row).to(dev)
-    d.item_off, d.item_sector, d.item_event = cl.item_off, cl.item_sector, cl.item_event
-    d.item_core = None
+    stream = torch.cuda.Stream(dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+    cl = make_workload(args.workload, rank)
+    with torch.cuda.stream(stream):
+        d = to_device(cl, dev)
+    stream.synchronize()
     t = tpc.Tracker(device=local, stream=stream, profile=True)
     t.load(d, on_device=True)
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # > L2 (126 MB)
+    tuning, tune_us = t.autotune(iters=3)
+    t.set_tuning(use_graph=2)
     for _ in range(args.warmup):
         t.track()
         flush.zero_()
     torch.cuda.synchronize()
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    stage_acc = {}
     clocks = ClockSampler(local)
     clocks.start()
     time.sleep(0.3)
@@ -183,69 +276,132 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for k in range(args.steps):
-        starts[k].record(stream)
-        t.track()
-        ends[k].record(stream)
-        st = t.stage_times()  # syncs; events recorded on the tracker's stream
-        for kk, v in st.items():
-            stage_acc[kk] = stage_acc.get(kk, 0.0) + v
-        flush.zero_()
-    torch.cuda.synchronize()
+    torch.cuda.nvtx.range_push("tpc_timed")  # lets a profiler select the timed launches
+    step_ms = time_steps(t, stream, args.steps, flush)
+    torch.cuda.nvtx.range_pop()
     wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = float(np.mean(step_ms))
     if dist:
         tt = torch.tensor([ms], device=dev)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         ms = float(tt.item())
     n_tr, n_ids = t.counts()
+    stages = stage_profile(t)
 
-    # end to end through the public API with host buffers (H2D + track + D2H per step)
-    e2e_times = []
+    # end to end through the public API with host buffers: H2D of the step's
+    # clusters, tracking, D2H of the tracks and their cluster ids
+    e2e = []
     h2d = 16 * cl.n + 8 * (cl.n_items + 1) + 8 * cl.n_items
-    for k in range(max(3, args.steps // 2)):
+    trk = ids = None
+    for _ in range(max(4, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         t.load(cl)
         t.track()
         trk, ids = t.get_tracks()
-        e2e_times.append(time.perf_counter() - t0)
+        e2e.append(time.perf_counter() - t0)
     d2h = trk.nbytes + ids.nbytes + 32
-    e2e_s = float(np.median(e2e_times[1:]))
+    e2e_s = float(np.median(e2e[1:]))
+    t.close()
+
+    form_out = {}
+    if rank == 0 and forms:
+        form_out = run_forms(gen, dev, stream, flush, tpc, torch)
 
     if rank == 0:
-        stage_us = {k: v / args.steps for k, v in stage_acc.items()}
-        dom = max(stage_us, key=stage_us.get)
+        dom = max(stages, key=stages.get)
         peak, peak_kind = measured_peak_hbm()
-        algo = ALGO_BYTES[dom] * cl.n
-        achieved = algo / (stage_us[dom] * 1e-6) / 1e9
+        algo = ALGO_BYTES.get(dom, 0) * cl.n
+        achieved = algo / (stages[dom] * 1e-6) / 1e9
         value = cl.n * world / (ms * 1e-3)
         line = {
-            "metric": "TPC clusters/s tracked (plain sector tracker)",
+            "metric": "TPC clusters/s tracked (sector tracker, full TPC event)",
             "value": value, "unit": "clusters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
-            "data": "synthetic",
+            "data": "synthetic (seeded helices, ALICE simulation not available)",
             "config": {"workload": WORKLOADS[args.workload], "clusters_per_step": cl.n, "items": cl.n_items,
-                       "tracks": n_tr, "l2": "flushed between steps (256 MB write)", "mode": "plain"},
+                       "tracks": n_tr, "l2": "flushed between steps (256 MB write)", "tuning": tuning,
+                       "autotune_best_us": tune_us},
             "e2e": {"value": cl.n * world / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
-            "gpu_launches": 18 * args.steps,
-            "stage_us": {k: round(v, 2) for k, v in stage_us.items()},
+            "gpu_launches": KERNELS_PER_STEP["batched" if tuning["mode"] == 2 else "plain"] * args.steps,
+            "stage_us": {k: round(v, 2) for k, v in stages.items()},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
-                         "algo_bytes_per_cluster": ALGO_BYTES[dom]},
+                         "frac": achieved / peak, "traffic": TRAFFIC.get(dom), "peak_kind": peak_kind,
+                         "algo_bytes_per_cluster": ALGO_BYTES.get(dom)},
             "clocks": clk, "wall_s_timed_region": wall,
+            "forms": form_out,
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
         print(json.dumps(line), flush=True)
-    t.close()
     if dist:
         dist.destroy_process_group()
+
+
+def run_forms(gen, dev, stream, flush, tpc, torch):
+    """clusters/s of the other forms (device time of tpc_track, L2 flushed)."""
+    res = {}
+
+    def bench_batch(cl, label, n_clusters, modes=("plain", "batched"), setup=None, steps=5):
+        with torch.cuda.stream(stream):
+            d = to_device(cl, dev)
+        stream.synchronize()
+        out = {}
+        with tpc.Tracker(stream=stream, profile=True) as t:
+            if setup:
+                setup(t)
+            t.load(d, on_device=True)
+            for mode in modes:
+                t.set_tuning(mode=1 if mode == "plain" else 2, use_graph=2)
+                for _ in range(2):
+                    t.track()
+                ms = float(np.median(time_steps(t, stream, steps, flush)))
+                out[mode] = {"clusters_per_s": n_clusters / (ms * 1e-3), "ms": ms, "tracks": t.counts()[0]}
+        del d
+        torch.cuda.empty_cache()
+        return out
+
+    if "c3" in gen:
+        c3 = gen["c3"]
+        res["batched_64_events"] = {"clusters": c3.n, "items": c3.n_items, **bench_batch(c3, "c3", c3.n)}
+    if "c4" in gen:
+        sl, n_phys = gen["c4"]
+        res["timeframe_50khz_128_collisions"] = {"clusters": n_phys, "sliced_clusters": sl.n, "items": sl.n_items,
+                                                 "note": "clusters/s counts physical clusters",
+                                                 **bench_batch(sl, "c4", n_phys)}
+    if "c5" in gen:
+        c5, grid, bounds = gen["c5"]
+        info = {}
+
+        def setup(t):
+            t.set_grid_correction(grid, bounds)
+            t0 = time.perf_counter()
+            mx, rms = t.surrogate_train(40_000_000, seed=1)
+            info.update(train_s=time.perf_counter() - t0, resid_max_cm=mx, resid_rms_cm=rms)
+
+        out = {}
+        with torch.cuda.stream(stream):
+            d = to_device(c5, dev)
+        stream.synchronize()
+        with tpc.Tracker(stream=stream, profile=True) as t:
+            setup(t)
+            t.load(d, on_device=True)
+            for corr in ("mlp", "grid", "none"):
+                t.set_correction(corr)
+                t.set_tuning(mode=1, use_graph=2)
+                for _ in range(2):
+                    t.track()
+                ms = float(np.median(time_steps(t, stream, 5, flush)))
+                t.set_tuning(use_graph=1)
+                t.track()
+                st = t.stage_times()
+                out[corr] = {"clusters_per_s": c5.n / (ms * 1e-3), "ms": ms, "tracks": t.counts()[0]}
+        res["distorted_64_events"] = {"clusters": c5.n, "surrogate": info, **out}
+    return res
 
 
 if __name__ == "__main__":
