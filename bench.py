@@ -38,7 +38,7 @@ ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12
 # DRAM bytes per launch of the dominant kernel from the ncu capture summarised in
 # profiles/k_tracklets_config2.md (same kernel source); None = not captured.
 TRAFFIC = {"tracklets": None}
-KERNELS_PER_STEP = {"plain": 18, "batched": 3}
+KERNELS_PER_STEP = {"plain": 19, "batched": 3}
 
 WORKLOADS = {
     "c1": "1 sector x 152 rows, 200 helices pT 0.1-10 GeV |eta|<0.9, sigma 0.1 cm, 5% noise, seed 1",

@@ -433,18 +433,28 @@ int row_of_pos(const orc_result* R, int item, int pos) {
 }
 
 // One tracklet from a start hit:
-//  (i)   initial state from the first three chain hits, Kalman fit along the chain
-//        (chain hits are accepted without a chi2 test);
+//  (i)   initial state from the first, middle and last chain hits, Kalman fit
+//        along the chain (chain hits are accepted without a chi2 test);
 //  (ii)  extension to outer rows: predict, take the best hit with chi2 <= 16,
 //        stop after 5 consecutive misses;
 //  (iii) a refit from the outermost hit towards the inner rows, with the
 //        outer direction and curvature as starting values and their variances
 //        inflated 100-fold, re-picking hits as in (ii).
+// Pieces of one track that start from different chain heads reach the same
+// outermost hit in (ii) and would refit the same hits in (iii): only the
+// tracklet with the smallest id among those sharing an outermost hit runs
+// (iii); the others are dropped.
 // The tracklet is the set of hits of (iii); its parameters are those at the
 // innermost hit.  Guards end a pass: |sinphi| >= sin 70 deg, |y| > x tan(half
 // angle) (the track leaves the sector), an invalid propagation.  A non-finite or
 // non-positive covariance diagonal drops the tracklet.
-void build_tracklet(Ctx& c, int start, Tracklet& T) {
+struct Outward {
+  bool ok = false;
+  int out_hit = -1, out_row = 0;
+  double out_p[5] = {0, 0, 0, 0, 0}, out_var[3] = {0, 0, 0};
+};
+
+void outward(Ctx& c, int start, Tracklet& T, Outward& O) {
   orc_result* R = c.R;
   const int item = R->item_of_pos[start];
   T.item = item;
@@ -483,7 +493,7 @@ void build_tracklet(Ctx& c, int start, Tracklet& T) {
     x = X(r);
     if (!(std::fabs(p[2]) < SIN_MAX) || std::fabs(p[0]) > x * c.tanh_) { alive = false; break; }
     update(p, C, c.hy(chain[i]), c.hz(chain[i]), c.vy, c.vz);
-    if (!cov_ok(C)) { T.valid = false; return; }
+    if (!cov_ok(C)) { T.valid = false; O.ok = false; return; }
     out_hit = chain[i];
     out_row = r;
     std::memcpy(out_p, p, sizeof(p));
@@ -502,7 +512,7 @@ void build_tracklet(Ctx& c, int start, Tracklet& T) {
       const int h = pick(c, item, r, p, C, &x2v);
       if (h < 0) { ++misses; continue; }
       update(p, C, c.hy(h), c.hz(h), c.vy, c.vz);
-      if (!cov_ok(C)) { T.valid = false; return; }
+      if (!cov_ok(C)) { T.valid = false; O.ok = false; return; }
       misses = 0;
       out_hit = h;
       out_row = r;
@@ -512,6 +522,21 @@ void build_tracklet(Ctx& c, int start, Tracklet& T) {
       out_var[2] = C[4][4];
     }
   }
+  O.ok = true;
+  O.out_hit = out_hit;
+  O.out_row = out_row;
+  std::memcpy(O.out_p, out_p, sizeof(out_p));
+  std::memcpy(O.out_var, out_var, sizeof(out_var));
+}
+
+void inward(Ctx& c, Tracklet& T, const Outward& O) {
+  orc_result* R = c.R;
+  const int item = T.item;
+  auto X = [&](int r) { return R->row_x[r]; };
+  const int out_hit = O.out_hit, out_row = O.out_row;
+  const double* out_p = O.out_p;
+  const double* out_var = O.out_var;
+  double C[5][5];
   // (iii) refit inwards from the outermost hit: its measured y, z; the outward
   // direction and curvature with their variances inflated 100-fold (at most the
   // initial ones), so that the refit is well conditioned and the outward fit
@@ -521,7 +546,7 @@ void build_tracklet(Ctx& c, int start, Tracklet& T) {
   C[2][2] = std::min(C0_DIAG_ANGLE, INFLATE * out_var[0]);
   C[3][3] = std::min(C0_DIAG_ANGLE, INFLATE * out_var[1]);
   C[4][4] = std::min(C0_DIAG_QPT, INFLATE * out_var[2]);
-  x = X(out_row);
+  double x = X(out_row);
   T.hits.assign(1, out_hit);
   T.chi2 = 0.0;
   double in_p[5], in_C[5][5], in_x = x;
@@ -623,12 +648,26 @@ extern "C" int orc_run(const orc_config* cfg, const float* x, const float* y, co
   Ctx c{R, std::tan(cfg->half_angle_deg * M_PI / 180.0), cfg->sigma_y * cfg->sigma_y, cfg->sigma_z * cfg->sigma_z,
         cfg->bz_tesla};
   R->tracklets.resize(R->starts.size());
+  std::vector<Outward> O(R->starts.size());
   std::vector<int> local(n_items, 0);
   for (size_t t = 0; t < R->starts.size(); ++t) {
     Tracklet& T = R->tracklets[t];
-    build_tracklet(c, R->starts[t], T);
     T.item = R->item_of_pos[R->starts[t]];
     T.local_id = local[T.item]++;
+    outward(c, R->starts[t], T, O[t]);
+  }
+  // one inward refit per outermost hit: the smallest tracklet id reaching it
+  std::vector<int> first_at(R->qy.size(), -1);
+  for (size_t t = 0; t < O.size(); ++t)
+    if (O[t].ok && first_at[O[t].out_hit] < 0) first_at[O[t].out_hit] = (int)t;
+  for (size_t t = 0; t < O.size(); ++t) {
+    Tracklet& T = R->tracklets[t];
+    if (O[t].ok && first_at[O[t].out_hit] == (int)t) {
+      inward(c, T, O[t]);
+    } else {
+      T.valid = false;
+      T.n = 0;
+    }
   }
   selection(R, item_core);
   *out = R;

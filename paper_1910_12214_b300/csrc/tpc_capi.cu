@@ -174,6 +174,8 @@ tpc_status reserve(tpc_ctx* c, long long N, long long I, long long n_chunks) {
   b.start_ex = (int*)A(4 * (N + 1));
   b.starts = (int*)A(4 * Tcap);
   b.tl = (TrackletRec*)A(sizeof(TrackletRec) * Tcap);
+  b.tlu = (TrackletUp*)A(sizeof(TrackletUp) * Tcap);
+  b.out_owner = (int*)A(4 * N);
   b.tl_hits = (int*)A(4 * (size_t)Tcap * NR);
   b.hit_key = (unsigned long long*)A(8 * N);
   b.tl_cnt = (unsigned long long*)A(8 * Tcap);
@@ -581,7 +583,7 @@ extern "C" tpc_status tpc_debug_dump(tpc_ctx* c, int stage, int32_t* buf, uint64
       break;
     }
     case 8:
-    case 9: {
+    case 9: {  // (tracklets that lost their outermost hit to a smaller id read n = 0)
       std::vector<TrackletRec> tl(Tmax);
       if (Tmax && (e = cudaMemcpy(tl.data(), b.tl, sizeof(TrackletRec) * Tmax, cudaMemcpyDeviceToHost)) != cudaSuccess)
         return cuda_fail(c, e, "dump");

@@ -36,6 +36,16 @@ struct TrackletRec {
   int pad;
 };
 
+// Result of the outward passes (i)+(ii) of a tracklet, input of the inward
+// refit (iii).
+struct TrackletUp {
+  int out_hit;   // outermost hit (sorted position), -1 = dropped
+  int out_row;
+  float snp, tgl, qpt;
+  float v2, v3, v4;  // variances of sinphi, tanlambda, q/pT at the outermost hit
+  int z_base, item, local, pad;
+};
+
 struct DevParams {
   int n_rows;
   float tan_half;   // tan(sector half angle)
@@ -89,6 +99,8 @@ struct Buffers {
   // tracklets
   int T_cap;
   TrackletRec* tl;
+  TrackletUp* tlu;                // [T_cap]
+  int* out_owner;                 // smallest tracklet reaching each hit as its outermost [N]
   int* tl_hits;   // [T_cap * NR]
   unsigned long long* hit_key;  // [N]
   unsigned long long* tl_cnt;   // packed (1<<32 | owned) per tracklet

@@ -10,8 +10,9 @@
 //   k_links          per hit of an inner row: best (up, down) pair (integer metric)
 //   k_clean_start    mutual-link cleaning and start-hit flags
 //   k_scan_*         device-wide exclusive scans (reduce-then-scan, fixed grid)
-//   k_tracklets      FP32 Kalman tracklet per start hit (chain fit, outward
-//                    extension, inward refit with hit re-picking)
+//   k_tracklets_up   FP32 Kalman tracklet per start hit: chain fit and outward
+//                    extension; each tracklet claims its outermost hit
+//   k_tracklets_down inward refit with hit re-picking, one per outermost hit
 //   k_select_max/own shared-cluster resolution by 64-bit atomicMax keys
 //   k_output         track and cluster-id compaction
 //
@@ -893,11 +894,11 @@ __device__ __forceinline__ int pick_hit(const Buffers& b, const Grp<G>& g, int i
 // step.  A non-finite or non-positive covariance diagonal drops the tracklet.
 // z is carried relative to the start hit (z_base) so that FP32 keeps its
 // precision for time-frame z' of thousands of cm.
-// One tracklet from the start hit at sorted position `start`, built by a group
-// of G lanes: the record goes to b.tl[tl] and the hit list to
-// b.tl_hits[tl * n_rows ...]; `local` is the tracklet's item-local id.
+// Outward passes (i) and (ii) of the tracklet with start hit `start`, by a group
+// of G lanes: the result goes to b.tlu[tl] and the tracklet claims its outermost
+// hit (smallest tracklet index wins); `local` is the item-local id.
 template <int G>
-__device__ __forceinline__ void tracklet_build(const Buffers& b, const Grp<G>& g, int start, int tl, int local) {
+__device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, int start, int tl, int local) {
   const DevParams& P = b.par;
   const int NR = P.n_rows;
   const float Q = 1.0f / TPC_QSCALE;
@@ -985,6 +986,43 @@ __device__ __forceinline__ void tracklet_build(const Buffers& b, const Grp<G>& g
       ov4 = C[ix(4, 4)];
     }
   }
+  if (g.gl == 0) {
+    TrackletUp u;
+    u.out_hit = dead ? -1 : out_hit;
+    u.out_row = out_row;
+    u.snp = out_p[2];
+    u.tgl = out_p[3];
+    u.qpt = out_p[4];
+    u.v2 = ov2;
+    u.v3 = ov3;
+    u.v4 = ov4;
+    u.z_base = z_base;
+    u.item = item;
+    u.local = local;
+    u.pad = 0;
+    b.tlu[tl] = u;
+    if (!dead) atomicMin(&b.out_owner[out_hit], tl);
+  }
+  g.sync();
+}
+
+// Inward refit (iii) of tracklet tl by a group of G lanes, only if it is the
+// smallest tracklet that reached its outermost hit (the others are dropped):
+// the record goes to b.tl[tl] and the hit list to b.tl_hits[tl * n_rows ...].
+template <int G>
+__device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g, int tl) {
+  const DevParams& P = b.par;
+  const int NR = P.n_rows;
+  const float Q = 1.0f / TPC_QSCALE;
+  const TrackletUp u = b.tlu[tl];
+  const int item = u.item, local = u.local, z_base = u.z_base;
+  const int out_hit = u.out_hit, out_row = u.out_row;
+  bool dead = out_hit < 0 || b.out_owner[out_hit] != tl;
+  int* hl = b.tl_hits + (size_t)tl * NR;
+  const float out_p[5] = {0.f, 0.f, u.snp, u.tgl, u.qpt};
+  const float ov2 = u.v2, ov3 = u.v3, ov4 = u.v4;
+  float C[15];
+  float x = P.x[out_row];
   int n = 0;
   float chi2sum = 0.f, in_x = x;
   float in_p[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, in_C[15];
@@ -1054,7 +1092,7 @@ __device__ __forceinline__ void tracklet_build(const Buffers& b, const Grp<G>& g
 }
 
 template <int G>
-__global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Buffers b) {
+__global__ void __launch_bounds__(128) k_tracklets_up(const __grid_constant__ Buffers b) {
   const Grp<G> g;
   const int T = b.start_ex[b.N];
   const int NR = b.par.n_rows;
@@ -1063,18 +1101,37 @@ __global__ void __launch_bounds__(128) k_tracklets(const __grid_constant__ Buffe
   for (int t = grp; t < T; t += ngrp) {
     const int start = b.starts[t];
     const int item = b.s_hit[start].w / NR;
-    tracklet_build<G>(b, g, start, t, t - b.start_ex[b.item_off[item]]);
+    tracklet_up<G>(b, g, start, t, t - b.start_ex[b.item_off[item]]);
   }
 }
 
+template <int G>
+__global__ void __launch_bounds__(128) k_tracklets_down(const __grid_constant__ Buffers b) {
+  const Grp<G> g;
+  const int T = b.start_ex[b.N];
+  const int grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int ngrp = (gridDim.x * blockDim.x) / G;
+  for (int t = grp; t < T; t += ngrp) tracklet_down<G>(b, g, t);
+}
+
 cudaError_t tpc_launch_tracklets(const Buffers& b, int group, int grid, int block, cudaStream_t s) {
+  cudaMemsetAsync(b.out_owner, 0x7F, sizeof(int) * (size_t)b.N, s);
   switch (group) {
-    case 1: k_tracklets<1><<<grid, block, 0, s>>>(b); break;
-    case 2: k_tracklets<2><<<grid, block, 0, s>>>(b); break;
-    case 4: k_tracklets<4><<<grid, block, 0, s>>>(b); break;
-    case 8: k_tracklets<8><<<grid, block, 0, s>>>(b); break;
-    case 16: k_tracklets<16><<<grid, block, 0, s>>>(b); break;
-    default: k_tracklets<32><<<grid, block, 0, s>>>(b); break;
+#define TPC_TL(GG)                                        \
+  case GG:                                                \
+    k_tracklets_up<GG><<<grid, block, 0, s>>>(b);         \
+    k_tracklets_down<GG><<<grid, block, 0, s>>>(b);       \
+    break;
+    TPC_TL(1)
+    TPC_TL(2)
+    TPC_TL(4)
+    TPC_TL(8)
+    TPC_TL(16)
+    default:
+      k_tracklets_up<32><<<grid, block, 0, s>>>(b);
+      k_tracklets_down<32><<<grid, block, 0, s>>>(b);
+      break;
+#undef TPC_TL
   }
   return cudaGetLastError();
 }
@@ -1309,6 +1366,7 @@ __global__ void __launch_bounds__(BT) k_batched(const __grid_constant__ Buffers 
     __syncthreads();
     for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
       b.hit_key[i] = 0ull;
+      b.out_owner[i] = 0x7F7F7F7F;
       const float xv = b.x[i], yv = b.y[i], zv = b.z[i];
       const int r = b.row[i];
       if (!(r >= 0 && r < NR && fabsf(xv) < INFINITY && fabsf(yv) <= 1e6f && fabsf(zv) <= 1e6f)) {
@@ -1410,8 +1468,11 @@ __global__ void __launch_bounds__(BT) k_batched(const __grid_constant__ Buffers 
     }
     __syncthreads();
     const int ntl = s_ntl;
-    // ---- S6: tracklets, a group of G lanes each
-    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_build<G>(b, g, b.starts[tlb + t], tlb + t, t);
+    // ---- S6: tracklets, a group of G lanes each: outward passes, then one
+    // inward refit per outermost hit
+    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_up<G>(b, g, b.starts[tlb + t], tlb + t, t);
+    __syncthreads();
+    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_down<G>(b, g, tlb + t);
     __syncthreads();
     // ---- S7: ownership
     for (int t = warp; t < ntl; t += nwarps) select_max_warp(b, tlb + t, lane);
