@@ -35,9 +35,10 @@ sys.path.insert(0, ROOT)
 ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12 + 12, "row_sort": 12 + 16 + 8,
               "links": 16 + 8, "clean+starts": 8 + 8 + 4, "tracklets": 28, "selection": 20, "output": 8,
               "batched_items": 150, "batched_concat": 4}
-# DRAM bytes per launch of the dominant kernel from the ncu capture summarised in
-# profiles/k_tracklets_config2.md (same kernel source); None = not captured.
-TRAFFIC = {"tracklets": None}
+# DRAM bytes (read + write) of the dominant step per tracking step, from the ncu
+# capture summarised in profiles/k_tracklets_config2.md: k_tracklets_up 21.41 MB +
+# k_tracklets_down 18.60 MB on the full-TPC workload; None = not captured.
+TRAFFIC = {("c2", "tracklets"): 40.0e6}
 KERNELS_PER_STEP = {"plain": 19, "batched": 3}
 
 WORKLOADS = {
@@ -330,7 +331,7 @@ def main():
             "gpu_launches": KERNELS_PER_STEP["batched" if tuning["mode"] == 2 else "plain"] * args.steps,
             "stage_us": {k: round(v, 2) for k, v in stages.items()},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": TRAFFIC.get(dom), "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": TRAFFIC.get((args.workload, dom)), "peak_kind": peak_kind,
                          "algo_bytes_per_cluster": ALGO_BYTES.get(dom)},
             "clocks": clk, "wall_s_timed_region": wall,
             "forms": form_out,
