@@ -616,6 +616,11 @@ namespace {
 // packed lower triangle index
 __device__ __forceinline__ constexpr int ix(int i, int j) { return i * (i + 1) / 2 + j; }
 
+// a*b + c*d with the rounding fixed (the first product fused, the second
+// rounded): left to itself the compiler may fuse either product, and its choice
+// can differ between the kernels this code is inlined into.
+__device__ __forceinline__ float fma2(float a, float b, float c, float d) { return __fmaf_rn(a, b, __fmul_rn(c, d)); }
+
 __device__ __forceinline__ float asin_over_u(float u) {
   if (fabsf(u) < 0.1f) {
     const float u2 = u * u;
@@ -665,7 +670,7 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float
   const float bq = dx * dT_dq;                         // F04
   const float c = tgl * dx * dg_dT * dT_ds;            // F12
   const float d = ell;                                 // F13
-  const float e = tgl * dx * (dg_dT * dT_dq + dg_dk * kB);  // F14
+  const float e = tgl * dx * fma2(dg_dT, dT_dq, dg_dk, kB);  // F14
   const float g = -kB * dx;                            // F24
   p[0] += dx * T;
   p[1] += tgl * ell;
@@ -706,7 +711,7 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float
 // Kalman update with H = [I2 0]; residuals (r0, r1); returns the chi2 increment.
 __device__ __forceinline__ float kf_update(const DevParams& P, float* p, float* C, float r0, float r1) {
   const float S00 = C[ix(0, 0)] + P.vy, S01 = C[ix(1, 0)], S11 = C[ix(1, 1)] + P.vz;
-  const float inv_det = 1.0f / (S00 * S11 - S01 * S01);
+  const float inv_det = 1.0f / fma2(S00, S11, -S01, S01);
   const float I00 = S11 * inv_det, I01 = -S01 * inv_det, I11 = S00 * inv_det;
   // columns 0 and 1 of the symmetric covariance
   float c0[5], c1[5], K0[5], K1[5];
@@ -717,16 +722,16 @@ __device__ __forceinline__ float kf_update(const DevParams& P, float* p, float* 
   for (int i = 1; i < 5; ++i) c1[i] = C[ix(i, 1)];
 #pragma unroll
   for (int i = 0; i < 5; ++i) {
-    K0[i] = c0[i] * I00 + c1[i] * I01;
-    K1[i] = c0[i] * I01 + c1[i] * I11;
+    K0[i] = fma2(c0[i], I00, c1[i], I01);
+    K1[i] = fma2(c0[i], I01, c1[i], I11);
   }
 #pragma unroll
-  for (int i = 0; i < 5; ++i) p[i] += K0[i] * r0 + K1[i] * r1;
+  for (int i = 0; i < 5; ++i) p[i] += fma2(K0[i], r0, K1[i], r1);
 #pragma unroll
   for (int i = 0; i < 5; ++i)
 #pragma unroll
-    for (int j = 0; j <= i; ++j) C[ix(i, j)] -= K0[i] * c0[j] + K1[i] * c1[j];
-  return r0 * (I00 * r0 + I01 * r1) + r1 * (I01 * r0 + I11 * r1);
+    for (int j = 0; j <= i; ++j) C[ix(i, j)] -= fma2(K0[i], c0[j], K1[i], c1[j]);
+  return fma2(r0, fma2(I00, r0, I01, r1), r1, fma2(I01, r0, I11, r1));
 }
 
 __device__ __forceinline__ bool cov_ok(const float* C) {
@@ -785,105 +790,223 @@ struct Grp {
   }
 };
 
-// Best hit of row r for the predicted state: the smallest chi2 <= 16, ties to
-// the smaller original id (a 64-bit key of the chi2 bit pattern and the id,
-// minimised over the group).  The search box (max(0.5 cm, 4 sigma) plus 2
-// quanta) contains every hit with chi2 <= 16, so the box never changes the
-// result.  Every lane of the group returns the same position.
-template <int G>
-__device__ __forceinline__ int pick_hit(const Buffers& b, const Grp<G>& g, int item, int r, const float* p,
-                                        const float* C, int z_base) {
-  const DevParams& P = b.par;
-  const RowInfo ri = b.rows[item * P.n_rows + r];
-  if (ri.n == 0) return -1;
-  const float S00 = C[ix(0, 0)] + P.vy, S01 = C[ix(1, 0)], S11 = C[ix(1, 1)] + P.vz;
-  const float inv_det = 1.0f / (S00 * S11 - S01 * S01);
-  const float wy = fmaxf(WIN_MIN, 4.0f * sqrtf(S00));
-  const float wz = fmaxf(WIN_MIN, 4.0f * sqrtf(S11));
+// Read-only loads: through the non-coherent path where the data was written by
+// an earlier launch (NC = true); plain loads in the persistent kernel, which
+// writes the same arrays earlier in the same launch, and for shared memory.
+template <bool NC, class T>
+__device__ __forceinline__ T ld(const T* p) {
+  if constexpr (NC) return __ldg(p);
+  else return *p;
+}
+
+template <bool NC>
+__device__ __forceinline__ RowInfo load_row(const RowInfo* p) {
+  if constexpr (NC) {
+    const int4 a = __ldg(reinterpret_cast<const int4*>(p));
+    const int4 c = __ldg(reinterpret_cast<const int4*>(p) + 1);
+    RowInfo r;
+    r.pos0 = a.x;
+    r.n = a.y;
+    r.ymin = a.z;
+    r.zmin = a.w;
+    r.shift = c.x;
+    r.ny = c.y;
+    r.nz = c.z;
+    r.bin0 = c.w;
+    return r;
+  } else {
+    return *p;
+  }
+}
+
+// Search window of the predicted state: the innovation covariance S = C_yz + V,
+// its inverse determinant and the half-widths max(0.5 cm, 4 sqrt(S_ii)).
+struct Win {
+  float S00, S01, S11, inv_det, wy, wz;
+};
+
+__device__ __forceinline__ Win make_win(const DevParams& P, const float* C) {
+  Win w;
+  w.S00 = C[ix(0, 0)] + P.vy;
+  w.S01 = C[ix(1, 0)];
+  w.S11 = C[ix(1, 1)] + P.vz;
+  w.inv_det = 1.0f / fma2(w.S00, w.S11, -w.S01, w.S01);
+  w.wy = fmaxf(WIN_MIN, 4.0f * sqrtf(w.S00));
+  w.wz = fmaxf(WIN_MIN, 4.0f * sqrtf(w.S11));
+  return w;
+}
+
+// Bins [iy0, iy1] x [iz0, iz1] of a row's grid covered by the box
+// yc +- wy, zc +- wz (cm, z relative to z_base) widened by 2 quanta; empty
+// (iy1 < iy0 or iz1 < iz0) if it misses the grid or the row has no hits.
+struct Box {
+  int iy0, iy1, iz0, iz1;
+};
+
+__device__ __forceinline__ Box row_box(const RowInfo& ri, float yc, float zc, float wy, float wz, int z_base) {
+  Box x;
   // 32-bit conversions (values clamped to +-1e9): 64-bit ones run on the FP64 pipe
   const float lim = 1.0e9f;
-  const long long ylo = (long long)(int)floorf(fmaxf(-lim, (p[0] - wy) * TPC_QSCALE)) - 2;
-  const long long yhi = (long long)(int)ceilf(fminf(lim, (p[0] + wy) * TPC_QSCALE)) + 2;
-  const long long zlo = (long long)(int)floorf(fmaxf(-lim, (p[1] - wz) * TPC_QSCALE)) - 2 + z_base;
-  const long long zhi = (long long)(int)ceilf(fminf(lim, (p[1] + wz) * TPC_QSCALE)) + 2 + z_base;
-  int iy0, iy1, iz0, iz1;
-  bin_range(ylo, yhi, ri.ymin, ri.shift, ri.ny, &iy0, &iy1);
-  bin_range(zlo, zhi, ri.zmin, ri.shift, ri.nz, &iz0, &iz1);
-  if (iy1 < iy0 || iz1 < iz0) return -1;
-  // the bins (iy, iz0..iz1) of one y-bin row are contiguous: one hit range each
-  const int nyb = iy1 - iy0 + 1;
-  const int span = iz1 - iz0 + 1;
+  const long long ylo = (long long)(int)floorf(fmaxf(-lim, (yc - wy) * TPC_QSCALE)) - 2;
+  const long long yhi = (long long)(int)ceilf(fminf(lim, (yc + wy) * TPC_QSCALE)) + 2;
+  const long long zlo = (long long)(int)floorf(fmaxf(-lim, (zc - wz) * TPC_QSCALE)) - 2 + z_base;
+  const long long zhi = (long long)(int)ceilf(fminf(lim, (zc + wz) * TPC_QSCALE)) + 2 + z_base;
+  bin_range(ylo, yhi, ri.ymin, ri.shift, ri.ny, &x.iy0, &x.iy1);
+  bin_range(zlo, zhi, ri.zmin, ri.shift, ri.nz, &x.iz0, &x.iz1);
+  if (ri.n == 0) x.iy1 = -1;
+  return x;
+}
+
+__device__ __forceinline__ bool box_empty(const Box& x) { return x.iy1 < x.iy0 || x.iz1 < x.iz0; }
+
+// chi2 of hit q against the predicted (y, z) = (p[0], p[1]); the selection key
+// (chi2 bit pattern, original id) if chi2 <= 16, else ~0.
+__device__ __forceinline__ unsigned long long hit_key(const int4& q, const float* p, const Win& w, int z_base) {
   const float Q = 1.0f / TPC_QSCALE;
+  const float dy = (float)q.x * Q - p[0];
+  const float dz = (float)(q.y - z_base) * Q - p[1];
+  const float quad = __fmaf_rn(w.S00 * dz, dz, fma2(w.S11 * dy, dy, -2.0f * w.S01 * dy, dz));
+  const float chi2 = fmaxf(0.0f, quad * w.inv_det);
+  return chi2 <= CHI2_CUT ? ((unsigned long long)__float_as_uint(chi2) << 32) | (unsigned)q.z : ~0ull;
+}
+
+// Best hit of the row described by `ri` inside box `bx` for the predicted
+// state: the smallest chi2 <= 16, ties to the smaller original id (a 64-bit key
+// of the chi2 bit pattern and the id, minimised over the group).  The search box
+// (max(0.5 cm, 4 sigma) plus 2 quanta) contains every hit with chi2 <= 16, so
+// the box never changes the result.  Every lane of the group returns the same
+// position and the hit's (qy, qz, id, key) in *qout.
+template <int G, bool NC>
+__device__ __forceinline__ int pick_box(const Buffers& b, const Grp<G>& g, const RowInfo& ri, const Box& bx,
+                                        const float* p, const Win& w, int z_base, int4* qout) {
+  if (box_empty(bx)) return -1;
+  // the bins (iy, iz0..iz1) of one y-bin row are contiguous: one hit range each
+  const int nyb = bx.iy1 - bx.iy0 + 1;
+  const int span = bx.iz1 - bx.iz0 + 1;
   unsigned long long best = ~0ull;
   int best_pos = -1;
-  auto consider = [&](int h) {
-    const int4 q = b.s_hit[h];
-    const float dy = (float)q.x * Q - p[0];
-    const float dz = (float)(q.y - z_base) * Q - p[1];
-    const float chi2 = fmaxf(0.0f, (S11 * dy * dy - 2.0f * S01 * dy * dz + S00 * dz * dz) * inv_det);
-    if (chi2 <= CHI2_CUT) {
-      const unsigned long long key = ((unsigned long long)__float_as_uint(chi2) << 32) | (unsigned)q.z;
-      if (key < best) {
-        best = key;
-        best_pos = h;
-      }
+  int4 best_q = make_int4(0, 0, 0, 0);
+  auto consider = [&](int h, const int4& q) {
+    const unsigned long long key = hit_key(q, p, w, z_base);
+    if (key < best) {
+      best = key;
+      best_pos = h;
+      best_q = q;
     }
   };
-  if constexpr (G == 1) {
-    for (int iy = iy0; iy <= iy1; ++iy) {
-      const int b0 = ri.bin0 + iy * ri.nz + iz0;
-      const int a = b.first[b0], e = b.first[b0 + span];
+  if constexpr (G == 1 && !NC) {
+    // inside the persistent kernel: a plain scan (fewer registers)
+    for (int iy = bx.iy0; iy <= bx.iy1; ++iy) {
+      const int b0 = ri.bin0 + iy * ri.nz + bx.iz0;
+      const int a = ld<NC>(b.first + b0), e = ld<NC>(b.first + b0 + span);
       int h = a;
       for (; h + 1 < e; h += 2) {  // two loads in flight
-        consider(h);
-        consider(h + 1);
+        const int4 q0 = ld<NC>(b.s_hit + h), q1 = ld<NC>(b.s_hit + h + 1);
+        consider(h, q0);
+        consider(h + 1, q1);
       }
-      if (h < e) consider(h);
+      if (h < e) consider(h, ld<NC>(b.s_hit + h));
     }
+    *qout = best_q;
+    return best_pos;
+  } else if constexpr (G == 1) {
+    // The hit ranges of up to NYP y-bin rows are fetched together, then up to
+    // CB candidate hits together.
+    constexpr int NYP = 4, CB = 8;
+    int ra[NYP], nk[NYP];
+#pragma unroll
+    for (int k = 0; k < NYP; ++k) {
+      ra[k] = 0;
+      nk[k] = 0;
+      if (k < nyb) {
+        const int b0 = ri.bin0 + (bx.iy0 + k) * ri.nz + bx.iz0;
+        ra[k] = ld<NC>(b.first + b0);
+        nk[k] = ld<NC>(b.first + b0 + span) - ra[k];
+      }
+    }
+    const int c1 = nk[0], c2 = c1 + nk[1], c3 = c2 + nk[2], total = c3 + nk[3];
+    // candidate j of the concatenated ranges
+    auto pos_of = [&](int j) {
+      return j < c1 ? ra[0] + j : j < c2 ? ra[1] + (j - c1) : j < c3 ? ra[2] + (j - c2) : ra[3] + (j - c3);
+    };
+    for (int j0 = 0; j0 < total; j0 += CB) {
+      int4 qb[CB];
+#pragma unroll
+      for (int j = 0; j < CB; ++j)
+        if (j0 + j < total) qb[j] = ld<NC>(b.s_hit + pos_of(j0 + j));
+#pragma unroll
+      for (int j = 0; j < CB; ++j)
+        if (j0 + j < total) consider(pos_of(j0 + j), qb[j]);
+    }
+    for (int iy = bx.iy0 + NYP; iy <= bx.iy1; ++iy) {  // wider windows (rare)
+      const int b0 = ri.bin0 + iy * ri.nz + bx.iz0;
+      const int a = ld<NC>(b.first + b0), e = ld<NC>(b.first + b0 + span);
+      for (int h = a; h < e; ++h) consider(h, ld<NC>(b.s_hit + h));
+    }
+    *qout = best_q;
     return best_pos;
   } else {
-  for (int base = 0; base < nyb; base += G) {  // group-uniform loop
-    // one y-bin row per lane: its hit range [a, a + cnt)
-    const int j = base + g.gl;
-    int a = 0, cnt = 0;
-    if (j < nyb) {
-      const int b0 = ri.bin0 + (iy0 + j) * ri.nz + iz0;
-      a = b.first[b0];
-      cnt = b.first[b0 + span] - a;
-    }
-    const int inc = g.incl_scan(cnt);
-    const int ex = inc - cnt;
-    const int total = g.shfl(inc, G - 1);
-    for (int kk = 0; kk < total; kk += G) {  // group-uniform loop
-      const int k = kk + g.gl;
-      // lane holding candidate k: the first lane whose inclusive count exceeds k
-      int lo = 0;
-      int hi = G - 1;
-#pragma unroll
-      for (int step = 1; step < G; step <<= 1) {
-        const int mid = (lo + hi) >> 1;
-        const int v = g.shfl(inc, mid);
-        if (v > k) hi = mid; else lo = mid + 1;
+    for (int base = 0; base < nyb; base += G) {  // group-uniform loop
+      // one y-bin row per lane: its hit range [a, a + cnt)
+      const int j = base + g.gl;
+      int a = 0, cnt = 0;
+      if (j < nyb) {
+        const int b0 = ri.bin0 + (bx.iy0 + j) * ri.nz + bx.iz0;
+        a = ld<NC>(b.first + b0);
+        cnt = ld<NC>(b.first + b0 + span) - a;
       }
-      const int a_src = g.shfl(a, lo);
-      const int ex_src = g.shfl(ex, lo);
-      if (k < total) consider(a_src + (k - ex_src));
+      const int inc = g.incl_scan(cnt);
+      const int ex = inc - cnt;
+      const int total = g.shfl(inc, G - 1);
+      for (int kk = 0; kk < total; kk += 2 * G) {  // group-uniform loop, two hits per lane
+        int h2[2];
+        int4 q2[2];
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const int k = kk + t * G + g.gl;
+          // lane holding candidate k: the first lane whose inclusive count exceeds k
+          int lo = 0;
+          int hi = G - 1;
+#pragma unroll
+          for (int step = 1; step < G; step <<= 1) {
+            const int mid = (lo + hi) >> 1;
+            const int v = g.shfl(inc, mid);
+            if (v > k) hi = mid; else lo = mid + 1;
+          }
+          const int a_src = g.shfl(a, lo);
+          const int ex_src = g.shfl(ex, lo);
+          h2[t] = k < total ? a_src + (k - ex_src) : -1;
+          if (h2[t] >= 0) q2[t] = ld<NC>(b.s_hit + h2[t]);
+        }
+#pragma unroll
+        for (int t = 0; t < 2; ++t)
+          if (h2[t] >= 0) consider(h2[t], q2[t]);
+      }
     }
-  }
-  {
     const unsigned long long gbest = g.min64(best);
     if (gbest == ~0ull) return -1;
     const unsigned who = __ballot_sync(g.mask, best == gbest) & g.mask;
     const int src = (__ffs(who) - 1) & (G - 1);
+    qout->x = g.shfl(best_q.x, src);
+    qout->y = g.shfl(best_q.y, src);
+    qout->z = g.shfl(best_q.z, src);
+    qout->w = g.shfl(best_q.w, src);
     return g.shfl(best_pos, src);
   }
-  }
 }
+
+template <int G, bool NC>
+__device__ __forceinline__ int pick_hit(const Buffers& b, const Grp<G>& g, const RowInfo& ri, const float* p,
+                                        const float* C, int z_base, int4* qout) {
+  const Win w = make_win(b.par, C);
+  const Box bx = row_box(ri, p[0], p[1], w.wy, w.wz, z_base);
+  return pick_box<G, NC>(b, g, ri, bx, p, w, z_base, qout);
+}
+
 }  // namespace
 
-// One group of G lanes per tracklet (grid-stride over the device count of start
-// hits).  All lanes of a group run the same Kalman arithmetic on the same values;
-// the lanes split the chain loads and the hit search of every row.
+// One group of G lanes per tracklet; all lanes of a group run the same Kalman
+// arithmetic on the same values and split the hit search of every row.
 //  (i)   circle through the first, middle and last chain hits -> initial state;
 //        Kalman fit along the chain (chain hits accepted without a chi2 test);
 //  (ii)  outward extension: best hit with chi2 <= 16, 5 consecutive misses end it;
@@ -894,36 +1017,44 @@ __device__ __forceinline__ int pick_hit(const Buffers& b, const Grp<G>& g, int i
 // step.  A non-finite or non-positive covariance diagonal drops the tracklet.
 // z is carried relative to the start hit (z_base) so that FP32 keeps its
 // precision for time-frame z' of thousands of cm.
-// Outward passes (i) and (ii) of the tracklet with start hit `start`, by a group
-// of G lanes: the result goes to b.tlu[tl] and the tracklet claims its outermost
-// hit (smallest tracklet index wins); `local` is the item-local id.
-template <int G>
-__device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, int start, int tl, int local) {
+//
+// Outward passes (i) and (ii) of the tracklet with start hit `start`: one loop
+// over the rows above the start row, taking the chain hit while the chain lasts
+// and searching afterwards (so that lanes of a warp in different phases run the
+// same propagation and update code together).  The result goes to b.tlu[tl] and
+// the tracklet claims its outermost hit (smallest tracklet index wins); `local`
+// is the item-local id, `rows` the item's row table, `xr` the row positions.
+template <int G, bool NC>
+__device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, const RowInfo* rows, const float* xr,
+                                            int start, int tl, int local) {
   const DevParams& P = b.par;
   const int NR = P.n_rows;
   const float Q = 1.0f / TPC_QSCALE;
-  const int4 hs = b.s_hit[start];
+  const int4 hs = ld<NC>(b.s_hit + start);
   const int key = hs.w;
   const int item = key / NR;
   const int r0 = key - item * NR;
   const int z_base = hs.y;
   int* hl = b.tl_hits + (size_t)tl * NR;
   // chain walk (pointer chasing; every lane of the group loads the same address)
-  int L = 0;
-  for (int h = start; h >= 0 && L < NR; h = b.up[h]) {
+  int L = 0, last = start;
+  for (int h = start; h >= 0 && L < NR; h = ld<NC>(b.up + h)) {
     if (g.gl == 0) hl[L] = h;
+    last = h;
     ++L;
   }
   g.sync();
-  const int4 qa = b.s_hit[hl[0]], qm = b.s_hit[hl[L / 2]], qc = b.s_hit[hl[L - 1]];
-  const float x1 = P.x[r0], x2 = P.x[r0 + L / 2], x3 = P.x[r0 + L - 1];
+  const int hmid = hl[L / 2];
+  const int hn0 = L > 1 ? hl[1] : start, hn1 = L > 2 ? hl[2] : start;
+  const int4 qa = hs, qm = ld<NC>(b.s_hit + hmid), qc = ld<NC>(b.s_hit + last);
+  const float x1 = xr[r0], x2 = xr[r0 + L / 2], x3 = xr[r0 + L - 1];
   const float y1 = qa.x * Q, y2 = qm.x * Q, y3 = qc.x * Q;
   const float z3 = (float)(qc.y - z_base) * Q;
   const float dx13 = x3 - x1, dy13 = y3 - y1;
-  const float d13 = sqrtf(dx13 * dx13 + dy13 * dy13);
-  const float d12 = sqrtf((x2 - x1) * (x2 - x1) + (y2 - y1) * (y2 - y1));
-  const float d23 = sqrtf((x3 - x2) * (x3 - x2) + (y3 - y2) * (y3 - y2));
-  const float cross = (x2 - x1) * (y3 - y1) - (y2 - y1) * (x3 - x1);
+  const float d13 = sqrtf(fma2(dx13, dx13, dy13, dy13));
+  const float d12 = sqrtf(fma2(x2 - x1, x2 - x1, y2 - y1, y2 - y1));
+  const float d23 = sqrtf(fma2(x3 - x2, x3 - x2, y3 - y2, y3 - y2));
+  const float cross = fma2(x2 - x1, y3 - y1, -(y2 - y1), x3 - x1);
   const float kappa = -2.0f * cross / (d12 * d23 * d13);
   const float u = fminf(1.0f, fmaxf(-1.0f, 0.5f * kappa * d13));
   const float phi1 = atan2f(dy13, dx13) + asinf(u);
@@ -935,56 +1066,49 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, i
   int out_row = r0, out_hit = start;
   float out_p[5] = {p[0], p[1], p[2], p[3], p[4]};
   float ov2 = C[ix(2, 2)], ov3 = C[ix(3, 3)], ov4 = C[ix(4, 4)];
-  bool alive = true, dead = false;
-  // (i) chain: the lanes prefetch G chain hits at a time, broadcast in order
-  for (int c0 = 1; c0 < L && alive && !dead; c0 += G) {
-    int hpos = 0;
-    int4 mine = make_int4(0, 0, 0, 0);
-    if (c0 + g.gl < L) {
-      hpos = hl[c0 + g.gl];
-      mine = b.s_hit[hpos];
+  bool dead = false;
+  // the next chain hit (position and coordinates) and the one after it are
+  // fetched one row ahead of their use
+  int hn = hn0, hn2 = hn1;
+  int4 qn = ld<NC>(b.s_hit + hn);
+  int misses = 0;
+  for (int r = r0 + 1; r < NR && misses < MAX_MISS; ++r) {
+    const int i = r - r0;  // chain index of row r
+    const bool chain = i < L;
+    int h = -1;
+    int4 q = make_int4(0, 0, 0, 0);
+    // the row table entry is fetched for every row (one 32-byte load, off the
+    // dependency chain) so that it lives in registers
+    const RowInfo ri = load_row<NC>(rows + r);
+    if (chain) {
+      h = hn;
+      q = qn;
+      hn = hn2;
+      if (i + 1 < L) qn = ld<NC>(b.s_hit + hn);
+      if (i + 2 < L) hn2 = hl[i + 2];
     }
-    const int cend = min(L, c0 + G);
-    for (int i = c0; i < cend; ++i) {
-      const int qx_ = g.shfl(mine.x, i - c0);
-      const int qy_ = g.shfl(mine.y, i - c0);
-      const int hp = g.shfl(hpos, i - c0);
-      const int r = r0 + i;
-      if (!kf_propagate(P, p, C, x, P.x[r])) { alive = false; break; }
-      x = P.x[r];
-      if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) { alive = false; break; }
-      kf_update(P, p, C, qx_ * Q - p[0], (float)(qy_ - z_base) * Q - p[1]);
-      if (!cov_ok(C)) { dead = true; break; }
-      out_row = r;
-      out_hit = hp;
+    const float xn = xr[r];
+    if (!kf_propagate(P, p, C, x, xn)) break;
+    x = xn;
+    if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) break;
+    if (!chain) h = pick_hit<G, NC>(b, g, ri, p, C, z_base, &q);
+    if (!chain && h < 0) {
+      ++misses;
+      continue;
+    }
+    kf_update(P, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
+    if (!cov_ok(C)) {
+      dead = true;
+      break;
+    }
+    misses = 0;
+    out_row = r;
+    out_hit = h;
 #pragma unroll
-      for (int m = 0; m < 5; ++m) out_p[m] = p[m];
-      ov2 = C[ix(2, 2)];
-      ov3 = C[ix(3, 3)];
-      ov4 = C[ix(4, 4)];
-    }
-  }
-  // (ii) outward extension
-  if (alive && !dead) {
-    int misses = 0;
-    for (int r = out_row + 1; r < NR && misses < MAX_MISS; ++r) {
-      if (!kf_propagate(P, p, C, x, P.x[r])) break;
-      x = P.x[r];
-      if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) break;
-      const int h = pick_hit<G>(b, g, item, r, p, C, z_base);
-      if (h < 0) { ++misses; continue; }
-      const int4 q = b.s_hit[h];
-      kf_update(P, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
-      if (!cov_ok(C)) { dead = true; break; }
-      misses = 0;
-      out_row = r;
-      out_hit = h;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) out_p[m] = p[m];
-      ov2 = C[ix(2, 2)];
-      ov3 = C[ix(3, 3)];
-      ov4 = C[ix(4, 4)];
-    }
+    for (int m = 0; m < 5; ++m) out_p[m] = p[m];
+    ov2 = C[ix(2, 2)];
+    ov3 = C[ix(3, 3)];
+    ov4 = C[ix(4, 4)];
   }
   if (g.gl == 0) {
     TrackletUp u;
@@ -1009,8 +1133,10 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, i
 // Inward refit (iii) of tracklet tl by a group of G lanes, only if it is the
 // smallest tracklet that reached its outermost hit (the others are dropped):
 // the record goes to b.tl[tl] and the hit list to b.tl_hits[tl * n_rows ...].
-template <int G>
-__device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g, int tl) {
+// `rows` is the row table of the tracklet's item, or null for the global one.
+template <int G, bool NC>
+__device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g, const RowInfo* rows,
+                                              const float* xr, int tl) {
   const DevParams& P = b.par;
   const int NR = P.n_rows;
   const float Q = 1.0f / TPC_QSCALE;
@@ -1018,49 +1144,57 @@ __device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g,
   const int item = u.item, local = u.local, z_base = u.z_base;
   const int out_hit = u.out_hit, out_row = u.out_row;
   bool dead = out_hit < 0 || b.out_owner[out_hit] != tl;
+  if (!rows) rows = b.rows + (size_t)item * NR;
   int* hl = b.tl_hits + (size_t)tl * NR;
   const float out_p[5] = {0.f, 0.f, u.snp, u.tgl, u.qpt};
   const float ov2 = u.v2, ov3 = u.v3, ov4 = u.v4;
   float C[15];
-  float x = P.x[out_row];
+  float x = xr[out_row];
   int n = 0;
   float chi2sum = 0.f, in_x = x;
   float in_p[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, in_C[15];
 #pragma unroll
   for (int m = 0; m < 15; ++m) in_C[m] = 0.f;
-  int in_hit = out_hit;
+  int in_z = 0;
   if (!dead) {
     // (iii) inward refit from the outermost hit: its y, z; the outward direction
     // and curvature with variances inflated 100-fold (capped at the initial ones)
-    const int4 qo = b.s_hit[out_hit];
+    const int4 qo = ld<NC>(b.s_hit + out_hit);
     float q5[5] = {qo.x * Q, (float)(qo.y - z_base) * Q, out_p[2], out_p[3], out_p[4]};
     set_c0(P, C);
     C[ix(2, 2)] = fminf(1.0f, INFLATE * ov2);
     C[ix(3, 3)] = fminf(1.0f, INFLATE * ov3);
     C[ix(4, 4)] = fminf(100.0f, INFLATE * ov4);
-    x = P.x[out_row];
     g.sync();
     if (g.gl == 0) hl[0] = out_hit;
     n = 1;
-    in_x = x;
+    in_z = qo.y;
 #pragma unroll
     for (int m = 0; m < 5; ++m) in_p[m] = q5[m];
 #pragma unroll
     for (int m = 0; m < 15; ++m) in_C[m] = C[m];
     int misses = 0;
     for (int r = out_row - 1; r >= 0 && misses < MAX_MISS; --r) {
-      if (!kf_propagate(P, q5, C, x, P.x[r])) break;
-      x = P.x[r];
+      const RowInfo ri = load_row<NC>(rows + r);  // independent of the state: in flight during the step
+      const float xn = xr[r];
+      if (!kf_propagate(P, q5, C, x, xn)) break;
+      x = xn;
       if (!(fabsf(q5[2]) < SIN_MAX) || fabsf(q5[0]) > x * P.tan_half) break;
-      const int h = pick_hit<G>(b, g, item, r, q5, C, z_base);
-      if (h < 0) { ++misses; continue; }
-      const int4 q = b.s_hit[h];
+      int4 q;
+      const int h = pick_hit<G, NC>(b, g, ri, q5, C, z_base, &q);
+      if (h < 0) {
+        ++misses;
+        continue;
+      }
       chi2sum += kf_update(P, q5, C, q.x * Q - q5[0], (float)(q.y - z_base) * Q - q5[1]);
-      if (!cov_ok(C)) { dead = true; break; }
+      if (!cov_ok(C)) {
+        dead = true;
+        break;
+      }
       misses = 0;
       if (g.gl == 0) hl[n] = h;
       ++n;
-      in_hit = h;
+      in_z = q.y;
       in_x = x;
 #pragma unroll
       for (int m = 0; m < 5; ++m) in_p[m] = q5[m];
@@ -1072,7 +1206,7 @@ __device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g,
   // the 112-byte record, fields split over the lanes of the group
   float* rf = reinterpret_cast<float*>(b.tl + tl);
   int* ri_ = reinterpret_cast<int*>(b.tl + tl);
-  const int z_in = n ? b.s_hit[in_hit].y : 0;
+  const int z_in = n ? in_z : 0;
   for (int fld = g.gl; fld < 27; fld += G) {
     float fv = 0.f;
 #pragma unroll
@@ -1093,6 +1227,9 @@ __device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g,
 
 template <int G>
 __global__ void __launch_bounds__(128) k_tracklets_up(const __grid_constant__ Buffers b) {
+  __shared__ float s_x[TPC_MAX_ROWS];
+  for (int r = threadIdx.x; r < b.par.n_rows; r += blockDim.x) s_x[r] = b.par.x[r];
+  __syncthreads();
   const Grp<G> g;
   const int T = b.start_ex[b.N];
   const int NR = b.par.n_rows;
@@ -1100,18 +1237,21 @@ __global__ void __launch_bounds__(128) k_tracklets_up(const __grid_constant__ Bu
   const int ngrp = (gridDim.x * blockDim.x) / G;
   for (int t = grp; t < T; t += ngrp) {
     const int start = b.starts[t];
-    const int item = b.s_hit[start].w / NR;
-    tracklet_up<G>(b, g, start, t, t - b.start_ex[b.item_off[item]]);
+    const int item = __ldg(&b.s_hit[start].w) / NR;
+    tracklet_up<G, true>(b, g, b.rows + (size_t)item * NR, s_x, start, t, t - b.start_ex[b.item_off[item]]);
   }
 }
 
 template <int G>
 __global__ void __launch_bounds__(128) k_tracklets_down(const __grid_constant__ Buffers b) {
+  __shared__ float s_x[TPC_MAX_ROWS];
+  for (int r = threadIdx.x; r < b.par.n_rows; r += blockDim.x) s_x[r] = b.par.x[r];
+  __syncthreads();
   const Grp<G> g;
   const int T = b.start_ex[b.N];
   const int grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int ngrp = (gridDim.x * blockDim.x) / G;
-  for (int t = grp; t < T; t += ngrp) tracklet_down<G>(b, g, t);
+  for (int t = grp; t < T; t += ngrp) tracklet_down<G, true>(b, g, nullptr, s_x, t);
 }
 
 cudaError_t tpc_launch_tracklets(const Buffers& b, int group, int grid, int block, cudaStream_t s) {
@@ -1340,6 +1480,7 @@ template <int G>
 __global__ void __launch_bounds__(BT) k_batched(const __grid_constant__ Buffers b) {
   const DevParams& P = b.par;
   __shared__ RowInfo s_rows[TPC_MAX_ROWS];
+  __shared__ float s_x[TPC_MAX_ROWS];
   __shared__ int s_cnt[TPC_MAX_ROWS], s_min[4][TPC_MAX_ROWS], s_fill[TPC_MAX_ROWS];
   __shared__ int s_cu[LINK_MAXC][BT], s_cd[LINK_MAXC][BT];
   __shared__ int sm[33];
@@ -1347,6 +1488,7 @@ __global__ void __launch_bounds__(BT) k_batched(const __grid_constant__ Buffers 
   const int NR = P.n_rows;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
   const Grp<G> g;
+  for (int r = threadIdx.x; r < NR; r += blockDim.x) s_x[r] = P.x[r];
   for (;;) {
     if (threadIdx.x == 0) {
       const int k = atomicAdd(b.queue_head, 1);
@@ -1470,9 +1612,9 @@ __global__ void __launch_bounds__(BT) k_batched(const __grid_constant__ Buffers 
     const int ntl = s_ntl;
     // ---- S6: tracklets, a group of G lanes each: outward passes, then one
     // inward refit per outermost hit
-    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_up<G>(b, g, b.starts[tlb + t], tlb + t, t);
+    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_up<G, false>(b, g, s_rows, s_x, b.starts[tlb + t], tlb + t, t);
     __syncthreads();
-    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_down<G>(b, g, tlb + t);
+    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_down<G, false>(b, g, s_rows, s_x, tlb + t);
     __syncthreads();
     // ---- S7: ownership
     for (int t = warp; t < ntl; t += nwarps) select_max_warp(b, tlb + t, lane);
