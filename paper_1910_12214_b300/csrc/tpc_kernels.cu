@@ -44,6 +44,8 @@ constexpr long long LINK_D = 512;       // 0.5 cm chord deviation
 constexpr float INFLATE = 100.0f;       // covariance inflation of the inward refit
 constexpr int LINK_THREADS = 128;
 constexpr int LINK_MAXC = 24;           // window candidates per side and hit
+constexpr int LINK_MAXC_STAGED = 12;    // the same in k_links (overflow: direct enumeration)
+constexpr int LINK_STAGE_MAX = 96 * 1024;  // shared-memory staging of k_links
 
 __device__ __forceinline__ int warp_incl_scan(int v) {
   const int lane = threadIdx.x & 31;
@@ -348,73 +350,102 @@ __device__ __forceinline__ void bin_range(long long lo, long long hi, int vmin, 
 }
 }  // namespace
 
-// One CTA per block of `rows_per_cta` consecutive rows of one item (their hits
-// are contiguous in sorted order, so the threads take a flat range of them).
 // For every hit h of an inner row: the pair (u on r+1, d on r-1) inside the
 // windows |dqy| <= 11*dqx/4, |dqz| <= 16*dqx/5 that minimises m = dY^2 + dZ^2,
 // dY = (qy_u-qy_h)*dx_dn - (qy_h-qy_d)*dx_up (int64), accepted if
 // m <= ((dx_up+dx_dn)*512)^2; ties: smaller id_u, then smaller id_d.  Rows 0 and
-// n_rows-1 get no links (targets only).  Neighbour rows are read through L1.
+// n_rows-1 get no links (targets only).
 namespace {
+// Sorted hits and bin index entries, read from global memory or from the rows
+// of one item staged in shared memory (positions offset by p_lo, bins by f_lo).
+struct GlobalSrc {
+  const int4* h;
+  const int* f;
+  __device__ __forceinline__ int4 hit(int p) const { return h[p]; }
+  __device__ __forceinline__ int first(int i) const { return f[i]; }
+};
+
+struct StageSrc {
+  const int4* h;
+  const int* f;
+  int p_lo, f_lo;
+  __device__ __forceinline__ int4 hit(int p) const { return h[p - p_lo]; }
+  __device__ __forceinline__ int first(int i) const { return f[i - f_lo]; }
+};
+
+// m of one (u, d) pair given the window offsets ey = qy_u - qy_h, ez, fy =
+// qy_h - qy_d, fz; false if m > cut^2.  With W32 the factors are 32-bit integers
+// (exact for a row pitch of at most 2^14 quanta, checked on the host) squared by
+// widening multiplies; |dY| > cut or |dZ| > cut already implies m > cut^2.
+template <bool W32>
+__device__ __forceinline__ bool link_metric(int ey, int ez, int fy, int fz, int dxu, int dxd, long long cut,
+                                            long long cut2, long long* m) {
+  if constexpr (W32) {
+    const int dY = ey * dxd - fy * dxu;
+    const int dZ = ez * dxd - fz * dxu;
+    if (dY > cut || -dY > cut || dZ > cut || -dZ > cut) return false;
+    *m = (long long)dY * dY + (long long)dZ * dZ;
+  } else {
+    const long long dY = (long long)ey * dxd - (long long)fy * dxu;
+    const long long dZ = (long long)ez * dxd - (long long)fz * dxu;
+    *m = dY * dY + dZ * dZ;
+  }
+  return *m <= cut2;
+}
+
 // Neighbour search of one hit at sorted position pos on inner row r of an item
-// (rows[r - lo] is row r); s_cu / s_cd are this thread's candidate lists.
-template <int W>
-__device__ __forceinline__ void link_hit(const Buffers& b, const RowInfo* rows, int lo, int pos, int4 qh, int r,
-                                         int (*s_cu)[W], int (*s_cd)[W], int t) {
+// (rows[r - lo] is row r): the window candidates of each side go to this
+// thread's lists s_cu / s_cd (MAXC entries), then every pair is scored; with
+// more candidates than the lists hold, the pairs are enumerated directly.
+template <int W, int MAXC, bool W32, class Src>
+__device__ __forceinline__ void link_hit(const Buffers& b, const Src& S, const RowInfo* rows, int lo, int pos,
+                                         int4 qh, int r, int (*s_cu)[W], int (*s_cd)[W], int t) {
   const DevParams& P = b.par;
   const RowInfo U = rows[r + 1 - lo], D = rows[r - 1 - lo];
-  const long long dxu = P.qx[r + 1] - P.qx[r];
-  const long long dxd = P.qx[r] - P.qx[r - 1];
-  const long long wyu = dxu * 11 / 4, wzu = dxu * 16 / 5;
-  const long long wyd = dxd * 11 / 4, wzd = dxd * 16 / 5;
-  const long long cut = (dxu + dxd) * LINK_D;
+  const int dxu = P.qx[r + 1] - P.qx[r];
+  const int dxd = P.qx[r] - P.qx[r - 1];
+  const int wyu = dxu * 11 / 4, wzu = dxu * 16 / 5;
+  const int wyd = dxd * 11 / 4, wzd = dxd * 16 / 5;
+  const long long cut = (long long)(dxu + dxd) * LINK_D;
   const long long cut2 = cut * cut;
-  const long long yh = qh.x, zh = qh.y;
+  const int yh = qh.x, zh = qh.y;
+  int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
+  bin_range((long long)yh - wyu, (long long)yh + wyu, U.ymin, U.shift, U.ny, &uy0, &uy1);
+  bin_range((long long)zh - wzu, (long long)zh + wzu, U.zmin, U.shift, U.nz, &uz0, &uz1);
+  bin_range((long long)yh - wyd, (long long)yh + wyd, D.ymin, D.shift, D.ny, &dy0, &dy1);
+  bin_range((long long)zh - wzd, (long long)zh + wzd, D.zmin, D.shift, D.nz, &dz0, &dz1);
   // candidates of each side: hits inside the window, from one contiguous hit
   // range per y-bin row (the z-bins of a y-bin row are adjacent)
   int nu = 0, nd = 0;
   bool ovf = false;
-  {
-    int y0, y1, z0, z1;
-    bin_range(yh - wyu, yh + wyu, U.ymin, U.shift, U.ny, &y0, &y1);
-    bin_range(zh - wzu, zh + wzu, U.zmin, U.shift, U.nz, &z0, &z1);
-    if (z1 >= z0)
-      for (int iy = y0; iy <= y1; ++iy) {
-        const int b0 = U.bin0 + iy * U.nz + z0;
-        const int e_ = b.first[b0 + z1 - z0 + 1];
-        for (int pu = b.first[b0]; pu < e_; ++pu) {
-          const int4 q = b.s_hit[pu];
-          const long long ey = q.x - yh, ez = q.y - zh;
-          if (ey > wyu || -ey > wyu || ez > wzu || -ez > wzu) continue;
-          if (nu < LINK_MAXC) s_cu[nu++][t] = pu; else ovf = true;
-        }
+  if (uz1 >= uz0 && dz1 >= dz0) {
+    for (int iy = uy0; iy <= uy1; ++iy) {
+      const int b0 = U.bin0 + iy * U.nz + uz0;
+      const int e_ = S.first(b0 + uz1 - uz0 + 1);
+      for (int pu = S.first(b0); pu < e_; ++pu) {
+        const int4 q = S.hit(pu);
+        const int ey = q.x - yh, ez = q.y - zh;
+        if (ey > wyu || -ey > wyu || ez > wzu || -ez > wzu) continue;
+        if (nu < MAXC) s_cu[nu++][t] = pu; else ovf = true;
       }
-  }
-  {
-    int y0, y1, z0, z1;
-    bin_range(yh - wyd, yh + wyd, D.ymin, D.shift, D.ny, &y0, &y1);
-    bin_range(zh - wzd, zh + wzd, D.zmin, D.shift, D.nz, &z0, &z1);
-    if (z1 >= z0 && nu > 0)
-      for (int iy = y0; iy <= y1; ++iy) {
-        const int b0 = D.bin0 + iy * D.nz + z0;
-        const int e_ = b.first[b0 + z1 - z0 + 1];
-        for (int pd = b.first[b0]; pd < e_; ++pd) {
-          const int4 q = b.s_hit[pd];
-          const long long fy = yh - q.x, fz = zh - q.y;
+    }
+    if (nu > 0)
+      for (int iy = dy0; iy <= dy1; ++iy) {
+        const int b0 = D.bin0 + iy * D.nz + dz0;
+        const int e_ = S.first(b0 + dz1 - dz0 + 1);
+        for (int pd = S.first(b0); pd < e_; ++pd) {
+          const int4 q = S.hit(pd);
+          const int fy = yh - q.x, fz = zh - q.y;
           if (fy > wyd || -fy > wyd || fz > wzd || -fz > wzd) continue;
-          if (nd < LINK_MAXC) s_cd[nd++][t] = pd; else ovf = true;
+          if (nd < MAXC) s_cd[nd++][t] = pd; else ovf = true;
         }
       }
   }
   long long best = -1;
   int bu = -1, bd = -1, bid_u = 0, bid_d = 0;
   auto pair = [&](int pu, const int4& qu, int pd, const int4& qd) {
-    const long long ey = qu.x - yh, ez = qu.y - zh;
-    const long long fy = yh - qd.x, fz = zh - qd.y;
-    const long long dY = ey * dxd - fy * dxu;
-    const long long dZ = ez * dxd - fz * dxu;
-    const long long m = dY * dY + dZ * dZ;
-    if (m > cut2) return;
+    long long m;
+    if (!link_metric<W32>(qu.x - yh, qu.y - zh, yh - qd.x, zh - qd.y, dxu, dxd, cut, cut2, &m)) return;
     bool better = best < 0 || m < best;
     if (!better && m == best) better = qu.z < bid_u || (qu.z == bid_u && qd.z < bid_d);
     if (better) {
@@ -428,32 +459,27 @@ __device__ __forceinline__ void link_hit(const Buffers& b, const RowInfo* rows, 
   if (!ovf) {
     for (int iu = 0; iu < nu; ++iu) {
       const int pu = s_cu[iu][t];
-      const int4 qu = b.s_hit[pu];
+      const int4 qu = S.hit(pu);
       for (int id = 0; id < nd; ++id) {
         const int pd = s_cd[id][t];
-        pair(pu, qu, pd, b.s_hit[pd]);
+        pair(pu, qu, pd, S.hit(pd));
       }
     }
   } else {
     // more candidates than the lists hold (very dense rows): direct enumeration
-    int uy0, uy1, uz0, uz1, dy0, dy1, dz0, dz1;
-    bin_range(yh - wyu, yh + wyu, U.ymin, U.shift, U.ny, &uy0, &uy1);
-    bin_range(zh - wzu, zh + wzu, U.zmin, U.shift, U.nz, &uz0, &uz1);
-    bin_range(yh - wyd, yh + wyd, D.ymin, D.shift, D.ny, &dy0, &dy1);
-    bin_range(zh - wzd, zh + wzd, D.zmin, D.shift, D.nz, &dz0, &dz1);
     for (int iy = uy0; iy <= uy1; ++iy) {
       const int bu0 = U.bin0 + iy * U.nz + uz0;
-      const int ue = b.first[bu0 + uz1 - uz0 + 1];
-      for (int pu = b.first[bu0]; pu < ue; ++pu) {
-        const int4 qu = b.s_hit[pu];
-        const long long ey = qu.x - yh, ez = qu.y - zh;
+      const int ue = S.first(bu0 + uz1 - uz0 + 1);
+      for (int pu = S.first(bu0); pu < ue; ++pu) {
+        const int4 qu = S.hit(pu);
+        const int ey = qu.x - yh, ez = qu.y - zh;
         if (ey > wyu || -ey > wyu || ez > wzu || -ez > wzu) continue;
         for (int jy = dy0; jy <= dy1; ++jy) {
           const int bd0 = D.bin0 + jy * D.nz + dz0;
-          const int de = b.first[bd0 + dz1 - dz0 + 1];
-          for (int pd = b.first[bd0]; pd < de; ++pd) {
-            const int4 qd = b.s_hit[pd];
-            const long long fy = yh - qd.x, fz = zh - qd.y;
+          const int de = S.first(bd0 + dz1 - dz0 + 1);
+          for (int pd = S.first(bd0); pd < de; ++pd) {
+            const int4 qd = S.hit(pd);
+            const int fy = yh - qd.x, fz = zh - qd.y;
             if (fy > wyd || -fy > wyd || fz > wzd || -fz > wzd) continue;
             pair(pu, qu, pd, qd);
           }
@@ -466,10 +492,18 @@ __device__ __forceinline__ void link_hit(const Buffers& b, const RowInfo* rows, 
 }
 }  // namespace
 
-__global__ void __launch_bounds__(LINK_THREADS) k_links(const __grid_constant__ Buffers b, int rows_per_cta) {
+// One CTA per block of `rows_per_cta` consecutive rows of one item (their hits
+// are contiguous in sorted order, so the threads take a flat range of them).
+// The block's rows and the rows on either side are staged in shared memory
+// (sorted hits and bin index, at most `stage_bytes`); a block that does not fit
+// reads global memory instead.
+template <bool W32>
+__global__ void __launch_bounds__(LINK_THREADS) k_links(const __grid_constant__ Buffers b, int rows_per_cta,
+                                                        int stage_bytes) {
   const DevParams& P = b.par;
+  extern __shared__ int4 s_stage[];
   __shared__ RowInfo s_rows[TPC_MAX_ROWS + 2];
-  __shared__ int s_cu[LINK_MAXC][LINK_THREADS], s_cd[LINK_MAXC][LINK_THREADS];
+  __shared__ int s_cu[LINK_MAXC_STAGED][LINK_THREADS], s_cd[LINK_MAXC_STAGED][LINK_THREADS];
   const int NR = P.n_rows;
   const int nrb = (NR + rows_per_cta - 1) / rows_per_cta;
   const int item = blockIdx.x / nrb;
@@ -480,16 +514,33 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(const __grid_constant__ 
   __syncthreads();
   const int p_begin = s_rows[r_begin - lo].pos0;
   const int p_end = s_rows[r_end - 1 - lo].pos0 + s_rows[r_end - 1 - lo].n;
+  const RowInfo& rl = s_rows[0];
+  const RowInfo& rh = s_rows[hi - lo];
+  const int p_lo = rl.pos0, p_hi = rh.pos0 + rh.n;
+  const int f_lo = rl.bin0, f_hi = rh.bin0 + (rh.n > 0 ? rh.ny * rh.nz : 0) + 1;
+  const int nh = p_hi - p_lo, nf = f_hi - f_lo;
+  const bool staged = (long long)nh * 16 + (long long)nf * 4 <= stage_bytes;
+  int* sf = reinterpret_cast<int*>(s_stage + (staged ? nh : 0));
+  if (staged) {
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) s_stage[i] = __ldg(b.s_hit + p_lo + i);
+    for (int i = threadIdx.x; i < nf; i += blockDim.x) sf[i] = __ldg(b.first + f_lo + i);
+  }
+  __syncthreads();
   const int t = threadIdx.x;
+  const StageSrc SS{s_stage, sf, p_lo, f_lo};
+  const GlobalSrc GS{b.s_hit, b.first};
   for (int pos = p_begin + t; pos < p_end; pos += blockDim.x) {
-    const int4 qh = b.s_hit[pos];
+    const int4 qh = staged ? s_stage[pos - p_lo] : b.s_hit[pos];
     const int r = qh.w - item * NR;
     if (r == 0 || r == NR - 1) {
       b.up_raw[pos] = -1;
       b.dn_raw[pos] = -1;
       continue;
     }
-    link_hit<LINK_THREADS>(b, s_rows, lo, pos, qh, r, s_cu, s_cd, t);
+    if (staged)
+      link_hit<LINK_THREADS, LINK_MAXC_STAGED, W32>(b, SS, s_rows, lo, pos, qh, r, s_cu, s_cd, t);
+    else
+      link_hit<LINK_THREADS, LINK_MAXC_STAGED, W32>(b, GS, s_rows, lo, pos, qh, r, s_cu, s_cd, t);
   }
 }
 
@@ -1578,7 +1629,7 @@ __global__ void __launch_bounds__(BT) k_batched(const __grid_constant__ Buffers 
         b.dn_raw[pos] = -1;
         continue;
       }
-      link_hit<BT>(b, s_rows, 0, pos, qh, r, s_cu, s_cd, threadIdx.x);
+      link_hit<BT, LINK_MAXC, false>(b, GlobalSrc{b.s_hit, b.first}, s_rows, 0, pos, qh, r, s_cu, s_cd, threadIdx.x);
     }
     for (int pos = p_end + threadIdx.x; pos < a1; pos += blockDim.x) {  // rejected clusters: no links
       b.up_raw[pos] = -1;
@@ -1788,7 +1839,12 @@ cudaError_t tpc_batched_occupancy(int per_sm[3]) {
 
 cudaError_t tpc_configure_kernels(int sort_smem, int link_smem) {
   (void)link_smem;
-  return cudaFuncSetAttribute(k_row_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, sort_smem);
+  cudaError_t e = cudaFuncSetAttribute(k_row_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, sort_smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_links<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, LINK_STAGE_MAX);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_links<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, LINK_STAGE_MAX);
+  return e;
 }
 
 static void scan_i32(const int* in, int* out, long long n, unsigned long long* bsum, int G, cudaStream_t s) {
@@ -1832,7 +1888,18 @@ cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t 
     // default: 8 rows per CTA (measured best between 4 for one event and 16 for 64 events)
     const int rpc = c.link_rows > 0 ? std::min(c.link_rows, NR) : std::min(8, NR);
     const int nrb = (NR + rpc - 1) / rpc;
-    k_links<<<b.I * nrb, LINK_THREADS, 0, s>>>(b, rpc);
+    // staging room for the block's rows at up to 1.5 times the mean row
+    // occupancy (hits 16 B; bin index about one entry per hit, at most 2n + 3);
+    // blocks with denser rows read global memory
+    const long long avg = (b.N + (long long)b.I * NR - 1) / std::max(1LL, (long long)b.I * NR);
+    long long stage = (long long)(rpc + 2) * (16 * (3 * avg / 2) + 4 * (2 * avg + 4)) + 64;
+    stage = std::min<long long>(LINK_STAGE_MAX, std::max<long long>(4096, (stage + 15) / 16 * 16));
+    int max_dx = 0;
+    for (int r = 0; r + 1 < NR; ++r) max_dx = std::max(max_dx, b.par.qx[r + 1] - b.par.qx[r]);
+    if (max_dx <= 16384)
+      k_links<true><<<b.I * nrb, LINK_THREADS, stage, s>>>(b, rpc, (int)stage);
+    else
+      k_links<false><<<b.I * nrb, LINK_THREADS, stage, s>>>(b, rpc, (int)stage);
   }
   mark(5);
   const int gN = (int)((b.N + 255) / 256) < c.num_sms * 8 ? (int)((b.N + 255) / 256) : c.num_sms * 8;
