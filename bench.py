@@ -248,7 +248,7 @@ def main():
     gen = generate_forms(forms) if forms else {}  # CPU work before CUDA is touched
 
     import torch
-    from paper_1910_12214_b300 import tpc
+    from paper_1910_12214_b300 import shard, tpc
 
     torch.cuda.set_device(local)
     dist = None
@@ -284,11 +284,8 @@ def main():
     if dist:
         dist.barrier()
     clk = clocks.stop()
-    ms = float(np.mean(step_ms))
-    if dist:
-        tt = torch.tensor([ms], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ms = float(tt.item())
+    ms = shard.max_over_ranks(float(np.mean(step_ms)), dist, device=dev)
+    n_all = shard.sum_over_ranks(cl.n, dist, device=dev)  # clusters of all ranks' events
     n_tr, n_ids = t.counts()
     stages = stage_profile(t)
 
@@ -305,7 +302,7 @@ def main():
         trk, ids = t.get_tracks()
         e2e.append(time.perf_counter() - t0)
     d2h = trk.nbytes + ids.nbytes + 32
-    e2e_s = float(np.median(e2e[1:]))
+    e2e_s = shard.max_over_ranks(float(np.median(e2e[1:])), dist, device=dev)
     t.close()
 
     form_out = {}
@@ -317,7 +314,7 @@ def main():
         peak, peak_kind = measured_peak_hbm()
         algo = ALGO_BYTES.get(dom, 0) * cl.n
         achieved = algo / (stages[dom] * 1e-6) / 1e9
-        value = cl.n * world / (ms * 1e-3)
+        value = n_all / (ms * 1e-3)
         line = {
             "metric": "TPC clusters/s tracked (sector tracker, full TPC event)",
             "value": value, "unit": "clusters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
@@ -326,7 +323,7 @@ def main():
             "config": {"workload": WORKLOADS[args.workload], "clusters_per_step": cl.n, "items": cl.n_items,
                        "tracks": n_tr, "l2": "flushed between steps (256 MB write)", "tuning": tuning,
                        "autotune_best_us": tune_us},
-            "e2e": {"value": cl.n * world / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
+            "e2e": {"value": n_all / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
                     "d2h_bytes_per_step": int(d2h)},
             "gpu_launches": KERNELS_PER_STEP["batched" if tuning["mode"] == 2 else "plain"] * args.steps,
             "stage_us": {k: round(v, 2) for k, v in stages.items()},
