@@ -209,9 +209,10 @@ tpc_status tpc_surrogate_load(tpc_ctx* ctx, const char* path);
  * same output bit for bit).  tracklet_lanes: lanes that share one tracklet
  * (1, 2, 4, 8, 16 or 32; they split the hit search of every row);
  * tracklet_block: threads per block of the tracklet kernel (32, 64, 96
- * or 128); tracklet_blocks_per_sm: grid = this x SM count; sort_smem,
- * link_smem: dynamic shared memory [bytes] of the per-row sort and neighbour
- * kernels (rows that do not fit use global memory).  0 keeps a field. */
+ * or 128); tracklet_blocks_per_sm: grid = this x SM count; sort_smem: dynamic
+ * shared memory [bytes] of the per-row sort (rows that do not fit use global
+ * memory); link_rows: pad rows per block of the neighbour kernel (-1 = 8; the
+ * block's rows are staged in shared memory when they fit).  0 keeps a field. */
 typedef struct {
   int tracklet_lanes;
   int tracklet_block;
