@@ -216,12 +216,17 @@ def time_steps(t, stream, steps, flush):
     return [a.elapsed_time(b) for a, b in ms]
 
 
-def stage_profile(t, steps=3):
-    """Per-step device times from the library's events (direct launches)."""
+def stage_profile(t, stream, steps=3):
+    """Per-step device times from the library's events (direct launches).  A
+    bounded spin kernel ahead of each step keeps the GPU busy while the host
+    enqueues the step, so that the events time the kernels, not the host."""
+    import torch
     tun = t.get_tuning()
     t.set_tuning(use_graph=1)
     acc = {}
     for _ in range(steps):
+        with torch.cuda.stream(stream):
+            torch.cuda._sleep(2_000_000)  # about 1 ms of clock cycles
         t.track()
         for k, v in t.stage_times().items():
             acc[k] = acc.get(k, 0.0) + v / steps
@@ -287,7 +292,7 @@ def main():
     ms = shard.max_over_ranks(float(np.mean(step_ms)), dist, device=dev)
     n_all = shard.sum_over_ranks(cl.n, dist, device=dev)  # clusters of all ranks' events
     n_tr, n_ids = t.counts()
-    stages = stage_profile(t)
+    stages = stage_profile(t, stream)
 
     # end to end through the public API with host buffers: H2D of the step's
     # clusters, tracking, D2H of the tracks and their cluster ids
@@ -354,11 +359,13 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
                 setup(t)
             t.load(d, on_device=True)
             for mode in modes:
-                t.set_tuning(mode=1 if mode == "plain" else 2, use_graph=2)
+                tun, _ = t.autotune(iters=2, mode=1 if mode == "plain" else 2)  # best shapes of this mode
+                t.set_tuning(use_graph=2)
                 for _ in range(2):
                     t.track()
                 ms = float(np.median(time_steps(t, stream, steps, flush)))
-                out[mode] = {"clusters_per_s": n_clusters / (ms * 1e-3), "ms": ms, "tracks": t.counts()[0]}
+                out[mode] = {"clusters_per_s": n_clusters / (ms * 1e-3), "ms": ms, "tracks": t.counts()[0],
+                             "tuning": tun}
         del d
         torch.cuda.empty_cache()
         return out
@@ -390,7 +397,8 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
             t.load(d, on_device=True)
             for corr in ("mlp", "grid", "none"):
                 t.set_correction(corr)
-                t.set_tuning(mode=1, use_graph=2)
+                t.autotune(iters=2, mode=1)
+                t.set_tuning(use_graph=2)
                 for _ in range(2):
                     t.track()
                 ms = float(np.median(time_steps(t, stream, 5, flush)))

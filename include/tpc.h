@@ -233,6 +233,9 @@ tpc_status tpc_get_tuning(tpc_ctx* ctx, tpc_tuning* t);
  * returns it in *best (nullable) with its time in *best_us (nullable).  The
  * last run leaves the batch tracked with the chosen shape. */
 tpc_status tpc_autotune(tpc_ctx* ctx, int iters, tpc_tuning* best, float* best_us);
+/* The same over the shapes of one mode only (1 = plain, 2 = batched; 0 = both,
+ * as tpc_autotune), for comparing the two modes at their best shapes. */
+tpc_status tpc_autotune_mode(tpc_ctx* ctx, int iters, int mode, tpc_tuning* best, float* best_us);
 
 /* Binning of ONE sector without any device allocation.  The paper has no
  * counterpart: this entry point exists for callers that cannot allocate GPU

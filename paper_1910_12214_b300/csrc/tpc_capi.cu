@@ -695,7 +695,11 @@ extern "C" tpc_status tpc_get_tuning(tpc_ctx* c, tpc_tuning* t) {
 }
 
 extern "C" tpc_status tpc_autotune(tpc_ctx* c, int iters, tpc_tuning* best_out, float* best_us) {
-  if (!c || iters < 1) return TPC_ERR_INVALID_ARG;
+  return tpc_autotune_mode(c, iters, 0, best_out, best_us);
+}
+
+extern "C" tpc_status tpc_autotune_mode(tpc_ctx* c, int iters, int mode, tpc_tuning* best_out, float* best_us) {
+  if (!c || iters < 1 || mode < 0 || mode > 2) return TPC_ERR_INVALID_ARG;
   if (!c->loaded) return fail(c, TPC_ERR_STATE, "tpc_autotune before tpc_load_clusters");
   cudaError_t e = cudaSetDevice(c->cfg.device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
@@ -707,11 +711,18 @@ extern "C" tpc_status tpc_autotune(tpc_ctx* c, int iters, tpc_tuning* best_out, 
   for (int sm : {6 * 1024, 12 * 1024, 24 * 1024})
     for (int lr : {-1, 4, 16, 152}) cand.push_back({0, 0, 0, sm, lr, 1, 0, 0});
   for (int bl : {1, 2, 4}) cand.push_back({0, 0, 0, 0, 0, 2, bl, 0});
+  if (mode) {  // only the shapes of one mode
+    std::vector<tpc_tuning> keep;
+    for (const tpc_tuning& t : cand)
+      if (t.mode == mode) keep.push_back(t);
+    cand.swap(keep);
+  }
   cudaEvent_t e0, e1;
   cudaEventCreate(&e0);
   cudaEventCreate(&e1);
   tpc_tuning best{};
   tpc_get_tuning(c, &best);
+  if (mode) best.mode = mode;
   float best_t = 1e30f;
   const LaunchCfg saved = c->lc;
   auto time_cfg = [&](const tpc_tuning& t, float* us) -> tpc_status {

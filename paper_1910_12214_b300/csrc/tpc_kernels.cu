@@ -672,6 +672,10 @@ __device__ __forceinline__ constexpr int ix(int i, int j) { return i * (i + 1) /
 // can differ between the kernels this code is inlined into.
 __device__ __forceinline__ float fma2(float a, float b, float c, float d) { return __fmaf_rn(a, b, __fmul_rn(c, d)); }
 
+// square root of x > 0 from the hardware reciprocal square root (a few ulp;
+// one multiply instead of the correctly rounded sequence)
+__device__ __forceinline__ float sqrt_pos(float x) { return x * rsqrtf(x); }
+
 __device__ __forceinline__ float asin_over_u(float u) {
   if (fabsf(u) < 0.1f) {
     const float u2 = u * u;
@@ -697,13 +701,13 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float
   const float kappa = kB * p[4];
   const float s2 = s1 - kappa * dx;
   if (!(fabsf(s1) < SNP_LIMIT) || !(fabsf(s2) < SNP_LIMIT)) return false;
-  const float c1 = sqrtf((1.0f - s1) * (1.0f + s1));
-  const float c2 = sqrtf((1.0f - s2) * (1.0f + s2));
+  const float c1 = sqrt_pos((1.0f - s1) * (1.0f + s1));
+  const float c2 = sqrt_pos((1.0f - s2) * (1.0f + s2));
   // fast reciprocals (2 ulp): the Jacobian only feeds the covariance
   const float cc = c1 + c2;
   const float inv_cc = __fdividef(1.0f, cc);
   const float T = (s1 + s2) * inv_cc;
-  const float w = sqrtf(1.0f + T * T);
+  const float w = sqrt_pos(1.0f + T * T);
   const float adx = fabsf(dx);
   const float u = 0.5f * kappa * adx * w;
   if (!(fabsf(u) < 1.0f)) return false;
@@ -759,11 +763,28 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float
   return true;
 }
 
-// Kalman update with H = [I2 0]; residuals (r0, r1); returns the chi2 increment.
-__device__ __forceinline__ float kf_update(const DevParams& P, float* p, float* C, float r0, float r1) {
-  const float S00 = C[ix(0, 0)] + P.vy, S01 = C[ix(1, 0)], S11 = C[ix(1, 1)] + P.vz;
-  const float inv_det = 1.0f / fma2(S00, S11, -S01, S01);
-  const float I00 = S11 * inv_det, I01 = -S01 * inv_det, I11 = S00 * inv_det;
+// Search window of the predicted state: the innovation covariance S = C_yz + V,
+// its inverse determinant and the half-widths max(0.5 cm, 4 sqrt(S_ii)).
+struct Win {
+  float S00, S01, S11, inv_det, wy, wz;
+};
+
+__device__ __forceinline__ Win make_win(const DevParams& P, const float* C) {
+  Win w;
+  w.S00 = C[ix(0, 0)] + P.vy;
+  w.S01 = C[ix(1, 0)];
+  w.S11 = C[ix(1, 1)] + P.vz;
+  w.inv_det = 1.0f / fma2(w.S00, w.S11, -w.S01, w.S01);
+  // window only: the 2-quantum margin of the box covers the approximation
+  w.wy = fmaxf(WIN_MIN, 4.0f * sqrt_pos(w.S00));
+  w.wz = fmaxf(WIN_MIN, 4.0f * sqrt_pos(w.S11));
+  return w;
+}
+
+// Kalman update with H = [I2 0] and the innovation covariance of `w` (made
+// from the same predicted C); residuals (r0, r1); returns the chi2 increment.
+__device__ __forceinline__ float kf_update(const Win& w, float* p, float* C, float r0, float r1) {
+  const float I00 = w.S11 * w.inv_det, I01 = -w.S01 * w.inv_det, I11 = w.S00 * w.inv_det;
   // columns 0 and 1 of the symmetric covariance
   float c0[5], c1[5], K0[5], K1[5];
 #pragma unroll
@@ -868,23 +889,6 @@ __device__ __forceinline__ RowInfo load_row(const RowInfo* p) {
   } else {
     return *p;
   }
-}
-
-// Search window of the predicted state: the innovation covariance S = C_yz + V,
-// its inverse determinant and the half-widths max(0.5 cm, 4 sqrt(S_ii)).
-struct Win {
-  float S00, S01, S11, inv_det, wy, wz;
-};
-
-__device__ __forceinline__ Win make_win(const DevParams& P, const float* C) {
-  Win w;
-  w.S00 = C[ix(0, 0)] + P.vy;
-  w.S01 = C[ix(1, 0)];
-  w.S11 = C[ix(1, 1)] + P.vz;
-  w.inv_det = 1.0f / fma2(w.S00, w.S11, -w.S01, w.S01);
-  w.wy = fmaxf(WIN_MIN, 4.0f * sqrtf(w.S00));
-  w.wz = fmaxf(WIN_MIN, 4.0f * sqrtf(w.S11));
-  return w;
 }
 
 // Bins [iy0, iy1] x [iz0, iz1] of a row's grid covered by the box
@@ -996,6 +1000,21 @@ __device__ __forceinline__ int pick_box(const Buffers& b, const Grp<G>& g, const
     }
     *qout = best_q;
     return best_pos;
+  } else if (nyb == 1) {
+    // one y-bin row (the usual case): every lane reads its hit range (one
+    // address for the group) and takes hits gl and gl + G of each 2G
+    const int b0 = ri.bin0 + bx.iy0 * ri.nz + bx.iz0;
+    const int a = ld<NC>(b.first + b0);
+    const int total = ld<NC>(b.first + b0 + span) - a;
+    for (int kk = g.gl; kk < total; kk += 2 * G) {
+      const int h0 = a + kk, h1 = a + kk + G;
+      const bool two = kk + G < total;
+      const int4 q0 = ld<NC>(b.s_hit + h0);
+      int4 q1 = q0;
+      if (two) q1 = ld<NC>(b.s_hit + h1);
+      consider(h0, q0);
+      if (two) consider(h1, q1);
+    }
   } else {
     for (int base = 0; base < nyb; base += G) {  // group-uniform loop
       // one y-bin row per lane: its hit range [a, a + cnt)
@@ -1034,6 +1053,8 @@ __device__ __forceinline__ int pick_box(const Buffers& b, const Grp<G>& g, const
           if (h2[t] >= 0) consider(h2[t], q2[t]);
       }
     }
+  }
+  if constexpr (G > 1) {
     const unsigned long long gbest = g.min64(best);
     if (gbest == ~0ull) return -1;
     const unsigned who = __ballot_sync(g.mask, best == gbest) & g.mask;
@@ -1044,12 +1065,12 @@ __device__ __forceinline__ int pick_box(const Buffers& b, const Grp<G>& g, const
     qout->w = g.shfl(best_q.w, src);
     return g.shfl(best_pos, src);
   }
+  return -1;  // not reached: every branch above returns
 }
 
 template <int G, bool NC>
 __device__ __forceinline__ int pick_hit(const Buffers& b, const Grp<G>& g, const RowInfo& ri, const float* p,
-                                        const float* C, int z_base, int4* qout) {
-  const Win w = make_win(b.par, C);
+                                        const Win& w, int z_base, int4* qout) {
   const Box bx = row_box(ri, p[0], p[1], w.wy, w.wz, z_base);
   return pick_box<G, NC>(b, g, ri, bx, p, w, z_base, qout);
 }
@@ -1142,12 +1163,13 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
     if (!kf_propagate(P, p, C, x, xn)) break;
     x = xn;
     if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) break;
-    if (!chain) h = pick_hit<G, NC>(b, g, ri, p, C, z_base, &q);
+    const Win w = make_win(P, C);
+    if (!chain) h = pick_hit<G, NC>(b, g, ri, p, w, z_base, &q);
     if (!chain && h < 0) {
       ++misses;
       continue;
     }
-    kf_update(P, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
+    kf_update(w, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
     if (!cov_ok(C)) {
       dead = true;
       break;
@@ -1232,12 +1254,13 @@ __device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g,
       x = xn;
       if (!(fabsf(q5[2]) < SIN_MAX) || fabsf(q5[0]) > x * P.tan_half) break;
       int4 q;
-      const int h = pick_hit<G, NC>(b, g, ri, q5, C, z_base, &q);
+      const Win w = make_win(P, C);
+      const int h = pick_hit<G, NC>(b, g, ri, q5, w, z_base, &q);
       if (h < 0) {
         ++misses;
         continue;
       }
-      chi2sum += kf_update(P, q5, C, q.x * Q - q5[0], (float)(q.y - z_base) * Q - q5[1]);
+      chi2sum += kf_update(w, q5, C, q.x * Q - q5[0], (float)(q.y - z_base) * Q - q5[1]);
       if (!cov_ok(C)) {
         dead = true;
         break;

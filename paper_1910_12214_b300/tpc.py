@@ -72,6 +72,7 @@ _sig = {
     "tpc_set_tuning": ([_P, C.POINTER(tpc_tuning)], C.c_int),
     "tpc_get_tuning": ([_P, C.POINTER(tpc_tuning)], C.c_int),
     "tpc_autotune": ([_P, C.c_int, C.POINTER(tpc_tuning), C.POINTER(C.c_float)], C.c_int),
+    "tpc_autotune_mode": ([_P, C.c_int, C.c_int, C.POINTER(tpc_tuning), C.POINTER(C.c_float)], C.c_int),
     "tpc_set_grid_correction": ([_P, _P, _P, C.c_uint32, C.c_int, C.c_int, C.c_int], C.c_int),
     "tpc_set_correction": ([_P, C.c_int], C.c_int),
     "tpc_surrogate_train": ([_P, C.c_uint64, C.c_uint64, C.c_int, C.c_float, C.POINTER(C.c_float),
@@ -243,10 +244,12 @@ class Tracker:
         self._check(_lib.tpc_get_tuning(self._h, C.byref(t)))
         return {f: getattr(t, f) for f, _ in tpc_tuning._fields_}
 
-    def autotune(self, iters: int = 3):
+    def autotune(self, iters: int = 3, mode: int = 0):
+        """Fastest launch shapes for the loaded batch (mode 1 = plain only,
+        2 = batched only, 0 = both); returns (tuning dict, microseconds)."""
         t = tpc_tuning()
         us = C.c_float()
-        self._check(_lib.tpc_autotune(self._h, iters, C.byref(t), C.byref(us)))
+        self._check(_lib.tpc_autotune_mode(self._h, iters, mode, C.byref(t), C.byref(us)))
         return {f: getattr(t, f) for f, _ in tpc_tuning._fields_}, float(us.value)
 
     def set_grid_correction(self, grid, bounds):
