@@ -709,7 +709,7 @@ extern "C" tpc_status tpc_autotune_mode(tpc_ctx* c, int iters, int mode, tpc_tun
     for (int blk : {32, 64, 128})
       for (int per_sm : {8, 16, 32}) cand.push_back({lanes, blk, per_sm, 0, 0, 1, 0, 0});
   for (int sm : {6 * 1024, 12 * 1024, 24 * 1024})
-    for (int lr : {-1, 4, 16, 152}) cand.push_back({0, 0, 0, sm, lr, 1, 0, 0});
+    for (int lr : {-1, 1, 2, 4, 16, 152}) cand.push_back({0, 0, 0, sm, lr, 1, 0, 0});
   for (int bl : {1, 2, 4}) cand.push_back({0, 0, 0, 0, 0, 2, bl, 0});
   if (mode) {  // only the shapes of one mode
     std::vector<tpc_tuning> keep;

@@ -42,10 +42,10 @@ constexpr int MIN_HITS = 10;
 constexpr int SHIFT_MIN = 10;
 constexpr long long LINK_D = 512;       // 0.5 cm chord deviation
 constexpr float INFLATE = 100.0f;       // covariance inflation of the inward refit
-constexpr int LINK_THREADS = 128;
+constexpr int LINK_THREADS = 256;
 constexpr int LINK_MAXC = 24;           // window candidates per side and hit
-constexpr int LINK_MAXC_STAGED = 12;    // the same in k_links (overflow: direct enumeration)
-constexpr int LINK_STAGE_MAX = 96 * 1024;  // shared-memory staging of k_links
+constexpr int LINK_MAXC_STAGED = 8;     // the same in k_links (overflow: direct enumeration)
+constexpr int LINK_STAGE_MAX = 160 * 1024;  // shared-memory staging of k_links
 
 __device__ __forceinline__ int warp_incl_scan(int v) {
   const int lane = threadIdx.x & 31;
@@ -366,10 +366,14 @@ struct GlobalSrc {
 };
 
 struct StageSrc {
-  const int4* h;
+  const int2* q;   // (qy, qz)
+  const int* id;   // original id
   const int* f;
   int p_lo, f_lo;
-  __device__ __forceinline__ int4 hit(int p) const { return h[p - p_lo]; }
+  __device__ __forceinline__ int4 hit(int p) const {
+    const int2 v = q[p - p_lo];
+    return make_int4(v.x, v.y, id[p - p_lo], 0);
+  }
   __device__ __forceinline__ int first(int i) const { return f[i - f_lo]; }
 };
 
@@ -501,7 +505,7 @@ template <bool W32>
 __global__ void __launch_bounds__(LINK_THREADS) k_links(const __grid_constant__ Buffers b, int rows_per_cta,
                                                         int stage_bytes) {
   const DevParams& P = b.par;
-  extern __shared__ int4 s_stage[];
+  extern __shared__ int2 s_stage[];
   __shared__ RowInfo s_rows[TPC_MAX_ROWS + 2];
   __shared__ int s_cu[LINK_MAXC_STAGED][LINK_THREADS], s_cd[LINK_MAXC_STAGED][LINK_THREADS];
   const int NR = P.n_rows;
@@ -519,18 +523,24 @@ __global__ void __launch_bounds__(LINK_THREADS) k_links(const __grid_constant__ 
   const int p_lo = rl.pos0, p_hi = rh.pos0 + rh.n;
   const int f_lo = rl.bin0, f_hi = rh.bin0 + (rh.n > 0 ? rh.ny * rh.nz : 0) + 1;
   const int nh = p_hi - p_lo, nf = f_hi - f_lo;
-  const bool staged = (long long)nh * 16 + (long long)nf * 4 <= stage_bytes;
-  int* sf = reinterpret_cast<int*>(s_stage + (staged ? nh : 0));
+  // staged layout: (qy, qz) int2 [nh], id int [nh], bin index int [nf]
+  const bool staged = (long long)nh * 12 + (long long)nf * 4 <= stage_bytes;
+  int* sid = reinterpret_cast<int*>(s_stage + (staged ? nh : 0));
+  int* sf = sid + (staged ? nh : 0);
   if (staged) {
-    for (int i = threadIdx.x; i < nh; i += blockDim.x) s_stage[i] = __ldg(b.s_hit + p_lo + i);
+    for (int i = threadIdx.x; i < nh; i += blockDim.x) {
+      const int4 v = __ldg(b.s_hit + p_lo + i);
+      s_stage[i] = make_int2(v.x, v.y);
+      sid[i] = v.z;
+    }
     for (int i = threadIdx.x; i < nf; i += blockDim.x) sf[i] = __ldg(b.first + f_lo + i);
   }
   __syncthreads();
   const int t = threadIdx.x;
-  const StageSrc SS{s_stage, sf, p_lo, f_lo};
+  const StageSrc SS{s_stage, sid, sf, p_lo, f_lo};
   const GlobalSrc GS{b.s_hit, b.first};
   for (int pos = p_begin + t; pos < p_end; pos += blockDim.x) {
-    const int4 qh = staged ? s_stage[pos - p_lo] : b.s_hit[pos];
+    const int4 qh = __ldg(b.s_hit + pos);
     const int r = qh.w - item * NR;
     if (r == 0 || r == NR - 1) {
       b.up_raw[pos] = -1;
@@ -949,54 +959,19 @@ __device__ __forceinline__ int pick_box(const Buffers& b, const Grp<G>& g, const
       best_q = q;
     }
   };
-  if constexpr (G == 1 && !NC) {
-    // inside the persistent kernel: a plain scan (fewer registers)
+  if constexpr (G == 1) {
+    // one lane: a plain scan, two hit loads in flight (batching more loads
+    // per step did not shorten the step and costs registers)
     for (int iy = bx.iy0; iy <= bx.iy1; ++iy) {
       const int b0 = ri.bin0 + iy * ri.nz + bx.iz0;
       const int a = ld<NC>(b.first + b0), e = ld<NC>(b.first + b0 + span);
       int h = a;
-      for (; h + 1 < e; h += 2) {  // two loads in flight
+      for (; h + 1 < e; h += 2) {
         const int4 q0 = ld<NC>(b.s_hit + h), q1 = ld<NC>(b.s_hit + h + 1);
         consider(h, q0);
         consider(h + 1, q1);
       }
       if (h < e) consider(h, ld<NC>(b.s_hit + h));
-    }
-    *qout = best_q;
-    return best_pos;
-  } else if constexpr (G == 1) {
-    // The hit ranges of up to NYP y-bin rows are fetched together, then up to
-    // CB candidate hits together.
-    constexpr int NYP = 4, CB = 8;
-    int ra[NYP], nk[NYP];
-#pragma unroll
-    for (int k = 0; k < NYP; ++k) {
-      ra[k] = 0;
-      nk[k] = 0;
-      if (k < nyb) {
-        const int b0 = ri.bin0 + (bx.iy0 + k) * ri.nz + bx.iz0;
-        ra[k] = ld<NC>(b.first + b0);
-        nk[k] = ld<NC>(b.first + b0 + span) - ra[k];
-      }
-    }
-    const int c1 = nk[0], c2 = c1 + nk[1], c3 = c2 + nk[2], total = c3 + nk[3];
-    // candidate j of the concatenated ranges
-    auto pos_of = [&](int j) {
-      return j < c1 ? ra[0] + j : j < c2 ? ra[1] + (j - c1) : j < c3 ? ra[2] + (j - c2) : ra[3] + (j - c3);
-    };
-    for (int j0 = 0; j0 < total; j0 += CB) {
-      int4 qb[CB];
-#pragma unroll
-      for (int j = 0; j < CB; ++j)
-        if (j0 + j < total) qb[j] = ld<NC>(b.s_hit + pos_of(j0 + j));
-#pragma unroll
-      for (int j = 0; j < CB; ++j)
-        if (j0 + j < total) consider(pos_of(j0 + j), qb[j]);
-    }
-    for (int iy = bx.iy0 + NYP; iy <= bx.iy1; ++iy) {  // wider windows (rare)
-      const int b0 = ri.bin0 + iy * ri.nz + bx.iz0;
-      const int a = ld<NC>(b.first + b0), e = ld<NC>(b.first + b0 + span);
-      for (int h = a; h < e; ++h) consider(h, ld<NC>(b.s_hit + h));
     }
     *qout = best_q;
     return best_pos;
@@ -1911,11 +1886,12 @@ cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t 
     // default: 8 rows per CTA (measured best between 4 for one event and 16 for 64 events)
     const int rpc = c.link_rows > 0 ? std::min(c.link_rows, NR) : std::min(8, NR);
     const int nrb = (NR + rpc - 1) / rpc;
-    // staging room for the block's rows at up to 1.5 times the mean row
-    // occupancy (hits 16 B; bin index about one entry per hit, at most 2n + 3);
+    // staging room for the block's rows at up to 1.25 times the mean row
+    // occupancy (hits 12 B; bin index about one entry per hit, at most 2n + 3);
     // blocks with denser rows read global memory
     const long long avg = (b.N + (long long)b.I * NR - 1) / std::max(1LL, (long long)b.I * NR);
-    long long stage = (long long)(rpc + 2) * (16 * (3 * avg / 2) + 4 * (2 * avg + 4)) + 64;
+    const long long n125 = (5 * avg + 3) / 4;
+    long long stage = (long long)(rpc + 2) * (12 * n125 + 4 * (n125 + 4)) + 64;
     stage = std::min<long long>(LINK_STAGE_MAX, std::max<long long>(4096, (stage + 15) / 16 * 16));
     int max_dx = 0;
     for (int r = 0; r + 1 < NR; ++r) max_dx = std::max(max_dx, b.par.qx[r + 1] - b.par.qx[r]);
