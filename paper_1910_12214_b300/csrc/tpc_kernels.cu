@@ -901,6 +901,20 @@ __device__ __forceinline__ RowInfo load_row(const RowInfo* p) {
   }
 }
 
+// Where a tracklet reads its item's row table, bin index, sorted hits and clean
+// up-links.  `r` is the pad row of the position read (it selects the CTA that
+// holds it in the cluster form).
+template <bool NC>
+struct GSrc {  // global memory; NC: data written by an earlier launch
+  const Buffers* b;
+  const RowInfo* rows;  // the item's row table (global, or shared memory)
+  __device__ __forceinline__ RowInfo row(int r) const { return load_row<NC>(rows + r); }
+  __device__ __forceinline__ int first(int, int f) const { return ld<NC>(b->first + f); }
+  __device__ __forceinline__ int4 hit(int, int p) const { return ld<NC>(b->s_hit + p); }
+  __device__ __forceinline__ int up(int, int p) const { return ld<NC>(b->up + p); }
+};
+
+
 // Bins [iy0, iy1] x [iz0, iz1] of a row's grid covered by the box
 // yc +- wy, zc +- wz (cm, z relative to z_base) widened by 2 quanta; empty
 // (iy1 < iy0 or iz1 < iz0) if it misses the grid or the row has no hits.
@@ -941,8 +955,8 @@ __device__ __forceinline__ unsigned long long hit_key(const int4& q, const float
 // (max(0.5 cm, 4 sigma) plus 2 quanta) contains every hit with chi2 <= 16, so
 // the box never changes the result.  Every lane of the group returns the same
 // position and the hit's (qy, qz, id, key) in *qout.
-template <int G, bool NC>
-__device__ __forceinline__ int pick_box(const Buffers& b, const Grp<G>& g, const RowInfo& ri, const Box& bx,
+template <int G, class Src>
+__device__ __forceinline__ int pick_box(const Src& S, const Grp<G>& g, int r, const RowInfo& ri, const Box& bx,
                                         const float* p, const Win& w, int z_base, int4* qout) {
   if (box_empty(bx)) return -1;
   // the bins (iy, iz0..iz1) of one y-bin row are contiguous: one hit range each
@@ -964,14 +978,14 @@ __device__ __forceinline__ int pick_box(const Buffers& b, const Grp<G>& g, const
     // per step did not shorten the step and costs registers)
     for (int iy = bx.iy0; iy <= bx.iy1; ++iy) {
       const int b0 = ri.bin0 + iy * ri.nz + bx.iz0;
-      const int a = ld<NC>(b.first + b0), e = ld<NC>(b.first + b0 + span);
+      const int a = S.first(r, b0), e = S.first(r, b0 + span);
       int h = a;
       for (; h + 1 < e; h += 2) {
-        const int4 q0 = ld<NC>(b.s_hit + h), q1 = ld<NC>(b.s_hit + h + 1);
+        const int4 q0 = S.hit(r, h), q1 = S.hit(r, h + 1);
         consider(h, q0);
         consider(h + 1, q1);
       }
-      if (h < e) consider(h, ld<NC>(b.s_hit + h));
+      if (h < e) consider(h, S.hit(r, h));
     }
     *qout = best_q;
     return best_pos;
@@ -979,14 +993,14 @@ __device__ __forceinline__ int pick_box(const Buffers& b, const Grp<G>& g, const
     // one y-bin row (the usual case): every lane reads its hit range (one
     // address for the group) and takes hits gl and gl + G of each 2G
     const int b0 = ri.bin0 + bx.iy0 * ri.nz + bx.iz0;
-    const int a = ld<NC>(b.first + b0);
-    const int total = ld<NC>(b.first + b0 + span) - a;
+    const int a = S.first(r, b0);
+    const int total = S.first(r, b0 + span) - a;
     for (int kk = g.gl; kk < total; kk += 2 * G) {
       const int h0 = a + kk, h1 = a + kk + G;
       const bool two = kk + G < total;
-      const int4 q0 = ld<NC>(b.s_hit + h0);
+      const int4 q0 = S.hit(r, h0);
       int4 q1 = q0;
-      if (two) q1 = ld<NC>(b.s_hit + h1);
+      if (two) q1 = S.hit(r, h1);
       consider(h0, q0);
       if (two) consider(h1, q1);
     }
@@ -997,8 +1011,8 @@ __device__ __forceinline__ int pick_box(const Buffers& b, const Grp<G>& g, const
       int a = 0, cnt = 0;
       if (j < nyb) {
         const int b0 = ri.bin0 + (bx.iy0 + j) * ri.nz + bx.iz0;
-        a = ld<NC>(b.first + b0);
-        cnt = ld<NC>(b.first + b0 + span) - a;
+        a = S.first(r, b0);
+        cnt = S.first(r, b0 + span) - a;
       }
       const int inc = g.incl_scan(cnt);
       const int ex = inc - cnt;
@@ -1021,7 +1035,7 @@ __device__ __forceinline__ int pick_box(const Buffers& b, const Grp<G>& g, const
           const int a_src = g.shfl(a, lo);
           const int ex_src = g.shfl(ex, lo);
           h2[t] = k < total ? a_src + (k - ex_src) : -1;
-          if (h2[t] >= 0) q2[t] = ld<NC>(b.s_hit + h2[t]);
+          if (h2[t] >= 0) q2[t] = S.hit(r, h2[t]);
         }
 #pragma unroll
         for (int t = 0; t < 2; ++t)
@@ -1043,11 +1057,11 @@ __device__ __forceinline__ int pick_box(const Buffers& b, const Grp<G>& g, const
   return -1;  // not reached: every branch above returns
 }
 
-template <int G, bool NC>
-__device__ __forceinline__ int pick_hit(const Buffers& b, const Grp<G>& g, const RowInfo& ri, const float* p,
+template <int G, class Src>
+__device__ __forceinline__ int pick_hit(const Src& S, const Grp<G>& g, int r, const RowInfo& ri, const float* p,
                                         const Win& w, int z_base, int4* qout) {
   const Box bx = row_box(ri, p[0], p[1], w.wy, w.wz, z_base);
-  return pick_box<G, NC>(b, g, ri, bx, p, w, z_base, qout);
+  return pick_box<G>(S, g, r, ri, bx, p, w, z_base, qout);
 }
 
 }  // namespace
@@ -1071,13 +1085,12 @@ __device__ __forceinline__ int pick_hit(const Buffers& b, const Grp<G>& g, const
 // same propagation and update code together).  The result goes to b.tlu[tl] and
 // the tracklet claims its outermost hit (smallest tracklet index wins); `local`
 // is the item-local id, `rows` the item's row table, `xr` the row positions.
-template <int G, bool NC>
-__device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, const RowInfo* rows, const float* xr,
-                                            int start, int tl, int local) {
+template <int G, class Src>
+__device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, const Src& S, const float* xr,
+                                            int start, int4 hs, int tl, int local) {
   const DevParams& P = b.par;
   const int NR = P.n_rows;
   const float Q = 1.0f / TPC_QSCALE;
-  const int4 hs = ld<NC>(b.s_hit + start);
   const int key = hs.w;
   const int item = key / NR;
   const int r0 = key - item * NR;
@@ -1085,7 +1098,7 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
   int* hl = b.tl_hits + (size_t)tl * NR;
   // chain walk (pointer chasing; every lane of the group loads the same address)
   int L = 0, last = start;
-  for (int h = start; h >= 0 && L < NR; h = ld<NC>(b.up + h)) {
+  for (int h = start; h >= 0 && L < NR; h = S.up(r0 + L - 1, h)) {
     if (g.gl == 0) hl[L] = h;
     last = h;
     ++L;
@@ -1093,7 +1106,7 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
   g.sync();
   const int hmid = hl[L / 2];
   const int hn0 = L > 1 ? hl[1] : start, hn1 = L > 2 ? hl[2] : start;
-  const int4 qa = hs, qm = ld<NC>(b.s_hit + hmid), qc = ld<NC>(b.s_hit + last);
+  const int4 qa = hs, qm = S.hit(r0 + L / 2, hmid), qc = S.hit(r0 + L - 1, last);
   const float x1 = xr[r0], x2 = xr[r0 + L / 2], x3 = xr[r0 + L - 1];
   const float y1 = qa.x * Q, y2 = qm.x * Q, y3 = qc.x * Q;
   const float z3 = (float)(qc.y - z_base) * Q;
@@ -1117,7 +1130,7 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
   // the next chain hit (position and coordinates) and the one after it are
   // fetched one row ahead of their use
   int hn = hn0, hn2 = hn1;
-  int4 qn = ld<NC>(b.s_hit + hn);
+  int4 qn = S.hit(L > 1 ? r0 + 1 : r0, hn);
   int misses = 0;
   for (int r = r0 + 1; r < NR && misses < MAX_MISS; ++r) {
     const int i = r - r0;  // chain index of row r
@@ -1126,12 +1139,12 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
     int4 q = make_int4(0, 0, 0, 0);
     // the row table entry is fetched for every row (one 32-byte load, off the
     // dependency chain) so that it lives in registers
-    const RowInfo ri = load_row<NC>(rows + r);
+    const RowInfo ri = S.row(r);
     if (chain) {
       h = hn;
       q = qn;
       hn = hn2;
-      if (i + 1 < L) qn = ld<NC>(b.s_hit + hn);
+      if (i + 1 < L) qn = S.hit(r + 1, hn);
       if (i + 2 < L) hn2 = hl[i + 2];
     }
     const float xn = xr[r];
@@ -1139,7 +1152,7 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
     x = xn;
     if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) break;
     const Win w = make_win(P, C);
-    if (!chain) h = pick_hit<G, NC>(b, g, ri, p, w, z_base, &q);
+    if (!chain) h = pick_hit<G>(S, g, r, ri, p, w, z_base, &q);
     if (!chain && h < 0) {
       ++misses;
       continue;
@@ -1182,17 +1195,17 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
 // smallest tracklet that reached its outermost hit (the others are dropped):
 // the record goes to b.tl[tl] and the hit list to b.tl_hits[tl * n_rows ...].
 // `rows` is the row table of the tracklet's item, or null for the global one.
-template <int G, bool NC>
-__device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g, const RowInfo* rows,
-                                              const float* xr, int tl) {
+template <int G, class Src>
+__device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g, const Src& S, const float* xr,
+                                              int tl) {
   const DevParams& P = b.par;
   const int NR = P.n_rows;
   const float Q = 1.0f / TPC_QSCALE;
   const TrackletUp u = b.tlu[tl];
   const int item = u.item, local = u.local, z_base = u.z_base;
   const int out_hit = u.out_hit, out_row = u.out_row;
-  bool dead = out_hit < 0 || b.out_owner[out_hit] != tl;
-  if (!rows) rows = b.rows + (size_t)item * NR;
+  // claims of other threads of the previous launch: read from L2
+  bool dead = out_hit < 0 || __ldcg(b.out_owner + out_hit) != tl;
   int* hl = b.tl_hits + (size_t)tl * NR;
   const float out_p[5] = {0.f, 0.f, u.snp, u.tgl, u.qpt};
   const float ov2 = u.v2, ov3 = u.v3, ov4 = u.v4;
@@ -1207,7 +1220,7 @@ __device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g,
   if (!dead) {
     // (iii) inward refit from the outermost hit: its y, z; the outward direction
     // and curvature with variances inflated 100-fold (capped at the initial ones)
-    const int4 qo = ld<NC>(b.s_hit + out_hit);
+    const int4 qo = S.hit(out_row, out_hit);
     float q5[5] = {qo.x * Q, (float)(qo.y - z_base) * Q, out_p[2], out_p[3], out_p[4]};
     set_c0(P, C);
     C[ix(2, 2)] = fminf(1.0f, INFLATE * ov2);
@@ -1223,14 +1236,14 @@ __device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g,
     for (int m = 0; m < 15; ++m) in_C[m] = C[m];
     int misses = 0;
     for (int r = out_row - 1; r >= 0 && misses < MAX_MISS; --r) {
-      const RowInfo ri = load_row<NC>(rows + r);  // independent of the state: in flight during the step
+      const RowInfo ri = S.row(r);  // independent of the state: in flight during the step
       const float xn = xr[r];
       if (!kf_propagate(P, q5, C, x, xn)) break;
       x = xn;
       if (!(fabsf(q5[2]) < SIN_MAX) || fabsf(q5[0]) > x * P.tan_half) break;
       int4 q;
       const Win w = make_win(P, C);
-      const int h = pick_hit<G, NC>(b, g, ri, q5, w, z_base, &q);
+      const int h = pick_hit<G>(S, g, r, ri, q5, w, z_base, &q);
       if (h < 0) {
         ++misses;
         continue;
@@ -1286,8 +1299,10 @@ __global__ void __launch_bounds__(128) k_tracklets_up(const __grid_constant__ Bu
   const int ngrp = (gridDim.x * blockDim.x) / G;
   for (int t = grp; t < T; t += ngrp) {
     const int start = b.starts[t];
-    const int item = __ldg(&b.s_hit[start].w) / NR;
-    tracklet_up<G, true>(b, g, b.rows + (size_t)item * NR, s_x, start, t, t - b.start_ex[b.item_off[item]]);
+    const int4 hs = __ldg(b.s_hit + start);
+    const int item = hs.w / NR;
+    const GSrc<true> S{&b, b.rows + (size_t)item * NR};
+    tracklet_up<G>(b, g, S, s_x, start, hs, t, t - b.start_ex[b.item_off[item]]);
   }
 }
 
@@ -1300,12 +1315,17 @@ __global__ void __launch_bounds__(128) k_tracklets_down(const __grid_constant__ 
   const int T = b.start_ex[b.N];
   const int grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
   const int ngrp = (gridDim.x * blockDim.x) / G;
-  for (int t = grp; t < T; t += ngrp) tracklet_down<G, true>(b, g, nullptr, s_x, t);
+  for (int t = grp; t < T; t += ngrp) {
+    const GSrc<true> S{&b, b.rows + (size_t)b.tlu[t].item * b.par.n_rows};
+    tracklet_down<G>(b, g, S, s_x, t);
+  }
 }
 
-cudaError_t tpc_launch_tracklets(const Buffers& b, int group, int grid, int block, cudaStream_t s) {
+
+cudaError_t tpc_launch_tracklets(const Buffers& b, const LaunchCfg& c, cudaStream_t s) {
   cudaMemsetAsync(b.out_owner, 0x7F, sizeof(int) * (size_t)b.N, s);
-  switch (group) {
+  const int grid = c.grid_tl, block = c.block_tl;
+  switch (c.tl_group) {
 #define TPC_TL(GG)                                        \
   case GG:                                                \
     k_tracklets_up<GG><<<grid, block, 0, s>>>(b);         \
@@ -1661,9 +1681,13 @@ __global__ void __launch_bounds__(BT) k_batched(const __grid_constant__ Buffers 
     const int ntl = s_ntl;
     // ---- S6: tracklets, a group of G lanes each: outward passes, then one
     // inward refit per outermost hit
-    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_up<G, false>(b, g, s_rows, s_x, b.starts[tlb + t], tlb + t, t);
+    const GSrc<false> S{&b, s_rows};
+    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) {
+      const int start = b.starts[tlb + t];
+      tracklet_up<G>(b, g, S, s_x, start, b.s_hit[start], tlb + t, t);
+    }
     __syncthreads();
-    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_down<G, false>(b, g, s_rows, s_x, tlb + t);
+    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_down<G>(b, g, S, s_x, tlb + t);
     __syncthreads();
     // ---- S7: ownership
     for (int t = warp; t < ntl; t += nwarps) select_max_warp(b, tlb + t, lane);
@@ -1906,7 +1930,7 @@ cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t 
   scan_i32(b.flags, b.start_ex, b.N, b.scan_tmp, c.grid_scan, s);
   k_starts<<<gN > 0 ? gN : 1, 256, 0, s>>>(b);
   mark(6);
-  tpc_launch_tracklets(b, c.tl_group, c.grid_tl, c.block_tl, s);
+  tpc_launch_tracklets(b, c, s);
   mark(7);
   k_select_max<<<c.num_sms * 4, 256, 0, s>>>(b);
   k_select_own<<<c.num_sms * 4, 256, 0, s>>>(b);
