@@ -178,6 +178,37 @@ def cpu_baseline(name: str, budget_s: float = 12.0):
             "sample": f"{runs} full events of workload {name} ({cl.n} clusters each), single-threaded FP64"}
 
 
+def _oracle_share(args):
+    """Worker of the all-cores baseline: the oracle on one share of the items."""
+    name, items, reps = args
+    import oracle
+    from paper_1910_12214_b300 import shard
+    cl = make_workload(name, 0)
+    sub, _ = shard.take_items(cl, items)
+    best = float("inf")
+    for _ in range(reps):
+        t0 = time.perf_counter()
+        oracle.run(sub, what=["trk_i"])
+        best = min(best, time.perf_counter() - t0)
+    return best, sub.n
+
+
+def cpu_baseline_all_cores(name: str, reps: int = 2):
+    """The same oracle, one single-threaded instance per host core, each on an
+    LPT share of the event's items (spawned processes; each times its own run;
+    the event takes as long as the slowest share)."""
+    from paper_1910_12214_b300 import shard, synth
+    cl = make_workload(name, 0)
+    cores = os.cpu_count() or 1
+    parts = [p for p in shard.lpt_partition(shard.item_costs(cl), min(cores, cl.n_items)) if p.size]
+    with mp.get_context("spawn").Pool(len(parts)) as pool:
+        res = pool.map(_oracle_share, [(name, p, reps) for p in parts])
+    t = max(r[0] for r in res)
+    return {"value": cl.n / t, "unit": "clusters/s", "cores": len(parts), "kind": "oracle",
+            "sample": f"one event of workload {name} ({cl.n} clusters, {cl.n_items} items) split over "
+                      f"{len(parts)} single-threaded oracle processes, best of {reps}"}
+
+
 def run_reference(args, rank, world):
     if rank != 0:
         return
@@ -340,6 +371,7 @@ def main():
         }
         if not args.no_cpu_baseline:
             line["cpu_baseline"] = cpu_baseline(args.workload)
+            line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.workload)
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
