@@ -859,13 +859,16 @@ struct Grp {
     }
     return v;
   }
+  // minimum of a 64-bit key over the group: two warp reductions (high word,
+  // then low word among the lanes holding the smallest high word)
   __device__ __forceinline__ unsigned long long min64(unsigned long long v) const {
-#pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) {
-      const unsigned long long w = __shfl_xor_sync(mask, v, o, G);
-      v = w < v ? w : v;
+    if constexpr (G == 1) {
+      return v;
+    } else {
+      const unsigned hi = __reduce_min_sync(mask, (unsigned)(v >> 32));
+      const unsigned lo = __reduce_min_sync(mask, (unsigned)(v >> 32) == hi ? (unsigned)v : 0xFFFFFFFFu);
+      return ((unsigned long long)hi << 32) | lo;
     }
-    return v;
   }
   __device__ __forceinline__ void sync() const {
     if constexpr (G > 1) __syncwarp(mask);
