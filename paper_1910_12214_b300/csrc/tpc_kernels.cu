@@ -977,18 +977,50 @@ __device__ __forceinline__ int pick_box(const Src& S, const Grp<G>& g, int r, co
     }
   };
   if constexpr (G == 1) {
-    // one lane: a plain scan, two hit loads in flight (batching more loads
-    // per step did not shorten the step and costs registers)
-    for (int iy = bx.iy0; iy <= bx.iy1; ++iy) {
-      const int b0 = ri.bin0 + iy * ri.nz + bx.iz0;
-      const int a = S.first(r, b0), e = S.first(r, b0 + span);
-      int h = a;
-      for (; h + 1 < e; h += 2) {
-        const int4 q0 = S.hit(r, h), q1 = S.hit(r, h + 1);
-        consider(h, q0);
-        consider(h + 1, q1);
+    // one lane: the hit ranges of the first two y-bin rows (windows rarely
+    // cover more), then the candidates four at a time: four loads in flight,
+    // four keys formed independently and reduced by a tree before the one
+    // compare with the running best (short dependency chains: the step's
+    // time is issue latency more than memory latency)
+    const int b0 = ri.bin0 + bx.iy0 * ri.nz + bx.iz0;
+    const int a0 = S.first(r, b0), e0 = S.first(r, b0 + span);
+    int a1 = 0, e1 = 0;
+    if (nyb > 1) {
+      a1 = S.first(r, b0 + ri.nz);
+      e1 = S.first(r, b0 + ri.nz + span);
+    }
+    const int n0 = e0 - a0, total = n0 + (e1 - a1);
+    for (int j0 = 0; j0 < total; j0 += 4) {
+      int pos[4];
+      int4 qk[4];
+      unsigned long long key[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int j = j0 + k;
+        pos[k] = j < n0 ? a0 + j : a1 + (j - n0);
+        if (j < total) qk[k] = S.hit(r, pos[k]);
       }
-      if (h < e) consider(h, S.hit(r, h));
+#pragma unroll
+      for (int k = 0; k < 4; ++k) key[k] = j0 + k < total ? hit_key(qk[k], p, w, z_base) : ~0ull;
+      const bool b01 = key[1] < key[0], b23 = key[3] < key[2];
+      const unsigned long long k01 = b01 ? key[1] : key[0], k23 = b23 ? key[3] : key[2];
+      const bool hi = k23 < k01;
+      const int im = hi ? (b23 ? 3 : 2) : (b01 ? 1 : 0);
+      const unsigned long long km = hi ? k23 : k01;
+      if (km < best) {
+        best = km;
+#pragma unroll
+        for (int k = 0; k < 4; ++k)
+          if (im == k) {
+            best_pos = pos[k];
+            best_q = qk[k];
+          }
+      }
+    }
+    for (int iy = bx.iy0 + 2; iy <= bx.iy1; ++iy) {  // wider windows (rare)
+      const int b1 = ri.bin0 + iy * ri.nz + bx.iz0;
+      const int a = S.first(r, b1), e = S.first(r, b1 + span);
+      for (int h = a; h < e; ++h) consider(h, S.hit(r, h));
     }
     *qout = best_q;
     return best_pos;
@@ -1004,8 +1036,15 @@ __device__ __forceinline__ int pick_box(const Src& S, const Grp<G>& g, int r, co
       const int4 q0 = S.hit(r, h0);
       int4 q1 = q0;
       if (two) q1 = S.hit(r, h1);
-      consider(h0, q0);
-      if (two) consider(h1, q1);
+      const unsigned long long k0 = hit_key(q0, p, w, z_base);
+      const unsigned long long k1 = two ? hit_key(q1, p, w, z_base) : ~0ull;
+      const bool second = k1 < k0;
+      const unsigned long long km = second ? k1 : k0;
+      if (km < best) {
+        best = km;
+        best_pos = second ? h1 : h0;
+        best_q = second ? q1 : q0;
+      }
     }
   } else {
     for (int base = 0; base < nyb; base += G) {  // group-uniform loop
