@@ -909,6 +909,9 @@ __device__ __forceinline__ RowInfo load_row(const RowInfo* p) {
 // holds it in the cluster form).
 template <bool NC>
 struct GSrc {  // global memory; NC: data written by an earlier launch
+  // candidates per round of the single-lane search: 8 for the plain kernels,
+  // 4 in the persistent kernel (whose other phases need the registers)
+  static constexpr int kRound = NC ? 8 : 4;
   const Buffers* b;
   const RowInfo* rows;  // the item's row table (global, or shared memory)
   __device__ __forceinline__ RowInfo row(int r) const { return load_row<NC>(rows + r); }
@@ -990,27 +993,41 @@ __device__ __forceinline__ int pick_box(const Src& S, const Grp<G>& g, int r, co
       e1 = S.first(r, b0 + ri.nz + span);
     }
     const int n0 = e0 - a0, total = n0 + (e1 - a1);
-    for (int j0 = 0; j0 < total; j0 += 4) {
-      int pos[4];
-      int4 qk[4];
-      unsigned long long key[4];
+    // candidates CB at a time (the warp runs as many rounds as its lane with
+    // the most candidates: a wide round keeps that count at one); keys of
+    // four slots at a time reduced by a tree, one compare with the running best
+    constexpr int CB = Src::kRound;
+    const int off1 = a1 - n0;  // candidate j is at a0 + j below n0, else at off1 + j
+    for (int j0 = 0; j0 < total; j0 += CB) {
+      int pos[CB];
+      int4 qk[CB];
 #pragma unroll
-      for (int k = 0; k < 4; ++k) {
+      for (int k = 0; k < CB; ++k) {
         const int j = j0 + k;
-        pos[k] = j < n0 ? a0 + j : a1 + (j - n0);
+        pos[k] = j + (j < n0 ? a0 : off1);
         if (j < total) qk[k] = S.hit(r, pos[k]);
       }
+      unsigned long long km = ~0ull;
+      int im = 0;
 #pragma unroll
-      for (int k = 0; k < 4; ++k) key[k] = j0 + k < total ? hit_key(qk[k], p, w, z_base) : ~0ull;
-      const bool b01 = key[1] < key[0], b23 = key[3] < key[2];
-      const unsigned long long k01 = b01 ? key[1] : key[0], k23 = b23 ? key[3] : key[2];
-      const bool hi = k23 < k01;
-      const int im = hi ? (b23 ? 3 : 2) : (b01 ? 1 : 0);
-      const unsigned long long km = hi ? k23 : k01;
+      for (int h4 = 0; h4 < CB; h4 += 4) {
+        unsigned long long key[4];
+#pragma unroll
+        for (int k = 0; k < 4; ++k) key[k] = j0 + h4 + k < total ? hit_key(qk[h4 + k], p, w, z_base) : ~0ull;
+        const bool b01 = key[1] < key[0], b23 = key[3] < key[2];
+        const unsigned long long k01 = b01 ? key[1] : key[0], k23 = b23 ? key[3] : key[2];
+        const bool hi = k23 < k01;
+        const unsigned long long kq = hi ? k23 : k01;
+        const int iq = h4 + (hi ? (b23 ? 3 : 2) : (b01 ? 1 : 0));
+        if (kq < km) {
+          km = kq;
+          im = iq;
+        }
+      }
       if (km < best) {
         best = km;
 #pragma unroll
-        for (int k = 0; k < 4; ++k)
+        for (int k = 0; k < CB; ++k)
           if (im == k) {
             best_pos = pos[k];
             best_q = qk[k];
