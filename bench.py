@@ -36,9 +36,9 @@ ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12
               "links": 16 + 8, "clean+starts": 8 + 8 + 4, "tracklets": 28, "selection": 20, "output": 8,
               "batched_items": 150, "batched_concat": 4}
 # DRAM bytes (read + write) of the dominant step per tracking step, from the ncu
-# capture summarised in profiles/k_tracklets_config2.md: k_tracklets_up 21.41 MB +
+# capture summarised in profiles/k_tracklets_config2.md: k_tracklets_up 21.53 MB +
 # k_tracklets_down 18.60 MB on the full-TPC workload; None = not captured.
-TRAFFIC = {("c2", "tracklets"): 40.0e6}
+TRAFFIC = {("c2", "tracklets"): 40.13e6}
 KERNELS_PER_STEP = {"plain": 19, "batched": 3}
 
 WORKLOADS = {
