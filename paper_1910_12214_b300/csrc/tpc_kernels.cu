@@ -1862,6 +1862,9 @@ __global__ void __launch_bounds__(256) k_correct_grid(const __grid_constant__ Bu
     if (threadIdx.x == 0 && ch.end > ch.begin) atomicOr(b.err, TPC_DERR_BAD_INPUT);
     return;
   }
+  __shared__ float s_x[TPC_MAX_ROWS];  // row positions (lanes read different rows)
+  for (int r = threadIdx.x; r < P.n_rows; r += blockDim.x) s_x[r] = P.x[r];
+  __syncthreads();
   const float* B = b.grid_bounds + 6 * sector;
   const float bx0 = B[0], sx = (b.grid_nx - 1) / (B[1] - B[0]);
   const float bv0 = B[2], sv = (b.grid_ny - 1) / (B[3] - B[2]);
@@ -1875,7 +1878,7 @@ __global__ void __launch_bounds__(256) k_correct_grid(const __grid_constant__ Bu
       b.cz[i] = z;
       continue;
     }
-    const float x = P.x[r];
+    const float x = s_x[r];
     const float v = y / (x * P.tan_half);
     float u[3] = {(x - bx0) * sx, (v - bv0) * sv, (z - bz0) * sz};
     const int dims[3] = {b.grid_nx, b.grid_ny, b.grid_nz};

@@ -52,6 +52,22 @@ __device__ __forceinline__ float counter_uniform(uint64_t seed, uint64_t a, uint
 
 __device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
 __device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
+
+// SiLU of the deployed network (inference and its residual evaluation):
+// z * sigmoid(z) = h + h tanh(h) with h = z / 2 and the hardware tanh (relative
+// error about 2^-11, below the BF16 rounding that follows); one special-function
+// operation instead of an exponential and a division.  (The BF16x2 form of the
+// hardware tanh was measured too coarse: trained-network residual 0.61 cm rms
+// instead of 0.02 cm.)
+__device__ __forceinline__ float tanh_hw(float x) {
+  float y;
+  asm("tanh.approx.f32 %0, %1;" : "=f"(y) : "f"(x));
+  return y;
+}
+__device__ __forceinline__ float silu_fast(float z) {
+  const float hz = 0.5f * z;
+  return fmaf(hz, tanh_hw(hz), hz);
+}
 __device__ __forceinline__ float dsilu(float z) {
   const float s = 1.0f / (1.0f + expf(-z));
   return s * (1.0f + z * (1.0f - s));
@@ -281,13 +297,13 @@ __global__ void __launch_bounds__(TB) k_mlp_eval(const __grid_constant__ MlpEval
   float a1[H];
 #pragma unroll
   for (int j = 0; j < H; ++j)
-    a1[j] = bf(silu(W[OB1 + j] + W[OW1 + 3 * j] * in[0] + W[OW1 + 3 * j + 1] * in[1] + W[OW1 + 3 * j + 2] * in[2]));
+    a1[j] = bf(silu_fast(W[OB1 + j] + W[OW1 + 3 * j] * in[0] + W[OW1 + 3 * j + 1] * in[1] + W[OW1 + 3 * j + 2] * in[2]));
   float o[3] = {W[OB3], W[OB3 + 1], W[OB3 + 2]};
   for (int j = 0; j < H; ++j) {
     float z2 = W[OB2 + j];
 #pragma unroll
     for (int i = 0; i < H; ++i) z2 += W[OW2 + H * j + i] * a1[i];
-    const float a2 = bf(silu(z2));
+    const float a2 = bf(silu_fast(z2));
 #pragma unroll
     for (int c = 0; c < 3; ++c) o[c] += W[OW3 + H * c + j] * a2;
   }
@@ -311,8 +327,9 @@ __global__ void __launch_bounds__(TB) k_mlp_eval(const __grid_constant__ MlpEval
 }
 
 // ---------------------------------------------------------------------------- inference
-// Per-sector inference copy: W2 in BF16 with padded rows (conflict-free
-// fragment loads), the other parameters as floats (weights BF16-rounded).
+// Per-sector inference copy: W2 in BF16 with padded rows (16-byte aligned rows
+// for ldmatrix, conflict-free), the other parameters as floats (weights
+// BF16-rounded, biases FP32).
 constexpr int W2S = 72;  // padded row stride of W2 in BF16 elements
 struct __align__(16) MlpInfer {
   __nv_bfloat16 w2[H * W2S];
@@ -346,6 +363,15 @@ __device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// four 8x8 BF16 matrices from shared memory (rows given by lanes 8j..8j+7 for
+// matrix j); lane l receives row l/4, columns 2(l%4) and 2(l%4)+1 of each
+__device__ __forceinline__ void ldmatrix_x4(uint32_t* r, const void* smem_row) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem_row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
 __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
   asm volatile(
       "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
@@ -355,11 +381,16 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
 }
 
 // One CTA per cluster chunk (one item): the sector's network in shared memory;
-// each warp takes 16 clusters at a time.  Fragment layout of m16n8k16 (lane =
-// 4 g + q): A rows g and g+8, columns 2q, 2q+1 and +8; B column g, rows 2q, 2q+1
-// and +8; accumulators rows g and g+8, columns 2q, 2q+1.
+// each warp takes 16 clusters at a time and runs all three layers on the
+// tensor cores (mma.sync m16n8k16, BF16 operands, FP32 accumulators starting
+// from the FP32 biases): layer 1 with K padded from 3 to 16, layer 3 with N
+// padded from 3 to 8; each layer's accumulators become the next layer's A
+// fragments in registers (after SiLU and BF16 rounding).  Fragment layout
+// (lane = 4 g + q): A rows g and g+8, columns 2q, 2q+1 and +8; B column g, rows
+// 2q, 2q+1 and +8; accumulators rows g and g+8, columns 2q, 2q+1.
 __global__ void __launch_bounds__(128) k_correct_mlp(const __grid_constant__ Buffers b) {
   __shared__ __align__(16) MlpInfer S;
+  __shared__ float s_x[TPC_MAX_ROWS];  // row positions (lanes read different rows)
   const DevParams& P = b.par;
   const Chunk ch = b.chunks[blockIdx.x];
   const int sector = b.item_sector ? (int)b.item_sector[ch.item] : 0;
@@ -371,13 +402,53 @@ __global__ void __launch_bounds__(128) k_correct_mlp(const __grid_constant__ Buf
     const int4* src = reinterpret_cast<const int4*>(reinterpret_cast<const MlpInfer*>(b.mlp) + sector);
     int4* dst = reinterpret_cast<int4*>(&S);
     for (int p = threadIdx.x; p < (int)(sizeof(MlpInfer) / 16); p += blockDim.x) dst[p] = src[p];
+    for (int r = threadIdx.x; r < P.n_rows; r += blockDim.x) s_x[r] = P.x[r];
   }
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int g = lane >> 2, q = lane & 3;
+  // per-lane B fragments of layers 1 and 3 (constant over the chunk)
+  uint32_t B1[8];  // n-tile t: rows 2q, 2q+1 of W1^T at unit 8t + g (inputs x, v | z, 0 | 0)
+#pragma unroll
+  for (int t = 0; t < 8; ++t) {
+    const int n = 8 * t + g;
+    B1[t] = q == 0 ? pack_bf2(S.w1[3 * n], S.w1[3 * n + 1]) : q == 1 ? pack_bf2(S.w1[3 * n + 2], 0.0f) : 0u;
+  }
+  uint32_t B3[4][2];  // k-step ks: output g (< 3) at hidden units 16 ks + 2q, +1 and +8, +9
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    const int k0 = 16 * ks + 2 * q;
+    B3[ks][0] = g < 3 ? pack_bf2(S.w3[64 * g + k0], S.w3[64 * g + k0 + 1]) : 0u;
+    B3[ks][1] = g < 3 ? pack_bf2(S.w3[64 * g + k0 + 8], S.w3[64 * g + k0 + 9]) : 0u;
+  }
+  // layer-3 accumulator start: the output biases at columns 2q, 2q+1 (3 outputs)
+  const float c3a = q == 0 ? S.b3[0] : q == 1 ? S.b3[2] : 0.0f;
+  const float c3b = q == 0 ? S.b3[1] : 0.0f;
   const float sx = 2.0f / (S.bounds[1] - S.bounds[0]), sv = 2.0f / (S.bounds[3] - S.bounds[2]);
   const float sz = 2.0f / (S.bounds[5] - S.bounds[4]);
+  // the cluster inputs of the two rows a lane touches are fetched one
+  // iteration ahead
+  int r_nx[2];
+  float y_nx[2], z_nx[2];
+  auto fetch = [&](int base) {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int i = base + g + 8 * h;
+      r_nx[h] = -1;
+      y_nx[h] = 0.f;
+      z_nx[h] = 0.f;
+      if (i < ch.end) {
+        r_nx[h] = __ldg(b.row + i);
+        y_nx[h] = __ldg(b.y + i);
+        z_nx[h] = __ldg(b.z + i);
+      }
+    }
+  };
+  fetch(ch.begin + warp * 16);
   for (int base = ch.begin + warp * 16; base < ch.end; base += 64) {
+    const int r_cur[2] = {r_nx[0], r_nx[1]};
+    const float y_cur[2] = {y_nx[0], y_nx[1]}, z_cur[2] = {z_nx[0], z_nx[1]};
+    fetch(base + 64);
     // normalised inputs of the two rows this lane touches
     float in[2][3];
     int idx[2];
@@ -386,82 +457,67 @@ __global__ void __launch_bounds__(128) k_correct_mlp(const __grid_constant__ Buf
     for (int h = 0; h < 2; ++h) {
       const int i = base + g + 8 * h;
       idx[h] = i;
-      ok[h] = i < ch.end;
+      const int r = r_cur[h];
+      ok[h] = i < ch.end && r >= 0 && r < P.n_rows;
       float x = 0.f, y = 0.f, z = 0.f;
       if (ok[h]) {
-        const int r = b.row[i];
-        ok[h] = r >= 0 && r < P.n_rows;
-        if (ok[h]) {
-          x = P.x[r];
-          y = b.y[i];
-          z = b.z[i];
-        }
+        x = s_x[r];
+        y = y_cur[h];
+        z = z_cur[h];
       }
       const float v = y / (x > 0.f ? x * P.tan_half : 1.0f);
-      in[h][0] = bf((x - S.bounds[0]) * sx - 1.0f);
-      in[h][1] = bf((v - S.bounds[2]) * sv - 1.0f);
-      in[h][2] = bf((z - S.bounds[4]) * sz - 1.0f);
+      in[h][0] = (x - S.bounds[0]) * sx - 1.0f;
+      in[h][1] = (v - S.bounds[2]) * sv - 1.0f;
+      in[h][2] = (z - S.bounds[4]) * sz - 1.0f;
     }
-    // layer 1 straight into the A fragments of the four k-steps
-    uint32_t A[4][4];
+    // layer 1: A = inputs (row g: x, v at q = 0, z at q = 1), K padded to 16
+    uint32_t A1[4];
+    A1[0] = q == 0 ? pack_bf2(in[0][0], in[0][1]) : q == 1 ? pack_bf2(in[0][2], 0.0f) : 0u;
+    A1[1] = q == 0 ? pack_bf2(in[1][0], in[1][1]) : q == 1 ? pack_bf2(in[1][2], 0.0f) : 0u;
+    A1[2] = 0u;
+    A1[3] = 0u;
+    uint32_t A[4][4];  // layer-2 A fragments
 #pragma unroll
-    for (int ks = 0; ks < 4; ++ks) {
-#pragma unroll
-      for (int half = 0; half < 2; ++half) {
-        const int c0 = 16 * ks + 2 * q + 8 * half;
-        float h1[2][2];
-#pragma unroll
-        for (int h = 0; h < 2; ++h)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            const int c = c0 + e;
-            const float z1 = S.b1[c] + S.w1[3 * c] * in[h][0] + S.w1[3 * c + 1] * in[h][1] + S.w1[3 * c + 2] * in[h][2];
-            h1[h][e] = silu(z1);
-          }
-        A[ks][2 * half] = pack_bf2(h1[0][0], h1[0][1]);      // row g
-        A[ks][2 * half + 1] = pack_bf2(h1[1][0], h1[1][1]);  // row g + 8
-      }
+    for (int t = 0; t < 8; ++t) {
+      const float2 bb = *reinterpret_cast<const float2*>(S.b1 + 8 * t + 2 * q);
+      float d[4] = {bb.x, bb.y, bb.x, bb.y};
+      mma_bf16(d, A1, B1[t], 0u);
+      const int ks = t >> 1, half = t & 1;
+      A[ks][2 * half] = pack_bf2(silu_fast(d[0]), silu_fast(d[1]));      // row g
+      A[ks][2 * half + 1] = pack_bf2(silu_fast(d[2]), silu_fast(d[3]));  // row g + 8
     }
-    // layer 2 on the tensor cores, layer 3 on the fly
-    float o[2][3] = {{0.f, 0.f, 0.f}, {0.f, 0.f, 0.f}};
+    // layer 2: B fragments of two k-steps per ldmatrix (matrix j = lane / 8 is
+    // rows 8nt..8nt+7 of W2 at columns 16 (ks + j/2) + 8 (j%2))
+    uint32_t A3[4][4];  // layer-3 A fragments
 #pragma unroll
     for (int nt = 0; nt < 8; ++nt) {
-      float d[4] = {0.f, 0.f, 0.f, 0.f};
-      const __nv_bfloat16* wrow = S.w2 + (8 * nt + g) * W2S;
+      const float2 bb = *reinterpret_cast<const float2*>(S.b2 + 8 * nt + 2 * q);
+      float d[4] = {bb.x, bb.y, bb.x, bb.y};
 #pragma unroll
-      for (int ks = 0; ks < 4; ++ks) {
-        const uint32_t b0 = *reinterpret_cast<const uint32_t*>(wrow + 16 * ks + 2 * q);
-        const uint32_t b1 = *reinterpret_cast<const uint32_t*>(wrow + 16 * ks + 2 * q + 8);
-        mma_bf16(d, A[ks], b0, b1);
+      for (int ks = 0; ks < 4; ks += 2) {
+        uint32_t bf4[4];
+        const int j = lane >> 3;
+        ldmatrix_x4(bf4, S.w2 + (8 * nt + (lane & 7)) * W2S + 16 * (ks + (j >> 1)) + 8 * (j & 1));
+        mma_bf16(d, A[ks], bf4[0], bf4[1]);
+        mma_bf16(d, A[ks + 1], bf4[2], bf4[3]);
       }
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const int col = 8 * nt + 2 * q + (e & 1);
-        const int h = e >> 1;
-        const float a2 = bf(silu(d[e] + S.b2[col]));
-#pragma unroll
-        for (int c = 0; c < 3; ++c) o[h][c] += S.w3[64 * c + col] * a2;
-      }
+      const int ks3 = nt >> 1, half = nt & 1;
+      A3[ks3][2 * half] = pack_bf2(silu_fast(d[0]), silu_fast(d[1]));
+      A3[ks3][2 * half + 1] = pack_bf2(silu_fast(d[2]), silu_fast(d[3]));
     }
+    // layer 3: outputs 0..2 in columns 0..2 (column 1 = dy, column 2 = dz)
+    float o[4] = {c3a, c3b, c3a, c3b};
 #pragma unroll
-    for (int h = 0; h < 2; ++h)
-#pragma unroll
-      for (int c = 0; c < 3; ++c) {
-        o[h][c] += __shfl_xor_sync(0xffffffffu, o[h][c], 1);
-        o[h][c] += __shfl_xor_sync(0xffffffffu, o[h][c], 2);
-      }
-    if (q == 0) {
+    for (int ks = 0; ks < 4; ++ks) mma_bf16(o, A3[ks], B3[ks][0], B3[ks][1]);
+    // dy sits in lane q = 0 (column 1), dz in lane q = 1 (column 0 + 2)
+    if (q < 2) {
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int i = idx[h];
         if (i >= ch.end) continue;
-        if (ok[h]) {
-          b.cy[i] = b.y[i] + OUT_SCALE * (o[h][1] + S.b3[1]);
-          b.cz[i] = b.z[i] + OUT_SCALE * (o[h][2] + S.b3[2]);
-        } else {
-          b.cy[i] = b.y[i];
-          b.cz[i] = b.z[i];
-        }
+        const float corr = q == 0 ? o[2 * h + 1] : o[2 * h];
+        if (q == 0) b.cy[i] = y_cur[h] + (ok[h] ? OUT_SCALE * corr : 0.0f);
+        else b.cz[i] = z_cur[h] + (ok[h] ? OUT_SCALE * corr : 0.0f);
       }
     }
   }
