@@ -905,8 +905,8 @@ __device__ __forceinline__ RowInfo load_row(const RowInfo* p) {
 }
 
 // Where a tracklet reads its item's row table, bin index, sorted hits and clean
-// up-links.  `r` is the pad row of the position read (it selects the CTA that
-// holds it in the cluster form).
+// up-links.  `r` is the pad row of the position read (unused by these global
+// sources; a source that splits an item's rows over several places needs it).
 template <bool NC>
 struct GSrc {  // global memory; NC: data written by an earlier launch
   // candidates per round of the single-lane search: 8 for the plain kernels,
