@@ -926,6 +926,7 @@ struct GSrc {  // global memory; NC: data written by an earlier launch
 // (iy1 < iy0 or iz1 < iz0) if it misses the grid or the row has no hits.
 struct Box {
   int iy0, iy1, iz0, iz1;
+  int qy0, qy1, qz0, qz1;  // the box itself in quanta (absolute z)
 };
 
 __device__ __forceinline__ Box row_box(const RowInfo& ri, float yc, float zc, float wy, float wz, int z_base) {
@@ -939,6 +940,11 @@ __device__ __forceinline__ Box row_box(const RowInfo& ri, float yc, float zc, fl
   bin_range(ylo, yhi, ri.ymin, ri.shift, ri.ny, &x.iy0, &x.iy1);
   bin_range(zlo, zhi, ri.zmin, ri.shift, ri.nz, &x.iz0, &x.iz1);
   if (ri.n == 0) x.iy1 = -1;
+  // within int range: |float bounds| <= 1e9 + 2 quanta, |z_base| < 1.03e9
+  x.qy0 = (int)ylo;
+  x.qy1 = (int)yhi;
+  x.qz0 = (int)zlo;
+  x.qz1 = (int)zhi;
   return x;
 }
 
@@ -1007,31 +1013,27 @@ __device__ __forceinline__ int pick_box(const Src& S, const Grp<G>& g, int r, co
         pos[k] = j + (j < n0 ? a0 : off1);
         if (j < total) qk[k] = S.hit(r, pos[k]);
       }
-      unsigned long long km = ~0ull;
-      int im = 0;
+      // a hit with chi2 <= 16 lies inside the box (|dy| <= 4 sqrt(S_yy) <= wy,
+      // likewise z), so an integer box test rejects most candidates of the
+      // bins; only the survivors (typically the one hit of the track) get a
+      // chi2 key, their record read again from the first-level cache
+      unsigned live = 0;
 #pragma unroll
-      for (int h4 = 0; h4 < CB; h4 += 4) {
-        unsigned long long key[4];
-#pragma unroll
-        for (int k = 0; k < 4; ++k) key[k] = j0 + h4 + k < total ? hit_key(qk[h4 + k], p, w, z_base) : ~0ull;
-        const bool b01 = key[1] < key[0], b23 = key[3] < key[2];
-        const unsigned long long k01 = b01 ? key[1] : key[0], k23 = b23 ? key[3] : key[2];
-        const bool hi = k23 < k01;
-        const unsigned long long kq = hi ? k23 : k01;
-        const int iq = h4 + (hi ? (b23 ? 3 : 2) : (b01 ? 1 : 0));
-        if (kq < km) {
-          km = kq;
-          im = iq;
+      for (int k = 0; k < CB; ++k)
+        if (j0 + k < total && qk[k].x >= bx.qy0 && qk[k].x <= bx.qy1 && qk[k].y >= bx.qz0 && qk[k].y <= bx.qz1)
+          live |= 1u << k;
+      while (live) {
+        const int k = __ffs(live) - 1;
+        live &= live - 1;
+        const int j = j0 + k;
+        const int ps = j + (j < n0 ? a0 : off1);
+        const int4 q = S.hit(r, ps);
+        const unsigned long long key = hit_key(q, p, w, z_base);
+        if (key < best) {
+          best = key;
+          best_pos = ps;
+          best_q = q;
         }
-      }
-      if (km < best) {
-        best = km;
-#pragma unroll
-        for (int k = 0; k < CB; ++k)
-          if (im == k) {
-            best_pos = pos[k];
-            best_q = qk[k];
-          }
       }
     }
     for (int iy = bx.iy0 + 2; iy <= bx.iy1; ++iy) {  // wider windows (rare)
