@@ -231,6 +231,21 @@ def to_device(cl, dev):
     return d
 
 
+def pinned_clusters(cl, torch):
+    """The cluster arrays in pinned (page-locked) host memory."""
+    d = type("P", (), {})()
+    d.keep = []  # the pinned tensors behind the numpy views
+    for name, dt in (("x", torch.float32), ("y", torch.float32), ("z", torch.float32), ("row", torch.int32)):
+        a = getattr(cl, name)
+        buf = torch.empty(a.shape[0], dtype=dt, pin_memory=True)
+        buf.numpy()[:] = a
+        d.keep.append(buf)
+        setattr(d, name, buf.numpy())
+    d.item_off, d.item_sector, d.item_event = cl.item_off, cl.item_sector, cl.item_event
+    d.item_core = getattr(cl, "item_core", None)
+    return d
+
+
 def time_steps(t, stream, steps, flush):
     """Device time of `steps` tpc_track() calls, L2 flushed between them."""
     import torch
@@ -326,16 +341,22 @@ def main():
     stages = stage_profile(t, stream)
 
     # end to end through the public API with host buffers: H2D of the step's
-    # clusters, tracking, D2H of the tracks and their cluster ids
+    # clusters from pinned host memory, tracking, D2H of the tracks and their
+    # cluster ids into pinned host memory
     e2e = []
     h2d = 16 * cl.n + 8 * (cl.n_items + 1) + 8 * cl.n_items
+    hcl = pinned_clusters(cl, torch)
+    nt0, ni0 = t.counts()
+    out_t = torch.empty((nt0 + 64) * tpc.TRACK_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+    out_i = torch.empty(ni0 + 4096, dtype=torch.int32, pin_memory=True)
+    out = (out_t.numpy().view(tpc.TRACK_DTYPE), out_i.numpy().view(np.uint32))
     trk = ids = None
     for _ in range(max(4, args.steps // 2)):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        t.load(cl)
+        t.load(hcl)
         t.track()
-        trk, ids = t.get_tracks()
+        trk, ids = t.get_tracks(out=out)
         e2e.append(time.perf_counter() - t0)
     d2h = trk.nbytes + ids.nbytes + 32
     e2e_s = shard.max_over_ranks(float(np.median(e2e[1:])), dist, device=dev)

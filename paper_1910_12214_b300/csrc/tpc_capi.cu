@@ -41,6 +41,7 @@ struct tpc_ctx {
   // execution mode and CUDA graph of tpc_track
   bool batched = false, use_graph = false, last_batched = false;
   cudaGraphExec_t graph = nullptr;
+  Buffers graph_b{}, graph_tb{};  // kernel arguments the graph was built with
   // space-point correction: mode and model buffers (kept across batch loads)
   tpc_corr corr = TPC_CORR_NONE;
   std::vector<void*> persist;
@@ -380,7 +381,8 @@ extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
   if (e != cudaSuccess) return cuda_fail(c, e, "metadata upload");
   // host arrays must stay valid only during the call
   if (!cl->on_device && (e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "sync");
-  drop_graph(c);  // kernel arguments changed
+  // a captured graph stays: tpc_track rebuilds or updates it if the kernel
+  // arguments changed (a batch of the same sizes into the same buffers reuses it)
   c->loaded = true;
   c->tracked = false;
   return TPC_OK;
@@ -413,19 +415,31 @@ extern "C" tpc_status tpc_track(tpc_ctx* c) {
                       : tpc_launch_plain(tb, c->lc, c->stream, c->have_events ? c->ev : nullptr);
   };
   if (c->use_graph && capturable(c->stream)) {
-    if (!c->graph) {
+    const bool stale = c->graph && (std::memcmp(&c->graph_b, &c->b, sizeof(Buffers)) != 0 ||
+                                    std::memcmp(&c->graph_tb, &tb, sizeof(Buffers)) != 0);
+    if (!c->graph || stale) {
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
       if (e != cudaSuccess) return cuda_fail(c, e, "graph capture");
       cudaError_t le = launch();
       e = cudaStreamEndCapture(c->stream, &g);
       if (le != cudaSuccess) e = le;
-      if (e == cudaSuccess) e = cudaGraphInstantiate(&c->graph, g, 0);
+      if (e == cudaSuccess && stale) {
+        // same launch sequence with new arguments: update the executable graph in place
+        cudaGraphExecUpdateResultInfo info{};
+        if (cudaGraphExecUpdate(c->graph, g, &info) != cudaSuccess) {
+          cudaGetLastError();
+          drop_graph(c);
+        }
+      }
+      if (e == cudaSuccess && !c->graph) e = cudaGraphInstantiate(&c->graph, g, 0);
       if (g) cudaGraphDestroy(g);
       if (e != cudaSuccess) {
-        c->graph = nullptr;
+        drop_graph(c);
         return cuda_fail(c, e, "graph build");
       }
+      c->graph_b = c->b;
+      c->graph_tb = tb;
     }
     e = cudaGraphLaunch(c->graph, c->stream);
   } else {

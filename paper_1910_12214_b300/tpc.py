@@ -206,10 +206,16 @@ class Tracker:
             self._check(st)
         return int(nt.value), int(ni.value)
 
-    def get_tracks(self):
+    def get_tracks(self, out=None):
+        """Tracks (TRACK_DTYPE records) and their cluster ids.  out = (tracks,
+        ids): caller-owned arrays (e.g. views of pinned host memory) reused if
+        large enough; the returned arrays are then views of them."""
         nt, ni = self.counts()
-        trk = np.zeros(nt, dtype=TRACK_DTYPE)
-        ids = np.zeros(ni, dtype=np.uint32)
+        if out is not None and out[0].shape[0] >= nt and out[1].shape[0] >= ni:
+            trk, ids = out[0][:nt], out[1][:ni]
+        else:
+            trk = np.zeros(nt, dtype=TRACK_DTYPE)
+            ids = np.zeros(ni, dtype=np.uint32)
         a, b = C.c_uint64(), C.c_uint64()
         self._check(_lib.tpc_get_tracks(self._h, _ptr(trk) if nt else None, nt, _ptr(ids) if ni else None, ni,
                                         C.byref(a), C.byref(b)))

@@ -286,3 +286,28 @@ def test_dense_rows_take_the_direct_neighbour_enumeration():
     ref = oracle.run(c, oracle.OracleConfig(n_rows=n_rows, x_max=x_max))
     trk, ids, d = run_gpu(c, n_rows=n_rows, row_x_max=x_max)
     compare_stages(d, ref)
+
+
+def test_graph_follows_reloads_of_other_sizes_and_contents():
+    """With graph replay, a reload into the same buffers reuses the graph and a
+    reload with other sizes updates it; every result equals a fresh tracker's."""
+    from paper_1910_12214_b300 import tpc
+    a = synth.make_config1(seed=21)
+    b = synth.make_config1(seed=22)
+    c = synth.make_batched(seed=23, n_events=2, mult=(50, 300))
+
+    def fresh(cl):
+        with tpc.Tracker() as t:
+            t.set_tuning(use_graph=1)
+            t.load(cl).track()
+            return t.get_tracks()
+
+    import torch
+    s = torch.cuda.Stream()
+    with tpc.Tracker(stream=s) as t:
+        t.set_tuning(use_graph=2)
+        for cl in (a, b, a, c, b):
+            t.load(cl).track()
+            trk, ids = t.get_tracks()
+            trk0, ids0 = fresh(cl)
+            assert trk.tobytes() == trk0.tobytes() and np.array_equal(ids, ids0)
