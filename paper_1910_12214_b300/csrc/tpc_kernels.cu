@@ -1444,24 +1444,24 @@ __device__ __forceinline__ unsigned long long select_own_warp(const Buffers& b, 
 __device__ __forceinline__ void emit_warp(const Buffers& b, int tl, unsigned long long cnt, unsigned io,
                                           tpc_track_t* dst, uint32_t* ids, int lane) {
   const TrackletRec& r = b.tl[tl];
-  if (lane == 0) {
-    tpc_track_t o;
-    o.x_ref = r.x_ref;
-    o.y = r.p[0];
-    o.z = r.p[1] + (float)r.z_base * (1.0f / TPC_QSCALE);
-    o.snp = r.p[2];
-    o.tgl = r.p[3];
-    o.qpt = r.p[4];
-#pragma unroll
-    for (int m = 0; m < 15; ++m) o.cov[m] = r.C[m];
-    o.chi2 = r.chi2;
-    o.ndf = 2 * r.n - 5;
-    o.item = r.item;
-    o.sector = b.item_sector ? b.item_sector[r.item] : 0u;
-    o.event = b.item_event ? b.item_event[r.item] : 0u;
-    o.first_cluster = io;
-    o.n_clusters = (unsigned)(cnt & 0xFFFFFFFFull);
-    *dst = o;
+  // the 112-byte record, one 32-bit word per lane (words 0-4 params, 5-19
+  // covariance, 20 chi2, 21 ndf, 22 item, 23 sector, 24 event, 25 first
+  // cluster, 26 cluster count, with x_ref first: the tpc_track_t layout)
+  if (lane < 28) {
+    const float* rf = reinterpret_cast<const float*>(&r);
+    uint32_t v = 0;
+    if (lane == 0) v = __float_as_uint(r.x_ref);
+    else if (lane == 2) v = __float_as_uint(r.p[1] + (float)r.z_base * (1.0f / TPC_QSCALE));
+    else if (lane <= 5) v = __float_as_uint(rf[lane - 1]);           // y, (z), snp, tgl, qpt
+    else if (lane <= 20) v = __float_as_uint(rf[lane - 1]);          // cov[0..14]
+    else if (lane == 21) v = __float_as_uint(r.chi2);
+    else if (lane == 22) v = (uint32_t)(2 * r.n - 5);
+    else if (lane == 23) v = (uint32_t)r.item;
+    else if (lane == 24) v = b.item_sector ? b.item_sector[r.item] : 0u;
+    else if (lane == 25) v = b.item_event ? b.item_event[r.item] : 0u;
+    else if (lane == 26) v = io;
+    else v = (uint32_t)(cnt & 0xFFFFFFFFull);
+    reinterpret_cast<uint32_t*>(dst)[lane] = v;
   }
   const unsigned long long key = tl_key(r.n, r.local);
   const int* hl = b.tl_hits + (size_t)tl * b.par.n_rows;
@@ -1996,11 +1996,12 @@ cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t 
   mark(6);
   tpc_launch_tracklets(b, c, s);
   mark(7);
-  k_select_max<<<c.num_sms * 4, 256, 0, s>>>(b);
-  k_select_own<<<c.num_sms * 4, 256, 0, s>>>(b);
+  // a warp per tracklet: enough blocks for every resident warp slot
+  k_select_max<<<c.num_sms * 8, 256, 0, s>>>(b);
+  k_select_own<<<c.num_sms * 8, 256, 0, s>>>(b);
   scan_u64_dev(b.tl_cnt, b.tl_ex, b.start_ex + b.N, b.scan_tmp, c.grid_scan, s);
   mark(8);
-  k_output<<<c.num_sms * 4, 256, 0, s>>>(b);
+  k_output<<<c.num_sms * 8, 256, 0, s>>>(b);
   k_counts<<<1, 1, 0, s>>>(b);
   mark(9);
   return cudaGetLastError();
