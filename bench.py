@@ -41,6 +41,7 @@ ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12
 TRAFFIC = {("c2", "tracklets"): 40.13e6}
 KERNELS_PER_STEP = {"plain": 19, "batched": 3}
 
+METRIC = "TPC clusters/s tracked (sector tracker, full TPC event)"
 WORKLOADS = {
     "c1": "1 sector x 152 rows, 200 helices pT 0.1-10 GeV |eta|<0.9, sigma 0.1 cm, 5% noise, seed 1",
     "c2": "36 sectors x 152 rows, 6000 helices (central Pb-Pb-like), sigma 0.1 cm, 5% noise, seed 1",
@@ -213,10 +214,13 @@ def run_reference(args, rank, world):
     if rank != 0:
         return
     cb = cpu_baseline(args.workload, budget_s=max(3.0, min(60.0, 6.0 * args.steps)))
-    line = {"impl": "reference", "metric": "TPC clusters/s tracked", "value": cb["value"], "unit": "clusters/s",
+    cl = make_workload(args.workload, 0)
+    line = {"impl": "reference", "metric": METRIC, "value": cb["value"], "unit": "clusters/s",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOADS[args.workload]}, "cpu_baseline": cb,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic (seeded helices, ALICE simulation not available)",
+            "config": {"workload": WORKLOADS[args.workload], "clusters_per_step": cl.n, "items": cl.n_items},
+            "cpu_baseline": cb,
             "e2e": {"value": cb["value"], "unit": "clusters/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -373,7 +377,7 @@ def main():
         achieved = algo / (stages[dom] * 1e-6) / 1e9
         value = n_all / (ms * 1e-3)
         line = {
-            "metric": "TPC clusters/s tracked (sector tracker, full TPC event)",
+            "metric": METRIC,
             "value": value, "unit": "clusters/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": ms, "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
             "data": "synthetic (seeded helices, ALICE simulation not available)",
