@@ -10,7 +10,7 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
-SRC = [os.path.join(HERE, f) for f in ("tpc_oracle.cpp", "corr_oracle.cpp", "mlp_oracle.cpp")
+SRC = [os.path.join(HERE, f) for f in ("tpc_oracle.cpp", "corr_oracle.cpp", "mlp_oracle.cpp", "codec_oracle.cpp")
        if os.path.exists(os.path.join(HERE, f))]
 
 
@@ -84,6 +84,10 @@ def _load():
             lib.orc_mlp_batch.restype = None
             lib.orc_mlp_batch.argtypes = [C.c_uint64, C.c_int, C.c_uint64, C.c_int, C.c_void_p, C.c_int, C.c_int,
                                           C.c_int, C.c_void_p, C.c_void_p]
+        lib.orc_dyn_round.restype = C.c_uint32
+        lib.orc_dyn_round.argtypes = [C.c_uint32, C.c_int, C.c_int]
+        lib.orc_encode_clusters.restype = C.c_int64
+        lib.orc_encode_clusters.argtypes = [C.c_int64, C.c_int] + [C.c_void_p] * 14
         lib.orc_chi2.restype = C.c_double
         lib.orc_chi2.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         _lib = lib
@@ -243,3 +247,24 @@ def mlp_batch(seed, sector, step, n, grid_sector):
 
 def bf16(v):
     return _load().orc_bf16(float(v))
+
+
+CODE_FIELDS = (("y", np.int16), ("z", np.int32), ("row", np.uint8), ("q_tot", np.uint16), ("q_max", np.uint16),
+               ("sigma_y", np.uint8), ("sigma_z", np.uint8))
+
+
+def dyn_round(v, n, width):
+    """Dynamic precision of one non-negative integer (n bits after the leading one)."""
+    return int(_load().orc_dyn_round(int(v), int(n), int(width)))
+
+
+def encode_clusters(props, n_rows=152):
+    """Integer codes of cluster properties (dict of y, z, row, q_tot, q_max, sigma_y,
+    sigma_z arrays); returns (dict of code arrays, number of bad clusters)."""
+    lib = _load()
+    src = [np.ascontiguousarray(props[k], np.int32 if k == "row" else np.float32)
+           for k in ("y", "z", "row", "q_tot", "q_max", "sigma_y", "sigma_z")]
+    n = src[0].shape[0]
+    out = {k: np.empty(n, dt) for k, dt in CODE_FIELDS}
+    bad = lib.orc_encode_clusters(n, n_rows, *[_p(a) for a in src], *[_p(out[k]) for k, _ in CODE_FIELDS])
+    return out, int(bad)
