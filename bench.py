@@ -8,7 +8,8 @@ launch shapes chosen by the library's autotuner, replayed as a CUDA graph.
 Further forms (rank 0, N=1): 64 uneven events (plain vs batched persistent
 kernel), a 50 kHz continuous-readout time frame (128 collisions, sliced), and
 the same 64 events distorted by a space-charge field, corrected by the grid or
-by the trained BF16 network.
+by the trained BF16 network, and the cluster codec (float to integer with
+dynamic precision) over the 64 events' clusters.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
 bounded sample of the same workload instead.
@@ -86,7 +87,7 @@ def generate_forms(forms):
     jobs = {}
     ctx = mp.get_context("spawn")
     with ctx.Pool(3) as pool:
-        if "c3" in forms or "c5" in forms:
+        if "c3" in forms or "c5" in forms or "c6" in forms:
             jobs["c3"] = pool.apply_async(_gen_batched)
         if "c4" in forms:
             jobs["c4"] = pool.apply_async(_gen_frame)
@@ -94,10 +95,15 @@ def generate_forms(forms):
             jobs["grid"] = pool.apply_async(_gen_grid)
         for k, j in jobs.items():
             out[k] = j.get()
+    if "c6" in forms:
+        from paper_1910_12214_b300 import synth
+        out["c6"] = synth.cluster_props(out["c3"], seed=1)
     if "c5" in forms:
         from paper_1910_12214_b300 import synth
         d, g, b = out["grid"]
         out["c5"] = (synth.distort(out["c3"], d), g, b)
+    if "c3" not in forms:
+        out.pop("c3", None)  # generated only as the input of another form
     return out
 
 
@@ -260,7 +266,8 @@ def time_steps(t, stream, steps, flush):
         e0.record(stream)
         t.track()
         e1.record(stream)
-        flush.zero_()
+        with torch.cuda.stream(stream):  # on the timed stream: between steps, not beside the next one
+            flush.zero_()
         ms.append((e0, e1))
     torch.cuda.synchronize()
     return [a.elapsed_time(b) for a, b in ms]
@@ -291,7 +298,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--forms", default="c3,c4,c5", help="extra forms at N=1: c3,c4,c5 or none")
+    ap.add_argument("--forms", default="c3,c4,c5,c6", help="extra forms at N=1: c3,c4,c5,c6 or none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -323,7 +330,8 @@ def main():
     t.set_tuning(use_graph=2)
     for _ in range(args.warmup):
         t.track()
-        flush.zero_()
+        with torch.cuda.stream(stream):
+            flush.zero_()
     torch.cuda.synchronize()
     clocks = ClockSampler(local)
     clocks.start()
@@ -464,6 +472,78 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
                 st = t.stage_times()
                 out[corr] = {"clusters_per_s": c5.n / (ms * 1e-3), "ms": ms, "tracks": t.counts()[0]}
         res["distorted_64_events"] = {"clusters": c5.n, "surrogate": info, **out}
+    if "c6" in gen:
+        res["codec_64_events"] = bench_codec(gen["c6"], dev, stream, flush, tpc, torch)
+    return res
+
+
+CODEC_BYTES = 28 + 13  # per cluster: 7 float/int32 properties in, 13 bytes of codes out
+
+
+def bench_codec(props, dev, stream, flush, tpc, torch, steps=10):
+    """Cluster codec (Sec. 4, step 2) on the 64-event batch: device-resident
+    properties (L2 flushed between calls), then end to end with pinned host
+    buffers; the oracle on a bounded sample for the CPU baseline."""
+    n = int(props["y"].shape[0])
+    d = {k: torch.from_numpy(np.ascontiguousarray(props[k], dt)).to(dev) for k, dt in tpc.PROP_FIELDS}
+    tdt = {np.int16: torch.int16, np.int32: torch.int32, np.uint8: torch.uint8, np.uint16: torch.uint16}
+    out = {k: torch.empty(n, dtype=tdt[dt], device=dev) for k, dt in tpc.CODE_FIELDS}
+    torch.cuda.synchronize()
+    res = {"clusters": n}
+    with tpc.Tracker(stream=stream) as t:
+        for _ in range(3):
+            t.encode_clusters(d, out=out, report_bad=False)
+        ev = []
+        for _ in range(steps):
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t.encode_clusters(d, out=out, report_bad=False)
+            e1.record(stream)
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            ev.append((e0, e1))
+        torch.cuda.synchronize()
+        ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+        _, bad = t.encode_clusters(d, out=out)
+        peak, kind = measured_peak_hbm()
+        gbs = CODEC_BYTES * n / (ms * 1e-3) / 1e9
+        res.update(clusters_per_s=n / (ms * 1e-3), ms=ms, bad=bad,
+                   roofline={"bound": "hbm", "kernel": "k_encode_vec", "achieved": gbs, "peak": peak, "unit": "GB/s",
+                             "frac": gbs / peak, "peak_kind": kind, "algo_bytes_per_cluster": CODEC_BYTES})
+        # end to end: pinned host properties in, pinned host codes out, copies inside the timed region
+        hp = {}
+        keep = []
+        for k, dt in tpc.PROP_FIELDS:
+            buf = torch.empty(n, dtype=torch.from_numpy(np.zeros(1, dt)).dtype, pin_memory=True)
+            buf.numpy()[:] = props[k]
+            keep.append(buf)
+            hp[k] = buf.numpy()
+        ho = {}
+        for k, dt in tpc.CODE_FIELDS:
+            buf = torch.empty(n, dtype=tdt[dt], pin_memory=True)
+            keep.append(buf)
+            ho[k] = buf.numpy()
+        wall = []
+        for _ in range(5):
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            t.encode_clusters(hp, out=ho)
+            wall.append(time.perf_counter() - w0)
+        e2e = float(np.median(wall[1:]))
+        res["e2e"] = {"value": n / e2e, "unit": "clusters/s", "h2d_bytes_per_step": 28 * n,
+                      "d2h_bytes_per_step": 13 * n}
+    del d, out
+    torch.cuda.empty_cache()
+    # the oracle on a bounded sample, one host core
+    import oracle
+    m = min(n, 4_000_000)
+    sample = {k: np.ascontiguousarray(props[k][:m]) for k, _ in tpc.PROP_FIELDS}
+    t0 = time.perf_counter()
+    oracle.encode_clusters(sample)
+    dt = time.perf_counter() - t0
+    res["cpu_baseline"] = {"value": m / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+                           "sample": f"first {m} clusters of the 64-event batch"}
     return res
 
 

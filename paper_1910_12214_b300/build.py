@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtpc.so")
-SOURCES = ["tpc_kernels.cu", "tpc_capi.cu", "tpc_mlp.cu", "tpc_noalloc.cu"]
+SOURCES = ["tpc_kernels.cu", "tpc_capi.cu", "tpc_mlp.cu", "tpc_noalloc.cu", "tpc_reduce.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
 
@@ -18,7 +18,8 @@ def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
-    deps = [os.path.join(CSRC, f) for f in os.listdir(CSRC)] + [os.path.join(ROOT, "include", "tpc.h"), __file__]
+    deps = ([os.path.join(CSRC, f) for f in os.listdir(CSRC)] +
+            [os.path.join(ROOT, "include", h) for h in os.listdir(os.path.join(ROOT, "include"))] + [__file__])
     return any(os.path.getmtime(d) > t for d in deps if os.path.exists(d))
 
 

@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "tpc.h"
+#include "tpc_reduce.h"
 #include "tpc_internal.cuh"
 
 struct tpc_ctx {
@@ -56,6 +57,10 @@ struct tpc_ctx {
   float* mlp_bounds = nullptr;
   void* mlp_infer = nullptr;
   std::vector<float> mlp_bounds_host;
+  // cluster codec: staging of host-mode calls (inputs then codes) and the bad-cluster counter
+  void* codec_stage = nullptr;
+  uint64_t codec_cap = 0;
+  unsigned long long* codec_bad = nullptr;
 };
 
 namespace {
@@ -1077,6 +1082,92 @@ extern "C" tpc_status tpc_surrogate_load(tpc_ctx* c, const char* path) {
           cudaSuccess)
     return cuda_fail(c, e, "surrogate upload");
   return mlp_publish(c);
+}
+
+// ---- cluster codec (Sec. 4, step 2) ----
+
+namespace {
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Byte offsets of the 7 input and 7 code arrays of n clusters in one staging block.
+void codec_layout(uint64_t n, size_t off[15]) {
+  static const int sz[14] = {4, 4, 4, 4, 4, 4, 4, 2, 4, 1, 2, 2, 1, 1};
+  size_t o = 0;
+  for (int i = 0; i < 14; ++i) {
+    off[i] = o;
+    o += align256((size_t)n * sz[i]);
+  }
+  off[14] = o;
+}
+
+}  // namespace
+
+extern "C" tpc_status tpc_encode_clusters(tpc_ctx* c, const tpc_cluster_props* in, const tpc_cluster_codes* out,
+                                          int on_device, uint64_t* n_bad) {
+  if (!c || !in || !out) return fail(c, TPC_ERR_INVALID_ARG, "null argument");
+  if (n_bad) *n_bad = 0;
+  const uint64_t n = in->n;
+  if (n == 0) return TPC_OK;
+  if (n > (1ull << 40)) return fail(c, TPC_ERR_INVALID_ARG, "too many clusters");
+  if (!in->y || !in->z || !in->row || !in->q_tot || !in->q_max || !in->sigma_y || !in->sigma_z || !out->y ||
+      !out->z || !out->row || !out->q_tot || !out->q_max || !out->sigma_y || !out->sigma_z)
+    return fail(c, TPC_ERR_INVALID_ARG, "null array");
+  cudaError_t e;
+  if (!c->codec_bad) {
+    c->codec_bad = (unsigned long long*)persist_alloc(c, 256);
+    if (!c->codec_bad) return fail(c, TPC_ERR_OOM, "codec counter");
+  }
+  if ((e = cudaMemsetAsync(c->codec_bad, 0, 8, c->stream)) != cudaSuccess) return cuda_fail(c, e, "codec counter");
+  CodecIn di{in->y, in->z, in->row, in->q_tot, in->q_max, in->sigma_y, in->sigma_z};
+  CodecOut dout{out->y, out->z, out->row, out->q_tot, out->q_max, out->sigma_y, out->sigma_z};
+  size_t off[15];
+  if (!on_device) {
+    codec_layout(n, off);
+    if (n > c->codec_cap) {
+      persist_free(c, c->codec_stage);
+      c->codec_stage = nullptr;
+      c->codec_cap = 0;
+      uint64_t cap = std::max<uint64_t>(n, 1 << 16);
+      size_t o2[15];
+      codec_layout(cap, o2);
+      c->codec_stage = persist_alloc(c, o2[14]);
+      if (!c->codec_stage) return fail(c, TPC_ERR_OOM, "codec staging");
+      c->codec_cap = cap;
+    }
+    char* base = (char*)c->codec_stage;
+    const void* src[7] = {in->y, in->z, in->row, in->q_tot, in->q_max, in->sigma_y, in->sigma_z};
+    for (int i = 0; i < 7; ++i)
+      if ((e = cudaMemcpyAsync(base + off[i], src[i], 4 * n, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "codec upload");
+    di = CodecIn{(const float*)(base + off[0]), (const float*)(base + off[1]), (const int*)(base + off[2]),
+                 (const float*)(base + off[3]), (const float*)(base + off[4]), (const float*)(base + off[5]),
+                 (const float*)(base + off[6])};
+    dout = CodecOut{(int16_t*)(base + off[7]), (int*)(base + off[8]), (uint8_t*)(base + off[9]),
+                    (uint16_t*)(base + off[10]), (uint16_t*)(base + off[11]), (uint8_t*)(base + off[12]),
+                    (uint8_t*)(base + off[13])};
+  }
+  if ((e = launch_encode(di, dout, (long long)n, c->cfg.n_rows, c->codec_bad, c->lc.num_sms, c->stream)) !=
+      cudaSuccess)
+    return cuda_fail(c, e, "codec launch");
+  if (!on_device) {
+    char* base = (char*)c->codec_stage;
+    void* dst[7] = {out->y, out->z, out->row, out->q_tot, out->q_max, out->sigma_y, out->sigma_z};
+    static const int w[7] = {2, 4, 1, 2, 2, 1, 1};
+    for (int i = 0; i < 7; ++i)
+      if ((e = cudaMemcpyAsync(dst[i], base + off[7 + i], (size_t)w[i] * n, cudaMemcpyDeviceToHost, c->stream)) !=
+          cudaSuccess)
+        return cuda_fail(c, e, "codec download");
+  } else if (!n_bad) {
+    return TPC_OK;
+  }
+  unsigned long long bad = 0;
+  if ((e = cudaMemcpyAsync(&bad, c->codec_bad, 8, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "codec sync");
+  if (n_bad) *n_bad = bad;
+  if (bad) return fail(c, TPC_ERR_BAD_INPUT, "a cluster has a bad row or a non-finite value");
+  return TPC_OK;
 }
 
 extern "C" void tpc_destroy(tpc_ctx* c) {

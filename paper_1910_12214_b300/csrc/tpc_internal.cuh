@@ -168,3 +168,20 @@ cudaError_t tpc_mlp_grad_only(const float* master, float* partial, float* loss, 
 cudaError_t tpc_mlp_eval(const float* master, const float2* grid, int nx, int ny, int nz, int S, int nblk,
                          uint64_t seed, float* out, cudaStream_t s);
 cudaError_t tpc_mlp_prepare(const float* master, const float* bounds, void* infer, int S, cudaStream_t s);
+
+// Cluster codec (tpc_reduce.cu): float properties -> integer codes.
+struct CodecIn {
+  const float *y, *z;
+  const int* row;
+  const float *qt, *qm, *sy, *sz;
+};
+struct CodecOut {
+  int16_t* y;
+  int* z;
+  uint8_t* row;
+  uint16_t *qt, *qm;
+  uint8_t *sy, *sz;
+};
+bool codec_vector_ok(const CodecIn& in, const CodecOut& out);
+cudaError_t launch_encode(const CodecIn& in, const CodecOut& out, long long n, int n_rows, unsigned long long* n_bad,
+                          int num_sms, cudaStream_t s);

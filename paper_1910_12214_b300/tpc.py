@@ -53,6 +53,21 @@ class tpc_tuning(C.Structure):
                 ("batch_lanes", C.c_int), ("use_graph", C.c_int)]
 
 
+class tpc_cluster_props(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("z", C.c_void_p), ("row", C.c_void_p), ("q_tot", C.c_void_p),
+                ("q_max", C.c_void_p), ("sigma_y", C.c_void_p), ("sigma_z", C.c_void_p), ("n", C.c_uint64)]
+
+
+class tpc_cluster_codes(C.Structure):
+    _fields_ = [("y", C.c_void_p), ("z", C.c_void_p), ("row", C.c_void_p), ("q_tot", C.c_void_p),
+                ("q_max", C.c_void_p), ("sigma_y", C.c_void_p), ("sigma_z", C.c_void_p)]
+
+
+PROP_FIELDS = (("y", np.float32), ("z", np.float32), ("row", np.int32), ("q_tot", np.float32),
+               ("q_max", np.float32), ("sigma_y", np.float32), ("sigma_z", np.float32))
+CODE_FIELDS = (("y", np.int16), ("z", np.int32), ("row", np.uint8), ("q_tot", np.uint16), ("q_max", np.uint16),
+               ("sigma_y", np.uint8), ("sigma_z", np.uint8))
+
 TRACK_DTYPE = np.dtype([("x_ref", "<f4"), ("y", "<f4"), ("z", "<f4"), ("snp", "<f4"), ("tgl", "<f4"),
                         ("qpt", "<f4"), ("cov", "<f4", (15,)), ("chi2", "<f4"), ("ndf", "<i4"), ("item", "<u4"),
                         ("sector", "<u4"), ("event", "<u4"), ("first_cluster", "<u4"), ("n_clusters", "<u4")])
@@ -84,6 +99,8 @@ _sig = {
     "tpc_surrogate_save": ([_P, C.c_char_p], C.c_int),
     "tpc_surrogate_load": ([_P, C.c_char_p], C.c_int),
     "tpc_bin_sector_noalloc": ([_P, _P, _P, C.c_uint32, C.c_int, _P, _P, _P, _P], C.c_int),
+    "tpc_encode_clusters": ([_P, C.POINTER(tpc_cluster_props), C.POINTER(tpc_cluster_codes), C.c_int,
+                             C.POINTER(C.c_uint64)], C.c_int),
     "tpc_destroy": ([_P], None),
     "tpc_last_error": ([_P], C.c_char_p),
 }
@@ -305,6 +322,39 @@ class Tracker:
 
     def surrogate_load(self, path):
         self._check(_lib.tpc_surrogate_load(self._h, str(path).encode()))
+
+    def encode_clusters(self, props, out=None, report_bad=True):
+        """Integer codes of cluster properties (Sec. 4, step 2; include/tpc_reduce.h).
+
+        props: dict of y, z, row, q_tot, q_max, sigma_y, sigma_z -- numpy arrays
+        (host call: copied, encoded, copied back, waited for) or CUDA torch
+        tensors (device call on the tracker's stream).  out: dict of code arrays
+        of the same kind (allocated if None).  Returns (codes, n_bad); with a
+        device call and report_bad=False the call does not wait and n_bad is
+        None."""
+        on_device = hasattr(props["y"], "is_cuda") and props["y"].is_cuda
+        n = int(props["y"].shape[0])
+        keep = []
+        if on_device:
+            import torch
+            src = [props[k] for k, _ in PROP_FIELDS]
+            if out is None:
+                tdt = {np.int16: torch.int16, np.int32: torch.int32, np.uint8: torch.uint8, np.uint16: torch.uint16}
+                out = {k: torch.empty(n, dtype=tdt[dt], device=props["y"].device) for k, dt in CODE_FIELDS}
+        else:
+            src = [np.ascontiguousarray(props[k], dt) for k, dt in PROP_FIELDS]
+            keep.append(src)
+            if out is None:
+                out = {k: np.empty(n, dt) for k, dt in CODE_FIELDS}
+        pin = tpc_cluster_props(*[_ptr(a) for a in src], n)
+        cod = tpc_cluster_codes(*[_ptr(out[k]) for k, _ in CODE_FIELDS])
+        bad = C.c_uint64()
+        want = report_bad or not on_device
+        st = _lib.tpc_encode_clusters(self._h, C.byref(pin), C.byref(cod), int(on_device),
+                                      C.byref(bad) if want else None)
+        if st not in (TPC_OK, 7):
+            self._check(st)
+        return out, (int(bad.value) if want else None)
 
     def close(self):
         if getattr(self, "_h", None):

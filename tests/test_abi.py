@@ -1,5 +1,5 @@
 """Host-only checks of the C ABI: the library builds and loads, exports every
-function include/tpc.h declares, and the ctypes mirrors have the C layout.
+function include/*.h declares, and the ctypes mirrors have the C layout.
 No compute call is made (no GPU needed)."""
 import ctypes
 import os
@@ -9,7 +9,8 @@ import subprocess
 import pytest
 
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
-HEADER = os.path.join(ROOT, "include", "tpc.h")
+HEADERS = sorted(os.path.join(ROOT, "include", f) for f in os.listdir(os.path.join(ROOT, "include"))
+                 if f.endswith(".h"))
 
 
 @pytest.fixture(scope="module")
@@ -19,7 +20,7 @@ def lib_path():
 
 
 def declared_functions():
-    src = open(HEADER).read()
+    src = "".join(open(h).read() for h in HEADERS)
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(tpc_[a-z_]+)\s*\(", src)))
 
@@ -82,3 +83,16 @@ def test_product_package_does_not_import_the_oracle():
             if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
                 txt = open(os.path.join(dirpath, f)).read()
                 assert "import oracle" not in txt and "from oracle" not in txt and "tpc_oracle" not in txt, f
+
+
+def test_reduce_struct_layouts_match_c(tmp_path, lib_path):
+    from paper_1910_12214_b300 import tpc
+    prog = tmp_path / "rz.c"
+    prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "tpc_reduce.h"\nint main(void){'
+                    'printf("%zu %zu %zu\\n", sizeof(tpc_cluster_props), sizeof(tpc_cluster_codes), '
+                    'offsetof(tpc_cluster_props, n)); return 0;}\n')
+    exe = tmp_path / "rz"
+    subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
+    vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
+    assert vals == [ctypes.sizeof(tpc.tpc_cluster_props), ctypes.sizeof(tpc.tpc_cluster_codes),
+                    tpc.tpc_cluster_props.n.offset]
