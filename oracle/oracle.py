@@ -10,7 +10,8 @@ import numpy as np
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
-SRC = [os.path.join(HERE, f) for f in ("tpc_oracle.cpp", "corr_oracle.cpp", "mlp_oracle.cpp", "codec_oracle.cpp")
+SRC = [os.path.join(HERE, f) for f in ("tpc_oracle.cpp", "corr_oracle.cpp", "mlp_oracle.cpp", "codec_oracle.cpp",
+                                                        "masks_oracle.cpp")
        if os.path.exists(os.path.join(HERE, f))]
 
 
@@ -88,6 +89,10 @@ def _load():
         lib.orc_dyn_round.argtypes = [C.c_uint32, C.c_int, C.c_int]
         lib.orc_encode_clusters.restype = C.c_int64
         lib.orc_encode_clusters.argtypes = [C.c_int64, C.c_int] + [C.c_void_p] * 14
+        lib.orc_cluster_masks.restype = C.c_int64
+        lib.orc_cluster_masks.argtypes = ([C.c_int, C.c_double, C.c_double, C.c_double, C.c_int64] + [C.c_void_p] * 4 +
+                                          [C.c_int64, C.c_int64] + [C.c_void_p] * 4 + [C.c_double, C.c_float,
+                                                                                     C.c_float] + [C.c_void_p] * 3)
         lib.orc_chi2.restype = C.c_double
         lib.orc_chi2.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         _lib = lib
@@ -268,3 +273,50 @@ def encode_clusters(props, n_rows=152):
     out = {k: np.empty(n, dt) for k, dt in CODE_FIELDS}
     bad = lib.orc_encode_clusters(n, n_rows, *[_p(a) for a in src], *[_p(out[k]) for k, _ in CODE_FIELDS])
     return out, int(bad)
+
+
+MASK_ASSOCIATED, MASK_PROTECTED, MASK_REMOVE_A, MASK_REMOVE_B = 1, 2, 4, 8
+
+
+def mask_thresholds(min_pt=0.05, max_incl_deg=70.0):
+    """The float32 thresholds of the protection test: |q/pT| < fl(1/min_pt) and
+    |sin phi| < fl(sin max_incl), from the float32 parameters."""
+    import math
+    max_qpt = np.float32(1.0 / float(np.float32(min_pt)))
+    max_snp = np.float32(math.sin(float(np.float32(max_incl_deg)) * math.pi / 180.0))
+    return max_qpt, max_snp
+
+
+def cluster_masks(cl, trk_f, trk_i, ids, leg=None, tube=1.5, min_pt=0.05, max_incl_deg=70.0, bz=0.5, n_rows=152,
+                  x_min=85.0, x_max=246.0):
+    """Association, protection and strategy A/B removal of every cluster.
+
+    trk_f: [n, 6] float32 (x_ref, y, z, sinphi, tanlambda, q/pT); trk_i: [n, 3]
+    int64 (item, first, count) into ids (cluster indices, innermost first);
+    leg: uint8 per track (0 = primary) or None.  Returns (mask uint8, owner
+    int32 (-1 = none), ambiguous uint8)."""
+    lib = _load()
+    y = np.ascontiguousarray(cl.y, np.float32)
+    z = np.ascontiguousarray(cl.z, np.float32)
+    row = np.ascontiguousarray(cl.row, np.int32)
+    off = np.ascontiguousarray(cl.item_off, np.uint64)
+    tf = np.ascontiguousarray(np.asarray(trk_f, np.float32).reshape(-1, 6))
+    ti = np.ascontiguousarray(np.asarray(trk_i, np.int64).reshape(-1, 3))
+    ids = np.ascontiguousarray(ids, np.uint32)
+    lg = None if leg is None else np.ascontiguousarray(leg, np.uint8)
+    n = y.shape[0]
+    mask = np.empty(n, np.uint8)
+    owner = np.empty(n, np.int32)
+    amb = np.empty(n, np.uint8)
+    mq, ms = mask_thresholds(min_pt, max_incl_deg)
+    lib.orc_cluster_masks(n_rows, x_min, x_max, bz, n, _p(y), _p(z), _p(row), _p(off), off.shape[0] - 1,
+                          tf.shape[0], _p(tf), _p(ti), _p(ids), _p(lg), float(tube), float(mq), float(ms),
+                          _p(mask), _p(owner), _p(amb))
+    return mask, owner, amb
+
+
+def oracle_tracks(ref):
+    """(trk_f [n,6] float32, trk_i [n,3] int64, ids uint32) of the oracle tracker's output."""
+    tf = ref["trk_f"][:, :6].astype(np.float32)
+    ti = ref["trk_i"][:, :3].astype(np.int64)
+    return tf, ti, ref["trk_ids"].astype(np.uint32)
