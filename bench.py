@@ -8,8 +8,9 @@ launch shapes chosen by the library's autotuner, replayed as a CUDA graph.
 Further forms (rank 0, N=1): 64 uneven events (plain vs batched persistent
 kernel), a 50 kHz continuous-readout time frame (128 collisions, sliced), and
 the same 64 events distorted by a space-charge field, corrected by the grid or
-by the trained BF16 network, and the cluster codec (float to integer with
-dynamic precision) over the 64 events' clusters.
+by the trained BF16 network, the cluster codec (float to integer with dynamic
+precision) over the 64 events' clusters, and the cluster removal masks
+(attachment, adjacency, protection, strategies A and B) of the 64 events.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
 bounded sample of the same workload instead.
@@ -87,7 +88,7 @@ def generate_forms(forms):
     jobs = {}
     ctx = mp.get_context("spawn")
     with ctx.Pool(3) as pool:
-        if "c3" in forms or "c5" in forms or "c6" in forms:
+        if "c3" in forms or "c5" in forms or "c6" in forms or "c7" in forms:
             jobs["c3"] = pool.apply_async(_gen_batched)
         if "c4" in forms:
             jobs["c4"] = pool.apply_async(_gen_frame)
@@ -98,6 +99,8 @@ def generate_forms(forms):
     if "c6" in forms:
         from paper_1910_12214_b300 import synth
         out["c6"] = synth.cluster_props(out["c3"], seed=1)
+    if "c7" in forms:
+        out["c7"] = out["c3"]
     if "c5" in forms:
         from paper_1910_12214_b300 import synth
         d, g, b = out["grid"]
@@ -298,7 +301,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--forms", default="c3,c4,c5,c6", help="extra forms at N=1: c3,c4,c5,c6 or none")
+    ap.add_argument("--forms", default="c3,c4,c5,c6,c7", help="extra forms at N=1: c3,...,c7 or none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -474,6 +477,64 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
         res["distorted_64_events"] = {"clusters": c5.n, "surrogate": info, **out}
     if "c6" in gen:
         res["codec_64_events"] = bench_codec(gen["c6"], dev, stream, flush, tpc, torch)
+    if "c7" in gen:
+        res["masks_64_events"] = bench_masks(gen["c7"], dev, stream, flush, tpc, torch)
+    return res
+
+
+def time_masks(t, stream, flush, steps=10):
+    """Device time of tpc_cluster_masks on the tracker's own tracks (device
+    buffers, L2 flushed between calls) and of its two kernels."""
+    import torch
+    for _ in range(3):
+        t.cluster_masks(on_device=True)
+    ev, st = [], {"mask_assoc": [], "mask_final": []}
+    for _ in range(steps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        mask, owner = t.cluster_masks(on_device=True)
+        e1.record(stream)
+        for k, v in t.stage_times().items():  # waits for the stream
+            if k in st:
+                st[k].append(v)
+        with torch.cuda.stream(stream):
+            flush.zero_()
+        ev.append((e0, e1))
+    torch.cuda.synchronize()
+    ms = float(np.median([a.elapsed_time(b) for a, b in ev]))
+    m = mask.cpu().numpy()
+    counts = {"protected": int((m == 3).sum()), "removed_by_a": int(((m & 4) != 0).sum()),
+              "removed_by_b": int(((m & 8) != 0).sum())}
+    return ms, {k: float(np.median(v)) for k, v in st.items()}, counts
+
+
+def bench_masks(cl, dev, stream, flush, tpc, torch, steps=10):
+    """Cluster association, protection and strategy A/B masks (Sec. 4) over
+    the 64-event batch with the tracker's own tracks (graph-replayed
+    tracking first, then the masks, device resident)."""
+    with torch.cuda.stream(stream):
+        d = to_device(cl, dev)
+    stream.synchronize()
+    res = {"clusters": cl.n}
+    with tpc.Tracker(stream=stream, profile=True) as t:
+        t.load(d, on_device=True)
+        t.track()
+        n_trk, n_ids = t.counts()
+        ms, kern, counts = time_masks(t, stream, flush, steps)
+    peak, kind = measured_peak_hbm()
+    n_assoc = counts["protected"] + counts["removed_by_a"]  # associated = protected or removed by A
+    # algorithmic bytes: pass 1 reads every sorted hit (16 B) and the tracks' cluster ids (4 B), and
+    # reads and writes the association word of every associated cluster (16 B); pass 2 reads the word
+    # and the row (12 B), clears the associated words (8 B), writes mask and owner (5 B)
+    algo = {"mask_assoc": 16 * cl.n + 4 * n_ids + 16 * n_assoc, "mask_final": 17 * cl.n + 8 * n_assoc}
+    dom = max(kern, key=kern.get)
+    achieved = algo[dom] / (kern[dom] * 1e-6) / 1e9
+    res.update(tracks=n_trk, clusters_per_s=cl.n / (ms * 1e-3), ms=ms, kernel_us=kern, **counts,
+               roofline={"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "peak_kind": kind, "algo_bytes": algo[dom]})
+    del d
+    torch.cuda.empty_cache()
     return res
 
 

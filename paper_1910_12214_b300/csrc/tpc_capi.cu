@@ -35,6 +35,8 @@ struct tpc_ctx {
   bool loaded = false, tracked = false;
   bool input_on_device = false;
   cudaEvent_t ev[TPC_N_STAGES + 1] = {};
+  cudaEvent_t mask_ev[3] = {};  // around the two kernels of tpc_cluster_masks (profile = 1)
+  bool mask_timed = false;
   bool have_events = false;
   // host copies used by the debug dump and the work queue
   std::vector<uint64_t> h_item_off;
@@ -61,6 +63,12 @@ struct tpc_ctx {
   void* codec_stage = nullptr;
   uint64_t codec_cap = 0;
   unsigned long long* codec_bad = nullptr;
+  // cluster masks: per-cluster association words (zero between calls) and host-mode staging
+  unsigned long long* mask_assoc = nullptr;
+  uint64_t mask_cap = 0;
+  bool mask_dirty = false;
+  void* mask_stage = nullptr;
+  size_t mask_stage_bytes = 0;
 };
 
 namespace {
@@ -289,6 +297,7 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
   }
   if (cfg->profile) {
     for (int i = 0; i <= TPC_N_STAGES; ++i) cudaEventCreate(&c->ev[i]);
+    for (int i = 0; i < 3; ++i) cudaEventCreate(&c->mask_ev[i]);
     c->have_events = true;
   }
   if (cfg->max_clusters || cfg->max_items) {
@@ -390,6 +399,7 @@ extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
   // arguments changed (a batch of the same sizes into the same buffers reuses it)
   c->loaded = true;
   c->tracked = false;
+  c->mask_timed = false;
   return TPC_OK;
 }
 
@@ -467,6 +477,8 @@ extern "C" tpc_status tpc_sync(tpc_ctx* c) {
   if (err & TPC_DERR_BAD_INPUT) return fail(c, TPC_ERR_BAD_INPUT, "a cluster has a bad row or a non-finite value");
   if (err & TPC_DERR_ROW_CAP) return fail(c, TPC_ERR_CAPACITY, "row too large");
   if (err & TPC_DERR_TIMEOUT) return fail(c, TPC_ERR_TIMEOUT, "device wait timed out");
+  if (err & TPC_DERR_BAD_TRACK)
+    return fail(c, TPC_ERR_BAD_INPUT, "a track given to tpc_cluster_masks refers to an item or cluster out of range");
   return TPC_OK;
 }
 
@@ -500,23 +512,26 @@ extern "C" tpc_status tpc_device_tracks(tpc_ctx* c, const tpc_track_t** trk, con
   return TPC_OK;
 }
 
-static const char* kStageNames[TPC_N_STAGES] = {"quantise+row_stats", "row_setup", "group_scatter", "row_sort",
-                                                "links", "clean+starts", "tracklets", "selection", "output",
-                                                "batched_items", "batched_concat"};
+static const char* kStageNames[TPC_N_REPORTED_STAGES] = {
+    "quantise+row_stats", "row_setup", "group_scatter", "row_sort", "links", "clean+starts", "tracklets",
+    "selection", "output", "batched_items", "batched_concat", "mask_assoc", "mask_final"};
 
-extern "C" const char* tpc_stage_name(int i) { return (i >= 0 && i < TPC_N_STAGES) ? kStageNames[i] : ""; }
+extern "C" const char* tpc_stage_name(int i) { return (i >= 0 && i < TPC_N_REPORTED_STAGES) ? kStageNames[i] : ""; }
 
 extern "C" tpc_status tpc_stage_times(tpc_ctx* c, float* us, int n, int* n_stages) {
   if (!c) return TPC_ERR_INVALID_ARG;
-  if (n_stages) *n_stages = TPC_N_STAGES;
+  if (n_stages) *n_stages = TPC_N_REPORTED_STAGES;
   if (!c->have_events) return fail(c, TPC_ERR_STATE, "context created without profile = 1");
   if (!c->tracked) return fail(c, TPC_ERR_STATE, "no tpc_track yet");
   cudaError_t e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "stream");
-  for (int i = 0; i < TPC_N_STAGES && i < n; ++i) {
+  for (int i = 0; i < TPC_N_REPORTED_STAGES && i < n; ++i) {
     float ms = 0.f;
-    const bool mine = c->last_batched ? (i >= 9) : (i < 9);
-    if (mine && cudaEventElapsedTime(&ms, c->ev[i], c->ev[i + 1]) != cudaSuccess) {
+    const bool mask = i >= TPC_N_STAGES;
+    const bool mine = mask ? c->mask_timed : (c->last_batched ? (i >= 9) : (i < 9));
+    const cudaEvent_t a = mask ? c->mask_ev[i - TPC_N_STAGES] : c->ev[i];
+    const cudaEvent_t b = mask ? c->mask_ev[i - TPC_N_STAGES + 1] : c->ev[i + 1];
+    if (mine && cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
       cudaGetLastError();
       ms = 0.f;
     }
@@ -1170,6 +1185,117 @@ extern "C" tpc_status tpc_encode_clusters(tpc_ctx* c, const tpc_cluster_props* i
   return TPC_OK;
 }
 
+// ---- cluster association, protection and removal masks (Sec. 4) ----
+
+extern "C" tpc_status tpc_cluster_masks(tpc_ctx* c, const tpc_mask_params* prm, const tpc_track_t* tracks,
+                                        uint64_t n_tracks, const uint32_t* cluster_ids, uint64_t n_ids,
+                                        const uint8_t* leg, int on_device, uint8_t* mask, int32_t* owner) {
+  if (!c || !mask) return fail(c, TPC_ERR_INVALID_ARG, "null argument");
+  if (!c->tracked) return fail(c, TPC_ERR_STATE, "tpc_cluster_masks before tpc_track");
+  const tpc_mask_params def{1.5f, 0.05f, 70.0f};
+  const tpc_mask_params P = prm ? *prm : def;
+  if (!(P.tube_cm >= 0.f) || !std::isfinite(P.tube_cm) || !(P.min_pt_gev > 0.f) || !std::isfinite(P.min_pt_gev) ||
+      !(P.max_incl_deg > 0.f) || !(P.max_incl_deg <= 90.f))
+    return fail(c, TPC_ERR_INVALID_ARG, "mask parameters out of range");
+  if (tracks && ((n_tracks && !cluster_ids) || n_tracks > 0x7fffffffull || n_ids > 0xffffffffull))
+    return fail(c, TPC_ERR_INVALID_ARG, "track arrays");
+  const long long N = c->b.N;
+  if (N == 0) return TPC_OK;
+  cudaError_t e;
+  // association words: zero on entry (each call's second pass clears what the first set)
+  if ((uint64_t)N > c->mask_cap || !c->mask_assoc) {
+    persist_free(c, c->mask_assoc);
+    c->mask_assoc = nullptr;
+    c->mask_cap = 0;
+    const uint64_t cap = std::max<uint64_t>((uint64_t)N, 1 << 16);
+    c->mask_assoc = (unsigned long long*)persist_alloc(c, 8 * cap);
+    if (!c->mask_assoc) return fail(c, TPC_ERR_OOM, "mask words");
+    c->mask_cap = cap;
+    c->mask_dirty = true;
+  }
+  if (c->mask_dirty) {
+    if ((e = cudaMemsetAsync(c->mask_assoc, 0, 8 * (size_t)c->mask_cap, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "mask words");
+    c->mask_dirty = false;
+  }
+  MaskArgs a{};
+  a.rows = c->b.rows;
+  a.first = c->b.first;
+  a.s_hit = c->b.s_hit;
+  a.row = c->b.row;
+  a.N = (int)N;
+  a.I = c->b.I;
+  a.assoc = c->mask_assoc;
+  a.tube = P.tube_cm;
+  a.max_qpt = (float)(1.0 / (double)P.min_pt_gev);
+  a.max_snp = (float)std::sin((double)P.max_incl_deg * M_PI / 180.0);
+  a.err = c->b.err;
+  a.mask = mask;
+  a.owner = owner;
+  a.leg = leg;
+  if (!tracks) {  // the context's own output of the last tpc_track(): counts read on the device
+    a.trk = c->b.trk;
+    a.ids = c->b.trk_ids;
+    a.counts = c->b.counts;
+  } else {
+    a.trk = tracks;
+    a.ids = cluster_ids;
+    a.n_trk = (long long)n_tracks;
+    a.n_ids = (long long)n_ids;
+  }
+  char* st = nullptr;
+  size_t off_trk = 0, off_ids = 0, off_leg = 0, off_mask = 0, off_own = 0;
+  if (!on_device) {  // stage the host arrays
+    auto al = [](size_t v) { return (v + 255) & ~size_t(255); };
+    const uint64_t nt = tracks ? n_tracks : (leg ? n_tracks : 0);
+    off_trk = 0;
+    off_ids = off_trk + al(tracks ? sizeof(tpc_track_t) * n_tracks : 0);
+    off_leg = off_ids + al(tracks ? 4 * n_ids : 0);
+    off_mask = off_leg + al(leg ? nt : 0);
+    off_own = off_mask + al((size_t)N);
+    const size_t total = off_own + al(owner ? 4 * (size_t)N : 0);
+    if (total > c->mask_stage_bytes) {
+      persist_free(c, c->mask_stage);
+      c->mask_stage = persist_alloc(c, total);
+      c->mask_stage_bytes = c->mask_stage ? total : 0;
+      if (!c->mask_stage) return fail(c, TPC_ERR_OOM, "mask staging");
+    }
+    st = (char*)c->mask_stage;
+    if (tracks && n_tracks &&
+        (e = cudaMemcpyAsync(st + off_trk, tracks, sizeof(tpc_track_t) * n_tracks, cudaMemcpyHostToDevice,
+                             c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "track upload");
+    if (tracks && n_ids &&
+        (e = cudaMemcpyAsync(st + off_ids, cluster_ids, 4 * n_ids, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "id upload");
+    if (leg && nt && (e = cudaMemcpyAsync(st + off_leg, leg, nt, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "leg upload");
+    if (tracks) {
+      a.trk = st + off_trk;
+      a.ids = (const uint32_t*)(st + off_ids);
+    }
+    if (leg) a.leg = (const uint8_t*)(st + off_leg);
+    a.mask = (uint8_t*)(st + off_mask);
+    a.owner = owner ? (int*)(st + off_own) : nullptr;
+  }
+  c->mask_timed = c->have_events;
+  if ((e = launch_masks(a, c->par, c->lc.num_sms, c->stream, c->have_events ? c->mask_ev : nullptr)) != cudaSuccess) {
+    c->mask_dirty = true;
+    return cuda_fail(c, e, "mask launch");
+  }
+  if (on_device) return TPC_OK;
+  if ((e = cudaMemcpyAsync(mask, a.mask, (size_t)N, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (owner && (e = cudaMemcpyAsync(owner, a.owner, 4 * (size_t)N, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess))
+    return cuda_fail(c, e, "mask download");
+  unsigned int err = 0;
+  if ((e = cudaMemcpyAsync(&err, c->b.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "mask sync");
+  if (err & TPC_DERR_BAD_TRACK)
+    return fail(c, TPC_ERR_BAD_INPUT, "a track refers to an item or cluster out of range (skipped)");
+  return TPC_OK;
+}
+
 extern "C" void tpc_destroy(tpc_ctx* c) {
   if (!c) return;
   cudaSetDevice(c->cfg.device);
@@ -1177,6 +1303,7 @@ extern "C" void tpc_destroy(tpc_ctx* c) {
   while (!c->persist.empty()) persist_free(c, c->persist.back());
   if (c->have_events)
     for (int i = 0; i <= TPC_N_STAGES; ++i) cudaEventDestroy(c->ev[i]);
+    for (int i = 0; i < 3; ++i) cudaEventDestroy(c->mask_ev[i]);
   if (c->own_stream) {
     cudaStreamSynchronize(c->stream);
     cudaStreamDestroy(c->stream);

@@ -12,6 +12,7 @@
 #define TPC_DERR_BAD_INPUT 1u
 #define TPC_DERR_ROW_CAP 2u
 #define TPC_DERR_TIMEOUT 4u
+#define TPC_DERR_BAD_TRACK 8u  // a track given to tpc_cluster_masks refers to an item or cluster out of range
 
 // One (item, pad row) of the binning grid: 32 bytes, one load.
 struct RowInfo {
@@ -133,6 +134,7 @@ struct Buffers {
 };
 
 #define TPC_N_STAGES 11  // 9 plain-mode steps, then the batched kernel and its compaction
+#define TPC_N_REPORTED_STAGES 13  // ... then the two kernels of tpc_cluster_masks
 
 struct LaunchCfg {
   int n_rows;
@@ -185,3 +187,24 @@ struct CodecOut {
 bool codec_vector_ok(const CodecIn& in, const CodecOut& out);
 cudaError_t launch_encode(const CodecIn& in, const CodecOut& out, long long n, int n_rows, unsigned long long* n_bad,
                           int num_sms, cudaStream_t s);
+
+// Cluster association and removal masks (tpc_reduce.cu).
+struct MaskArgs {
+  const RowInfo* rows;        // the tracker's per-(item, row) grids of the loaded batch
+  const int* first;
+  const int4* s_hit;          // sorted hits (qy, qz, original id, item*NR+row)
+  const int* row;             // input pad row of every cluster
+  int N, I;
+  const void* trk;            // tpc_track_t records
+  const uint32_t* ids;        // cluster ids of the tracks
+  const unsigned long long* counts;  // device (n_trk, n_ids) of the context's own output, or null
+  long long n_trk, n_ids;     // used when counts is null
+  const uint8_t* leg;         // per track, 0 = primary; null = all primary
+  unsigned long long* assoc;  // per cluster: best (pT, track) key, 0 = none; zero on entry and on exit
+  uint8_t* mask;
+  int* owner;                 // nullable
+  float tube, max_qpt, max_snp;
+  unsigned int* err;          // the batch's error word (TPC_DERR_BAD_TRACK)
+};
+// ev (nullable): 3 events recorded around the two kernels
+cudaError_t launch_masks(const MaskArgs& a, const DevParams& par, int num_sms, cudaStream_t s, cudaEvent_t* ev);

@@ -191,3 +191,173 @@ cudaError_t launch_encode(const CodecIn& in, const CodecOut& out, long long n, i
     k_encode_scalar<<<(unsigned)blocks, threads, 0, s>>>(in, out, n, n_rows, n_bad);
   return cudaGetLastError();
 }
+
+// ============================================================================
+// Cluster association, protection and removal masks (Sec. 4, cluster removal).
+//
+// Pass 1 (k_mask_assoc), one warp per track: every candidate (track, cluster)
+// pair bids the 64-bit key (~bits(|q/pT|) << 32 | ~track) into the cluster's
+// word with atomicMax, so the highest pT wins and equal pT goes to the smaller
+// track index whatever the order of the bids.  The lanes first bid for the
+// track's own clusters (attachment), then take one pad row each of the track's
+// row span, place the track on the row, and scan the bins of the tracker's
+// y-z grid that overlap the tube's bounding box, bidding for every hit inside
+// the tube (adjacency).  Pass 2 (k_mask_final), one thread per cluster: the
+// winning track's pT, leg and local inclination at the cluster's row decide
+// protection and the two strategies; the word is cleared for the next call.
+#include <climits>
+
+#include "tpc.h"
+
+namespace {
+
+constexpr float MASK_SNP_LIMIT = 0.9999f;  // the tracker's propagation validity
+enum : uint8_t { M_ASSOC = 1, M_PROT = 2, M_REMOVE_A = 4, M_REMOVE_B = 8 };
+
+// (y, z) where the track crosses the plane x = X (helix model of the tracker:
+// sin phi linear in x, chord slope (s1 + s2) / (c1 + c2), arc length from
+// asin); false where the track does not reach X.
+__device__ __forceinline__ bool track_at(const tpc_track_t& t, float kB, float X, float* yo, float* zo) {
+  const float dx = X - t.x_ref;
+  const float kappa = kB * t.qpt;
+  const float s1 = t.snp, s2 = s1 - kappa * dx;
+  if (!(fabsf(s1) < MASK_SNP_LIMIT) || !(fabsf(s2) < MASK_SNP_LIMIT)) return false;
+  const float c1 = sqrtf(1.0f - s1 * s1), c2 = sqrtf(1.0f - s2 * s2);
+  const float T = (s1 + s2) / (c1 + c2);
+  const float w = sqrtf(1.0f + T * T);
+  const float u = 0.5f * kappa * fabsf(dx) * w;
+  if (!(fabsf(u) < 1.0f)) return false;
+  float f;
+  if (fabsf(u) < 0.1f) {
+    const float u2 = u * u;
+    f = 1.0f + u2 * (1.0f / 6.0f + u2 * (3.0f / 40.0f + u2 * (5.0f / 112.0f)));
+  } else {
+    f = asinf(u) / u;
+  }
+  *yo = t.y + dx * T;
+  *zo = t.z + t.tgl * (dx * w * f);
+  return true;
+}
+
+// bins [a, e] of the values [lo, hi] along one axis of a row grid; e < a if none
+__device__ __forceinline__ void axis_bins(long long lo, long long hi, int vmin, int shift, int nbin, int* a, int* e) {
+  const long long vmax = (long long)vmin + ((long long)nbin << shift) - 1;
+  if (nbin == 0 || hi < vmin || lo > vmax) {
+    *a = 0;
+    *e = -1;
+    return;
+  }
+  *a = lo <= vmin ? 0 : (int)((lo - vmin) >> shift);
+  const long long t = (hi - vmin) >> shift;
+  *e = t < nbin - 1 ? (int)t : nbin - 1;
+}
+
+__global__ void k_mask_assoc(const __grid_constant__ MaskArgs a, const __grid_constant__ DevParams par) {
+  const int lane = threadIdx.x & 31;
+  const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const long long n_warps = ((long long)gridDim.x * blockDim.x) >> 5;
+  const long long n_trk = a.counts ? (long long)a.counts[0] : a.n_trk;
+  const long long n_ids = a.counts ? (long long)a.counts[1] : a.n_ids;
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const float Q = 1.0f / TPC_QSCALE;
+  const float tube2 = a.tube * a.tube;
+  const int NR = par.n_rows;
+  for (long long t = warp; t < n_trk; t += n_warps) {
+    const tpc_track_t T = trk[t];
+    const long long first = T.first_cluster, cnt = T.n_clusters;
+    if (T.item >= (uint32_t)a.I || first + cnt > n_ids) {
+      if (lane == 0) atomicOr(a.err, TPC_DERR_BAD_TRACK);
+      continue;
+    }
+    if (cnt == 0) continue;
+    const unsigned long long key =
+        ((unsigned long long)(~__float_as_uint(fabsf(T.qpt))) << 32) | (0xFFFFFFFFull - (unsigned long long)t);
+    // attachment: the track's own clusters
+    bool bad = false;
+    for (long long j = lane; j < cnt; j += 32) {
+      const uint32_t id = a.ids[first + j];
+      if (id < (uint32_t)a.N)
+        atomicMax(a.assoc + id, key);
+      else
+        bad = true;
+    }
+    if (__any_sync(0xffffffffu, bad)) {
+      if (lane == 0) atomicOr(a.err, TPC_DERR_BAD_TRACK);
+      continue;
+    }
+    // adjacency: the tube on every row of the span
+    const int ra = a.row[a.ids[first]], rb = a.row[a.ids[first + cnt - 1]];
+    const int lo = max(0, min(ra, rb)), hi = min(NR - 1, max(ra, rb));
+    for (int r = lo + lane; r <= hi; r += 32) {
+      float yt, zt;
+      if (!track_at(T, par.kB, par.x[r], &yt, &zt)) continue;
+      yt = fminf(1.0e6f, fmaxf(-1.0e6f, yt));  // keeps the box arithmetic in range (NaN: no hit passes)
+      zt = fminf(1.0e6f, fmaxf(-1.0e6f, zt));
+      const RowInfo ri = a.rows[(long long)T.item * NR + r];
+      if (ri.n == 0) continue;
+      int iy0, iy1, iz0, iz1;
+      axis_bins((long long)floorf((yt - a.tube) * TPC_QSCALE) - 2, (long long)ceilf((yt + a.tube) * TPC_QSCALE) + 2,
+                ri.ymin, ri.shift, ri.ny, &iy0, &iy1);
+      axis_bins((long long)floorf((zt - a.tube) * TPC_QSCALE) - 2, (long long)ceilf((zt + a.tube) * TPC_QSCALE) + 2,
+                ri.zmin, ri.shift, ri.nz, &iz0, &iz1);
+      if (iz1 < iz0) continue;
+      for (int iy = iy0; iy <= iy1; ++iy) {
+        const int b0 = ri.bin0 + iy * ri.nz;
+        const int h1 = a.first[b0 + iz1 + 1];
+        for (int h = a.first[b0 + iz0]; h < h1; ++h) {
+          const int4 q = a.s_hit[h];
+          const float dy = (float)q.x * Q - yt, dz = (float)q.y * Q - zt;
+          if (dy * dy + dz * dz <= tube2) atomicMax(a.assoc + q.z, key);
+        }
+      }
+    }
+  }
+}
+
+__global__ void k_mask_final(const __grid_constant__ MaskArgs a, const __grid_constant__ DevParams par) {
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += stride) {
+    const unsigned long long key = a.assoc[c];
+    uint8_t m = M_REMOVE_B;
+    int w = -1;
+    if (key) {
+      a.assoc[c] = 0;
+      w = (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
+      const float x_ref = trk[w].x_ref, snp = trk[w].snp, qpt = trk[w].qpt;
+      const int r = a.row[c];
+      const float X = (r >= 0 && r < par.n_rows) ? par.x[r] : x_ref;
+      const float s = fabsf(snp - par.kB * qpt * (X - x_ref));
+      const bool prot = fabsf(qpt) < a.max_qpt && (!a.leg || a.leg[w] == 0) && s < a.max_snp;
+      m = prot ? (M_ASSOC | M_PROT) : (M_ASSOC | M_REMOVE_A | M_REMOVE_B);
+    }
+    a.mask[c] = m;
+    if (a.owner) a.owner[c] = w;
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_masks(const MaskArgs& a, const DevParams& par, int num_sms, cudaStream_t s, cudaEvent_t* ev) {
+  if (a.N <= 0) return cudaSuccess;
+  // grid-stride kernels sized to one resident wave
+  static int per_sm[2] = {0, 0};
+  if (!per_sm[0]) {
+    cudaError_t e;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_mask_assoc, 256, 0)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_mask_final, 256, 0)) != cudaSuccess) {
+      per_sm[0] = 0;
+      return e;
+    }
+    per_sm[0] = per_sm[0] < 1 ? 1 : per_sm[0];
+    per_sm[1] = per_sm[1] < 1 ? 1 : per_sm[1];
+  }
+  if (ev) cudaEventRecord(ev[0], s);
+  k_mask_assoc<<<num_sms * per_sm[0], 256, 0, s>>>(a, par);
+  if (ev) cudaEventRecord(ev[1], s);
+  long long blocks = ((long long)a.N + 255) / 256;
+  if (blocks > (long long)num_sms * per_sm[1]) blocks = (long long)num_sms * per_sm[1];
+  k_mask_final<<<(unsigned)blocks, 256, 0, s>>>(a, par);
+  if (ev) cudaEventRecord(ev[2], s);
+  return cudaGetLastError();
+}

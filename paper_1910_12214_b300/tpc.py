@@ -63,6 +63,12 @@ class tpc_cluster_codes(C.Structure):
                 ("q_max", C.c_void_p), ("sigma_y", C.c_void_p), ("sigma_z", C.c_void_p)]
 
 
+class tpc_mask_params(C.Structure):
+    _fields_ = [("tube_cm", C.c_float), ("min_pt_gev", C.c_float), ("max_incl_deg", C.c_float)]
+
+
+MASK_ASSOCIATED, MASK_PROTECTED, MASK_REMOVE_A, MASK_REMOVE_B = 1, 2, 4, 8
+
 PROP_FIELDS = (("y", np.float32), ("z", np.float32), ("row", np.int32), ("q_tot", np.float32),
                ("q_max", np.float32), ("sigma_y", np.float32), ("sigma_z", np.float32))
 CODE_FIELDS = (("y", np.int16), ("z", np.int32), ("row", np.uint8), ("q_tot", np.uint16), ("q_max", np.uint16),
@@ -101,6 +107,8 @@ _sig = {
     "tpc_bin_sector_noalloc": ([_P, _P, _P, C.c_uint32, C.c_int, _P, _P, _P, _P], C.c_int),
     "tpc_encode_clusters": ([_P, C.POINTER(tpc_cluster_props), C.POINTER(tpc_cluster_codes), C.c_int,
                              C.POINTER(C.c_uint64)], C.c_int),
+    "tpc_cluster_masks": ([_P, C.POINTER(tpc_mask_params), _P, C.c_uint64, _P, C.c_uint64, _P, C.c_int, _P, _P],
+                          C.c_int),
     "tpc_destroy": ([_P], None),
     "tpc_last_error": ([_P], C.c_char_p),
 }
@@ -207,6 +215,7 @@ class Tracker:
                          _ptr(ev), _ptr(core), int(bool(on_device)))
         self._check(_lib.tpc_load_clusters(self._h, C.byref(c)))
         self._loaded = (cl, keep) if on_device else None
+        self.n_loaded = n
         return self
 
     def track(self):
@@ -355,6 +364,37 @@ class Tracker:
         if st not in (TPC_OK, 7):
             self._check(st)
         return out, (int(bad.value) if want else None)
+
+    def cluster_masks(self, tracks=None, ids=None, leg=None, tube=1.5, min_pt=0.05, max_incl_deg=70.0,
+                      on_device=False, with_owner=True, n_tracks=None):
+        """Association, protection and strategy A/B removal masks of the loaded
+        clusters (Sec. 4; include/tpc_reduce.h).  tracks=None uses the last
+        tpc_track() output on the device; else tracks (TRACK_DTYPE records, or
+        with on_device a CUDA uint8 tensor [n, 112]) and ids (uint32).  leg: one
+        byte per track (0 = primary) or None; with tracks=None pass n_tracks.
+        Returns (mask uint8, owner int32 or None) per loaded cluster: numpy, or
+        CUDA tensors with on_device (enqueued on the tracker's stream)."""
+        prm = tpc_mask_params(tube, min_pt, max_incl_deg)
+        n = self.n_loaded
+        if on_device:
+            import torch
+            dev = torch.device("cuda", self.cfg.device)
+            mask = torch.empty(max(n, 1), dtype=torch.uint8, device=dev)[:n]
+            owner = torch.empty(max(n, 1), dtype=torch.int32, device=dev)[:n] if with_owner else None
+            nt = int(tracks.shape[0]) if tracks is not None else int(n_tracks or 0)
+        else:
+            mask = np.empty(n, np.uint8)
+            owner = np.empty(n, np.int32) if with_owner else None
+            if tracks is not None:
+                tracks = np.ascontiguousarray(tracks, TRACK_DTYPE)
+                ids = np.ascontiguousarray(ids, np.uint32)
+            if leg is not None:
+                leg = np.ascontiguousarray(leg, np.uint8)
+            nt = int(tracks.shape[0]) if tracks is not None else int(n_tracks or 0)
+        ni = int(ids.shape[0]) if ids is not None else 0
+        self._check(_lib.tpc_cluster_masks(self._h, C.byref(prm), _ptr(tracks), nt, _ptr(ids), ni, _ptr(leg),
+                                           int(on_device), _ptr(mask), _ptr(owner)))
+        return mask, owner
 
     def close(self):
         if getattr(self, "_h", None):
