@@ -252,6 +252,43 @@ __device__ __forceinline__ void axis_bins(long long lo, long long hi, int vmin, 
   *e = t < nbin - 1 ? (int)t : nbin - 1;
 }
 
+// Bids `key` for every hit of grid row `ri` inside the tube around (yt, zt).
+__device__ __forceinline__ void scan_row(const MaskArgs& a, const RowInfo& ri, float yt, float zt, float tube2,
+                                         unsigned long long key) {
+  const float Q = 1.0f / TPC_QSCALE;
+  // the tube's bounding box in quanta (2 quanta of margin) and its bins
+  const int qy0 = (int)floorf((yt - a.tube) * TPC_QSCALE) - 2, qy1 = (int)ceilf((yt + a.tube) * TPC_QSCALE) + 2;
+  const int qz0 = (int)floorf((zt - a.tube) * TPC_QSCALE) - 2, qz1 = (int)ceilf((zt + a.tube) * TPC_QSCALE) + 2;
+  int iy0, iy1, iz0, iz1;
+  axis_bins(qy0, qy1, ri.ymin, ri.shift, ri.ny, &iy0, &iy1);
+  axis_bins(qz0, qz1, ri.zmin, ri.shift, ri.nz, &iz0, &iz1);
+  if (iz1 < iz0 || iy1 < iy0) return;
+  for (int iy = iy0; iy <= iy1; iy += 2) {
+    // the hit ranges of two y-bin rows at once (bins iz0..iz1 of a y-bin row are contiguous)
+    const int b0 = ri.bin0 + iy * ri.nz;
+    const bool two = iy + 1 <= iy1;
+    const int a0 = a.first[b0 + iz0], e0 = a.first[b0 + iz1 + 1];
+    const int a1 = two ? a.first[b0 + ri.nz + iz0] : 0, e1 = two ? a.first[b0 + ri.nz + iz1 + 1] : 0;
+    const int n0 = e0 - a0, total = n0 + (e1 - a1);
+    // candidates four at a time: four independent loads in flight, an integer
+    // test against the box, then the distance of the survivors
+    for (int j0 = 0; j0 < total; j0 += 4) {
+      int4 q[4];
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const int j = j0 + k;
+        q[k] = j < total ? a.s_hit[j < n0 ? a0 + j : a1 + (j - n0)] : make_int4(INT_MIN, INT_MIN, 0, 0);
+      }
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        if (q[k].x < qy0 || q[k].x > qy1 || q[k].y < qz0 || q[k].y > qz1) continue;
+        const float dy = (float)q[k].x * Q - yt, dz = (float)q[k].y * Q - zt;
+        if (dy * dy + dz * dz <= tube2) atomicMax(a.assoc + q[k].z, key);
+      }
+    }
+  }
+}
+
 __global__ void k_mask_assoc(const __grid_constant__ MaskArgs a, const __grid_constant__ DevParams par) {
   const int lane = threadIdx.x & 31;
   const long long warp = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
@@ -259,7 +296,6 @@ __global__ void k_mask_assoc(const __grid_constant__ MaskArgs a, const __grid_co
   const long long n_trk = a.counts ? (long long)a.counts[0] : a.n_trk;
   const long long n_ids = a.counts ? (long long)a.counts[1] : a.n_ids;
   const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
-  const float Q = 1.0f / TPC_QSCALE;
   const float tube2 = a.tube * a.tube;
   const int NR = par.n_rows;
   for (long long t = warp; t < n_trk; t += n_warps) {
@@ -288,51 +324,85 @@ __global__ void k_mask_assoc(const __grid_constant__ MaskArgs a, const __grid_co
     // adjacency: the tube on every row of the span
     const int ra = a.row[a.ids[first]], rb = a.row[a.ids[first + cnt - 1]];
     const int lo = max(0, min(ra, rb)), hi = min(NR - 1, max(ra, rb));
-    for (int r = lo + lane; r <= hi; r += 32) {
-      float yt, zt;
-      if (!track_at(T, par.kB, par.x[r], &yt, &zt)) continue;
-      yt = fminf(1.0e6f, fmaxf(-1.0e6f, yt));  // keeps the box arithmetic in range (NaN: no hit passes)
-      zt = fminf(1.0e6f, fmaxf(-1.0e6f, zt));
-      const RowInfo ri = a.rows[(long long)T.item * NR + r];
-      if (ri.n == 0) continue;
-      int iy0, iy1, iz0, iz1;
-      axis_bins((long long)floorf((yt - a.tube) * TPC_QSCALE) - 2, (long long)ceilf((yt + a.tube) * TPC_QSCALE) + 2,
-                ri.ymin, ri.shift, ri.ny, &iy0, &iy1);
-      axis_bins((long long)floorf((zt - a.tube) * TPC_QSCALE) - 2, (long long)ceilf((zt + a.tube) * TPC_QSCALE) + 2,
-                ri.zmin, ri.shift, ri.nz, &iz0, &iz1);
-      if (iz1 < iz0) continue;
-      for (int iy = iy0; iy <= iy1; ++iy) {
-        const int b0 = ri.bin0 + iy * ri.nz;
-        const int h1 = a.first[b0 + iz1 + 1];
-        for (int h = a.first[b0 + iz0]; h < h1; ++h) {
-          const int4 q = a.s_hit[h];
-          const float dy = (float)q.x * Q - yt, dz = (float)q.y * Q - zt;
-          if (dy * dy + dz * dz <= tube2) atomicMax(a.assoc + q.z, key);
-        }
+    // one row per lane; the next row's crossing point and grid record are
+    // requested before the current row's bins are scanned (software pipeline)
+    int r = lo + lane;
+    bool ok = false;
+    float yt = 0.f, zt = 0.f;
+    RowInfo ri{};
+    if (r <= hi && (ok = track_at(T, par.kB, par.x[r], &yt, &zt))) ri = a.rows[(long long)T.item * NR + r];
+    while (r <= hi) {
+      const int rn = r + 32;
+      bool okn = false;
+      float ytn = 0.f, ztn = 0.f;
+      RowInfo rin{};
+      if (rn <= hi && (okn = track_at(T, par.kB, par.x[rn], &ytn, &ztn))) rin = a.rows[(long long)T.item * NR + rn];
+      if (ok && ri.n > 0) {
+        yt = fminf(1.0e6f, fmaxf(-1.0e6f, yt));  // keeps the box arithmetic in range (NaN: no hit passes)
+        zt = fminf(1.0e6f, fmaxf(-1.0e6f, zt));
+        scan_row(a, ri, yt, zt, tube2, key);
       }
+      r = rn;
+      ok = okn;
+      yt = ytn;
+      zt = ztn;
+      ri = rin;
     }
   }
 }
 
+// Mask and owner of one cluster from its association word.
+__device__ __forceinline__ void final_one(const MaskArgs& a, const DevParams& par, const tpc_track_t* trk,
+                                          unsigned long long key, int r, uint8_t* m, int* w) {
+  *m = M_REMOVE_B;
+  *w = -1;
+  if (!key) return;
+  const int t = (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
+  const float x_ref = trk[t].x_ref, snp = trk[t].snp, qpt = trk[t].qpt;
+  const float X = (r >= 0 && r < par.n_rows) ? par.x[r] : x_ref;
+  const float s = fabsf(snp - par.kB * qpt * (X - x_ref));
+  const bool prot = fabsf(qpt) < a.max_qpt && (!a.leg || a.leg[t] == 0) && s < a.max_snp;
+  *m = prot ? (M_ASSOC | M_PROT) : (M_ASSOC | M_REMOVE_A | M_REMOVE_B);
+  *w = t;
+}
+
+// VEC: four clusters per thread with 16-byte loads of the words and rows and
+// vector stores of masks and owners (row 16-, mask 4-, owner 16-byte aligned);
+// the words are cleared for the next call.
+template <bool VEC>
 __global__ void k_mask_final(const __grid_constant__ MaskArgs a, const __grid_constant__ DevParams par) {
   const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
   const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += stride) {
-    const unsigned long long key = a.assoc[c];
-    uint8_t m = M_REMOVE_B;
-    int w = -1;
-    if (key) {
-      a.assoc[c] = 0;
-      w = (int)(0xFFFFFFFFu - (unsigned)(key & 0xFFFFFFFFull));
-      const float x_ref = trk[w].x_ref, snp = trk[w].snp, qpt = trk[w].qpt;
-      const int r = a.row[c];
-      const float X = (r >= 0 && r < par.n_rows) ? par.x[r] : x_ref;
-      const float s = fabsf(snp - par.kB * qpt * (X - x_ref));
-      const bool prot = fabsf(qpt) < a.max_qpt && (!a.leg || a.leg[w] == 0) && s < a.max_snp;
-      m = prot ? (M_ASSOC | M_PROT) : (M_ASSOC | M_REMOVE_A | M_REMOVE_B);
+  const long long i0 = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  long long done = 0;
+  if constexpr (VEC) {
+    const long long nq = (long long)a.N >> 2;
+    ulonglong2* w2 = reinterpret_cast<ulonglong2*>(a.assoc);
+    for (long long q = i0; q < nq; q += stride) {
+      const ulonglong2 k01 = w2[2 * q], k23 = w2[2 * q + 1];
+      const int4 r = reinterpret_cast<const int4*>(a.row)[q];
+      if (k01.x | k01.y) w2[2 * q] = make_ulonglong2(0, 0);
+      if (k23.x | k23.y) w2[2 * q + 1] = make_ulonglong2(0, 0);
+      uint8_t m0, m1, m2, m3;
+      int o0, o1, o2, o3;
+      final_one(a, par, trk, k01.x, r.x, &m0, &o0);
+      final_one(a, par, trk, k01.y, r.y, &m1, &o1);
+      final_one(a, par, trk, k23.x, r.z, &m2, &o2);
+      final_one(a, par, trk, k23.y, r.w, &m3, &o3);
+      reinterpret_cast<unsigned*>(a.mask)[q] =
+          (unsigned)m0 | ((unsigned)m1 << 8) | ((unsigned)m2 << 16) | ((unsigned)m3 << 24);
+      if (a.owner) reinterpret_cast<int4*>(a.owner)[q] = make_int4(o0, o1, o2, o3);
     }
+    done = 4 * nq;
+  }
+  for (long long c = done + i0; c < a.N; c += stride) {
+    const unsigned long long key = a.assoc[c];
+    if (key) a.assoc[c] = 0;
+    uint8_t m;
+    int o;
+    final_one(a, par, trk, key, a.row[c], &m, &o);
     a.mask[c] = m;
-    if (a.owner) a.owner[c] = w;
+    if (a.owner) a.owner[c] = o;
   }
 }
 
@@ -341,23 +411,29 @@ __global__ void k_mask_final(const __grid_constant__ MaskArgs a, const __grid_co
 cudaError_t launch_masks(const MaskArgs& a, const DevParams& par, int num_sms, cudaStream_t s, cudaEvent_t* ev) {
   if (a.N <= 0) return cudaSuccess;
   // grid-stride kernels sized to one resident wave
-  static int per_sm[2] = {0, 0};
+  static int per_sm[3] = {0, 0, 0};
   if (!per_sm[0]) {
     cudaError_t e;
     if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_mask_assoc, 256, 0)) != cudaSuccess ||
-        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_mask_final, 256, 0)) != cudaSuccess) {
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_mask_final<true>, 256, 0)) != cudaSuccess ||
+        (e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_mask_final<false>, 256, 0)) != cudaSuccess) {
       per_sm[0] = 0;
       return e;
     }
-    per_sm[0] = per_sm[0] < 1 ? 1 : per_sm[0];
-    per_sm[1] = per_sm[1] < 1 ? 1 : per_sm[1];
+    for (int& v : per_sm) v = v < 1 ? 1 : v;
   }
+  auto al = [](const void* p, uintptr_t n) { return (reinterpret_cast<uintptr_t>(p) & (n - 1)) == 0; };
+  const bool vec = al(a.row, 16) && al(a.mask, 4) && (!a.owner || al(a.owner, 16)) && al(a.assoc, 16);
   if (ev) cudaEventRecord(ev[0], s);
   k_mask_assoc<<<num_sms * per_sm[0], 256, 0, s>>>(a, par);
   if (ev) cudaEventRecord(ev[1], s);
-  long long blocks = ((long long)a.N + 255) / 256;
-  if (blocks > (long long)num_sms * per_sm[1]) blocks = (long long)num_sms * per_sm[1];
-  k_mask_final<<<(unsigned)blocks, 256, 0, s>>>(a, par);
+  long long blocks = (((long long)a.N >> (vec ? 2 : 0)) + 255) / 256;
+  const long long cap = (long long)num_sms * per_sm[vec ? 1 : 2];
+  blocks = blocks < 1 ? 1 : (blocks > cap ? cap : blocks);
+  if (vec)
+    k_mask_final<true><<<(unsigned)blocks, 256, 0, s>>>(a, par);
+  else
+    k_mask_final<false><<<(unsigned)blocks, 256, 0, s>>>(a, par);
   if (ev) cudaEventRecord(ev[2], s);
   return cudaGetLastError();
 }

@@ -140,3 +140,28 @@ def test_edge_cases():
         t.cluster_masks(rec, ids)
     assert e.value.status == 7
     t.close()
+
+
+def test_unaligned_buffers_take_the_scalar_final_pass():
+    """Cluster arrays and outputs off their vector alignment: the scalar form of
+    the final pass gives the same masks and owners as the vector form."""
+    import torch
+    from paper_1910_12214_b300 import synth, tpc
+    cl = synth.make_config1(seed=8)
+    ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids"])
+    tf, ti, ids = oracle.oracle_tracks(ref)
+    rec = to_records(tf, ti)
+    with tracked(cl) as t:
+        want_m, want_o = t.cluster_masks(rec, ids)
+    d = type("D", (), {})()
+    for name in ("x", "y", "z", "row"):
+        a = torch.from_numpy(np.ascontiguousarray(getattr(cl, name)))
+        buf = torch.empty(a.shape[0] + 1, dtype=a.dtype, device="cuda")
+        buf[1:].copy_(a)
+        setattr(d, name, buf[1:])  # 4 bytes past a 16-byte boundary
+    d.item_off, d.item_sector, d.item_event, d.item_core = cl.item_off, cl.item_sector, cl.item_event, None
+    with tpc.Tracker(device=0) as t:
+        t.load(d, on_device=True).track()
+        t.sync()
+        mask, owner = t.cluster_masks(rec, ids)
+    assert np.array_equal(mask, want_m) and np.array_equal(owner, want_o)
