@@ -11,7 +11,7 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
 SRC = [os.path.join(HERE, f) for f in ("tpc_oracle.cpp", "corr_oracle.cpp", "mlp_oracle.cpp", "codec_oracle.cpp",
-                                                        "masks_oracle.cpp")
+                                                        "masks_oracle.cpp", "entropy_oracle.cpp")
        if os.path.exists(os.path.join(HERE, f))]
 
 
@@ -93,6 +93,17 @@ def _load():
         lib.orc_cluster_masks.argtypes = ([C.c_int, C.c_double, C.c_double, C.c_double, C.c_int64] + [C.c_void_p] * 4 +
                                           [C.c_int64, C.c_int64] + [C.c_void_p] * 4 + [C.c_double, C.c_float,
                                                                                      C.c_float] + [C.c_void_p] * 3)
+        lib.orc_compress.restype = C.c_int64
+        lib.orc_compress.argtypes = ([C.c_int, C.c_double, C.c_double, C.c_float, C.c_int64] + [C.c_void_p] * 7 +
+                                     [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64] + [C.c_void_p] * 4 + [C.c_int64])
+        lib.orc_decompress.restype = C.c_int64
+        lib.orc_decompress.argtypes = [C.c_void_p, C.c_int64, C.c_int64] + [C.c_void_p] * 9
+        lib.orc_code_stream.restype = C.c_int64
+        lib.orc_code_stream.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]
+        lib.orc_decode_stream.restype = C.c_int64
+        lib.orc_decode_stream.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]
+        lib.orc_predict.restype = None
+        lib.orc_predict.argtypes = [C.c_void_p, C.c_float, C.c_float, C.c_void_p, C.c_void_p]
         lib.orc_chi2.restype = C.c_double
         lib.orc_chi2.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         _lib = lib
@@ -320,3 +331,85 @@ def oracle_tracks(ref):
     tf = ref["trk_f"][:, :6].astype(np.float32)
     ti = ref["trk_i"][:, :3].astype(np.int64)
     return tf, ti, ref["trk_ids"].astype(np.uint32)
+
+
+def compress(cl, props, order, seg_off, trk_f, trk_i, ids, bz=0.5, n_rows=152, x_min=85.0, x_max=246.0):
+    """Compressed blob (bytes) of a tracked batch: entropy reduction and rANS
+    coding.  props: charges and sizes (q_tot, q_max, sigma_y, sigma_z);
+    order / seg_off: canonical order of the binned clusters and its (item, row)
+    segment offsets; tracks as for cluster_masks."""
+    lib = _load()
+    f32 = lambda a: np.ascontiguousarray(a, np.float32)
+    y, z = f32(cl.y), f32(cl.z)
+    row = np.ascontiguousarray(cl.row, np.int32)
+    pr = [f32(props[k]) for k in ("q_tot", "q_max", "sigma_y", "sigma_z")]
+    order = np.ascontiguousarray(order, np.int32)
+    seg_off = np.ascontiguousarray(seg_off, np.int64)
+    tf = np.ascontiguousarray(np.asarray(trk_f, np.float32).reshape(-1, 6))
+    ti = np.ascontiguousarray(np.asarray(trk_i, np.int64).reshape(-1, 3))
+    ids = np.ascontiguousarray(ids, np.uint32)
+    kB = np.float32(0.299792458e-2 * np.float32(bz))
+    n_items = (seg_off.shape[0] - 1) // n_rows
+    args = [n_rows, x_min, x_max, float(kB), y.shape[0], _p(y), _p(z), _p(row), *[_p(a) for a in pr], n_items,
+            _p(order), _p(seg_off), tf.shape[0], _p(tf), _p(ti), _p(ids)]
+    size = lib.orc_compress(*args, None, 0)
+    if size < 0:
+        raise ValueError("bad input")
+    out = np.empty(size, np.uint8)
+    lib.orc_compress(*args, _p(out), size)
+    return out
+
+
+def decompress(blob):
+    """Stored clusters of a blob: dict of item, row, y, z, q_tot, q_max,
+    sigma_y, sigma_z codes and track (-1 = unattached)."""
+    lib = _load()
+    blob = np.ascontiguousarray(blob, np.uint8)
+    n = lib.orc_decompress(_p(blob), blob.shape[0], 0, *([None] * 9))
+    if n < 0:
+        raise ValueError("malformed blob")
+    keys = ("item", "row", "y", "z", "q_tot", "q_max", "sigma_y", "sigma_z", "track")
+    out = {k: np.empty(n, np.int32) for k in keys}
+    if lib.orc_decompress(_p(blob), blob.shape[0], n, *[_p(out[k]) for k in keys]) != n:
+        raise ValueError("malformed blob")
+    return out
+
+
+def grid_order(ref, n_rows=152):
+    """(order, seg_off) of the oracle tracker's binning: canonical sorted ids and
+    the offsets of its (item, row) segments."""
+    rows = ref["rows"]
+    seg_off = np.zeros(rows.shape[0] + 1, np.int64)
+    seg_off[1:] = np.cumsum(rows[:, 1])
+    return ref["sorted_id"].astype(np.int32), seg_off
+
+
+def code_stream(values):
+    """One symbol stream (uint64 values) coded by byte planes and rANS, as in a blob."""
+    lib = _load()
+    v = np.ascontiguousarray(values, np.uint64)
+    n = lib.orc_code_stream(_p(v), v.shape[0], None, 0)
+    out = np.empty(n, np.uint8)
+    lib.orc_code_stream(_p(v), v.shape[0], _p(out), n)
+    return out
+
+
+def decode_stream(blob):
+    lib = _load()
+    b = np.ascontiguousarray(blob, np.uint8)
+    n = lib.orc_decode_stream(_p(b), b.shape[0], None, 0)
+    if n < 0:
+        raise ValueError("malformed stream")
+    v = np.empty(n, np.uint64)
+    lib.orc_decode_stream(_p(b), b.shape[0], _p(v), n)
+    return v
+
+
+def predict_codes(state6, bz, X):
+    """(y, z) codes of the track model at pad-row radius X (float32 arithmetic)."""
+    lib = _load()
+    st = np.ascontiguousarray(state6, np.float32)
+    py, pz = C.c_int64(), C.c_int64()
+    kB = np.float32(0.299792458e-2 * np.float32(bz))
+    lib.orc_predict(_p(st), float(kB), float(np.float32(X)), C.byref(py), C.byref(pz))
+    return int(py.value), int(pz.value)
