@@ -143,6 +143,68 @@ tpc_status tpc_cluster_masks(tpc_ctx* ctx, const tpc_mask_params* prm, const tpc
                              const uint32_t* cluster_ids, uint64_t n_ids, const uint8_t* leg, int on_device,
                              uint8_t* mask, int32_t* owner);
 
+/* ---- Compression of the clusters (Sec. 4, steps 3 and 4) ----------------
+ *
+ * The paper's steps: clusters not assigned to tracks are ordered in y and z
+ * and stored as differences to the previous cluster; clusters assigned to
+ * tracks are stored as residuals to the extrapolated track; an ANS entropy
+ * coder compresses the result.  This library's format (one self-contained
+ * little-endian blob):
+ *  - integer codes of every cluster as tpc_encode_clusters makes them;
+ *  - unattached clusters (in no track's cluster list) in the tracker's
+ *    canonical order of the pad row (the cells of its y-z grid, y-major, then
+ *    the cluster index): per (item, row) their number, then per cluster the
+ *    zigzag differences (0, -1, 1, -2 -> 0, 1, 2, 3) of the y and z codes to
+ *    the previous unattached cluster of the row (the first one to 0);
+ *  - attached clusters track by track, innermost first: the zigzag row
+ *    increment (the first to row 0) and the zigzag residuals of the y and z
+ *    codes to the track's prediction at that row (the tracker's helix from
+ *    the track's float32 state, asin(a)/a by two half-angle steps and a series
+ *    to a^8, every operation correctly rounded float32 without fused
+ *    multiply-add, rounded to the nearest code; 0 if not finite);
+ *  - the charge and size codes, unattached clusters first, then attached;
+ *  - 11 symbol streams (row counts, dy, dz, row increments, y and z
+ *    residuals, q_tot, q_max, sigma_y, sigma_z, clusters per track), each
+ *    split into byte planes (as many as its largest value needs, at least
+ *    one), each plane coded by rANS: 32-bit states, 16-bit renormalisation,
+ *    frequencies scaled to 4096 (f = max(1, floor(count*4096/total)) for
+ *    present bytes; an excess is taken one by one from the largest f,
+ *    smallest byte first; a shortfall goes to the largest f), chunks of 8192
+ *    symbols coded by 32 interleaved states (symbol i by state i mod 32), a
+ *    chunk being its final states (2 words each, low first) followed by the
+ *    renormalisation words in decoding order;
+ *  - layout: header (u32 magic 0x5A435054, u32 version 1, u32 items, u32
+ *    rows, u32 tracks, u32 bits of kB = 0.299792458e-2 * Bz as float32, f64
+ *    x of the first and last pad row, u64 unattached, u64 attached); per
+ *    stream u64 values, u32 planes, per plane u16 f[256], u32 chunks, u32
+ *    words per chunk, u16 words; then per track 7 u32: x_ref, y, z, sinphi,
+ *    tanlambda, q/pT (float32 bits) and item.
+ * Clusters excluded from the binning (bad row or non-finite position) are
+ * not stored. */
+typedef struct {
+  const float* q_tot;   /* one value per loaded cluster */
+  const float* q_max;
+  const float* sigma_y;
+  const float* sigma_z;
+} tpc_cluster_charges;
+
+/* Compresses the clusters loaded by tpc_load_clusters, with the tracker's
+ * binning of the last tpc_track() (TPC_ERR_STATE otherwise).
+ *  charges: charges and sizes of the loaded clusters.
+ *  tracks: NULL = the context's own tracks of the last tpc_track()
+ *    (n_tracks, cluster_ids, n_ids ignored); else n_tracks records (item,
+ *    first_cluster, n_clusters, x_ref, y, z, snp, tgl, qpt used) with
+ *    cluster_ids (indices of loaded clusters, innermost first per track).  A
+ *    track out of range (item, cluster id or row) gives TPC_ERR_BAD_INPUT.
+ *  on_device: 1 = charges, tracks, cluster_ids and out are device pointers;
+ *    0 = host pointers.
+ *  out, cap: the caller's buffer; *size receives the blob's size; if cap is
+ *    smaller nothing is copied and TPC_ERR_CAPACITY is returned (out may be
+ *    NULL with cap 0 to ask for the size).  The call waits for its stream. */
+tpc_status tpc_compress(tpc_ctx* ctx, const tpc_cluster_charges* charges, const tpc_track_t* tracks,
+                        uint64_t n_tracks, const uint32_t* cluster_ids, uint64_t n_ids, int on_device, uint8_t* out,
+                        uint64_t cap, uint64_t* size);
+
 #ifdef __cplusplus
 }
 #endif

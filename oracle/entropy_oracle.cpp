@@ -84,8 +84,9 @@ void predict(const float* st, float kB, float X, int64_t* py, int64_t* pz) {
     g = 4.0f * a2 * ser / a;
   }
   const float z = z0 + tgl * (chord * g);
-  *py = (int64_t)std::nearbyint((double)y * 64.0);
-  *pz = (int64_t)std::nearbyint((double)z * 64.0);
+  // code of a prediction; 0 where it is not finite or beyond the codes' reach
+  *py = std::fabs(y) < 1.0e17f ? (int64_t)std::nearbyint((double)y * 64.0) : 0;
+  *pz = std::fabs(z) < 1.0e17f ? (int64_t)std::nearbyint((double)z * 64.0) : 0;
 }
 
 void scale_freqs(const uint64_t* cnt, uint16_t* f) {

@@ -69,6 +69,9 @@ struct tpc_ctx {
   bool mask_dirty = false;
   void* mask_stage = nullptr;
   size_t mask_stage_bytes = 0;
+  // compression: persistent work buffers, grown on demand
+  void* cmp_buf[32] = {};
+  size_t cmp_cap[32] = {};
 };
 
 namespace {
@@ -1293,6 +1296,197 @@ extern "C" tpc_status tpc_cluster_masks(tpc_ctx* c, const tpc_mask_params* prm, 
     return cuda_fail(c, e, "mask sync");
   if (err & TPC_DERR_BAD_TRACK)
     return fail(c, TPC_ERR_BAD_INPUT, "a track refers to an item or cluster out of range (skipped)");
+  return TPC_OK;
+}
+
+// ---- compression (Sec. 4, steps 3 and 4) ----
+
+namespace {
+
+// persistent buffer slot i with at least `bytes` bytes (contents not kept on growth)
+void* cmp_buffer(tpc_ctx* c, int i, size_t bytes) {
+  bytes = std::max<size_t>(bytes, 256);
+  if (c->cmp_cap[i] >= bytes) return c->cmp_buf[i];
+  persist_free(c, c->cmp_buf[i]);
+  c->cmp_buf[i] = persist_alloc(c, bytes + bytes / 4);
+  c->cmp_cap[i] = c->cmp_buf[i] ? bytes + bytes / 4 : 0;
+  return c->cmp_buf[i];
+}
+
+}  // namespace
+
+extern "C" tpc_status tpc_compress(tpc_ctx* c, const tpc_cluster_charges* ch, const tpc_track_t* tracks,
+                                   uint64_t n_tracks, const uint32_t* cluster_ids, uint64_t n_ids, int on_device,
+                                   uint8_t* out, uint64_t cap, uint64_t* size) {
+  if (!c || !ch || !size) return fail(c, TPC_ERR_INVALID_ARG, "null argument");
+  if (!c->tracked) return fail(c, TPC_ERR_STATE, "tpc_compress before tpc_track");
+  *size = 0;
+  const long long N = c->b.N;
+  if (N > 0 && (!ch->q_tot || !ch->q_max || !ch->sigma_y || !ch->sigma_z))
+    return fail(c, TPC_ERR_INVALID_ARG, "null charge array");
+  if (tracks && n_tracks && !cluster_ids) return fail(c, TPC_ERR_INVALID_ARG, "null cluster ids");
+  if (cap && !out) return fail(c, TPC_ERR_INVALID_ARG, "null output");
+  cudaError_t e;
+  // tracks: the context's own (their count read back) or the caller's (staged if on the host)
+  const void* trk;
+  const uint32_t* ids;
+  long long nt, ni;
+  if (!tracks) {
+    unsigned long long cnt[2];
+    if ((e = cudaMemcpyAsync(cnt, c->b.counts, 16, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "track counts");
+    trk = c->b.trk;
+    ids = c->b.trk_ids;
+    nt = (long long)cnt[0];
+    ni = (long long)cnt[1];
+  } else if (on_device) {
+    trk = tracks;
+    ids = cluster_ids;
+    nt = (long long)n_tracks;
+    ni = (long long)n_ids;
+  } else {
+    nt = (long long)n_tracks;
+    ni = (long long)n_ids;
+    void* t = cmp_buffer(c, 0, sizeof(tpc_track_t) * (size_t)nt);
+    void* d = cmp_buffer(c, 1, 4 * (size_t)ni);
+    if (!t || !d) return fail(c, TPC_ERR_OOM, "track staging");
+    if ((nt && (e = cudaMemcpyAsync(t, tracks, sizeof(tpc_track_t) * nt, cudaMemcpyHostToDevice, c->stream)) !=
+                   cudaSuccess) ||
+        (ni && (e = cudaMemcpyAsync(d, cluster_ids, 4 * ni, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess))
+      return cuda_fail(c, e, "track upload");
+    trk = t;
+    ids = (const uint32_t*)d;
+  }
+  const float* q[4] = {ch->q_tot, ch->q_max, ch->sigma_y, ch->sigma_z};
+  if (!on_device && N > 0) {
+    float* st = (float*)cmp_buffer(c, 2, 16 * (size_t)N);
+    if (!st) return fail(c, TPC_ERR_OOM, "charge staging");
+    for (int k = 0; k < 4; ++k) {
+      if ((e = cudaMemcpyAsync(st + k * N, q[k], 4 * N, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+        return cuda_fail(c, e, "charge upload");
+      q[k] = st + k * N;
+    }
+  }
+  // sorted positions: one per loaded cluster (those of clusters left out of the binning are unused)
+  const int NR = c->cfg.n_rows, I = c->b.I;
+  const long long P = N;
+  const long long NN = std::max<long long>(N, 1), NA = std::max<long long>(std::max(N, ni), 1);
+  CmpArgs a{};
+  a.rows = c->b.rows;
+  a.s_hit = c->b.s_hit;
+  a.y = c->b.y;
+  a.z = c->b.z;
+  a.row = c->b.row;
+  a.N = (int)N;
+  a.I = I;
+  a.P = (int)P;
+  a.qt = q[0];
+  a.qm = q[1];
+  a.sy = q[2];
+  a.sz = q[3];
+  a.trk = trk;
+  a.ids = ids;
+  a.counts = nullptr;
+  a.n_trk = nt;
+  a.n_ids = ni;
+  a.err = c->b.err;
+  a.attached = (uint8_t*)cmp_buffer(c, 3, NN);
+  a.kpos = (int*)cmp_buffer(c, 4, 4 * (size_t)(P + 1));
+  a.unatt_id = (int*)cmp_buffer(c, 5, 4 * (size_t)NN);
+  a.unatt_first = (uint8_t*)cmp_buffer(c, 6, NN);
+  a.trk_n = (int*)cmp_buffer(c, 7, 4 * (size_t)(nt + 1));
+  const long long len_cap[TPC_CMP_STREAMS] = {(long long)I * NR, NN, NN, NA, NA, NA, NN + NA, NN + NA, NN + NA, NN + NA,
+                                              std::max<long long>(nt, 1)};
+  for (int k = 0; k < TPC_CMP_STREAMS; ++k)
+    a.val[k] = (unsigned long long*)cmp_buffer(c, 8 + k, 8 * (size_t)len_cap[k]);
+  a.vmax = (unsigned long long*)cmp_buffer(c, 19, 8 * TPC_CMP_STREAMS);
+  a.hist = (unsigned long long*)cmp_buffer(c, 20, 8ull * TPC_CMP_STREAMS * 2048);
+  a.scan_tmp = (int*)cmp_buffer(c, 21, 4 * (size_t)(P / 8192 + nt / 8192 + 8));
+  for (int k = 3; k <= 21; ++k)
+    if (!c->cmp_buf[k]) return fail(c, TPC_ERR_OOM, "compression buffers");
+  unsigned int err0 = 0;
+  if ((e = cudaMemcpyAsync(&err0, c->b.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "error word");
+  if ((e = cmp_symbols(a, c->par, c->lc.num_sms, c->stream)) != cudaSuccess) return cuda_fail(c, e, "symbols");
+  // stream lengths and largest values
+  unsigned long long vmax[TPC_CMP_STREAMS];
+  int n_un = 0, n_att = 0;
+  unsigned int err = 0;
+  if ((e = cudaMemcpyAsync(vmax, a.vmax, sizeof(vmax), cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&n_un, a.kpos + P, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&n_att, a.trk_n + nt, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&err, c->b.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "stream sizes");
+  if ((err & ~err0) & TPC_DERR_BAD_TRACK) return fail(c, TPC_ERR_BAD_INPUT, "a track refers to an item, cluster or row out of range");
+  const long long stream_n[TPC_CMP_STREAMS] = {(long long)I * NR, n_un, n_un, n_att, n_att, n_att, (long long)n_un + n_att,
+                                               (long long)n_un + n_att, (long long)n_un + n_att,
+                                               (long long)n_un + n_att, nt};
+  // planes and chunks
+  std::vector<CmpPlane> planes;
+  std::vector<int> plane_stream, chunk_plane, stream_planes(TPC_CMP_STREAMS);
+  long long scratch = 0, bound = 56 + 12 * TPC_CMP_STREAMS + 28 * nt;
+  int n_chunks = 0;
+  for (int s = 0; s < TPC_CMP_STREAMS; ++s) {
+    int np = 1;
+    while (np < 8 && (vmax[s] >> (8 * np))) ++np;
+    stream_planes[s] = np;
+    const int nch = (int)((stream_n[s] + TPC_CMP_CHUNK - 1) / TPC_CMP_CHUNK);
+    for (int p = 0; p < np; ++p) {
+      planes.push_back(CmpPlane{a.val[s], stream_n[s], p, n_chunks, scratch});
+      plane_stream.push_back(s);
+      for (int k = 0; k < nch; ++k) chunk_plane.push_back((int)planes.size() - 1);
+      n_chunks += nch;
+      scratch += (long long)nch * (TPC_CMP_CHUNK + 64);
+      bound += 516 + 4ll * nch + 2ll * (stream_n[s] + 64ll * nch);
+    }
+  }
+  const int NP = (int)planes.size();
+  CmpPlane* d_planes = (CmpPlane*)cmp_buffer(c, 22, sizeof(CmpPlane) * NP);
+  int* d_pstream = (int*)cmp_buffer(c, 23, 4 * (size_t)NP + 4 * TPC_CMP_STREAMS + 8 * TPC_CMP_STREAMS + 16);
+  int* d_cplane = (int*)cmp_buffer(c, 24, 4 * (size_t)std::max(n_chunks, 1));
+  uint16_t* d_ftab = (uint16_t*)cmp_buffer(c, 25, 1024 * (size_t)NP);
+  uint16_t* d_scratch = (uint16_t*)cmp_buffer(c, 26, 2 * (size_t)std::max<long long>(scratch, 1));
+  long long* d_cptr = (long long*)cmp_buffer(c, 27, 8 * (size_t)std::max(n_chunks, 1));
+  int* d_clen = (int*)cmp_buffer(c, 28, 4 * (size_t)std::max(n_chunks, 1));
+  long long* d_cdst = (long long*)cmp_buffer(c, 29, 8 * (size_t)std::max(n_chunks, 1));
+  uint8_t* d_blob = (uint8_t*)cmp_buffer(c, 30, (size_t)bound);
+  long long* d_size = (long long*)cmp_buffer(c, 31, 16);
+  for (int k = 22; k <= 31; ++k)
+    if (!c->cmp_buf[k]) return fail(c, TPC_ERR_OOM, "compression buffers");
+  int* d_splanes = d_pstream + NP;
+  long long* d_sn = (long long*)(d_splanes + TPC_CMP_STREAMS + (((NP + TPC_CMP_STREAMS) & 1) ? 1 : 0));
+  // host copies of the small tables must outlive the asynchronous uploads: wait before returning
+  if ((e = cudaMemcpyAsync(d_planes, planes.data(), sizeof(CmpPlane) * NP, cudaMemcpyHostToDevice, c->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(d_pstream, plane_stream.data(), 4 * NP, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(d_splanes, stream_planes.data(), 4 * TPC_CMP_STREAMS, cudaMemcpyHostToDevice, c->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemcpyAsync(d_sn, stream_n, 8 * TPC_CMP_STREAMS, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (n_chunks && (e = cudaMemcpyAsync(d_cplane, chunk_plane.data(), 4 * (size_t)n_chunks, cudaMemcpyHostToDevice,
+                                        c->stream)) != cudaSuccess))
+    return cuda_fail(c, e, "plane tables");
+  if ((e = cmp_encode(d_planes, NP, n_chunks, a.hist, d_pstream, d_ftab, d_scratch, d_cptr, d_clen, d_cplane,
+                      c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "rANS");
+  const float kBf = c->par.kB;
+  uint32_t kb;
+  std::memcpy(&kb, &kBf, 4);
+  const double xmin = c->cfg.row_x_min, xmax = c->cfg.row_x_max;
+  if ((e = cmp_layout(d_planes, NP, d_splanes, d_sn, d_ftab, d_scratch, d_cptr, d_clen, n_chunks, trk, nt, kb, xmin,
+                      xmax, I, NR, n_un, n_att, d_blob, d_size, d_cdst, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "layout");
+  long long sz[2] = {0, 0};
+  if ((e = cudaMemcpyAsync(sz, d_size, 16, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "blob size");
+  *size = (uint64_t)sz[0];
+  if ((uint64_t)sz[0] > cap) return fail(c, TPC_ERR_CAPACITY, "output buffer too small");
+  if ((e = cudaMemcpyAsync(out, d_blob, (size_t)sz[0], on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "blob copy");
   return TPC_OK;
 }
 

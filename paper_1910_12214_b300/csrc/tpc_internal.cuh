@@ -208,3 +208,50 @@ struct MaskArgs {
 };
 // ev (nullable): 3 events recorded around the two kernels
 cudaError_t launch_masks(const MaskArgs& a, const DevParams& par, int num_sms, cudaStream_t s, cudaEvent_t* ev);
+
+// Cluster compression (tpc_reduce.cu): entropy reduction and rANS coding.
+#define TPC_CMP_STREAMS 11
+#define TPC_CMP_CHUNK 8192
+struct CmpArgs {
+  // the loaded, tracked batch
+  const RowInfo* rows;
+  const int4* s_hit;
+  const float *y, *z;
+  const int* row;
+  int N, I, P;  // clusters, items, sorted positions (= N; positions outside every row's range are unused)
+  // charges and sizes
+  const float *qt, *qm, *sy, *sz;
+  // tracks
+  const void* trk;
+  const uint32_t* ids;
+  const unsigned long long* counts;  // own output (n_trk, n_ids) or null
+  long long n_trk, n_ids;
+  unsigned int* err;
+  // work arrays
+  uint8_t* attached;     // [N]
+  int* kpos;             // [P + 1] exclusive scan of the unattached flags over the sorted positions
+  int* unatt_id;         // [N]
+  uint8_t* unatt_first;  // [N]
+  int* trk_n;            // [n_trk + 1] cluster counts -> exclusive scan
+  unsigned long long* val[TPC_CMP_STREAMS];  // symbol streams
+  unsigned long long* vmax;                  // [TPC_CMP_STREAMS]
+  unsigned long long* hist;                  // [TPC_CMP_STREAMS][8][256]
+  int* scan_tmp;                             // block partials
+};
+cudaError_t cmp_symbols(const CmpArgs& a, const DevParams& par, int num_sms, cudaStream_t s);
+// plane coding: one warp per chunk of every (stream, plane)
+struct CmpPlane {
+  const unsigned long long* v;
+  long long n;         // values
+  int plane;           // byte index
+  int chunk0;          // first global chunk index of this plane
+  long long scratch0;  // first scratch word of this plane
+};
+cudaError_t cmp_encode(const CmpPlane* planes, int n_planes, int n_chunks_total, const unsigned long long* hist,
+                       const int* plane_stream, uint16_t* ftab, uint16_t* scratch, long long* chunk_ptr, int* chunk_len,
+                       const int* chunk_plane, cudaStream_t s);
+cudaError_t cmp_layout(const CmpPlane* planes, int n_planes, const int* stream_planes, const long long* stream_n,
+                       const uint16_t* ftab, const uint16_t* scratch, const long long* chunk_ptr, const int* chunk_len,
+                       int n_chunks_total, const void* trk, long long n_trk, uint32_t kB_bits, double x_min,
+                       double x_max, int n_items, int n_rows, long long n_unatt, long long n_att, uint8_t* out,
+                       long long* out_size, long long* chunk_dst, cudaStream_t s);

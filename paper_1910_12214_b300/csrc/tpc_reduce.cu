@@ -8,7 +8,9 @@
 // take a scalar path with the same arithmetic.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cstdint>
+#include <cstring>
 
 #include "tpc_internal.cuh"
 
@@ -435,5 +437,528 @@ cudaError_t launch_masks(const MaskArgs& a, const DevParams& par, int num_sms, c
   else
     k_mask_final<false><<<(unsigned)blocks, 256, 0, s>>>(a, par);
   if (ev) cudaEventRecord(ev[2], s);
+  return cudaGetLastError();
+}
+
+// ============================================================================
+// Cluster compression (Sec. 4, steps 3 and 4).
+//
+// Entropy reduction: clusters not attached to a track are taken in the
+// tracker's canonical order (the cells of each pad row's y-z grid, y-major,
+// then the cluster index) and stored as zigzag differences of their y and z
+// codes to the previous unattached cluster of the row; attached clusters are
+// stored track by track as the row increment and the residuals of their codes
+// to the track's prediction.  The prediction is a fixed sequence of correctly
+// rounded float32 operations (explicit _rn intrinsics: no contraction into
+// fused multiply-adds), so any decoder that performs the same sequence
+// reproduces it bit for bit.
+//
+// Entropy coding: each symbol stream is split into byte planes, each plane is
+// coded by rANS (32-bit states, 16-bit renormalisation, frequencies scaled to
+// 2^12) in chunks of 8192 symbols, one warp per chunk with symbol i of the
+// chunk on lane i mod 32.  Encoding runs backwards; at every step the lanes
+// that renormalise place their 16-bit word by a ballot and a population count,
+// so the words land in exactly the order a decoder warp reads them.
+namespace {
+
+enum { C_UNATT_N, C_DY, C_DZ, C_DROW, C_RY, C_RZ, C_QT, C_QM, C_SY, C_SZ, C_TRK_N };
+constexpr int SCAN_TILE = 8192;  // elements per block of the scans (1024 threads x 8)
+
+__device__ __forceinline__ unsigned long long zigzag(long long v) {
+  return v >= 0 ? (unsigned long long)v << 1 : (((unsigned long long)(-(v + 1))) << 1) | 1ull;
+}
+
+// code (step 2^-6 cm) of a predicted coordinate; 0 where it is not finite or out of reach
+__device__ __forceinline__ long long pred_code(float v) {
+  if (!(fabsf(v) < 1.0e17f)) return 0;
+  return __double2ll_rn((double)v * 64.0);
+}
+
+// The track model's (y, z) codes at pad-row radius X.
+__device__ void predict_codes(const tpc_track_t& t, float kB, float X, long long* py, long long* pz) {
+  const float dx = __fsub_rn(X, t.x_ref);
+  const float kappa = __fmul_rn(kB, t.qpt);
+  const float s2 = fminf(fmaxf(__fsub_rn(t.snp, __fmul_rn(kappa, dx)), -0.9999f), 0.9999f);
+  const float s1 = fminf(fmaxf(t.snp, -0.9999f), 0.9999f);
+  const float c1 = __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(s1, s1)));
+  const float c2 = __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(s2, s2)));
+  const float T = __fdiv_rn(__fadd_rn(s1, s2), __fadd_rn(c1, c2));
+  const float y = __fadd_rn(t.y, __fmul_rn(dx, T));
+  const float chord = __fmul_rn(dx, __fsqrt_rn(__fadd_rn(1.0f, __fmul_rn(T, T))));
+  const float a = fminf(fabsf(__fmul_rn(__fmul_rn(0.5f, kappa), chord)), 1.0f);
+  float g = 1.0f;  // asin(a) / a by two half-angle steps and a series to a^8
+  if (a > 1e-6f) {
+    const float a1 =
+        __fdiv_rn(a, __fsqrt_rn(__fmul_rn(2.0f, __fadd_rn(1.0f, __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(a, a)))))));
+    const float a2 =
+        __fdiv_rn(a1, __fsqrt_rn(__fmul_rn(2.0f, __fadd_rn(1.0f, __fsqrt_rn(__fsub_rn(1.0f, __fmul_rn(a1, a1)))))));
+    const float t2 = __fmul_rn(a2, a2);
+    float ser = __fmul_rn(t2, 35.0f / 1152.0f);
+    ser = __fmul_rn(t2, __fadd_rn(5.0f / 112.0f, ser));
+    ser = __fmul_rn(t2, __fadd_rn(3.0f / 40.0f, ser));
+    ser = __fmul_rn(t2, __fadd_rn(1.0f / 6.0f, ser));
+    ser = __fadd_rn(1.0f, ser);
+    g = __fdiv_rn(__fmul_rn(__fmul_rn(4.0f, a2), ser), a);
+  }
+  const float z = __fadd_rn(t.z, __fmul_rn(t.tgl, __fmul_rn(chord, g)));
+  *py = pred_code(y);
+  *pz = pred_code(z);
+}
+
+// ---- exclusive scan of int32 values in place; a[n] receives the total
+__global__ void __launch_bounds__(1024) k_scan_reduce(const int* a, long long n, int* partial) {
+  __shared__ int ws[32];
+  const long long base = (long long)blockIdx.x * SCAN_TILE;
+  int s = 0;
+  for (int k = 0; k < 8; ++k) {
+    const long long i = base + (long long)k * 1024 + threadIdx.x;
+    if (i < n) s += a[i];
+  }
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    s = ws[threadIdx.x];
+    for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+    if (threadIdx.x == 0) partial[blockIdx.x] = s;
+  }
+}
+
+// block-wide exclusive scan of one value per thread (1024 threads)
+__device__ __forceinline__ int block_exscan(int v, int* total) {
+  __shared__ int ws[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  int inc = v;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
+  }
+  __syncthreads();
+  if (lane == 31) ws[w] = inc;
+  __syncthreads();
+  if (w == 0) {
+    int x = ws[lane];
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += u;
+    }
+    ws[lane] = x;
+  }
+  __syncthreads();
+  *total = ws[31];
+  return inc - v + (w ? ws[w - 1] : 0);
+}
+
+__global__ void __launch_bounds__(1024) k_scan_partials(int* partial, int nb) {
+  int carry = 0;
+  for (int b0 = 0; b0 < nb; b0 += 1024) {
+    const int i = b0 + threadIdx.x;
+    const int v = i < nb ? partial[i] : 0;
+    int tot;
+    const int ex = block_exscan(v, &tot);
+    if (i < nb) partial[i] = carry + ex;
+    carry += tot;
+  }
+  if (threadIdx.x == 0) partial[nb] = carry;
+}
+
+__global__ void __launch_bounds__(1024) k_scan_apply(int* a, long long n, const int* partial, int nb) {
+  const long long base = (long long)blockIdx.x * SCAN_TILE;
+  int carry = partial[blockIdx.x];
+  for (int k = 0; k < 8; ++k) {
+    const long long i = base + (long long)k * 1024 + threadIdx.x;
+    const int v = i < n ? a[i] : 0;
+    int tot;
+    const int ex = block_exscan(v, &tot);
+    if (i < n) a[i] = carry + ex;
+    carry += tot;
+  }
+  if (blockIdx.x == nb - 1 && threadIdx.x == 0) a[n] = partial[nb];
+}
+
+cudaError_t scan_i32(int* a, long long n, int* tmp, cudaStream_t s) {
+  const int nb = (int)((n + SCAN_TILE - 1) / SCAN_TILE);
+  if (nb == 0) return cudaMemsetAsync(a, 0, 4, s);
+  k_scan_reduce<<<nb, 1024, 0, s>>>(a, n, tmp);
+  k_scan_partials<<<1, 1024, 0, s>>>(tmp, nb);
+  k_scan_apply<<<nb, 1024, 0, s>>>(a, n, tmp, nb);
+  return cudaGetLastError();
+}
+
+// ---- symbols
+__device__ __forceinline__ long long n_tracks_of(const CmpArgs& a) { return a.counts ? (long long)a.counts[0] : a.n_trk; }
+
+// attachment flags and per-track cluster counts (one warp per track); a track
+// outside the batch raises the error bit
+__global__ void k_cmp_attach(const __grid_constant__ CmpArgs a, const __grid_constant__ DevParams par) {
+  const int lane = threadIdx.x & 31;
+  const long long n_trk = n_tracks_of(a);
+  const long long n_ids = a.counts ? (long long)a.counts[1] : a.n_ids;
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_trk; t += nw) {
+    const long long first = trk[t].first_cluster, cnt = trk[t].n_clusters;
+    bool bad = trk[t].item >= (uint32_t)a.I || first + cnt > n_ids;
+    if (!bad)
+      for (long long j = lane; j < cnt; j += 32) {
+        const uint32_t c = a.ids[first + j];
+        if (c >= (uint32_t)a.N || a.row[c] < 0 || a.row[c] >= par.n_rows)
+          bad = true;
+        else
+          a.attached[c] = 1;
+      }
+    bad = __any_sync(0xffffffffu, bad);
+    if (lane == 0) {
+      a.trk_n[t] = bad ? 0 : (int)cnt;
+      if (bad) atomicOr(a.err, TPC_DERR_BAD_TRACK);
+    }
+  }
+}
+
+// unattached flags of the binned clusters, one warp per (item, row); the
+// positions between items' binned ranges (clusters left out of the binning)
+// keep the zero the array was cleared to
+__global__ void k_cmp_flags(const __grid_constant__ CmpArgs a, int n_rows) {
+  const int lane = threadIdx.x & 31;
+  const long long G = (long long)a.I * n_rows;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
+    const RowInfo ri = a.rows[g];
+    for (int p = ri.pos0 + lane; p < ri.pos0 + ri.n; p += 32) a.kpos[p] = a.attached[a.s_hit[p].z] ? 0 : 1;
+  }
+}
+
+// compaction of the unattached clusters; the row's first one is marked
+__global__ void k_cmp_unatt(const __grid_constant__ CmpArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long p = (long long)blockIdx.x * blockDim.x + threadIdx.x; p < a.P; p += stride) {
+    const int k = a.kpos[p];
+    if (a.kpos[p + 1] == k) continue;  // attached
+    const int4 h = a.s_hit[p];
+    a.unatt_id[k] = h.z;
+    a.unatt_first[k] = (uint8_t)(k == a.kpos[a.rows[h.w].pos0]);
+  }
+}
+
+__global__ void k_cmp_rowcounts(const __grid_constant__ CmpArgs a, int n_rows) {
+  const long long G = (long long)a.I * n_rows;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += stride) {
+    const RowInfo ri = a.rows[g];
+    a.val[C_UNATT_N][g] = ri.n > 0 ? (unsigned long long)(a.kpos[ri.pos0 + ri.n] - a.kpos[ri.pos0]) : 0ull;
+  }
+}
+
+__device__ __forceinline__ void put_props(const CmpArgs& a, long long k, int c) {
+  a.val[C_QT][k] = (unsigned long long)charge(a.qt[c]);
+  a.val[C_QM][k] = (unsigned long long)charge(a.qm[c]);
+  a.val[C_SY][k] = (unsigned long long)size(a.sy[c]);
+  a.val[C_SZ][k] = (unsigned long long)size(a.sz[c]);
+}
+
+__global__ void k_cmp_unatt_symbols(const __grid_constant__ CmpArgs a) {
+  const long long n_un = a.kpos[a.P];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_un; k += stride) {
+    const int c = a.unatt_id[k];
+    const long long yc = fix_sat(a.y[c], 64.f, -32768, 32767), zc = fix_sat(a.z[c], 64.f, INT32_MIN, INT32_MAX);
+    long long yp = 0, zp = 0;
+    if (!a.unatt_first[k]) {
+      const int b = a.unatt_id[k - 1];
+      yp = fix_sat(a.y[b], 64.f, -32768, 32767);
+      zp = fix_sat(a.z[b], 64.f, INT32_MIN, INT32_MAX);
+    }
+    a.val[C_DY][k] = zigzag(yc - yp);
+    a.val[C_DZ][k] = zigzag(zc - zp);
+    put_props(a, k, c);
+  }
+}
+
+// one warp per track: row increments, residuals to the prediction, charges
+__global__ void k_cmp_track_symbols(const __grid_constant__ CmpArgs a, const __grid_constant__ DevParams par) {
+  const int lane = threadIdx.x & 31;
+  const long long n_trk = n_tracks_of(a);
+  const long long n_un = a.kpos[a.P];
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_trk; t += nw) {
+    const tpc_track_t T = trk[t];
+    const long long base = a.trk_n[t], cnt = a.trk_n[t + 1] - base;
+    if (lane == 0) a.val[C_TRK_N][t] = (unsigned long long)cnt;
+    for (long long j = lane; j < cnt; j += 32) {
+      const int c = (int)a.ids[T.first_cluster + j];
+      const int r = a.row[c];
+      const int rp = j ? a.row[a.ids[T.first_cluster + j - 1]] : 0;
+      long long py, pz;
+      predict_codes(T, par.kB, par.x[r], &py, &pz);
+      a.val[C_DROW][base + j] = zigzag((long long)(r - rp));
+      a.val[C_RY][base + j] = zigzag((long long)fix_sat(a.y[c], 64.f, -32768, 32767) - py);
+      a.val[C_RZ][base + j] = zigzag((long long)fix_sat(a.z[c], 64.f, INT32_MIN, INT32_MAX) - pz);
+      put_props(a, n_un + base + j, c);
+    }
+  }
+}
+
+// largest value and byte-plane histograms of every stream (blockIdx.y = stream)
+__global__ void __launch_bounds__(256) k_cmp_stats(const __grid_constant__ CmpArgs a, int n_rows) {
+  __shared__ unsigned int h[8][256];
+  const int s = blockIdx.y;
+  const long long n_un = a.kpos[a.P], n_att = a.trk_n[n_tracks_of(a)];
+  const long long len[TPC_CMP_STREAMS] = {(long long)a.I * n_rows, n_un, n_un, n_att, n_att, n_att,
+                                          n_un + n_att, n_un + n_att, n_un + n_att, n_un + n_att, n_tracks_of(a)};
+  const long long n = len[s];
+  for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  unsigned long long mx = 0;
+  const unsigned long long* v = a.val[s];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long x = v[i];
+    mx = x > mx ? x : mx;
+#pragma unroll
+    for (int p = 0; p < 8; ++p) atomicAdd(&h[p][(x >> (8 * p)) & 255], 1u);
+  }
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, mx, o);
+    mx = u > mx ? u : mx;
+  }
+  if ((threadIdx.x & 31) == 0 && mx) atomicMax(a.vmax + s, mx);
+  __syncthreads();
+  for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) {
+    const unsigned int c = (&h[0][0])[i];
+    if (c) atomicAdd(a.hist + (long long)s * 2048 + i, (unsigned long long)c);
+  }
+}
+
+// ---- coding
+// frequencies of one (stream, plane): the oracle's scaling rule
+__global__ void k_cmp_norm(const CmpPlane* planes, int n_planes, const unsigned long long* hist,
+                           const int* plane_stream, uint16_t* ftab) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= n_planes) return;
+  const unsigned long long* cnt = hist + (long long)plane_stream[q] * 2048 + 256 * planes[q].plane;
+  uint16_t* f = ftab + 512 * q;
+  unsigned long long total = 0;
+  for (int s = 0; s < 256; ++s) total += cnt[s];
+  long long sum = 0;
+  for (int s = 0; s < 256; ++s) {
+    unsigned long long v = cnt[s] ? (cnt[s] * 4096ull) / total : 0ull;
+    if (cnt[s] && v == 0) v = 1;
+    f[s] = (uint16_t)v;
+    sum += (long long)v;
+  }
+  if (total) {
+    auto largest = [&]() {
+      int b = 0;
+      for (int s = 1; s < 256; ++s)
+        if (f[s] > f[b]) b = s;
+      return b;
+    };
+    while (sum > 4096) {
+      f[largest()] -= 1;
+      --sum;
+    }
+    if (sum < 4096) f[largest()] += (uint16_t)(4096 - sum);
+  }
+  unsigned acc = 0;
+  for (int s = 0; s < 256; ++s) {
+    f[256 + s] = (uint16_t)acc;
+    acc += f[s];
+  }
+}
+
+// one warp per chunk: interleaved rANS, words written backwards from the end
+// of the chunk's scratch region (64 + n words), states last
+__global__ void __launch_bounds__(128) k_cmp_rans(const CmpPlane* planes, const int* chunk_plane, int n_chunks,
+                                                   const uint16_t* ftab, uint16_t* scratch, long long* chunk_ptr,
+                                                   int* chunk_len) {
+  __shared__ uint32_t tab[4][256];  // per warp: f | c << 16
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int ch = blockIdx.x * 4 + w;
+  const bool live = ch < n_chunks;
+  const int q = live ? chunk_plane[ch] : 0;
+  const CmpPlane P = planes[q];
+  for (int s = lane; s < 256; s += 32) tab[w][s] = live ? (ftab[512 * q + s] | ((uint32_t)ftab[512 * q + 256 + s] << 16)) : 0u;
+  __syncwarp();
+  if (!live) return;
+  const long long c0 = ch - P.chunk0;
+  const long long a0 = c0 * TPC_CMP_CHUNK;
+  const int n = (int)min((long long)TPC_CMP_CHUNK, P.n - a0);
+  uint16_t* buf = scratch + P.scratch0 + c0 * (TPC_CMP_CHUNK + 64);
+  long long ptr = 64 + n;
+  uint32_t x = 1u << 16;
+  const int sh = 8 * P.plane;
+  for (int k = (n + 31) / 32 - 1; k >= 0; --k) {
+    const int i = k * 32 + lane;
+    const bool act = i < n;
+    const uint32_t sym = act ? (uint32_t)((P.v[a0 + i] >> sh) & 255ull) : 0u;
+    const uint32_t e = tab[w][sym];
+    const uint32_t fs = e & 0xffffu, cs = e >> 16;
+    const bool emit = act && (unsigned long long)x >= ((unsigned long long)fs << 20);
+    const unsigned m = __ballot_sync(0xffffffffu, emit);
+    ptr -= __popc(m);
+    if (emit) {
+      buf[ptr + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(x & 0xffffu);
+      x >>= 16;
+    }
+    if (act) x = ((x / fs) << 12) + (x % fs) + cs;
+  }
+  ptr -= 64;
+  buf[ptr + 2 * lane] = (uint16_t)(x & 0xffffu);
+  buf[ptr + 2 * lane + 1] = (uint16_t)(x >> 16);
+  if (lane == 0) {
+    chunk_ptr[ch] = P.scratch0 + c0 * (TPC_CMP_CHUNK + 64) + ptr;
+    chunk_len[ch] = (int)(64 + n - ptr);
+  }
+}
+
+// ---- blob assembly
+__device__ __forceinline__ void put16(uint8_t* o, long long at, unsigned v) {
+  *reinterpret_cast<uint16_t*>(o + at) = (uint16_t)v;
+}
+__device__ __forceinline__ void put32(uint8_t* o, long long at, unsigned v) {
+  put16(o, at, v & 0xffffu);
+  put16(o, at + 2, v >> 16);
+}
+__device__ __forceinline__ void put64(uint8_t* o, long long at, unsigned long long v) {
+  put32(o, at, (unsigned)v);
+  put32(o, at + 4, (unsigned)(v >> 32));
+}
+
+// One block: the header, every stream's and plane's fixed fields, each chunk's
+// destination, the offset of the track table (written to out_size[1]) and the
+// blob's size (out_size[0]).
+__global__ void __launch_bounds__(1024) k_cmp_layout(const CmpPlane* planes, int n_planes, const int* stream_planes,
+                                                      const long long* stream_n, const uint16_t* ftab,
+                                                      const int* chunk_len, long long n_trk, uint32_t kB_bits,
+                                                      unsigned long long xb0, unsigned long long xb1, int n_items,
+                                                      int n_rows, long long n_unatt, long long n_att, uint8_t* out,
+                                                      long long* out_size, long long* chunk_dst) {
+  __shared__ long long at_s;
+  if (threadIdx.x == 0) {
+    put32(out, 0, 0x5A435054u);
+    put32(out, 4, 1u);
+    put32(out, 8, (unsigned)n_items);
+    put32(out, 12, (unsigned)n_rows);
+    put32(out, 16, (unsigned)n_trk);
+    put32(out, 20, kB_bits);
+    put64(out, 24, xb0);
+    put64(out, 32, xb1);
+    put64(out, 40, (unsigned long long)n_unatt);
+    put64(out, 48, (unsigned long long)n_att);
+    at_s = 56;
+  }
+  __syncthreads();
+  int q = 0;
+  for (int s = 0; s < TPC_CMP_STREAMS; ++s) {
+    if (threadIdx.x == 0) {
+      put64(out, at_s, (unsigned long long)stream_n[s]);
+      put32(out, at_s + 8, (unsigned)stream_planes[s]);
+      at_s += 12;
+    }
+    __syncthreads();
+    for (int p = 0; p < stream_planes[s]; ++p, ++q) {
+      const CmpPlane P = planes[q];
+      const int nch = (int)((P.n + TPC_CMP_CHUNK - 1) / TPC_CMP_CHUNK);
+      long long at = at_s;
+      for (int i = threadIdx.x; i < 256; i += blockDim.x) put16(out, at + 2 * i, ftab[512 * q + i]);
+      at += 512;
+      if (threadIdx.x == 0) put32(out, at, (unsigned)nch);
+      at += 4;
+      for (int i = threadIdx.x; i < nch; i += blockDim.x) put32(out, at + 4 * i, (unsigned)chunk_len[P.chunk0 + i]);
+      at += 4ll * nch;
+      // destinations of the chunks' words: a block scan of their lengths
+      long long carry = at;
+      for (int b0 = 0; b0 < nch; b0 += 1024) {
+        const int i = b0 + threadIdx.x;
+        const int len = i < nch ? chunk_len[P.chunk0 + i] : 0;
+        int tot;
+        const int ex = block_exscan(len, &tot);
+        if (i < nch) chunk_dst[P.chunk0 + i] = carry + 2ll * ex;
+        carry += 2ll * tot;
+      }
+      __syncthreads();
+      if (threadIdx.x == 0) at_s = carry;
+      __syncthreads();
+    }
+  }
+  if (threadIdx.x == 0) {
+    out_size[1] = at_s;
+    out_size[0] = at_s + 28ll * n_trk;
+  }
+}
+
+__global__ void k_cmp_copy(const uint16_t* scratch, const long long* chunk_ptr, const int* chunk_len,
+                           const long long* chunk_dst, int n_chunks, uint8_t* out) {
+  const int lane = threadIdx.x & 31;
+  const int nw = (gridDim.x * blockDim.x) >> 5;
+  for (int ch = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; ch < n_chunks; ch += nw) {
+    const uint16_t* src = scratch + chunk_ptr[ch];
+    uint16_t* dst = reinterpret_cast<uint16_t*>(out + chunk_dst[ch]);
+    for (int i = lane; i < chunk_len[ch]; i += 32) dst[i] = src[i];
+  }
+}
+
+__global__ void k_cmp_tracks(const void* trk_v, long long n_trk, const long long* out_size, uint8_t* out) {
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(trk_v);
+  const long long at0 = out_size[1];
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_trk; t += stride) {
+    const tpc_track_t& T = trk[t];
+    const long long at = at0 + 28 * t;
+    put32(out, at, __float_as_uint(T.x_ref));
+    put32(out, at + 4, __float_as_uint(T.y));
+    put32(out, at + 8, __float_as_uint(T.z));
+    put32(out, at + 12, __float_as_uint(T.snp));
+    put32(out, at + 16, __float_as_uint(T.tgl));
+    put32(out, at + 20, __float_as_uint(T.qpt));
+    put32(out, at + 24, T.item);
+  }
+}
+
+}  // namespace
+
+cudaError_t cmp_symbols(const CmpArgs& a, const DevParams& par, int num_sms, cudaStream_t s) {
+  cudaError_t e;
+  const int g = num_sms * 8;
+  if ((e = cudaMemsetAsync(a.attached, 0, (size_t)a.N, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(a.vmax, 0, 8 * TPC_CMP_STREAMS, s)) != cudaSuccess ||
+      (e = cudaMemsetAsync(a.hist, 0, 8ull * TPC_CMP_STREAMS * 2048, s)) != cudaSuccess)
+    return e;
+  k_cmp_attach<<<g, 256, 0, s>>>(a, par);
+  // the track counts' scan needs their number on the host side: own tracks are
+  // counted on the device, so scan the capacity (unused entries are zero)
+  if ((e = cudaMemsetAsync(a.kpos, 0, 4 * ((size_t)a.P + 1), s)) != cudaSuccess) return e;
+  k_cmp_flags<<<g, 256, 0, s>>>(a, par.n_rows);
+  if ((e = scan_i32(a.kpos, a.P, a.scan_tmp, s)) != cudaSuccess) return e;
+  if ((e = scan_i32(a.trk_n, a.n_trk, a.scan_tmp + (a.P / SCAN_TILE + 2), s)) != cudaSuccess) return e;
+  k_cmp_unatt<<<g, 256, 0, s>>>(a);
+  k_cmp_rowcounts<<<g, 256, 0, s>>>(a, par.n_rows);
+  k_cmp_unatt_symbols<<<g, 256, 0, s>>>(a);
+  k_cmp_track_symbols<<<g, 256, 0, s>>>(a, par);
+  k_cmp_stats<<<dim3(num_sms * 2, TPC_CMP_STREAMS), 256, 0, s>>>(a, par.n_rows);
+  return cudaGetLastError();
+}
+
+cudaError_t cmp_encode(const CmpPlane* planes, int n_planes, int n_chunks_total, const unsigned long long* hist,
+                       const int* plane_stream, uint16_t* ftab, uint16_t* scratch, long long* chunk_ptr, int* chunk_len,
+                       const int* chunk_plane, cudaStream_t s) {
+  if (n_planes == 0) return cudaSuccess;
+  k_cmp_norm<<<(n_planes + 63) / 64, 64, 0, s>>>(planes, n_planes, hist, plane_stream, ftab);
+  if (n_chunks_total) k_cmp_rans<<<(n_chunks_total + 3) / 4, 128, 0, s>>>(planes, chunk_plane, n_chunks_total, ftab, scratch, chunk_ptr, chunk_len);
+  return cudaGetLastError();
+}
+
+cudaError_t cmp_layout(const CmpPlane* planes, int n_planes, const int* stream_planes, const long long* stream_n,
+                       const uint16_t* ftab, const uint16_t* scratch, const long long* chunk_ptr, const int* chunk_len,
+                       int n_chunks_total, const void* trk, long long n_trk, uint32_t kB_bits, double x_min,
+                       double x_max, int n_items, int n_rows, long long n_unatt, long long n_att, uint8_t* out,
+                       long long* out_size, long long* chunk_dst, cudaStream_t s) {
+  unsigned long long xb0, xb1;
+  memcpy(&xb0, &x_min, 8);
+  memcpy(&xb1, &x_max, 8);
+  k_cmp_layout<<<1, 1024, 0, s>>>(planes, n_planes, stream_planes, stream_n, ftab, chunk_len, n_trk, kB_bits, xb0, xb1,
+                                  n_items, n_rows, n_unatt, n_att, out, out_size, chunk_dst);
+  if (n_chunks_total) k_cmp_copy<<<(n_chunks_total + 7) / 8, 256, 0, s>>>(scratch, chunk_ptr, chunk_len, chunk_dst, n_chunks_total, out);
+  if (n_trk) k_cmp_tracks<<<(int)std::min<long long>((n_trk + 255) / 256, 4096), 256, 0, s>>>(trk, n_trk, out_size, out);
   return cudaGetLastError();
 }

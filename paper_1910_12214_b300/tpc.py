@@ -69,6 +69,10 @@ class tpc_mask_params(C.Structure):
 
 MASK_ASSOCIATED, MASK_PROTECTED, MASK_REMOVE_A, MASK_REMOVE_B = 1, 2, 4, 8
 
+
+class tpc_cluster_charges(C.Structure):
+    _fields_ = [("q_tot", C.c_void_p), ("q_max", C.c_void_p), ("sigma_y", C.c_void_p), ("sigma_z", C.c_void_p)]
+
 PROP_FIELDS = (("y", np.float32), ("z", np.float32), ("row", np.int32), ("q_tot", np.float32),
                ("q_max", np.float32), ("sigma_y", np.float32), ("sigma_z", np.float32))
 CODE_FIELDS = (("y", np.int16), ("z", np.int32), ("row", np.uint8), ("q_tot", np.uint16), ("q_max", np.uint16),
@@ -109,6 +113,8 @@ _sig = {
                              C.POINTER(C.c_uint64)], C.c_int),
     "tpc_cluster_masks": ([_P, C.POINTER(tpc_mask_params), _P, C.c_uint64, _P, C.c_uint64, _P, C.c_int, _P, _P],
                           C.c_int),
+    "tpc_compress": ([_P, C.POINTER(tpc_cluster_charges), _P, C.c_uint64, _P, C.c_uint64, C.c_int, _P, C.c_uint64,
+                      C.POINTER(C.c_uint64)], C.c_int),
     "tpc_destroy": ([_P], None),
     "tpc_last_error": ([_P], C.c_char_p),
 }
@@ -395,6 +401,48 @@ class Tracker:
         self._check(_lib.tpc_cluster_masks(self._h, C.byref(prm), _ptr(tracks), nt, _ptr(ids), ni, _ptr(leg),
                                            int(on_device), _ptr(mask), _ptr(owner)))
         return mask, owner
+
+    def compress(self, charges, tracks=None, ids=None, on_device=False, out=None):
+        """Compressed blob of the loaded, tracked clusters (Sec. 4, steps 3-4;
+        include/tpc_reduce.h).  charges: dict of q_tot, q_max, sigma_y, sigma_z
+        (numpy, or CUDA tensors with on_device).  tracks=None uses the last
+        tpc_track() output; else TRACK_DTYPE records and uint32 ids (numpy), or
+        a CUDA uint8 tensor [n, 112] and int32 ids with on_device.  out: a
+        buffer to write into (numpy uint8, or a CUDA uint8 tensor with
+        on_device); too small or None: sized by a first call.  Returns the blob
+        (a view of out)."""
+        keep = []
+        if on_device:
+            arrs = [charges[k] for k in ("q_tot", "q_max", "sigma_y", "sigma_z")]
+            nt = int(tracks.shape[0]) if tracks is not None else 0
+        else:
+            arrs = [np.ascontiguousarray(charges[k], np.float32) for k in ("q_tot", "q_max", "sigma_y", "sigma_z")]
+            if tracks is not None:
+                tracks = np.ascontiguousarray(tracks, TRACK_DTYPE)
+                ids = np.ascontiguousarray(ids, np.uint32)
+                keep += [tracks, ids]
+            nt = int(tracks.shape[0]) if tracks is not None else 0
+        keep += arrs
+        ch = tpc_cluster_charges(*[_ptr(a) for a in arrs])
+        ni = int(ids.shape[0]) if ids is not None else 0
+        size = C.c_uint64()
+
+        def call(buf):
+            cap = int(buf.shape[0]) if buf is not None else 0
+            return _lib.tpc_compress(self._h, C.byref(ch), _ptr(tracks), nt, _ptr(ids), ni, int(on_device),
+                                     _ptr(buf) if cap else None, cap, C.byref(size))
+
+        st = call(out)
+        if st == 5:  # TPC_ERR_CAPACITY: size the buffer and run again
+            n = int(size.value)
+            if on_device:
+                import torch
+                out = torch.empty(n, dtype=torch.uint8, device=torch.device("cuda", self.cfg.device))
+            else:
+                out = np.empty(n, np.uint8)
+            st = call(out)
+        self._check(st)
+        return out[:int(size.value)]
 
     def close(self):
         if getattr(self, "_h", None):

@@ -90,9 +90,10 @@ def test_reduce_struct_layouts_match_c(tmp_path, lib_path):
     prog = tmp_path / "rz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "tpc_reduce.h"\nint main(void){'
                     'printf("%zu %zu %zu %zu\\n", sizeof(tpc_cluster_props), sizeof(tpc_cluster_codes), '
-                    'offsetof(tpc_cluster_props, n), sizeof(tpc_mask_params)); return 0;}\n')
+                    'offsetof(tpc_cluster_props, n), sizeof(tpc_mask_params) + 100 * sizeof(tpc_cluster_charges)); return 0;}\n')
     exe = tmp_path / "rz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert vals == [ctypes.sizeof(tpc.tpc_cluster_props), ctypes.sizeof(tpc.tpc_cluster_codes),
-                    tpc.tpc_cluster_props.n.offset, ctypes.sizeof(tpc.tpc_mask_params)]
+                    tpc.tpc_cluster_props.n.offset,
+                    ctypes.sizeof(tpc.tpc_mask_params) + 100 * ctypes.sizeof(tpc.tpc_cluster_charges)]
