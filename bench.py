@@ -9,8 +9,9 @@ Further forms (rank 0, N=1): 64 uneven events (plain vs batched persistent
 kernel), a 50 kHz continuous-readout time frame (128 collisions, sliced), and
 the same 64 events distorted by a space-charge field, corrected by the grid or
 by the trained BF16 network, the cluster codec (float to integer with dynamic
-precision) over the 64 events' clusters, and the cluster removal masks
-(attachment, adjacency, protection, strategies A and B) of the 64 events.
+precision) over the 64 events' clusters, the cluster removal masks
+(attachment, adjacency, protection, strategies A and B) of the 64 events, and
+their compression (delta and track-model coding, rANS).
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
 bounded sample of the same workload instead.
@@ -88,7 +89,7 @@ def generate_forms(forms):
     jobs = {}
     ctx = mp.get_context("spawn")
     with ctx.Pool(3) as pool:
-        if "c3" in forms or "c5" in forms or "c6" in forms or "c7" in forms:
+        if any(f in forms for f in ("c3", "c5", "c6", "c7", "c8")):
             jobs["c3"] = pool.apply_async(_gen_batched)
         if "c4" in forms:
             jobs["c4"] = pool.apply_async(_gen_frame)
@@ -101,6 +102,9 @@ def generate_forms(forms):
         out["c6"] = synth.cluster_props(out["c3"], seed=1)
     if "c7" in forms:
         out["c7"] = out["c3"]
+    if "c8" in forms:
+        from paper_1910_12214_b300 import synth
+        out["c8"] = (out["c3"], out["c6"] if "c6" in out else synth.cluster_props(out["c3"], seed=1))
     if "c5" in forms:
         from paper_1910_12214_b300 import synth
         d, g, b = out["grid"]
@@ -301,7 +305,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--forms", default="c3,c4,c5,c6,c7", help="extra forms at N=1: c3,...,c7 or none")
+    ap.add_argument("--forms", default="c3,c4,c5,c6,c7,c8", help="extra forms at N=1: c3,...,c8 or none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -479,6 +483,48 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
         res["codec_64_events"] = bench_codec(gen["c6"], dev, stream, flush, tpc, torch)
     if "c7" in gen:
         res["masks_64_events"] = bench_masks(gen["c7"], dev, stream, flush, tpc, torch)
+    if "c8" in gen:
+        res["compress_64_events"] = bench_compress(*gen["c8"], dev, stream, flush, tpc, torch)
+    return res
+
+
+def bench_compress(cl, props, dev, stream, flush, tpc, torch, steps=10):
+    """Compression of the 64-event batch (Sec. 4, steps 3-4) with the tracker's
+    own tracks, charges and output on the device.  The call waits for its
+    result (it reads the sizes it needs), so it is timed by the host clock; the
+    phases by the library's events.  L2 flushed between calls."""
+    with torch.cuda.stream(stream):
+        d = to_device(cl, dev)
+        ch = {k: torch.from_numpy(np.ascontiguousarray(props[k])).to(dev)
+              for k in ("q_tot", "q_max", "sigma_y", "sigma_z")}
+    stream.synchronize()
+    res = {"clusters": cl.n}
+    with tpc.Tracker(stream=stream, profile=True) as t:
+        t.load(d, on_device=True)
+        t.track()
+        blob = t.compress(ch, on_device=True)
+        out = torch.empty(blob.shape[0] + (1 << 20), dtype=torch.uint8, device=dev)
+        for _ in range(3):
+            t.compress(ch, on_device=True, out=out)
+        wall, ph = [], {}
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            b = t.compress(ch, on_device=True, out=out)
+            wall.append(time.perf_counter() - w0)
+            for k, v in t.stage_times().items():
+                if k.startswith("compress"):
+                    ph.setdefault(k, []).append(v)
+        size = int(b.shape[0])
+    ms = 1e3 * float(np.median(wall))
+    phases = {k: float(np.median(v)) for k, v in ph.items()}
+    res.update(clusters_per_s=cl.n / (ms * 1e-3), ms=ms, phase_us=phases, blob_bytes=size,
+               bytes_per_cluster=size / cl.n, ratio_vs_integer_codes=13.0 * cl.n / size,
+               ratio_vs_float_clusters=28.0 * cl.n / size)
+    del d, ch
+    torch.cuda.empty_cache()
     return res
 
 

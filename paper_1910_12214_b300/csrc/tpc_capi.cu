@@ -37,6 +37,8 @@ struct tpc_ctx {
   cudaEvent_t ev[TPC_N_STAGES + 1] = {};
   cudaEvent_t mask_ev[3] = {};  // around the two kernels of tpc_cluster_masks (profile = 1)
   bool mask_timed = false;
+  cudaEvent_t cmp_ev[6] = {};  // around the symbol, rANS and layout phases of tpc_compress (profile = 1)
+  bool cmp_timed = false;
   bool have_events = false;
   // host copies used by the debug dump and the work queue
   std::vector<uint64_t> h_item_off;
@@ -70,8 +72,8 @@ struct tpc_ctx {
   void* mask_stage = nullptr;
   size_t mask_stage_bytes = 0;
   // compression: persistent work buffers, grown on demand
-  void* cmp_buf[32] = {};
-  size_t cmp_cap[32] = {};
+  void* cmp_buf[40] = {};
+  size_t cmp_cap[40] = {};
 };
 
 namespace {
@@ -301,6 +303,7 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
   if (cfg->profile) {
     for (int i = 0; i <= TPC_N_STAGES; ++i) cudaEventCreate(&c->ev[i]);
     for (int i = 0; i < 3; ++i) cudaEventCreate(&c->mask_ev[i]);
+    for (int i = 0; i < 6; ++i) cudaEventCreate(&c->cmp_ev[i]);
     c->have_events = true;
   }
   if (cfg->max_clusters || cfg->max_items) {
@@ -403,6 +406,7 @@ extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
   c->loaded = true;
   c->tracked = false;
   c->mask_timed = false;
+  c->cmp_timed = false;
   return TPC_OK;
 }
 
@@ -517,7 +521,8 @@ extern "C" tpc_status tpc_device_tracks(tpc_ctx* c, const tpc_track_t** trk, con
 
 static const char* kStageNames[TPC_N_REPORTED_STAGES] = {
     "quantise+row_stats", "row_setup", "group_scatter", "row_sort", "links", "clean+starts", "tracklets",
-    "selection", "output", "batched_items", "batched_concat", "mask_assoc", "mask_final"};
+    "selection", "output", "batched_items", "batched_concat", "mask_assoc", "mask_final", "compress_symbols",
+    "compress_rans", "compress_layout"};
 
 extern "C" const char* tpc_stage_name(int i) { return (i >= 0 && i < TPC_N_REPORTED_STAGES) ? kStageNames[i] : ""; }
 
@@ -530,10 +535,11 @@ extern "C" tpc_status tpc_stage_times(tpc_ctx* c, float* us, int n, int* n_stage
   if (e != cudaSuccess) return cuda_fail(c, e, "stream");
   for (int i = 0; i < TPC_N_REPORTED_STAGES && i < n; ++i) {
     float ms = 0.f;
-    const bool mask = i >= TPC_N_STAGES;
-    const bool mine = mask ? c->mask_timed : (c->last_batched ? (i >= 9) : (i < 9));
-    const cudaEvent_t a = mask ? c->mask_ev[i - TPC_N_STAGES] : c->ev[i];
-    const cudaEvent_t b = mask ? c->mask_ev[i - TPC_N_STAGES + 1] : c->ev[i + 1];
+    const bool mask = i >= TPC_N_STAGES && i < TPC_N_STAGES + 2, cmp = i >= TPC_N_STAGES + 2;
+    const bool mine = cmp ? c->cmp_timed : (mask ? c->mask_timed : (c->last_batched ? (i >= 9) : (i < 9)));
+    const int j = i - TPC_N_STAGES - 2;
+    const cudaEvent_t a = cmp ? c->cmp_ev[2 * j] : (mask ? c->mask_ev[i - TPC_N_STAGES] : c->ev[i]);
+    const cudaEvent_t b = cmp ? c->cmp_ev[2 * j + 1] : (mask ? c->mask_ev[i - TPC_N_STAGES + 1] : c->ev[i + 1]);
     if (mine && cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
       cudaGetLastError();
       ms = 0.f;
@@ -1403,12 +1409,17 @@ extern "C" tpc_status tpc_compress(tpc_ctx* c, const tpc_cluster_charges* ch, co
   a.vmax = (unsigned long long*)cmp_buffer(c, 19, 8 * TPC_CMP_STREAMS);
   a.hist = (unsigned long long*)cmp_buffer(c, 20, 8ull * TPC_CMP_STREAMS * 2048);
   a.scan_tmp = (int*)cmp_buffer(c, 21, 4 * (size_t)(P / 8192 + nt / 8192 + 8));
+  a.rec = (int4*)cmp_buffer(c, 32, 16 * (size_t)NN);
+  if (!a.rec) return fail(c, TPC_ERR_OOM, "compression buffers");
   for (int k = 3; k <= 21; ++k)
     if (!c->cmp_buf[k]) return fail(c, TPC_ERR_OOM, "compression buffers");
   unsigned int err0 = 0;
   if ((e = cudaMemcpyAsync(&err0, c->b.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "error word");
+  const bool timed = c->have_events;
+  if (timed) cudaEventRecord(c->cmp_ev[0], c->stream);
   if ((e = cmp_symbols(a, c->par, c->lc.num_sms, c->stream)) != cudaSuccess) return cuda_fail(c, e, "symbols");
+  if (timed) cudaEventRecord(c->cmp_ev[1], c->stream);
   // stream lengths and largest values
   unsigned long long vmax[TPC_CMP_STREAMS];
   int n_un = 0, n_att = 0;
@@ -1467,16 +1478,23 @@ extern "C" tpc_status tpc_compress(tpc_ctx* c, const tpc_cluster_charges* ch, co
       (n_chunks && (e = cudaMemcpyAsync(d_cplane, chunk_plane.data(), 4 * (size_t)n_chunks, cudaMemcpyHostToDevice,
                                         c->stream)) != cudaSuccess))
     return cuda_fail(c, e, "plane tables");
+  if (timed) cudaEventRecord(c->cmp_ev[2], c->stream);
+  if ((e = cmp_hist_high(a, c->par, c->lc.num_sms, stream_planes.data(), c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "histograms");
   if ((e = cmp_encode(d_planes, NP, n_chunks, a.hist, d_pstream, d_ftab, d_scratch, d_cptr, d_clen, d_cplane,
                       c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "rANS");
+  if (timed) cudaEventRecord(c->cmp_ev[3], c->stream);
   const float kBf = c->par.kB;
   uint32_t kb;
   std::memcpy(&kb, &kBf, 4);
   const double xmin = c->cfg.row_x_min, xmax = c->cfg.row_x_max;
+  if (timed) cudaEventRecord(c->cmp_ev[4], c->stream);
   if ((e = cmp_layout(d_planes, NP, d_splanes, d_sn, d_ftab, d_scratch, d_cptr, d_clen, n_chunks, trk, nt, kb, xmin,
                       xmax, I, NR, n_un, n_att, d_blob, d_size, d_cdst, c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "layout");
+  if (timed) cudaEventRecord(c->cmp_ev[5], c->stream);
+  c->cmp_timed = timed;
   long long sz[2] = {0, 0};
   if ((e = cudaMemcpyAsync(sz, d_size, 16, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
@@ -1498,6 +1516,7 @@ extern "C" void tpc_destroy(tpc_ctx* c) {
   if (c->have_events)
     for (int i = 0; i <= TPC_N_STAGES; ++i) cudaEventDestroy(c->ev[i]);
     for (int i = 0; i < 3; ++i) cudaEventDestroy(c->mask_ev[i]);
+    for (int i = 0; i < 6; ++i) cudaEventDestroy(c->cmp_ev[i]);
   if (c->own_stream) {
     cudaStreamSynchronize(c->stream);
     cudaStreamDestroy(c->stream);

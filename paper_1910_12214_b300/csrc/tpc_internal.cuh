@@ -134,7 +134,7 @@ struct Buffers {
 };
 
 #define TPC_N_STAGES 11  // 9 plain-mode steps, then the batched kernel and its compaction
-#define TPC_N_REPORTED_STAGES 13  // ... then the two kernels of tpc_cluster_masks
+#define TPC_N_REPORTED_STAGES 16  // ... then the two kernels of tpc_cluster_masks, the 3 phases of tpc_compress
 
 struct LaunchCfg {
   int n_rows;
@@ -233,12 +233,16 @@ struct CmpArgs {
   int* unatt_id;         // [N]
   uint8_t* unatt_first;  // [N]
   int* trk_n;            // [n_trk + 1] cluster counts -> exclusive scan
+  int4* rec;             // [N] per-cluster codes: (z, y | q_tot << 16, q_max | row << 16, sigma_y | sigma_z << 8)
   unsigned long long* val[TPC_CMP_STREAMS];  // symbol streams
   unsigned long long* vmax;                  // [TPC_CMP_STREAMS]
   unsigned long long* hist;                  // [TPC_CMP_STREAMS][8][256]
   int* scan_tmp;                             // block partials
 };
 cudaError_t cmp_symbols(const CmpArgs& a, const DevParams& par, int num_sms, cudaStream_t s);
+// histograms of byte planes 2.. of the streams that need them (stream_planes: host array)
+cudaError_t cmp_hist_high(const CmpArgs& a, const DevParams& par, int num_sms, const int* stream_planes,
+                          cudaStream_t s);
 // plane coding: one warp per chunk of every (stream, plane)
 struct CmpPlane {
   const unsigned long long* v;

@@ -602,7 +602,7 @@ __global__ void k_cmp_attach(const __grid_constant__ CmpArgs a, const __grid_con
     if (!bad)
       for (long long j = lane; j < cnt; j += 32) {
         const uint32_t c = a.ids[first + j];
-        if (c >= (uint32_t)a.N || a.row[c] < 0 || a.row[c] >= par.n_rows)
+        if (c >= (uint32_t)a.N)
           bad = true;
         else
           a.attached[c] = 1;
@@ -614,6 +614,21 @@ __global__ void k_cmp_attach(const __grid_constant__ CmpArgs a, const __grid_con
     }
   }
 }
+
+// the codes of every cluster packed in one 16-byte record, in the input order
+// (coalesced), so that the symbol kernels gather one sector per cluster
+__global__ void k_cmp_records(const __grid_constant__ CmpArgs a, int n_rows) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < a.N; c += stride) {
+    const int r = a.row[c];
+    const unsigned ry = (unsigned)fix_sat(a.y[c], 64.f, -32768, 32767) & 0xffffu;
+    a.rec[c] = make_int4(fix_sat(a.z[c], 64.f, INT32_MIN, INT32_MAX), (int)(ry | ((unsigned)charge(a.qt[c]) << 16)),
+                         (int)((unsigned)charge(a.qm[c]) | ((unsigned)(r >= 0 && r < n_rows ? r : 0xffff) << 16)),
+                         (int)((unsigned)size(a.sy[c]) | ((unsigned)size(a.sz[c]) << 8)));
+  }
+}
+__device__ __forceinline__ int rec_y(const int4& q) { return (int)(int16_t)(q.y & 0xffff); }
+__device__ __forceinline__ int rec_row(const int4& q) { return (int)((unsigned)q.z >> 16); }  // 0xffff = out of range
 
 // unattached flags of the binned clusters, one warp per (item, row); the
 // positions between items' binned ranges (clusters left out of the binning)
@@ -649,28 +664,27 @@ __global__ void k_cmp_rowcounts(const __grid_constant__ CmpArgs a, int n_rows) {
   }
 }
 
-__device__ __forceinline__ void put_props(const CmpArgs& a, long long k, int c) {
-  a.val[C_QT][k] = (unsigned long long)charge(a.qt[c]);
-  a.val[C_QM][k] = (unsigned long long)charge(a.qm[c]);
-  a.val[C_SY][k] = (unsigned long long)size(a.sy[c]);
-  a.val[C_SZ][k] = (unsigned long long)size(a.sz[c]);
+__device__ __forceinline__ void put_props(const CmpArgs& a, long long k, const int4& q) {
+  a.val[C_QT][k] = (unsigned long long)((unsigned)q.y >> 16);
+  a.val[C_QM][k] = (unsigned long long)((unsigned)q.z & 0xffffu);
+  a.val[C_SY][k] = (unsigned long long)((unsigned)q.w & 0xffu);
+  a.val[C_SZ][k] = (unsigned long long)(((unsigned)q.w >> 8) & 0xffu);
 }
 
 __global__ void k_cmp_unatt_symbols(const __grid_constant__ CmpArgs a) {
   const long long n_un = a.kpos[a.P];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_un; k += stride) {
-    const int c = a.unatt_id[k];
-    const long long yc = fix_sat(a.y[c], 64.f, -32768, 32767), zc = fix_sat(a.z[c], 64.f, INT32_MIN, INT32_MAX);
+    const int4 q = a.rec[a.unatt_id[k]];
     long long yp = 0, zp = 0;
     if (!a.unatt_first[k]) {
-      const int b = a.unatt_id[k - 1];
-      yp = fix_sat(a.y[b], 64.f, -32768, 32767);
-      zp = fix_sat(a.z[b], 64.f, INT32_MIN, INT32_MAX);
+      const int4 b = a.rec[a.unatt_id[k - 1]];
+      yp = rec_y(b);
+      zp = b.x;
     }
-    a.val[C_DY][k] = zigzag(yc - yp);
-    a.val[C_DZ][k] = zigzag(zc - zp);
-    put_props(a, k, c);
+    a.val[C_DY][k] = zigzag((long long)rec_y(q) - yp);
+    a.val[C_DZ][k] = zigzag((long long)q.x - zp);
+    put_props(a, k, q);
   }
 }
 
@@ -685,37 +699,58 @@ __global__ void k_cmp_track_symbols(const __grid_constant__ CmpArgs a, const __g
     const tpc_track_t T = trk[t];
     const long long base = a.trk_n[t], cnt = a.trk_n[t + 1] - base;
     if (lane == 0) a.val[C_TRK_N][t] = (unsigned long long)cnt;
-    for (long long j = lane; j < cnt; j += 32) {
-      const int c = (int)a.ids[T.first_cluster + j];
-      const int r = a.row[c];
-      const int rp = j ? a.row[a.ids[T.first_cluster + j - 1]] : 0;
+    int carry = 0;  // row of the previous cluster (0 before the first)
+    for (long long j0 = 0; j0 < cnt; j0 += 32) {
+      const long long j = j0 + lane;
+      const bool act = j < cnt;
+      const int4 q = act ? a.rec[a.ids[T.first_cluster + j]] : make_int4(0, 0, 0, 0);
+      const int r = rec_row(q);
+      const int up = __shfl_up_sync(0xffffffffu, r, 1);
+      const int rp = lane ? up : carry;
+      carry = __shfl_sync(0xffffffffu, r, 31);
+      if (!act) continue;
+      if (r >= par.n_rows) {  // a cluster with a pad row out of range: the track cannot be stored
+        atomicOr(a.err, TPC_DERR_BAD_TRACK);
+        continue;
+      }
       long long py, pz;
       predict_codes(T, par.kB, par.x[r], &py, &pz);
       a.val[C_DROW][base + j] = zigzag((long long)(r - rp));
-      a.val[C_RY][base + j] = zigzag((long long)fix_sat(a.y[c], 64.f, -32768, 32767) - py);
-      a.val[C_RZ][base + j] = zigzag((long long)fix_sat(a.z[c], 64.f, INT32_MIN, INT32_MAX) - pz);
-      put_props(a, n_un + base + j, c);
+      a.val[C_RY][base + j] = zigzag((long long)rec_y(q) - py);
+      a.val[C_RZ][base + j] = zigzag((long long)q.x - pz);
+      put_props(a, n_un + base + j, q);
     }
   }
 }
 
-// largest value and byte-plane histograms of every stream (blockIdx.y = stream)
-__global__ void __launch_bounds__(256) k_cmp_stats(const __grid_constant__ CmpArgs a, int n_rows) {
-  __shared__ unsigned int h[8][256];
-  const int s = blockIdx.y;
+// length of stream s from the device-side totals
+__device__ __forceinline__ long long stream_len(const CmpArgs& a, int s, int n_rows) {
   const long long n_un = a.kpos[a.P], n_att = a.trk_n[n_tracks_of(a)];
-  const long long len[TPC_CMP_STREAMS] = {(long long)a.I * n_rows, n_un, n_un, n_att, n_att, n_att,
-                                          n_un + n_att, n_un + n_att, n_un + n_att, n_un + n_att, n_tracks_of(a)};
-  const long long n = len[s];
-  for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+  switch (s) {
+    case C_UNATT_N: return (long long)a.I * n_rows;
+    case C_DY: case C_DZ: return n_un;
+    case C_DROW: case C_RY: case C_RZ: return n_att;
+    case C_TRK_N: return n_tracks_of(a);
+    default: return n_un + n_att;
+  }
+}
+
+// largest value and the histograms of byte planes 0 and 1 of every stream
+// (blockIdx.y = stream); planes 2..7 only where the largest value needs them
+// (k_cmp_hist_high)
+__global__ void __launch_bounds__(256) k_cmp_stats(const __grid_constant__ CmpArgs a, int n_rows) {
+  __shared__ unsigned int h[2][256];
+  const int s = blockIdx.y;
+  const long long n = stream_len(a, s, n_rows);
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
   __syncthreads();
   unsigned long long mx = 0;
   const unsigned long long* v = a.val[s];
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
     const unsigned long long x = v[i];
     mx = x > mx ? x : mx;
-#pragma unroll
-    for (int p = 0; p < 8; ++p) atomicAdd(&h[p][(x >> (8 * p)) & 255], 1u);
+    atomicAdd(&h[0][x & 255], 1u);
+    atomicAdd(&h[1][(x >> 8) & 255], 1u);
   }
   for (int o = 16; o; o >>= 1) {
     const unsigned long long u = __shfl_xor_sync(0xffffffffu, mx, o);
@@ -723,47 +758,96 @@ __global__ void __launch_bounds__(256) k_cmp_stats(const __grid_constant__ CmpAr
   }
   if ((threadIdx.x & 31) == 0 && mx) atomicMax(a.vmax + s, mx);
   __syncthreads();
-  for (int i = threadIdx.x; i < 8 * 256; i += blockDim.x) {
+  for (int i = threadIdx.x; i < 512; i += blockDim.x) {
     const unsigned int c = (&h[0][0])[i];
     if (c) atomicAdd(a.hist + (long long)s * 2048 + i, (unsigned long long)c);
   }
 }
 
-// ---- coding
-// frequencies of one (stream, plane): the oracle's scaling rule
-__global__ void k_cmp_norm(const CmpPlane* planes, int n_planes, const unsigned long long* hist,
-                           const int* plane_stream, uint16_t* ftab) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= n_planes) return;
-  const unsigned long long* cnt = hist + (long long)plane_stream[q] * 2048 + 256 * planes[q].plane;
-  uint16_t* f = ftab + 512 * q;
-  unsigned long long total = 0;
-  for (int s = 0; s < 256; ++s) total += cnt[s];
-  long long sum = 0;
-  for (int s = 0; s < 256; ++s) {
-    unsigned long long v = cnt[s] ? (cnt[s] * 4096ull) / total : 0ull;
-    if (cnt[s] && v == 0) v = 1;
-    f[s] = (uint16_t)v;
-    sum += (long long)v;
+// histograms of byte planes 2 .. n_planes-1 of stream s
+__global__ void __launch_bounds__(256) k_cmp_hist_high(const __grid_constant__ CmpArgs a, int n_rows, int s,
+                                                        int n_planes) {
+  __shared__ unsigned int h[6][256];
+  const long long n = stream_len(a, s, n_rows);
+  for (int i = threadIdx.x; i < 6 * 256; i += blockDim.x) (&h[0][0])[i] = 0;
+  __syncthreads();
+  const unsigned long long* v = a.val[s];
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
+    const unsigned long long x = v[i];
+    for (int p = 2; p < n_planes; ++p) atomicAdd(&h[p - 2][(x >> (8 * p)) & 255], 1u);
   }
+  __syncthreads();
+  for (int i = threadIdx.x; i < 6 * 256; i += blockDim.x) {
+    const unsigned int c = (&h[0][0])[i];
+    if (c) atomicAdd(a.hist + (long long)s * 2048 + 512 + i, (unsigned long long)c);
+  }
+}
+
+// ---- coding
+// index of the largest f (smallest index on ties) over a block of 256 threads
+__device__ __forceinline__ int block_argmax256(unsigned f) {
+  __shared__ unsigned long long red[8];
+  unsigned long long key = ((unsigned long long)f << 32) | (255u - threadIdx.x);  // larger f, then smaller index
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long u = __shfl_xor_sync(0xffffffffu, key, o);
+    key = u > key ? u : key;
+  }
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = key;
+  __syncthreads();
+  unsigned long long m = red[0];
+  for (int w = 1; w < 8; ++w) m = red[w] > m ? red[w] : m;
+  return 255 - (int)(m & 0xffffffffu);
+}
+
+// frequencies of one (stream, plane), one block of 256 threads (one per byte
+// value): the scaling rule of the format; the excess is removed one unit at a
+// time from the current largest frequency, as the rule states
+__global__ void __launch_bounds__(256) k_cmp_norm(const CmpPlane* planes, const unsigned long long* hist,
+                                                  const int* plane_stream, uint16_t* ftab) {
+  __shared__ unsigned long long s_tot;
+  __shared__ int s_sum;
+  const int q = blockIdx.x, b = threadIdx.x;
+  const unsigned long long cnt = hist[(long long)plane_stream[q] * 2048 + 256 * planes[q].plane + b];
+  if (b == 0) {
+    s_tot = 0;
+    s_sum = 0;
+  }
+  __syncthreads();
+  atomicAdd(&s_tot, cnt);
+  __syncthreads();
+  const unsigned long long total = s_tot;
+  unsigned f = cnt ? (unsigned)((cnt * 4096ull) / total) : 0u;
+  if (cnt && f == 0) f = 1;
+  atomicAdd(&s_sum, (int)f);
+  __syncthreads();
+  int sum = s_sum;
   if (total) {
-    auto largest = [&]() {
-      int b = 0;
-      for (int s = 1; s < 256; ++s)
-        if (f[s] > f[b]) b = s;
-      return b;
-    };
-    while (sum > 4096) {
-      f[largest()] -= 1;
+    while (sum > 4096) {  // at most one unit per byte value raised to 1: <= 256 rounds
+      const int m = block_argmax256(f);
+      if (b == m) f -= 1;
       --sum;
     }
-    if (sum < 4096) f[largest()] += (uint16_t)(4096 - sum);
+    if (sum < 4096) {
+      const int m = block_argmax256(f);
+      if (b == m) f += (unsigned)(4096 - sum);
+    }
   }
-  unsigned acc = 0;
-  for (int s = 0; s < 256; ++s) {
-    f[256 + s] = (uint16_t)acc;
-    acc += f[s];
+  // cumulative frequencies: exclusive scan over the 256 byte values
+  __shared__ unsigned ws[8];
+  const int lane = b & 31, w = b >> 5;
+  unsigned inc = f;
+  for (int o = 1; o < 32; o <<= 1) {
+    const unsigned u = __shfl_up_sync(0xffffffffu, inc, o);
+    if (lane >= o) inc += u;
   }
+  __syncthreads();
+  if (lane == 31) ws[w] = inc;
+  __syncthreads();
+  unsigned base = 0;
+  for (int k = 0; k < w; ++k) base += ws[k];
+  ftab[512 * q + b] = (uint16_t)f;
+  ftab[512 * q + 256 + b] = (uint16_t)(base + inc - f);
 }
 
 // one warp per chunk: interleaved rANS, words written backwards from the end
@@ -771,13 +855,26 @@ __global__ void k_cmp_norm(const CmpPlane* planes, int n_planes, const unsigned 
 __global__ void __launch_bounds__(128) k_cmp_rans(const CmpPlane* planes, const int* chunk_plane, int n_chunks,
                                                    const uint16_t* ftab, uint16_t* scratch, long long* chunk_ptr,
                                                    int* chunk_len) {
-  __shared__ uint32_t tab[4][256];  // per warp: f | c << 16
+  // per warp and byte value: (f | c << 16, m), m the multiplier of the exact
+  // division by f through a multiply-high (Granlund and Montgomery, "Division
+  // by invariant integers using multiplication", 1994: for l = ceil(log2 f),
+  // m = floor(2^32 (2^l - f) / f) + 1, x / f = (t + ((x - t) >> 1)) >> (l - 1)
+  // with t = mulhi(m, x); f = 1 divides trivially)
+  __shared__ uint2 tab[4][256];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const int ch = blockIdx.x * 4 + w;
   const bool live = ch < n_chunks;
   const int q = live ? chunk_plane[ch] : 0;
   const CmpPlane P = planes[q];
-  for (int s = lane; s < 256; s += 32) tab[w][s] = live ? (ftab[512 * q + s] | ((uint32_t)ftab[512 * q + 256 + s] << 16)) : 0u;
+  for (int s = lane; s < 256; s += 32) {
+    const uint32_t f = live ? ftab[512 * q + s] : 0u, c = live ? ftab[512 * q + 256 + s] : 0u;
+    uint32_t m = 0;
+    if (f >= 2) {
+      const int l = 32 - __clz(f - 1);
+      m = (uint32_t)((((1ull << 32) * ((1ull << l) - f)) / f) + 1);
+    }
+    tab[w][s] = make_uint2(f | (c << 16), m);
+  }
   __syncwarp();
   if (!live) return;
   const long long c0 = ch - P.chunk0;
@@ -791,8 +888,8 @@ __global__ void __launch_bounds__(128) k_cmp_rans(const CmpPlane* planes, const 
     const int i = k * 32 + lane;
     const bool act = i < n;
     const uint32_t sym = act ? (uint32_t)((P.v[a0 + i] >> sh) & 255ull) : 0u;
-    const uint32_t e = tab[w][sym];
-    const uint32_t fs = e & 0xffffu, cs = e >> 16;
+    const uint2 e = tab[w][sym];
+    const uint32_t fs = e.x & 0xffffu, cs = e.x >> 16;
     const bool emit = act && (unsigned long long)x >= ((unsigned long long)fs << 20);
     const unsigned m = __ballot_sync(0xffffffffu, emit);
     ptr -= __popc(m);
@@ -800,7 +897,14 @@ __global__ void __launch_bounds__(128) k_cmp_rans(const CmpPlane* planes, const 
       buf[ptr + __popc(m & ((1u << lane) - 1u))] = (uint16_t)(x & 0xffffu);
       x >>= 16;
     }
-    if (act) x = ((x / fs) << 12) + (x % fs) + cs;
+    if (act) {
+      uint32_t qt = x;
+      if (fs >= 2) {
+        const uint32_t t = __umulhi(e.y, x);
+        qt = (t + ((x - t) >> 1)) >> (31 - __clz(fs - 1));  // l - 1
+      }
+      x = (qt << 12) + (x - qt * fs) + cs;
+    }
   }
   ptr -= 64;
   buf[ptr + 2 * lane] = (uint16_t)(x & 0xffffu);
@@ -924,6 +1028,7 @@ cudaError_t cmp_symbols(const CmpArgs& a, const DevParams& par, int num_sms, cud
       (e = cudaMemsetAsync(a.vmax, 0, 8 * TPC_CMP_STREAMS, s)) != cudaSuccess ||
       (e = cudaMemsetAsync(a.hist, 0, 8ull * TPC_CMP_STREAMS * 2048, s)) != cudaSuccess)
     return e;
+  k_cmp_records<<<g, 256, 0, s>>>(a, par.n_rows);
   k_cmp_attach<<<g, 256, 0, s>>>(a, par);
   // the track counts' scan needs their number on the host side: own tracks are
   // counted on the device, so scan the capacity (unused entries are zero)
@@ -939,11 +1044,18 @@ cudaError_t cmp_symbols(const CmpArgs& a, const DevParams& par, int num_sms, cud
   return cudaGetLastError();
 }
 
+cudaError_t cmp_hist_high(const CmpArgs& a, const DevParams& par, int num_sms, const int* stream_planes,
+                          cudaStream_t s) {
+  for (int st = 0; st < TPC_CMP_STREAMS; ++st)
+    if (stream_planes[st] > 2) k_cmp_hist_high<<<num_sms * 2, 256, 0, s>>>(a, par.n_rows, st, stream_planes[st]);
+  return cudaGetLastError();
+}
+
 cudaError_t cmp_encode(const CmpPlane* planes, int n_planes, int n_chunks_total, const unsigned long long* hist,
                        const int* plane_stream, uint16_t* ftab, uint16_t* scratch, long long* chunk_ptr, int* chunk_len,
                        const int* chunk_plane, cudaStream_t s) {
   if (n_planes == 0) return cudaSuccess;
-  k_cmp_norm<<<(n_planes + 63) / 64, 64, 0, s>>>(planes, n_planes, hist, plane_stream, ftab);
+  k_cmp_norm<<<n_planes, 256, 0, s>>>(planes, hist, plane_stream, ftab);
   if (n_chunks_total) k_cmp_rans<<<(n_chunks_total + 3) / 4, 128, 0, s>>>(planes, chunk_plane, n_chunks_total, ftab, scratch, chunk_ptr, chunk_len);
   return cudaGetLastError();
 }
