@@ -520,9 +520,17 @@ def bench_compress(cl, props, dev, stream, flush, tpc, torch, steps=10):
         size = int(b.shape[0])
     ms = 1e3 * float(np.median(wall))
     phases = {k: float(np.median(v)) for k, v in ph.items()}
+    # algorithmic bytes of a call: every input read once (positions, row and charges 28 B, the
+    # grid order 16 B per cluster, track cluster ids 4 B per cluster at most) and the blob written
+    algo = (28 + 16 + 4) * cl.n + size
+    peak, kind = measured_peak_hbm()
+    dev_us = sum(phases.values())
+    achieved = algo / (dev_us * 1e-6) / 1e9
     res.update(clusters_per_s=cl.n / (ms * 1e-3), ms=ms, phase_us=phases, blob_bytes=size,
                bytes_per_cluster=size / cl.n, ratio_vs_integer_codes=13.0 * cl.n / size,
-               ratio_vs_float_clusters=28.0 * cl.n / size)
+               ratio_vs_float_clusters=28.0 * cl.n / size,
+               roofline={"bound": "hbm", "kernel": "all phases (device time)", "achieved": achieved, "peak": peak,
+                         "unit": "GB/s", "frac": achieved / peak, "peak_kind": kind, "algo_bytes": algo})
     del d, ch
     torch.cuda.empty_cache()
     return res
