@@ -11,7 +11,8 @@ import numpy as np
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB = os.path.join(HERE, "liboracle.so")
 SRC = [os.path.join(HERE, f) for f in ("tpc_oracle.cpp", "corr_oracle.cpp", "mlp_oracle.cpp", "codec_oracle.cpp",
-                                                        "masks_oracle.cpp", "entropy_oracle.cpp")
+                                                        "masks_oracle.cpp", "entropy_oracle.cpp",
+                                                        "merge_oracle.cpp")
        if os.path.exists(os.path.join(HERE, f))]
 
 
@@ -104,6 +105,9 @@ def _load():
         lib.orc_decode_stream.argtypes = [C.c_void_p, C.c_int64, C.c_void_p, C.c_int64]
         lib.orc_predict.restype = None
         lib.orc_predict.argtypes = [C.c_void_p, C.c_float, C.c_float, C.c_void_p, C.c_void_p]
+        lib.orc_merge.restype = C.c_int64
+        lib.orc_merge.argtypes = ([C.c_int, C.c_double, C.c_double, C.c_double, C.c_int64] + [C.c_void_p] * 3 +
+                                  [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64] + [C.c_void_p] * 7)
         lib.orc_chi2.restype = C.c_double
         lib.orc_chi2.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         _lib = lib
@@ -413,3 +417,35 @@ def predict_codes(state6, bz, X):
     kB = np.float32(0.299792458e-2 * np.float32(bz))
     lib.orc_predict(_p(st), float(kB), float(np.float32(X)), C.byref(py), C.byref(pz))
     return int(py.value), int(pz.value)
+
+
+def merge(cl, trk_f, trk_i, ids, bz=0.5, n_rows=152, x_min=85.0, x_max=246.0):
+    """Sector-track merger of tracks trk_f [n,7] (x_ref, y, z, sinphi, tanlambda,
+    q/pT, variance of q/pT), trk_i [n,3] (item, first, count): (link [n,2] (partner in sector k+1, k-1; -1 none),
+    group [n] (smallest index of the group), ambiguous [n], fit [n,7] (per group
+    root: centre x, y, radius, tan lambda, z0, clusters, tracks))."""
+    lib = _load()
+    y = np.ascontiguousarray(cl.y, np.float32)
+    z = np.ascontiguousarray(cl.z, np.float32)
+    row = np.ascontiguousarray(cl.row, np.int32)
+    sec = np.ascontiguousarray(cl.item_sector, np.uint32)
+    ev = np.ascontiguousarray(cl.item_event, np.uint32)
+    tf = np.ascontiguousarray(np.asarray(trk_f, np.float32).reshape(-1, 7))
+    ti = np.ascontiguousarray(np.asarray(trk_i, np.int64).reshape(-1, 3))
+    ids = np.ascontiguousarray(ids, np.uint32)
+    n = tf.shape[0]
+    link = np.empty((n, 2), np.int32)
+    group = np.empty(n, np.int32)
+    amb = np.empty(n, np.uint8)
+    fit = np.empty((n, 7), np.float64)
+    st = lib.orc_merge(n_rows, x_min, x_max, bz, y.shape[0], _p(y), _p(z), _p(row), sec.shape[0], _p(sec), _p(ev),
+                       n, _p(tf), _p(ti), _p(ids), _p(link), _p(group), _p(amb), _p(fit))
+    if st < 0:
+        raise ValueError("bad input")
+    return link, group, amb, fit
+
+
+def merge_tracks(ref):
+    """(trk_f [n,7] float32 with the q/pT variance, trk_i, ids) of the oracle tracker's output."""
+    tf = np.concatenate([ref["trk_f"][:, :6], ref["trk_f"][:, 20:21]], axis=1).astype(np.float32)
+    return tf, ref["trk_i"][:, :3].astype(np.int64), ref["trk_ids"].astype(np.uint32)

@@ -1,0 +1,145 @@
+"""Pins of the sector-track merger oracle: a hand-built split helix, the
+refit on exact helices, MC-truth purity and efficiency of the links, and the
+structure of links and groups."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from test_oracle_masks_pins import row_x
+
+KB = 0.299792458e-2 * 0.5
+WEDGE = 2.0 * math.pi / 18.0
+
+
+def local_state(xc, yc, R, q, k, X, tgl, z):
+    """Track state (x_ref, y, z, sinphi, tanlambda, q/pT) in sector k's frame at
+    local x = X on the circle of global centre (xc, yc) and radius R; the sign q
+    of the curvature picks the branch (centre = (x + sinphi/kappa, y - cosphi/kappa))."""
+    a = k * WEDGE
+    lx, ly = xc * math.cos(a) + yc * math.sin(a), -xc * math.sin(a) + yc * math.cos(a)
+    kap = q / (R * 1.0)  # kappa = kB q/pT = q / R
+    s = (lx - X) * kap  # from x_c = x + s / kappa
+    y = ly + math.sqrt(1.0 - s * s) / kap
+    return [X, y, z, s, tgl, q / (R * KB), 1e-6]
+
+
+def test_hand_built_split_helix_is_linked_and_a_bent_copy_is_not():
+    """One helix from the beam axis (R = 150 cm, centre at azimuth 75 degrees,
+    q = -1: it bends from sector 0 into sector 1) seen as a sector-0 piece at
+    x = 100 cm and a sector-1 piece at x = 150 cm: the two states describe the
+    same circle, so they link; the same pair with tan(lambda) 0.03 apart does
+    not."""
+    R, q, tgl = 150.0, -1.0, 0.2
+    xc, yc = R * math.cos(math.radians(75.0)), R * math.sin(math.radians(75.0))
+    s0 = local_state(xc, yc, R, q, 0, 100.0, tgl, 10.0)
+    s1 = local_state(xc, yc, R, q, 1, 150.0, tgl, 0.0)
+    assert abs(s0[1]) < 100.0 * math.tan(math.radians(10)) and abs(s1[1]) < 150.0 * math.tan(math.radians(10))
+    # z of the second piece from the chord-series arc between the two reference points
+    a1 = WEDGE
+    P0 = np.array([s0[0], s0[1]])
+    P1 = np.array([s1[0] * math.cos(a1) - s1[1] * math.sin(a1), s1[0] * math.sin(a1) + s1[1] * math.cos(a1)])
+    c = float(np.hypot(*(P1 - P0)))
+    s1[2] = 10.0 + tgl * c * (1 + c * c / (24 * R * R))
+    assert abs(s0[3]) < 0.9 and abs(s1[3]) < 0.9
+
+    def run(tf):
+        cl = type("C", (), {})()
+        n_rows = 152
+        # each track needs clusters for the refit: put 3 on each track's reference row
+        cl.y = np.array([s0[1]] * 3 + [s1[1]] * 3, np.float32)
+        cl.z = np.array([s0[2]] * 3 + [s1[2]] * 3, np.float32)
+        cl.row = np.array([0] * 6, np.int32)
+        cl.item_sector = np.array([0, 1], np.uint32)
+        cl.item_event = np.array([0, 0], np.uint32)
+        ti = np.array([[0, 0, 3], [1, 3, 3]])
+        return oracle.merge(cl, tf, ti, np.arange(6, dtype=np.uint32), n_rows=n_rows)
+
+    tf = np.array([s0, s1], np.float32)
+    link, group, amb, _ = run(tf)
+    assert link[0].tolist() == [1, -1] and link[1].tolist() == [-1, 0]
+    assert group.tolist() == [0, 0] and not amb.any()
+    tf2 = tf.copy()
+    tf2[1, 4] += 0.03
+    link, group, _, _ = run(tf2)
+    assert (link == -1).all() and group.tolist() == [0, 1]
+
+
+def test_refit_recovers_exact_helices():
+    """Noise-free helices of one full event: every refitted group (one track or
+    several) gives the true radius and tan(lambda) of its MC particle."""
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_config2(seed=21, n_tracks=600, sigma_y=0.0, sigma_z=0.0, noise_frac=0.0, pt_range=(0.3, 3.0))
+    ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids"])
+    tf, ti, ids = oracle.merge_tracks(ref)
+    link, group, amb, fit = oracle.merge(cl, tf, ti, ids)
+    roots = np.unique(group)
+    R_true = cl.tracks["pt"] / KB
+    checked = 0
+    for g in roots:
+        members = np.flatnonzero(group == g)
+        mc = cl.mc[np.concatenate([ids[ti[t, 1]:ti[t, 1] + ti[t, 2]] for t in members])]
+        if (mc < 0).any() or np.unique(mc).size != 1:
+            continue
+        m = mc[0]
+        # the clusters are quantised to 2^-10 cm by nothing here: exact float32 positions
+        assert abs(fit[g, 2] - R_true[m]) < 2e-4 * R_true[m] + 0.05, (g, fit[g, 2], R_true[m])
+        assert abs(fit[g, 3] - cl.tracks["tgl"][m]) < 2e-3
+        checked += 1
+    assert checked > 500
+
+
+@pytest.fixture(scope="module")
+def event_merge():
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_config2(seed=22)
+    ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids"])
+    tf, ti, ids = oracle.merge_tracks(ref)
+    link, group, amb, fit = oracle.merge(cl, tf, ti, ids)
+    labels = np.array([np.bincount(cl.mc[ids[f:f + n]][cl.mc[ids[f:f + n]] >= 0]).argmax()
+                       if (cl.mc[ids[f:f + n]] >= 0).any() else -1 for _, f, n in ti])
+    return cl, tf, ti, ids, link, group, amb, fit, labels
+
+
+def test_links_are_pure_and_split_tracks_are_merged(event_merge):
+    cl, tf, ti, ids, link, group, amb, fit, labels = event_merge
+    a, d = np.nonzero(link >= 0)
+    b = link[a, d]
+    assert a.size > 500
+    assert (labels[a] == labels[b]).mean() > 0.995
+    # MC particles found as two or more tracks in neighbouring sectors of one side: merged into one group
+    sec = cl.item_sector[ti[:, 0]].astype(np.int64)
+    split, merged = 0, 0
+    for m in np.unique(labels[labels >= 0]):
+        tr = np.flatnonzero(labels == m)
+        if tr.size < 2:
+            continue
+        ks = sec[tr] % 18
+        if sec[tr].max() // 18 != sec[tr].min() // 18:
+            continue
+        if not any(((ks[i] - ks[j]) % 18) in (1, 17) for i in range(tr.size) for j in range(tr.size)):
+            continue
+        split += 1
+        merged += np.unique(group[tr]).size == 1
+    assert split > 200
+    assert merged / split > 0.95
+
+
+def test_link_and_group_structure(event_merge):
+    cl, tf, ti, ids, link, group, amb, fit, labels = event_merge
+    sec = cl.item_sector[ti[:, 0]].astype(np.int64)
+    for t in range(tf.shape[0]):
+        for d in range(2):
+            b = link[t, d]
+            if b < 0:
+                continue
+            assert link[b, 1 - d] == t
+            assert sec[b] // 18 == sec[t] // 18
+            assert (sec[b] % 18 - sec[t] % 18) % 18 == (1 if d == 0 else 17)
+            assert group[b] == group[t]
+    for g in np.unique(group):
+        members = np.flatnonzero(group == g)
+        assert members.min() == g
+        assert fit[g, 6] == members.size
+        assert fit[g, 5] == ti[members, 2].sum()
