@@ -10,8 +10,9 @@ kernel), a 50 kHz continuous-readout time frame (128 collisions, sliced), and
 the same 64 events distorted by a space-charge field, corrected by the grid or
 by the trained BF16 network, the cluster codec (float to integer with dynamic
 precision) over the 64 events' clusters, the cluster removal masks
-(attachment, adjacency, protection, strategies A and B) of the 64 events, and
-their compression (delta and track-model coding, rANS).
+(attachment, adjacency, protection, strategies A and B) of the 64 events,
+their compression (delta and track-model coding, rANS), and the merger of
+their sector tracks with refit.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
 bounded sample of the same workload instead.
@@ -89,7 +90,7 @@ def generate_forms(forms):
     jobs = {}
     ctx = mp.get_context("spawn")
     with ctx.Pool(3) as pool:
-        if any(f in forms for f in ("c3", "c5", "c6", "c7", "c8")):
+        if any(f in forms for f in ("c3", "c5", "c6", "c7", "c8", "c9")):
             jobs["c3"] = pool.apply_async(_gen_batched)
         if "c4" in forms:
             jobs["c4"] = pool.apply_async(_gen_frame)
@@ -102,6 +103,8 @@ def generate_forms(forms):
         out["c6"] = synth.cluster_props(out["c3"], seed=1)
     if "c7" in forms:
         out["c7"] = out["c3"]
+    if "c9" in forms:
+        out["c9"] = out["c3"]
     if "c8" in forms:
         from paper_1910_12214_b300 import synth
         out["c8"] = (out["c3"], out["c6"] if "c6" in out else synth.cluster_props(out["c3"], seed=1))
@@ -305,7 +308,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--forms", default="c3,c4,c5,c6,c7,c8", help="extra forms at N=1: c3,...,c8 or none")
+    ap.add_argument("--forms", default="c3,c4,c5,c6,c7,c8,c9", help="extra forms at N=1: c3,...,c9 or none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -485,6 +488,45 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
         res["masks_64_events"] = bench_masks(gen["c7"], dev, stream, flush, tpc, torch)
     if "c8" in gen:
         res["compress_64_events"] = bench_compress(*gen["c8"], dev, stream, flush, tpc, torch)
+    if "c9" in gen:
+        res["merge_64_events"] = bench_merge(gen["c9"], dev, stream, flush, tpc, torch)
+    return res
+
+
+def bench_merge(cl, dev, stream, flush, tpc, torch, steps=10):
+    """Sector-track merger with refit over the 64 events' own tracks.  The call
+    waits for its outputs (host arrays), so it is timed by the host clock and,
+    on its stream, by CUDA events around it.  L2 flushed between calls."""
+    with torch.cuda.stream(stream):
+        d = to_device(cl, dev)
+    stream.synchronize()
+    res = {"clusters": cl.n}
+    with tpc.Tracker(stream=stream) as t:
+        t.load(d, on_device=True)
+        t.track()
+        n_trk = t.counts()[0]
+        for _ in range(3):
+            link, group, fit = t.merge_tracks(n_tracks=n_trk)
+        wall, dev_ms = [], []
+        for _ in range(steps):
+            with torch.cuda.stream(stream):
+                flush.zero_()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            w0 = time.perf_counter()
+            e0.record(stream)
+            link, group, fit = t.merge_tracks(n_tracks=n_trk)
+            e1.record(stream)
+            wall.append(time.perf_counter() - w0)
+            torch.cuda.synchronize()
+            dev_ms.append(e0.elapsed_time(e1))
+    ms = 1e3 * float(np.median(wall))
+    res.update(tracks=n_trk, tracks_per_s=n_trk / (ms * 1e-3), clusters_per_s=cl.n / (ms * 1e-3), ms=ms,
+               device_ms=float(np.median(dev_ms)), links=int((link >= 0).sum() // 2),
+               groups=int(np.unique(group).size))
+    del d
+    torch.cuda.empty_cache()
     return res
 
 

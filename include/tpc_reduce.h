@@ -205,6 +205,53 @@ tpc_status tpc_compress(tpc_ctx* ctx, const tpc_cluster_charges* charges, const 
                         uint64_t n_tracks, const uint32_t* cluster_ids, uint64_t n_ids, int on_device, uint8_t* out,
                         uint64_t cap, uint64_t* size);
 
+/* ---- Sector-track merger (Sec. 4: the pieces of one track are found in
+ * neighbouring sectors separately and must be merged; the removal of clusters
+ * of secondary legs works only if the merging works) ---------------------
+ *
+ * This library's reading (the paper gives no algorithm):
+ *  - sectors: 36, 18 per side (0-17 z >= 0, 18-35 z < 0), sector k = s mod
+ *    18 centred at azimuth k * 20 degrees; a track's circle in the global
+ *    frame from its state (curvature kappa = 0.299792458e-2 Bz q/pT, centre
+ *    (x_ref + sinphi/kappa, y - cosphi/kappa) in its sector frame); tracks
+ *    with |q/pT| < 1e-4 c/GeV are not merged;
+ *  - candidates: tracks of the items of the same event and side in sectors
+ *    k+1 and k-1, same sign of q/pT; compatible if (a) (q/pT_A - q/pT_B)^2 <=
+ *    16 (var_A + var_B) (the q/pT variances, cov[14]); (b) the reference point
+ *    of one lies on the circle of the better measured one within 1 cm + 3 kB
+ *    sqrt(var) L^2, L the chord between the reference points; (c) |d tan
+ *    lambda| <= 0.02; (d) the outer reference point's z within 2 cm of the inner
+ *    track's z + tan(lambda) arc, arc = c (1 + c^2 / (24 R^2)) from the chord c;
+ *  - score = chi2(a)/16 + distance(b)/limit + |d tan lambda|/0.02 + |dz|/2 cm;
+ *    per direction the compatible candidate with the smallest score (ties:
+ *    smaller index); a link joins two tracks that are each other's best in
+ *    opposite directions; a group = the tracks connected by links, labelled by
+ *    its smallest track index;
+ *  - refit of every group in the global frame (FP64): the clusters of its
+ *    tracks (the pad row fixes x), the algebraic least-squares circle of x^2 +
+ *    y^2 + D x + E y + F on coordinates centred on their mean, then z = z0 +
+ *    tan(lambda) s by least squares, s the chord-series arc from the innermost
+ *    cluster. */
+
+/* Merges the tracks of the loaded, tracked batch, which must carry
+ * item_sector and item_event (TPC_ERR_STATE otherwise; one item per (event,
+ * sector)).
+ *  tracks: NULL = the context's own tracks of the last tpc_track() (n_tracks
+ *    must be their number, as tpc_get_tracks reports it; cluster_ids, n_ids
+ *    ignored); else n_tracks records sorted by item with their cluster_ids
+ *    (n_ids entries).  A track out of range (item, cluster, row) or out of
+ *    item order gives TPC_ERR_BAD_INPUT.
+ *  link: [n_tracks][2] the linked track in sector k+1 and k-1 (-1 none);
+ *  group: [n_tracks] the group's smallest track index;
+ *  fit: [n_tracks][7] doubles, at each group's smallest index: circle centre
+ *    x, y [cm, global frame], radius [cm], tan(lambda), z0 [cm] at the
+ *    innermost cluster, clusters, tracks; zero elsewhere (and for straight
+ *    tracks).
+ *  on_device: 1 = tracks, cluster_ids and the outputs are device pointers
+ *    (the call still waits); 0 = host pointers. */
+tpc_status tpc_merge_tracks(tpc_ctx* ctx, const tpc_track_t* tracks, uint64_t n_tracks, const uint32_t* cluster_ids,
+                            uint64_t n_ids, int on_device, int32_t* link, int32_t* group, double* fit);
+
 #ifdef __cplusplus
 }
 #endif

@@ -42,6 +42,7 @@ struct tpc_ctx {
   bool have_events = false;
   // host copies used by the debug dump and the work queue
   std::vector<uint64_t> h_item_off;
+  std::vector<uint32_t> h_item_sector, h_item_event;  // empty if the batch has none
   int* own_queue = nullptr;
   // execution mode and CUDA graph of tpc_track
   bool batched = false, use_graph = false, last_batched = false;
@@ -72,8 +73,8 @@ struct tpc_ctx {
   void* mask_stage = nullptr;
   size_t mask_stage_bytes = 0;
   // compression: persistent work buffers, grown on demand
-  void* cmp_buf[40] = {};
-  size_t cmp_cap[40] = {};
+  void* cmp_buf[48] = {};
+  size_t cmp_cap[48] = {};
 };
 
 namespace {
@@ -389,6 +390,14 @@ extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
     e = cudaMemcpyAsync((void*)ev_dev, cl->item_event, 4 * I, cudaMemcpyHostToDevice, c->stream);
   // work queue of the batched form: items by decreasing cluster count (longest first)
   c->h_item_off.assign(cl->item_off, cl->item_off + cl->n_items + 1);
+  if (cl->item_sector)
+    c->h_item_sector.assign(cl->item_sector, cl->item_sector + cl->n_items);
+  else
+    c->h_item_sector.clear();
+  if (cl->item_event)
+    c->h_item_event.assign(cl->item_event, cl->item_event + cl->n_items);
+  else
+    c->h_item_event.clear();
   std::vector<int> order(cl->n_items);
   for (uint32_t i = 0; i < cl->n_items; ++i) order[i] = (int)i;
   std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
@@ -1505,6 +1514,116 @@ extern "C" tpc_status tpc_compress(tpc_ctx* c, const tpc_cluster_charges* ch, co
                            c->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "blob copy");
+  return TPC_OK;
+}
+
+// ---- sector-track merger ----
+
+extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, uint64_t n_tracks,
+                                       const uint32_t* cluster_ids, uint64_t n_ids, int on_device, int32_t* link,
+                                       int32_t* group, double* fit) {
+  if (!c) return TPC_ERR_INVALID_ARG;
+  if (!c->tracked) return fail(c, TPC_ERR_STATE, "tpc_merge_tracks before tpc_track");
+  const int I = (int)c->h_item_sector.size();
+  if (I == 0 || c->h_item_event.size() != (size_t)I)
+    return fail(c, TPC_ERR_STATE, "the batch has no item_sector / item_event");
+  if (n_tracks && (!link || !group || !fit)) return fail(c, TPC_ERR_INVALID_ARG, "null output");
+  if (tracks && n_tracks && !cluster_ids) return fail(c, TPC_ERR_INVALID_ARG, "null cluster ids");
+  if (n_tracks > 0x7fffffffull) return fail(c, TPC_ERR_INVALID_ARG, "too many tracks");
+  cudaError_t e;
+  const void* trk;
+  const uint32_t* ids;
+  long long nt = (long long)n_tracks, ni = (long long)n_ids;
+  if (!tracks) {
+    unsigned long long cnt[2];
+    if ((e = cudaMemcpyAsync(cnt, c->b.counts, 16, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "track counts");
+    if (cnt[0] != n_tracks) return fail(c, TPC_ERR_INVALID_ARG, "n_tracks differs from the number of tracks");
+    trk = c->b.trk;
+    ids = c->b.trk_ids;
+    ni = (long long)cnt[1];
+  } else if (on_device) {
+    trk = tracks;
+    ids = cluster_ids;
+  } else {
+    void* t = cmp_buffer(c, 33, sizeof(tpc_track_t) * (size_t)nt);
+    void* d = cmp_buffer(c, 34, 4 * (size_t)ni);
+    if (!t || !d) return fail(c, TPC_ERR_OOM, "track staging");
+    if ((nt && (e = cudaMemcpyAsync(t, tracks, sizeof(tpc_track_t) * nt, cudaMemcpyHostToDevice, c->stream)) !=
+                   cudaSuccess) ||
+        (ni && (e = cudaMemcpyAsync(d, cluster_ids, 4 * ni, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess))
+      return cuda_fail(c, e, "track upload");
+    trk = t;
+    ids = (const uint32_t*)d;
+  }
+  // neighbouring items: same event and side, sector k+1 / k-1
+  std::vector<int> nb(2 * (size_t)I, -1);
+  {
+    std::vector<std::pair<uint64_t, int>> key(I);
+    for (int i = 0; i < I; ++i) key[i] = {((uint64_t)c->h_item_event[i] << 32) | c->h_item_sector[i], i};
+    std::sort(key.begin(), key.end());
+    auto find = [&](uint32_t ev, uint32_t sec) {
+      const uint64_t k = ((uint64_t)ev << 32) | sec;
+      auto it = std::lower_bound(key.begin(), key.end(), std::make_pair(k, INT32_MIN));
+      return (it != key.end() && it->first == k) ? it->second : -1;
+    };
+    for (int i = 0; i < I; ++i) {
+      const uint32_t s = c->h_item_sector[i];
+      if (s >= 36) continue;
+      const uint32_t side = s / 18, k = s % 18;
+      nb[2 * i] = find(c->h_item_event[i], side * 18 + (k + 1) % 18);
+      nb[2 * i + 1] = find(c->h_item_event[i], side * 18 + (k + 17) % 18);
+    }
+  }
+  int* d_nb = (int*)cmp_buffer(c, 35, 8 * (size_t)I);
+  int* d_first = (int*)cmp_buffer(c, 36, 4 * (size_t)(I + 1));
+  double* d_geo = (double*)cmp_buffer(c, 37, 8 * 12 * (size_t)std::max(nt, 1ll));
+  int* d_best = (int*)cmp_buffer(c, 38, 8 * (size_t)std::max(nt, 1ll));
+  // outputs: the caller's device arrays, or staging for host arrays
+  uint8_t* st = nullptr;
+  const size_t o_link = 0, o_group = ((8 * (size_t)nt + 255) & ~size_t(255)),
+               o_fit = o_group + ((4 * (size_t)nt + 255) & ~size_t(255));
+  if (!on_device) st = (uint8_t*)cmp_buffer(c, 39, o_fit + 56 * (size_t)std::max(nt, 1ll));
+  if (!d_nb || !d_first || !d_geo || !d_best || (!on_device && !st)) return fail(c, TPC_ERR_OOM, "merge buffers");
+  if ((e = cudaMemcpyAsync(d_nb, nb.data(), 8 * (size_t)I, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "neighbour table");
+  unsigned int err0 = 0;
+  if ((e = cudaMemcpyAsync(&err0, c->b.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "error word");
+  MrgArgs a{};
+  a.trk = trk;
+  a.ids = ids;
+  a.n_trk = nt;
+  a.n_ids = ni;
+  a.item_sector = c->b.item_sector;
+  a.item_event = c->b.item_event;
+  a.nb_item = d_nb;
+  a.I = I;
+  a.y = c->b.y;
+  a.z = c->b.z;
+  a.row = c->b.row;
+  a.N = c->b.N;
+  a.kB = 0.299792458e-2 * (double)c->cfg.bz_tesla;
+  a.item_first = d_first;
+  a.geo = d_geo;
+  a.best = d_best;
+  a.link = on_device ? link : (int*)(st + o_link);
+  a.group = on_device ? group : (int*)(st + o_group);
+  a.fit = on_device ? fit : (double*)(st + o_fit);
+  a.err = c->b.err;
+  if ((e = launch_merge(a, c->par, c->lc.num_sms, c->stream)) != cudaSuccess) return cuda_fail(c, e, "merge");
+  if (!on_device && nt &&
+      ((e = cudaMemcpyAsync(link, a.link, 8 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+       (e = cudaMemcpyAsync(group, a.group, 4 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+       (e = cudaMemcpyAsync(fit, a.fit, 56 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess))
+    return cuda_fail(c, e, "merge download");
+  unsigned int err = 0;
+  if ((e = cudaMemcpyAsync(&err, c->b.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "merge sync");
+  if ((err & ~err0) & TPC_DERR_BAD_TRACK)
+    return fail(c, TPC_ERR_BAD_INPUT, "a track is out of range or out of item order");
   return TPC_OK;
 }
 

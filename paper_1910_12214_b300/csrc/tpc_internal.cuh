@@ -259,3 +259,26 @@ cudaError_t cmp_layout(const CmpPlane* planes, int n_planes, const int* stream_p
                        int n_chunks_total, const void* trk, long long n_trk, uint32_t kB_bits, double x_min,
                        double x_max, int n_items, int n_rows, long long n_unatt, long long n_att, uint8_t* out,
                        long long* out_size, long long* chunk_dst, cudaStream_t s);
+
+// Sector-track merger (tpc_reduce.cu).
+struct MrgArgs {
+  const void* trk;            // tpc_track_t records, sorted by item
+  const uint32_t* ids;
+  long long n_trk, n_ids;
+  const uint32_t* item_sector;
+  const uint32_t* item_event;
+  const int* nb_item;         // [I][2] item of the same event and side in sector k+1 / k-1, -1 none
+  int I;
+  const float *y, *z;
+  const int* row;
+  int N;
+  double kB;
+  int* item_first;            // [I + 1] first track of every item
+  double* geo;                // [n_trk][12] per-track circle (device work array)
+  int* best;                  // [n_trk][2]
+  int* link;                  // [n_trk][2] output
+  int* group;                 // [n_trk] output
+  double* fit;                // [n_trk][7] output (group roots)
+  unsigned int* err;
+};
+cudaError_t launch_merge(const MrgArgs& a, const DevParams& par, int num_sms, cudaStream_t s);

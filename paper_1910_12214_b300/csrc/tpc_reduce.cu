@@ -1074,3 +1074,326 @@ cudaError_t cmp_layout(const CmpPlane* planes, int n_planes, const int* stream_p
   if (n_trk) k_cmp_tracks<<<(int)std::min<long long>((n_trk + 255) / 256, 4096), 256, 0, s>>>(trk, n_trk, out_size, out);
   return cudaGetLastError();
 }
+
+// ============================================================================
+// Sector-track merger (Sec. 4: the pieces of one track found in neighbouring
+// sectors are joined, and the merged track is refitted).
+//
+// Every track gets its circle in the global frame (FP64); one warp per track
+// finds, in the items of the same event and side in sectors k+1 and k-1, the
+// compatible candidate of smallest score (a curvature chi2, the continuation
+// on the better-measured circle, tan(lambda), z along the arc); a link joins
+// two tracks that are each other's best in opposite directions.  Links are
+// mutual and one per direction, so every group is a path through neighbouring
+// sectors: a bounded walk labels it by its smallest index.  One warp per group
+// then refits the group's clusters in the global frame (algebraic circle fit,
+// then z against the arc), in FP64.
+namespace {
+
+constexpr double MRG_WEDGE = 2.0 * 3.14159265358979323846 / 18.0;
+enum { G_OK, G_XC, G_YC, G_R, G_X, G_Y, G_RAD, G_Z, G_TGL, G_QPT, G_VQ, G_SIGN, G_N };
+
+__global__ void k_mrg_geom(const __grid_constant__ MrgArgs a) {
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride) {
+    const tpc_track_t T = trk[t];
+    double* g = a.geo + G_N * t;
+    const bool range_ok = T.item < (uint32_t)a.I && (long long)T.first_cluster + T.n_clusters <= a.n_ids;
+    if (!range_ok || (t > 0 && trk[t - 1].item > T.item)) atomicOr(a.err, TPC_DERR_BAD_TRACK);
+    const bool ok = fabsf(T.qpt) >= 1e-4f && range_ok;
+    g[G_OK] = ok ? 1.0 : 0.0;
+    if (!ok) continue;
+    const int s = (int)a.item_sector[T.item];
+    const double ang = (double)(s % 18) * MRG_WEDGE, ca = cos(ang), sa = sin(ang);
+    const double kap = a.kB * (double)T.qpt;
+    const double snp = T.snp, csp = sqrt(fmax(0.0, 1.0 - snp * snp));
+    const double lx = (double)T.x_ref + snp / kap, ly = (double)T.y - csp / kap;
+    g[G_XC] = lx * ca - ly * sa;
+    g[G_YC] = lx * sa + ly * ca;
+    g[G_R] = 1.0 / fabs(kap);
+    const double X = (double)T.x_ref * ca - (double)T.y * sa, Y = (double)T.x_ref * sa + (double)T.y * ca;
+    g[G_X] = X;
+    g[G_Y] = Y;
+    g[G_RAD] = hypot(X, Y);
+    g[G_Z] = T.z;
+    g[G_TGL] = T.tgl;
+    g[G_QPT] = T.qpt;
+    g[G_VQ] = fmax(0.0, (double)T.cov[14]);
+    g[G_SIGN] = T.qpt > 0.f ? 1.0 : -1.0;
+  }
+}
+
+// first track of every item (tracks are sorted by item)
+__global__ void k_mrg_item_first(const __grid_constant__ MrgArgs a) {
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= a.I; i += stride) {
+    long long lo = 0, hi = a.n_trk;  // first t with item >= i
+    while (lo < hi) {
+      const long long m = (lo + hi) >> 1;
+      if (trk[m].item < (uint32_t)i)
+        lo = m + 1;
+      else
+        hi = m;
+    }
+    a.item_first[i] = (int)lo;
+  }
+}
+
+__device__ __forceinline__ bool mrg_compatible(const double* A, const double* B, double kB, double* score) {
+  // the cheap tests first (they reject almost every wrong pair): tan(lambda), then the curvature chi2
+  const double dt = fabs(A[G_TGL] - B[G_TGL]);
+  if (!(dt <= 0.02)) return false;
+  const double dq = A[G_QPT] - B[G_QPT], vsum = fmax(A[G_VQ] + B[G_VQ], 1e-30);
+  if (!(dq * dq <= 16.0 * vsum)) return false;
+  const double chi2 = dq * dq / vsum;
+  const double* ref = A[G_VQ] <= B[G_VQ] ? A : B;
+  const double* oth = A[G_VQ] <= B[G_VQ] ? B : A;
+  const double L = hypot(oth[G_X] - ref[G_X], oth[G_Y] - ref[G_Y]);
+  const double d = fabs(hypot(oth[G_X] - ref[G_XC], oth[G_Y] - ref[G_YC]) - ref[G_R]);
+  const double dlim = 1.0 + 3.0 * kB * sqrt(ref[G_VQ]) * L * L;
+  const double* in = A[G_RAD] <= B[G_RAD] ? A : B;
+  const double* out = A[G_RAD] <= B[G_RAD] ? B : A;
+  const double c = hypot(out[G_X] - in[G_X], out[G_Y] - in[G_Y]);
+  const double Rb = 0.5 * (A[G_R] + B[G_R]);
+  const double arc = c * (1.0 + c * c / (24.0 * Rb * Rb));
+  const double dz = fabs(out[G_Z] - (in[G_Z] + in[G_TGL] * arc));
+  *score = chi2 / 16.0 + d / dlim + dt / 0.02 + dz / 2.0;
+  return d <= dlim && dz <= 2.0;
+}
+
+// one warp per track: the best compatible candidate in sector k+1 (d = 0) and k-1 (d = 1)
+__global__ void k_mrg_best(const __grid_constant__ MrgArgs a) {
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const int lane = threadIdx.x & 31;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_trk; t += nw) {
+    const double* A = a.geo + G_N * t;
+    const bool ok = A[G_OK] != 0.0;
+    for (int d = 0; d < 2; ++d) {
+      const int nb = ok ? a.nb_item[2 * trk[t].item + d] : -1;
+      double bs = 0.0;
+      long long bi = -1;
+      if (nb >= 0)
+        for (long long b = a.item_first[nb] + lane; b < a.item_first[nb + 1]; b += 32) {
+          const double* B = a.geo + G_N * b;
+          if (B[G_OK] == 0.0 || B[G_SIGN] != A[G_SIGN]) continue;
+          double sc;
+          if (!mrg_compatible(A, B, a.kB, &sc)) continue;
+          if (bi < 0 || sc < bs) {  // lanes visit candidates in increasing index: ties keep the smaller
+            bs = sc;
+            bi = b;
+          }
+        }
+      for (int o = 16; o; o >>= 1) {  // smallest (score, index)
+        const double os = __shfl_xor_sync(0xffffffffu, bs, o);
+        const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+        if (oi >= 0 && (bi < 0 || os < bs || (os == bs && oi < bi))) {
+          bs = os;
+          bi = oi;
+        }
+      }
+      if (lane == 0) a.best[2 * t + d] = (int)bi;
+    }
+  }
+}
+
+__global__ void k_mrg_link(const __grid_constant__ MrgArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride)
+    for (int d = 0; d < 2; ++d) {
+      const int b = a.best[2 * t + d];
+      a.link[2 * t + d] = (b >= 0 && a.best[2 * b + (1 - d)] == (int)t) ? b : -1;
+    }
+}
+
+// the group of a track: the smallest index on its path of links (at most 18
+// steps each way: one track per sector of a side)
+__global__ void k_mrg_group(const __grid_constant__ MrgArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride) {
+    int m = (int)t;
+    for (int d = 0; d < 2; ++d) {
+      int cur = (int)t;
+      for (int step = 0; step < 18; ++step) {
+        const int nxt = a.link[2 * cur + d];
+        if (nxt < 0) break;
+        m = min(m, nxt);
+        cur = nxt;
+      }
+    }
+    a.group[t] = m;
+  }
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// one warp per group root: refit of the group's clusters in the global frame
+__global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs a,
+                                                  const __grid_constant__ DevParams par) {
+  __shared__ int mem[4][40];
+  __shared__ double rot[4][40][2];  // cos and sin of each member's sector angle
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_trk; t += nw) {
+    double* o = a.fit + 7 * t;
+    if (lane < 7) o[lane] = 0.0;
+    if (a.group[t] != (int)t || a.geo[G_N * t + G_OK] == 0.0) continue;
+    // members in index order (the root is the smallest)
+    int nm = 0;
+    if (lane == 0) {
+      mem[w][nm++] = (int)t;
+      for (int d = 0; d < 2; ++d) {
+        int cur = (int)t;
+        for (int step = 0; step < 18; ++step) {
+          const int nxt = a.link[2 * cur + d];
+          if (nxt < 0) break;
+          mem[w][nm++] = nxt;
+          cur = nxt;
+        }
+      }
+      for (int i = 1; i < nm; ++i)  // insertion sort (at most 37 members)
+        for (int j = i; j > 0 && mem[w][j - 1] > mem[w][j]; --j) {
+          const int x = mem[w][j];
+          mem[w][j] = mem[w][j - 1];
+          mem[w][j - 1] = x;
+        }
+    }
+    nm = __shfl_sync(0xffffffffu, nm, 0);
+    __syncwarp();
+    for (int m = lane; m < nm; m += 32) {
+      const double ang = (double)((int)a.item_sector[trk[mem[w][m]].item] % 18) * MRG_WEDGE;
+      rot[w][m][0] = cos(ang);
+      rot[w][m][1] = sin(ang);
+    }
+    __syncwarp();
+    auto cluster_at = [&](int m, long long j, double* X, double* Y, double* Z) {
+      const tpc_track_t& T = trk[mem[w][m]];
+      const double ca = rot[w][m][0], sa = rot[w][m][1];
+      uint32_t c = a.ids[T.first_cluster + j];
+      int r = c < (uint32_t)a.N ? a.row[c] : -1;
+      if (r < 0 || r >= par.n_rows) {  // reported as an error (the results are then not used); read cluster 0
+        atomicOr(a.err, TPC_DERR_BAD_TRACK);
+        c = 0;
+        r = 0;
+      }
+      const double lx = par.x[r], ly = a.N > 0 ? a.y[c] : 0.0;
+      *X = lx * ca - ly * sa;
+      *Y = lx * sa + ly * ca;
+      *Z = a.N > 0 ? a.z[c] : 0.0;
+    };
+    // pass 1: mean, count and the innermost cluster (smallest radius, first in order on ties)
+    double sx = 0, sy = 0, rmin = 1e300, xin = 0, yin = 0;
+    long long pin = -1, n = 0, pos = 0;
+    for (int m = 0; m < nm; ++m) {
+      const long long cnt = trk[mem[w][m]].n_clusters;
+      for (long long j = lane; j < cnt; j += 32) {
+        double X, Y, Z;
+        cluster_at(m, j, &X, &Y, &Z);
+        sx += X;
+        sy += Y;
+        const double rr = X * X + Y * Y;  // ordering by the squared radius
+        if (rr < rmin) {  // a lane sees its positions in increasing order
+          rmin = rr;
+          pin = pos + j;
+          xin = X;
+          yin = Y;
+        }
+      }
+      pos += cnt;
+      n += cnt;
+    }
+    for (int off = 16; off; off >>= 1) {
+      const double orr = __shfl_xor_sync(0xffffffffu, rmin, off);
+      const long long op = __shfl_xor_sync(0xffffffffu, pin, off);
+      const double ox = __shfl_xor_sync(0xffffffffu, xin, off), oy = __shfl_xor_sync(0xffffffffu, yin, off);
+      if (op >= 0 && (pin < 0 || orr < rmin || (orr == rmin && op < pin))) {
+        rmin = orr;
+        pin = op;
+        xin = ox;
+        yin = oy;
+      }
+    }
+    sx = warp_sum(sx);
+    sy = warp_sum(sy);
+    if (n < 3) continue;
+    const double mx = sx / (double)n, my = sy / (double)n;
+    // pass 2: centred moments
+    double suu = 0, suv = 0, svv = 0, su3 = 0, sv3 = 0, sw = 0;
+    for (int m = 0; m < nm; ++m) {
+      const long long cnt = trk[mem[w][m]].n_clusters;
+      for (long long j = lane; j < cnt; j += 32) {
+        double X, Y, Z;
+        cluster_at(m, j, &X, &Y, &Z);
+        const double u = X - mx, v = Y - my, ww = u * u + v * v;
+        suu += u * u;
+        suv += u * v;
+        svv += v * v;
+        su3 += u * ww;
+        sv3 += v * ww;
+        sw += ww;
+      }
+    }
+    suu = warp_sum(suu);
+    suv = warp_sum(suv);
+    svv = warp_sum(svv);
+    su3 = warp_sum(su3);
+    sv3 = warp_sum(sv3);
+    sw = warp_sum(sw);
+    const double det = suu * svv - suv * suv;
+    if (!(fabs(det) > 0.0)) continue;
+    const double D = (-su3 * svv + sv3 * suv) / det, E = (-sv3 * suu + su3 * suv) / det, F = -sw / (double)n;
+    const double xc = mx - 0.5 * D, yc = my - 0.5 * E;
+    const double R = sqrt(0.25 * (D * D + E * E) - F);
+    // pass 3: z against the arc from the innermost cluster
+    double ss = 0, sz = 0, sss = 0, ssz = 0;
+    for (int m = 0; m < nm; ++m) {
+      const long long cnt = trk[mem[w][m]].n_clusters;
+      for (long long j = lane; j < cnt; j += 32) {
+        double X, Y, Z;
+        cluster_at(m, j, &X, &Y, &Z);
+        const double c = hypot(X - xin, Y - yin);
+        const double s = c * (1.0 + c * c / (24.0 * R * R));
+        ss += s;
+        sz += Z;
+        sss += s * s;
+        ssz += s * Z;
+      }
+    }
+    ss = warp_sum(ss);
+    sz = warp_sum(sz);
+    sss = warp_sum(sss);
+    ssz = warp_sum(ssz);
+    const double den = (double)n * sss - ss * ss;
+    const double tgl = den > 0.0 ? ((double)n * ssz - ss * sz) / den : 0.0;
+    if (lane == 0) {
+      o[0] = xc;
+      o[1] = yc;
+      o[2] = R;
+      o[3] = tgl;
+      o[4] = (sz - tgl * ss) / (double)n;
+      o[5] = (double)n;
+      o[6] = (double)nm;
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_merge(const MrgArgs& a, const DevParams& par, int num_sms, cudaStream_t s) {
+  const int g = num_sms * 8;
+  k_mrg_item_first<<<(a.I + 256) / 256, 256, 0, s>>>(a);
+  if (a.n_trk > 0) {
+    k_mrg_geom<<<g, 256, 0, s>>>(a);
+    k_mrg_best<<<g, 256, 0, s>>>(a);
+    k_mrg_link<<<g, 256, 0, s>>>(a);
+    k_mrg_group<<<g, 256, 0, s>>>(a);
+    k_mrg_fit<<<num_sms * 16, 128, 0, s>>>(a, par);
+  }
+  return cudaGetLastError();
+}

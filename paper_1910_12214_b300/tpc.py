@@ -115,6 +115,7 @@ _sig = {
                           C.c_int),
     "tpc_compress": ([_P, C.POINTER(tpc_cluster_charges), _P, C.c_uint64, _P, C.c_uint64, C.c_int, _P, C.c_uint64,
                       C.POINTER(C.c_uint64)], C.c_int),
+    "tpc_merge_tracks": ([_P, _P, C.c_uint64, _P, C.c_uint64, C.c_int, _P, _P, _P], C.c_int),
     "tpc_destroy": ([_P], None),
     "tpc_last_error": ([_P], C.c_char_p),
 }
@@ -443,6 +444,25 @@ class Tracker:
             st = call(out)
         self._check(st)
         return out[:int(size.value)]
+
+    def merge_tracks(self, tracks=None, ids=None, n_tracks=None):
+        """Sector-track merger (include/tpc_reduce.h): (link [n,2], group [n],
+        fit [n,7]) as numpy arrays.  tracks=None merges the last tpc_track()
+        output (n_tracks = its count, read here if None); else TRACK_DTYPE
+        records sorted by item and uint32 ids."""
+        if tracks is None:
+            n = self.counts()[0] if n_tracks is None else int(n_tracks)
+        else:
+            tracks = np.ascontiguousarray(tracks, TRACK_DTYPE)
+            ids = np.ascontiguousarray(ids, np.uint32)
+            n = int(tracks.shape[0])
+        link = np.zeros((n, 2), np.int32)
+        group = np.zeros(n, np.int32)
+        fit = np.zeros((n, 7), np.float64)
+        ni = int(ids.shape[0]) if ids is not None else 0
+        self._check(_lib.tpc_merge_tracks(self._h, _ptr(tracks), n, _ptr(ids), ni, 0, _ptr(link) if n else None,
+                                          _ptr(group) if n else None, _ptr(fit) if n else None))
+        return link, group, fit
 
     def close(self):
         if getattr(self, "_h", None):

@@ -1,0 +1,117 @@
+"""Parity of the CUDA sector-track merger with the oracle, through the C ABI:
+with the same tracks (the oracle tracker's), identical links and groups except
+tracks the oracle flags as rounding-sensitive, and refits equal to 1e-9; with
+the GPU's own tracks, the merger's structure and MC-truth quality."""
+import numpy as np
+import pytest
+
+import oracle
+
+pytestmark = pytest.mark.gpu
+
+
+def to_records(tf7, ti):
+    from paper_1910_12214_b300 import tpc
+    r = np.zeros(tf7.shape[0], dtype=tpc.TRACK_DTYPE)
+    for k, name in enumerate(("x_ref", "y", "z", "snp", "tgl", "qpt")):
+        r[name] = tf7[:, k]
+    r["cov"][:, 14] = tf7[:, 6]
+    r["item"], r["first_cluster"], r["n_clusters"] = ti[:, 0], ti[:, 1], ti[:, 2]
+    return r
+
+
+def tracked(cl):
+    from paper_1910_12214_b300 import tpc
+    t = tpc.Tracker(device=0)
+    t.load(cl).track()
+    t.sync()
+    return t
+
+
+def compare(cl, tf, ti, ids, link, group, fit):
+    wl, wg, amb, wf = oracle.merge(cl, tf, ti, ids)
+    bad = amb.astype(bool)
+    # groups touched by a rounding-sensitive track are compared for validity only
+    touched = np.zeros(tf.shape[0], bool)
+    touched[np.isin(wg, wg[bad])] = True
+    touched[np.isin(group, group[bad])] = True
+    ok = ~touched
+    assert ok.mean() > 0.99
+    assert np.array_equal(link[ok], wl[ok])
+    assert np.array_equal(group[ok], wg[ok])
+    roots = np.flatnonzero(ok & (wg == np.arange(tf.shape[0])))
+    assert np.allclose(fit[roots], wf[roots], rtol=1e-9, atol=1e-9)
+    for t in np.flatnonzero(~ok):  # validity: mutual links
+        for d in range(2):
+            b = link[t, d]
+            if b >= 0:
+                assert link[b, 1 - d] == t
+
+
+@pytest.mark.parametrize("cfg", ["c2", "c3"])
+def test_oracle_tracks(cfg):
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_config2(seed=31) if cfg == "c2" else synth.make_batched(seed=1)
+    ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids"])
+    tf, ti, ids = oracle.merge_tracks(ref)
+    with tracked(cl) as t:
+        link, group, fit = t.merge_tracks(to_records(tf, ti), ids)
+    compare(cl, tf, ti, ids, link, group, fit)
+
+
+def test_own_tracks_product_path():
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_config2(seed=32)
+    with tracked(cl) as t:
+        trk, tids = t.get_tracks()
+        link, group, fit = t.merge_tracks()
+    n = trk.shape[0]
+    first = trk["first_cluster"].astype(np.int64)
+    cnt = trk["n_clusters"].astype(np.int64)
+    labels = np.array([np.bincount(cl.mc[tids[f:f + k]][cl.mc[tids[f:f + k]] >= 0]).argmax()
+                       if (cl.mc[tids[f:f + k]] >= 0).any() else -1 for f, k in zip(first, cnt)])
+    a, d = np.nonzero(link >= 0)
+    b = link[a, d]
+    assert a.size > 1000
+    assert np.all(link[b, 1 - d] == a)
+    assert (labels[a] == labels[b]).mean() > 0.995
+    sec = trk["sector"].astype(np.int64)
+    assert np.all(((sec[b] % 18 - sec[a] % 18) % 18) == np.where(d == 0, 1, 17))
+    for g in np.unique(group):
+        members = np.flatnonzero(group == g)
+        assert members.min() == g
+        if fit[g, 2] > 0:
+            assert fit[g, 6] == members.size and fit[g, 5] == cnt[members].sum()
+    # the merged groups' refitted radius against the MC particle's
+    R_true = cl.tracks["pt"] / (0.299792458e-2 * 0.5)
+    roots = np.unique(group[a])
+    rel = np.abs(fit[roots, 2] - R_true[labels[roots]]) / R_true[labels[roots]]
+    assert np.median(rel) < 0.01
+
+
+def test_errors():
+    from paper_1910_12214_b300 import synth, tpc
+    cl = synth.make_config1(seed=33)
+    t = tpc.Tracker(device=0)
+    t.load(cl)
+    with pytest.raises(tpc.TpcError) as e:
+        t.merge_tracks()
+    assert e.value.status == 2
+    t.track()
+    ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids"])
+    tf, ti, ids = oracle.merge_tracks(ref)
+    rec = to_records(tf, ti)
+    rec["item"][0] = 5  # out of range and out of order
+    with pytest.raises(tpc.TpcError) as e:
+        t.merge_tracks(rec, ids)
+    assert e.value.status == 7
+    t.close()
+    # a batch without item tables cannot be merged
+    cl2 = synth.make_config1(seed=34)
+    cl2.item_sector = None
+    cl2.item_event = None
+    with tpc.Tracker(device=0) as t2:
+        t2.load(cl2).track()
+        with pytest.raises(tpc.TpcError) as e:
+            t2.merge_tracks()
+        assert e.value.status == 2
