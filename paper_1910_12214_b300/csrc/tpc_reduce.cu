@@ -1103,6 +1103,8 @@ __global__ void k_mrg_geom(const __grid_constant__ MrgArgs a) {
     if (!range_ok || (t > 0 && trk[t - 1].item > T.item)) atomicOr(a.err, TPC_DERR_BAD_TRACK);
     const bool ok = fabsf(T.qpt) >= 1e-4f && range_ok;
     g[G_OK] = ok ? 1.0 : 0.0;
+    a.pre[t] = make_float4(ok ? T.tgl : __int_as_float(0x7fc00000), T.qpt, sqrtf(fmaxf(T.cov[14], 0.f)),
+                           T.qpt > 0.f ? 1.f : -1.f);
     if (!ok) continue;
     const int s = (int)a.item_sector[T.item];
     const double ang = (double)(s % 18) * MRG_WEDGE, ca = cos(ang), sa = sin(ang);
@@ -1175,8 +1177,15 @@ __global__ void k_mrg_best(const __grid_constant__ MrgArgs a) {
       const int nb = ok ? a.nb_item[2 * trk[t].item + d] : -1;
       double bs = 0.0;
       long long bi = -1;
+      const float4 pa = a.pre[t];
       if (nb >= 0)
         for (long long b = a.item_first[nb] + lane; b < a.item_first[nb + 1]; b += 32) {
+          // FP32 prefilter with margins wider than any FP32 rounding of the FP64 tests
+          // (a NaN tan lambda marks a track without a circle: every comparison fails)
+          const float4 pb = a.pre[b];
+          if (!(fabsf(pa.x - pb.x) <= 0.0201f) || pa.w != pb.w) continue;
+          const float dq = pa.y - pb.y, sq = pa.z * pa.z + pb.z * pb.z;
+          if (!(dq * dq <= 16.2f * sq + 1e-28f)) continue;
           const double* B = a.geo + G_N * b;
           if (B[G_OK] == 0.0 || B[G_SIGN] != A[G_SIGN]) continue;
           double sc;
@@ -1237,6 +1246,8 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
                                                   const __grid_constant__ DevParams par) {
   __shared__ int mem[4][40];
   __shared__ double rot[4][40][2];  // cos and sin of each member's sector angle
+  constexpr int STAGE = 384;        // clusters of a group kept in shared memory (larger groups re-gather)
+  __shared__ double sX[4][STAGE], sY[4][STAGE], sZ[4][STAGE];
   const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -1272,7 +1283,10 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
       rot[w][m][1] = sin(ang);
     }
     __syncwarp();
-    auto cluster_at = [&](int m, long long j, double* X, double* Y, double* Z) {
+    long long n_all = 0;
+    for (int m = 0; m < nm; ++m) n_all += trk[mem[w][m]].n_clusters;
+    const bool staged = n_all <= STAGE;
+    auto gather = [&](int m, long long j, double* X, double* Y, double* Z) {
       const tpc_track_t& T = trk[mem[w][m]];
       const double ca = rot[w][m][0], sa = rot[w][m][1];
       uint32_t c = a.ids[T.first_cluster + j];
@@ -1287,6 +1301,25 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
       *Y = lx * sa + ly * ca;
       *Z = a.N > 0 ? a.z[c] : 0.0;
     };
+    if (staged) {
+      long long base = 0;
+      for (int m = 0; m < nm; ++m) {
+        const long long cnt = trk[mem[w][m]].n_clusters;
+        for (long long j = lane; j < cnt; j += 32) gather(m, j, &sX[w][base + j], &sY[w][base + j], &sZ[w][base + j]);
+        base += cnt;
+      }
+      __syncwarp();
+    }
+    // cluster j of member m (p = its position over the group): from shared memory or gathered again
+    auto cluster_at = [&](int m, long long j, long long p, double* X, double* Y, double* Z) {
+      if (staged) {
+        *X = sX[w][p];
+        *Y = sY[w][p];
+        *Z = sZ[w][p];
+      } else {
+        gather(m, j, X, Y, Z);
+      }
+    };
     // pass 1: mean, count and the innermost cluster (smallest radius, first in order on ties)
     double sx = 0, sy = 0, rmin = 1e300, xin = 0, yin = 0;
     long long pin = -1, n = 0, pos = 0;
@@ -1294,7 +1327,7 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
       const long long cnt = trk[mem[w][m]].n_clusters;
       for (long long j = lane; j < cnt; j += 32) {
         double X, Y, Z;
-        cluster_at(m, j, &X, &Y, &Z);
+        cluster_at(m, j, pos + j, &X, &Y, &Z);
         sx += X;
         sy += Y;
         const double rr = X * X + Y * Y;  // ordering by the squared radius
@@ -1325,11 +1358,12 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
     const double mx = sx / (double)n, my = sy / (double)n;
     // pass 2: centred moments
     double suu = 0, suv = 0, svv = 0, su3 = 0, sv3 = 0, sw = 0;
+    pos = 0;
     for (int m = 0; m < nm; ++m) {
       const long long cnt = trk[mem[w][m]].n_clusters;
       for (long long j = lane; j < cnt; j += 32) {
         double X, Y, Z;
-        cluster_at(m, j, &X, &Y, &Z);
+        cluster_at(m, j, pos + j, &X, &Y, &Z);
         const double u = X - mx, v = Y - my, ww = u * u + v * v;
         suu += u * u;
         suv += u * v;
@@ -1338,6 +1372,7 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
         sv3 += v * ww;
         sw += ww;
       }
+      pos += cnt;
     }
     suu = warp_sum(suu);
     suv = warp_sum(suv);
@@ -1352,11 +1387,12 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
     const double R = sqrt(0.25 * (D * D + E * E) - F);
     // pass 3: z against the arc from the innermost cluster
     double ss = 0, sz = 0, sss = 0, ssz = 0;
+    pos = 0;
     for (int m = 0; m < nm; ++m) {
       const long long cnt = trk[mem[w][m]].n_clusters;
       for (long long j = lane; j < cnt; j += 32) {
         double X, Y, Z;
-        cluster_at(m, j, &X, &Y, &Z);
+        cluster_at(m, j, pos + j, &X, &Y, &Z);
         const double c = hypot(X - xin, Y - yin);
         const double s = c * (1.0 + c * c / (24.0 * R * R));
         ss += s;
@@ -1364,6 +1400,7 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
         sss += s * s;
         ssz += s * Z;
       }
+      pos += cnt;
     }
     ss = warp_sum(ss);
     sz = warp_sum(sz);
