@@ -36,6 +36,17 @@
 //    fit of x^2 + y^2 + D x + E y + F (coordinates centred on their mean), then
 //    z = z0 + tan(lambda) s by least squares, s the chord-series arc from the
 //    innermost cluster (smallest radius);
+//  - looper legs: a helix with radius R < 250 cm can turn inside a sector and
+//    comes back inward; the tracker fits the returning (secondary) leg as a
+//    track of opposite q/pT and tan(lambda) sign on the same circle (the
+//    centre does not change when the direction is reversed).  Candidates:
+//    tracks with R < 250 cm of the same event and side, opposite signs of q/pT
+//    and of tan(lambda); compatible if (|q/pT_A| - |q/pT_B|)^2 <= 16 (var_A +
+//    var_B), the centres lie within 1 cm + 3 kB sqrt(var_A + var_B) R^2, and
+//    |tan(lambda)_A + tan(lambda)_B| <= 0.02; score = chi2 / 16 + centre
+//    distance / its limit + |sum of tan(lambda)| / 0.02; mutual best pairs are
+//    the two legs of one looper; the leg whose reference z is farther from 0
+//    (the vertex of an event) is the secondary one (ties: the larger index);
 //  - ambiguous: a compatibility quantity within 1e-6 (relative) of its bound,
 //    or best and second-best scores within 1e-9: the test then checks only
 //    validity for that track.
@@ -44,6 +55,7 @@
 #include <cstdint>
 #include <map>
 #include <tuple>
+#include <utility>
 #include <vector>
 
 namespace {
@@ -81,11 +93,13 @@ bool compatible(const G& a, const G& b, double kB, double* score, bool* near) {
 }  // namespace
 
 // trk_f: [n][7] x_ref, y, z, sinphi, tanlambda, q/pT, variance of q/pT;
-// trk_i: [n][3] item, first, count into ids.
+// trk_i: [n][3] item, first, count into ids.  partner (nullable): the other
+// leg of a looper, -1 none; leg (nullable): 1 for a secondary leg, else 0.
 extern "C" int64_t orc_merge(int n_rows, double x_min, double x_max, double bz, int64_t n, const float* y,
                              const float* z, const int32_t* row, int64_t n_items, const uint32_t* item_sector,
                              const uint32_t* item_event, int64_t n_trk, const float* trk_f, const int64_t* trk_i,
-                             const uint32_t* ids, int32_t* link, int32_t* group, uint8_t* amb, double* fit) {
+                             const uint32_t* ids, int32_t* link, int32_t* group, uint8_t* amb, double* fit,
+                             int32_t* partner, uint8_t* leg) {
   const double kB = 0.299792458e-2 * bz;
   const double wedge = 2.0 * M_PI / 18.0;
   std::vector<double> xr(n_rows);
@@ -173,6 +187,51 @@ extern "C" int64_t orc_merge(int n_rows, double x_min, double x_max, double bz, 
       }
   }
   for (int64_t t = 0; t < n_trk; ++t) group[t] = (int32_t)lab[t];
+  // looper legs
+  {
+    std::map<std::pair<int64_t, int>, std::vector<int64_t>> loopers;  // (event, side) -> tracks with R < 250 cm
+    for (int64_t t = 0; t < n_trk; ++t)
+      if (g[t].ok && g[t].R < 250.0) loopers[std::make_pair(g[t].event, g[t].side)].push_back(t);
+    std::vector<int64_t> lbest(n_trk, -1);
+    for (auto& kv : loopers) {
+      const auto& v = kv.second;
+      for (int64_t a : v) {
+        double bs = 0, second = 1e300;
+        int64_t bi = -1;
+        for (int64_t b : v) {
+          if (b == a || g[b].sign == g[a].sign || (g[a].tgl > 0) == (g[b].tgl > 0)) continue;
+          const double qa = std::fabs(g[a].qpt), qb = std::fabs(g[b].qpt);
+          const double chi2 = (qa - qb) * (qa - qb) / std::max(g[a].vq + g[b].vq, 1e-30);
+          const double Rm = std::max(g[a].R, g[b].R);
+          const double dlim = 1.0 + 3.0 * kB * std::sqrt(g[a].vq + g[b].vq) * Rm * Rm;
+          const double dc = std::hypot(g[a].xc - g[b].xc, g[a].yc - g[b].yc);
+          const double st = std::fabs(g[a].tgl + g[b].tgl);
+          auto close = [](double x, double lim) { return std::fabs(x - lim) <= 1e-6 * std::max(1.0, lim); };
+          if (close(chi2, 16.0) || close(dc, dlim) || close(st, 0.02)) amb[a] = 1;
+          if (!(chi2 <= 16.0 && dc <= dlim && st <= 0.02)) continue;
+          const double sc = chi2 / 16.0 + dc / dlim + st / 0.02;
+          if (bi < 0 || sc < bs) {
+            if (bi >= 0) second = std::min(second, bs);
+            bs = sc;
+            bi = b;
+          } else {
+            second = std::min(second, sc);
+          }
+        }
+        if (bi >= 0 && second - bs <= 1e-9 * std::max(1.0, bs)) amb[a] = 1;
+        lbest[a] = bi;
+      }
+    }
+    for (int64_t t = 0; t < n_trk; ++t) {
+      const int64_t p = lbest[t];
+      const bool mutual = p >= 0 && lbest[p] == t;
+      if (partner) partner[t] = mutual ? (int32_t)p : -1;
+      if (leg) {
+        const double zt = std::fabs(g[t].z), zp = mutual ? std::fabs(g[p].z) : 0.0;
+        leg[t] = (mutual && (zt > zp || (zt == zp && t > p))) ? 1 : 0;
+      }
+    }
+  }
   // refit of every group: fit[root] = (xc, yc, R, tgl, z0, n_clusters, n_tracks)
   std::vector<std::vector<int64_t>> members(n_trk);
   for (int64_t t = 0; t < n_trk; ++t) members[lab[t]].push_back(t);

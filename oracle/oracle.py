@@ -107,7 +107,7 @@ def _load():
         lib.orc_predict.argtypes = [C.c_void_p, C.c_float, C.c_float, C.c_void_p, C.c_void_p]
         lib.orc_merge.restype = C.c_int64
         lib.orc_merge.argtypes = ([C.c_int, C.c_double, C.c_double, C.c_double, C.c_int64] + [C.c_void_p] * 3 +
-                                  [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64] + [C.c_void_p] * 7)
+                                  [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64] + [C.c_void_p] * 9)
         lib.orc_chi2.restype = C.c_double
         lib.orc_chi2.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         _lib = lib
@@ -419,11 +419,12 @@ def predict_codes(state6, bz, X):
     return int(py.value), int(pz.value)
 
 
-def merge(cl, trk_f, trk_i, ids, bz=0.5, n_rows=152, x_min=85.0, x_max=246.0):
+def merge(cl, trk_f, trk_i, ids, bz=0.5, n_rows=152, x_min=85.0, x_max=246.0, legs=False):
     """Sector-track merger of tracks trk_f [n,7] (x_ref, y, z, sinphi, tanlambda,
     q/pT, variance of q/pT), trk_i [n,3] (item, first, count): (link [n,2] (partner in sector k+1, k-1; -1 none),
     group [n] (smallest index of the group), ambiguous [n], fit [n,7] (per group
-    root: centre x, y, radius, tan lambda, z0, clusters, tracks))."""
+    root: centre x, y, radius, tan lambda, z0, clusters, tracks)); with legs=True
+    also (partner [n] (the other leg of a looper, -1), leg [n] (1 secondary))."""
     lib = _load()
     y = np.ascontiguousarray(cl.y, np.float32)
     z = np.ascontiguousarray(cl.z, np.float32)
@@ -438,10 +439,14 @@ def merge(cl, trk_f, trk_i, ids, bz=0.5, n_rows=152, x_min=85.0, x_max=246.0):
     group = np.empty(n, np.int32)
     amb = np.empty(n, np.uint8)
     fit = np.empty((n, 7), np.float64)
+    partner = np.empty(n, np.int32)
+    leg = np.empty(n, np.uint8)
     st = lib.orc_merge(n_rows, x_min, x_max, bz, y.shape[0], _p(y), _p(z), _p(row), sec.shape[0], _p(sec), _p(ev),
-                       n, _p(tf), _p(ti), _p(ids), _p(link), _p(group), _p(amb), _p(fit))
+                       n, _p(tf), _p(ti), _p(ids), _p(link), _p(group), _p(amb), _p(fit), _p(partner), _p(leg))
     if st < 0:
         raise ValueError("bad input")
+    if legs:
+        return link, group, amb, fit, partner, leg
     return link, group, amb, fit
 
 

@@ -56,6 +56,7 @@ class Clusters:
     item_core: Optional[np.ndarray] = None  # int32 [n_items, 2]: slice core [lo, hi) in z quanta
     mc: Optional[np.ndarray] = None         # int32 [n]: MC track index, -1 = noise
     truth: Optional[np.ndarray] = None      # float64 [n, 5]: (y, z, sinphi, tanlambda, q/pT) at the row
+    leg: Optional[np.ndarray] = None        # int8 [n]: helix leg of the cluster (0 first, 1 second), -1 noise
     tracks: Optional[dict] = None           # per MC track arrays
     n_physical: int = 0                     # clusters before slice duplication
 
@@ -92,14 +93,17 @@ def draw_tracks(rng: np.random.Generator, n: int, pt_range=(0.1, 10.0), eta_max=
     return dict(pt=pt, tgl=np.sinh(eta), q=q, phi0=phi0, z0=np.zeros(n), t0=np.zeros(n))
 
 
-def _crossings(tr: dict, geom: Geometry, single_sector: bool, chunk: int = 4096):
+def _crossings(tr: dict, geom: Geometry, single_sector: bool, chunk: int = 4096, second_leg: bool = False):
     """Exact first-leg crossings of each helix with every pad-row plane it meets.
 
-    Returns per-crossing arrays: track index, sector, row, y_loc, z, sin(phi_loc).
-    A crossing is kept if the track moves outward in local x there (cos phi_loc > 0),
-    |sin phi_loc| < 0.999, it lies on the first leg (arc length <= pi*R from the
-    vertex), inside the wedge |y| <= x tan(half angle) and inside |z| <= z_max on the
-    sector's side.  At most one crossing exists per (track, sector, row).
+    Returns per-crossing arrays: track index, sector, row, y_loc, z, sin(phi_loc)
+    and the leg (0 first, 1 second).  A crossing is kept if the track moves outward
+    in local x there (cos phi_loc > 0), |sin phi_loc| < 0.999, it lies on the first
+    leg (arc length <= pi*R from the vertex), inside the wedge |y| <= x tan(half
+    angle) and inside |z| <= z_max on the sector's side.  At most one crossing
+    exists per (track, sector, row).  second_leg: also the crossings of the second
+    half-turn (pi*R < arc length <= 2*pi*R), where a helix that turns inside the
+    chamber comes back inward (cos phi_loc < 0): the looper's secondary leg.
     """
     kB = C_LIGHT_CM * geom.bz_tesla
     xr = geom.row_x()
@@ -144,8 +148,37 @@ def _crossings(tr: dict, geom: Geometry, single_sector: bool, chunk: int = 4096)
         else:
             sector = cand
         ti, ri, ci = np.nonzero(ok)
-        out.append((ti + c0, sector[ti, ri, ci], ri, y[ti, ri, ci], z[ti, ri, ci], s[ti, ri, ci]))
-    cat = [np.concatenate([o[i] for o in out]) if out else np.zeros(0) for i in range(6)]
+        out.append((ti + c0, sector[ti, ri, ci], ri, y[ti, ri, ci], z[ti, ri, ci], s[ti, ri, ci],
+                    np.zeros(ti.shape[0], np.int64)))
+        if second_leg:
+            # the inward branch of the second half-turn: at radius r the helix is at azimuth
+            # phi0 - q (pi - asin(r / 2R)), moving in direction pi - phil (local), on the
+            # other side of the centre
+            if single_sector:
+                cand2 = cand
+            else:
+                phipos2 = phi0[:, None] - q[:, None] * (math.pi - np.arcsin(ratio))
+                k2 = np.floor(phipos2 / wedge + 0.5).astype(np.int64)
+                cand2 = (k2[:, :, None] + np.array([-1, 0, 1])[None, None, :]) % n_side
+            alpha2 = cand2 * wedge
+            ca2, sa2 = np.cos(alpha2), np.sin(alpha2)
+            xc2 = Xc[:, None, None] * ca2 + Yc[:, None, None] * sa2
+            yc2 = -Xc[:, None, None] * sa2 + Yc[:, None, None] * ca2
+            s2 = (xc2 - xr[None, :, None]) / qR
+            ok2 = np.abs(s2) < 0.999
+            s2 = np.where(ok2, s2, 0.0)
+            phil2 = math.pi - np.arcsin(s2)
+            ell2 = R[:, None, None] * np.mod(q[:, None, None] * (phi0[:, None, None] - alpha2 - phil2), 2.0 * math.pi)
+            ok2 &= (ell2 > math.pi * R[:, None, None]) & (ell2 <= 2.0 * math.pi * R[:, None, None])
+            y2 = yc2 - qR * np.sqrt(1.0 - s2 * s2)
+            ok2 &= np.abs(y2) <= xr[None, :, None] * tan_h
+            z2 = z0[:, None, None] + tgl[:, None, None] * ell2
+            ok2 &= np.abs(z2) <= geom.z_max
+            sector2 = cand2 if single_sector else np.where(z2 < 0.0, cand2 + n_side, cand2)
+            t2, r2, c2 = np.nonzero(ok2)
+            out.append((t2 + c0, sector2[t2, r2, c2], r2, y2[t2, r2, c2], z2[t2, r2, c2], s2[t2, r2, c2],
+                        np.ones(t2.shape[0], np.int64)))
+    cat = [np.concatenate([o[i] for o in out]) if out else np.zeros(0) for i in range(7)]
     return cat
 
 
@@ -171,7 +204,7 @@ def _noise(rng, n_noise, geom: Geometry, single_sector: bool, z_lo=None, z_hi=No
 def make_event(seed: int, n_tracks: int, *, geom: Geometry = None, single_sector: bool = False,
                sigma_y: float = 0.1, sigma_z: float = 0.1, noise_frac: float = 0.05,
                pt_range=(0.1, 10.0), eta_max: float = 0.9, event_id: int = 0,
-               shuffle: bool = True) -> Clusters:
+               shuffle: bool = True, second_leg: bool = False) -> Clusters:
     """One collision at the origin (config-1 and config-2 shapes).
 
     single_sector: one 152-row wedge (sector 0) spanning both z sides; each helix's
@@ -187,18 +220,20 @@ def make_event(seed: int, n_tracks: int, *, geom: Geometry = None, single_sector
         r_ref = np.minimum(165.0, (geom.x_min + 2.0 * R) / 2.0)
         target = np.radians(rng.uniform(-geom.half_angle_deg, geom.half_angle_deg, n_tracks))
         tr["phi0"] = target + tr["q"] * np.arcsin(np.minimum(r_ref / (2.0 * R), 1.0))
-    return _assemble([tr], [event_id], rng, geom, single_sector, sigma_y, sigma_z, noise_frac, shuffle)
+    return _assemble([tr], [event_id], rng, geom, single_sector, sigma_y, sigma_z, noise_frac, shuffle,
+                     second_leg=second_leg)
 
 
 def _assemble(track_sets, event_ids, rng, geom, single_sector, sigma_y, sigma_z, noise_frac, shuffle,
-              drift=None):
+              drift=None, second_leg=False):
     n_sec = 1 if single_sector else int(round(360.0 / geom.half_angle_deg))
-    xs, ys, zs, rows, secs, evs, mcs, truths = [], [], [], [], [], [], [], []
+    xs, ys, zs, rows, secs, evs, mcs, truths, legs = [], [], [], [], [], [], [], [], []
     base = 0
     all_tracks = {k: [] for k in ("pt", "tgl", "q", "phi0", "z0", "t0")}
     for tr, ev in zip(track_sets, event_ids):
-        ti, sec, row, y, z, s = _crossings(tr, geom, single_sector)
+        ti, sec, row, y, z, s, lg = _crossings(tr, geom, single_sector, second_leg=second_leg)
         ti = ti.astype(np.int64)
+        lg = lg.astype(np.int64)
         row = row.astype(np.int64)
         sec = sec.astype(np.int64)
         n_sig = ti.shape[0]
@@ -225,6 +260,7 @@ def _assemble(track_sets, event_ids, rng, geom, single_sector, sigma_y, sigma_z,
             zm = np.concatenate([zm, nz])
             truth = np.concatenate([truth, np.full((n_noise, 5), np.nan)])
             ti = np.concatenate([ti, np.full(n_noise, -1 - base)])
+            lg = np.concatenate([lg, np.full(n_noise, -1)])
         xs.append(geom.row_x()[row])
         ys.append(ym)
         zs.append(zm)
@@ -233,6 +269,7 @@ def _assemble(track_sets, event_ids, rng, geom, single_sector, sigma_y, sigma_z,
         evs.append(np.full(sec.shape[0], ev, dtype=np.int64))
         mcs.append(np.where(ti >= 0, ti + base, -1))
         truths.append(truth)
+        legs.append(lg)
         for k in all_tracks:
             all_tracks[k].append(tr[k])
         base += tr["pt"].shape[0]
@@ -244,6 +281,7 @@ def _assemble(track_sets, event_ids, rng, geom, single_sector, sigma_y, sigma_z,
     ev = np.concatenate(evs)
     mc = np.concatenate(mcs)
     truth = np.concatenate(truths)
+    leg = np.concatenate(legs)
     # group by item = (event, sector); shuffle inside each item
     ev_ids = np.asarray(event_ids, dtype=np.int64)
     ev_rank = np.searchsorted(np.sort(ev_ids), ev)
@@ -260,7 +298,7 @@ def _assemble(track_sets, event_ids, rng, geom, single_sector, sigma_y, sigma_z,
         row=row[order].astype(np.int32), item_off=item_off,
         item_sector=np.tile(np.arange(n_sec, dtype=np.uint32), len(event_ids)),
         item_event=np.repeat(sorted_ev.astype(np.uint32), n_sec),
-        mc=mc[order].astype(np.int32), truth=truth[order],
+        mc=mc[order].astype(np.int32), truth=truth[order], leg=leg[order].astype(np.int8),
         tracks={k: np.concatenate(v) for k, v in all_tracks.items()}, n_physical=int(x.shape[0]))
 
 

@@ -143,3 +143,64 @@ def test_link_and_group_structure(event_merge):
         assert members.min() == g
         assert fit[g, 6] == members.size
         assert fit[g, 5] == ti[members, 2].sum()
+
+
+def test_hand_built_looper_legs_are_paired():
+    """One looper (R = 100 cm through the beam axis, centre at azimuth 60 deg):
+    its outgoing leg seen in sector 1 and its returning leg in sector 5, the
+    latter fitted in the reversed direction (opposite q/pT and tan lambda
+    signs) and farther along the helix (larger |z|).  They pair, the returning
+    one is the secondary leg; with tan lambda no longer opposite they do not."""
+    R = 100.0
+    xc, yc = R * math.cos(math.radians(60.0)), R * math.sin(math.radians(60.0))
+    prim = local_state(xc, yc, R, -1.0, 1, 150.0, 0.3, 20.0)
+    secd = local_state(xc, yc, R, 1.0, 5, 150.0, -0.3, 60.0)
+    assert abs(prim[1]) < 150 * math.tan(math.radians(10)) and abs(secd[1]) < 150 * math.tan(math.radians(10))
+
+    def run(tf):
+        cl = type("C", (), {})()
+        cl.y = np.array([prim[1]] * 3 + [secd[1]] * 3, np.float32)
+        cl.z = np.array([prim[2]] * 3 + [secd[2]] * 3, np.float32)
+        cl.row = np.array([60] * 6, np.int32)
+        cl.item_sector = np.array([1, 5], np.uint32)
+        cl.item_event = np.array([0, 0], np.uint32)
+        ti = np.array([[0, 0, 3], [1, 3, 3]])
+        return oracle.merge(cl, tf, ti, np.arange(6, dtype=np.uint32), legs=True)
+
+    tf = np.array([prim, secd], np.float32)
+    link, group, amb, fit, partner, leg = run(tf)
+    assert partner.tolist() == [1, 0] and leg.tolist() == [0, 1] and not amb.any()
+    assert (link == -1).all()  # sectors 1 and 5 are not neighbours: no sector link
+    tf2 = tf.copy()
+    tf2[1, 4] = -0.33
+    *_, partner, leg = run(tf2)
+    assert partner.tolist() == [-1, -1] and leg.tolist() == [0, 0]
+
+
+def test_looper_legs_on_an_event_with_secondary_legs():
+    """Helices that turn inside the chamber also leave their returning leg: the
+    pairs found are the two legs of one particle (>= 97%), most particles whose
+    two legs were both tracked get paired (>= 70%), and the secondary one is the
+    returning leg (>= 99%)."""
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_event(41, 6000, second_leg=True)
+    ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids"])
+    tf, ti, ids = oracle.merge_tracks(ref)
+    link, group, amb, fit, partner, leg = oracle.merge(cl, tf, ti, ids, legs=True)
+    lab = np.full(tf.shape[0], -1)
+    true_leg = np.full(tf.shape[0], -1)
+    for t, (_, f, n) in enumerate(ti):
+        m, lg = cl.mc[ids[f:f + n]], cl.leg[ids[f:f + n]]
+        if (m >= 0).any():
+            lab[t] = np.bincount(m[m >= 0]).argmax()
+            true_leg[t] = int(np.round(lg[m == lab[t]].mean()))
+    p = np.flatnonzero(partner >= 0)
+    assert np.all(partner[partner[p]] == p)
+    assert np.all(leg[p] + leg[partner[p]] == 1)
+    assert np.all(np.sign(tf[p, 5]) != np.sign(tf[partner[p], 5]))
+    assert p.size > 1000
+    assert (lab[p] == lab[partner[p]]).mean() > 0.97
+    both = [m for m in np.unique(lab[true_leg == 1]) if ((lab == m) & (true_leg == 0)).any()]
+    paired = np.mean([((lab == m) & (partner >= 0)).any() for m in both])
+    assert len(both) > 500 and paired > 0.70
+    assert (leg[p] == true_leg[p]).mean() > 0.99
