@@ -247,10 +247,24 @@ tpc_status tpc_compress(tpc_ctx* ctx, const tpc_cluster_charges* charges, const 
  *    x, y [cm, global frame], radius [cm], tan(lambda), z0 [cm] at the
  *    innermost cluster, clusters, tracks; zero elsewhere (and for straight
  *    tracks).
+ *  leg_partner, leg (both nullable; either one asks for the looper legs):
+ *    [n_tracks] the other leg of a looper (-1 none) and 1 for its secondary
+ *    leg, else 0.  A helix of radius R < 250 cm can turn inside a sector and
+ *    come back inward; the tracker fits the returning leg as a track of
+ *    opposite q/pT and tan(lambda) sign on the same circle.  Candidates: both
+ *    R < 250 cm, same event and side, opposite signs of q/pT and of
+ *    tan(lambda); compatible if (|q/pT_A| - |q/pT_B|)^2 <= 16 (var_A + var_B),
+ *    the circle centres lie within 1 cm + 3 kB sqrt(var_A + var_B) R^2 (R the
+ *    larger radius) and |tan(lambda)_A + tan(lambda)_B| <= 0.02; score =
+ *    chi2/16 + centre distance/limit + |sum|/0.02; mutual best pairs are the
+ *    two legs; the one whose reference z is farther from 0 (the vertex of an
+ *    event) is the secondary leg (ties: the larger index).  Feed `leg` to
+ *    tpc_cluster_masks to let strategy A remove the secondary legs.
  *  on_device: 1 = tracks, cluster_ids and the outputs are device pointers
  *    (the call still waits); 0 = host pointers. */
 tpc_status tpc_merge_tracks(tpc_ctx* ctx, const tpc_track_t* tracks, uint64_t n_tracks, const uint32_t* cluster_ids,
-                            uint64_t n_ids, int on_device, int32_t* link, int32_t* group, double* fit);
+                            uint64_t n_ids, int on_device, int32_t* link, int32_t* group, double* fit,
+                            int32_t* leg_partner, uint8_t* leg);
 
 #ifdef __cplusplus
 }

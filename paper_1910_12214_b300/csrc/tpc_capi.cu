@@ -1521,7 +1521,7 @@ extern "C" tpc_status tpc_compress(tpc_ctx* c, const tpc_cluster_charges* ch, co
 
 extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, uint64_t n_tracks,
                                        const uint32_t* cluster_ids, uint64_t n_ids, int on_device, int32_t* link,
-                                       int32_t* group, double* fit) {
+                                       int32_t* group, double* fit, int32_t* leg_partner, uint8_t* leg) {
   if (!c) return TPC_ERR_INVALID_ARG;
   if (!c->tracked) return fail(c, TPC_ERR_STATE, "tpc_merge_tracks before tpc_track");
   const int I = (int)c->h_item_sector.size();
@@ -1576,7 +1576,24 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
       nb[2 * i + 1] = find(c->h_item_event[i], side * 18 + (k + 17) % 18);
     }
   }
-  int* d_nb = (int*)cmp_buffer(c, 35, 8 * (size_t)I);
+  // items of the same event and side (for the looper legs)
+  const bool legs = leg_partner || leg;
+  std::vector<int> side_items(legs ? 18 * (size_t)I : 0, -1);
+  if (legs) {
+    std::vector<std::pair<uint64_t, int>> es(I);
+    for (int i = 0; i < I; ++i)
+      es[i] = {((uint64_t)c->h_item_event[i] << 1) | (c->h_item_sector[i] >= 18 ? 1u : 0u), i};
+    std::sort(es.begin(), es.end());
+    for (size_t lo = 0; lo < es.size();) {
+      size_t hi = lo;
+      while (hi < es.size() && es[hi].first == es[lo].first) ++hi;
+      for (size_t k = lo; k < hi; ++k)
+        for (size_t j = lo, m = 0; j < hi && m < 18; ++j, ++m) side_items[18 * (size_t)es[k].second + m] = es[j].second;
+      lo = hi;
+    }
+  }
+  int* d_nb = (int*)cmp_buffer(c, 35, 8 * (size_t)I + (legs ? 72 * (size_t)I : 0));
+  int* d_lbest = (int*)cmp_buffer(c, 40, 4 * (size_t)std::max(nt, 1ll));
   int* d_first = (int*)cmp_buffer(c, 36, 4 * (size_t)(I + 1));
   double* d_geo = (double*)cmp_buffer(c, 37, (8 * 12 + 16) * (size_t)std::max(nt, 1ll));
   int* d_best = (int*)cmp_buffer(c, 38, 8 * (size_t)std::max(nt, 1ll));
@@ -1584,9 +1601,13 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
   uint8_t* st = nullptr;
   const size_t o_link = 0, o_group = ((8 * (size_t)nt + 255) & ~size_t(255)),
                o_fit = o_group + ((4 * (size_t)nt + 255) & ~size_t(255));
-  if (!on_device) st = (uint8_t*)cmp_buffer(c, 39, o_fit + 56 * (size_t)std::max(nt, 1ll));
-  if (!d_nb || !d_first || !d_geo || !d_best || (!on_device && !st)) return fail(c, TPC_ERR_OOM, "merge buffers");
-  if ((e = cudaMemcpyAsync(d_nb, nb.data(), 8 * (size_t)I, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+  const size_t o_part = o_fit + 56 * (size_t)std::max(nt, 1ll), o_leg = o_part + 4 * (size_t)std::max(nt, 1ll);
+  if (!on_device) st = (uint8_t*)cmp_buffer(c, 39, o_leg + (size_t)std::max(nt, 1ll));
+  if (!d_nb || !d_first || !d_geo || !d_best || !d_lbest || (!on_device && !st))
+    return fail(c, TPC_ERR_OOM, "merge buffers");
+  if ((e = cudaMemcpyAsync(d_nb, nb.data(), 8 * (size_t)I, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+      (legs && (e = cudaMemcpyAsync(d_nb + 2 * I, side_items.data(), 72 * (size_t)I, cudaMemcpyHostToDevice,
+                                    c->stream)) != cudaSuccess))
     return cuda_fail(c, e, "neighbour table");
   unsigned int err0 = 0;
   if ((e = cudaMemcpyAsync(&err0, c->b.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
@@ -1612,12 +1633,25 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
   a.link = on_device ? link : (int*)(st + o_link);
   a.group = on_device ? group : (int*)(st + o_group);
   a.fit = on_device ? fit : (double*)(st + o_fit);
+  a.side_items = legs ? d_nb + 2 * I : nullptr;
+  a.lbest = d_lbest;
+  // the partner array is needed whenever legs are asked for (the leg flags derive from it)
+  a.partner = !legs ? nullptr : (on_device && leg_partner ? leg_partner : (int*)(st ? st + o_part : nullptr));
+  a.leg = !leg ? nullptr : (on_device ? leg : st + o_leg);
+  if (legs && !a.partner) {  // device call without a partner array: a scratch one
+    a.partner = (int*)cmp_buffer(c, 41, 4 * (size_t)std::max(nt, 1ll));
+    if (!a.partner) return fail(c, TPC_ERR_OOM, "merge buffers");
+  }
   a.err = c->b.err;
   if ((e = launch_merge(a, c->par, c->lc.num_sms, c->stream)) != cudaSuccess) return cuda_fail(c, e, "merge");
   if (!on_device && nt &&
       ((e = cudaMemcpyAsync(link, a.link, 8 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
        (e = cudaMemcpyAsync(group, a.group, 4 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
-       (e = cudaMemcpyAsync(fit, a.fit, 56 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess))
+       (e = cudaMemcpyAsync(fit, a.fit, 56 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+       (leg_partner &&
+        (e = cudaMemcpyAsync(leg_partner, a.partner, 4 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) !=
+            cudaSuccess) ||
+       (leg && (e = cudaMemcpyAsync(leg, a.leg, (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)))
     return cuda_fail(c, e, "merge download");
   unsigned int err = 0;
   if ((e = cudaMemcpyAsync(&err, c->b.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||

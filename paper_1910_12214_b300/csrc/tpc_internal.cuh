@@ -280,6 +280,10 @@ struct MrgArgs {
   int* link;                  // [n_trk][2] output
   int* group;                 // [n_trk] output
   double* fit;                // [n_trk][7] output (group roots)
+  const int* side_items;      // [I][18] the items of the same event and side (-1 padded), null: no legs
+  int* lbest;                 // [n_trk] best other-leg candidate
+  int* partner;               // [n_trk] output: the other leg of a looper, -1 none
+  uint8_t* leg;               // [n_trk] output: 1 for a secondary leg
   unsigned int* err;
 };
 cudaError_t launch_merge(const MrgArgs& a, const DevParams& par, int num_sms, cudaStream_t s);

@@ -1420,6 +1420,72 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
   }
 }
 
+// Looper legs, one warp per track that can turn inside a sector (R < 250 cm):
+// the best candidate of opposite q/pT and tan(lambda) sign on the same circle
+// among the tracks of the same event and side.
+__global__ void k_mrg_legs(const __grid_constant__ MrgArgs a) {
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const int lane = threadIdx.x & 31;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_trk; t += nw) {
+    const double* A = a.geo + G_N * t;
+    double bs = 0.0;
+    long long bi = -1;
+    if (A[G_OK] != 0.0 && A[G_R] < 250.0) {
+      const float4 pa = a.pre[t];
+      const int* items = a.side_items + 18 * (long long)trk[t].item;
+      for (int k = 0; k < 18; ++k) {
+        const int it = items[k];
+        if (it < 0) continue;
+        for (long long b = a.item_first[it] + lane; b < a.item_first[it + 1]; b += 32) {
+          // FP32 prefilter (margins wider than FP32 rounding; R < 250 cm <=> |q/pT| > 2.668 c/GeV at 0.5 T)
+          const float4 pb = a.pre[b];
+          if (pb.w == pa.w || !((pa.x > 0.f) != (pb.x > 0.f)) || !(fabsf(pa.x + pb.x) <= 0.0201f)) continue;
+          const float dq = fabsf(pa.y) - fabsf(pb.y), sq = pa.z * pa.z + pb.z * pb.z;
+          if (!(dq * dq <= 16.2f * sq + 1e-28f)) continue;
+          const double* B = a.geo + G_N * b;
+          if (B[G_OK] == 0.0 || !(B[G_R] < 250.0)) continue;
+          const double qa = fabs(A[G_QPT]), qb = fabs(B[G_QPT]);
+          const double vs = fmax(A[G_VQ] + B[G_VQ], 1e-30);
+          const double chi2 = (qa - qb) * (qa - qb) / vs;
+          const double Rm = fmax(A[G_R], B[G_R]);
+          const double dlim = 1.0 + 3.0 * a.kB * sqrt(A[G_VQ] + B[G_VQ]) * Rm * Rm;
+          const double dc = hypot(A[G_XC] - B[G_XC], A[G_YC] - B[G_YC]);
+          const double st = fabs(A[G_TGL] + B[G_TGL]);
+          if (!(chi2 <= 16.0 && dc <= dlim && st <= 0.02)) continue;
+          const double sc = chi2 / 16.0 + dc / dlim + st / 0.02;
+          if (bi < 0 || sc < bs || (sc == bs && b < bi)) {
+            bs = sc;
+            bi = b;
+          }
+        }
+      }
+    }
+    for (int o = 16; o; o >>= 1) {  // smallest (score, index)
+      const double os = __shfl_xor_sync(0xffffffffu, bs, o);
+      const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (oi >= 0 && (bi < 0 || os < bs || (os == bs && oi < bi))) {
+        bs = os;
+        bi = oi;
+      }
+    }
+    if (lane == 0) a.lbest[t] = (int)bi;
+  }
+}
+
+__global__ void k_mrg_legs_final(const __grid_constant__ MrgArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride) {
+    const int p = a.lbest[t];
+    const bool mutual = p >= 0 && a.lbest[p] == (int)t;
+    a.partner[t] = mutual ? p : -1;
+    if (a.leg) {
+      const double zt = fabs(a.geo[G_N * t + G_Z]), zp = mutual ? fabs(a.geo[G_N * (long long)p + G_Z]) : 0.0;
+      a.leg[t] = (mutual && (zt > zp || (zt == zp && (int)t > p))) ? 1 : 0;
+    }
+  }
+}
+
 }  // namespace
 
 cudaError_t launch_merge(const MrgArgs& a, const DevParams& par, int num_sms, cudaStream_t s) {
@@ -1431,6 +1497,10 @@ cudaError_t launch_merge(const MrgArgs& a, const DevParams& par, int num_sms, cu
     k_mrg_link<<<g, 256, 0, s>>>(a);
     k_mrg_group<<<g, 256, 0, s>>>(a);
     k_mrg_fit<<<num_sms * 16, 128, 0, s>>>(a, par);
+    if (a.side_items) {
+      k_mrg_legs<<<g, 256, 0, s>>>(a);
+      k_mrg_legs_final<<<g, 256, 0, s>>>(a);
+    }
   }
   return cudaGetLastError();
 }

@@ -115,7 +115,7 @@ _sig = {
                           C.c_int),
     "tpc_compress": ([_P, C.POINTER(tpc_cluster_charges), _P, C.c_uint64, _P, C.c_uint64, C.c_int, _P, C.c_uint64,
                       C.POINTER(C.c_uint64)], C.c_int),
-    "tpc_merge_tracks": ([_P, _P, C.c_uint64, _P, C.c_uint64, C.c_int, _P, _P, _P], C.c_int),
+    "tpc_merge_tracks": ([_P, _P, C.c_uint64, _P, C.c_uint64, C.c_int, _P, _P, _P, _P, _P], C.c_int),
     "tpc_destroy": ([_P], None),
     "tpc_last_error": ([_P], C.c_char_p),
 }
@@ -445,9 +445,10 @@ class Tracker:
         self._check(st)
         return out[:int(size.value)]
 
-    def merge_tracks(self, tracks=None, ids=None, n_tracks=None):
+    def merge_tracks(self, tracks=None, ids=None, n_tracks=None, legs=False):
         """Sector-track merger (include/tpc_reduce.h): (link [n,2], group [n],
-        fit [n,7]) as numpy arrays.  tracks=None merges the last tpc_track()
+        fit [n,7]) as numpy arrays, with legs=True also (leg_partner [n], leg
+        [n]) of the looper legs.  tracks=None merges the last tpc_track()
         output (n_tracks = its count, read here if None); else TRACK_DTYPE
         records sorted by item and uint32 ids."""
         if tracks is None:
@@ -459,10 +460,13 @@ class Tracker:
         link = np.zeros((n, 2), np.int32)
         group = np.zeros(n, np.int32)
         fit = np.zeros((n, 7), np.float64)
+        partner = np.zeros(n, np.int32) if legs else None
+        leg = np.zeros(n, np.uint8) if legs else None
         ni = int(ids.shape[0]) if ids is not None else 0
-        self._check(_lib.tpc_merge_tracks(self._h, _ptr(tracks), n, _ptr(ids), ni, 0, _ptr(link) if n else None,
-                                          _ptr(group) if n else None, _ptr(fit) if n else None))
-        return link, group, fit
+        nz = lambda a: _ptr(a) if (a is not None and n) else None
+        self._check(_lib.tpc_merge_tracks(self._h, _ptr(tracks), n, _ptr(ids), ni, 0, nz(link), nz(group), nz(fit),
+                                          nz(partner), nz(leg)))
+        return (link, group, fit, partner, leg) if legs else (link, group, fit)
 
     def close(self):
         if getattr(self, "_h", None):

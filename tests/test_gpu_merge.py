@@ -115,3 +115,46 @@ def test_errors():
         with pytest.raises(tpc.TpcError) as e:
             t2.merge_tracks()
         assert e.value.status == 2
+
+
+def test_looper_legs_oracle_tracks():
+    """An event whose low-pT helices also leave their returning leg: with the
+    oracle tracker's tracks the leg pairs and secondary flags equal the
+    oracle's, except tracks it flags as rounding-sensitive."""
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_event(41, 6000, second_leg=True)
+    ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids"])
+    tf, ti, ids = oracle.merge_tracks(ref)
+    wl, wg, amb, wf, wp, wleg = oracle.merge(cl, tf, ti, ids, legs=True)
+    with tracked(cl) as t:
+        link, group, fit, partner, leg = t.merge_tracks(to_records(tf, ti), ids, legs=True)
+    touched = amb.astype(bool)
+    touched |= (wp >= 0) & touched[np.maximum(wp, 0)]
+    touched |= (partner >= 0) & touched[np.maximum(partner, 0)]
+    ok = ~touched
+    assert ok.mean() > 0.99 and (wp[ok] >= 0).sum() > 1000
+    assert np.array_equal(partner[ok], wp[ok])
+    assert np.array_equal(leg[ok], wleg[ok])
+    compare(cl, tf, ti, ids, link, group, fit)
+
+
+def test_secondary_legs_removed_by_strategy_a():
+    """The chain the paper describes: the merger marks the returning legs of
+    loopers, and strategy A removes their clusters (they are no longer
+    protected), while the primary legs stay protected."""
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_event(42, 6000, second_leg=True)
+    with tracked(cl) as t:
+        trk, tids = t.get_tracks()
+        link, group, fit, partner, leg = t.merge_tracks(legs=True)
+        m0, _ = t.cluster_masks(leg=None, n_tracks=trk.shape[0])
+        m1, _ = t.cluster_masks(leg=leg, n_tracks=trk.shape[0])
+    sec_cl = cl.leg == 1
+    prim_cl = cl.leg == 0
+    removed0 = (m0 & 4) != 0
+    removed1 = (m1 & 4) != 0
+    assert leg.sum() > 500
+    # clusters of returning legs: strategy A removes many more of them once the legs are known
+    assert removed1[sec_cl].mean() > removed0[sec_cl].mean() + 0.3
+    # clusters of first legs: essentially untouched
+    assert removed1[prim_cl].mean() < removed0[prim_cl].mean() + 0.02
