@@ -494,7 +494,7 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
 
 
 def bench_merge(cl, dev, stream, flush, tpc, torch, steps=10):
-    """Sector-track merger with refit over the 64 events' own tracks.  The call
+    """Sector-track merger with refit and looper legs over the 64 events' own tracks.  The call
     waits for its outputs (host arrays), so it is timed by the host clock and,
     on its stream, by CUDA events around it.  L2 flushed between calls."""
     with torch.cuda.stream(stream):
@@ -506,7 +506,7 @@ def bench_merge(cl, dev, stream, flush, tpc, torch, steps=10):
         t.track()
         n_trk = t.counts()[0]
         for _ in range(3):
-            link, group, fit = t.merge_tracks(n_tracks=n_trk)
+            link, group, fit, partner, leg = t.merge_tracks(n_tracks=n_trk, legs=True)
         wall, dev_ms = [], []
         for _ in range(steps):
             with torch.cuda.stream(stream):
@@ -516,7 +516,7 @@ def bench_merge(cl, dev, stream, flush, tpc, torch, steps=10):
             e1 = torch.cuda.Event(enable_timing=True)
             w0 = time.perf_counter()
             e0.record(stream)
-            link, group, fit = t.merge_tracks(n_tracks=n_trk)
+            link, group, fit, partner, leg = t.merge_tracks(n_tracks=n_trk, legs=True)
             e1.record(stream)
             wall.append(time.perf_counter() - w0)
             torch.cuda.synchronize()
@@ -524,7 +524,7 @@ def bench_merge(cl, dev, stream, flush, tpc, torch, steps=10):
     ms = 1e3 * float(np.median(wall))
     res.update(tracks=n_trk, tracks_per_s=n_trk / (ms * 1e-3), clusters_per_s=cl.n / (ms * 1e-3), ms=ms,
                device_ms=float(np.median(dev_ms)), links=int((link >= 0).sum() // 2),
-               groups=int(np.unique(group).size))
+               groups=int(np.unique(group).size), leg_pairs=int((partner >= 0).sum() // 2))
     del d
     torch.cuda.empty_cache()
     return res
