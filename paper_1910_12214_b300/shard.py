@@ -31,6 +31,17 @@ def lpt_partition(costs, world: int) -> list[np.ndarray]:
     return [np.flatnonzero(owner == r) for r in range(world)]
 
 
+def lpt_partition_grouped(costs, groups, world: int) -> list[np.ndarray]:
+    """As lpt_partition, with the items of one group (e.g. the sectors of one
+    event, which the sector-track merger joins) kept on one rank: the groups
+    are the units, each costing the sum of its items."""
+    costs = np.asarray(costs, dtype=np.int64)
+    groups = np.asarray(groups, dtype=np.int64)
+    uniq, inv = np.unique(groups, return_inverse=True)
+    per_rank = lpt_partition(np.bincount(inv, weights=costs, minlength=uniq.size).astype(np.int64), world)
+    return [np.flatnonzero(np.isin(inv, g)) for g in per_rank]
+
+
 def item_costs(cl) -> np.ndarray:
     """Cluster count of every item of a batch."""
     off = np.asarray(cl.item_off, dtype=np.int64)

@@ -36,6 +36,25 @@ def test_lpt_partition_known_case():
     assert parts[0].tolist() == [0, 1] and parts[1].tolist() == [2, 3, 4]
 
 
+def test_grouped_partition_keeps_events_together():
+    """The sectors of one event (which the sector-track merger joins) land on
+    one rank; every item exactly once; balanced by events."""
+    cl = synth.make_batched(seed=6, n_events=9, mult=(20, 400))
+    costs = shard.item_costs(cl)
+    for world in (1, 2, 4):
+        parts = shard.lpt_partition_grouped(costs, cl.item_event, world)
+        allv = np.concatenate(parts)
+        assert np.array_equal(np.sort(allv), np.arange(costs.size))
+        owner = np.empty(costs.size, int)
+        for r, p in enumerate(parts):
+            owner[p] = r
+        for ev in np.unique(cl.item_event):
+            assert np.unique(owner[cl.item_event == ev]).size == 1
+        ev_cost = {ev: costs[cl.item_event == ev].sum() for ev in np.unique(cl.item_event)}
+        loads = np.array([costs[p].sum() for p in parts])
+        assert loads.max() - loads.min() <= max(ev_cost.values())
+
+
 def test_take_items_slices_the_batch():
     cl = synth.make_batched(seed=4, n_events=3, mult=(5, 30))
     sub, index = shard.take_items(cl, np.arange(cl.n_items))
