@@ -27,6 +27,10 @@
 //    agree bit for bit: the helix of the tracker, with the arc length's
 //    asin(a)/a from two half-angle reductions and a series to a^8;
 //  - charges and sizes: their codes, in the order the positions are stored;
+//  - removal (Sec. 4, step 5: clusters not used for physics are discarded):
+//    with a keep mask, a cluster with keep = 0 is stored neither as an
+//    unattached cluster nor in its track (a track keeps its place with the
+//    clusters left; its row increments refer to its previous kept cluster);
 //  - every symbol stream is split into byte planes (as many as its largest
 //    value needs, at least one) and each plane is coded by rANS: 32-bit
 //    states, 16-bit renormalisation, frequencies scaled to 2^12, chunks of
@@ -287,8 +291,8 @@ extern "C" {
 int64_t orc_compress(int n_rows, double x_min, double x_max, float kB, int64_t n, const float* y, const float* z,
                      const int32_t* row, const float* q_tot, const float* q_max, const float* sigma_y,
                      const float* sigma_z, int64_t n_items, const int32_t* order, const int64_t* seg_off,
-                     int64_t n_trk, const float* trk_f, const int64_t* trk_i, const uint32_t* ids, uint8_t* out,
-                     int64_t cap) {
+                     int64_t n_trk, const float* trk_f, const int64_t* trk_i, const uint32_t* ids,
+                     const uint8_t* keep, uint8_t* out, int64_t cap) {
   std::vector<int16_t> cy(n);
   std::vector<int32_t> cz(n);
   std::vector<uint8_t> crow(n), csy(n), csz(n);
@@ -317,7 +321,7 @@ int64_t orc_compress(int n_rows, double x_min, double x_max, float kB, int64_t n
     int64_t prev_y = 0, prev_z = 0, cnt = 0;
     for (int64_t p = seg_off[g]; p < seg_off[g + 1]; ++p) {
       const uint32_t c = (uint32_t)order[p];
-      if (attached[c]) continue;
+      if (attached[c] || (keep && !keep[c])) continue;
       S[S_DY].push_back(zigzag((int64_t)cy[c] - prev_y));
       S[S_DZ].push_back(zigzag((int64_t)cz[c] - prev_z));
       prev_y = cy[c];
@@ -330,12 +334,15 @@ int64_t orc_compress(int n_rows, double x_min, double x_max, float kB, int64_t n
   }
   for (int64_t t = 0; t < n_trk; ++t) {
     const int64_t first = trk_i[3 * t + 1], cnt = trk_i[3 * t + 2];
-    S[S_TRK_N].push_back((uint64_t)cnt);
+    int64_t kept = 0;
+    for (int64_t j = 0; j < cnt; ++j) kept += (!keep || keep[ids[first + j]]) ? 1 : 0;
+    S[S_TRK_N].push_back((uint64_t)kept);
     int64_t prev_row = 0;
     for (int64_t j = 0; j < cnt; ++j) {
       const uint32_t c = ids[first + j];
       const int r = row[c];
       if (r < 0 || r >= n_rows) return -1;
+      if (keep && !keep[c]) continue;
       S[S_DROW].push_back(zigzag(r - prev_row));
       prev_row = r;
       int64_t py, pz;

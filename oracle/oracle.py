@@ -96,7 +96,7 @@ def _load():
                                                                                      C.c_float] + [C.c_void_p] * 3)
         lib.orc_compress.restype = C.c_int64
         lib.orc_compress.argtypes = ([C.c_int, C.c_double, C.c_double, C.c_float, C.c_int64] + [C.c_void_p] * 7 +
-                                     [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64] + [C.c_void_p] * 4 + [C.c_int64])
+                                     [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64] + [C.c_void_p] * 5 + [C.c_int64])
         lib.orc_decompress.restype = C.c_int64
         lib.orc_decompress.argtypes = [C.c_void_p, C.c_int64, C.c_int64] + [C.c_void_p] * 9
         lib.orc_code_stream.restype = C.c_int64
@@ -337,11 +337,12 @@ def oracle_tracks(ref):
     return tf, ti, ref["trk_ids"].astype(np.uint32)
 
 
-def compress(cl, props, order, seg_off, trk_f, trk_i, ids, bz=0.5, n_rows=152, x_min=85.0, x_max=246.0):
+def compress(cl, props, order, seg_off, trk_f, trk_i, ids, bz=0.5, n_rows=152, x_min=85.0, x_max=246.0, keep=None):
     """Compressed blob (bytes) of a tracked batch: entropy reduction and rANS
     coding.  props: charges and sizes (q_tot, q_max, sigma_y, sigma_z);
     order / seg_off: canonical order of the binned clusters and its (item, row)
-    segment offsets; tracks as for cluster_masks."""
+    segment offsets; tracks as for cluster_masks; keep: uint8 per cluster (0 =
+    removed, not stored) or None."""
     lib = _load()
     f32 = lambda a: np.ascontiguousarray(a, np.float32)
     y, z = f32(cl.y), f32(cl.z)
@@ -354,8 +355,9 @@ def compress(cl, props, order, seg_off, trk_f, trk_i, ids, bz=0.5, n_rows=152, x
     ids = np.ascontiguousarray(ids, np.uint32)
     kB = np.float32(0.299792458e-2 * np.float32(bz))
     n_items = (seg_off.shape[0] - 1) // n_rows
+    kp = None if keep is None else np.ascontiguousarray(keep, np.uint8)
     args = [n_rows, x_min, x_max, float(kB), y.shape[0], _p(y), _p(z), _p(row), *[_p(a) for a in pr], n_items,
-            _p(order), _p(seg_off), tf.shape[0], _p(tf), _p(ti), _p(ids)]
+            _p(order), _p(seg_off), tf.shape[0], _p(tf), _p(ti), _p(ids), _p(kp)]
     size = lib.orc_compress(*args, None, 0)
     if size < 0:
         raise ValueError("bad input")

@@ -130,3 +130,31 @@ def test_blob_round_trip_of_a_tracked_event():
     trk_of = np.repeat(np.arange(tf.shape[0]), ti[:, 2])
     assert np.array_equal(d["track"], np.concatenate([np.full(un.shape[0], -1), trk_of]))
     assert blob.size < 13 * seq.shape[0]
+
+
+def test_removed_clusters_are_not_stored():
+    """With a keep mask (Sec. 4, step 5) the blob decodes to exactly the kept
+    clusters: unattached ones in grid order, attached ones track by track with
+    their row increments across the removed ones; fewer clusters, fewer bytes."""
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_config1(seed=10)
+    props = synth.cluster_props(cl, seed=10)
+    ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids", "sorted_id", "rows"])
+    tf, ti, ids = oracle.oracle_tracks(ref)
+    order, seg = oracle.grid_order(ref)
+    keep = (np.random.default_rng(3).uniform(size=cl.n) < 0.5).astype(np.uint8)
+    full = oracle.compress(cl, props, order, seg, tf, ti, ids)
+    part = oracle.compress(cl, props, order, seg, tf, ti, ids, keep=keep)
+    d = oracle.decompress(part)
+    codes, _ = oracle.encode_clusters(props)
+    attached = np.zeros(cl.n, bool)
+    attached[ids] = True
+    un = order[~attached[order] & (keep[order] == 1)]
+    att = ids[keep[ids] == 1].astype(np.int64)
+    seq = np.concatenate([un, att])
+    for k in ("y", "z", "q_tot", "sigma_z"):
+        assert np.array_equal(d[k], codes[k][seq].astype(np.int32)), k
+    assert np.array_equal(d["row"], cl.row[seq])
+    trk_of = np.repeat(np.arange(tf.shape[0]), ti[:, 2])[keep[ids] == 1]
+    assert np.array_equal(d["track"][un.size:], trk_of)
+    assert part.size < 0.7 * full.size
