@@ -11,8 +11,9 @@ the same 64 events distorted by a space-charge field, corrected by the grid or
 by the trained BF16 network, the cluster codec (float to integer with dynamic
 precision) over the 64 events' clusters, the cluster removal masks
 (attachment, adjacency, protection, strategies A and B) of the 64 events,
-their compression (delta and track-model coding, rANS), and the merger of
-their sector tracks with refit.
+their compression (delta and track-model coding, rANS), the merger of their
+sector tracks with refit and looper legs, and the whole reduction chain (legs,
+masks, removal, compression) on an event whose low-pT helices loop.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
 bounded sample of the same workload instead.
@@ -77,6 +78,12 @@ def _gen_frame():
     return sl, fr.n
 
 
+def _gen_loopers():
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_event(42, 6000, second_leg=True)
+    return cl, synth.cluster_props(cl, seed=42)
+
+
 def _gen_grid():
     from paper_1910_12214_b300 import synth
     d = synth.make_distortion(seed=1, n_sectors=36)
@@ -90,6 +97,8 @@ def generate_forms(forms):
     jobs = {}
     ctx = mp.get_context("spawn")
     with ctx.Pool(3) as pool:
+        if "c10" in forms:
+            jobs["c10"] = pool.apply_async(_gen_loopers)
         if any(f in forms for f in ("c3", "c5", "c6", "c7", "c8", "c9")):
             jobs["c3"] = pool.apply_async(_gen_batched)
         if "c4" in forms:
@@ -308,7 +317,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
-    ap.add_argument("--forms", default="c3,c4,c5,c6,c7,c8,c9", help="extra forms at N=1: c3,...,c9 or none")
+    ap.add_argument("--forms", default="c3,c4,c5,c6,c7,c8,c9,c10", help="extra forms at N=1: c3,...,c10 or none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
@@ -490,6 +499,47 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
         res["compress_64_events"] = bench_compress(*gen["c8"], dev, stream, flush, tpc, torch)
     if "c9" in gen:
         res["merge_64_events"] = bench_merge(gen["c9"], dev, stream, flush, tpc, torch)
+    if "c10" in gen:
+        res["removal_chain_loopers"] = bench_removal_chain(*gen["c10"], dev, stream, tpc, torch)
+    return res
+
+
+def bench_removal_chain(cl, props, dev, stream, tpc, torch):
+    """The paper's data-reduction chain (Sec. 4) on one central event whose
+    low-pT helices also leave their returning legs: tracking, merger with
+    looper legs, masks with the legs, compression without removal and with
+    strategies A and B (the form of Fig. 6 on synthetic data)."""
+    with torch.cuda.stream(stream):
+        d = to_device(cl, dev)
+        ch = {k: torch.from_numpy(np.ascontiguousarray(props[k])).to(dev)
+              for k in ("q_tot", "q_max", "sigma_y", "sigma_z")}
+    stream.synchronize()
+    res = {"clusters": cl.n, "returning_leg_clusters": int((cl.leg == 1).sum())}
+    with tpc.Tracker(stream=stream) as t:
+        t.load(d, on_device=True)
+        for _ in range(2):  # the second pass is timed (the first allocates the buffers)
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            t.track()
+            n_trk = t.counts()[0]
+            link, group, fit, partner, leg = t.merge_tracks(n_tracks=n_trk, legs=True)
+            d_leg = torch.from_numpy(leg).to(dev)
+            m, _ = t.cluster_masks(on_device=True, with_owner=False, leg=d_leg, n_tracks=n_trk)
+            sizes = {}
+            for name, bit in (("none", 0), ("A", 4), ("B", 8)):
+                keep = None if bit == 0 else ((m & bit) == 0).to(torch.uint8)
+                sizes[name] = int(t.compress(ch, on_device=True, keep=keep).shape[0])
+            torch.cuda.synchronize()
+            wall = time.perf_counter() - w0
+    mh = m.cpu().numpy()
+    sec = cl.leg == 1
+    res.update(tracks=n_trk, leg_pairs=int((partner >= 0).sum() // 2), chain_wall_ms=1e3 * wall,
+               removed_by_a=float(((mh & 4) != 0).mean()), removed_by_b=float(((mh & 8) != 0).mean()),
+               returning_leg_removed_by_a=float(((mh & 4) != 0)[sec].mean()),
+               bytes_per_cluster={k: v / cl.n for k, v in sizes.items()},
+               reduction_vs_float_clusters={k: 28.0 * cl.n / v for k, v in sizes.items()})
+    del d, ch
+    torch.cuda.empty_cache()
     return res
 
 
@@ -560,6 +610,15 @@ def bench_compress(cl, props, dev, stream, flush, tpc, torch, steps=10):
                 if k.startswith("compress"):
                     ph.setdefault(k, []).append(v)
         size = int(b.shape[0])
+        # the form of the paper's Fig. 6 on synthetic data: stored volume without removal and with the
+        # removal of strategies A and B (masks of the tracker's own tracks)
+        m, _ = t.cluster_masks(on_device=True, with_owner=False)
+        strategies = {}
+        for name, bit in (("A", 4), ("B", 8)):
+            keep = ((m & bit) == 0).to(torch.uint8)
+            bs = t.compress(ch, on_device=True, out=out, keep=keep).shape[0]
+            strategies[name] = {"blob_bytes": int(bs), "bytes_per_cluster": bs / cl.n,
+                                "kept_clusters": int(keep.sum().item()), "reduction_vs_float_clusters": 28.0 * cl.n / bs}
     ms = 1e3 * float(np.median(wall))
     phases = {k: float(np.median(v)) for k, v in ph.items()}
     # algorithmic bytes of a call: every input read once (positions, row and charges 28 B, the
@@ -570,7 +629,7 @@ def bench_compress(cl, props, dev, stream, flush, tpc, torch, steps=10):
     achieved = algo / (dev_us * 1e-6) / 1e9
     res.update(clusters_per_s=cl.n / (ms * 1e-3), ms=ms, phase_us=phases, blob_bytes=size,
                bytes_per_cluster=size / cl.n, ratio_vs_integer_codes=13.0 * cl.n / size,
-               ratio_vs_float_clusters=28.0 * cl.n / size,
+               ratio_vs_float_clusters=28.0 * cl.n / size, removal=strategies,
                roofline={"bound": "hbm", "kernel": "all phases (device time)", "achieved": achieved, "peak": peak,
                          "unit": "GB/s", "frac": achieved / peak, "peak_kind": kind, "algo_bytes": algo})
     del d, ch

@@ -196,14 +196,20 @@ typedef struct {
  *    first_cluster, n_clusters, x_ref, y, z, snp, tgl, qpt used) with
  *    cluster_ids (indices of loaded clusters, innermost first per track).  A
  *    track out of range (item, cluster id or row) gives TPC_ERR_BAD_INPUT.
- *  on_device: 1 = charges, tracks, cluster_ids and out are device pointers;
- *    0 = host pointers.
+ *  keep (nullable): one byte per loaded cluster, 0 = removed (Sec. 4, step 5:
+ *    clusters not used for physics analysis are discarded), e.g. from the
+ *    TPC_MASK_REMOVE_A or _B bit of tpc_cluster_masks.  A removed cluster is
+ *    stored neither as unattached nor in its track; a track keeps its place
+ *    with the clusters left (its count may be 0), its row increments referring
+ *    to its previous stored cluster.
+ *  on_device: 1 = charges, tracks, cluster_ids, keep and out are device
+ *    pointers; 0 = host pointers.
  *  out, cap: the caller's buffer; *size receives the blob's size; if cap is
  *    smaller nothing is copied and TPC_ERR_CAPACITY is returned (out may be
  *    NULL with cap 0 to ask for the size).  The call waits for its stream. */
 tpc_status tpc_compress(tpc_ctx* ctx, const tpc_cluster_charges* charges, const tpc_track_t* tracks,
-                        uint64_t n_tracks, const uint32_t* cluster_ids, uint64_t n_ids, int on_device, uint8_t* out,
-                        uint64_t cap, uint64_t* size);
+                        uint64_t n_tracks, const uint32_t* cluster_ids, uint64_t n_ids, const uint8_t* keep,
+                        int on_device, uint8_t* out, uint64_t cap, uint64_t* size);
 
 /* ---- Sector-track merger (Sec. 4: the pieces of one track are found in
  * neighbouring sectors separately and must be merged; the removal of clusters

@@ -1331,8 +1331,8 @@ void* cmp_buffer(tpc_ctx* c, int i, size_t bytes) {
 }  // namespace
 
 extern "C" tpc_status tpc_compress(tpc_ctx* c, const tpc_cluster_charges* ch, const tpc_track_t* tracks,
-                                   uint64_t n_tracks, const uint32_t* cluster_ids, uint64_t n_ids, int on_device,
-                                   uint8_t* out, uint64_t cap, uint64_t* size) {
+                                   uint64_t n_tracks, const uint32_t* cluster_ids, uint64_t n_ids, const uint8_t* keep,
+                                   int on_device, uint8_t* out, uint64_t cap, uint64_t* size) {
   if (!c || !ch || !size) return fail(c, TPC_ERR_INVALID_ARG, "null argument");
   if (!c->tracked) return fail(c, TPC_ERR_STATE, "tpc_compress before tpc_track");
   *size = 0;
@@ -1383,6 +1383,14 @@ extern "C" tpc_status tpc_compress(tpc_ctx* c, const tpc_cluster_charges* ch, co
       q[k] = st + k * N;
     }
   }
+  const uint8_t* d_keep = keep;
+  if (keep && !on_device && N > 0) {
+    uint8_t* kb = (uint8_t*)cmp_buffer(c, 42, (size_t)N);
+    if (!kb) return fail(c, TPC_ERR_OOM, "keep staging");
+    if ((e = cudaMemcpyAsync(kb, keep, (size_t)N, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "keep upload");
+    d_keep = kb;
+  }
   // sorted positions: one per loaded cluster (those of clusters left out of the binning are unused)
   const int NR = c->cfg.n_rows, I = c->b.I;
   const long long P = N;
@@ -1400,6 +1408,7 @@ extern "C" tpc_status tpc_compress(tpc_ctx* c, const tpc_cluster_charges* ch, co
   a.qm = q[1];
   a.sy = q[2];
   a.sz = q[3];
+  a.keep = d_keep;
   a.trk = trk;
   a.ids = ids;
   a.counts = nullptr;

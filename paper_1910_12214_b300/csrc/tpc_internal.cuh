@@ -221,6 +221,7 @@ struct CmpArgs {
   int N, I, P;  // clusters, items, sorted positions (= N; positions outside every row's range are unused)
   // charges and sizes
   const float *qt, *qm, *sy, *sz;
+  const uint8_t* keep;  // per cluster, 0 = removed (not stored); null = keep all
   // tracks
   const void* trk;
   const uint32_t* ids;

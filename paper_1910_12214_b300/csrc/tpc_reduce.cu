@@ -599,17 +599,21 @@ __global__ void k_cmp_attach(const __grid_constant__ CmpArgs a, const __grid_con
   for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_trk; t += nw) {
     const long long first = trk[t].first_cluster, cnt = trk[t].n_clusters;
     bool bad = trk[t].item >= (uint32_t)a.I || first + cnt > n_ids;
+    int kept = 0;
     if (!bad)
       for (long long j = lane; j < cnt; j += 32) {
         const uint32_t c = a.ids[first + j];
-        if (c >= (uint32_t)a.N)
+        if (c >= (uint32_t)a.N) {
           bad = true;
-        else
+        } else {
           a.attached[c] = 1;
+          kept += (!a.keep || a.keep[c]) ? 1 : 0;
+        }
       }
     bad = __any_sync(0xffffffffu, bad);
+    for (int o = 16; o; o >>= 1) kept += __shfl_xor_sync(0xffffffffu, kept, o);
     if (lane == 0) {
-      a.trk_n[t] = bad ? 0 : (int)cnt;
+      a.trk_n[t] = bad ? 0 : kept;  // the clusters the track stores
       if (bad) atomicOr(a.err, TPC_DERR_BAD_TRACK);
     }
   }
@@ -639,7 +643,10 @@ __global__ void k_cmp_flags(const __grid_constant__ CmpArgs a, int n_rows) {
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long g = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; g < G; g += nw) {
     const RowInfo ri = a.rows[g];
-    for (int p = ri.pos0 + lane; p < ri.pos0 + ri.n; p += 32) a.kpos[p] = a.attached[a.s_hit[p].z] ? 0 : 1;
+    for (int p = ri.pos0 + lane; p < ri.pos0 + ri.n; p += 32) {
+      const int c = a.s_hit[p].z;
+      a.kpos[p] = (a.attached[c] || (a.keep && !a.keep[c])) ? 0 : 1;
+    }
   }
 }
 
@@ -697,17 +704,29 @@ __global__ void k_cmp_track_symbols(const __grid_constant__ CmpArgs a, const __g
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
   for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < n_trk; t += nw) {
     const tpc_track_t T = trk[t];
-    const long long base = a.trk_n[t], cnt = a.trk_n[t + 1] - base;
-    if (lane == 0) a.val[C_TRK_N][t] = (unsigned long long)cnt;
-    int carry = 0;  // row of the previous cluster (0 before the first)
+    const long long base = a.trk_n[t], stored = a.trk_n[t + 1] - base;
+    // the track's clusters (all of them when it stores any; a bad track stores none)
+    const long long cnt = stored > 0 ? (long long)T.n_clusters : 0;
+    if (lane == 0) a.val[C_TRK_N][t] = (unsigned long long)stored;
+    int carry = 0;        // row of the previous stored cluster (0 before the first)
+    long long done = 0;   // stored clusters of the previous rounds
     for (long long j0 = 0; j0 < cnt; j0 += 32) {
       const long long j = j0 + lane;
-      const bool act = j < cnt;
-      const int4 q = act ? a.rec[a.ids[T.first_cluster + j]] : make_int4(0, 0, 0, 0);
+      const uint32_t c = j < cnt ? a.ids[T.first_cluster + j] : 0u;
+      const bool act = j < cnt && (!a.keep || a.keep[c]);
+      const int4 q = act ? a.rec[c] : make_int4(0, 0, 0, 0);
       const int r = rec_row(q);
-      const int up = __shfl_up_sync(0xffffffffu, r, 1);
-      const int rp = lane ? up : carry;
-      carry = __shfl_sync(0xffffffffu, r, 31);
+      // the stored clusters of this round: rank among them, row of the previous one
+      const unsigned m = __ballot_sync(0xffffffffu, act);
+      const unsigned below = m & ((1u << lane) - 1u);
+      const int src = below ? 31 - __clz(below) : 0;
+      const int rsrc = __shfl_sync(0xffffffffu, r, src);
+      const int rp = below ? rsrc : carry;
+      const int last = m ? 31 - __clz(m) : 0;
+      const int rlast = __shfl_sync(0xffffffffu, r, last);
+      const long long pos = done + __popc(below);
+      done += __popc(m);
+      if (m) carry = rlast;
       if (!act) continue;
       if (r >= par.n_rows) {  // a cluster with a pad row out of range: the track cannot be stored
         atomicOr(a.err, TPC_DERR_BAD_TRACK);
@@ -715,10 +734,10 @@ __global__ void k_cmp_track_symbols(const __grid_constant__ CmpArgs a, const __g
       }
       long long py, pz;
       predict_codes(T, par.kB, par.x[r], &py, &pz);
-      a.val[C_DROW][base + j] = zigzag((long long)(r - rp));
-      a.val[C_RY][base + j] = zigzag((long long)rec_y(q) - py);
-      a.val[C_RZ][base + j] = zigzag((long long)q.x - pz);
-      put_props(a, n_un + base + j, q);
+      a.val[C_DROW][base + pos] = zigzag((long long)(r - rp));
+      a.val[C_RY][base + pos] = zigzag((long long)rec_y(q) - py);
+      a.val[C_RZ][base + pos] = zigzag((long long)q.x - pz);
+      put_props(a, n_un + base + pos, q);
     }
   }
 }

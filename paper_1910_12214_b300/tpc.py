@@ -113,8 +113,8 @@ _sig = {
                              C.POINTER(C.c_uint64)], C.c_int),
     "tpc_cluster_masks": ([_P, C.POINTER(tpc_mask_params), _P, C.c_uint64, _P, C.c_uint64, _P, C.c_int, _P, _P],
                           C.c_int),
-    "tpc_compress": ([_P, C.POINTER(tpc_cluster_charges), _P, C.c_uint64, _P, C.c_uint64, C.c_int, _P, C.c_uint64,
-                      C.POINTER(C.c_uint64)], C.c_int),
+    "tpc_compress": ([_P, C.POINTER(tpc_cluster_charges), _P, C.c_uint64, _P, C.c_uint64, _P, C.c_int, _P,
+                      C.c_uint64, C.POINTER(C.c_uint64)], C.c_int),
     "tpc_merge_tracks": ([_P, _P, C.c_uint64, _P, C.c_uint64, C.c_int, _P, _P, _P, _P, _P], C.c_int),
     "tpc_destroy": ([_P], None),
     "tpc_last_error": ([_P], C.c_char_p),
@@ -403,35 +403,36 @@ class Tracker:
                                            int(on_device), _ptr(mask), _ptr(owner)))
         return mask, owner
 
-    def compress(self, charges, tracks=None, ids=None, on_device=False, out=None):
-        """Compressed blob of the loaded, tracked clusters (Sec. 4, steps 3-4;
+    def compress(self, charges, tracks=None, ids=None, on_device=False, out=None, keep=None):
+        """Compressed blob of the loaded, tracked clusters (Sec. 4, steps 3-5;
         include/tpc_reduce.h).  charges: dict of q_tot, q_max, sigma_y, sigma_z
         (numpy, or CUDA tensors with on_device).  tracks=None uses the last
         tpc_track() output; else TRACK_DTYPE records and uint32 ids (numpy), or
-        a CUDA uint8 tensor [n, 112] and int32 ids with on_device.  out: a
-        buffer to write into (numpy uint8, or a CUDA uint8 tensor with
-        on_device); too small or None: sized by a first call.  Returns the blob
-        (a view of out)."""
-        keep = []
+        a CUDA uint8 tensor [n, 112] and int32 ids with on_device.  keep: one
+        byte per loaded cluster, 0 = removed and not stored (numpy, or a CUDA
+        tensor with on_device), None = keep all.  out: a buffer to write into
+        (numpy uint8, or a CUDA uint8 tensor with on_device); too small or None:
+        sized by a first call.  Returns the blob (a view of out)."""
+        hold = []  # host arrays that must outlive the call
         if on_device:
             arrs = [charges[k] for k in ("q_tot", "q_max", "sigma_y", "sigma_z")]
-            nt = int(tracks.shape[0]) if tracks is not None else 0
         else:
             arrs = [np.ascontiguousarray(charges[k], np.float32) for k in ("q_tot", "q_max", "sigma_y", "sigma_z")]
             if tracks is not None:
                 tracks = np.ascontiguousarray(tracks, TRACK_DTYPE)
                 ids = np.ascontiguousarray(ids, np.uint32)
-                keep += [tracks, ids]
-            nt = int(tracks.shape[0]) if tracks is not None else 0
-        keep += arrs
+            if keep is not None:
+                keep = np.ascontiguousarray(keep, np.uint8)
+        hold += arrs + [tracks, ids, keep]
+        nt = int(tracks.shape[0]) if tracks is not None else 0
         ch = tpc_cluster_charges(*[_ptr(a) for a in arrs])
         ni = int(ids.shape[0]) if ids is not None else 0
         size = C.c_uint64()
 
         def call(buf):
             cap = int(buf.shape[0]) if buf is not None else 0
-            return _lib.tpc_compress(self._h, C.byref(ch), _ptr(tracks), nt, _ptr(ids), ni, int(on_device),
-                                     _ptr(buf) if cap else None, cap, C.byref(size))
+            return _lib.tpc_compress(self._h, C.byref(ch), _ptr(tracks), nt, _ptr(ids), ni, _ptr(keep),
+                                     int(on_device), _ptr(buf) if cap else None, cap, C.byref(size))
 
         st = call(out)
         if st == 5:  # TPC_ERR_CAPACITY: size the buffer and run again

@@ -1,4 +1,4 @@
-"""Parity of the CUDA compression (Sec. 4, steps 3 and 4) with the oracle,
+"""Parity of the CUDA compression (Sec. 4, steps 3 to 5) with the oracle,
 through the C ABI: given the same tracks (the oracle tracker's), the GPU's blob
 equals the oracle's byte for byte; with the GPU's own tracks the oracle's
 decoder restores every stored cluster exactly."""
@@ -112,7 +112,7 @@ def test_edge_cases():
     ch = tpc.tpc_cluster_charges(*[props[k].ctypes.data for k in ("q_tot", "q_max", "sigma_y", "sigma_z")])
     size = C.c_uint64()
     small = np.zeros(16, np.uint8)
-    st = tpc._lib.tpc_compress(t._h, C.byref(ch), empty.ctypes.data, 0, None, 0, 0, small.ctypes.data, 16,
+    st = tpc._lib.tpc_compress(t._h, C.byref(ch), empty.ctypes.data, 0, None, 0, None, 0, small.ctypes.data, 16,
                                C.byref(size))
     assert st == 5 and size.value == want.size and not small.any()
     # a track outside the batch
@@ -123,3 +123,27 @@ def test_edge_cases():
         t.compress(props, rec, rids)
     assert e.value.status == 7
     t.close()
+
+
+def test_removal_by_strategy_a_b_and_random():
+    """Sec. 4, step 5: with the keep masks of strategies A and B (from the
+    oracle's masks) and a random one, the blob equals the oracle's byte for
+    byte, and the stored volume shrinks in the order none > A > B."""
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_config2(seed=15)
+    props = synth.cluster_props(cl, seed=15)
+    ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids", "sorted_id", "rows"])
+    tf, ti, ids = oracle.oracle_tracks(ref)
+    order, seg = oracle.grid_order(ref)
+    wm, _, _ = oracle.cluster_masks(cl, tf, ti, ids)
+    keeps = {"A": ((wm & 4) == 0).astype(np.uint8), "B": ((wm & 8) == 0).astype(np.uint8),
+             "random": (np.random.default_rng(1).uniform(size=cl.n) < 0.7).astype(np.uint8)}
+    sizes = {}
+    with tracked(cl) as t:
+        full = t.compress(props, to_records(tf, ti), ids)
+        for name, keep in keeps.items():
+            want = oracle.compress(cl, props, order, seg, tf, ti, ids, keep=keep)
+            got = t.compress(props, to_records(tf, ti), ids, keep=keep)
+            assert got.size == want.size and np.array_equal(got, want), (name, first_difference(got, want))
+            sizes[name] = got.size
+    assert full.size > sizes["A"] > sizes["B"]
