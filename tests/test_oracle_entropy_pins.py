@@ -38,6 +38,26 @@ def test_hand_worked_rans_chunk():
     assert words.tolist() == want
 
 
+def test_frequency_scaling_floor_and_excess():
+    """The scaling rule worked by hand.  Counts {0: 10000, 1: 1}: f0 =
+    floor(10000*4096/10001) = 4095, f1 = max(1, floor(4096/10001) = 0) = 1,
+    sum 4096.  Counts {0: 100000, 1..255: 1 each}: f0 = floor(100000*4096/100255)
+    = 4085, every other byte is raised to 1 (255 of them), sum 4340: the excess
+    of 244 is taken from the largest, f0 = 3841."""
+    _, _, f, _, _ = stream_fields(oracle.code_stream(np.array([0] * 10000 + [1], np.uint64)))
+    assert f[0] == 4095 and f[1] == 1 and f[2:].sum() == 0
+    v = np.concatenate([np.zeros(100000, np.uint64), np.arange(1, 256, dtype=np.uint64)])
+    _, _, f, _, _ = stream_fields(oracle.code_stream(v))
+    assert f[0] == 3841 and np.all(f[1:] == 1) and int(f.sum()) == 4096
+    # two large counts {0: 60000, 1: 40000, 2..255: 1 each}: f0 = floor(60000*4096/100254)
+    # = 2451, f1 = floor(40000*4096/100254) = 1634, 254 bytes raised to 1, sum 4339: the
+    # excess of 243 is taken one unit at a time from the largest, which stays byte 0
+    # (2208 > 1634), so f1 keeps its floor
+    v = np.concatenate([np.zeros(60000, np.uint64), np.ones(40000, np.uint64), np.arange(2, 256, dtype=np.uint64)])
+    _, _, f, _, _ = stream_fields(oracle.code_stream(v))
+    assert f[0] == 2208 and f[1] == 1634 and np.all(f[2:] == 1)
+
+
 def test_single_symbol_plane_costs_no_words():
     """A plane with one symbol value has frequency 4096: encoding leaves every
     state unchanged, so each chunk is its 32 initial states."""

@@ -64,6 +64,14 @@ def test_hand_built_split_helix_is_linked_and_a_bent_copy_is_not():
     tf2[1, 4] += 0.03
     link, group, _, _ = run(tf2)
     assert (link == -1).all() and group.tolist() == [0, 1]
+    # curvatures 5 sigma apart (chi2 = 25 > 16; the sector-0 piece's circle, which the
+    # continuity test uses, is unchanged): no link; 3 sigma apart (chi2 = 9): linked
+    sig = math.sqrt(float(tf[0, 6]) + float(tf[1, 6]))
+    for k, want in ((5.0, [-1, -1]), (3.0, [1, -1])):
+        tf3 = tf.copy()
+        tf3[1, 5] += np.float32(k * sig)
+        link, _, _, _ = run(tf3)
+        assert link[0].tolist() == want, k
 
 
 def test_refit_recovers_exact_helices():
@@ -86,6 +94,10 @@ def test_refit_recovers_exact_helices():
         # the clusters are quantised to 2^-10 cm by nothing here: exact float32 positions
         assert abs(fit[g, 2] - R_true[m]) < 2e-4 * R_true[m] + 0.05, (g, fit[g, 2], R_true[m])
         assert abs(fit[g, 3] - cl.tracks["tgl"][m]) < 2e-3
+        # the centre of the circle through the vertex: q R (sin phi0, -cos phi0)
+        q, ph = cl.tracks["q"][m], cl.tracks["phi0"][m]
+        xc, yc = q * R_true[m] * math.sin(ph), -q * R_true[m] * math.cos(ph)
+        assert math.hypot(fit[g, 0] - xc, fit[g, 1] - yc) < 2e-4 * R_true[m] + 0.05
         checked += 1
     assert checked > 500
 
