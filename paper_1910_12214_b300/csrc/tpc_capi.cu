@@ -1604,7 +1604,7 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
   int* d_nb = (int*)cmp_buffer(c, 35, 8 * (size_t)I + (legs ? 72 * (size_t)I : 0));
   int* d_lbest = (int*)cmp_buffer(c, 40, 4 * (size_t)std::max(nt, 1ll));
   int* d_first = (int*)cmp_buffer(c, 36, 4 * (size_t)(I + 1));
-  double* d_geo = (double*)cmp_buffer(c, 37, (8 * 12 + 16) * (size_t)std::max(nt, 1ll));
+  double* d_geo = (double*)cmp_buffer(c, 37, (8 * 12 + 16 + 32) * (size_t)std::max(nt, 1ll));
   int* d_best = (int*)cmp_buffer(c, 38, 8 * (size_t)std::max(nt, 1ll));
   // outputs: the caller's device arrays, or staging for host arrays
   uint8_t* st = nullptr;
@@ -1638,6 +1638,7 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
   a.item_first = d_first;
   a.geo = d_geo;
   a.pre = (float4*)(d_geo + 12 * (size_t)std::max(nt, 1ll));  // 16-byte aligned: 96 bytes per track before it
+  a.geo32 = a.pre + std::max(nt, 1ll);
   a.best = d_best;
   a.link = on_device ? link : (int*)(st + o_link);
   a.group = on_device ? group : (int*)(st + o_group);

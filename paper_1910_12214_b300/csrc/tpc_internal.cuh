@@ -277,6 +277,7 @@ struct MrgArgs {
   int* item_first;            // [I + 1] first track of every item
   double* geo;                // [n_trk][12] per-track circle (device work array)
   float4* pre;                // [n_trk] (ok ? tan lambda : NaN, q/pT, sqrt(var q/pT), sign): the FP32 prefilter
+  float4* geo32;              // [n_trk][2] (xc, yc, R, var q/pT), (x, y, z, radius) of geo rounded to FP32
   int* best;                  // [n_trk][2]
   int* link;                  // [n_trk][2] output
   int* group;                 // [n_trk] output

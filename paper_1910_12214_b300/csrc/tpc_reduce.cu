@@ -1124,7 +1124,11 @@ __global__ void k_mrg_geom(const __grid_constant__ MrgArgs a) {
     g[G_OK] = ok ? 1.0 : 0.0;
     a.pre[t] = make_float4(ok ? T.tgl : __int_as_float(0x7fc00000), T.qpt, sqrtf(fmaxf(T.cov[14], 0.f)),
                            T.qpt > 0.f ? 1.f : -1.f);
-    if (!ok) continue;
+    if (!ok) {
+      a.geo32[2 * t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a.geo32[2 * t + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
     const int s = (int)a.item_sector[T.item];
     const double ang = (double)(s % 18) * MRG_WEDGE, ca = cos(ang), sa = sin(ang);
     const double kap = a.kB * (double)T.qpt;
@@ -1142,6 +1146,9 @@ __global__ void k_mrg_geom(const __grid_constant__ MrgArgs a) {
     g[G_QPT] = T.qpt;
     g[G_VQ] = fmax(0.0, (double)T.cov[14]);
     g[G_SIGN] = T.qpt > 0.f ? 1.0 : -1.0;
+    // the same quantities rounded to FP32 (var q/pT is a float: exact) for the prefilters
+    a.geo32[2 * t] = make_float4((float)g[G_XC], (float)g[G_YC], (float)g[G_R], (float)g[G_VQ]);
+    a.geo32[2 * t + 1] = make_float4((float)X, (float)Y, T.z, (float)g[G_RAD]);
   }
 }
 
@@ -1184,6 +1191,45 @@ __device__ __forceinline__ bool mrg_compatible(const double* A, const double* B,
   return d <= dlim && dz <= 2.0;
 }
 
+// FP32 form of the continuity and dz tests of mrg_compatible that never rejects
+// a pair the FP64 tests accept.  Inputs are the FP64 values rounded to FP32
+// (relative error u = 2^-24 each).  With M the sum of the magnitudes entering a
+// difference, a rounded difference is off by at most 2u M, a rounded hypot by
+// 5u M, and the distance |h - R| by 7u (M + R); the limit 1 + 3 kB sqrt(V) L^2
+// by 8u of its value plus 8u kB sqrt(V) M^2; dz by 8u times the magnitudes of
+// its terms.  The margins below are about 20 times these bounds.  The reference
+// (smaller var q/pT) is chosen alike in both precisions because the variance is
+// a float; the inner track (smaller radius) too unless the rounded radii are
+// equal, where the dz test is left to FP64.  A NaN or infinity passes.
+__device__ __forceinline__ bool mrg_maybe_compatible(const float4* A32, const float4* B32, float tgl_a,
+                                                     float tgl_b, float kB) {
+  constexpr float e = 1e-5f;
+  const float4 a0 = A32[0], a1 = A32[1], b0 = B32[0], b1 = B32[1];
+  const bool a_ref = a0.w <= b0.w;
+  const float4 r0 = a_ref ? a0 : b0, r1 = a_ref ? a1 : b1, o1 = a_ref ? b1 : a1;
+  const float dxl = o1.x - r1.x, dyl = o1.y - r1.y;
+  const float L2 = fmaf(dxl, dxl, dyl * dyl);
+  const float ex = o1.x - r0.x, ey = o1.y - r0.y;
+  const float d = fabsf(sqrtf(fmaf(ex, ex, ey * ey)) - r0.z);
+  const float kv = 3.0f * kB * sqrtf(r0.w);
+  const float Q = fabsf(o1.x) + fabsf(o1.y) + fabsf(r1.x) + fabsf(r1.y);
+  const float Mc = fabsf(o1.x) + fabsf(o1.y) + fabsf(r0.x) + fabsf(r0.y) + r0.z;
+  const float dlim = fmaf(kv, L2, 1.0f);
+  if (d > dlim * (1.0f + e) + e * (kv * Q * Q + Mc) + 1e-6f) return false;
+  if (a1.w == b1.w) return true;
+  const bool a_in = a1.w < b1.w;
+  const float4 in1 = a_in ? a1 : b1, out1 = a_in ? b1 : a1;
+  const float tin = a_in ? tgl_a : tgl_b;
+  const float cx = out1.x - in1.x, cy = out1.y - in1.y;
+  const float c = sqrtf(fmaf(cx, cx, cy * cy));
+  const float Rb = 0.5f * (a0.z + b0.z);
+  const float t = c * c / (24.0f * Rb * Rb);
+  const float arc = c * (1.0f + t);
+  const float dz = fabsf(out1.z - fmaf(tin, arc, in1.z));
+  const float Qz = fabsf(in1.x) + fabsf(in1.y) + fabsf(out1.x) + fabsf(out1.y);
+  return !(dz > 2.0f + e * (fabsf(out1.z) + fabsf(in1.z) + fabsf(tin) * (arc + Qz) * (2.0f + 4.0f * t)) + 1e-6f);
+}
+
 // one warp per track: the best compatible candidate in sector k+1 (d = 0) and k-1 (d = 1)
 __global__ void k_mrg_best(const __grid_constant__ MrgArgs a) {
   const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
@@ -1192,6 +1238,7 @@ __global__ void k_mrg_best(const __grid_constant__ MrgArgs a) {
   for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_trk; t += nw) {
     const double* A = a.geo + G_N * t;
     const bool ok = A[G_OK] != 0.0;
+    const float kBf = (float)a.kB;
     for (int d = 0; d < 2; ++d) {
       const int nb = ok ? a.nb_item[2 * trk[t].item + d] : -1;
       double bs = 0.0;
@@ -1205,6 +1252,7 @@ __global__ void k_mrg_best(const __grid_constant__ MrgArgs a) {
           if (!(fabsf(pa.x - pb.x) <= 0.0201f) || pa.w != pb.w) continue;
           const float dq = pa.y - pb.y, sq = pa.z * pa.z + pb.z * pb.z;
           if (!(dq * dq <= 16.2f * sq + 1e-28f)) continue;
+          if (!mrg_maybe_compatible(a.geo32 + 2 * t, a.geo32 + 2 * b, pa.x, pb.x, kBf)) continue;
           const double* B = a.geo + G_N * b;
           if (B[G_OK] == 0.0 || B[G_SIGN] != A[G_SIGN]) continue;
           double sc;
@@ -1404,7 +1452,8 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
     const double D = (-su3 * svv + sv3 * suv) / det, E = (-sv3 * suu + su3 * suv) / det, F = -sw / (double)n;
     const double xc = mx - 0.5 * D, yc = my - 0.5 * E;
     const double R = sqrt(0.25 * (D * D + E * E) - F);
-    // pass 3: z against the arc from the innermost cluster
+    const double k24 = 1.0 / (24.0 * R * R);
+    // pass 3: z against the arc from the innermost cluster (chord c, arc c (1 + c^2 / 24 R^2))
     double ss = 0, sz = 0, sss = 0, ssz = 0;
     pos = 0;
     for (int m = 0; m < nm; ++m) {
@@ -1412,8 +1461,8 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
       for (long long j = lane; j < cnt; j += 32) {
         double X, Y, Z;
         cluster_at(m, j, pos + j, &X, &Y, &Z);
-        const double c = hypot(X - xin, Y - yin);
-        const double s = c * (1.0 + c * c / (24.0 * R * R));
+        const double cx = X - xin, cy = Y - yin, c2 = cx * cx + cy * cy;
+        const double s = sqrt(c2) * (1.0 + c2 * k24);
         ss += s;
         sz += Z;
         sss += s * s;
@@ -1452,6 +1501,8 @@ __global__ void k_mrg_legs(const __grid_constant__ MrgArgs a) {
     long long bi = -1;
     if (A[G_OK] != 0.0 && A[G_R] < 250.0) {
       const float4 pa = a.pre[t];
+      const float4 ga = a.geo32[2 * t];
+      const float kBf = (float)a.kB;
       const int* items = a.side_items + 18 * (long long)trk[t].item;
       for (int k = 0; k < 18; ++k) {
         const int it = items[k];
@@ -1462,6 +1513,15 @@ __global__ void k_mrg_legs(const __grid_constant__ MrgArgs a) {
           if (pb.w == pa.w || !((pa.x > 0.f) != (pb.x > 0.f)) || !(fabsf(pa.x + pb.x) <= 0.0201f)) continue;
           const float dq = fabsf(pa.y) - fabsf(pb.y), sq = pa.z * pa.z + pb.z * pb.z;
           if (!(dq * dq <= 16.2f * sq + 1e-28f)) continue;
+          {  // the centre distance in FP32, margins as in mrg_maybe_compatible
+            const float4 gb = a.geo32[2 * b];
+            const float ex = ga.x - gb.x, ey = ga.y - gb.y;
+            const float Rm = fmaxf(ga.z, gb.z);
+            const float kv = 3.0f * kBf * sqrtf(ga.w + gb.w);
+            const float dl = fmaf(kv * Rm, Rm, 1.0f);
+            const float M = fabsf(ga.x) + fabsf(ga.y) + fabsf(gb.x) + fabsf(gb.y);
+            if (sqrtf(fmaf(ex, ex, ey * ey)) > dl * (1.0f + 1e-5f) + 1e-5f * (kv * Rm * Rm + M) + 1e-6f) continue;
+          }
           const double* B = a.geo + G_N * b;
           if (B[G_OK] == 0.0 || !(B[G_R] < 250.0)) continue;
           const double qa = fabs(A[G_QPT]), qb = fabs(B[G_QPT]);
