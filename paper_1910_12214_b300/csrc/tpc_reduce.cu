@@ -1106,7 +1106,7 @@ cudaError_t cmp_layout(const CmpPlane* planes, int n_planes, const int* stream_p
 // mutual and one per direction, so every group is a path through neighbouring
 // sectors: a bounded walk labels it by its smallest index.  One warp per group
 // then refits the group's clusters in the global frame (algebraic circle fit,
-// then z against the arc), in FP64.
+// then z against the arc): per-cluster sums in float-float, the solves in FP64.
 namespace {
 
 constexpr double MRG_WEDGE = 2.0 * 3.14159265358979323846 / 18.0;
@@ -1303,18 +1303,86 @@ __global__ void k_mrg_group(const __grid_constant__ MrgArgs a) {
   }
 }
 
-__device__ __forceinline__ double warp_sum(double v) {
-  for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+// Float-float ("double-float") numbers for the refit's per-cluster sums: a
+// value is hi + lo with |lo| <= ulp(hi) / 2, a 48-bit significand computed on
+// the FP32 pipe, which the B300 has about 60 times wider than the FP64 one.
+// The error-free transformations are Knuth's TwoSum, Dekker's Fast2Sum (valid
+// for |a| >= |b|) and the fused-multiply-add TwoProduct; the additions are the
+// "sloppy" form (absolute error a few 2^-46 of |a| + |b|, like an FP64 sum's
+// 2^-53 of its terms).  Explicit _rn intrinsics keep the compiler from fusing
+// or reordering any of it.
+struct F2 {
+  float hi, lo;
+};
+
+__device__ __forceinline__ F2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  return {s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb))};
+}
+
+__device__ __forceinline__ F2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ F2 f2_add(F2 a, F2 b) {
+  const F2 s = two_sum(a.hi, b.hi);
+  return fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ F2 f2_neg(F2 a) { return {-a.hi, -a.lo}; }
+
+__device__ __forceinline__ F2 f2_mul(F2 a, F2 b) {
+  const float p = __fmul_rn(a.hi, b.hi);
+  float e = __fmaf_rn(a.hi, b.hi, -p);
+  e = __fmaf_rn(a.hi, b.lo, e);
+  e = __fmaf_rn(a.lo, b.hi, e);
+  return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ F2 f2_mul_f(F2 a, float b) {  // times a float
+  const float p = __fmul_rn(a.hi, b);
+  return fast_two_sum(p, __fmaf_rn(a.lo, b, __fmaf_rn(a.hi, b, -p)));
+}
+
+// square root by one Newton correction of the correctly rounded FP32 root
+// (x + (a - x^2) / 2x, the residual a - x^2 formed exactly by TwoProduct)
+__device__ __forceinline__ F2 f2_sqrt(F2 a) {
+  if (!(a.hi > 0.0f)) return {0.0f, 0.0f};
+  const float x = __fsqrt_rn(a.hi);
+  const float p = __fmul_rn(x, x);
+  const float r = __fadd_rn(__fsub_rn(__fsub_rn(a.hi, p), __fmaf_rn(x, x, -p)), a.lo);
+  return fast_two_sum(x, __fmul_rn(r, __fdividef(0.5f, x)));
+}
+
+__device__ __forceinline__ F2 f2_from(double v) {
+  const float hi = (float)v;
+  return {hi, (float)(v - (double)hi)};
+}
+
+__device__ __forceinline__ double f2_val(F2 a) { return (double)a.hi + (double)a.lo; }
+
+__device__ __forceinline__ bool f2_less(F2 a, F2 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
+
+__device__ __forceinline__ F2 warp_sum(F2 v) {
+  for (int o = 16; o; o >>= 1) {
+    const F2 w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = f2_add(v, w);
+  }
   return v;
 }
 
-// one warp per group root: refit of the group's clusters in the global frame
+// one warp per group root: refit of the group's clusters in the global frame.
+// Cluster positions and the per-cluster sums are float-float; the mean, the
+// 2x2 solve for the circle and the line in (s, z) are FP64, once per group.
 __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs a,
                                                   const __grid_constant__ DevParams par) {
   __shared__ int mem[4][40];
-  __shared__ double rot[4][40][2];  // cos and sin of each member's sector angle
-  constexpr int STAGE = 384;        // clusters of a group kept in shared memory (larger groups re-gather)
-  __shared__ double sX[4][STAGE], sY[4][STAGE], sZ[4][STAGE];
+  __shared__ F2 rot[4][40][2];  // cos and sin of each member's sector angle
+  constexpr int STAGE = 384;    // clusters of a group kept in shared memory (larger groups re-gather)
+  __shared__ F2 sX[4][STAGE], sY[4][STAGE];
+  __shared__ float sZ[4][STAGE];
   const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
@@ -1346,16 +1414,17 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
     __syncwarp();
     for (int m = lane; m < nm; m += 32) {
       const double ang = (double)((int)a.item_sector[trk[mem[w][m]].item] % 18) * MRG_WEDGE;
-      rot[w][m][0] = cos(ang);
-      rot[w][m][1] = sin(ang);
+      rot[w][m][0] = f2_from(cos(ang));
+      rot[w][m][1] = f2_from(sin(ang));
     }
     __syncwarp();
     long long n_all = 0;
     for (int m = 0; m < nm; ++m) n_all += trk[mem[w][m]].n_clusters;
     const bool staged = n_all <= STAGE;
-    auto gather = [&](int m, long long j, double* X, double* Y, double* Z) {
+    // global position of cluster j of member m: x_row cos - y sin, x_row sin + y cos
+    auto gather = [&](int m, long long j, F2* X, F2* Y, float* Z) {
       const tpc_track_t& T = trk[mem[w][m]];
-      const double ca = rot[w][m][0], sa = rot[w][m][1];
+      const F2 ca = rot[w][m][0], sa = rot[w][m][1];
       uint32_t c = a.ids[T.first_cluster + j];
       int r = c < (uint32_t)a.N ? a.row[c] : -1;
       if (r < 0 || r >= par.n_rows) {  // reported as an error (the results are then not used); read cluster 0
@@ -1363,10 +1432,10 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
         c = 0;
         r = 0;
       }
-      const double lx = par.x[r], ly = a.N > 0 ? a.y[c] : 0.0;
-      *X = lx * ca - ly * sa;
-      *Y = lx * sa + ly * ca;
-      *Z = a.N > 0 ? a.z[c] : 0.0;
+      const float lx = par.x[r], ly = a.N > 0 ? a.y[c] : 0.0f;
+      *X = f2_add(f2_mul_f(ca, lx), f2_neg(f2_mul_f(sa, ly)));
+      *Y = f2_add(f2_mul_f(sa, lx), f2_mul_f(ca, ly));
+      *Z = a.N > 0 ? a.z[c] : 0.0f;
     };
     if (staged) {
       long long base = 0;
@@ -1378,7 +1447,7 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
       __syncwarp();
     }
     // cluster j of member m (p = its position over the group): from shared memory or gathered again
-    auto cluster_at = [&](int m, long long j, long long p, double* X, double* Y, double* Z) {
+    auto cluster_at = [&](int m, long long j, long long p, F2* X, F2* Y, float* Z) {
       if (staged) {
         *X = sX[w][p];
         *Y = sY[w][p];
@@ -1388,17 +1457,18 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
       }
     };
     // pass 1: mean, count and the innermost cluster (smallest radius, first in order on ties)
-    double sx = 0, sy = 0, rmin = 1e300, xin = 0, yin = 0;
+    F2 sx = {0.f, 0.f}, sy = {0.f, 0.f}, rmin = {INFINITY, 0.f}, xin = {0.f, 0.f}, yin = {0.f, 0.f};
     long long pin = -1, n = 0, pos = 0;
     for (int m = 0; m < nm; ++m) {
       const long long cnt = trk[mem[w][m]].n_clusters;
       for (long long j = lane; j < cnt; j += 32) {
-        double X, Y, Z;
+        F2 X, Y;
+        float Z;
         cluster_at(m, j, pos + j, &X, &Y, &Z);
-        sx += X;
-        sy += Y;
-        const double rr = X * X + Y * Y;  // ordering by the squared radius
-        if (rr < rmin) {  // a lane sees its positions in increasing order
+        sx = f2_add(sx, X);
+        sy = f2_add(sy, Y);
+        const F2 rr = f2_add(f2_mul(X, X), f2_mul(Y, Y));  // ordering by the squared radius
+        if (f2_less(rr, rmin)) {  // a lane sees its positions in increasing order
           rmin = rr;
           pin = pos + j;
           xin = X;
@@ -1409,10 +1479,11 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
       n += cnt;
     }
     for (int off = 16; off; off >>= 1) {
-      const double orr = __shfl_xor_sync(0xffffffffu, rmin, off);
+      const F2 orr = {__shfl_xor_sync(0xffffffffu, rmin.hi, off), __shfl_xor_sync(0xffffffffu, rmin.lo, off)};
       const long long op = __shfl_xor_sync(0xffffffffu, pin, off);
-      const double ox = __shfl_xor_sync(0xffffffffu, xin, off), oy = __shfl_xor_sync(0xffffffffu, yin, off);
-      if (op >= 0 && (pin < 0 || orr < rmin || (orr == rmin && op < pin))) {
+      const F2 ox = {__shfl_xor_sync(0xffffffffu, xin.hi, off), __shfl_xor_sync(0xffffffffu, xin.lo, off)};
+      const F2 oy = {__shfl_xor_sync(0xffffffffu, yin.hi, off), __shfl_xor_sync(0xffffffffu, yin.lo, off)};
+      if (op >= 0 && (pin < 0 || f2_less(orr, rmin) || (orr.hi == rmin.hi && orr.lo == rmin.lo && op < pin))) {
         rmin = orr;
         pin = op;
         xin = ox;
@@ -1422,66 +1493,66 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
     sx = warp_sum(sx);
     sy = warp_sum(sy);
     if (n < 3) continue;
-    const double mx = sx / (double)n, my = sy / (double)n;
+    const double mxd = f2_val(sx) / (double)n, myd = f2_val(sy) / (double)n;
+    const F2 nmx = f2_neg(f2_from(mxd)), nmy = f2_neg(f2_from(myd));
     // pass 2: centred moments
-    double suu = 0, suv = 0, svv = 0, su3 = 0, sv3 = 0, sw = 0;
+    F2 suu = {0.f, 0.f}, suv = suu, svv = suu, su3 = suu, sv3 = suu, sw = suu;
     pos = 0;
     for (int m = 0; m < nm; ++m) {
       const long long cnt = trk[mem[w][m]].n_clusters;
       for (long long j = lane; j < cnt; j += 32) {
-        double X, Y, Z;
+        F2 X, Y;
+        float Z;
         cluster_at(m, j, pos + j, &X, &Y, &Z);
-        const double u = X - mx, v = Y - my, ww = u * u + v * v;
-        suu += u * u;
-        suv += u * v;
-        svv += v * v;
-        su3 += u * ww;
-        sv3 += v * ww;
-        sw += ww;
+        const F2 u = f2_add(X, nmx), v = f2_add(Y, nmy);
+        const F2 uu = f2_mul(u, u), vv = f2_mul(v, v), ww = f2_add(uu, vv);
+        suu = f2_add(suu, uu);
+        suv = f2_add(suv, f2_mul(u, v));
+        svv = f2_add(svv, vv);
+        su3 = f2_add(su3, f2_mul(u, ww));
+        sv3 = f2_add(sv3, f2_mul(v, ww));
+        sw = f2_add(sw, ww);
       }
       pos += cnt;
     }
-    suu = warp_sum(suu);
-    suv = warp_sum(suv);
-    svv = warp_sum(svv);
-    su3 = warp_sum(su3);
-    sv3 = warp_sum(sv3);
-    sw = warp_sum(sw);
-    const double det = suu * svv - suv * suv;
+    const double Suu = f2_val(warp_sum(suu)), Suv = f2_val(warp_sum(suv)), Svv = f2_val(warp_sum(svv));
+    const double Su3 = f2_val(warp_sum(su3)), Sv3 = f2_val(warp_sum(sv3)), Sw = f2_val(warp_sum(sw));
+    const double det = Suu * Svv - Suv * Suv;
     if (!(fabs(det) > 0.0)) continue;
-    const double D = (-su3 * svv + sv3 * suv) / det, E = (-sv3 * suu + su3 * suv) / det, F = -sw / (double)n;
-    const double xc = mx - 0.5 * D, yc = my - 0.5 * E;
+    const double D = (-Su3 * Svv + Sv3 * Suv) / det, E = (-Sv3 * Suu + Su3 * Suv) / det, F = -Sw / (double)n;
+    const double xc = mxd - 0.5 * D, yc = myd - 0.5 * E;
     const double R = sqrt(0.25 * (D * D + E * E) - F);
-    const double k24 = 1.0 / (24.0 * R * R);
+    const F2 k24 = f2_from(1.0 / (24.0 * R * R));
+    const F2 nxin = f2_neg(xin), nyin = f2_neg(yin);
     // pass 3: z against the arc from the innermost cluster (chord c, arc c (1 + c^2 / 24 R^2))
-    double ss = 0, sz = 0, sss = 0, ssz = 0;
+    F2 ss = {0.f, 0.f}, sz = ss, sss = ss, ssz = ss;
     pos = 0;
     for (int m = 0; m < nm; ++m) {
       const long long cnt = trk[mem[w][m]].n_clusters;
       for (long long j = lane; j < cnt; j += 32) {
-        double X, Y, Z;
+        F2 X, Y;
+        float Z;
         cluster_at(m, j, pos + j, &X, &Y, &Z);
-        const double cx = X - xin, cy = Y - yin, c2 = cx * cx + cy * cy;
-        const double s = sqrt(c2) * (1.0 + c2 * k24);
-        ss += s;
-        sz += Z;
-        sss += s * s;
-        ssz += s * Z;
+        const F2 cx = f2_add(X, nxin), cy = f2_add(Y, nyin);
+        const F2 c2 = f2_add(f2_mul(cx, cx), f2_mul(cy, cy));
+        const F2 s = f2_mul(f2_sqrt(c2), f2_add({1.0f, 0.0f}, f2_mul(c2, k24)));
+        ss = f2_add(ss, s);
+        sz = f2_add(sz, {Z, 0.0f});
+        sss = f2_add(sss, f2_mul(s, s));
+        ssz = f2_add(ssz, f2_mul_f(s, Z));
       }
       pos += cnt;
     }
-    ss = warp_sum(ss);
-    sz = warp_sum(sz);
-    sss = warp_sum(sss);
-    ssz = warp_sum(ssz);
-    const double den = (double)n * sss - ss * ss;
-    const double tgl = den > 0.0 ? ((double)n * ssz - ss * sz) / den : 0.0;
+    const double Ss = f2_val(warp_sum(ss)), Sz = f2_val(warp_sum(sz));
+    const double Sss = f2_val(warp_sum(sss)), Ssz = f2_val(warp_sum(ssz));
+    const double den = (double)n * Sss - Ss * Ss;
+    const double tgl = den > 0.0 ? ((double)n * Ssz - Ss * Sz) / den : 0.0;
     if (lane == 0) {
       o[0] = xc;
       o[1] = yc;
       o[2] = R;
       o[3] = tgl;
-      o[4] = (sz - tgl * ss) / (double)n;
+      o[4] = (Sz - tgl * Ss) / (double)n;
       o[5] = (double)n;
       o[6] = (double)nm;
     }
