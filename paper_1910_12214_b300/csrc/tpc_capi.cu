@@ -1585,10 +1585,11 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
       nb[2 * i + 1] = find(c->h_item_event[i], side * 18 + (k + 17) % 18);
     }
   }
-  // items of the same event and side (for the looper legs)
+  // segments: the items of one event and side (at most 18 listed), for the tan(lambda)-sorted
+  // candidate lists of the merger and the looper-leg search
   const bool legs = leg_partner || leg;
-  std::vector<int> side_items(legs ? 18 * (size_t)I : 0, -1);
-  if (legs) {
+  std::vector<int> item_seg(I, -1), seg_items;
+  {
     std::vector<std::pair<uint64_t, int>> es(I);
     for (int i = 0; i < I; ++i)
       es[i] = {((uint64_t)c->h_item_event[i] << 1) | (c->h_item_sector[i] >= 18 ? 1u : 0u), i};
@@ -1596,15 +1597,20 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
     for (size_t lo = 0; lo < es.size();) {
       size_t hi = lo;
       while (hi < es.size() && es[hi].first == es[lo].first) ++hi;
-      for (size_t k = lo; k < hi; ++k)
-        for (size_t j = lo, m = 0; j < hi && m < 18; ++j, ++m) side_items[18 * (size_t)es[k].second + m] = es[j].second;
+      const size_t sg = seg_items.size() / 19;
+      seg_items.resize(seg_items.size() + 19, -1);
+      for (size_t j = lo, m = 0; j < hi && m < 18; ++j, ++m) seg_items[19 * sg + m] = es[j].second;
+      seg_items[19 * sg + 18] = (int)(hi - lo);
+      for (size_t k = lo; k < hi; ++k) item_seg[es[k].second] = (int)sg;
       lo = hi;
     }
   }
-  int* d_nb = (int*)cmp_buffer(c, 35, 8 * (size_t)I + (legs ? 72 * (size_t)I : 0));
+  const int S = (int)(seg_items.size() / 19);
+  // [nb 2I][item_seg I][seg_items 19S] from the host, then [seg_n S][seg_off S + 1][seg_ok S] on the device
+  int* d_nb = (int*)cmp_buffer(c, 35, 4 * (3 * (size_t)I + 22 * (size_t)S + 1));
   int* d_lbest = (int*)cmp_buffer(c, 40, 4 * (size_t)std::max(nt, 1ll));
   int* d_first = (int*)cmp_buffer(c, 36, 4 * (size_t)(I + 1));
-  double* d_geo = (double*)cmp_buffer(c, 37, (8 * 12 + 16 + 32) * (size_t)std::max(nt, 1ll));
+  double* d_geo = (double*)cmp_buffer(c, 37, (8 * 12 + 16 + 32 + 64 + 4 + 4) * (size_t)std::max(nt, 1ll));
   int* d_best = (int*)cmp_buffer(c, 38, 8 * (size_t)std::max(nt, 1ll));
   // outputs: the caller's device arrays, or staging for host arrays
   uint8_t* st = nullptr;
@@ -1615,8 +1621,10 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
   if (!d_nb || !d_first || !d_geo || !d_best || !d_lbest || (!on_device && !st))
     return fail(c, TPC_ERR_OOM, "merge buffers");
   if ((e = cudaMemcpyAsync(d_nb, nb.data(), 8 * (size_t)I, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
-      (legs && (e = cudaMemcpyAsync(d_nb + 2 * I, side_items.data(), 72 * (size_t)I, cudaMemcpyHostToDevice,
-                                    c->stream)) != cudaSuccess))
+      (e = cudaMemcpyAsync(d_nb + 2 * (size_t)I, item_seg.data(), 4 * (size_t)I, cudaMemcpyHostToDevice,
+                           c->stream)) != cudaSuccess ||
+      (S && (e = cudaMemcpyAsync(d_nb + 3 * (size_t)I, seg_items.data(), 4 * seg_items.size(),
+                                 cudaMemcpyHostToDevice, c->stream)) != cudaSuccess))
     return cuda_fail(c, e, "neighbour table");
   unsigned int err0 = 0;
   if ((e = cudaMemcpyAsync(&err0, c->b.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
@@ -1639,11 +1647,20 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
   a.geo = d_geo;
   a.pre = (float4*)(d_geo + 12 * (size_t)std::max(nt, 1ll));  // 16-byte aligned: 96 bytes per track before it
   a.geo32 = a.pre + std::max(nt, 1ll);
+  a.geof2 = a.geo32 + 2 * std::max(nt, 1ll);
+  a.sidx = (int*)(a.geof2 + 4 * std::max(nt, 1ll));
+  a.skey = (unsigned*)(a.sidx + std::max(nt, 1ll));
+  a.item_seg = d_nb + 2 * (size_t)I;
+  a.seg_items = d_nb + 3 * (size_t)I;
+  a.S = S;
+  a.seg_n = d_nb + 3 * (size_t)I + 19 * (size_t)S;
+  a.seg_off = a.seg_n + S;
+  a.seg_ok = a.seg_off + S + 1;
   a.best = d_best;
   a.link = on_device ? link : (int*)(st + o_link);
   a.group = on_device ? group : (int*)(st + o_group);
   a.fit = on_device ? fit : (double*)(st + o_fit);
-  a.side_items = legs ? d_nb + 2 * I : nullptr;
+  a.legs = legs ? 1 : 0;
   a.lbest = d_lbest;
   // the partner array is needed whenever legs are asked for (the leg flags derive from it)
   a.partner = !legs ? nullptr : (on_device && leg_partner ? leg_partner : (int*)(st ? st + o_part : nullptr));

@@ -282,7 +282,16 @@ struct MrgArgs {
   int* link;                  // [n_trk][2] output
   int* group;                 // [n_trk] output
   double* fit;                // [n_trk][7] output (group roots)
-  const int* side_items;      // [I][18] the items of the same event and side (-1 padded), null: no legs
+  const int* item_seg;        // [I] segment (event and side) of every item
+  const int* seg_items;       // [S][19] the segment's items (at most 18, -1 padded), then its item count
+  int S;                      // segments
+  int legs;                   // pair looper legs
+  int* seg_n;                 // [S] tracks of the segment
+  int* seg_off;               // [S + 1] offsets of the sorted lists
+  int* seg_ok;                // [S] 1: sorted list built (else the candidates are scanned item by item)
+  unsigned* skey;             // [n_trk] order-preserving tan(lambda) bits, ascending per segment
+  int* sidx;                  // [n_trk] the tracks in the same order
+  float4* geof2;              // [n_trk][4] float-float circle and reference point for the compatibility tests
   int* lbest;                 // [n_trk] best other-leg candidate
   int* partner;               // [n_trk] output: the other leg of a looper, -1 none
   uint8_t* leg;               // [n_trk] output: 1 for a secondary leg

@@ -1110,200 +1110,9 @@ cudaError_t cmp_layout(const CmpPlane* planes, int n_planes, const int* stream_p
 namespace {
 
 constexpr double MRG_WEDGE = 2.0 * 3.14159265358979323846 / 18.0;
-enum { G_OK, G_XC, G_YC, G_R, G_X, G_Y, G_RAD, G_Z, G_TGL, G_QPT, G_VQ, G_SIGN, G_N };
 
-__global__ void k_mrg_geom(const __grid_constant__ MrgArgs a) {
-  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride) {
-    const tpc_track_t T = trk[t];
-    double* g = a.geo + G_N * t;
-    const bool range_ok = T.item < (uint32_t)a.I && (long long)T.first_cluster + T.n_clusters <= a.n_ids;
-    if (!range_ok || (t > 0 && trk[t - 1].item > T.item)) atomicOr(a.err, TPC_DERR_BAD_TRACK);
-    const bool ok = fabsf(T.qpt) >= 1e-4f && range_ok;
-    g[G_OK] = ok ? 1.0 : 0.0;
-    a.pre[t] = make_float4(ok ? T.tgl : __int_as_float(0x7fc00000), T.qpt, sqrtf(fmaxf(T.cov[14], 0.f)),
-                           T.qpt > 0.f ? 1.f : -1.f);
-    if (!ok) {
-      a.geo32[2 * t] = make_float4(0.f, 0.f, 0.f, 0.f);
-      a.geo32[2 * t + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
-      continue;
-    }
-    const int s = (int)a.item_sector[T.item];
-    const double ang = (double)(s % 18) * MRG_WEDGE, ca = cos(ang), sa = sin(ang);
-    const double kap = a.kB * (double)T.qpt;
-    const double snp = T.snp, csp = sqrt(fmax(0.0, 1.0 - snp * snp));
-    const double lx = (double)T.x_ref + snp / kap, ly = (double)T.y - csp / kap;
-    g[G_XC] = lx * ca - ly * sa;
-    g[G_YC] = lx * sa + ly * ca;
-    g[G_R] = 1.0 / fabs(kap);
-    const double X = (double)T.x_ref * ca - (double)T.y * sa, Y = (double)T.x_ref * sa + (double)T.y * ca;
-    g[G_X] = X;
-    g[G_Y] = Y;
-    g[G_RAD] = hypot(X, Y);
-    g[G_Z] = T.z;
-    g[G_TGL] = T.tgl;
-    g[G_QPT] = T.qpt;
-    g[G_VQ] = fmax(0.0, (double)T.cov[14]);
-    g[G_SIGN] = T.qpt > 0.f ? 1.0 : -1.0;
-    // the same quantities rounded to FP32 (var q/pT is a float: exact) for the prefilters
-    a.geo32[2 * t] = make_float4((float)g[G_XC], (float)g[G_YC], (float)g[G_R], (float)g[G_VQ]);
-    a.geo32[2 * t + 1] = make_float4((float)X, (float)Y, T.z, (float)g[G_RAD]);
-  }
-}
-
-// first track of every item (tracks are sorted by item)
-__global__ void k_mrg_item_first(const __grid_constant__ MrgArgs a) {
-  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= a.I; i += stride) {
-    long long lo = 0, hi = a.n_trk;  // first t with item >= i
-    while (lo < hi) {
-      const long long m = (lo + hi) >> 1;
-      if (trk[m].item < (uint32_t)i)
-        lo = m + 1;
-      else
-        hi = m;
-    }
-    a.item_first[i] = (int)lo;
-  }
-}
-
-__device__ __forceinline__ bool mrg_compatible(const double* A, const double* B, double kB, double* score) {
-  // the cheap tests first (they reject almost every wrong pair): tan(lambda), then the curvature chi2
-  const double dt = fabs(A[G_TGL] - B[G_TGL]);
-  if (!(dt <= 0.02)) return false;
-  const double dq = A[G_QPT] - B[G_QPT], vsum = fmax(A[G_VQ] + B[G_VQ], 1e-30);
-  if (!(dq * dq <= 16.0 * vsum)) return false;
-  const double chi2 = dq * dq / vsum;
-  const double* ref = A[G_VQ] <= B[G_VQ] ? A : B;
-  const double* oth = A[G_VQ] <= B[G_VQ] ? B : A;
-  const double L = hypot(oth[G_X] - ref[G_X], oth[G_Y] - ref[G_Y]);
-  const double d = fabs(hypot(oth[G_X] - ref[G_XC], oth[G_Y] - ref[G_YC]) - ref[G_R]);
-  const double dlim = 1.0 + 3.0 * kB * sqrt(ref[G_VQ]) * L * L;
-  const double* in = A[G_RAD] <= B[G_RAD] ? A : B;
-  const double* out = A[G_RAD] <= B[G_RAD] ? B : A;
-  const double c = hypot(out[G_X] - in[G_X], out[G_Y] - in[G_Y]);
-  const double Rb = 0.5 * (A[G_R] + B[G_R]);
-  const double arc = c * (1.0 + c * c / (24.0 * Rb * Rb));
-  const double dz = fabs(out[G_Z] - (in[G_Z] + in[G_TGL] * arc));
-  *score = chi2 / 16.0 + d / dlim + dt / 0.02 + dz / 2.0;
-  return d <= dlim && dz <= 2.0;
-}
-
-// FP32 form of the continuity and dz tests of mrg_compatible that never rejects
-// a pair the FP64 tests accept.  Inputs are the FP64 values rounded to FP32
-// (relative error u = 2^-24 each).  With M the sum of the magnitudes entering a
-// difference, a rounded difference is off by at most 2u M, a rounded hypot by
-// 5u M, and the distance |h - R| by 7u (M + R); the limit 1 + 3 kB sqrt(V) L^2
-// by 8u of its value plus 8u kB sqrt(V) M^2; dz by 8u times the magnitudes of
-// its terms.  The margins below are about 20 times these bounds.  The reference
-// (smaller var q/pT) is chosen alike in both precisions because the variance is
-// a float; the inner track (smaller radius) too unless the rounded radii are
-// equal, where the dz test is left to FP64.  A NaN or infinity passes.
-__device__ __forceinline__ bool mrg_maybe_compatible(const float4* A32, const float4* B32, float tgl_a,
-                                                     float tgl_b, float kB) {
-  constexpr float e = 1e-5f;
-  const float4 a0 = A32[0], a1 = A32[1], b0 = B32[0], b1 = B32[1];
-  const bool a_ref = a0.w <= b0.w;
-  const float4 r0 = a_ref ? a0 : b0, r1 = a_ref ? a1 : b1, o1 = a_ref ? b1 : a1;
-  const float dxl = o1.x - r1.x, dyl = o1.y - r1.y;
-  const float L2 = fmaf(dxl, dxl, dyl * dyl);
-  const float ex = o1.x - r0.x, ey = o1.y - r0.y;
-  const float d = fabsf(sqrtf(fmaf(ex, ex, ey * ey)) - r0.z);
-  const float kv = 3.0f * kB * sqrtf(r0.w);
-  const float Q = fabsf(o1.x) + fabsf(o1.y) + fabsf(r1.x) + fabsf(r1.y);
-  const float Mc = fabsf(o1.x) + fabsf(o1.y) + fabsf(r0.x) + fabsf(r0.y) + r0.z;
-  const float dlim = fmaf(kv, L2, 1.0f);
-  if (d > dlim * (1.0f + e) + e * (kv * Q * Q + Mc) + 1e-6f) return false;
-  if (a1.w == b1.w) return true;
-  const bool a_in = a1.w < b1.w;
-  const float4 in1 = a_in ? a1 : b1, out1 = a_in ? b1 : a1;
-  const float tin = a_in ? tgl_a : tgl_b;
-  const float cx = out1.x - in1.x, cy = out1.y - in1.y;
-  const float c = sqrtf(fmaf(cx, cx, cy * cy));
-  const float Rb = 0.5f * (a0.z + b0.z);
-  const float t = c * c / (24.0f * Rb * Rb);
-  const float arc = c * (1.0f + t);
-  const float dz = fabsf(out1.z - fmaf(tin, arc, in1.z));
-  const float Qz = fabsf(in1.x) + fabsf(in1.y) + fabsf(out1.x) + fabsf(out1.y);
-  return !(dz > 2.0f + e * (fabsf(out1.z) + fabsf(in1.z) + fabsf(tin) * (arc + Qz) * (2.0f + 4.0f * t)) + 1e-6f);
-}
-
-// one warp per track: the best compatible candidate in sector k+1 (d = 0) and k-1 (d = 1)
-__global__ void k_mrg_best(const __grid_constant__ MrgArgs a) {
-  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
-  const int lane = threadIdx.x & 31;
-  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
-  for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_trk; t += nw) {
-    const double* A = a.geo + G_N * t;
-    const bool ok = A[G_OK] != 0.0;
-    const float kBf = (float)a.kB;
-    for (int d = 0; d < 2; ++d) {
-      const int nb = ok ? a.nb_item[2 * trk[t].item + d] : -1;
-      double bs = 0.0;
-      long long bi = -1;
-      const float4 pa = a.pre[t];
-      if (nb >= 0)
-        for (long long b = a.item_first[nb] + lane; b < a.item_first[nb + 1]; b += 32) {
-          // FP32 prefilter with margins wider than any FP32 rounding of the FP64 tests
-          // (a NaN tan lambda marks a track without a circle: every comparison fails)
-          const float4 pb = a.pre[b];
-          if (!(fabsf(pa.x - pb.x) <= 0.0201f) || pa.w != pb.w) continue;
-          const float dq = pa.y - pb.y, sq = pa.z * pa.z + pb.z * pb.z;
-          if (!(dq * dq <= 16.2f * sq + 1e-28f)) continue;
-          if (!mrg_maybe_compatible(a.geo32 + 2 * t, a.geo32 + 2 * b, pa.x, pb.x, kBf)) continue;
-          const double* B = a.geo + G_N * b;
-          if (B[G_OK] == 0.0 || B[G_SIGN] != A[G_SIGN]) continue;
-          double sc;
-          if (!mrg_compatible(A, B, a.kB, &sc)) continue;
-          if (bi < 0 || sc < bs) {  // lanes visit candidates in increasing index: ties keep the smaller
-            bs = sc;
-            bi = b;
-          }
-        }
-      for (int o = 16; o; o >>= 1) {  // smallest (score, index)
-        const double os = __shfl_xor_sync(0xffffffffu, bs, o);
-        const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
-        if (oi >= 0 && (bi < 0 || os < bs || (os == bs && oi < bi))) {
-          bs = os;
-          bi = oi;
-        }
-      }
-      if (lane == 0) a.best[2 * t + d] = (int)bi;
-    }
-  }
-}
-
-__global__ void k_mrg_link(const __grid_constant__ MrgArgs a) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride)
-    for (int d = 0; d < 2; ++d) {
-      const int b = a.best[2 * t + d];
-      a.link[2 * t + d] = (b >= 0 && a.best[2 * b + (1 - d)] == (int)t) ? b : -1;
-    }
-}
-
-// the group of a track: the smallest index on its path of links (at most 18
-// steps each way: one track per sector of a side)
-__global__ void k_mrg_group(const __grid_constant__ MrgArgs a) {
-  const long long stride = (long long)gridDim.x * blockDim.x;
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride) {
-    int m = (int)t;
-    for (int d = 0; d < 2; ++d) {
-      int cur = (int)t;
-      for (int step = 0; step < 18; ++step) {
-        const int nxt = a.link[2 * cur + d];
-        if (nxt < 0) break;
-        m = min(m, nxt);
-        cur = nxt;
-      }
-    }
-    a.group[t] = m;
-  }
-}
-
-// Float-float ("double-float") numbers for the refit's per-cluster sums: a
+// Float-float ("double-float") numbers for the compatibility tests and the
+// refit's per-cluster sums: a
 // value is hi + lo with |lo| <= ulp(hi) / 2, a 48-bit significand computed on
 // the FP32 pipe, which the B300 has about 60 times wider than the FP64 one.
 // The error-free transformations are Knuth's TwoSum, Dekker's Fast2Sum (valid
@@ -1356,6 +1165,15 @@ __device__ __forceinline__ F2 f2_sqrt(F2 a) {
   return fast_two_sum(x, __fmul_rn(r, __fdividef(0.5f, x)));
 }
 
+// float-float form of a double known at compile time
+struct F2c {
+  float hi, lo;
+  constexpr F2c(double v) : hi((float)v), lo((float)(v - (double)(float)v)) {}
+};
+constexpr F2c kF2_002(0.02), kF2_1em30(1e-30);
+
+__device__ __forceinline__ F2 f2c(F2c c) { return {c.hi, c.lo}; }
+
 __device__ __forceinline__ F2 f2_from(double v) {
   const float hi = (float)v;
   return {hi, (float)(v - (double)hi)};
@@ -1365,12 +1183,418 @@ __device__ __forceinline__ double f2_val(F2 a) { return (double)a.hi + (double)a
 
 __device__ __forceinline__ bool f2_less(F2 a, F2 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 
+__device__ __forceinline__ bool f2_le(F2 a, F2 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
+
+__device__ __forceinline__ F2 f2_abs(F2 a) { return a.hi < 0.0f ? f2_neg(a) : a; }
+
+// quotient by long division: q1 = a / b in FP32, the remainder a - q1 b formed
+// in float-float, q2 = remainder / b
+__device__ __forceinline__ F2 f2_div(F2 a, F2 b) {
+  const float q1 = __fdiv_rn(a.hi, b.hi);
+  const F2 r = f2_add(a, f2_neg(f2_mul_f(b, q1)));
+  return fast_two_sum(q1, __fdiv_rn(r.hi, b.hi));
+}
+
 __device__ __forceinline__ F2 warp_sum(F2 v) {
   for (int o = 16; o; o >>= 1) {
     const F2 w = {__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
     v = f2_add(v, w);
   }
   return v;
+}
+
+enum { G_OK, G_XC, G_YC, G_R, G_X, G_Y, G_RAD, G_Z, G_TGL, G_QPT, G_VQ, G_SIGN, G_N };
+
+__global__ void k_mrg_geom(const __grid_constant__ MrgArgs a) {
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride) {
+    const tpc_track_t T = trk[t];
+    double* g = a.geo + G_N * t;
+    const bool range_ok = T.item < (uint32_t)a.I && (long long)T.first_cluster + T.n_clusters <= a.n_ids;
+    if (!range_ok || (t > 0 && trk[t - 1].item > T.item)) atomicOr(a.err, TPC_DERR_BAD_TRACK);
+    const bool ok = fabsf(T.qpt) >= 1e-4f && range_ok;
+    g[G_OK] = ok ? 1.0 : 0.0;
+    a.pre[t] = make_float4(ok ? T.tgl : __int_as_float(0x7fc00000), T.qpt, sqrtf(fmaxf(T.cov[14], 0.f)),
+                           T.qpt > 0.f ? 1.f : -1.f);
+    if (!ok) {
+      a.geo32[2 * t] = make_float4(0.f, 0.f, 0.f, 0.f);
+      a.geo32[2 * t + 1] = make_float4(0.f, 0.f, 0.f, 0.f);
+      for (int k = 0; k < 4; ++k) a.geof2[4 * t + k] = make_float4(0.f, 0.f, 0.f, 0.f);
+      continue;
+    }
+    const int s = (int)a.item_sector[T.item];
+    const double ang = (double)(s % 18) * MRG_WEDGE, ca = cos(ang), sa = sin(ang);
+    const double kap = a.kB * (double)T.qpt;
+    const double snp = T.snp, csp = sqrt(fmax(0.0, 1.0 - snp * snp));
+    const double lx = (double)T.x_ref + snp / kap, ly = (double)T.y - csp / kap;
+    g[G_XC] = lx * ca - ly * sa;
+    g[G_YC] = lx * sa + ly * ca;
+    g[G_R] = 1.0 / fabs(kap);
+    const double X = (double)T.x_ref * ca - (double)T.y * sa, Y = (double)T.x_ref * sa + (double)T.y * ca;
+    g[G_X] = X;
+    g[G_Y] = Y;
+    g[G_RAD] = hypot(X, Y);
+    g[G_Z] = T.z;
+    g[G_TGL] = T.tgl;
+    g[G_QPT] = T.qpt;
+    g[G_VQ] = fmax(0.0, (double)T.cov[14]);
+    g[G_SIGN] = T.qpt > 0.f ? 1.0 : -1.0;
+    // the same quantities rounded to FP32 (var q/pT is a float: exact) for the prefilters
+    a.geo32[2 * t] = make_float4((float)g[G_XC], (float)g[G_YC], (float)g[G_R], (float)g[G_VQ]);
+    a.geo32[2 * t + 1] = make_float4((float)X, (float)Y, T.z, (float)g[G_RAD]);
+    // and as float-float (z, tan lambda, q/pT and var q/pT are floats)
+    const F2 fxc = f2_from(g[G_XC]), fyc = f2_from(g[G_YC]), fr = f2_from(g[G_R]), fx = f2_from(X), fy = f2_from(Y);
+    a.geof2[4 * t] = make_float4(fxc.hi, fxc.lo, fyc.hi, fyc.lo);
+    a.geof2[4 * t + 1] = make_float4(fr.hi, fr.lo, fx.hi, fx.lo);
+    a.geof2[4 * t + 2] = make_float4(fy.hi, fy.lo, T.z, T.tgl);
+    a.geof2[4 * t + 3] = make_float4(T.qpt, fmaxf(0.f, T.cov[14]), 0.f, 0.f);
+  }
+}
+
+// first track of every item (tracks are sorted by item)
+__global__ void k_mrg_item_first(const __grid_constant__ MrgArgs a) {
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i <= a.I; i += stride) {
+    long long lo = 0, hi = a.n_trk;  // first t with item >= i
+    while (lo < hi) {
+      const long long m = (lo + hi) >> 1;
+      if (trk[m].item < (uint32_t)i)
+        lo = m + 1;
+      else
+        hi = m;
+    }
+    a.item_first[i] = (int)lo;
+  }
+}
+
+// a non-negative score as an integer key: the bits of a non-negative double
+// order like its value, and integer compares keep the reductions off the FP64 pipe
+__device__ __forceinline__ unsigned long long score_key(double sc) { return (unsigned long long)__double_as_longlong(sc); }
+
+// The compatibility tests of R-28 and the score of a compatible pair, in
+// float-float on the per-track records (geof2): a few 2^-46 relative, so every
+// decision equals the exact one except within about 1e-13 of a limit.
+struct TrkF2 {
+  F2 xc, yc, r, x, y;
+  float z, tgl, qpt, vq;
+};
+
+__device__ __forceinline__ TrkF2 load_trk_f2(const float4* g) {
+  const float4 g0 = g[0], g1 = g[1], g2 = g[2], g3 = g[3];
+  return {{g0.x, g0.y}, {g0.z, g0.w}, {g1.x, g1.y}, {g1.z, g1.w}, {g2.x, g2.y}, g2.z, g2.w, g3.x, g3.y};
+}
+
+__device__ __forceinline__ F2 f2_hypot(F2 dx, F2 dy) { return f2_sqrt(f2_add(f2_mul(dx, dx), f2_mul(dy, dy))); }
+
+__device__ __forceinline__ bool mrg_compatible(const TrkF2& A, const TrkF2& B, bool a_inner, F2 kB3,
+                                               unsigned long long* score) {
+  // the cheap tests first (they reject almost every wrong pair): tan(lambda), then the curvature chi2
+  const F2 dt = f2_abs(two_sum(A.tgl, -B.tgl));
+  if (!f2_le(dt, f2c(kF2_002))) return false;
+  const F2 dq = two_sum(A.qpt, -B.qpt);
+  F2 vsum = two_sum(A.vq, B.vq);
+  if (f2_less(vsum, f2c(kF2_1em30))) vsum = f2c(kF2_1em30);
+  const F2 dq2 = f2_mul(dq, dq);
+  if (!f2_le(dq2, f2_mul_f(vsum, 16.0f))) return false;
+  const F2 chi2 = f2_div(dq2, vsum);
+  const TrkF2& ref = A.vq <= B.vq ? A : B;
+  const TrkF2& oth = A.vq <= B.vq ? B : A;
+  const F2 L = f2_hypot(f2_add(oth.x, f2_neg(ref.x)), f2_add(oth.y, f2_neg(ref.y)));
+  const F2 d = f2_abs(f2_add(f2_hypot(f2_add(oth.x, f2_neg(ref.xc)), f2_add(oth.y, f2_neg(ref.yc))), f2_neg(ref.r)));
+  const F2 dlim = f2_add({1.0f, 0.0f}, f2_mul(f2_mul(kB3, f2_sqrt({ref.vq, 0.0f})), f2_mul(L, L)));
+  const TrkF2& in = a_inner ? A : B;
+  const TrkF2& out = a_inner ? B : A;
+  const F2 c = f2_hypot(f2_add(out.x, f2_neg(in.x)), f2_add(out.y, f2_neg(in.y)));
+  const F2 Rb = f2_mul_f(f2_add(A.r, B.r), 0.5f);
+  const F2 arc = f2_mul(c, f2_add({1.0f, 0.0f}, f2_div(f2_mul(c, c), f2_mul_f(f2_mul(Rb, Rb), 24.0f))));
+  const F2 dz = f2_abs(f2_add({out.z, 0.0f}, f2_neg(f2_add({in.z, 0.0f}, f2_mul_f(arc, in.tgl)))));
+  const F2 sc = f2_add(f2_add(f2_add(f2_mul_f(chi2, 0.0625f), f2_div(d, dlim)), f2_div(dt, f2c(kF2_002))),
+                       f2_mul_f(dz, 0.5f));
+  *score = score_key(f2_val(sc));
+  return f2_le(d, dlim) && f2_le(dz, {2.0f, 0.0f});
+}
+
+// FP32 form of the continuity and dz tests of mrg_compatible that never rejects
+// a pair the FP64 tests accept.  Inputs are the FP64 values rounded to FP32
+// (relative error u = 2^-24 each).  With M the sum of the magnitudes entering a
+// difference, a rounded difference is off by at most 2u M, a rounded hypot by
+// 5u M, and the distance |h - R| by 7u (M + R); the limit 1 + 3 kB sqrt(V) L^2
+// by 8u of its value plus 8u kB sqrt(V) M^2; dz by 8u times the magnitudes of
+// its terms.  The margins below are about 20 times these bounds.  The reference
+// (smaller var q/pT) is chosen alike in both precisions because the variance is
+// a float; the inner track (smaller radius) too unless the rounded radii are
+// equal, where the dz test is left to FP64.  A NaN or infinity passes.
+__device__ __forceinline__ bool mrg_maybe_compatible(const float4* A32, const float4* B32, float tgl_a,
+                                                     float tgl_b, float kB) {
+  constexpr float e = 1e-5f;
+  const float4 a0 = A32[0], a1 = A32[1], b0 = B32[0], b1 = B32[1];
+  const bool a_ref = a0.w <= b0.w;
+  const float4 r0 = a_ref ? a0 : b0, r1 = a_ref ? a1 : b1, o1 = a_ref ? b1 : a1;
+  const float dxl = o1.x - r1.x, dyl = o1.y - r1.y;
+  const float L2 = fmaf(dxl, dxl, dyl * dyl);
+  const float ex = o1.x - r0.x, ey = o1.y - r0.y;
+  const float d = fabsf(sqrtf(fmaf(ex, ex, ey * ey)) - r0.z);
+  const float kv = 3.0f * kB * sqrtf(r0.w);
+  const float Q = fabsf(o1.x) + fabsf(o1.y) + fabsf(r1.x) + fabsf(r1.y);
+  const float Mc = fabsf(o1.x) + fabsf(o1.y) + fabsf(r0.x) + fabsf(r0.y) + r0.z;
+  const float dlim = fmaf(kv, L2, 1.0f);
+  if (d > dlim * (1.0f + e) + e * (kv * Q * Q + Mc) + 1e-6f) return false;
+  if (a1.w == b1.w) return true;
+  const bool a_in = a1.w < b1.w;
+  const float4 in1 = a_in ? a1 : b1, out1 = a_in ? b1 : a1;
+  const float tin = a_in ? tgl_a : tgl_b;
+  const float cx = out1.x - in1.x, cy = out1.y - in1.y;
+  const float c = sqrtf(fmaf(cx, cx, cy * cy));
+  const float Rb = 0.5f * (a0.z + b0.z);
+  const float t = c * c / (24.0f * Rb * Rb);
+  const float arc = c * (1.0f + t);
+  const float dz = fabsf(out1.z - fmaf(tin, arc, in1.z));
+  const float Qz = fabsf(in1.x) + fabsf(in1.y) + fabsf(out1.x) + fabsf(out1.y);
+  return !(dz > 2.0f + e * (fabsf(out1.z) + fabsf(in1.z) + fabsf(tin) * (arc + Qz) * (2.0f + 4.0f * t)) + 1e-6f);
+}
+
+// Tan(lambda)-sorted candidate lists, one per segment (the items of one event
+// and side): every prefilter asks for |tan(lambda_a) -+ tan(lambda_b)| <= 0.0201,
+// so a window of the sorted list holds every candidate that can pass, and the
+// scans visit a few percent of the segment's tracks.  The selections are minima
+// of (score, index), so the order of the visits does not change them.
+constexpr int MRG_SORT_CAP = 16384;  // tracks of a segment sorted in shared memory (more: item-by-item scans)
+
+__device__ __forceinline__ unsigned tgl_key(float v) {  // order-preserving bits; every NaN last
+  const unsigned u = __float_as_uint(v);
+  if (v != v) return 0xffffffffu;
+  return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__global__ void k_mrg_seg_count(const __grid_constant__ MrgArgs a) {
+  const int stride = gridDim.x * blockDim.x;
+  for (int sg = blockIdx.x * blockDim.x + threadIdx.x; sg < a.S; sg += stride) {
+    const int* it = a.seg_items + 19 * (long long)sg;
+    int n = 0;
+    for (int k = 0; k < 18; ++k)
+      if (it[k] >= 0) n += a.item_first[it[k] + 1] - a.item_first[it[k]];
+    a.seg_n[sg] = n;
+  }
+}
+
+__global__ void __launch_bounds__(1024) k_mrg_seg_scan(const __grid_constant__ MrgArgs a) {
+  __shared__ int wsum[32];
+  __shared__ int carry;
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (threadIdx.x == 0) carry = 0;
+  __syncthreads();
+  for (int base = 0; base < a.S; base += 1024) {
+    const int i = base + (int)threadIdx.x;
+    const int v = i < a.S ? a.seg_n[i] : 0;
+    int x = v;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) wsum[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+      int w = wsum[lane];
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, w, o);
+        if (lane >= o) w += y;
+      }
+      wsum[lane] = w;
+    }
+    __syncthreads();
+    const int incl = x + (wid ? wsum[wid - 1] : 0) + carry;
+    if (i < a.S) a.seg_off[i] = incl - v;
+    __syncthreads();
+    if (threadIdx.x == 1023) carry = incl;
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) a.seg_off[a.S] = carry;
+}
+
+// one block per segment: (key, track) pairs sorted ascending by a bitonic network in shared memory
+__global__ void __launch_bounds__(1024) k_mrg_seg_sort(const __grid_constant__ MrgArgs a) {
+  extern __shared__ unsigned long long sk[];
+  __shared__ int s_first[18], s_pos[19];
+  const int sg = blockIdx.x;
+  const int* it = a.seg_items + 19 * (long long)sg;
+  const int n = a.seg_n[sg];
+  const bool ok = n <= MRG_SORT_CAP && it[18] <= 18;
+  if (threadIdx.x == 0) a.seg_ok[sg] = ok ? 1 : 0;
+  if (!ok || n == 0) return;
+  if (threadIdx.x < 32) {  // the listed items' track ranges and their offsets in the list
+    const int k = threadIdx.x;
+    const int item = k < 18 ? it[k] : -1;
+    const int f = item >= 0 ? a.item_first[item] : 0, cnt = item >= 0 ? a.item_first[item + 1] - f : 0;
+    int incl = cnt;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(0xffffffffu, incl, o);
+      if (k >= o) incl += y;
+    }
+    if (k < 18) {
+      s_first[k] = f;
+      s_pos[k] = incl - cnt;
+    }
+    if (k == 17) s_pos[18] = incl;
+  }
+  __syncthreads();
+  int P = 1;
+  while (P < n) P <<= 1;
+  for (int k = 0; k < 18; ++k) {
+    const int f = s_first[k], pos = s_pos[k], cnt = s_pos[k + 1] - pos;
+    for (int j = threadIdx.x; j < cnt; j += blockDim.x)
+      sk[pos + j] = ((unsigned long long)tgl_key(a.pre[f + j].x) << 32) | (unsigned)(f + j);
+  }
+  for (int p = n + threadIdx.x; p < P; p += blockDim.x) sk[p] = ~0ull;
+  for (int k = 2; k <= P; k <<= 1)
+    for (int j = k >> 1; j > 0; j >>= 1) {
+      __syncthreads();
+      for (int i = threadIdx.x; i < P; i += blockDim.x) {
+        const int l = i ^ j;
+        if (l > i) {
+          const unsigned long long x = sk[i], y = sk[l];
+          if ((x > y) == ((i & k) == 0)) {
+            sk[i] = y;
+            sk[l] = x;
+          }
+        }
+      }
+    }
+  __syncthreads();
+  const int off = a.seg_off[sg];
+  for (int p = threadIdx.x; p < n; p += blockDim.x) {
+    const unsigned long long x = sk[p];
+    a.skey[off + p] = (unsigned)(x >> 32);
+    a.sidx[off + p] = (int)(unsigned)x;
+  }
+}
+
+// first position of keys[0, n) (ascending) holding a key >= target, found by the
+// whole warp 32 ways at a time
+__device__ __forceinline__ int warp_lower_bound(const unsigned* keys, int n, unsigned target) {
+  const int lane = threadIdx.x & 31;
+  int lo = 0, hi = n;  // the answer lies in [lo, hi]
+  while (hi - lo > 32) {
+    const int step = (hi - lo + 31) >> 5;
+    const int p = lo + lane * step;
+    const int c = __popc(__ballot_sync(0xffffffffu, p < hi && keys[p] < target));
+    if (c == 0) return lo;
+    const int nlo = lo + (c - 1) * step + 1;
+    hi = min(hi, lo + c * step);
+    lo = nlo;
+  }
+  const int p = lo + lane;
+  return lo + __popc(__ballot_sync(0xffffffffu, p < hi && keys[p] < target));
+}
+
+// lane-local then warp-wide minimum of (score key, index)
+__device__ __forceinline__ void keep_best(unsigned long long sc, long long b, unsigned long long* bs, long long* bi) {
+  if (*bi < 0 || sc < *bs || (sc == *bs && b < *bi)) {
+    *bs = sc;
+    *bi = b;
+  }
+}
+
+__device__ __forceinline__ long long warp_best(unsigned long long bs, long long bi) {
+  for (int o = 16; o; o >>= 1) {
+    const unsigned long long os = __shfl_xor_sync(0xffffffffu, bs, o);
+    const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (oi >= 0) keep_best(os, oi, &bs, &bi);
+  }
+  return bi;
+}
+
+// one warp per track: the best compatible candidate in sector k+1 (d = 0) and k-1 (d = 1)
+__global__ void k_mrg_best(const __grid_constant__ MrgArgs a) {
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const int lane = threadIdx.x & 31;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const float kBf = (float)a.kB;
+  for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_trk; t += nw) {
+    const double* A = a.geo + G_N * t;
+    const bool ok = A[G_OK] != 0.0;
+    const int item = (int)trk[t].item;
+    const float4 pa = a.pre[t];
+    const int nb0 = ok ? a.nb_item[2 * item] : -1, nb1 = ok ? a.nb_item[2 * item + 1] : -1;
+    unsigned long long bs[2] = {0, 0};
+    long long bi[2] = {-1, -1};
+    const TrkF2 TA = load_trk_f2(a.geof2 + 4 * t);
+    const F2 kB3 = f2_mul_f(f2_from(a.kB), 3.0f);
+    // the tests of candidate b of direction d (the FP32 prefilter with margins wider
+    // than any FP32 rounding of the FP64 tests; a NaN tan lambda fails every comparison)
+    auto consider = [&](long long b, int d) {
+      const float4 pb = a.pre[b];
+      if (!(fabsf(pa.x - pb.x) <= 0.0201f) || pa.w != pb.w) return;
+      const float dq = pa.y - pb.y, sq = pa.z * pa.z + pb.z * pb.z;
+      if (!(dq * dq <= 16.2f * sq + 1e-28f)) return;
+      if (!mrg_maybe_compatible(a.geo32 + 2 * t, a.geo32 + 2 * b, pa.x, pb.x, kBf)) return;
+      // a track without a circle has a NaN tan lambda and the same sign test as G_SIGN: both were checked
+      const TrkF2 B = load_trk_f2(a.geof2 + 4 * b);
+      unsigned long long sc;
+      if (mrg_compatible(TA, B, A[G_RAD] <= a.geo[G_N * b + G_RAD], kB3, &sc)) keep_best(sc, b, &bs[d], &bi[d]);
+    };
+    const int sg = (nb0 >= 0 || nb1 >= 0) ? a.item_seg[item] : -1;
+    if (sg >= 0 && a.seg_ok[sg]) {
+      if (pa.x == pa.x) {  // the window |tan(lambda_b) - tan(lambda_a)| <= 0.0202 (+ the rounding of large values)
+        const float wd = 0.0202f + 1e-6f * fabsf(pa.x);
+        const unsigned lo_key = tgl_key(pa.x - wd), hi_key = tgl_key(pa.x + wd);
+        const unsigned* keys = a.skey + a.seg_off[sg];
+        const int* idx = a.sidx + a.seg_off[sg];
+        const int n = a.seg_n[sg];
+        const int f0 = nb0 >= 0 ? a.item_first[nb0] : 0, e0 = nb0 >= 0 ? a.item_first[nb0 + 1] : 0;
+        const int f1 = nb1 >= 0 ? a.item_first[nb1] : 0, e1 = nb1 >= 0 ? a.item_first[nb1 + 1] : 0;
+        for (int i0 = warp_lower_bound(keys, n, lo_key);; i0 += 32) {
+          const int i = i0 + lane;
+          const bool in = i < n && keys[i] <= hi_key;
+          if (in) {
+            const int b = idx[i];  // in the item of sector k+1 or k-1?
+            if (b >= f0 && b < e0) consider(b, 0);
+            else if (b >= f1 && b < e1) consider(b, 1);
+          }
+          if (__ballot_sync(0xffffffffu, in) != 0xffffffffu) break;
+        }
+      }
+    } else {
+      for (int d = 0; d < 2; ++d) {
+        const int nb = d ? nb1 : nb0;
+        if (nb >= 0)
+          for (long long b = a.item_first[nb] + lane; b < a.item_first[nb + 1]; b += 32) consider(b, d);
+      }
+    }
+    for (int d = 0; d < 2; ++d) {
+      const long long b = warp_best(bs[d], bi[d]);
+      if (lane == 0) a.best[2 * t + d] = (int)b;
+    }
+  }
+}
+
+__global__ void k_mrg_link(const __grid_constant__ MrgArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride)
+    for (int d = 0; d < 2; ++d) {
+      const int b = a.best[2 * t + d];
+      a.link[2 * t + d] = (b >= 0 && a.best[2 * b + (1 - d)] == (int)t) ? b : -1;
+    }
+}
+
+// the group of a track: the smallest index on its path of links (at most 18
+// steps each way: one track per sector of a side)
+__global__ void k_mrg_group(const __grid_constant__ MrgArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride) {
+    int m = (int)t;
+    for (int d = 0; d < 2; ++d) {
+      int cur = (int)t;
+      for (int step = 0; step < 18; ++step) {
+        const int nxt = a.link[2 * cur + d];
+        if (nxt < 0) break;
+        m = min(m, nxt);
+        cur = nxt;
+      }
+    }
+    a.group[t] = m;
+  }
 }
 
 // one warp per group root: refit of the group's clusters in the global frame.
@@ -1380,6 +1604,13 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
                                                   const __grid_constant__ DevParams par) {
   __shared__ int mem[4][40];
   __shared__ F2 rot[4][40][2];  // cos and sin of each member's sector angle
+  __shared__ F2 sec_rot[18][2];  // cos and sin of the 18 sector angles, once per block
+  if (threadIdx.x < 18) {
+    const double ang = (double)threadIdx.x * MRG_WEDGE;
+    sec_rot[threadIdx.x][0] = f2_from(cos(ang));
+    sec_rot[threadIdx.x][1] = f2_from(sin(ang));
+  }
+  __syncthreads();
   constexpr int STAGE = 384;    // clusters of a group kept in shared memory (larger groups re-gather)
   __shared__ F2 sX[4][STAGE], sY[4][STAGE];
   __shared__ float sZ[4][STAGE];
@@ -1389,7 +1620,8 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
   for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_trk; t += nw) {
     double* o = a.fit + 7 * t;
     if (lane < 7) o[lane] = 0.0;
-    if (a.group[t] != (int)t || a.geo[G_N * t + G_OK] == 0.0) continue;
+    if (a.group[t] != (int)t) continue;
+    if (a.geo[G_N * t + G_OK] == 0.0) continue;
     // members in index order (the root is the smallest)
     int nm = 0;
     if (lane == 0) {
@@ -1413,9 +1645,9 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
     nm = __shfl_sync(0xffffffffu, nm, 0);
     __syncwarp();
     for (int m = lane; m < nm; m += 32) {
-      const double ang = (double)((int)a.item_sector[trk[mem[w][m]].item] % 18) * MRG_WEDGE;
-      rot[w][m][0] = f2_from(cos(ang));
-      rot[w][m][1] = f2_from(sin(ang));
+      const int k = (int)(a.item_sector[trk[mem[w][m]].item] % 18u);
+      rot[w][m][0] = sec_rot[k][0];
+      rot[w][m][1] = sec_rot[k][1];
     }
     __syncwarp();
     long long n_all = 0;
@@ -1493,7 +1725,8 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
     sx = warp_sum(sx);
     sy = warp_sum(sy);
     if (n < 3) continue;
-    const double mxd = f2_val(sx) / (double)n, myd = f2_val(sy) / (double)n;
+    const double inv_n = 1.0 / (double)n;
+    const double mxd = f2_val(sx) * inv_n, myd = f2_val(sy) * inv_n;
     const F2 nmx = f2_neg(f2_from(mxd)), nmy = f2_neg(f2_from(myd));
     // pass 2: centred moments
     F2 suu = {0.f, 0.f}, suv = suu, svv = suu, su3 = suu, sv3 = suu, sw = suu;
@@ -1519,7 +1752,8 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
     const double Su3 = f2_val(warp_sum(su3)), Sv3 = f2_val(warp_sum(sv3)), Sw = f2_val(warp_sum(sw));
     const double det = Suu * Svv - Suv * Suv;
     if (!(fabs(det) > 0.0)) continue;
-    const double D = (-Su3 * Svv + Sv3 * Suv) / det, E = (-Sv3 * Suu + Su3 * Suv) / det, F = -Sw / (double)n;
+    const double inv_det = 1.0 / det;
+    const double D = (-Su3 * Svv + Sv3 * Suv) * inv_det, E = (-Sv3 * Suu + Su3 * Suv) * inv_det, F = -Sw * inv_n;
     const double xc = mxd - 0.5 * D, yc = myd - 0.5 * E;
     const double R = sqrt(0.25 * (D * D + E * E) - F);
     const F2 k24 = f2_from(1.0 / (24.0 * R * R));
@@ -1552,7 +1786,7 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
       o[1] = yc;
       o[2] = R;
       o[3] = tgl;
-      o[4] = (Sz - tgl * Ss) / (double)n;
+      o[4] = (Sz - tgl * Ss) * inv_n;
       o[5] = (double)n;
       o[6] = (double)nm;
     }
@@ -1566,60 +1800,67 @@ __global__ void k_mrg_legs(const __grid_constant__ MrgArgs a) {
   const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
   const int lane = threadIdx.x & 31;
   const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  const float kBf = (float)a.kB;
   for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_trk; t += nw) {
     const double* A = a.geo + G_N * t;
-    double bs = 0.0;
+    unsigned long long bs = 0;
     long long bi = -1;
     if (A[G_OK] != 0.0 && A[G_R] < 250.0) {
       const float4 pa = a.pre[t];
       const float4 ga = a.geo32[2 * t];
-      const float kBf = (float)a.kB;
-      const int* items = a.side_items + 18 * (long long)trk[t].item;
-      for (int k = 0; k < 18; ++k) {
-        const int it = items[k];
-        if (it < 0) continue;
-        for (long long b = a.item_first[it] + lane; b < a.item_first[it + 1]; b += 32) {
-          // FP32 prefilter (margins wider than FP32 rounding; R < 250 cm <=> |q/pT| > 2.668 c/GeV at 0.5 T)
-          const float4 pb = a.pre[b];
-          if (pb.w == pa.w || !((pa.x > 0.f) != (pb.x > 0.f)) || !(fabsf(pa.x + pb.x) <= 0.0201f)) continue;
-          const float dq = fabsf(pa.y) - fabsf(pb.y), sq = pa.z * pa.z + pb.z * pb.z;
-          if (!(dq * dq <= 16.2f * sq + 1e-28f)) continue;
-          {  // the centre distance in FP32, margins as in mrg_maybe_compatible
-            const float4 gb = a.geo32[2 * b];
-            const float ex = ga.x - gb.x, ey = ga.y - gb.y;
-            const float Rm = fmaxf(ga.z, gb.z);
-            const float kv = 3.0f * kBf * sqrtf(ga.w + gb.w);
-            const float dl = fmaf(kv * Rm, Rm, 1.0f);
-            const float M = fabsf(ga.x) + fabsf(ga.y) + fabsf(gb.x) + fabsf(gb.y);
-            if (sqrtf(fmaf(ex, ex, ey * ey)) > dl * (1.0f + 1e-5f) + 1e-5f * (kv * Rm * Rm + M) + 1e-6f) continue;
+      auto consider = [&](long long b) {
+        // FP32 prefilter (margins wider than FP32 rounding; R < 250 cm <=> |q/pT| > 2.668 c/GeV at 0.5 T)
+        const float4 pb = a.pre[b];
+        if (pb.w == pa.w || !((pa.x > 0.f) != (pb.x > 0.f)) || !(fabsf(pa.x + pb.x) <= 0.0201f)) return;
+        const float dq = fabsf(pa.y) - fabsf(pb.y), sq = pa.z * pa.z + pb.z * pb.z;
+        if (!(dq * dq <= 16.2f * sq + 1e-28f)) return;
+        {  // the centre distance in FP32, margins as in mrg_maybe_compatible
+          const float4 gb = a.geo32[2 * b];
+          const float ex = ga.x - gb.x, ey = ga.y - gb.y;
+          const float Rm = fmaxf(ga.z, gb.z);
+          const float kv = 3.0f * kBf * sqrtf(ga.w + gb.w);
+          const float dl = fmaf(kv * Rm, Rm, 1.0f);
+          const float M = fabsf(ga.x) + fabsf(ga.y) + fabsf(gb.x) + fabsf(gb.y);
+          if (sqrtf(fmaf(ex, ex, ey * ey)) > dl * (1.0f + 1e-5f) + 1e-5f * (kv * Rm * Rm + M) + 1e-6f) return;
+        }
+        const double* B = a.geo + G_N * b;
+        if (B[G_OK] == 0.0 || !(B[G_R] < 250.0)) return;
+        const double qa = fabs(A[G_QPT]), qb = fabs(B[G_QPT]);
+        const double vs = fmax(A[G_VQ] + B[G_VQ], 1e-30);
+        const double chi2 = (qa - qb) * (qa - qb) / vs;
+        const double Rm = fmax(A[G_R], B[G_R]);
+        const double dlim = 1.0 + 3.0 * a.kB * sqrt(A[G_VQ] + B[G_VQ]) * Rm * Rm;
+        const double dc = hypot(A[G_XC] - B[G_XC], A[G_YC] - B[G_YC]);
+        const double st = fabs(A[G_TGL] + B[G_TGL]);
+        if (!(chi2 <= 16.0 && dc <= dlim && st <= 0.02)) return;
+        keep_best(score_key(chi2 / 16.0 + dc / dlim + st / 0.02), b, &bs, &bi);
+      };
+      const int sg = a.item_seg[trk[t].item];
+      if (sg >= 0 && a.seg_ok[sg]) {
+        if (pa.x == pa.x) {  // the window |tan(lambda_b) + tan(lambda_a)| <= 0.0202 (+ rounding)
+          const float wd = 0.0202f + 1e-6f * fabsf(pa.x);
+          const unsigned lo_key = tgl_key(-pa.x - wd), hi_key = tgl_key(-pa.x + wd);
+          const unsigned* keys = a.skey + a.seg_off[sg];
+          const int* idx = a.sidx + a.seg_off[sg];
+          const int n = a.seg_n[sg];
+          for (int i0 = warp_lower_bound(keys, n, lo_key);; i0 += 32) {
+            const int i = i0 + lane;
+            const bool in = i < n && keys[i] <= hi_key;
+            if (in) consider(idx[i]);
+            if (__ballot_sync(0xffffffffu, in) != 0xffffffffu) break;
           }
-          const double* B = a.geo + G_N * b;
-          if (B[G_OK] == 0.0 || !(B[G_R] < 250.0)) continue;
-          const double qa = fabs(A[G_QPT]), qb = fabs(B[G_QPT]);
-          const double vs = fmax(A[G_VQ] + B[G_VQ], 1e-30);
-          const double chi2 = (qa - qb) * (qa - qb) / vs;
-          const double Rm = fmax(A[G_R], B[G_R]);
-          const double dlim = 1.0 + 3.0 * a.kB * sqrt(A[G_VQ] + B[G_VQ]) * Rm * Rm;
-          const double dc = hypot(A[G_XC] - B[G_XC], A[G_YC] - B[G_YC]);
-          const double st = fabs(A[G_TGL] + B[G_TGL]);
-          if (!(chi2 <= 16.0 && dc <= dlim && st <= 0.02)) continue;
-          const double sc = chi2 / 16.0 + dc / dlim + st / 0.02;
-          if (bi < 0 || sc < bs || (sc == bs && b < bi)) {
-            bs = sc;
-            bi = b;
-          }
+        }
+      } else if (sg >= 0) {
+        const int* items = a.seg_items + 19 * (long long)sg;
+        for (int k = 0; k < 18; ++k) {
+          const int it = items[k];
+          if (it < 0) continue;
+          for (long long b = a.item_first[it] + lane; b < a.item_first[it + 1]; b += 32) consider(b);
         }
       }
     }
-    for (int o = 16; o; o >>= 1) {  // smallest (score, index)
-      const double os = __shfl_xor_sync(0xffffffffu, bs, o);
-      const long long oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (oi >= 0 && (bi < 0 || os < bs || (os == bs && oi < bi))) {
-        bs = os;
-        bi = oi;
-      }
-    }
-    if (lane == 0) a.lbest[t] = (int)bi;
+    const long long b = warp_best(bs, bi);
+    if (lane == 0) a.lbest[t] = (int)b;
   }
 }
 
@@ -1643,11 +1884,23 @@ cudaError_t launch_merge(const MrgArgs& a, const DevParams& par, int num_sms, cu
   k_mrg_item_first<<<(a.I + 256) / 256, 256, 0, s>>>(a);
   if (a.n_trk > 0) {
     k_mrg_geom<<<g, 256, 0, s>>>(a);
+    if (a.S > 0) {
+      static bool smem_set = false;  // the sort's shared memory above the default 48 KB
+      if (!smem_set) {
+        const cudaError_t e = cudaFuncSetAttribute(k_mrg_seg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                   8 * MRG_SORT_CAP);
+        if (e != cudaSuccess) return e;
+        smem_set = true;
+      }
+      k_mrg_seg_count<<<(a.S + 255) / 256, 256, 0, s>>>(a);
+      k_mrg_seg_scan<<<1, 1024, 0, s>>>(a);
+      k_mrg_seg_sort<<<a.S, 1024, 8 * MRG_SORT_CAP, s>>>(a);
+    }
     k_mrg_best<<<g, 256, 0, s>>>(a);
     k_mrg_link<<<g, 256, 0, s>>>(a);
     k_mrg_group<<<g, 256, 0, s>>>(a);
     k_mrg_fit<<<num_sms * 16, 128, 0, s>>>(a, par);
-    if (a.side_items) {
+    if (a.legs) {
       k_mrg_legs<<<g, 256, 0, s>>>(a);
       k_mrg_legs_final<<<g, 256, 0, s>>>(a);
     }
