@@ -544,9 +544,11 @@ def bench_removal_chain(cl, props, dev, stream, tpc, torch):
 
 
 def bench_merge(cl, dev, stream, flush, tpc, torch, steps=10):
-    """Sector-track merger with refit and looper legs over the 64 events' own tracks.  The call
-    waits for its outputs (host arrays), so it is timed by the host clock and,
-    on its stream, by CUDA events around it.  L2 flushed between calls."""
+    """Sector-track merger with refit and looper legs over the 64 events' own tracks, outputs
+    on the device.  The call waits for its end, so it is timed by the host
+    clock and, on its stream, by CUDA events around it; the same call with
+    host outputs (12 MB of links, groups and refits copied back) beside it.
+    L2 flushed between calls."""
     with torch.cuda.stream(stream):
         d = to_device(cl, dev)
     stream.synchronize()
@@ -555,25 +557,30 @@ def bench_merge(cl, dev, stream, flush, tpc, torch, steps=10):
         t.load(d, on_device=True)
         t.track()
         n_trk = t.counts()[0]
-        for _ in range(3):
-            link, group, fit, partner, leg = t.merge_tracks(n_tracks=n_trk, legs=True)
-        wall, dev_ms = [], []
-        for _ in range(steps):
-            with torch.cuda.stream(stream):
-                flush.zero_()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            w0 = time.perf_counter()
-            e0.record(stream)
-            link, group, fit, partner, leg = t.merge_tracks(n_tracks=n_trk, legs=True)
-            e1.record(stream)
-            wall.append(time.perf_counter() - w0)
-            torch.cuda.synchronize()
-            dev_ms.append(e0.elapsed_time(e1))
-    ms = 1e3 * float(np.median(wall))
+        def timed(on_device):
+            for _ in range(3):
+                t.merge_tracks(n_tracks=n_trk, legs=True, on_device=on_device)
+            wall, dev_ms = [], []
+            for _ in range(steps):
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                w0 = time.perf_counter()
+                e0.record(stream)
+                out = t.merge_tracks(n_tracks=n_trk, legs=True, on_device=on_device)
+                e1.record(stream)
+                wall.append(time.perf_counter() - w0)
+                torch.cuda.synchronize()
+                dev_ms.append(e0.elapsed_time(e1))
+            return out, 1e3 * float(np.median(wall)), float(np.median(dev_ms))
+
+        (link, group, fit, partner, leg), ms, dms = timed(True)
+        link, group, partner = link.cpu().numpy(), group.cpu().numpy(), partner.cpu().numpy()
+        _, ms_host, _ = timed(False)
     res.update(tracks=n_trk, tracks_per_s=n_trk / (ms * 1e-3), clusters_per_s=cl.n / (ms * 1e-3), ms=ms,
-               device_ms=float(np.median(dev_ms)), links=int((link >= 0).sum() // 2),
+               device_ms=dms, ms_host_outputs=ms_host, links=int((link >= 0).sum() // 2),
                groups=int(np.unique(group).size), leg_pairs=int((partner >= 0).sum() // 2))
     del d
     torch.cuda.empty_cache()

@@ -1610,7 +1610,7 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
   int* d_nb = (int*)cmp_buffer(c, 35, 4 * (3 * (size_t)I + 22 * (size_t)S + 1));
   int* d_lbest = (int*)cmp_buffer(c, 40, 4 * (size_t)std::max(nt, 1ll));
   int* d_first = (int*)cmp_buffer(c, 36, 4 * (size_t)(I + 1));
-  double* d_geo = (double*)cmp_buffer(c, 37, (8 * 12 + 16 + 32 + 64 + 4 + 4) * (size_t)std::max(nt, 1ll));
+  double* d_geo = (double*)cmp_buffer(c, 37, (8 * 12 + 16 + 32 + 64 + 4 + 4 + 136) * (size_t)std::max(nt, 1ll));
   int* d_best = (int*)cmp_buffer(c, 38, 8 * (size_t)std::max(nt, 1ll));
   // outputs: the caller's device arrays, or staging for host arrays
   uint8_t* st = nullptr;
@@ -1650,6 +1650,7 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
   a.geof2 = a.geo32 + 2 * std::max(nt, 1ll);
   a.sidx = (int*)(a.geof2 + 4 * std::max(nt, 1ll));
   a.skey = (unsigned*)(a.sidx + std::max(nt, 1ll));
+  a.fit_sums = (float*)(a.skey + std::max(nt, 1ll));  // 34 floats per track
   a.item_seg = d_nb + 2 * (size_t)I;
   a.seg_items = d_nb + 3 * (size_t)I;
   a.S = S;

@@ -282,6 +282,7 @@ struct MrgArgs {
   int* link;                  // [n_trk][2] output
   int* group;                 // [n_trk] output
   double* fit;                // [n_trk][7] output (group roots)
+  float* fit_sums;            // [n_trk][MRG_FIT_SUMS] per group root: the refit's float-float sums
   const int* item_seg;        // [I] segment (event and side) of every item
   const int* seg_items;       // [S][19] the segment's items (at most 18, -1 padded), then its item count
   int S;                      // segments

@@ -1110,6 +1110,8 @@ cudaError_t cmp_layout(const CmpPlane* planes, int n_planes, const int* stream_p
 namespace {
 
 constexpr double MRG_WEDGE = 2.0 * 3.14159265358979323846 / 18.0;
+constexpr int MRG_FIT_NACC = 14;                        // float-float sums of the refit
+constexpr int MRG_FIT_SUMS = 4 + 2 * MRG_FIT_NACC + 2;  // floats per group record: n, members, mean, sums
 
 // Float-float ("double-float") numbers for the compatibility tests and the
 // refit's per-cluster sums: a
@@ -1597,9 +1599,14 @@ __global__ void k_mrg_group(const __grid_constant__ MrgArgs a) {
   }
 }
 
-// one warp per group root: refit of the group's clusters in the global frame.
-// Cluster positions and the per-cluster sums are float-float; the mean, the
-// 2x2 solve for the circle and the line in (s, z) are FP64, once per group.
+// Refit of every group in the global frame, in two kernels.  k_mrg_fit (one warp
+// per group root) takes the clusters twice: the mean and the innermost cluster,
+// then every sum the fits need, in float-float.  The arc length from the
+// innermost cluster, s = c (1 + k c^2) with chord c and k = 1 / (24 R^2), is a
+// polynomial in c, so the sums over s, s^2 and s z follow from sums of powers of
+// c before R is known.  k_mrg_fit_solve (one thread per group) then solves the
+// circle (algebraic fit on the centred moments) and the line z = z0 + tan(lambda) s
+// in FP64.
 __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs a,
                                                   const __grid_constant__ DevParams par) {
   __shared__ int mem[4][40];
@@ -1620,8 +1627,10 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
   for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_trk; t += nw) {
     double* o = a.fit + 7 * t;
     if (lane < 7) o[lane] = 0.0;
+    float* out = a.fit_sums + (long long)MRG_FIT_SUMS * t;
+    if (lane == 0) out[0] = 0.0f;  // no fit unless written below
     if (a.group[t] != (int)t) continue;
-    if (a.geo[G_N * t + G_OK] == 0.0) continue;
+    if (__double_as_longlong(a.geo[G_N * t + G_OK]) == 0) continue;  // 0.0: no circle
     // members in index order (the root is the smallest)
     int nm = 0;
     if (lane == 0) {
@@ -1725,11 +1734,13 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
     sx = warp_sum(sx);
     sy = warp_sum(sy);
     if (n < 3) continue;
-    const double inv_n = 1.0 / (double)n;
-    const double mxd = f2_val(sx) * inv_n, myd = f2_val(sy) * inv_n;
-    const F2 nmx = f2_neg(f2_from(mxd)), nmy = f2_neg(f2_from(myd));
-    // pass 2: centred moments
-    F2 suu = {0.f, 0.f}, suv = suu, svv = suu, su3 = suu, sv3 = suu, sw = suu;
+    const F2 fn = {(float)n, 0.0f};  // n < 2^24
+    const F2 mx = f2_div(sx, fn), my = f2_div(sy, fn);
+    const F2 nmx = f2_neg(mx), nmy = f2_neg(my), nxin = f2_neg(xin), nyin = f2_neg(yin);
+    // pass 2: centred moments of the circle fit and powers of the chord from the innermost cluster
+    F2 acc[MRG_FIT_NACC];
+#pragma unroll
+    for (int k = 0; k < MRG_FIT_NACC; ++k) acc[k] = {0.f, 0.f};
     pos = 0;
     for (int m = 0; m < nm; ++m) {
       const long long cnt = trk[mem[w][m]].n_clusters;
@@ -1739,57 +1750,74 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
         cluster_at(m, j, pos + j, &X, &Y, &Z);
         const F2 u = f2_add(X, nmx), v = f2_add(Y, nmy);
         const F2 uu = f2_mul(u, u), vv = f2_mul(v, v), ww = f2_add(uu, vv);
-        suu = f2_add(suu, uu);
-        suv = f2_add(suv, f2_mul(u, v));
-        svv = f2_add(svv, vv);
-        su3 = f2_add(su3, f2_mul(u, ww));
-        sv3 = f2_add(sv3, f2_mul(v, ww));
-        sw = f2_add(sw, ww);
-      }
-      pos += cnt;
-    }
-    const double Suu = f2_val(warp_sum(suu)), Suv = f2_val(warp_sum(suv)), Svv = f2_val(warp_sum(svv));
-    const double Su3 = f2_val(warp_sum(su3)), Sv3 = f2_val(warp_sum(sv3)), Sw = f2_val(warp_sum(sw));
-    const double det = Suu * Svv - Suv * Suv;
-    if (!(fabs(det) > 0.0)) continue;
-    const double inv_det = 1.0 / det;
-    const double D = (-Su3 * Svv + Sv3 * Suv) * inv_det, E = (-Sv3 * Suu + Su3 * Suv) * inv_det, F = -Sw * inv_n;
-    const double xc = mxd - 0.5 * D, yc = myd - 0.5 * E;
-    const double R = sqrt(0.25 * (D * D + E * E) - F);
-    const F2 k24 = f2_from(1.0 / (24.0 * R * R));
-    const F2 nxin = f2_neg(xin), nyin = f2_neg(yin);
-    // pass 3: z against the arc from the innermost cluster (chord c, arc c (1 + c^2 / 24 R^2))
-    F2 ss = {0.f, 0.f}, sz = ss, sss = ss, ssz = ss;
-    pos = 0;
-    for (int m = 0; m < nm; ++m) {
-      const long long cnt = trk[mem[w][m]].n_clusters;
-      for (long long j = lane; j < cnt; j += 32) {
-        F2 X, Y;
-        float Z;
-        cluster_at(m, j, pos + j, &X, &Y, &Z);
+        acc[0] = f2_add(acc[0], uu);
+        acc[1] = f2_add(acc[1], f2_mul(u, v));
+        acc[2] = f2_add(acc[2], vv);
+        acc[3] = f2_add(acc[3], f2_mul(u, ww));
+        acc[4] = f2_add(acc[4], f2_mul(v, ww));
+        acc[5] = f2_add(acc[5], ww);
         const F2 cx = f2_add(X, nxin), cy = f2_add(Y, nyin);
         const F2 c2 = f2_add(f2_mul(cx, cx), f2_mul(cy, cy));
-        const F2 s = f2_mul(f2_sqrt(c2), f2_add({1.0f, 0.0f}, f2_mul(c2, k24)));
-        ss = f2_add(ss, s);
-        sz = f2_add(sz, {Z, 0.0f});
-        sss = f2_add(sss, f2_mul(s, s));
-        ssz = f2_add(ssz, f2_mul_f(s, Z));
+        const F2 c = f2_sqrt(c2), c3 = f2_mul(c, c2), c4 = f2_mul(c2, c2);
+        acc[6] = f2_add(acc[6], c);
+        acc[7] = f2_add(acc[7], c2);
+        acc[8] = f2_add(acc[8], c3);
+        acc[9] = f2_add(acc[9], c4);
+        acc[10] = f2_add(acc[10], f2_mul(c4, c2));
+        acc[11] = f2_add(acc[11], {Z, 0.0f});
+        acc[12] = f2_add(acc[12], f2_mul_f(c, Z));
+        acc[13] = f2_add(acc[13], f2_mul_f(c3, Z));
       }
       pos += cnt;
     }
-    const double Ss = f2_val(warp_sum(ss)), Sz = f2_val(warp_sum(sz));
-    const double Sss = f2_val(warp_sum(sss)), Ssz = f2_val(warp_sum(ssz));
-    const double den = (double)n * Sss - Ss * Ss;
-    const double tgl = den > 0.0 ? ((double)n * Ssz - Ss * Sz) / den : 0.0;
-    if (lane == 0) {
-      o[0] = xc;
-      o[1] = yc;
-      o[2] = R;
-      o[3] = tgl;
-      o[4] = (Sz - tgl * Ss) * inv_n;
-      o[5] = (double)n;
-      o[6] = (double)nm;
+#pragma unroll
+    for (int k = 0; k < MRG_FIT_NACC; ++k) acc[k] = warp_sum(acc[k]);
+    // record: n, members, then the mean (x, y) and the sums, each as (hi, lo): lane l writes float 2 + l
+    float v = lane == 0 ? mx.hi : (lane == 1 ? mx.lo : (lane == 2 ? my.hi : my.lo));
+#pragma unroll
+    for (int k = 0; k < MRG_FIT_NACC; ++k) {
+      v = lane == 4 + 2 * k ? acc[k].hi : v;
+      v = lane == 5 + 2 * k ? acc[k].lo : v;
     }
+    out[2 + lane] = v;
+    if (lane == 0) {
+      out[1] = (float)nm;
+      out[0] = (float)n;
+    }
+  }
+}
+
+// one thread per group root: the circle from the centred moments (algebraic
+// fit u^2 + v^2 + D u + E v + F = 0), then the line z = z0 + tan(lambda) s from
+// the sums of powers of the chord (s = c + k c^3), in FP64
+__global__ void k_mrg_fit_solve(const __grid_constant__ MrgArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride) {
+    const float* r = a.fit_sums + (long long)MRG_FIT_SUMS * t;
+    const double n = r[0];
+    if (n < 3.0) continue;
+    auto val = [&](int k) { return (double)r[2 + 2 * k] + (double)r[3 + 2 * k]; };
+    const double mx = val(0), my = val(1);
+    const double Suu = val(2), Suv = val(3), Svv = val(4), Su3 = val(5), Sv3 = val(6), Sw = val(7);
+    const double det = Suu * Svv - Suv * Suv;
+    if (!(fabs(det) > 0.0)) continue;
+    const double inv_det = 1.0 / det, inv_n = 1.0 / n;
+    const double D = (-Su3 * Svv + Sv3 * Suv) * inv_det, E = (-Sv3 * Suu + Su3 * Suv) * inv_det, F = -Sw * inv_n;
+    const double R = sqrt(0.25 * (D * D + E * E) - F);
+    const double k = 1.0 / (24.0 * R * R);
+    const double Sc = val(8), Sc2 = val(9), Sc3 = val(10), Sc4 = val(11), Sc6 = val(12);
+    const double Sz = val(13), Scz = val(14), Sc3z = val(15);
+    const double Ss = Sc + k * Sc3, Sss = Sc2 + k * (2.0 * Sc4 + k * Sc6), Ssz = Scz + k * Sc3z;
+    const double den = n * Sss - Ss * Ss;
+    const double tgl = den > 0.0 ? (n * Ssz - Ss * Sz) / den : 0.0;
+    double* o = a.fit + 7 * t;
+    o[0] = mx - 0.5 * D;
+    o[1] = my - 0.5 * E;
+    o[2] = R;
+    o[3] = tgl;
+    o[4] = (Sz - tgl * Ss) * inv_n;
+    o[5] = n;
+    o[6] = r[1];
   }
 }
 
@@ -1900,6 +1928,7 @@ cudaError_t launch_merge(const MrgArgs& a, const DevParams& par, int num_sms, cu
     k_mrg_link<<<g, 256, 0, s>>>(a);
     k_mrg_group<<<g, 256, 0, s>>>(a);
     k_mrg_fit<<<num_sms * 16, 128, 0, s>>>(a, par);
+    k_mrg_fit_solve<<<g, 256, 0, s>>>(a);
     if (a.legs) {
       k_mrg_legs<<<g, 256, 0, s>>>(a);
       k_mrg_legs_final<<<g, 256, 0, s>>>(a);

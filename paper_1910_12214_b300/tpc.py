@@ -446,27 +446,40 @@ class Tracker:
         self._check(st)
         return out[:int(size.value)]
 
-    def merge_tracks(self, tracks=None, ids=None, n_tracks=None, legs=False):
+    def merge_tracks(self, tracks=None, ids=None, n_tracks=None, legs=False, on_device=False):
         """Sector-track merger (include/tpc_reduce.h): (link [n,2], group [n],
-        fit [n,7]) as numpy arrays, with legs=True also (leg_partner [n], leg
-        [n]) of the looper legs.  tracks=None merges the last tpc_track()
-        output (n_tracks = its count, read here if None); else TRACK_DTYPE
-        records sorted by item and uint32 ids."""
+        fit [n,7]) as numpy arrays, or CUDA tensors with on_device; with
+        legs=True also (leg_partner [n], leg [n]) of the looper legs.
+        tracks=None merges the last tpc_track() output (n_tracks = its count,
+        read here if None); else TRACK_DTYPE records sorted by item and uint32
+        ids (with on_device a CUDA uint8 tensor [n, 112] and int32 ids)."""
         if tracks is None:
             n = self.counts()[0] if n_tracks is None else int(n_tracks)
+        elif on_device:
+            n = int(tracks.shape[0])
         else:
             tracks = np.ascontiguousarray(tracks, TRACK_DTYPE)
             ids = np.ascontiguousarray(ids, np.uint32)
             n = int(tracks.shape[0])
-        link = np.zeros((n, 2), np.int32)
-        group = np.zeros(n, np.int32)
-        fit = np.zeros((n, 7), np.float64)
-        partner = np.zeros(n, np.int32) if legs else None
-        leg = np.zeros(n, np.uint8) if legs else None
+        if on_device:
+            import torch
+            dev = torch.device("cuda", self.cfg.device)
+            m = max(n, 1)
+            link = torch.empty((m, 2), dtype=torch.int32, device=dev)[:n]
+            group = torch.empty(m, dtype=torch.int32, device=dev)[:n]
+            fit = torch.empty((m, 7), dtype=torch.float64, device=dev)[:n]
+            partner = torch.empty(m, dtype=torch.int32, device=dev)[:n] if legs else None
+            leg = torch.empty(m, dtype=torch.uint8, device=dev)[:n] if legs else None
+        else:
+            link = np.zeros((n, 2), np.int32)
+            group = np.zeros(n, np.int32)
+            fit = np.zeros((n, 7), np.float64)
+            partner = np.zeros(n, np.int32) if legs else None
+            leg = np.zeros(n, np.uint8) if legs else None
         ni = int(ids.shape[0]) if ids is not None else 0
         nz = lambda a: _ptr(a) if (a is not None and n) else None
-        self._check(_lib.tpc_merge_tracks(self._h, _ptr(tracks), n, _ptr(ids), ni, 0, nz(link), nz(group), nz(fit),
-                                          nz(partner), nz(leg)))
+        self._check(_lib.tpc_merge_tracks(self._h, _ptr(tracks), n, _ptr(ids), ni, int(bool(on_device)), nz(link),
+                                          nz(group), nz(fit), nz(partner), nz(leg)))
         return (link, group, fit, partner, leg) if legs else (link, group, fit)
 
     def close(self):

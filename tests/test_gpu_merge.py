@@ -158,3 +158,24 @@ def test_secondary_legs_removed_by_strategy_a():
     assert removed1[sec_cl].mean() > removed0[sec_cl].mean() + 0.3
     # clusters of first legs: essentially untouched
     assert removed1[prim_cl].mean() < removed0[prim_cl].mean() + 0.02
+
+
+def test_device_outputs_equal_host_outputs():
+    """The same call with device inputs and outputs (the oracle tracker's tracks
+    uploaded) and with host arrays: identical links, groups, refits and legs."""
+    import torch
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_event(42, 3000, second_leg=True)
+    ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids"])
+    tf, ti, ids = oracle.merge_tracks(ref)
+    rec = to_records(tf, ti)
+    with tracked(cl) as t:
+        host = t.merge_tracks(rec, ids, legs=True)
+        d_rec = torch.from_numpy(rec.view(np.uint8).reshape(-1, rec.dtype.itemsize)).cuda()
+        d_ids = torch.from_numpy(ids.view(np.int32)).cuda()
+        dev = t.merge_tracks(d_rec, d_ids, legs=True, on_device=True)
+        own_host = t.merge_tracks(legs=True)
+        own_dev = t.merge_tracks(legs=True, on_device=True)
+    for h, d in zip(host + own_host, dev + own_dev):
+        assert np.array_equal(h, d.cpu().numpy(), equal_nan=True)
+    assert (host[0] >= 0).sum() > 100 and (host[3] >= 0).sum() > 10
