@@ -275,6 +275,52 @@ def pinned_clusters(cl, torch):
     return d
 
 
+def e2e_pipelined(hcl, tuning, tpc, torch, dev, local, steps):
+    """Seconds per step end to end through the public API, double-buffered.
+    A step is tpc_load_clusters of the step's clusters from pinned host memory
+    (H2D; the call returns when its copies are done), tpc_track, and
+    tpc_get_tracks of the tracks and ids into pinned host memory (D2H).  Two
+    contexts on two streams take alternate steps: while one tracks, the other
+    loads the next step and reads its previous result; a stream wait keeps the
+    tracking of consecutive steps in order, one event at a time on the GPU."""
+    ss = [torch.cuda.Stream(dev) for _ in range(2)]
+    ts = [tpc.Tracker(device=local, stream=s) for s in ss]
+    outs = []
+    for t in ts:
+        t.set_tuning(**{**tuning, "use_graph": 2})
+        t.load(hcl)
+        t.track()
+        t.sync()
+        nt, ni = t.counts()
+        ot = torch.empty((nt + 64) * tpc.TRACK_DTYPE.itemsize, dtype=torch.uint8, pin_memory=True)
+        oi = torch.empty(ni + 4096, dtype=torch.int32, pin_memory=True)
+        outs.append((ot.numpy().view(tpc.TRACK_DTYPE), oi.numpy().view(np.uint32), ot, oi))
+    done = [torch.cuda.Event(), torch.cuda.Event()]
+
+    def run(k_steps):
+        torch.cuda.synchronize()
+        w0 = time.perf_counter()
+        ts[0].load(hcl)
+        ts[0].track()
+        done[0].record(ss[0])
+        for k in range(k_steps):
+            cur, nxt = k % 2, (k + 1) % 2
+            if k + 1 < k_steps:
+                ts[nxt].load(hcl)
+                ss[nxt].wait_event(done[cur])
+                ts[nxt].track()
+                done[nxt].record(ss[nxt])
+            ts[cur].get_tracks(out=outs[cur][:2])
+        return (time.perf_counter() - w0) / k_steps
+
+    run(4)
+    per = [run(steps) for _ in range(3)]
+    res = [t.get_tracks(out=o[:2]) for t, o in zip(ts, outs)]
+    for t in ts:
+        t.close()
+    return float(np.median(per)), res[0]
+
+
 def time_steps(t, stream, steps, flush):
     """Device time of `steps` tpc_track() calls, L2 flushed between them."""
     import torch
@@ -390,8 +436,11 @@ def main():
         trk, ids = t.get_tracks(out=out)
         e2e.append(time.perf_counter() - t0)
     d2h = trk.nbytes + ids.nbytes + 32
-    e2e_s = shard.max_over_ranks(float(np.median(e2e[1:])), dist, device=dev)
+    e2e_serial = shard.max_over_ranks(float(np.median(e2e[1:])), dist, device=dev)
     t.close()
+    e2e_s, (trk_p, ids_p) = e2e_pipelined(hcl, tuning, tpc, torch, dev, local, max(8, args.steps))
+    same_tracks = bool(np.array_equal(trk_p, trk) and np.array_equal(ids_p, ids))  # as the serial calls
+    e2e_s = shard.max_over_ranks(e2e_s, dist, device=dev)
 
     form_out = {}
     if rank == 0 and forms:
@@ -412,7 +461,9 @@ def main():
                        "tracks": n_tr, "l2": "flushed between steps (256 MB write)", "tuning": tuning,
                        "autotune_best_us": tune_us},
             "e2e": {"value": n_all / e2e_s, "unit": "clusters/s", "h2d_bytes_per_step": int(h2d),
-                    "d2h_bytes_per_step": int(d2h)},
+                    "d2h_bytes_per_step": int(d2h), "pipeline": "two contexts, each step's H2D and D2H "
+                    "overlapping the other context's tracking; tracking serialised",
+                    "serial_value": n_all / e2e_serial, "tracks_equal_serial": same_tracks},
             "gpu_launches": KERNELS_PER_STEP["batched" if tuning["mode"] == 2 else "plain"] * args.steps,
             "stage_us": {k: round(v, 2) for k, v in stages.items()},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
