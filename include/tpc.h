@@ -215,7 +215,10 @@ tpc_status tpc_surrogate_load(tpc_ctx* ctx, const char* path);
  * or 128); tracklet_blocks_per_sm: grid = this x SM count; sort_smem: dynamic
  * shared memory [bytes] of the per-row sort (rows that do not fit use global
  * memory); link_rows: pad rows per block of the neighbour kernel (-1 = 8; the
- * block's rows are staged in shared memory when they fit).  0 keeps a field. */
+ * block's rows are staged in shared memory when they fit); merge_sort_cap:
+ * most tracks of one event and side that tpc_merge_tracks sorts by tan(lambda)
+ * in shared memory for its candidate search (1 to 16384; larger sets, or -1
+ * for every set, are scanned item by item).  0 keeps a field. */
 typedef struct {
   int tracklet_lanes;
   int tracklet_block;
@@ -225,6 +228,7 @@ typedef struct {
   int mode;          /* 1 = plain (one launch per step), 2 = batched (persistent kernel) */
   int batch_lanes;   /* lanes per tracklet in the batched kernel: 1, 2 or 4 */
   int use_graph;     /* 1 = launch directly, 2 = capture tpc_track once per load and replay it */
+  int merge_sort_cap;
 } tpc_tuning;
 
 tpc_status tpc_set_tuning(tpc_ctx* ctx, const tpc_tuning* t);

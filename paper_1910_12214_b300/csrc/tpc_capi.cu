@@ -291,6 +291,7 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
   L.grid_tl = sms * 16;
   L.tl_group = 1;
   L.batch_group = 1;
+  L.merge_sort_cap = 16384;
   c->batched = cfg->mode == TPC_MODE_BATCHED;
   c->corr = cfg->correction;
   c->use_graph = capturable(c->stream);
@@ -712,6 +713,11 @@ tpc_status apply_tuning(tpc_ctx* c, const tpc_tuning& t) {
       return fail(c, TPC_ERR_INVALID_ARG, "batch_lanes must be 1, 2 or 4");
     L.batch_group = t.batch_lanes;
   }
+  if (t.merge_sort_cap) {
+    if (t.merge_sort_cap < -1 || t.merge_sort_cap > 16384)
+      return fail(c, TPC_ERR_INVALID_ARG, "merge_sort_cap must be -1 or 1 to 16384");
+    L.merge_sort_cap = t.merge_sort_cap < 0 ? 0 : t.merge_sort_cap;
+  }
   if (t.use_graph) {
     if (t.use_graph != 1 && t.use_graph != 2) return fail(c, TPC_ERR_INVALID_ARG, "use_graph must be 1 or 2");
     use_graph = t.use_graph == 2 && capturable(c->stream);
@@ -743,6 +749,7 @@ extern "C" tpc_status tpc_get_tuning(tpc_ctx* c, tpc_tuning* t) {
   t->mode = c->batched ? 2 : 1;
   t->batch_lanes = c->lc.batch_group;
   t->use_graph = c->use_graph ? 2 : 1;
+  t->merge_sort_cap = c->lc.merge_sort_cap ? c->lc.merge_sort_cap : -1;
   return TPC_OK;
 }
 
@@ -1657,6 +1664,7 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
   a.seg_n = d_nb + 3 * (size_t)I + 19 * (size_t)S;
   a.seg_off = a.seg_n + S;
   a.seg_ok = a.seg_off + S + 1;
+  a.sort_cap = c->lc.merge_sort_cap;
   a.best = d_best;
   a.link = on_device ? link : (int*)(st + o_link);
   a.group = on_device ? group : (int*)(st + o_group);

@@ -148,6 +148,7 @@ struct LaunchCfg {
   int tl_group;   // lanes per tracklet (1, 2, 4, 8, 16, 32)
   int batch_group;  // lanes per tracklet in the batched kernel (1, 2, 4)
   int batch_per_sm[3];  // resident CTAs per SM of the batched kernel for 1, 2, 4 lanes
+  int merge_sort_cap;   // tracks of one event and side sorted by the merger (0: none)
 };
 
 cudaError_t tpc_configure_kernels(int sort_smem, int link_smem);
@@ -290,6 +291,7 @@ struct MrgArgs {
   int* seg_n;                 // [S] tracks of the segment
   int* seg_off;               // [S + 1] offsets of the sorted lists
   int* seg_ok;                // [S] 1: sorted list built (else the candidates are scanned item by item)
+  int sort_cap;               // largest segment sorted (at most MRG_SORT_CAP; 0: none)
   unsigned* skey;             // [n_trk] order-preserving tan(lambda) bits, ascending per segment
   int* sidx;                  // [n_trk] the tracks in the same order
   float4* geof2;              // [n_trk][4] float-float circle and reference point for the compatibility tests

@@ -1422,7 +1422,7 @@ __global__ void __launch_bounds__(1024) k_mrg_seg_sort(const __grid_constant__ M
   const int sg = blockIdx.x;
   const int* it = a.seg_items + 19 * (long long)sg;
   const int n = a.seg_n[sg];
-  const bool ok = n <= MRG_SORT_CAP && it[18] <= 18;
+  const bool ok = n <= min(a.sort_cap, MRG_SORT_CAP) && it[18] <= 18;
   if (threadIdx.x == 0) a.seg_ok[sg] = ok ? 1 : 0;
   if (!ok || n == 0) return;
   if (threadIdx.x < 32) {  // the listed items' track ranges and their offsets in the list

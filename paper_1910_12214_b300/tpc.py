@@ -50,7 +50,7 @@ class tpc_clusters(C.Structure):
 class tpc_tuning(C.Structure):
     _fields_ = [("tracklet_lanes", C.c_int), ("tracklet_block", C.c_int), ("tracklet_blocks_per_sm", C.c_int),
                 ("sort_smem", C.c_int), ("link_rows", C.c_int), ("mode", C.c_int),
-                ("batch_lanes", C.c_int), ("use_graph", C.c_int)]
+                ("batch_lanes", C.c_int), ("use_graph", C.c_int), ("merge_sort_cap", C.c_int)]
 
 
 class tpc_cluster_props(C.Structure):

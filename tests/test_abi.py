@@ -49,15 +49,17 @@ def test_struct_layouts_match_c(tmp_path, lib_path):
     from paper_1910_12214_b300 import tpc
     prog = tmp_path / "sz.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "tpc.h"\nint main(void){'
-                    'printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(tpc_config), sizeof(tpc_clusters), '
+                    'printf("%zu %zu %zu %zu %zu %zu %zu %zu\\n", sizeof(tpc_config), sizeof(tpc_clusters), '
                     'sizeof(tpc_track_t), offsetof(tpc_track_t, chi2), offsetof(tpc_config, allocator), '
-                    'offsetof(tpc_clusters, on_device)); return 0;}\n')
+                    'offsetof(tpc_clusters, on_device), sizeof(tpc_tuning), offsetof(tpc_tuning, merge_sort_cap));'
+                    ' return 0;}\n')
     exe = tmp_path / "sz"
     subprocess.check_call(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)])
     vals = [int(v) for v in subprocess.check_output([str(exe)]).split()]
     assert vals == [ctypes.sizeof(tpc.tpc_config), ctypes.sizeof(tpc.tpc_clusters), tpc.TRACK_DTYPE.itemsize,
                     tpc.TRACK_DTYPE.fields["chi2"][1], tpc.tpc_config.allocator.offset,
-                    tpc.tpc_clusters.on_device.offset]
+                    tpc.tpc_clusters.on_device.offset, ctypes.sizeof(tpc.tpc_tuning),
+                    tpc.tpc_tuning.merge_sort_cap.offset]
 
 
 def test_init_rejects_invalid_config_without_touching_the_gpu(lib_path):

@@ -179,3 +179,24 @@ def test_device_outputs_equal_host_outputs():
     for h, d in zip(host + own_host, dev + own_dev):
         assert np.array_equal(h, d.cpu().numpy(), equal_nan=True)
     assert (host[0] >= 0).sum() > 100 and (host[3] >= 0).sum() > 10
+
+
+def test_sorted_lists_and_item_scans_agree():
+    """The candidate search through the tan(lambda)-sorted lists, through the
+    item-by-item scans (merge_sort_cap = -1) and through a mix of both (a cap
+    between the sizes of the 64 uneven events' lists) gives the same links,
+    groups, refits and looper legs bit for bit."""
+    import torch
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_batched(seed=3)
+    with tracked(cl) as t:
+        n = t.counts()[0]
+        outs = []
+        for cap in (16384, -1, 1200):
+            t.set_tuning(merge_sort_cap=cap)
+            assert t.get_tuning()["merge_sort_cap"] == cap
+            outs.append([x.cpu().numpy() for x in t.merge_tracks(n_tracks=n, legs=True, on_device=True)])
+    for other in outs[1:]:
+        for a, b in zip(outs[0], other):
+            assert np.array_equal(a, b, equal_nan=True)
+    assert (outs[0][0] >= 0).sum() > 10000
