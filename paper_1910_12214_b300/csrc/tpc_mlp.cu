@@ -541,13 +541,10 @@ cudaError_t tpc_mlp_init(float* master, float* m, float* v, int S, uint64_t seed
 cudaError_t tpc_mlp_step(float* master, float* m, float* v, float* partial, float* loss, const float2* grid, int nx,
                          int ny, int nz, int S, int batch, uint64_t seed, uint64_t step, float lr_t, float c1, float c2,
                          cudaStream_t s) {
-  static bool attr = false;
   const size_t smem = sizeof(float) * (NPP + 2 * H * TB + 4 * WS);
-  if (!attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = true;
-  }
+  // an attribute of the current device: set per call (a process may train on several devices)
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
   MlpTrain a{master, partial, loss, grid, nx, ny, nz, seed, step, batch};
   const int nblk = batch / TB;
   k_mlp_grad<<<dim3(nblk, S), TB, smem, s>>>(a);

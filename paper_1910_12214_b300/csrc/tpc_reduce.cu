@@ -1913,13 +1913,10 @@ cudaError_t launch_merge(const MrgArgs& a, const DevParams& par, int num_sms, cu
   if (a.n_trk > 0) {
     k_mrg_geom<<<g, 256, 0, s>>>(a);
     if (a.S > 0) {
-      static bool smem_set = false;  // the sort's shared memory above the default 48 KB
-      if (!smem_set) {
-        const cudaError_t e = cudaFuncSetAttribute(k_mrg_seg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                   8 * MRG_SORT_CAP);
-        if (e != cudaSuccess) return e;
-        smem_set = true;
-      }
+      // the sort's shared memory above the default 48 KB (an attribute of the current device: set per call)
+      const cudaError_t e = cudaFuncSetAttribute(k_mrg_seg_sort, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 8 * MRG_SORT_CAP);
+      if (e != cudaSuccess) return e;
       k_mrg_seg_count<<<(a.S + 255) / 256, 256, 0, s>>>(a);
       k_mrg_seg_scan<<<1, 1024, 0, s>>>(a);
       k_mrg_seg_sort<<<a.S, 1024, 8 * MRG_SORT_CAP, s>>>(a);
