@@ -573,9 +573,8 @@ def bench_removal_chain(cl, props, dev, stream, tpc, torch):
             w0 = time.perf_counter()
             t.track()
             n_trk = t.counts()[0]
-            link, group, fit, partner, leg = t.merge_tracks(n_tracks=n_trk, legs=True)
-            d_leg = torch.from_numpy(leg).to(dev)
-            m, _ = t.cluster_masks(on_device=True, with_owner=False, leg=d_leg, n_tracks=n_trk)
+            link, group, fit, partner, leg = t.merge_tracks(n_tracks=n_trk, legs=True, on_device=True)
+            m, _ = t.cluster_masks(on_device=True, with_owner=False, leg=leg, n_tracks=n_trk)
             sizes = {}
             for name, bit in (("none", 0), ("A", 4), ("B", 8)):
                 keep = None if bit == 0 else ((m & bit) == 0).to(torch.uint8)
@@ -583,7 +582,25 @@ def bench_removal_chain(cl, props, dev, stream, tpc, torch):
             torch.cuda.synchronize()
             wall = time.perf_counter() - w0
     mh = m.cpu().numpy()
+    partner = partner.cpu().numpy()
     sec = cl.leg == 1
+    # the form of Fig. 6: per bin of the particle's pT, the fractions of its clusters that are
+    # associated to a track (attached or in the 1.5 cm tube), protected, and removed by A and by B
+    # (below 0.375 GeV/c a helix from the vertex turns inside the chamber, R < 250 cm at 0.5 T; below
+    # about 64 MeV/c it does not reach the inner radius of 85 cm, so no cluster has so low a pT here)
+    pt = np.where(cl.mc >= 0, cl.tracks["pt"][np.maximum(cl.mc, 0)], -1.0)
+    edges = [0.0, 0.15, 0.2, 0.3, 0.375, 0.5, 1.0, 2.0, 1e9]
+    by_pt = []
+    for lo, hi in zip(edges[:-1], edges[1:]):
+        sel = (pt >= lo) & (pt < hi)
+        if sel.any():
+            mm = mh[sel]
+            by_pt.append({"pt_gev": [lo, hi if hi < 1e9 else None], "clusters": int(sel.sum()),
+                          "associated": float(((mm & 1) != 0).mean()), "protected": float(((mm & 2) != 0).mean()),
+                          "removed_by_a": float(((mm & 4) != 0).mean()), "removed_by_b": float(((mm & 8) != 0).mean())})
+    noise = cl.mc < 0
+    res["by_pt"] = by_pt
+    res["noise_clusters"] = {"clusters": int(noise.sum()), "removed_by_b": float(((mh[noise] & 8) != 0).mean())}
     res.update(tracks=n_trk, leg_pairs=int((partner >= 0).sum() // 2), chain_wall_ms=1e3 * wall,
                removed_by_a=float(((mh & 4) != 0).mean()), removed_by_b=float(((mh & 8) != 0).mean()),
                returning_leg_removed_by_a=float(((mh & 4) != 0)[sec].mean()),
