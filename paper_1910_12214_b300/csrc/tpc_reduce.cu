@@ -1770,14 +1770,32 @@ __global__ void __launch_bounds__(128) k_mrg_fit(const __grid_constant__ MrgArgs
       }
       pos += cnt;
     }
+    // the sums over the warp: accumulators 0..11 through the staging area (free now; lanes 2k and
+    // 2k + 1 add the two halves of accumulator k and join them), 12 and 13 by shuffles
+    static_assert(12 * 32 <= STAGE && MRG_FIT_NACC == 14, "reduction layout");
+    __syncwarp();
+    F2* red = sX[w];
 #pragma unroll
-    for (int k = 0; k < MRG_FIT_NACC; ++k) acc[k] = warp_sum(acc[k]);
+    for (int k = 0; k < 12; ++k) red[k * 32 + lane] = acc[k];
+    __syncwarp();
+    F2 part = {0.f, 0.f};
+    if ((lane >> 1) < 12) {
+      const F2* src = red + (lane >> 1) * 32 + (lane & 1) * 16;
+#pragma unroll 4
+      for (int j = 0; j < 16; ++j) part = f2_add(part, src[j]);
+    }
+    part = f2_add(part, {__shfl_xor_sync(0xffffffffu, part.hi, 1), __shfl_xor_sync(0xffffffffu, part.lo, 1)});
+    const F2 a12 = warp_sum(acc[12]), a13 = warp_sum(acc[13]);
     // record: n, members, then the mean (x, y) and the sums, each as (hi, lo): lane l writes float 2 + l
-    float v = lane == 0 ? mx.hi : (lane == 1 ? mx.lo : (lane == 2 ? my.hi : my.lo));
-#pragma unroll
-    for (int k = 0; k < MRG_FIT_NACC; ++k) {
-      v = lane == 4 + 2 * k ? acc[k].hi : v;
-      v = lane == 5 + 2 * k ? acc[k].lo : v;
+    const int ka = (lane - 4) >> 1;  // the accumulator of lane l >= 4
+    const int from = lane < 4 ? 0 : 2 * ka;
+    const F2 got = {__shfl_sync(0xffffffffu, part.hi, from & 31), __shfl_sync(0xffffffffu, part.lo, from & 31)};
+    float v;
+    if (lane < 4) {
+      v = lane == 0 ? mx.hi : (lane == 1 ? mx.lo : (lane == 2 ? my.hi : my.lo));
+    } else {
+      const F2 val = ka < 12 ? got : (ka == 12 ? a12 : a13);
+      v = ((lane - 4) & 1) ? val.lo : val.hi;
     }
     out[2 + lane] = v;
     if (lane == 0) {
