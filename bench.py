@@ -36,7 +36,8 @@ sys.path.insert(0, ROOT)
 
 # Algorithmic bytes per input cluster of each step: the minimum HBM traffic the
 # step must move (cluster SoA 16 B, quantised (qy,qz) 8 B, sorted hit 16 B, link
-# words 4 B each, tracklet hits 4 B per hit and pass).
+# words 4 B each; the tracklets read about two passes of 8 B of coordinates and
+# 4 B of bin lookup per hit and write a 4 B hit slot).
 ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12 + 12, "row_sort": 12 + 16 + 8,
               "links": 16 + 8, "clean+starts": 8 + 8 + 4, "tracklets": 28, "selection": 20, "output": 8,
               "batched_items": 150, "batched_concat": 4}
