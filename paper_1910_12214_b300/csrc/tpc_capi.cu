@@ -39,6 +39,10 @@ struct tpc_ctx {
   bool mask_timed = false;
   cudaEvent_t cmp_ev[6] = {};  // around the symbol, rANS and layout phases of tpc_compress (profile = 1)
   bool cmp_timed = false;
+  // the merger's item tables of the loaded batch (built on its first call after a load)
+  std::vector<int> mrg_nb, mrg_item_seg, mrg_seg_items;
+  bool mrg_tab_built = false;
+  const void* mrg_tab_dev = nullptr;  // the device copy they were uploaded to
   bool have_events = false;
   // host copies used by the debug dump and the work queue
   std::vector<uint64_t> h_item_off;
@@ -416,6 +420,8 @@ extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
   c->loaded = true;
   c->tracked = false;
   c->mask_timed = false;
+  c->mrg_tab_built = false;
+  c->mrg_tab_dev = nullptr;
   c->cmp_timed = false;
   return TPC_OK;
 }
@@ -1573,9 +1579,12 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
     trk = t;
     ids = (const uint32_t*)d;
   }
-  // neighbouring items: same event and side, sector k+1 / k-1
-  std::vector<int> nb(2 * (size_t)I, -1);
-  {
+  // neighbouring items (same event and side, sector k+1 / k-1) and segments (the items of one event
+  // and side, at most 18 listed, for the tan(lambda)-sorted candidate lists): once per load
+  const bool legs = leg_partner || leg;
+  if (!c->mrg_tab_built) {
+    std::vector<int>& nb = c->mrg_nb;
+    nb.assign(2 * (size_t)I, -1);
     std::vector<std::pair<uint64_t, int>> key(I);
     for (int i = 0; i < I; ++i) key[i] = {((uint64_t)c->h_item_event[i] << 32) | c->h_item_sector[i], i};
     std::sort(key.begin(), key.end());
@@ -1591,12 +1600,10 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
       nb[2 * i] = find(c->h_item_event[i], side * 18 + (k + 1) % 18);
       nb[2 * i + 1] = find(c->h_item_event[i], side * 18 + (k + 17) % 18);
     }
-  }
-  // segments: the items of one event and side (at most 18 listed), for the tan(lambda)-sorted
-  // candidate lists of the merger and the looper-leg search
-  const bool legs = leg_partner || leg;
-  std::vector<int> item_seg(I, -1), seg_items;
-  {
+    std::vector<int>& item_seg = c->mrg_item_seg;
+    std::vector<int>& seg_items = c->mrg_seg_items;
+    item_seg.assign(I, -1);
+    seg_items.clear();
     std::vector<std::pair<uint64_t, int>> es(I);
     for (int i = 0; i < I; ++i)
       es[i] = {((uint64_t)c->h_item_event[i] << 1) | (c->h_item_sector[i] >= 18 ? 1u : 0u), i};
@@ -1611,7 +1618,12 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
       for (size_t k = lo; k < hi; ++k) item_seg[es[k].second] = (int)sg;
       lo = hi;
     }
+    c->mrg_tab_built = true;
+    c->mrg_tab_dev = nullptr;
   }
+  const std::vector<int>& nb = c->mrg_nb;
+  const std::vector<int>& item_seg = c->mrg_item_seg;
+  const std::vector<int>& seg_items = c->mrg_seg_items;
   const int S = (int)(seg_items.size() / 19);
   // [nb 2I][item_seg I][seg_items 19S] from the host, then [seg_n S][seg_off S + 1][seg_ok S] on the device
   int* d_nb = (int*)cmp_buffer(c, 35, 4 * (3 * (size_t)I + 22 * (size_t)S + 1));
@@ -1627,15 +1639,19 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
   if (!on_device) st = (uint8_t*)cmp_buffer(c, 39, o_leg + (size_t)std::max(nt, 1ll));
   if (!d_nb || !d_first || !d_geo || !d_best || !d_lbest || (!on_device && !st))
     return fail(c, TPC_ERR_OOM, "merge buffers");
-  if ((e = cudaMemcpyAsync(d_nb, nb.data(), 8 * (size_t)I, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
-      (e = cudaMemcpyAsync(d_nb + 2 * (size_t)I, item_seg.data(), 4 * (size_t)I, cudaMemcpyHostToDevice,
-                           c->stream)) != cudaSuccess ||
-      (S && (e = cudaMemcpyAsync(d_nb + 3 * (size_t)I, seg_items.data(), 4 * seg_items.size(),
-                                 cudaMemcpyHostToDevice, c->stream)) != cudaSuccess))
-    return cuda_fail(c, e, "neighbour table");
-  unsigned int err0 = 0;
-  if ((e = cudaMemcpyAsync(&err0, c->b.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)
-    return cuda_fail(c, e, "error word");
+  if (c->mrg_tab_dev != d_nb) {  // the tables go up once per load (and again if the buffer moved)
+    if ((e = cudaMemcpyAsync(d_nb, nb.data(), 8 * (size_t)I, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+        (e = cudaMemcpyAsync(d_nb + 2 * (size_t)I, item_seg.data(), 4 * (size_t)I, cudaMemcpyHostToDevice,
+                             c->stream)) != cudaSuccess ||
+        (S && (e = cudaMemcpyAsync(d_nb + 3 * (size_t)I, seg_items.data(), 4 * seg_items.size(),
+                                   cudaMemcpyHostToDevice, c->stream)) != cudaSuccess))
+      return cuda_fail(c, e, "neighbour table");
+    c->mrg_tab_dev = d_nb;
+  }
+  // the merger's own error word, cleared on the stream (no read of the shared one before the kernels)
+  unsigned int* d_merr = (unsigned int*)cmp_buffer(c, 43, 4);
+  if (!d_merr) return fail(c, TPC_ERR_OOM, "merge buffers");
+  if ((e = cudaMemsetAsync(d_merr, 0, 4, c->stream)) != cudaSuccess) return cuda_fail(c, e, "error word");
   MrgArgs a{};
   a.trk = trk;
   a.ids = ids;
@@ -1650,6 +1666,8 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
   a.row = c->b.row;
   a.N = c->b.N;
   a.kB = 0.299792458e-2 * (double)c->cfg.bz_tesla;
+  a.kB3_hi = (float)(3.0 * a.kB);
+  a.kB3_lo = (float)(3.0 * a.kB - (double)a.kB3_hi);
   a.item_first = d_first;
   a.geo = d_geo;
   a.pre = (float4*)(d_geo + 12 * (size_t)std::max(nt, 1ll));  // 16-byte aligned: 96 bytes per track before it
@@ -1678,7 +1696,7 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
     a.partner = (int*)cmp_buffer(c, 41, 4 * (size_t)std::max(nt, 1ll));
     if (!a.partner) return fail(c, TPC_ERR_OOM, "merge buffers");
   }
-  a.err = c->b.err;
+  a.err = d_merr;
   if ((e = launch_merge(a, c->par, c->lc.num_sms, c->stream)) != cudaSuccess) return cuda_fail(c, e, "merge");
   if (!on_device && nt &&
       ((e = cudaMemcpyAsync(link, a.link, 8 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
@@ -1690,11 +1708,10 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
        (leg && (e = cudaMemcpyAsync(leg, a.leg, (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess)))
     return cuda_fail(c, e, "merge download");
   unsigned int err = 0;
-  if ((e = cudaMemcpyAsync(&err, c->b.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+  if ((e = cudaMemcpyAsync(&err, d_merr, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "merge sync");
-  if ((err & ~err0) & TPC_DERR_BAD_TRACK)
-    return fail(c, TPC_ERR_BAD_INPUT, "a track is out of range or out of item order");
+  if (err & TPC_DERR_BAD_TRACK) return fail(c, TPC_ERR_BAD_INPUT, "a track is out of range or out of item order");
   return TPC_OK;
 }
 

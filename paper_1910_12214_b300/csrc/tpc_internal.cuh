@@ -275,6 +275,7 @@ struct MrgArgs {
   const int* row;
   int N;
   double kB;
+  float kB3_hi, kB3_lo;       // 3 kB as float-float
   int* item_first;            // [I + 1] first track of every item
   double* geo;                // [n_trk][12] per-track circle (device work array)
   float4* pre;                // [n_trk] (ok ? tan lambda : NaN, q/pT, sqrt(var q/pT), sign): the FP32 prefilter

@@ -1181,8 +1181,6 @@ __device__ __forceinline__ F2 f2_from(double v) {
   return {hi, (float)(v - (double)hi)};
 }
 
-__device__ __forceinline__ double f2_val(F2 a) { return (double)a.hi + (double)a.lo; }
-
 __device__ __forceinline__ bool f2_less(F2 a, F2 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo < b.lo); }
 
 __device__ __forceinline__ bool f2_le(F2 a, F2 b) { return a.hi < b.hi || (a.hi == b.hi && a.lo <= b.lo); }
@@ -1275,6 +1273,13 @@ __global__ void k_mrg_item_first(const __grid_constant__ MrgArgs a) {
 // order like its value, and integer compares keep the reductions off the FP64 pipe
 __device__ __forceinline__ unsigned long long score_key(double sc) { return (unsigned long long)__double_as_longlong(sc); }
 
+// the same for a non-negative float-float score: the bits of hi, then lo's bits
+// mapped to an order-preserving unsigned integer (hi, lo) compare like the value
+__device__ __forceinline__ unsigned long long score_key(F2 sc) {
+  const unsigned lo = __float_as_uint(sc.lo);
+  return ((unsigned long long)__float_as_uint(sc.hi) << 32) | ((lo & 0x80000000u) ? ~lo : (lo | 0x80000000u));
+}
+
 // The compatibility tests of R-28 and the score of a compatible pair, in
 // float-float on the per-track records (geof2): a few 2^-46 relative, so every
 // decision equals the exact one except within about 1e-13 of a limit.
@@ -1314,7 +1319,7 @@ __device__ __forceinline__ bool mrg_compatible(const TrkF2& A, const TrkF2& B, b
   const F2 dz = f2_abs(f2_add({out.z, 0.0f}, f2_neg(f2_add({in.z, 0.0f}, f2_mul_f(arc, in.tgl)))));
   const F2 sc = f2_add(f2_add(f2_add(f2_mul_f(chi2, 0.0625f), f2_div(d, dlim)), f2_div(dt, f2c(kF2_002))),
                        f2_mul_f(dz, 0.5f));
-  *score = score_key(f2_val(sc));
+  *score = score_key(sc);
   return f2_le(d, dlim) && f2_le(dz, {2.0f, 0.0f});
 }
 
@@ -1515,14 +1520,14 @@ __global__ void k_mrg_best(const __grid_constant__ MrgArgs a) {
   const float kBf = (float)a.kB;
   for (long long t = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; t < a.n_trk; t += nw) {
     const double* A = a.geo + G_N * t;
-    const bool ok = A[G_OK] != 0.0;
+    const bool ok = __double_as_longlong(A[G_OK]) != 0;  // 1.0 or 0.0
     const int item = (int)trk[t].item;
     const float4 pa = a.pre[t];
     const int nb0 = ok ? a.nb_item[2 * item] : -1, nb1 = ok ? a.nb_item[2 * item + 1] : -1;
     unsigned long long bs[2] = {0, 0};
     long long bi[2] = {-1, -1};
     const TrkF2 TA = load_trk_f2(a.geof2 + 4 * t);
-    const F2 kB3 = f2_mul_f(f2_from(a.kB), 3.0f);
+    const F2 kB3 = {a.kB3_hi, a.kB3_lo};
     // the tests of candidate b of direction d (the FP32 prefilter with margins wider
     // than any FP32 rounding of the FP64 tests; a NaN tan lambda fails every comparison)
     auto consider = [&](long long b, int d) {
