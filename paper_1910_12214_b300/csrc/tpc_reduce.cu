@@ -1098,15 +1098,18 @@ cudaError_t cmp_layout(const CmpPlane* planes, int n_planes, const int* stream_p
 // Sector-track merger (Sec. 4: the pieces of one track found in neighbouring
 // sectors are joined, and the merged track is refitted).
 //
-// Every track gets its circle in the global frame (FP64); one warp per track
-// finds, in the items of the same event and side in sectors k+1 and k-1, the
-// compatible candidate of smallest score (a curvature chi2, the continuation
-// on the better-measured circle, tan(lambda), z along the arc); a link joins
-// two tracks that are each other's best in opposite directions.  Links are
-// mutual and one per direction, so every group is a path through neighbouring
-// sectors: a bounded walk labels it by its smallest index.  One warp per group
-// then refits the group's clusters in the global frame (algebraic circle fit,
-// then z against the arc): per-cluster sums in float-float, the solves in FP64.
+// Every track gets its circle in the global frame (FP64, with FP32 and
+// float-float copies); the tracks of each event and side are sorted by
+// tan(lambda).  One warp per track finds, among the tracks of sectors k+1 and
+// k-1 inside its tan(lambda) window, the compatible candidate of smallest
+// score (a curvature chi2, the continuation on the better-measured circle,
+// tan(lambda), z along the arc): FP32 prefilters with safe margins, then the
+// tests in float-float.  A link joins two tracks that are each other's best
+// in opposite directions.  Links are mutual and one per direction, so every
+// group is a path through neighbouring sectors: a bounded walk labels it by
+// its smallest index.  One warp per group then refits the group's clusters in
+// the global frame (algebraic circle fit, then z against the arc): per-cluster
+// sums in float-float, the solves in FP64 one group per thread.
 namespace {
 
 constexpr double MRG_WEDGE = 2.0 * 3.14159265358979323846 / 18.0;
@@ -1114,8 +1117,8 @@ constexpr int MRG_FIT_NACC = 14;                        // float-float sums of t
 constexpr int MRG_FIT_SUMS = 4 + 2 * MRG_FIT_NACC + 2;  // floats per group record: n, members, mean, sums
 
 // Float-float ("double-float") numbers for the compatibility tests and the
-// refit's per-cluster sums: a
-// value is hi + lo with |lo| <= ulp(hi) / 2, a 48-bit significand computed on
+// refit's per-cluster sums: a value is hi + lo with |lo| <= ulp(hi) / 2, a
+// 48-bit significand computed on
 // the FP32 pipe, which the B300 has about 60 times wider than the FP64 one.
 // The error-free transformations are Knuth's TwoSum, Dekker's Fast2Sum (valid
 // for |a| >= |b|) and the fused-multiply-add TwoProduct; the additions are the
