@@ -39,7 +39,6 @@ const double SIN_MAX = 0.93969262078590838; // sin(70 deg)
 const int MIN_HITS = 10;                 // minimum tracklet / track size
 const double SNP_LIMIT = 0.9999;         // propagation validity
 const double C0_DIAG_ANGLE = 1.0, C0_DIAG_QPT = 100.0;
-const double INFLATE = 100.0;            // covariance inflation of the inward refit
 
 struct Row {  // one (item, pad row) of the binning grid
   int pos0 = 0, n = 0, ymin = 0, zmin = 0, shift = SHIFT_MIN, ny = 0, nz = 0;
@@ -437,9 +436,10 @@ int row_of_pos(const orc_result* R, int item, int pos) {
 //        along the chain (chain hits are accepted without a chi2 test);
 //  (ii)  extension to outer rows: predict, take the best hit with chi2 <= 16,
 //        stop after 5 consecutive misses;
-//  (iii) a refit from the outermost hit towards the inner rows, with the
-//        outer direction and curvature as starting values and their variances
-//        inflated 100-fold, re-picking hits as in (ii).
+//  (iii) a fresh fit from the outermost hit towards the inner rows: the outer
+//        direction and curvature are only the starting values, the covariance
+//        starts again from C0, so the refit's chi2 counts each hit once
+//        (ndf = 2n - 5); hits are re-picked as in (ii).
 // Pieces of one track that start from different chain heads reach the same
 // outermost hit in (ii) and would refit the same hits in (iii): only the
 // tracklet with the smallest id among those sharing an outermost hit runs
@@ -451,7 +451,7 @@ int row_of_pos(const orc_result* R, int item, int pos) {
 struct Outward {
   bool ok = false;
   int out_hit = -1, out_row = 0;
-  double out_p[5] = {0, 0, 0, 0, 0}, out_var[3] = {0, 0, 0};
+  double out_p[5] = {0, 0, 0, 0, 0};
 };
 
 void outward(Ctx& c, int start, Tracklet& T, Outward& O) {
@@ -484,7 +484,7 @@ void outward(Ctx& c, int start, Tracklet& T, Outward& O) {
   set_c0(C, c.vy, c.vz);
   double x = x1;
   int out_hit = chain[0], out_row = chain_row[0];
-  double out_p[5], out_var[3] = {C[2][2], C[3][3], C[4][4]};
+  double out_p[5];
   std::memcpy(out_p, p, sizeof(p));
   bool alive = true;
   for (size_t i = 1; i < chain.size(); ++i) {
@@ -497,9 +497,6 @@ void outward(Ctx& c, int start, Tracklet& T, Outward& O) {
     out_hit = chain[i];
     out_row = r;
     std::memcpy(out_p, p, sizeof(p));
-    out_var[0] = C[2][2];
-    out_var[1] = C[3][3];
-    out_var[2] = C[4][4];
   }
   // (ii) extension outwards
   if (alive) {
@@ -517,16 +514,12 @@ void outward(Ctx& c, int start, Tracklet& T, Outward& O) {
       out_hit = h;
       out_row = r;
       std::memcpy(out_p, p, sizeof(p));
-      out_var[0] = C[2][2];
-      out_var[1] = C[3][3];
-      out_var[2] = C[4][4];
     }
   }
   O.ok = true;
   O.out_hit = out_hit;
   O.out_row = out_row;
   std::memcpy(O.out_p, out_p, sizeof(out_p));
-  std::memcpy(O.out_var, out_var, sizeof(out_var));
 }
 
 void inward(Ctx& c, Tracklet& T, const Outward& O) {
@@ -535,17 +528,13 @@ void inward(Ctx& c, Tracklet& T, const Outward& O) {
   auto X = [&](int r) { return R->row_x[r]; };
   const int out_hit = O.out_hit, out_row = O.out_row;
   const double* out_p = O.out_p;
-  const double* out_var = O.out_var;
   double C[5][5];
-  // (iii) refit inwards from the outermost hit: its measured y, z; the outward
-  // direction and curvature with their variances inflated 100-fold (at most the
-  // initial ones), so that the refit is well conditioned and the outward fit
-  // enters with 1% of its weight.
+  // (iii) refit inwards from the outermost hit: its measured y, z and the
+  // outward direction and curvature as the starting state, with the initial
+  // covariance C0, so that the outward fit (of largely the same hits) does not
+  // enter the refit's estimate or its chi2 a second time.
   double q[5] = {c.hy(out_hit), c.hz(out_hit), out_p[2], out_p[3], out_p[4]};
   set_c0(C, c.vy, c.vz);
-  C[2][2] = std::min(C0_DIAG_ANGLE, INFLATE * out_var[0]);
-  C[3][3] = std::min(C0_DIAG_ANGLE, INFLATE * out_var[1]);
-  C[4][4] = std::min(C0_DIAG_QPT, INFLATE * out_var[2]);
   double x = X(out_row);
   T.hits.assign(1, out_hit);
   T.chi2 = 0.0;

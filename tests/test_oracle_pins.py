@@ -8,6 +8,7 @@ exact (noise-free) helices, and the chi2 / pull statistics of smeared ones.
 import json
 import math
 import os
+import types
 
 import numpy as np
 import pytest
@@ -425,6 +426,48 @@ def test_smeared_helices_chi2_and_pulls():
     P = P[good]
     assert np.all(np.abs(P.mean(0)) < 0.1)
     assert np.all((P.std(0) > 0.9) & (P.std(0) < 1.1))
+
+
+def _dedup_fixture():
+    g = json.load(open(os.path.join(HERE, "golden", "refit_dedup.json")))
+    geo = g["geometry"]
+
+    def x(r):
+        return geo["x_min"] + r * geo["row_pitch"]
+
+    x0, x29 = x(0), x(29)
+
+    def y_q(xx):
+        return 2.0 - 0.02 * (xx - x29)
+
+    def y_p(xx):
+        return y_q(xx) - 2.4 * (x29 - xx) / (x29 - x0)
+
+    pts = ([(r, y_p(x(r))) for r in list(range(10)) + list(range(13, 29))] + [(r, y_q(x(r))) for r in range(29)] +
+           [(29, 2.0)])
+    cl = types.SimpleNamespace()
+    cl.row = np.array([p[0] for p in pts], np.int32)
+    cl.x = np.array([x(p[0]) for p in pts], np.float32)
+    cl.y = np.array([p[1] for p in pts], np.float32)
+    cl.z = np.array([10 + 0.3 * (x(p[0]) - 85) for p in pts], np.float32)
+    cl.item_off = np.array([0, len(pts)], np.uint64)
+    cfg = oracle.OracleConfig(n_rows=geo["n_rows"], x_min=geo["x_min"], x_max=x(29), bz_tesla=geo["bz_tesla"])
+    return g, cl, cfg
+
+
+def test_one_refit_per_outermost_hit_golden():
+    """Hand-worked fixture (tests/golden/refit_dedup.json): three tracklets end on
+    one hit; only the smallest id is refitted.  Keeping the largest id, the most
+    outward hits, or every tracklet gives another track set."""
+    g, cl, cfg = _dedup_fixture()
+    r = oracle.run(cl, cfg)
+    assert r["starts"].tolist() == [1, 27, 11]  # P1, Q1, P14 in canonical order
+    assert r["up"][9] == -1 and r["dn"][10] == -1  # P9 and P13 have no links (the gap)
+    e = g["expected"]
+    assert r["tl_n"].tolist() == e["tl_n"]
+    assert r["trk_i"].shape[0] == e["n_tracks"]
+    assert int(r["trk_i"][0, 3]) == e["tracklet"]
+    assert sorted(r["trk_ids"].tolist()) == e["cluster_ids"]
 
 
 # ------------------------------------------------------------------ selection
