@@ -470,6 +470,47 @@ def test_one_refit_per_outermost_hit_golden():
     assert sorted(r["trk_ids"].tolist()) == e["cluster_ids"]
 
 
+def test_refit_prior_keeps_short_low_pt_pulls_unbiased():
+    """The inward refit starts from the outward variances x100: it re-uses 1% of
+    the outward information, which must not show on the tracks where the
+    outward fit carries the most weight.  Short low-pT tracks (pT < 0.3 GeV/c,
+    <= 30 hits, 40 events): chi2/ndf ~ 1 and pull widths within [0.9, 1.2]
+    (with the variances x1 they reach 1.25-1.7)."""
+    allp, chi, ndf = [], 0.0, 0.0
+    for seed in range(1, 41):
+        cl = synth.make_config1(seed=seed, noise_frac=0.0)
+        r = oracle.run(cl)
+        ti, ids, f = r["trk_i"], r["trk_ids"], r["trk_f"]
+        keep = np.zeros(f.shape[0], bool)
+        for k in range(f.shape[0]):
+            s = ids[ti[k, 1]:ti[k, 1] + ti[k, 2]]
+            lab = np.bincount(cl.mc[s][cl.mc[s] >= 0]).argmax()
+            keep[k] = cl.tracks["pt"][lab] < 0.3 and ti[k, 2] <= 30
+        sub = dict(r, trk_f=f[keep], trk_i=ti[keep])
+        allp.append(_pulls(cl, sub))
+        chi += f[keep, 21].sum()
+        ndf += f[keep, 22].sum()
+    P = np.concatenate(allp)
+    assert P.shape[0] >= 200
+    assert 0.93 <= chi / ndf <= 1.07
+    good = np.all(np.abs(P) < 5, axis=1)
+    assert good.mean() > 0.99
+    P = P[good]
+    assert np.all(np.abs(P.mean(0)) < 0.2)
+    assert np.all((P.std(0) > 0.9) & (P.std(0) < 1.2))
+
+
+def test_refit_prior_efficiency_full_event():
+    """Why the refit does not start from C0: from C0 its first rows are
+    unconstrained and, where the track's own hit is missing, it follows a
+    neighbour's hit.  Full TPC event: efficiency >= 98% with the x100 prior
+    (97.0% from C0), fake rate below 0.3%."""
+    cl = synth.make_config2(seed=1)
+    r = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids"])
+    e = trackeval.efficiency(cl, r["trk_i"], r["trk_ids"])
+    assert e["eff"] >= 0.98 and e["fake_rate"] < 0.003, e
+
+
 # ------------------------------------------------------------------ selection
 def test_selection_matches_brute_force():
     cl = synth.make_config2(seed=2, n_tracks=1500)
