@@ -41,7 +41,8 @@ constexpr float SNP_LIMIT = 0.9999f;
 constexpr int MIN_HITS = 10;
 constexpr int SHIFT_MIN = 10;
 constexpr long long LINK_D = 512;       // 0.5 cm chord deviation
-constexpr float INFLATE = 100.0f;       // covariance inflation of the inward refit
+constexpr float INFLATE = 100.0f;       // refit prior: outward variances x100 (at most C0)
+constexpr int JOSEPH_UPDATES = 3;       // first updates of a fit done in the Joseph form
 constexpr int LINK_THREADS = 256;
 constexpr int LINK_MAXC = 24;           // window candidates per side and hit
 constexpr int LINK_MAXC_STAGED = 8;     // the same in k_links (overflow: direct enumeration)
@@ -816,6 +817,55 @@ __device__ __forceinline__ float kf_update(const Win& w, float* p, float* C, flo
   return fma2(r0, fma2(I00, r0, I01, r1), r1, fma2(I01, r0, I11, r1));
 }
 
+// The same update with the covariance in the Joseph form
+//   C <- (I - K H) C (I - K H)^T + K V K^T,   V = diag(vy, vz):
+// algebraically equal to kf_update's C - K H C, but a sum of symmetric
+// positive terms instead of a difference.  A fit that starts from C0 (angle
+// variances 1, q/pT variance 100 against 0.01 cm^2 measurements) cancels most
+// digits of the small covariance entries in its first updates: in FP32 the
+// difference form lost up to 4% in q/pT on short low-pT tracks refitted from
+// C0, this form keeps them within 1e-3 of the FP64 filter.  Every product and
+// sum is an explicit fused operation, so every kernel that inlines this
+// rounds alike.
+__device__ __forceinline__ float kf_update_joseph(const Win& w, float vy, float vz, float* p, float* C, float r0,
+                                                  float r1) {
+  const float I00 = w.S11 * w.inv_det, I01 = -w.S01 * w.inv_det, I11 = w.S00 * w.inv_det;
+  float M[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      M[i][j] = C[ix(i, j)];
+      M[j][i] = C[ix(i, j)];
+    }
+  float K0[5], K1[5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    K0[i] = fma2(M[i][0], I00, M[i][1], I01);
+    K1[i] = fma2(M[i][0], I01, M[i][1], I11);
+  }
+#pragma unroll
+  for (int i = 0; i < 5; ++i) p[i] += fma2(K0[i], r0, K1[i], r1);
+  // T = (I - K H) C (rows 0..4; columns 0, 1 and the lower triangle are used)
+  float T[5][5];
+#pragma unroll
+  for (int i = 0; i < 5; ++i)
+#pragma unroll
+    for (int j = 0; j < 5; ++j) T[i][j] = __fmaf_rn(-K0[i], M[0][j], __fmaf_rn(-K1[i], M[1][j], M[i][j]));
+#pragma unroll
+  for (int i = 0; i < 5; ++i) {
+    const float a0 = __fmul_rn(vy, K0[i]), a1 = __fmul_rn(vz, K1[i]);
+#pragma unroll
+    for (int j = 0; j <= i; ++j) {
+      float v = __fmaf_rn(-T[i][0], K0[j], T[i][j]);
+      v = __fmaf_rn(-T[i][1], K1[j], v);
+      v = __fmaf_rn(a0, K0[j], v);
+      C[ix(i, j)] = __fmaf_rn(a1, K1[j], v);
+    }
+  }
+  return fma2(r0, fma2(I00, r0, I01, r1), r1, fma2(I01, r0, I11, r1));
+}
+
 __device__ __forceinline__ bool cov_ok(const float* C) {
   bool ok = true;
 #pragma unroll
@@ -1135,6 +1185,8 @@ __device__ __forceinline__ int pick_hit(const Src& S, const Grp<G>& g, int r, co
 //  (iii) inward refit from the outermost hit (its y, z; outward sinphi,
 //        tanlambda, q/pT with variances inflated 100-fold), re-picking hits
 //        down to row 0.
+// The first JOSEPH_UPDATES updates of each fit use the Joseph form (FP32
+// conditioning of a fit from a wide prior).
 // Guards end a pass: |sinphi| >= sin 70 deg, |y| > x tan(half angle), invalid
 // step.  A non-finite or non-positive covariance diagonal drops the tracklet.
 // z is carried relative to the start hit (z_base) so that FP32 keeps its
@@ -1192,7 +1244,7 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
   // fetched one row ahead of their use
   int hn = hn0, hn2 = hn1;
   int4 qn = S.hit(L > 1 ? r0 + 1 : r0, hn);
-  int misses = 0;
+  int misses = 0, n_upd = 0;
   for (int r = r0 + 1; r < NR && misses < MAX_MISS; ++r) {
     const int i = r - r0;  // chain index of row r
     const bool chain = i < L;
@@ -1218,7 +1270,11 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
       ++misses;
       continue;
     }
-    kf_update(w, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
+    if (n_upd < JOSEPH_UPDATES)
+      kf_update_joseph(w, P.vy, P.vz, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
+    else
+      kf_update(w, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
+    ++n_upd;
     if (!cov_ok(C)) {
       dead = true;
       break;
@@ -1309,7 +1365,8 @@ __device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g,
         ++misses;
         continue;
       }
-      chi2sum += kf_update(w, q5, C, q.x * Q - q5[0], (float)(q.y - z_base) * Q - q5[1]);
+      const float e0 = q.x * Q - q5[0], e1 = (float)(q.y - z_base) * Q - q5[1];
+      chi2sum += n <= JOSEPH_UPDATES ? kf_update_joseph(w, P.vy, P.vz, q5, C, e0, e1) : kf_update(w, q5, C, e0, e1);
       if (!cov_ok(C)) {
         dead = true;
         break;
