@@ -262,9 +262,9 @@ tpc_status tpc_autotune_mode(tpc_ctx* ctx, int iters, int mode, tpc_tuning* best
  * library (16 bytes per cluster, TPC_NOALLOC_MAX_CLUSTERS clusters; held by
  * every GPU that loads the library until the process exits).  Larger inputs
  * are rejected with TPC_ERR_CAPACITY before any GPU work; n_rows must be
- * 1..256.  The first call on a device looks up that array's device address,
- * so make the first call on each device before any stream capture.  Every
- * call uses the same array and it keeps the previous call's contents; calls
+ * 1..256.  Every call looks up that array's address in the current context
+ * and waits for its stream, so it cannot be called during stream capture.
+ * Every call uses the same array and it keeps the previous call's contents; calls
  * that overlap on the GPU (other streams, other host threads) race on it, so
  * run them one after another.  Returns TPC_ERR_BAD_INPUT if a row is out of
  * range or a coordinate is not finite (such clusters are left out). */

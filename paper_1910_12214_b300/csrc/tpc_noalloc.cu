@@ -16,7 +16,6 @@
 
 #include <cmath>
 #include <cstdint>
-#include <mutex>
 
 #include "tpc.h"
 
@@ -25,8 +24,8 @@ namespace {
 constexpr int NA_THREADS = 1024;
 constexpr int NA_MAX_ROWS = 256;
 
-// Scratch of one call: grouped (row-contiguous, unsorted) hits and their ids,
-// the arrival slot of every hit in its bin, and an error word.  Every call
+// Scratch of one call: grouped (row-contiguous, in input order) hits and
+// their ids, the slot of every hit in its bin, and an error word.  Every call
 // writes each entry it later reads, except the error word, which the kernel
 // clears first.  Size: 16 bytes per cluster (1 MiB) plus 256 bytes.
 struct __align__(16) NoAllocScratch {
@@ -68,12 +67,37 @@ __device__ __forceinline__ int na_block_excl_scan(int v, int* sm, int* total) {
   return r;
 }
 
+// Stable ranks for one chunk of blockDim.x items, one per thread in thread
+// order: each valid item gets counters[key] plus the number of valid items of
+// the same key in earlier threads of the chunk, and counters[key] grows by the
+// chunk's count of that key.  Within a warp the lanes of one key are found by
+// match_any (the lowest lane adds the warp's count); the warps add in warp
+// order, one per barrier.  The whole block must call it (uniform control flow).
+__device__ __forceinline__ int na_stable_rank(int key, bool valid, int* counters) {
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  // invalid lanes share a key no valid lane has (keys are >= 0)
+  const unsigned peers = __match_any_sync(0xffffffffu, valid ? key : -1);
+  const int leader = __ffs(peers) - 1;
+  const int before = __popc(peers & ((1u << lane) - 1u));
+  int base = 0;
+  for (int k = 0; k < nw; ++k) {
+    if (w == k && valid && lane == leader) {
+      base = counters[key];
+      counters[key] = base + __popc(peers);
+    }
+    __syncthreads();
+  }
+  return __shfl_sync(0xffffffffu, base, leader) + before;
+}
+
 // One CTA bins the whole sector: quantise y, z to 2^-10 cm (round half to
 // even; the scale is exact in FP32), per-row counts and extents, bin edge 2^s
 // quanta with s the smallest s >= 10 such that n*4^s >= Ly*Lz and
-// ny*nz <= 2n+2, counting sort into rows, then per row a bin histogram, scan,
-// scatter and in-bin sort by original id.  The output layout equals the one of
-// the tracker's own binning step for a single item.
+// ny*nz <= 2n+2, a stable counting sort into rows (input order kept inside a
+// row), then per row a bin histogram, scan and stable scatter, so that a bin
+// holds its hits in input order (the canonical order: row, bin, original
+// index) without a sort.  The output layout equals the one of the tracker's
+// own binning step for a single item.
 __global__ void __launch_bounds__(NA_THREADS) k_bin_sector_noalloc(NoAllocScratch* sc, const float* y, const float* z,
                                                                    const int* row, int n, int n_rows, int4* sorted,
                                                                    int* rows_out, int* first_out) {
@@ -148,17 +172,26 @@ __global__ void __launch_bounds__(NA_THREADS) k_bin_sector_noalloc(NoAllocScratc
     o[7] = bin_ex;
   }
   __syncthreads();
-  // counting sort into rows (arrival order inside a row; made canonical below)
-  for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    const float yv = y[i], zv = z[i];
-    const int rr = row[i];
-    if (!(rr >= 0 && rr < n_rows && fabsf(yv) <= 1e6f && fabsf(zv) <= 1e6f)) continue;
-    const int gp = s_pos0[rr] + atomicAdd(&s_fill[rr], 1);
-    sc->g_q[gp] = make_int2(__float2int_rn(yv * 1024.0f), __float2int_rn(zv * 1024.0f));
-    sc->g_id[gp] = i;
+  // stable counting sort into rows: chunks of the input in index order
+  for (int base = 0; base < n; base += blockDim.x) {
+    const int i = base + threadIdx.x;
+    float yv = 0.f, zv = 0.f;
+    int rr = -1;
+    if (i < n) {
+      yv = y[i];
+      zv = z[i];
+      rr = row[i];
+    }
+    const bool ok = i < n && rr >= 0 && rr < n_rows && fabsf(yv) <= 1e6f && fabsf(zv) <= 1e6f;
+    const int rank = na_stable_rank(ok ? rr : 0, ok, s_fill);
+    if (ok) {
+      const int gp = s_pos0[rr] + rank;
+      sc->g_q[gp] = make_int2(__float2int_rn(yv * 1024.0f), __float2int_rn(zv * 1024.0f));
+      sc->g_id[gp] = i;
+    }
   }
   __syncthreads();
-  // per row: bin histogram (in first_out), exclusive scan, scatter, in-bin sort by id
+  // per row: bin histogram (in first_out), exclusive scan, stable scatter
   for (int rr = 0; rr < n_rows; ++rr) {
     const int cn = s_cnt[rr], p0 = s_pos0[rr], b0 = s_bin0[rr];
     const int nbr = cn > 0 ? s_ny[rr] * s_nz[rr] : 0;
@@ -166,10 +199,15 @@ __global__ void __launch_bounds__(NA_THREADS) k_bin_sector_noalloc(NoAllocScratc
     for (int j = threadIdx.x; j <= nbr; j += blockDim.x) hist[j] = 0;
     __syncthreads();
     const int sh = s_shift[rr], ymin = s_min[0][rr], zmin = s_min[2][rr], nzr = s_nz[rr];
-    for (int j = threadIdx.x; j < cn; j += blockDim.x) {
-      const int2 q = sc->g_q[p0 + j];
-      const int bin = ((q.x - ymin) >> sh) * nzr + ((q.y - zmin) >> sh);
-      sc->slot[p0 + j] = atomicAdd(&hist[bin], 1);
+    for (int base = 0; base < cn; base += blockDim.x) {  // block-uniform loop
+      const int j = base + threadIdx.x;
+      int bin = 0;
+      if (j < cn) {
+        const int2 q = sc->g_q[p0 + j];
+        bin = ((q.x - ymin) >> sh) * nzr + ((q.y - zmin) >> sh);
+      }
+      const int slot = na_stable_rank(bin, j < cn, hist);
+      if (j < cn) sc->slot[p0 + j] = slot;
     }
     __syncthreads();
     int carry = 0;
@@ -188,28 +226,11 @@ __global__ void __launch_bounds__(NA_THREADS) k_bin_sector_noalloc(NoAllocScratc
       sorted[p0 + hist[bin] + sc->slot[p0 + j]] = make_int4(q.x, q.y, sc->g_id[p0 + j], rr);
     }
     __syncthreads();
-    for (int bin = threadIdx.x; bin < nbr; bin += blockDim.x) {
-      const int a = p0 + hist[bin], e = p0 + hist[bin + 1];
-      for (int i = a + 1; i < e; ++i) {
-        const int4 v = sorted[i];
-        int j = i - 1;
-        while (j >= a && sorted[j].z > v.z) {
-          sorted[j + 1] = sorted[j];
-          --j;
-        }
-        sorted[j + 1] = v;
-      }
-    }
-    __syncthreads();
     for (int j = threadIdx.x; j <= nbr; j += blockDim.x) hist[j] += p0;
     __syncthreads();
   }
   if (threadIdx.x == 0) sc->err = s_err;
 }
-
-// Device address of the scratch array, looked up once per device.
-std::mutex g_mu;
-void* g_scratch_ptr[64] = {};
 
 }  // namespace
 
@@ -217,23 +238,14 @@ extern "C" tpc_status tpc_bin_sector_noalloc(const float* y, const float* z, con
                                              int32_t* sorted, int32_t* rows_out, int32_t* first_out, void* stream) {
   if (n > TPC_NOALLOC_MAX_CLUSTERS || n_rows < 1 || n_rows > NA_MAX_ROWS) return TPC_ERR_CAPACITY;
   if ((n > 0 && (!y || !z || !row || !sorted)) || !rows_out || !first_out) return TPC_ERR_INVALID_ARG;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+  // The array's host-side name is not a device address: look the address up
+  // in the current context on every call (it allocates nothing).  An address
+  // kept from an earlier call could belong to another context of the device
+  // (a caller's own context, or one made after cudaDeviceReset).
+  void* ptr = nullptr;
+  if (cudaGetSymbolAddress(&ptr, g_noalloc_scratch) != cudaSuccess || !ptr) {
     cudaGetLastError();
     return TPC_ERR_CUDA;
-  }
-  void* ptr = nullptr;
-  {
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_scratch_ptr[dev]) {
-      // the current device is `dev`: the symbol resolves to its copy of the array
-      if (cudaGetSymbolAddress(&g_scratch_ptr[dev], g_noalloc_scratch) != cudaSuccess) {
-        cudaGetLastError();
-        g_scratch_ptr[dev] = nullptr;
-        return TPC_ERR_CUDA;
-      }
-    }
-    ptr = g_scratch_ptr[dev];
   }
   cudaStream_t s = (cudaStream_t)stream;
   k_bin_sector_noalloc<<<1, NA_THREADS, 0, s>>>(static_cast<NoAllocScratch*>(ptr), y, z, row, (int)n, n_rows,
