@@ -61,7 +61,7 @@ def test_tracks_on_corrected_clusters_match_oracle(distorted):
     same = np.mean((ref["sorted_qy"] == q[:, 0]) & (ref["sorted_qz"] == q[:, 1]))
     assert same > 0.99
     r = compare_tracks(ocl, trk, ids, ref)
-    assert r["matched"] >= 0.995 and r["param_ok"] >= 0.99, r
+    assert r["matched"] >= 0.995 and r["param_ok"] >= 0.995, r
 
 
 def test_correction_restores_tracking(distorted):
@@ -77,4 +77,6 @@ def test_correction_restores_tracking(distorted):
     chi_g = trk_g["chi2"].sum() / trk_g["ndf"].sum()
     print("eff undistorted", e0["eff"], "distorted none", en["eff"], "grid", eg["eff"], "chi2/ndf", chi_n, chi_g)
     assert eg["eff"] >= e0["eff"] - 0.02
-    assert chi_g < 1.3 and chi_n > 2 * chi_g
+    # the uncorrected distortion (up to 10 cm) shows in the fit quality; the
+    # correction brings chi2/ndf back to about 1
+    assert chi_g < 1.3 and chi_n > 1.5 * chi_g
