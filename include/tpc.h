@@ -71,6 +71,8 @@ typedef struct {
   uint32_t max_items;         /* initial reservation (0 = grow on demand) */
   const tpc_allocator* allocator; /* NULL = cudaMallocAsync */
   int profile;                /* 1 = record per-step CUDA events for tpc_stage_times */
+  const char* tune_cache_path;/* nullable: text file of autotuner results, read and updated by
+                                 tpc_autotune (the string is copied at tpc_init) */
 } tpc_config;
 
 /* Cluster batch, SoA, grouped by work item (event, sector[, time slice]).
@@ -109,22 +111,53 @@ typedef struct {
   uint32_t item, sector, event, first_cluster, n_clusters;
 } tpc_track_t;
 
-/* Creates a context on cfg->device.  *out receives the context or NULL. */
+/* Creates a context on cfg->device: one GPU of the reconstruction farm that
+ * runs the synchronous TPC processing (Sec. 2).  *out receives the context or
+ * NULL; the config is copied. */
 tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out);
 
-/* Loads one batch of clusters (copied to the device if on_device = 0) and
- * resets the previous output.  Grows the device buffers if needed. */
+/* Loads one batch of clusters from the cluster finder (Sec. 4, first step of
+ * the processing chain): items of (event, sector) or, under continuous
+ * read-out (Abstract, Sec. 2), time-frame slices.  Copied to the device if
+ * on_device = 0; resets the previous output; grows the device buffers if
+ * needed. */
 tpc_status tpc_load_clusters(tpc_ctx* ctx, const tpc_clusters* cl);
 
-/* Runs every step of the tracker on the loaded batch: quantisation, per-row
- * grids, neighbour links, mutual cleaning, start hits, Kalman tracklets,
- * shared-cluster resolution and output compaction.  Asynchronous. */
+/* Loads a continuous read-out time frame (the paper's Abstract and Sec. 2:
+ * 50 kHz continuous read-out with no a-priori vertex, so cluster z carries the
+ * drift-time offset of its collision) and cuts it into overlapping slices on
+ * the device, each an ordinary item of the loaded batch.  fr: the frame's
+ * clusters as in tpc_load_clusters, its items normally the 36 sectors with
+ * their whole z axis; item_core must be NULL.  Each item is cut along z into
+ * cores [c0 + k core_cm, c0 + (k + 1) core_cm) from c0 = floor(zmin / core_cm)
+ * core_cm up to the item's largest z (at most 64 per item); slice k holds every
+ * cluster of the item with c0 + k core - overlap <= z < c0 + (k + 1) core +
+ * overlap (decided as in FP64), in the frame's order, and reports a track only
+ * if its innermost cluster's z lies in the core.  With an overlap longer than a
+ * track's z extent slicing does not change the result: the tracks are those of
+ * the whole frame.  0 <= overlap_cm <= 3 core_cm.  The output cluster ids of
+ * tpc_get_tracks / tpc_device_tracks are frame indices; a track's item is its
+ * slice (sector and event from the frame item).  tpc_debug_dump shows the
+ * sliced batch; the data-reduction calls (tpc_reduce.h) refuse a frame
+ * (TPC_ERR_STATE).  The call waits for its stream (it reads the slice sizes).
+ * Errors: TPC_ERR_BAD_INPUT for a non-finite z, TPC_ERR_CAPACITY for more than
+ * 64 slices in one item. */
+tpc_status tpc_load_frame(tpc_ctx* ctx, const tpc_clusters* fr, float core_cm, float overlap_cm);
+
+/* Runs every step of the tracker on the loaded batch (Sec. 3: cellular-
+ * automaton track finding followed by a Kalman fit, derived from the Run 2 HLT
+ * tracker): quantisation, per-row grids, neighbour links, mutual cleaning,
+ * start hits, Kalman tracklets (segments at |phi| >= 70 deg are not fitted and
+ * a numerical failure ends a fit, Sec. 4), shared-cluster resolution (a
+ * cluster goes to one track only, Sec. 4) and output compaction.
+ * Asynchronous. */
 tpc_status tpc_track(tpc_ctx* ctx);
 
 /* Waits for the stream and returns a device-side error if one was flagged. */
 tpc_status tpc_sync(tpc_ctx* ctx);
 
-/* Waits for the stream and copies the tracks and their cluster ids to the
+/* Waits for the stream and copies the tracks and their cluster ids (the
+ * cluster-to-track attachment the compression steps consume, Sec. 4) to the
  * caller's host buffers.  *n_trk and *n_ids always receive the required sizes;
  * if trk_cap or id_cap is too small nothing is copied and TPC_ERR_CAPACITY is
  * returned.  trk / cluster_ids may be NULL with zero capacity (size query). */
@@ -141,7 +174,9 @@ tpc_status tpc_device_tracks(tpc_ctx* ctx, const tpc_track_t** trk, const uint32
  * last run's mode does not have read 0 (plain mode: 0..8, batched: 9..10).
  * Entries 11..12 are the two kernels of the last tpc_cluster_masks() call and
  * 13..15 the symbol, rANS and layout phases of the last tpc_compress() call
- * (tpc_reduce.h) since the batch was loaded, else 0. */
+ * (tpc_reduce.h) since the batch was loaded, else 0.  Entry 16 is the
+ * space-point correction (grid or network) of the last tpc_track(), 0 when no
+ * correction is on. */
 tpc_status tpc_stage_times(tpc_ctx* ctx, float* us, int n, int* n_stages);
 const char* tpc_stage_name(int i);
 
@@ -238,7 +273,10 @@ tpc_status tpc_get_tuning(tpc_ctx* ctx, tpc_tuning* t);
  * (lane groups x block sizes x shared-memory budgets), times each with CUDA
  * events (median of `iters` runs), keeps the fastest in the context and
  * returns it in *best (nullable) with its time in *best_us (nullable).  The
- * last run leaves the batch tracked with the chosen shape. */
+ * last run leaves the batch tracked with the chosen shape.  With a
+ * cfg.tune_cache_path, a result stored for the same GPU, mode and batch shape
+ * (clusters, items, rows, correction) is used without a search, and a new
+ * search's result is stored. */
 tpc_status tpc_autotune(tpc_ctx* ctx, int iters, tpc_tuning* best, float* best_us);
 /* The same over the shapes of one mode only (1 = plain, 2 = batched; 0 = both,
  * as tpc_autotune), for comparing the two modes at their best shapes. */

@@ -9,7 +9,7 @@ HERE = os.path.dirname(os.path.abspath(__file__))
 ROOT = os.path.dirname(HERE)
 CSRC = os.path.join(HERE, "csrc")
 LIB = os.path.join(HERE, "libtpc.so")
-SOURCES = ["tpc_kernels.cu", "tpc_capi.cu", "tpc_mlp.cu", "tpc_noalloc.cu", "tpc_reduce.cu"]
+SOURCES = ["tpc_kernels.cu", "tpc_capi.cu", "tpc_mlp.cu", "tpc_noalloc.cu", "tpc_reduce.cu", "tpc_frame.cu"]
 NVCC_FLAGS = ["-gencode", "arch=compute_103a,code=sm_103a", "-lineinfo", "-O3", "-std=c++17",
               "-Xcompiler", "-fPIC", "-Xcompiler", "-O2", "--expt-relaxed-constexpr"]
 

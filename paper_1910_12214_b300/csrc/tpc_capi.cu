@@ -5,6 +5,8 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <fstream>
+#include <sstream>
 #include <string>
 #include <vector>
 
@@ -14,6 +16,7 @@
 
 struct tpc_ctx {
   tpc_config cfg{};
+  std::string tune_path;  // autotuner cache file (cfg.tune_cache_path), empty = none
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   bool has_alloc = false;
@@ -37,7 +40,9 @@ struct tpc_ctx {
   cudaEvent_t ev[TPC_N_STAGES + 1] = {};
   cudaEvent_t mask_ev[3] = {};  // around the two kernels of tpc_cluster_masks (profile = 1)
   bool mask_timed = false;
-  cudaEvent_t cmp_ev[6] = {};  // around the symbol, rANS and layout phases of tpc_compress (profile = 1)
+  cudaEvent_t cmp_ev[6] = {};
+  cudaEvent_t corr_ev[2] = {};  // around the space-point correction of the last tpc_track (profile = 1)
+  bool corr_timed = false;  // around the symbol, rANS and layout phases of tpc_compress (profile = 1)
   bool cmp_timed = false;
   // the merger's item tables of the loaded batch (built on its first call after a load)
   std::vector<int> mrg_nb, mrg_item_seg, mrg_seg_items;
@@ -52,6 +57,30 @@ struct tpc_ctx {
   bool batched = false, use_graph = false, last_batched = false;
   cudaGraphExec_t graph = nullptr;
   Buffers graph_b{}, graph_tb{};  // kernel arguments the graph was built with
+  const int* graph_src = nullptr;  // frame id map the graph was built with
+  // time frames (tpc_load_frame): persistent work buffers, grown on demand;
+  // frame_src != null while the loaded batch is a sliced frame
+  struct FrameBufs {
+    float *x = nullptr, *y = nullptr, *z = nullptr;  // the frame, when given on the host
+    int* row = nullptr;
+    size_t cap_n = 0;
+    Chunk* chunks = nullptr;
+    size_t cap_chunks = 0;
+    int *chunk_first = nullptr, *ext = nullptr, *nslice = nullptr, *size = nullptr, *slice_first = nullptr;
+    double* c0 = nullptr;
+    float2* bounds = nullptr;
+    size_t cap_f = 0;
+    int* cnt = nullptr;
+    size_t cap_cnt = 0;
+    uint64_t* slice_off = nullptr;
+    size_t cap_s = 0;
+    float *sx = nullptr, *sy = nullptr, *sz = nullptr;  // the sliced batch
+    int *srow = nullptr, *src = nullptr;
+    uint32_t* ids = nullptr;  // output cluster ids as frame indices
+    size_t cap_ns = 0;
+    unsigned int* err = nullptr;
+  } fr;
+  const int* frame_src = nullptr;
   // space-point correction: mode and model buffers (kept across batch loads)
   tpc_corr corr = TPC_CORR_NONE;
   std::vector<void*> persist;
@@ -248,6 +277,8 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
   if (cfg->allocator && (!cfg->allocator->alloc || !cfg->allocator->free)) return TPC_ERR_INVALID_ARG;
   tpc_ctx* c = new tpc_ctx();
   c->cfg = *cfg;
+  if (cfg->tune_cache_path) c->tune_path = cfg->tune_cache_path;
+  c->cfg.tune_cache_path = nullptr;  // the caller's string is not kept
   cudaError_t e = cudaSetDevice(cfg->device);
   if (e != cudaSuccess) {
     cudaGetLastError();
@@ -310,6 +341,7 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
     for (int i = 0; i <= TPC_N_STAGES; ++i) cudaEventCreate(&c->ev[i]);
     for (int i = 0; i < 3; ++i) cudaEventCreate(&c->mask_ev[i]);
     for (int i = 0; i < 6; ++i) cudaEventCreate(&c->cmp_ev[i]);
+    for (int i = 0; i < 2; ++i) cudaEventCreate(&c->corr_ev[i]);
     c->have_events = true;
   }
   if (cfg->max_clusters || cfg->max_items) {
@@ -326,6 +358,7 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
 
 extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
   if (!c || !cl) return TPC_ERR_INVALID_ARG;
+  c->frame_src = nullptr;
   if (!cl->item_off) return fail(c, TPC_ERR_INVALID_ARG, "item_off is required");
   if (cl->n_items == 0 && cl->n != 0) return fail(c, TPC_ERR_INVALID_ARG, "clusters without items");
   if (cl->n > 0 && (!cl->x || !cl->y || !cl->z || !cl->row)) return fail(c, TPC_ERR_INVALID_ARG, "null cluster array");
@@ -426,6 +459,204 @@ extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
   return TPC_OK;
 }
 
+namespace {
+template <class T>
+bool grow_persist(tpc_ctx* c, T*& p, size_t& cap, size_t n) {
+  if (p && n <= cap) return true;
+  persist_free(c, p);
+  n = std::max<size_t>(n, 1);
+  p = static_cast<T*>(persist_alloc(c, sizeof(T) * n));
+  cap = p ? n : 0;
+  return p != nullptr;
+}
+}  // namespace
+
+extern "C" tpc_status tpc_load_frame(tpc_ctx* c, const tpc_clusters* fr, float core_cm, float overlap_cm) {
+  if (!c || !fr) return TPC_ERR_INVALID_ARG;
+  if (!fr->item_off) return fail(c, TPC_ERR_INVALID_ARG, "item_off is required");
+  if (fr->item_core) return fail(c, TPC_ERR_INVALID_ARG, "a frame has no item_core: its slices get one");
+  if (fr->n_items == 0 && fr->n != 0) return fail(c, TPC_ERR_INVALID_ARG, "clusters without items");
+  if (fr->n > 0 && (!fr->x || !fr->y || !fr->z || !fr->row)) return fail(c, TPC_ERR_INVALID_ARG, "null cluster array");
+  if (!(core_cm > 0.f) || !(overlap_cm >= 0.f) || !std::isfinite(core_cm) || !std::isfinite(overlap_cm) ||
+      std::ceil((double)overlap_cm / core_cm) > TF_WMAX - 1)
+    return fail(c, TPC_ERR_INVALID_ARG, "core_cm > 0 and 0 <= overlap_cm <= 3 core_cm");
+  if (fr->n >= (1ull << 31) / 8) return fail(c, TPC_ERR_CAPACITY, "frame too large");
+  if (fr->item_off[0] != 0 || fr->item_off[fr->n_items] != fr->n)
+    return fail(c, TPC_ERR_INVALID_ARG, "item_off must start at 0 and end at n");
+  for (uint32_t i = 0; i < fr->n_items; ++i)
+    if (fr->item_off[i + 1] < fr->item_off[i]) return fail(c, TPC_ERR_INVALID_ARG, "item_off not monotone");
+  cudaError_t e = cudaSetDevice(c->cfg.device);
+  if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  const uint32_t F = fr->n_items;
+  const size_t n = fr->n;
+  auto& B = c->fr;
+  // frame chunks (one item each, in item order) and every item's first chunk
+  std::vector<Chunk> chunks;
+  std::vector<int> chunk_first(F + 1, 0);
+  for (uint32_t i = 0; i < F; ++i) {
+    chunk_first[i] = (int)chunks.size();
+    for (uint64_t a = fr->item_off[i]; a < fr->item_off[i + 1]; a += TF_CHUNK)
+      chunks.push_back({(int)i, (int)a, (int)std::min<uint64_t>(a + TF_CHUNK, fr->item_off[i + 1])});
+  }
+  chunk_first[F] = (int)chunks.size();
+  const size_t nch = chunks.size();
+  bool ok = grow_persist(c, B.chunks, B.cap_chunks, nch) && grow_persist(c, B.cnt, B.cap_cnt, nch * TF_KMAX);
+  if (ok && (!B.ext || F > B.cap_f)) {  // every per-item array has room for cap_f items
+    for (void* p : {(void*)B.chunk_first, (void*)B.ext, (void*)B.nslice, (void*)B.size, (void*)B.slice_first,
+                    (void*)B.c0, (void*)B.bounds})
+      persist_free(c, p);
+    const size_t f = std::max<size_t>(F, 1);
+    B.chunk_first = (int*)persist_alloc(c, 4 * (f + 1));
+    B.ext = (int*)persist_alloc(c, 8 * f);
+    B.nslice = (int*)persist_alloc(c, 4 * f);
+    B.size = (int*)persist_alloc(c, 4 * f * TF_KMAX);
+    B.slice_first = (int*)persist_alloc(c, 4 * f);
+    B.c0 = (double*)persist_alloc(c, 8 * f);
+    B.bounds = (float2*)persist_alloc(c, 8 * f * TF_KMAX);
+    ok = B.chunk_first && B.ext && B.nslice && B.size && B.slice_first && B.c0 && B.bounds;
+    B.cap_f = ok ? f : 0;
+    if (!ok) B.ext = nullptr;
+  }
+  if (ok && !B.err) B.err = (unsigned int*)persist_alloc(c, 16);
+  ok = ok && B.err;
+  if (ok && !fr->on_device) {
+    size_t cap_n = B.cap_n;
+    if (!B.x || n > B.cap_n) {
+      persist_free(c, B.x);
+      persist_free(c, B.y);
+      persist_free(c, B.z);
+      persist_free(c, B.row);
+      const size_t m = std::max<size_t>(n, 1);
+      B.x = (float*)persist_alloc(c, 4 * m);
+      B.y = (float*)persist_alloc(c, 4 * m);
+      B.z = (float*)persist_alloc(c, 4 * m);
+      B.row = (int*)persist_alloc(c, 4 * m);
+      cap_n = m;
+    }
+    ok = B.x && B.y && B.z && B.row;
+    B.cap_n = ok ? cap_n : 0;
+  }
+  if (!ok) return fail(c, TPC_ERR_OOM, "device allocation failed (frame buffers)");
+  FrameArgs a{};
+  if (fr->on_device) {
+    a.x = fr->x;
+    a.y = fr->y;
+    a.z = fr->z;
+    a.row = fr->row;
+  } else {
+    a.x = B.x;
+    a.y = B.y;
+    a.z = B.z;
+    a.row = B.row;
+    if (n && ((e = cudaMemcpyAsync(B.x, fr->x, 4 * n, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+              (e = cudaMemcpyAsync(B.y, fr->y, 4 * n, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+              (e = cudaMemcpyAsync(B.z, fr->z, 4 * n, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+              (e = cudaMemcpyAsync(B.row, fr->row, 4 * n, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess))
+      return cuda_fail(c, e, "frame upload");
+  }
+  a.chunks = B.chunks;
+  a.n_chunks = (int)nch;
+  a.chunk_first = B.chunk_first;
+  a.F = (int)F;
+  a.core = core_cm;
+  a.overlap = overlap_cm;
+  a.W = 1 + (int)std::ceil((double)overlap_cm / core_cm);
+  a.ext = B.ext;
+  a.c0 = B.c0;
+  a.nslice = B.nslice;
+  a.bounds = B.bounds;
+  a.cnt = B.cnt;
+  a.size = B.size;
+  a.err = B.err;
+  if (nch && (e = cudaMemcpyAsync(B.chunks, chunks.data(), sizeof(Chunk) * nch, cudaMemcpyHostToDevice,
+                                  c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "frame chunks");
+  if ((e = cudaMemcpyAsync(B.chunk_first, chunk_first.data(), 4 * (F + 1), cudaMemcpyHostToDevice, c->stream)) !=
+          cudaSuccess ||
+      (e = cudaMemsetAsync(B.err, 0, 4, c->stream)) != cudaSuccess || (e = tpc_frame_count(a, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "frame slicing");
+  // slice counts and sizes back to the host: the sliced batch's item tables
+  std::vector<int> nslice(F), size((size_t)F * TF_KMAX);
+  std::vector<double> c0(F);
+  unsigned int err = 0;
+  if (F && ((e = cudaMemcpyAsync(nslice.data(), B.nslice, 4 * F, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(c0.data(), B.c0, 8 * F, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+            (e = cudaMemcpyAsync(size.data(), B.size, 4 * size.size(), cudaMemcpyDeviceToHost, c->stream)) !=
+                cudaSuccess))
+    return cuda_fail(c, e, "frame sizes");
+  if ((e = cudaMemcpyAsync(&err, B.err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "frame sizes");
+  if (err & TPC_DERR_BAD_INPUT) return fail(c, TPC_ERR_BAD_INPUT, "a frame cluster has a non-finite or huge z");
+  if (err & TPC_DERR_CAPACITY) return fail(c, TPC_ERR_CAPACITY, "a frame item spans more than 64 slices");
+  std::vector<int> slice_first(F);
+  std::vector<uint64_t> slice_off(1, 0);
+  std::vector<int32_t> core;
+  std::vector<uint32_t> sec, ev;
+  for (uint32_t i = 0; i < F; ++i) {
+    slice_first[i] = (int)slice_off.size() - 1;
+    for (int k = 0; k < nslice[i]; ++k) {
+      slice_off.push_back(slice_off.back() + (uint64_t)size[(size_t)i * TF_KMAX + k]);
+      const double cz = c0[i] + (double)k * core_cm;
+      core.push_back((int32_t)std::nearbyint(cz * 1024.0));
+      core.push_back((int32_t)std::nearbyint((cz + core_cm) * 1024.0));
+      sec.push_back(fr->item_sector ? fr->item_sector[i] : i);
+      ev.push_back(fr->item_event ? fr->item_event[i] : 0u);
+    }
+  }
+  const size_t S = slice_off.size() - 1, Ns = slice_off.back();
+  if (Ns >= (1ull << 31) / 3) return fail(c, TPC_ERR_CAPACITY, "sliced frame too large");
+  size_t cap_s = B.cap_s;
+  ok = grow_persist(c, B.slice_off, cap_s, S + 1);
+  B.cap_s = ok ? cap_s : 0;
+  if (ok && (!B.sx || Ns > B.cap_ns)) {
+    for (void* p : {(void*)B.sx, (void*)B.sy, (void*)B.sz, (void*)B.srow, (void*)B.src, (void*)B.ids})
+      persist_free(c, p);
+    const size_t m = std::max<size_t>(Ns, 1);
+    B.sx = (float*)persist_alloc(c, 4 * m);
+    B.sy = (float*)persist_alloc(c, 4 * m);
+    B.sz = (float*)persist_alloc(c, 4 * m);
+    B.srow = (int*)persist_alloc(c, 4 * m);
+    B.src = (int*)persist_alloc(c, 4 * m);
+    B.ids = (uint32_t*)persist_alloc(c, 4 * m);
+    ok = B.sx && B.sy && B.sz && B.srow && B.src && B.ids;
+    B.cap_ns = ok ? m : 0;
+  }
+  if (!ok) return fail(c, TPC_ERR_OOM, "device allocation failed (sliced frame)");
+  // slices in place: the frame's chunks scatter into the sliced batch
+  a.slice_first = B.slice_first;
+  a.slice_off = B.slice_off;
+  a.ox = B.sx;
+  a.oy = B.sy;
+  a.oz = B.sz;
+  a.orow = B.srow;
+  a.src = B.src;
+  if ((F && (e = cudaMemcpyAsync(B.slice_first, slice_first.data(), 4 * F, cudaMemcpyHostToDevice, c->stream)) !=
+                cudaSuccess) ||
+      (e = cudaMemcpyAsync(B.slice_off, slice_off.data(), 8 * (S + 1), cudaMemcpyHostToDevice, c->stream)) !=
+          cudaSuccess ||
+      (e = tpc_frame_scatter(a, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "frame scatter");
+  // the sliced batch is an ordinary batch on the device (borrowed from the frame buffers)
+  tpc_clusters sl{};
+  sl.x = B.sx;
+  sl.y = B.sy;
+  sl.z = B.sz;
+  sl.row = B.srow;
+  sl.n = Ns;
+  sl.item_off = slice_off.data();
+  sl.n_items = (uint32_t)S;
+  sl.item_sector = sec.data();
+  sl.item_event = ev.data();
+  sl.item_core = core.data();
+  sl.on_device = 1;
+  tpc_status st = tpc_load_clusters(c, &sl);
+  if (st != TPC_OK) return st;
+  if ((e = cudaStreamSynchronize(c->stream)) != cudaSuccess) return cuda_fail(c, e, "frame load");
+  c->frame_src = B.src;
+  return TPC_OK;
+}
+
 extern "C" tpc_status tpc_track(tpc_ctx* c) {
   if (!c) return TPC_ERR_INVALID_ARG;
   if (!c->loaded) return fail(c, TPC_ERR_STATE, "tpc_track before tpc_load_clusters");
@@ -446,15 +677,22 @@ extern "C" tpc_status tpc_track(tpc_ctx* c) {
   }
   auto launch = [&]() {
     cudaError_t ce = cudaSuccess;
+    const bool tc = c->have_events && c->corr != TPC_CORR_NONE;
+    if (tc) cudaEventRecord(c->corr_ev[0], c->stream);
     if (c->corr == TPC_CORR_GRID) ce = tpc_launch_grid_correction(c->b, c->stream);
     if (c->corr == TPC_CORR_MLP) ce = tpc_launch_mlp_correction(c->b, c->stream);
+    if (tc) cudaEventRecord(c->corr_ev[1], c->stream);
     if (ce != cudaSuccess) return ce;
-    return c->batched ? tpc_launch_batched(tb, c->lc, c->stream, c->have_events ? c->ev : nullptr)
-                      : tpc_launch_plain(tb, c->lc, c->stream, c->have_events ? c->ev : nullptr);
+    ce = c->batched ? tpc_launch_batched(tb, c->lc, c->stream, c->have_events ? c->ev : nullptr)
+                    : tpc_launch_plain(tb, c->lc, c->stream, c->have_events ? c->ev : nullptr);
+    if (ce == cudaSuccess && c->frame_src)  // output ids of a sliced frame -> frame indices
+      ce = tpc_frame_map_ids(c->b.trk_ids, c->frame_src, c->fr.ids, c->b.counts, 4 * c->lc.num_sms, c->stream);
+    return ce;
   };
   if (c->use_graph && capturable(c->stream)) {
     const bool stale = c->graph && (std::memcmp(&c->graph_b, &c->b, sizeof(Buffers)) != 0 ||
-                                    std::memcmp(&c->graph_tb, &tb, sizeof(Buffers)) != 0);
+                                    std::memcmp(&c->graph_tb, &tb, sizeof(Buffers)) != 0 ||
+                                    c->graph_src != c->frame_src);
     if (!c->graph || stale) {
       cudaGraph_t g = nullptr;
       e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
@@ -478,6 +716,7 @@ extern "C" tpc_status tpc_track(tpc_ctx* c) {
       }
       c->graph_b = c->b;
       c->graph_tb = tb;
+      c->graph_src = c->frame_src;
     }
     e = cudaGraphLaunch(c->graph, c->stream);
   } else {
@@ -485,6 +724,7 @@ extern "C" tpc_status tpc_track(tpc_ctx* c) {
   }
   if (e != cudaSuccess) return cuda_fail(c, e, "launch");
   c->last_batched = c->batched;
+  c->corr_timed = c->have_events && c->corr != TPC_CORR_NONE;
   c->tracked = true;
   return TPC_OK;
 }
@@ -520,7 +760,8 @@ extern "C" tpc_status tpc_get_tracks(tpc_ctx* c, tpc_track_t* trk, uint64_t trk_
   if ((cnt[0] && !trk) || (cnt[1] && !ids)) return fail(c, TPC_ERR_INVALID_ARG, "null output buffer");
   if (cnt[0] && (e = cudaMemcpy(trk, c->b.trk, sizeof(tpc_track_t) * cnt[0], cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(c, e, "track copy");
-  if (cnt[1] && (e = cudaMemcpy(ids, c->b.trk_ids, 4 * cnt[1], cudaMemcpyDeviceToHost)) != cudaSuccess)
+  const uint32_t* src_ids = c->frame_src ? c->fr.ids : c->b.trk_ids;
+  if (cnt[1] && (e = cudaMemcpy(ids, src_ids, 4 * cnt[1], cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(c, e, "id copy");
   return TPC_OK;
 }
@@ -530,7 +771,7 @@ extern "C" tpc_status tpc_device_tracks(tpc_ctx* c, const tpc_track_t** trk, con
   if (!c) return TPC_ERR_INVALID_ARG;
   if (!c->loaded) return fail(c, TPC_ERR_STATE, "nothing loaded");
   if (trk) *trk = (const tpc_track_t*)c->b.trk;
-  if (ids) *ids = c->b.trk_ids;
+  if (ids) *ids = c->frame_src ? c->fr.ids : c->b.trk_ids;
   if (counts) *counts = (const uint64_t*)c->b.counts;
   return TPC_OK;
 }
@@ -538,7 +779,7 @@ extern "C" tpc_status tpc_device_tracks(tpc_ctx* c, const tpc_track_t** trk, con
 static const char* kStageNames[TPC_N_REPORTED_STAGES] = {
     "quantise+row_stats", "row_setup", "group_scatter", "row_sort", "links", "clean+starts", "tracklets",
     "selection", "output", "batched_items", "batched_concat", "mask_assoc", "mask_final", "compress_symbols",
-    "compress_rans", "compress_layout"};
+    "compress_rans", "compress_layout", "correction"};
 
 extern "C" const char* tpc_stage_name(int i) { return (i >= 0 && i < TPC_N_REPORTED_STAGES) ? kStageNames[i] : ""; }
 
@@ -551,11 +792,15 @@ extern "C" tpc_status tpc_stage_times(tpc_ctx* c, float* us, int n, int* n_stage
   if (e != cudaSuccess) return cuda_fail(c, e, "stream");
   for (int i = 0; i < TPC_N_REPORTED_STAGES && i < n; ++i) {
     float ms = 0.f;
-    const bool mask = i >= TPC_N_STAGES && i < TPC_N_STAGES + 2, cmp = i >= TPC_N_STAGES + 2;
-    const bool mine = cmp ? c->cmp_timed : (mask ? c->mask_timed : (c->last_batched ? (i >= 9) : (i < 9)));
+    const bool corr = i == TPC_N_REPORTED_STAGES - 1;
+    const bool mask = i >= TPC_N_STAGES && i < TPC_N_STAGES + 2, cmp = !corr && i >= TPC_N_STAGES + 2;
+    const bool mine = corr ? c->corr_timed
+                           : cmp ? c->cmp_timed : (mask ? c->mask_timed : (c->last_batched ? (i >= 9) : (i < 9)));
     const int j = i - TPC_N_STAGES - 2;
-    const cudaEvent_t a = cmp ? c->cmp_ev[2 * j] : (mask ? c->mask_ev[i - TPC_N_STAGES] : c->ev[i]);
-    const cudaEvent_t b = cmp ? c->cmp_ev[2 * j + 1] : (mask ? c->mask_ev[i - TPC_N_STAGES + 1] : c->ev[i + 1]);
+    const cudaEvent_t a = corr ? c->corr_ev[0]
+                               : cmp ? c->cmp_ev[2 * j] : (mask ? c->mask_ev[i - TPC_N_STAGES] : c->ev[i]);
+    const cudaEvent_t b = corr ? c->corr_ev[1]
+                               : cmp ? c->cmp_ev[2 * j + 1] : (mask ? c->mask_ev[i - TPC_N_STAGES + 1] : c->ev[i + 1]);
     if (mine && cudaEventElapsedTime(&ms, a, b) != cudaSuccess) {
       cudaGetLastError();
       ms = 0.f;
@@ -763,11 +1008,87 @@ extern "C" tpc_status tpc_autotune(tpc_ctx* c, int iters, tpc_tuning* best_out, 
   return tpc_autotune_mode(c, iters, 0, best_out, best_us);
 }
 
+namespace {
+// Autotuner cache: one line per key, "key|lanes block per_sm smem link_rows
+// mode batch_lanes use_graph merge_cap|best_us".  The key names the GPU, the
+// mode searched and the batch's shape (clusters, items, rows, correction), so
+// a later process with the same workload skips the search.  File errors only
+// disable the cache.
+std::string tune_key(const tpc_ctx* c, int mode) {
+  cudaDeviceProp p{};
+  if (cudaGetDeviceProperties(&p, c->cfg.device) != cudaSuccess) {
+    cudaGetLastError();
+    return std::string();
+  }
+  std::ostringstream k;
+  std::string name(p.name);
+  for (char& ch : name)
+    if (ch == ' ' || ch == '|') ch = '_';
+  k << name << ":sm" << p.multiProcessorCount << ":mode" << mode << ":n" << c->b.N << ":items" << c->b.I << ":rows"
+    << c->cfg.n_rows << ":corr" << (int)c->corr;
+  return k.str();
+}
+
+bool tune_lookup(const std::string& path, const std::string& key, tpc_tuning* t, float* us) {
+  std::ifstream f(path);
+  std::string line;
+  while (f && std::getline(f, line)) {
+    const size_t a = line.find('|'), b = line.rfind('|');
+    if (a == std::string::npos || b == a || line.compare(0, a, key) != 0 || a != key.size()) continue;
+    std::istringstream v(line.substr(a + 1, b - a - 1));
+    tpc_tuning r{};
+    if (!(v >> r.tracklet_lanes >> r.tracklet_block >> r.tracklet_blocks_per_sm >> r.sort_smem >> r.link_rows >>
+          r.mode >> r.batch_lanes >> r.use_graph >> r.merge_sort_cap))
+      continue;
+    *t = r;
+    *us = std::strtof(line.c_str() + b + 1, nullptr);
+    return true;
+  }
+  return false;
+}
+
+void tune_store(const std::string& path, const std::string& key, const tpc_tuning& t, float us) {
+  std::vector<std::string> keep;
+  {
+    std::ifstream f(path);
+    std::string line;
+    while (f && std::getline(f, line))
+      if (line.compare(0, key.size() + 1, key + "|") != 0) keep.push_back(line);
+  }
+  char buf[256];
+  std::snprintf(buf, sizeof(buf), "|%d %d %d %d %d %d %d %d %d|%.9g", t.tracklet_lanes, t.tracklet_block,
+                t.tracklet_blocks_per_sm, t.sort_smem, t.link_rows, t.mode, t.batch_lanes, t.use_graph,
+                t.merge_sort_cap, us);
+  keep.push_back(key + buf);
+  const std::string tmp = path + ".tmp";
+  {
+    std::ofstream o(tmp, std::ios::trunc);
+    for (const std::string& l : keep) o << l << "\n";
+    if (!o) return;
+  }
+  std::rename(tmp.c_str(), path.c_str());
+}
+}  // namespace
+
 extern "C" tpc_status tpc_autotune_mode(tpc_ctx* c, int iters, int mode, tpc_tuning* best_out, float* best_us) {
   if (!c || iters < 1 || mode < 0 || mode > 2) return TPC_ERR_INVALID_ARG;
   if (!c->loaded) return fail(c, TPC_ERR_STATE, "tpc_autotune before tpc_load_clusters");
   cudaError_t e = cudaSetDevice(c->cfg.device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  const std::string key = c->tune_path.empty() ? std::string() : tune_key(c, mode);
+  {
+    tpc_tuning cached{};
+    float cached_us = 0.f;
+    if (!key.empty() && tune_lookup(c->tune_path, key, &cached, &cached_us)) {
+      tpc_status st = apply_tuning(c, cached);
+      if (st == TPC_OK) {
+        st = tpc_track(c);  // as after a search: the batch is tracked with the chosen shape
+        if (best_out) *best_out = cached;
+        if (best_us) *best_us = cached_us;
+        return st;
+      }
+    }
+  }
   // plain-mode shapes, then shared memory and row blocks, then the batched kernel
   std::vector<tpc_tuning> cand;
   for (int lanes : {1, 2, 4, 8, 16, 32})
@@ -840,6 +1161,7 @@ extern "C" tpc_status tpc_autotune_mode(tpc_ctx* c, int iters, int mode, tpc_tun
   }
   apply_tuning(c, best);
   st = tpc_track(c);
+  if (st == TPC_OK && !key.empty()) tune_store(c->tune_path, key, best, best_t);
   if (best_out) *best_out = best;
   if (best_us) *best_us = best_t;
   return st;
@@ -1221,6 +1543,8 @@ extern "C" tpc_status tpc_encode_clusters(tpc_ctx* c, const tpc_cluster_props* i
 extern "C" tpc_status tpc_cluster_masks(tpc_ctx* c, const tpc_mask_params* prm, const tpc_track_t* tracks,
                                         uint64_t n_tracks, const uint32_t* cluster_ids, uint64_t n_ids,
                                         const uint8_t* leg, int on_device, uint8_t* mask, int32_t* owner) {
+  if (c && c->frame_src)
+    return fail(c, TPC_ERR_STATE, "the data-reduction calls take a batch loaded by tpc_load_clusters, not a frame");
   if (!c || !mask) return fail(c, TPC_ERR_INVALID_ARG, "null argument");
   if (!c->tracked) return fail(c, TPC_ERR_STATE, "tpc_cluster_masks before tpc_track");
   const tpc_mask_params def{1.5f, 0.05f, 70.0f};
@@ -1346,6 +1670,8 @@ void* cmp_buffer(tpc_ctx* c, int i, size_t bytes) {
 extern "C" tpc_status tpc_compress(tpc_ctx* c, const tpc_cluster_charges* ch, const tpc_track_t* tracks,
                                    uint64_t n_tracks, const uint32_t* cluster_ids, uint64_t n_ids, const uint8_t* keep,
                                    int on_device, uint8_t* out, uint64_t cap, uint64_t* size) {
+  if (c && c->frame_src)
+    return fail(c, TPC_ERR_STATE, "the data-reduction calls take a batch loaded by tpc_load_clusters, not a frame");
   if (!c || !ch || !size) return fail(c, TPC_ERR_INVALID_ARG, "null argument");
   if (!c->tracked) return fail(c, TPC_ERR_STATE, "tpc_compress before tpc_track");
   *size = 0;
@@ -1544,6 +1870,8 @@ extern "C" tpc_status tpc_compress(tpc_ctx* c, const tpc_cluster_charges* ch, co
 extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, uint64_t n_tracks,
                                        const uint32_t* cluster_ids, uint64_t n_ids, int on_device, int32_t* link,
                                        int32_t* group, double* fit, int32_t* leg_partner, uint8_t* leg) {
+  if (c && c->frame_src)
+    return fail(c, TPC_ERR_STATE, "the data-reduction calls take a batch loaded by tpc_load_clusters, not a frame");
   if (!c) return TPC_ERR_INVALID_ARG;
   if (!c->tracked) return fail(c, TPC_ERR_STATE, "tpc_merge_tracks before tpc_track");
   const int I = (int)c->h_item_sector.size();
@@ -1720,10 +2048,12 @@ extern "C" void tpc_destroy(tpc_ctx* c) {
   cudaSetDevice(c->cfg.device);
   free_all(c);
   while (!c->persist.empty()) persist_free(c, c->persist.back());
-  if (c->have_events)
+  if (c->have_events) {
     for (int i = 0; i <= TPC_N_STAGES; ++i) cudaEventDestroy(c->ev[i]);
     for (int i = 0; i < 3; ++i) cudaEventDestroy(c->mask_ev[i]);
     for (int i = 0; i < 6; ++i) cudaEventDestroy(c->cmp_ev[i]);
+    for (int i = 0; i < 2; ++i) cudaEventDestroy(c->corr_ev[i]);
+  }
   if (c->own_stream) {
     cudaStreamSynchronize(c->stream);
     cudaStreamDestroy(c->stream);

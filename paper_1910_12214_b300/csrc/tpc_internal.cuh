@@ -13,6 +13,7 @@
 #define TPC_DERR_ROW_CAP 2u
 #define TPC_DERR_TIMEOUT 4u
 #define TPC_DERR_BAD_TRACK 8u  // a track given to tpc_cluster_masks refers to an item or cluster out of range
+#define TPC_DERR_CAPACITY 16u  // a time-frame item needs more than TF_KMAX slices
 
 // One (item, pad row) of the binning grid: 32 bytes, one load.
 struct RowInfo {
@@ -134,7 +135,8 @@ struct Buffers {
 };
 
 #define TPC_N_STAGES 11  // 9 plain-mode steps, then the batched kernel and its compaction
-#define TPC_N_REPORTED_STAGES 16  // ... then the two kernels of tpc_cluster_masks, the 3 phases of tpc_compress
+#define TPC_N_REPORTED_STAGES 17  // ... then the two kernels of tpc_cluster_masks, the 3 phases of
+                                  // tpc_compress, and the space-point correction of tpc_track
 
 struct LaunchCfg {
   int n_rows;
@@ -156,6 +158,38 @@ cudaError_t tpc_batched_occupancy(int per_sm[3]);
 cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t tpc_launch_batched(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t tpc_launch_grid_correction(const Buffers& b, cudaStream_t s);
+
+// Continuous read-out time frames cut into overlapping slices on the device
+// (tpc_frame.cu; the host side is tpc_load_frame in tpc_capi.cu).
+constexpr int TF_KMAX = 64;     // slices of one frame item
+constexpr int TF_WMAX = 4;      // overlap <= (TF_WMAX - 1) cores: a cluster is in at most 2 TF_WMAX - 1 slices
+constexpr int TF_CHUNK = 4096;  // frame clusters per block
+struct FrameArgs {
+  const float *x, *y, *z;     // the frame (device)
+  const int* row;
+  const Chunk* chunks;        // frame chunks of <= TF_CHUNK clusters, one item each, in item order
+  int n_chunks;
+  const int* chunk_first;     // [F + 1] first chunk of every item
+  int F;                      // frame items
+  float core, overlap;        // cm
+  int W;                      // candidate slices on each side of the estimate: 1 + ceil(overlap / core)
+  int* ext;                   // [F][2] order-preserving integers of min z, max z
+  double* c0;                 // [F] start of the first core
+  int* nslice;                // [F] slices of the item
+  float2* bounds;             // [F][TF_KMAX] extended range [lo, hi) of every slice, FP64-exact as floats
+  int* cnt;                   // [n_chunks][TF_KMAX] memberships, then the chunk's base inside each slice
+  int* size;                  // [F][TF_KMAX] clusters of every slice
+  const int* slice_first;     // [F] index of the item's first slice in the sliced batch
+  const uint64_t* slice_off;  // [S + 1] first cluster of every slice in the sliced batch
+  float *ox, *oy, *oz;        // the sliced batch (device)
+  int* orow;
+  int* src;                   // frame index of every sliced cluster
+  unsigned int* err;
+};
+cudaError_t tpc_frame_count(const FrameArgs& a, cudaStream_t s);
+cudaError_t tpc_frame_scatter(const FrameArgs& a, cudaStream_t s);
+cudaError_t tpc_frame_map_ids(const uint32_t* in, const int* src, uint32_t* out, const unsigned long long* counts,
+                              int blocks, cudaStream_t s);
 cudaError_t tpc_launch_mlp_correction(const Buffers& b, cudaStream_t s);
 
 // MLP surrogate (tpc_mlp.cu)

@@ -1283,7 +1283,8 @@ __device__ __forceinline__ unsigned long long score_key(F2 sc) {
   return ((unsigned long long)__float_as_uint(sc.hi) << 32) | ((lo & 0x80000000u) ? ~lo : (lo | 0x80000000u));
 }
 
-// The compatibility tests of R-28 and the score of a compatible pair, in
+// The merger's compatibility tests (curvature chi2, the reference point on the
+// better-measured circle, tan(lambda), z continuity) and the score of a compatible pair, in
 // float-float on the per-track records (geof2): a few 2^-46 relative, so every
 // decision equals the exact one except within about 1e-13 of a limit.
 struct TrkF2 {

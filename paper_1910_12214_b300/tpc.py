@@ -38,7 +38,7 @@ class tpc_config(C.Structure):
                 ("row_x_min", C.c_float), ("row_x_max", C.c_float), ("sector_half_angle_deg", C.c_float),
                 ("sigma_y", C.c_float), ("sigma_z", C.c_float), ("mode", C.c_int), ("correction", C.c_int),
                 ("max_clusters", C.c_uint64), ("max_items", C.c_uint32), ("allocator", C.POINTER(tpc_allocator)),
-                ("profile", C.c_int)]
+                ("profile", C.c_int), ("tune_cache_path", C.c_char_p)]
 
 
 class tpc_clusters(C.Structure):
@@ -109,6 +109,7 @@ _sig = {
     "tpc_surrogate_save": ([_P, C.c_char_p], C.c_int),
     "tpc_surrogate_load": ([_P, C.c_char_p], C.c_int),
     "tpc_bin_sector_noalloc": ([_P, _P, _P, C.c_uint32, C.c_int, _P, _P, _P, _P], C.c_int),
+    "tpc_load_frame": ([_P, C.POINTER(tpc_clusters), C.c_float, C.c_float], C.c_int),
     "tpc_encode_clusters": ([_P, C.POINTER(tpc_cluster_props), C.POINTER(tpc_cluster_codes), C.c_int,
                              C.POINTER(C.c_uint64)], C.c_int),
     "tpc_cluster_masks": ([_P, C.POINTER(tpc_mask_params), _P, C.c_uint64, _P, C.c_uint64, _P, C.c_int, _P, _P],
@@ -165,7 +166,8 @@ class Tracker:
     def __init__(self, device: int = 0, stream=None, n_rows: int = 152, row_x_min: float = 85.0,
                  row_x_max: float = 246.0, half_angle_deg: float = 10.0, bz_tesla: float = 0.5,
                  sigma_y: float = 0.1, sigma_z: float = 0.1, mode: str = "plain", correction: str = "none",
-                 max_clusters: int = 0, max_items: int = 0, torch_allocator: bool = True, profile: bool = False):
+                 max_clusters: int = 0, max_items: int = 0, torch_allocator: bool = True, profile: bool = False,
+                 tune_cache_path: str = None):
         self._keep = []
         alloc_ptr = None
         if torch_allocator:
@@ -180,7 +182,8 @@ class Tracker:
         if not sptr:
             sptr = 1  # cudaStreamLegacy: torch's default stream (a NULL handle would mean a library stream)
         self.cfg = tpc_config(device, sptr, bz_tesla, n_rows, row_x_min, row_x_max, half_angle_deg, sigma_y, sigma_z,
-                              MODE[mode], CORR[correction], max_clusters, max_items, alloc_ptr, int(profile))
+                              MODE[mode], CORR[correction], max_clusters, max_items, alloc_ptr, int(profile),
+                              None if tune_cache_path is None else os.fsencode(tune_cache_path))
         self.n_rows = n_rows
         h = _P()
         st = _lib.tpc_init(C.byref(self.cfg), C.byref(h))
@@ -196,6 +199,15 @@ class Tracker:
     def load(self, cl, on_device: bool = None):
         """cl: object with x, y, z, row (numpy or torch), item_off, optional item_sector,
         item_event, item_core (host numpy)."""
+        return self._load(cl, on_device, None)
+
+    def load_frame(self, fr, core_cm: float = 1000.0, overlap_cm: float = 300.0, on_device: bool = None):
+        """A continuous read-out frame (items = sectors over their whole z axis),
+        cut into overlapping slices on the device (tpc_load_frame); the tracks'
+        cluster ids are frame indices."""
+        return self._load(fr, on_device, (core_cm, overlap_cm))
+
+    def _load(self, cl, on_device, frame):
         if on_device is None:
             on_device = hasattr(cl.x, "is_cuda") and cl.x.is_cuda
         keep = []
@@ -217,10 +229,13 @@ class Tracker:
         off = host(cl.item_off, np.uint64)
         sec = host(getattr(cl, "item_sector", None), np.uint32)
         ev = host(getattr(cl, "item_event", None), np.uint32)
-        core = host(getattr(cl, "item_core", None), np.int32)
+        core = None if frame else host(getattr(cl, "item_core", None), np.int32)
         c = tpc_clusters(_ptr(x), _ptr(y), _ptr(z), _ptr(row), n, _ptr(off), int(off.shape[0] - 1), _ptr(sec),
                          _ptr(ev), _ptr(core), int(bool(on_device)))
-        self._check(_lib.tpc_load_clusters(self._h, C.byref(c)))
+        if frame:
+            self._check(_lib.tpc_load_frame(self._h, C.byref(c), float(frame[0]), float(frame[1])))
+        else:
+            self._check(_lib.tpc_load_clusters(self._h, C.byref(c)))
         self._loaded = (cl, keep) if on_device else None
         self.n_loaded = n
         return self
