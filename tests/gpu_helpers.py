@@ -14,7 +14,7 @@ def run_gpu(cl, **kw):
     with tpc.Tracker(**kw) as t:
         t.load(cl).track()
         trk, ids = t.get_tracks()
-        dumps = {s: t.debug_dump(s) for s in range(10)}
+        dumps = {s: t.debug_dump(s) for s in range(11)}
     return trk, ids, dumps
 
 
@@ -68,4 +68,45 @@ def compare_tracks(cl, trk, ids, ref, min_match=0.995, min_param=0.995):
                 worst_rel_identical=worst_same, bad_by_param=bad_params.tolist(),
                 ok=frac >= min_match and pfrac >= min_param)
     print("PARITY", res)
+    return res
+
+
+def compare_tracklets_and_selection(trk, ids, dumps, ref, min_identical=0.995):
+    """Element-wise comparison of the tracklets (S6) and of the selection (S7/S8).
+    The start hits are bit-exact, so tracklet t is built from the same start on
+    both sides: its hit count and hit list (outermost first) must be equal on
+    >= min_identical of the tracklets (the hit choice is an FP32 vs FP64 chi2
+    decision).  Selection is integer work: on every item whose tracklets are all
+    identical, the output tracks (tracklet, owned cluster ids) must equal the
+    oracle's bit for bit.  Returns the fractions compared."""
+    n_g, n_o = dumps[8].astype(np.int64), ref["tl_n"].astype(np.int64)
+    assert n_g.shape == n_o.shape
+    off_g = np.concatenate([[0], np.cumsum(n_g)])
+    off_o = np.concatenate([[0], np.cumsum(n_o)])
+    hits_g, hits_o = dumps[9], ref["tl_hits"]
+    meta = ref["tl_meta"].reshape(-1, 2)
+    same = np.array([n_g[t] == n_o[t] and np.array_equal(hits_g[off_g[t]:off_g[t + 1]], hits_o[off_o[t]:off_o[t + 1]])
+                     for t in range(n_g.shape[0])], bool)
+    frac = float(same.mean()) if same.size else 1.0
+    assert frac >= min_identical, frac
+    items_all = np.unique(meta[:, 0])
+    bad_items = set(meta[~same, 0].tolist())
+    clean = [int(i) for i in items_all if int(i) not in bad_items]
+    # GPU tracks per item: (item-local tracklet id, sorted owned cluster ids)
+    tl_of_track = dumps[10]
+    got, want = {}, {}
+    for k in range(trk.shape[0]):
+        it, loc = (int(v) for v in meta[tl_of_track[k]])
+        assert it == int(trk["item"][k])
+        f, n = int(trk["first_cluster"][k]), int(trk["n_clusters"][k])
+        got.setdefault(it, []).append((loc, tuple(sorted(ids[f:f + n].tolist()))))
+    ti, tids = ref["trk_i"].reshape(-1, 4), ref["trk_ids"]
+    for it, f, n, loc in ti:
+        want.setdefault(int(it), []).append((int(loc), tuple(sorted(tids[f:f + n].tolist()))))
+    for it in clean:
+        assert sorted(got.get(it, [])) == sorted(want.get(it, [])), it
+    n_tracks_clean = sum(len(want.get(it, [])) for it in clean)
+    res = dict(tracklets=int(n_g.shape[0]), identical=frac, items=int(items_all.shape[0]), items_all_identical=len(clean),
+               tracks_compared_bitwise=n_tracks_clean, tracks=int(ti.shape[0]))
+    print("TRACKLETS", res)
     return res
