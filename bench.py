@@ -41,10 +41,11 @@ sys.path.insert(0, ROOT)
 ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12 + 12, "row_sort": 12 + 16 + 8,
               "links": 16 + 8, "clean+starts": 8 + 8 + 4, "tracklets": 28, "selection": 20, "output": 8,
               "batched_items": 150, "batched_concat": 4}
-# DRAM bytes (read + write) of the dominant step per tracking step, from the ncu
-# capture summarised in profiles/k_tracklets_config2.md: k_tracklets_up 21.53 MB +
-# k_tracklets_down 18.60 MB on the full-TPC workload; None = not captured.
-TRAFFIC = {("c2", "tracklets"): 40.13e6}
+# DRAM bytes (read + write) of the dominant step per tracking step, as one ncu
+# capture of the current kernels measured them (dram__bytes_read.sum +
+# dram__bytes_write.sum); they cannot be measured inside this run.  None: no
+# capture of the kernels as they are now.
+TRAFFIC = {}
 KERNELS_PER_STEP = {"plain": 19, "batched": 3}
 
 METRIC = "TPC clusters/s tracked (sector tracker, full TPC event)"
@@ -73,10 +74,8 @@ def _gen_batched():
 def _gen_frame():
     from paper_1910_12214_b300 import synth
     fr = synth.make_timeframe(seed=1)
-    sl = synth.slice_frame(fr)
-    sl.src_index = None
-    sl.truth = None
-    return sl, fr.n
+    fr.truth = None
+    return fr
 
 
 def _gen_loopers():
@@ -188,21 +187,97 @@ def measured_peak_hbm():
         return 6400.0, "fallback"
 
 
-def cpu_baseline(name: str, budget_s: float = 12.0):
+def _parity(cl, trk, ids, ref):
+    """Track parity of the GPU's tracks with the oracle's on the same clusters:
+    >= 99.5% of oracle tracks matched with >= 90% shared clusters, and >= 99.5%
+    of the matched ones with parameters within 1e-3 relative."""
+    import contextlib
+    sys.path.insert(0, os.path.join(ROOT, "tests"))
+    from gpu_helpers import compare_tracks
+    with contextlib.redirect_stdout(sys.stderr):  # one JSON line on stdout
+        r = compare_tracks(cl, trk, ids, ref)
+    return {k: (round(v, 6) if isinstance(v, float) else v) for k, v in r.items() if k != "bad_by_param"}
+
+
+def cpu_baseline(name: str, budget_s: float = 12.0, gpu=None):
     """The FP64 oracle as it stands, single-threaded on the host, over whole
-    events of the same workload until about budget_s of CPU work."""
+    events of the same workload until about budget_s of CPU work.  With the
+    GPU's tracks of the same event (gpu = (tracks, ids)), the oracle's first run
+    also gives the parity check of this run."""
     import oracle
     cl = make_workload(name, 0)
     n, t = 0, 0.0
     runs = 0
+    parity = None
     while t < budget_s and runs < 50:
         t0 = time.perf_counter()
-        oracle.run(cl, what=["trk_i"])
+        ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids"] if runs == 0 else ["trk_i"])
         t += time.perf_counter() - t0
+        if runs == 0 and gpu is not None:
+            parity = _parity(cl, gpu[0], gpu[1], ref)
         n += cl.n
         runs += 1
-    return {"value": n / t, "unit": "clusters/s", "cores": 1, "kind": "oracle",
-            "sample": f"{runs} full events of workload {name} ({cl.n} clusters each), single-threaded FP64"}
+    out = {"value": n / t, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+           "sample": f"{runs} full events of workload {name} ({cl.n} clusters each), single-threaded FP64"}
+    if parity is not None:
+        out["parity"] = parity
+    return out
+
+
+def sample_items(cl, k, seed):
+    """k items of a batch for the oracle: the 4 largest and k - 4 at random."""
+    from paper_1910_12214_b300 import shard
+    costs = shard.item_costs(cl)
+    k = min(k, cl.n_items)
+    largest = np.argsort(-costs, kind="stable")[:min(4, k)]
+    rng = np.random.default_rng(seed)
+    rest = rng.choice(np.setdiff1d(np.arange(cl.n_items), largest), size=k - largest.shape[0], replace=False)
+    return np.sort(np.concatenate([largest, rest]))
+
+
+def tracks_of_items(trk, ids, items, index, key="item"):
+    """GPU tracks of the given items, renumbered for the sub-batch that
+    shard.take_items(cl, items) makes (item numbers and cluster ids).  key:
+    the track field that names the item ("sector" for the tracks of a sliced
+    frame, whose items are the frame's sectors)."""
+    pos_of_item = {int(it): j for j, it in enumerate(items)}
+    inv = np.full(max(int(ids.max()) + 1 if ids.size else 1, int(np.max(index)) + 1 if len(index) else 1), -1,
+                  np.int64)
+    inv[np.asarray(index, np.int64)] = np.arange(len(index))
+    keep = np.array([i for i in range(len(trk)) if int(trk[key][i]) in pos_of_item], np.int64)
+    sub = trk[keep].copy()
+    out_ids, base = [], 0
+    for j, i in enumerate(keep):
+        f, n = int(trk["first_cluster"][i]), int(trk["n_clusters"][i])
+        out_ids.append(inv[ids[f:f + n].astype(np.int64)])
+        sub["item"][j] = pos_of_item[int(trk[key][i])]
+        sub["first_cluster"][j] = base
+        base += n
+    return sub, (np.concatenate(out_ids) if out_ids else np.zeros(0, np.int64)).astype(np.uint32)
+
+
+def form_baseline(cl, trk, ids, k, seed, correct=None, key="item"):
+    """CPU-baseline leg of a form: the oracle on a seeded sample of k items
+    (timed, single-threaded FP64) and the parity of the GPU's tracks of those
+    items with the oracle's.  correct = (grid, bounds): the oracle corrects the
+    sampled clusters with its own trilinear grid first (grid-corrected form).
+    key = "sector": cl is a frame tracked through tpc_load_frame, sampled by
+    whole (unsliced) sectors."""
+    import oracle
+    from paper_1910_12214_b300 import shard
+    items = sample_items(cl, k, seed)
+    sub, index = shard.take_items(cl, items)
+    t0 = time.perf_counter()
+    if correct is not None:
+        oy, oz = oracle.correct_clusters(sub, *correct)
+        sub.y, sub.z = oy.astype(np.float32), oz.astype(np.float32)
+    ref = oracle.run(sub, what=["trk_f", "trk_i", "trk_ids"])
+    dt = time.perf_counter() - t0
+    g_trk, g_ids = tracks_of_items(trk, ids, items, index, key=key)
+    return ({"value": sub.n / dt, "unit": "clusters/s", "cores": 1, "kind": "oracle",
+             "sample": f"{len(items)} items of the form (4 largest, the rest seeded at random; {sub.n} clusters)"
+                       + (", corrected by the oracle's grid" if correct is not None else "")},
+            _parity(sub, g_trk, g_ids, ref))
 
 
 def _oracle_share(args):
@@ -468,14 +543,24 @@ def main():
             "gpu_launches": KERNELS_PER_STEP["batched" if tuning["mode"] == 2 else "plain"] * args.steps,
             "stage_us": {k: round(v, 2) for k, v in stages.items()},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": TRAFFIC.get((args.workload, dom)), "peak_kind": peak_kind,
+                         "frac": achieved / peak, "traffic": TRAFFIC.get((args.workload, dom)),
+                         "traffic_source": "ncu capture of the same kernels (not measurable in this run)"
+                         if TRAFFIC.get((args.workload, dom)) else "null: no ncu capture of the current kernels",
+                         "peak_kind": peak_kind,
                          "algo_bytes_per_cluster": ALGO_BYTES.get(dom)},
             "clocks": clk, "wall_s_timed_region": wall,
             "forms": form_out,
         }
         if not args.no_cpu_baseline:
-            line["cpu_baseline"] = cpu_baseline(args.workload)
+            cb = cpu_baseline(args.workload, gpu=(trk, ids))
+            line["parity"] = cb.pop("parity")
+            line["cpu_baseline"] = cb
             line["cpu_baseline_all_cores"] = cpu_baseline_all_cores(args.workload)
+            if not line["parity"]["ok"]:  # a number is reported only with its parity check passed
+                line["invalid"] = "parity check against the oracle failed on this run"
+                line["value"] = None
+        else:
+            line["parity"] = "not checked (--no-cpu-baseline)"
         print(json.dumps(line), flush=True)
     if dist:
         dist.destroy_process_group()
@@ -485,11 +570,12 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
     """clusters/s of the other forms (device time of tpc_track, L2 flushed)."""
     res = {}
 
-    def bench_batch(cl, label, n_clusters, modes=("plain", "batched"), setup=None, steps=5):
+    def bench_batch(cl, label, n_clusters, modes=("plain", "batched"), setup=None, steps=5, sample=40, seed=11):
         with torch.cuda.stream(stream):
             d = to_device(cl, dev)
         stream.synchronize()
         out = {}
+        first = None
         with tpc.Tracker(stream=stream, profile=True) as t:
             if setup:
                 setup(t)
@@ -500,20 +586,26 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
                 for _ in range(2):
                     t.track()
                 ms = float(np.median(time_steps(t, stream, steps, flush)))
+                trk, ids = t.get_tracks()
                 out[mode] = {"clusters_per_s": n_clusters / (ms * 1e-3), "ms": ms, "tracks": t.counts()[0],
                              "tuning": tun}
+                if first is None:
+                    first = (trk, ids)
+                else:  # every mode must give the first mode's tracks byte for byte
+                    out[mode]["identical_to_" + modes[0]] = bool(trk.tobytes() == first[0].tobytes() and
+                                                                 np.array_equal(ids, first[1]))
         del d
         torch.cuda.empty_cache()
+        cb, par = form_baseline(cl, first[0], first[1], sample, seed)
+        out["parity"] = par
+        out["cpu_baseline"] = cb
         return out
 
     if "c3" in gen:
         c3 = gen["c3"]
         res["batched_64_events"] = {"clusters": c3.n, "items": c3.n_items, **bench_batch(c3, "c3", c3.n)}
     if "c4" in gen:
-        sl, n_phys = gen["c4"]
-        res["timeframe_50khz_128_collisions"] = {"clusters": n_phys, "sliced_clusters": sl.n, "items": sl.n_items,
-                                                 "note": "clusters/s counts physical clusters",
-                                                 **bench_batch(sl, "c4", n_phys)}
+        res["timeframe_50khz_128_collisions"] = bench_frame(gen["c4"], dev, stream, flush, tpc, torch)
     if "c5" in gen:
         c5, grid, bounds = gen["c5"]
         info = {}
@@ -531,6 +623,7 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
         with tpc.Tracker(stream=stream, profile=True) as t:
             setup(t)
             t.load(d, on_device=True)
+            grid_tracks = None
             for corr in ("mlp", "grid", "none"):
                 t.set_correction(corr)
                 t.autotune(iters=2, mode=1)
@@ -538,10 +631,18 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
                 for _ in range(2):
                     t.track()
                 ms = float(np.median(time_steps(t, stream, 5, flush)))
+                if corr == "grid":
+                    grid_tracks = t.get_tracks()
                 t.set_tuning(use_graph=1)
                 t.track()
                 st = t.stage_times()
-                out[corr] = {"clusters_per_s": c5.n / (ms * 1e-3), "ms": ms, "tracks": t.counts()[0]}
+                out[corr] = {"clusters_per_s": c5.n / (ms * 1e-3), "ms": ms, "tracks": t.counts()[0],
+                             "correction_us": round(st.get("correction", 0.0), 2)}
+        cb, par = form_baseline(c5, grid_tracks[0], grid_tracks[1], 40, 13, correct=(grid, bounds))
+        out["grid"]["parity"] = par
+        out["grid"]["cpu_baseline"] = cb
+        out["mlp"]["parity"] = ("by the GPU tests: the network here is trained on the GPU, and the oracle takes "
+                                "no input from the CUDA path")
         res["distorted_64_events"] = {"clusters": c5.n, "surrogate": info, **out}
     if "c6" in gen:
         res["codec_64_events"] = bench_codec(gen["c6"], dev, stream, flush, tpc, torch)
@@ -554,6 +655,55 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
     if "c10" in gen:
         res["removal_chain_loopers"] = bench_removal_chain(*gen["c10"], dev, stream, tpc, torch)
     return res
+
+
+def bench_frame(fr, dev, stream, flush, tpc, torch, steps=5):
+    """The continuous read-out frame resident on the device: every step cuts it
+    into slices on the device (tpc_load_frame: 1000 cm cores, 300 cm overlaps;
+    the call waits for the slice sizes) and tracks them (tpc_track); the time
+    runs from before the slicing to the end of the tracking."""
+    with torch.cuda.stream(stream):
+        d = to_device(fr, dev)
+    d.item_core = None
+    stream.synchronize()
+    out = {"clusters": fr.n, "items": fr.n_items,
+           "note": "clusters/s counts the frame's clusters; slicing on the device is inside the timed step"}
+    first = None
+    with tpc.Tracker(stream=stream, profile=True) as t:
+        t.load_frame(d, 1000.0, 300.0, on_device=True)
+        t.track()
+        out["slices"] = int(t.debug_dump(1).shape[0] // (7 * t.n_rows))
+        for mode in ("plain", "batched"):
+            tun, _ = t.autotune(iters=2, mode=1 if mode == "plain" else 2)
+            t.set_tuning(use_graph=2)
+            ms = []
+            for k in range(steps + 2):
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                t.load_frame(d, 1000.0, 300.0, on_device=True)
+                t.track()
+                e1.record(stream)
+                with torch.cuda.stream(stream):
+                    flush.zero_()
+                torch.cuda.synchronize()
+                if k >= 2:
+                    ms.append(e0.elapsed_time(e1))
+            m = float(np.median(ms))
+            trk, ids = t.get_tracks()
+            out[mode] = {"clusters_per_s": fr.n / (m * 1e-3), "ms": m, "tracks": int(trk.shape[0]), "tuning": tun}
+            if first is None:
+                first = (trk, ids)
+            else:
+                out[mode]["identical_to_plain"] = bool(trk.tobytes() == first[0].tobytes() and
+                                                       np.array_equal(ids, first[1]))
+    del d
+    torch.cuda.empty_cache()
+    cb, par = form_baseline(fr, first[0], first[1], 3, 12, key="sector")
+    cb["sample"] += " (whole, unsliced sectors of the frame)"
+    out["parity"] = par
+    out["cpu_baseline"] = cb
+    return out
 
 
 def bench_removal_chain(cl, props, dev, stream, tpc, torch):
