@@ -301,3 +301,139 @@ extern "C" int64_t orc_merge(int n_rows, double x_min, double x_max, double bz, 
   }
   return 0;
 }
+
+// Looper legs joined into one track (Sec. 4: the tracker finds the legs of a
+// looping track separately and merges them into one track).  Reading:
+//  - components: the groups of the merger joined through every mutual leg
+//    pair (union of the two legs' groups), labelled by their smallest track
+//    index; tracks of other groups keep their group label;
+//  - refit of every component that contains a pair: the clusters of all its
+//    tracks in the global frame, the algebraic circle as for the groups, then
+//    z = z0 + tan(lambda) s by least squares, s = R dtheta the arc along the
+//    circle from the innermost cluster of the primary legs (the first leg from
+//    the vertex, leg = 0; ties: the first cluster in track-index order), dtheta
+//    the turning angle in the particle's sense of rotation (clockwise for
+//    q/pT > 0 of the primary leg with the smallest index: its centre lies to
+//    the right of its direction) taken in [-0.1, 2 pi - 0.1).  The chord from
+//    the innermost cluster cannot be used: the returning leg passes the same
+//    radii again.
+//  joined: [n] component label; jfit: [n][7] at each joined component's label:
+//  centre x, y, radius, tan(lambda), z0 (at the reference cluster), clusters,
+//  tracks; zero elsewhere.  Returns the number of joined components, -1 on bad
+//  input.
+extern "C" int64_t orc_join_loopers(int n_rows, double x_min, double x_max, double bz, int64_t n, const float* y,
+                                    const float* z, const int32_t* row, int64_t n_items, const uint32_t* item_sector,
+                                    int64_t n_trk, const float* trk_f, const int64_t* trk_i, const uint32_t* ids,
+                                    const int32_t* group, const int32_t* partner, const uint8_t* leg, int32_t* joined,
+                                    double* jfit) {
+  (void)bz;
+  const double wedge = 2.0 * M_PI / 18.0;
+  std::vector<double> xr(n_rows);
+  for (int r = 0; r < n_rows; ++r)
+    xr[r] = std::nearbyint((x_min + r * ((x_max - x_min) / (n_rows - 1))) * 1024.0) / 1024.0;
+  // union of groups through the pairs: lab[g] of every group root g ends as the
+  // smallest root of its component (= its smallest track index)
+  std::vector<int64_t> lab(n_trk);
+  for (int64_t t = 0; t < n_trk; ++t) lab[t] = group[t];
+  std::vector<char> paired(n_trk, 0);
+  for (bool changed = true; changed;) {
+    changed = false;
+    for (int64_t t = 0; t < n_trk; ++t) {
+      const int64_t p = partner[t];
+      if (p < 0 || p >= n_trk || partner[p] != t) continue;
+      paired[t] = 1;
+      const int64_t m = std::min(lab[group[t]], lab[group[p]]);
+      if (lab[group[t]] != m) lab[group[t]] = m, changed = true;
+      if (lab[group[p]] != m) lab[group[p]] = m, changed = true;
+    }
+  }
+  for (int64_t t = 0; t < n_trk; ++t) joined[t] = (int32_t)lab[group[t]];
+  for (int64_t t = 0; t < 7 * n_trk; ++t) jfit[t] = 0.0;
+  std::vector<std::vector<int64_t>> members(n_trk);
+  std::vector<char> has_pair(n_trk, 0);
+  for (int64_t t = 0; t < n_trk; ++t) {
+    members[joined[t]].push_back(t);
+    if (paired[t]) has_pair[joined[t]] = 1;
+  }
+  int64_t n_joined = 0;
+  for (int64_t root = 0; root < n_trk; ++root) {
+    if (!has_pair[root]) continue;
+    // the primary legs' groups and the sense of rotation
+    std::vector<char> prim_group(n_trk, 0);
+    int64_t first_prim = -1;
+    for (int64_t t : members[root])
+      if (paired[t] && leg[t] == 0) {
+        prim_group[group[t]] = 1;
+        if (first_prim < 0) first_prim = t;
+      }
+    if (first_prim < 0) continue;
+    std::vector<double> X, Y, Z;
+    std::vector<char> P;
+    for (int64_t t : members[root]) {
+      if (trk_i[3 * t] < 0 || trk_i[3 * t] >= n_items) return -1;
+      const int s = (int)item_sector[trk_i[3 * t]];
+      const double a = (s % 18) * wedge, ca = std::cos(a), sa = std::sin(a);
+      for (int64_t j = 0; j < trk_i[3 * t + 2]; ++j) {
+        const uint32_t c = ids[trk_i[3 * t + 1] + j];
+        if (c >= (uint64_t)n || row[c] < 0 || row[c] >= n_rows) return -1;
+        const double lx = xr[row[c]], ly = y[c];
+        X.push_back(lx * ca - ly * sa);
+        Y.push_back(lx * sa + ly * ca);
+        Z.push_back(z[c]);
+        P.push_back(prim_group[group[t]]);
+      }
+    }
+    const size_t m = X.size();
+    if (m < 3) continue;
+    double mx = 0, my = 0;
+    for (size_t i = 0; i < m; ++i) {
+      mx += X[i];
+      my += Y[i];
+    }
+    mx /= m;
+    my /= m;
+    double suu = 0, suv = 0, svv = 0, su3 = 0, sv3 = 0, sw = 0;
+    for (size_t i = 0; i < m; ++i) {
+      const double u = X[i] - mx, v = Y[i] - my, w = u * u + v * v;
+      suu += u * u;
+      suv += u * v;
+      svv += v * v;
+      su3 += u * w;
+      sv3 += v * w;
+      sw += w;
+    }
+    const double det = suu * svv - suv * suv;
+    if (!(std::fabs(det) > 0)) continue;
+    const double D = (-su3 * svv + sv3 * suv) / det, E = (-sv3 * suu + su3 * suv) / det, F = -sw / m;
+    const double xc = mx - 0.5 * D, yc = my - 0.5 * E;
+    const double R = std::sqrt(0.25 * (D * D + E * E) - F);
+    size_t ref = m;
+    for (size_t i = 0; i < m; ++i)
+      if (P[i] && (ref == m || std::hypot(X[i], Y[i]) < std::hypot(X[ref], Y[ref]))) ref = i;
+    const bool cw = trk_f[7 * first_prim + 5] > 0.0f;
+    const double th0 = std::atan2(Y[ref] - yc, X[ref] - xc);
+    double ss = 0, sz = 0, sss = 0, ssz = 0;
+    for (size_t i = 0; i < m; ++i) {
+      double d = cw ? th0 - std::atan2(Y[i] - yc, X[i] - xc) : std::atan2(Y[i] - yc, X[i] - xc) - th0;
+      d -= 2.0 * M_PI * std::floor((d + 0.1) / (2.0 * M_PI));
+      const double s = R * d;
+      ss += s;
+      sz += Z[i];
+      sss += s * s;
+      ssz += s * Z[i];
+    }
+    const double den = m * sss - ss * ss;
+    const double tgl = den > 0 ? (m * ssz - ss * sz) / den : 0.0;
+    const double z0 = (sz - tgl * ss) / m;
+    double* o = jfit + 7 * root;
+    o[0] = xc;
+    o[1] = yc;
+    o[2] = R;
+    o[3] = tgl;
+    o[4] = z0;
+    o[5] = (double)m;
+    o[6] = (double)members[root].size();
+    ++n_joined;
+  }
+  return n_joined;
+}

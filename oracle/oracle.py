@@ -108,6 +108,9 @@ def _load():
         lib.orc_merge.restype = C.c_int64
         lib.orc_merge.argtypes = ([C.c_int, C.c_double, C.c_double, C.c_double, C.c_int64] + [C.c_void_p] * 3 +
                                   [C.c_int64, C.c_void_p, C.c_void_p, C.c_int64] + [C.c_void_p] * 9)
+        lib.orc_join_loopers.restype = C.c_int64
+        lib.orc_join_loopers.argtypes = ([C.c_int, C.c_double, C.c_double, C.c_double, C.c_int64] + [C.c_void_p] * 3 +
+                                         [C.c_int64, C.c_void_p, C.c_int64] + [C.c_void_p] * 8)
         lib.orc_chi2.restype = C.c_double
         lib.orc_chi2.argtypes = [C.c_void_p, C.c_void_p, C.c_double, C.c_double, C.c_double, C.c_double]
         _lib = lib
@@ -450,6 +453,32 @@ def merge(cl, trk_f, trk_i, ids, bz=0.5, n_rows=152, x_min=85.0, x_max=246.0, le
     if legs:
         return link, group, amb, fit, partner, leg
     return link, group, amb, fit
+
+
+def join_loopers(cl, trk_f, trk_i, ids, group, partner, leg, bz=0.5, n_rows=152, x_min=85.0, x_max=246.0):
+    """The legs of every looper joined into one track (after merge(..., legs=True)):
+    (joined [n] component label, jfit [n,7] per joined component (centre x, y,
+    radius, tan lambda, z0 at the primary legs' innermost cluster, clusters,
+    tracks)), and the number of joined components."""
+    lib = _load()
+    y = np.ascontiguousarray(cl.y, np.float32)
+    z = np.ascontiguousarray(cl.z, np.float32)
+    row = np.ascontiguousarray(cl.row, np.int32)
+    sec = np.ascontiguousarray(cl.item_sector, np.uint32)
+    tf = np.ascontiguousarray(np.asarray(trk_f, np.float32).reshape(-1, 7))
+    ti = np.ascontiguousarray(np.asarray(trk_i, np.int64).reshape(-1, 3))
+    ids = np.ascontiguousarray(ids, np.uint32)
+    group = np.ascontiguousarray(group, np.int32)
+    partner = np.ascontiguousarray(partner, np.int32)
+    leg = np.ascontiguousarray(leg, np.uint8)
+    n = tf.shape[0]
+    joined = np.empty(n, np.int32)
+    jfit = np.empty((n, 7), np.float64)
+    k = lib.orc_join_loopers(n_rows, x_min, x_max, bz, y.shape[0], _p(y), _p(z), _p(row), sec.shape[0], _p(sec), n,
+                             _p(tf), _p(ti), _p(ids), _p(group), _p(partner), _p(leg), _p(joined), _p(jfit))
+    if k < 0:
+        raise ValueError("bad input")
+    return joined, jfit, int(k)
 
 
 def merge_tracks(ref):

@@ -216,3 +216,73 @@ def test_looper_legs_on_an_event_with_secondary_legs():
     paired = np.mean([((lab == m) & (partner >= 0)).any() for m in both])
     assert len(both) > 500 and paired > 0.70
     assert (leg[p] == true_leg[p]).mean() > 0.99
+
+
+def _looper_pieces(seed=43):
+    """A noise-free event whose low-pT helices leave both legs; for one particle
+    with both legs in two or more sectors each, its pieces per (leg, sector) as
+    tracks: primary pieces first (one group), then the secondary pieces (another
+    group), the first pieces of the two legs paired."""
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_event(seed, 400, sigma_y=0.0, sigma_z=0.0, noise_frac=0.0, pt_range=(0.15, 0.35),
+                          second_leg=True)
+    item_of = np.repeat(np.arange(cl.n_items), np.diff(cl.item_off.astype(np.int64)))
+    for m in range(cl.tracks["pt"].shape[0]):
+        pieces = []
+        for lg in (0, 1):
+            sel = (cl.mc == m) & (cl.leg == lg)
+            its = [it for it in np.unique(item_of[sel]) if ((item_of == it) & sel).sum() >= 10]
+            pieces.append([np.flatnonzero(sel & (item_of == it)) for it in its])
+        if len(pieces[0]) >= 2 and len(pieces[1]) >= 1:
+            break
+    ids, ti = [], []
+    for lg in (0, 1):
+        for p in pieces[lg]:
+            ti.append([item_of[p[0]], len(ids), p.shape[0]])
+            ids.extend(p.tolist())
+    n0, n = len(pieces[0]), len(ti)
+    tf = np.zeros((n, 7), np.float32)
+    q, pt = cl.tracks["q"][m], cl.tracks["pt"][m]
+    tf[:n0, 5] = q / pt       # primary pieces move outward with the particle's charge
+    tf[n0:, 5] = -q / pt      # the returning leg is fitted in the reversed direction
+    group = np.array([0] * n0 + [n0] * (n - n0), np.int32)
+    partner = np.full(n, -1, np.int32)
+    partner[0], partner[n0] = n0, 0
+    leg = np.array([0] * n0 + [1] * (n - n0), np.uint8)
+    return cl, m, tf, np.array(ti, np.int64), np.array(ids, np.uint32), group, partner, leg
+
+
+def test_joined_looper_refit_recovers_the_helix():
+    """The two legs of a noise-free looper, joined: one component labelled by
+    its smallest track, and its refit (circle over both legs, z against the arc
+    R dtheta turned from the primary leg's innermost cluster) gives the true
+    radius, centre and tan(lambda), and z0 = z of that cluster."""
+    cl, m, tf, ti, ids, group, partner, leg = _looper_pieces()
+    joined, jfit, k = oracle.join_loopers(cl, tf, ti, ids, group, partner, leg)
+    assert k == 1 and (joined == 0).all()
+    R = cl.tracks["pt"][m] / KB
+    q, ph = cl.tracks["q"][m], cl.tracks["phi0"][m]
+    xc, yc = q * R * math.sin(ph), -q * R * math.cos(ph)
+    f = jfit[0]
+    assert abs(f[2] - R) < 1e-4 * R, (f[2], R)
+    assert math.hypot(f[0] - xc, f[1] - yc) < 1e-4 * R
+    assert abs(f[3] - cl.tracks["tgl"][m]) < 1e-4, (f[3], cl.tracks["tgl"][m])
+    prim = ids[:ti[group == 0][:, 2].sum()]
+    xr = row_x()
+    gx, gy = [], []
+    for t in range(ti.shape[0]):
+        if group[t] != 0:
+            continue
+        a = (int(cl.item_sector[ti[t, 0]]) % 18) * WEDGE
+        c = ids[ti[t, 1]:ti[t, 1] + ti[t, 2]]
+        gx.extend(xr[cl.row[c]] * math.cos(a) - cl.y[c] * math.sin(a))
+        gy.extend(xr[cl.row[c]] * math.sin(a) + cl.y[c] * math.cos(a))
+    ref = prim[int(np.argmin(np.hypot(gx, gy)))]
+    assert abs(f[4] - cl.z[ref]) < 1e-3, (f[4], cl.z[ref])
+    assert f[5] == ids.shape[0] and f[6] == ti.shape[0]
+
+
+def test_unpaired_groups_are_not_joined():
+    cl, m, tf, ti, ids, group, partner, leg = _looper_pieces()
+    joined, jfit, k = oracle.join_loopers(cl, tf, ti, ids, group, np.full_like(partner, -1), np.zeros_like(leg))
+    assert k == 0 and np.array_equal(joined, group) and not jfit.any()
