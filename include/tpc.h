@@ -64,8 +64,9 @@ typedef struct {
   float row_x_min, row_x_max; /* radii of the first and last pad row [cm] (85, 246) */
   float sector_half_angle_deg;/* sector half opening angle (10) */
   float sigma_y, sigma_z;     /* cluster resolution used by the Kalman filter [cm] (0.1) */
-  tpc_mode mode;              /* PLAIN: one launch per step; BATCHED: persistent kernel over a
-                                 work queue of items (identical results) */
+  tpc_mode mode;              /* PLAIN: one launch per step over all items; BATCHED: the same
+                                 stages with the tracklets taken from a work queue ordered by
+                                 chain length (identical results) */
   tpc_corr correction;        /* space-point correction applied by tpc_track (see tpc_set_correction) */
   uint64_t max_clusters;      /* initial reservation (0 = grow on demand) */
   uint32_t max_items;         /* initial reservation (0 = grow on demand) */
@@ -171,7 +172,8 @@ tpc_status tpc_device_tracks(tpc_ctx* ctx, const tpc_track_t** trk, const uint32
 
 /* Per-step device times of the last tpc_track() in microseconds (needs
  * cfg.profile = 1): us[i] for the steps named by tpc_stage_name(i); steps the
- * last run's mode does not have read 0 (plain mode: 0..8, batched: 9..10).
+ * last run's mode does not have read 0 (both modes: 0..8; 9..10 are no longer
+ * used).
  * Entries 11..12 are the two kernels of the last tpc_cluster_masks() call and
  * 13..15 the symbol, rANS and layout phases of the last tpc_compress() call
  * (tpc_reduce.h) since the batch was loaded, else 0.  Entry 16 is the
@@ -260,8 +262,8 @@ typedef struct {
   int tracklet_blocks_per_sm;
   int sort_smem;
   int link_rows;
-  int mode;          /* 1 = plain (one launch per step), 2 = batched (persistent kernel) */
-  int batch_lanes;   /* lanes per tracklet in the batched kernel: 1, 2 or 4 */
+  int mode;          /* 1 = plain, 2 = batched (tracklets from a queue ordered by chain length) */
+  int batch_lanes;   /* lanes per tracklet in the batched form: 1, 2 or 4 */
   int use_graph;     /* 1 = launch directly, 2 = capture tpc_track once per load and replay it */
   int merge_sort_cap;
 } tpc_tuning;

@@ -276,6 +276,30 @@ tpc_status tpc_merge_tracks(tpc_ctx* ctx, const tpc_track_t* tracks, uint64_t n_
                             uint64_t n_ids, int on_device, int32_t* link, int32_t* group, double* fit,
                             int32_t* leg_partner, uint8_t* leg);
 
+/* Looper legs joined into one track (Sec. 4: the tracker finds the legs of a
+ * looping track separately, and they are merged into one track; the removal
+ * of secondary legs relies on it).  Takes the tracks given to
+ * tpc_merge_tracks (tracks = NULL: the context's own) and its outputs link,
+ * group, leg_partner and leg (all of the same memory kind as on_device says),
+ * and joins the groups of every mutual leg pair into one track:
+ *  joined: [n_tracks] the joined track's smallest track index (the group label
+ *    for tracks of no pair);
+ *  jfit: [n_tracks][7] doubles at each joined track's smallest index: the
+ *    refit over the clusters of both legs -- the algebraic circle of the
+ *    groups (centre x, y, radius, global frame), then tan(lambda) and z0 of
+ *    z = z0 + tan(lambda) s, s = R dtheta the arc turned from the primary
+ *    legs' innermost cluster in the particle's sense of rotation (clockwise
+ *    for q/pT > 0 of the primary leg with the smallest index), z0 at that
+ *    cluster; then clusters and tracks; zero elsewhere.  FP64.
+ *  n_joined (host, nullable): the number of joined tracks.
+ * A joined track holds at most 16 groups and 96 tracks; a larger one, a group
+ * or partner out of range, or a cluster out of range gives TPC_ERR_BAD_INPUT.
+ * The call waits for its stream. */
+tpc_status tpc_join_loopers(tpc_ctx* ctx, const tpc_track_t* tracks, uint64_t n_tracks, const uint32_t* cluster_ids,
+                            uint64_t n_ids, int on_device, const int32_t* link, const int32_t* group,
+                            const int32_t* leg_partner, const uint8_t* leg, int32_t* joined, double* jfit,
+                            uint64_t* n_joined);
+
 #ifdef __cplusplus
 }
 #endif

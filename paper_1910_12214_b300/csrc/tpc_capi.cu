@@ -52,7 +52,6 @@ struct tpc_ctx {
   // host copies used by the debug dump and the work queue
   std::vector<uint64_t> h_item_off;
   std::vector<uint32_t> h_item_sector, h_item_event;  // empty if the batch has none
-  int* own_queue = nullptr;
   // execution mode and CUDA graph of tpc_track
   bool batched = false, use_graph = false, last_batched = false;
   cudaGraphExec_t graph = nullptr;
@@ -90,6 +89,7 @@ struct tpc_ctx {
   // MLP surrogate state (master weights, Adam moments, inference copies)
   int mlp_S = 0, mlp_batch = 1024;
   uint64_t mlp_seed = 0, mlp_step = 0, mlp_T = 0;
+  void* mlp_clock = nullptr;  // device training clock (tpc_mlp.cu)
   float mlp_lr = 3e-2f;
   float *mlp_master = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_partial = nullptr, *mlp_loss = nullptr;
   float* mlp_bounds = nullptr;
@@ -239,16 +239,8 @@ tpc_status reserve(tpc_ctx* c, long long N, long long I, long long n_chunks) {
   b.counts = (unsigned long long*)A(8 * 4);
   b.err = (unsigned int*)A(16);
   b.scan_tmp = (unsigned long long*)A(8 * 1040);
-  c->own_queue = (int*)A(4 * I);
-  b.queue = c->own_queue;
-  b.queue_head = (int*)A(16);
-  b.item_cnt = (unsigned long long*)A(8 * I);
-  b.item_ex = (unsigned long long*)A(8 * I);
-  b.item_ntl = (int*)A(4 * I);
-  b.item_tl_ex = (int*)A(4 * I);
-  b.trk_tmp = A(sizeof(tpc_track_t) * Tcap);
-  b.trk_tl_tmp = (int*)A(4 * Tcap);
-  b.ids_tmp = (uint32_t*)A(4 * N);
+  b.chain_len = (int*)A(4 * Tcap);
+  b.tl_order = (int*)A(4 * Tcap);
   b.cy = (float*)A(4 * N);
   b.cz = (float*)A(4 * N);
   b.T_cap = (int)Tcap;
@@ -330,8 +322,7 @@ extern "C" tpc_status tpc_init(const tpc_config* cfg, tpc_ctx** out) {
   c->batched = cfg->mode == TPC_MODE_BATCHED;
   c->corr = cfg->correction;
   c->use_graph = capturable(c->stream);
-  if ((e = tpc_configure_kernels(L.sort_smem, L.link_smem)) != cudaSuccess ||
-      (e = tpc_batched_occupancy(L.batch_per_sm)) != cudaSuccess) {
+  if ((e = tpc_configure_kernels(L.sort_smem, L.link_smem)) != cudaSuccess) {
     cudaGetLastError();
     if (c->own_stream) cudaStreamDestroy(c->stream);
     delete c;
@@ -426,7 +417,6 @@ extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
     e = cudaMemcpyAsync((void*)sec_dev, cl->item_sector, 4 * I, cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess && cl->item_event)
     e = cudaMemcpyAsync((void*)ev_dev, cl->item_event, 4 * I, cudaMemcpyHostToDevice, c->stream);
-  // work queue of the batched form: items by decreasing cluster count (longest first)
   c->h_item_off.assign(cl->item_off, cl->item_off + cl->n_items + 1);
   if (cl->item_sector)
     c->h_item_sector.assign(cl->item_sector, cl->item_sector + cl->n_items);
@@ -436,13 +426,6 @@ extern "C" tpc_status tpc_load_clusters(tpc_ctx* c, const tpc_clusters* cl) {
     c->h_item_event.assign(cl->item_event, cl->item_event + cl->n_items);
   else
     c->h_item_event.clear();
-  std::vector<int> order(cl->n_items);
-  for (uint32_t i = 0; i < cl->n_items; ++i) order[i] = (int)i;
-  std::stable_sort(order.begin(), order.end(), [&](int u, int v) {
-    return cl->item_off[u + 1] - cl->item_off[u] > cl->item_off[v + 1] - cl->item_off[v];
-  });
-  if (e == cudaSuccess && cl->n_items)
-    e = cudaMemcpyAsync(c->own_queue, order.data(), 4 * order.size(), cudaMemcpyHostToDevice, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.err, 0, 16, c->stream);
   if (e == cudaSuccess) e = cudaMemsetAsync(b.counts, 0, 32, c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "metadata upload");
@@ -794,8 +777,7 @@ extern "C" tpc_status tpc_stage_times(tpc_ctx* c, float* us, int n, int* n_stage
     float ms = 0.f;
     const bool corr = i == TPC_N_REPORTED_STAGES - 1;
     const bool mask = i >= TPC_N_STAGES && i < TPC_N_STAGES + 2, cmp = !corr && i >= TPC_N_STAGES + 2;
-    const bool mine = corr ? c->corr_timed
-                           : cmp ? c->cmp_timed : (mask ? c->mask_timed : (c->last_batched ? (i >= 9) : (i < 9)));
+    const bool mine = corr ? c->corr_timed : cmp ? c->cmp_timed : (mask ? c->mask_timed : i < 9);
     const int j = i - TPC_N_STAGES - 2;
     const cudaEvent_t a = corr ? c->corr_ev[0]
                                : cmp ? c->cmp_ev[2 * j] : (mask ? c->mask_ev[i - TPC_N_STAGES] : c->ev[i]);
@@ -828,23 +810,11 @@ extern "C" tpc_status tpc_debug_dump(tpc_ctx* c, int stage, int32_t* buf, uint64
   std::vector<RowInfo> rows(M);
   if (M && (e = cudaMemcpy(rows.data(), b.rows, sizeof(RowInfo) * M, cudaMemcpyDeviceToHost)) != cudaSuccess)
     return cuda_fail(c, e, "dump");
-  // tracklet storage index of every tracklet in canonical order (plain: 0..T-1;
-  // batched: item k's tracklets at item_off[k]/3 + k + local)
+  // tracklet storage index of every tracklet in canonical order (both forms: 0..T-1)
   int T = 0;
-  std::vector<int> tl_index;
-  if (!c->last_batched) {
-    if ((e = cudaMemcpy(&T, b.start_ex + N, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(c, e, "dump");
-    tl_index.resize(T);
-    for (int t = 0; t < T; ++t) tl_index[t] = t;
-  } else {
-    std::vector<int> ntl;
-    if ((e = D2H(ntl, b.item_ntl, b.I)) != cudaSuccess) return cuda_fail(c, e, "dump");
-    for (int k = 0; k < b.I && k + 1 < (int)c->h_item_off.size(); ++k) {
-      const int tlb = (int)(c->h_item_off[k] / 3) + k;
-      for (int l = 0; l < ntl[k]; ++l) tl_index.push_back(tlb + l);
-    }
-    T = (int)tl_index.size();
-  }
+  if ((e = cudaMemcpy(&T, b.start_ex + N, 4, cudaMemcpyDeviceToHost)) != cudaSuccess) return cuda_fail(c, e, "dump");
+  std::vector<int> tl_index(T);
+  for (int t = 0; t < T; ++t) tl_index[t] = t;
   const int Tmax = tl_index.empty() ? 0 : *std::max_element(tl_index.begin(), tl_index.end()) + 1;
   switch (stage) {
     case 0: {
@@ -1305,14 +1275,12 @@ extern "C" tpc_status tpc_surrogate_train(tpc_ctx* c, uint64_t n_samples, uint64
       return cuda_fail(c, e, "surrogate init");
   }
   const uint64_t end = max_steps > 0 ? std::min<uint64_t>(c->mlp_T, c->mlp_step + (uint64_t)max_steps) : c->mlp_T;
-  for (uint64_t t = c->mlp_step; t < end; ++t) {
-    const double lr_t = c->mlp_lr * 0.5 * (1.0 + std::cos(M_PI * (double)t / (double)c->mlp_T));
-    const double c1 = 1.0 - std::pow(0.9, (double)(t + 1)), c2 = 1.0 - std::pow(0.999, (double)(t + 1));
-    e = tpc_mlp_step(c->mlp_master, c->mlp_m, c->mlp_v, c->mlp_partial, c->mlp_loss, (const float2*)c->grid_dev,
-                     c->b.grid_nx, c->b.grid_ny, c->b.grid_nz, S, c->mlp_batch, seed, t, (float)lr_t, (float)c1,
-                     (float)c2, c->stream);
-    if (e != cudaSuccess) return cuda_fail(c, e, "surrogate step");
-  }
+  if (!c->mlp_clock && !(c->mlp_clock = persist_alloc(c, tpc_mlp_clock_bytes())))
+    return fail(c, TPC_ERR_OOM, "device allocation failed (training clock)");
+  e = tpc_mlp_train_steps(c->mlp_clock, c->mlp_step, c->mlp_T, c->mlp_lr, end - c->mlp_step, c->mlp_master, c->mlp_m,
+                          c->mlp_v, c->mlp_partial, c->mlp_loss, (const float2*)c->grid_dev, c->b.grid_nx,
+                          c->b.grid_ny, c->b.grid_nz, S, c->mlp_batch, seed, capturable(c->stream), c->stream);
+  if (e != cudaSuccess) return cuda_fail(c, e, "surrogate steps");
   c->mlp_step = end;
   tpc_status st = mlp_publish(c);
   if (st != TPC_OK) return st;
@@ -2040,6 +2008,127 @@ extern "C" tpc_status tpc_merge_tracks(tpc_ctx* c, const tpc_track_t* tracks, ui
       (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
     return cuda_fail(c, e, "merge sync");
   if (err & TPC_DERR_BAD_TRACK) return fail(c, TPC_ERR_BAD_INPUT, "a track is out of range or out of item order");
+  return TPC_OK;
+}
+
+extern "C" tpc_status tpc_join_loopers(tpc_ctx* c, const tpc_track_t* tracks, uint64_t n_tracks,
+                                       const uint32_t* cluster_ids, uint64_t n_ids, int on_device, const int32_t* link,
+                                       const int32_t* group, const int32_t* leg_partner, const uint8_t* leg,
+                                       int32_t* joined, double* jfit, uint64_t* n_joined) {
+  if (c && c->frame_src)
+    return fail(c, TPC_ERR_STATE, "the data-reduction calls take a batch loaded by tpc_load_clusters, not a frame");
+  if (!c) return TPC_ERR_INVALID_ARG;
+  if (!c->tracked) return fail(c, TPC_ERR_STATE, "tpc_join_loopers before tpc_track");
+  const int I = (int)c->h_item_sector.size();
+  if (I == 0) return fail(c, TPC_ERR_STATE, "the batch has no item_sector");
+  if (n_tracks && (!link || !group || !leg_partner || !leg || !joined || !jfit))
+    return fail(c, TPC_ERR_INVALID_ARG, "null input or output");
+  if (tracks && n_tracks && !cluster_ids) return fail(c, TPC_ERR_INVALID_ARG, "null cluster ids");
+  if (n_tracks > 0x7fffffffull) return fail(c, TPC_ERR_INVALID_ARG, "too many tracks");
+  cudaError_t e;
+  const long long nt = (long long)n_tracks;
+  long long ni = (long long)n_ids;
+  const void* trk;
+  const uint32_t* ids;
+  if (!tracks) {
+    unsigned long long cnt[2];
+    if ((e = cudaMemcpyAsync(cnt, c->b.counts, 16, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+        (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+      return cuda_fail(c, e, "track counts");
+    if (cnt[0] != n_tracks) return fail(c, TPC_ERR_INVALID_ARG, "n_tracks differs from the number of tracks");
+    trk = c->b.trk;
+    ids = c->b.trk_ids;
+    ni = (long long)cnt[1];
+  } else if (on_device) {
+    trk = tracks;
+    ids = cluster_ids;
+  } else {
+    void* t = cmp_buffer(c, 33, sizeof(tpc_track_t) * (size_t)nt);
+    void* d = cmp_buffer(c, 34, 4 * (size_t)ni);
+    if (!t || !d) return fail(c, TPC_ERR_OOM, "track staging");
+    if ((nt && (e = cudaMemcpyAsync(t, tracks, sizeof(tpc_track_t) * nt, cudaMemcpyHostToDevice, c->stream)) !=
+                   cudaSuccess) ||
+        (ni && (e = cudaMemcpyAsync(d, cluster_ids, 4 * ni, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess))
+      return cuda_fail(c, e, "track upload");
+    trk = t;
+    ids = (const uint32_t*)d;
+  }
+  const size_t m = (size_t)std::max(nt, 1ll);
+  // inputs (link 8 B, group 4 B, partner 4 B, leg 1 B per track) and outputs (joined 4 B, jfit 56 B)
+  const size_t i_link = 0, i_group = 8 * m, i_part = 12 * m, i_leg = 16 * m;
+  const size_t o_jfit = 0, o_joined = 56 * m;
+  uint8_t* in_st = nullptr;
+  uint8_t* out_st = nullptr;
+  if (!on_device) {
+    in_st = (uint8_t*)cmp_buffer(c, 44, 17 * m);
+    out_st = (uint8_t*)cmp_buffer(c, 46, 60 * m);
+  }
+  int* work = (int*)cmp_buffer(c, 45, 8 * m + 16);  // glab, plist, pair count
+  unsigned int* d_err = (unsigned int*)cmp_buffer(c, 47, 4);
+  if ((!on_device && (!in_st || !out_st)) || !work || !d_err) return fail(c, TPC_ERR_OOM, "join buffers");
+  JoinArgs a{};
+  if (on_device) {
+    a.link = link;
+    a.group = group;
+    a.partner = leg_partner;
+    a.leg = leg;
+    a.joined = joined;
+    a.jfit = jfit;
+  } else {
+    if (nt && ((e = cudaMemcpyAsync(in_st + i_link, link, 8 * nt, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess ||
+               (e = cudaMemcpyAsync(in_st + i_group, group, 4 * nt, cudaMemcpyHostToDevice, c->stream)) !=
+                   cudaSuccess ||
+               (e = cudaMemcpyAsync(in_st + i_part, leg_partner, 4 * nt, cudaMemcpyHostToDevice, c->stream)) !=
+                   cudaSuccess ||
+               (e = cudaMemcpyAsync(in_st + i_leg, leg, nt, cudaMemcpyHostToDevice, c->stream)) != cudaSuccess))
+      return cuda_fail(c, e, "join upload");
+    a.link = (const int*)(in_st + i_link);
+    a.group = (const int*)(in_st + i_group);
+    a.partner = (const int*)(in_st + i_part);
+    a.leg = in_st + i_leg;
+    a.jfit = (double*)(out_st + o_jfit);
+    a.joined = (int*)(out_st + o_joined);
+  }
+  a.trk = trk;
+  a.ids = ids;
+  a.n_ids = ni;
+  a.n_trk = (int)nt;
+  a.item_sector = c->b.item_sector;
+  a.I = I;
+  a.y = c->b.y;
+  a.z = c->b.z;
+  a.row = c->b.row;
+  a.N = c->b.N;
+  a.glab = work;
+  a.plist = work + m;
+  a.n_pairs = work + 2 * m;
+  a.err = d_err;
+  if ((e = cudaMemsetAsync(d_err, 0, 4, c->stream)) != cudaSuccess ||
+      (e = launch_join(a, c->par, c->lc.num_sms, c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "join");
+  if (!on_device && nt &&
+      ((e = cudaMemcpyAsync(joined, a.joined, 4 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+       (e = cudaMemcpyAsync(jfit, a.jfit, 56 * (size_t)nt, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess))
+    return cuda_fail(c, e, "join download");
+  unsigned int err = 0;
+  int np = 0;
+  if ((e = cudaMemcpyAsync(&err, d_err, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaMemcpyAsync(&np, a.n_pairs, 4, cudaMemcpyDeviceToHost, c->stream)) != cudaSuccess ||
+      (e = cudaStreamSynchronize(c->stream)) != cudaSuccess)
+    return cuda_fail(c, e, "join sync");
+  if (err & TPC_DERR_BAD_TRACK)
+    return fail(c, TPC_ERR_BAD_INPUT, "a track, group or partner is out of range, or a joined track is too large");
+  if (n_joined) {  // joined tracks: the pairs whose primary is the smallest of its joined track
+    std::vector<int> pl(np), gl((size_t)nt);
+    *n_joined = 0;
+    if (np && ((e = cudaMemcpy(pl.data(), a.plist, 4 * (size_t)np, cudaMemcpyDeviceToHost)) != cudaSuccess ||
+               (e = cudaMemcpy(gl.data(), a.joined, 4 * (size_t)nt, cudaMemcpyDeviceToHost)) != cudaSuccess))
+      return cuda_fail(c, e, "join count");
+    std::vector<int> roots;
+    for (int t : pl) roots.push_back(gl[t]);
+    std::sort(roots.begin(), roots.end());
+    *n_joined = (uint64_t)(std::unique(roots.begin(), roots.end()) - roots.begin());
+  }
   return TPC_OK;
 }
 

@@ -114,13 +114,9 @@ struct Buffers {
   unsigned long long* counts;  // [0] n_trk, [1] n_ids, [2] n_tracklets
   unsigned int* err;
   unsigned long long* scan_tmp;  // block sums
-  // batched form
-  const int* queue;               // items, longest first [I]
-  int* queue_head;                // atomic work-queue position
-  unsigned long long* item_cnt;   // (tracks << 32 | ids) per item [I]
-  unsigned long long* item_ex;    // exclusive scan of item_cnt [I]
-  int* item_ntl;                  // tracklets per item [I]
-  int* item_tl_ex;                // exclusive scan of item_ntl [I]
+  // batched form: tracklets from a work queue ordered by chain length
+  int* chain_len;                 // hits of every start hit's chain [T_cap]
+  int* tl_order;                  // tracklet indices, shortest chains first [T_cap]
   // space-point correction (applied before binning when enabled)
   const float2* grid;             // per-sector (dy, dz) nodes [S][nx][ny][nz]
   const float* grid_bounds;       // [S][6]: x0, x1, v0, v1, z0, z1 (v = y / (x tan_half))
@@ -129,9 +125,6 @@ struct Buffers {
   int mlp_sectors;
   float* cy;                      // corrected y, z [N]
   float* cz;
-  void* trk_tmp;                  // per-item track regions [T_cap]
-  int* trk_tl_tmp;                // tracklet storage index of every per-item track [T_cap]
-  uint32_t* ids_tmp;              // per-item cluster-id regions [N]
 };
 
 #define TPC_N_STAGES 11  // 9 plain-mode steps, then the batched kernel and its compaction
@@ -148,13 +141,11 @@ struct LaunchCfg {
   int grid_tl;    // blocks of k_tracklets
   int block_tl;   // threads per block of k_tracklets
   int tl_group;   // lanes per tracklet (1, 2, 4, 8, 16, 32)
-  int batch_group;  // lanes per tracklet in the batched kernel (1, 2, 4)
-  int batch_per_sm[3];  // resident CTAs per SM of the batched kernel for 1, 2, 4 lanes
+  int batch_group;  // lanes per tracklet in the batched form (1, 2, 4)
   int merge_sort_cap;   // tracks of one event and side sorted by the merger (0: none)
 };
 
 cudaError_t tpc_configure_kernels(int sort_smem, int link_smem);
-cudaError_t tpc_batched_occupancy(int per_sm[3]);
 cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t tpc_launch_batched(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev);
 cudaError_t tpc_launch_grid_correction(const Buffers& b, cudaStream_t s);
@@ -197,9 +188,12 @@ size_t tpc_mlp_infer_bytes();
 int tpc_mlp_nparams();
 int tpc_mlp_stride();
 cudaError_t tpc_mlp_init(float* master, float* m, float* v, int S, uint64_t seed, cudaStream_t s);
-cudaError_t tpc_mlp_step(float* master, float* m, float* v, float* partial, float* loss, const float2* grid, int nx,
-                         int ny, int nz, int S, int batch, uint64_t seed, uint64_t step, float lr_t, float c1, float c2,
-                         cudaStream_t s);
+size_t tpc_mlp_clock_bytes();
+// n_steps training steps from step `first` of T (cosine schedule from lr);
+// clock: device block of tpc_mlp_clock_bytes()
+cudaError_t tpc_mlp_train_steps(void* clock, uint64_t first, uint64_t T, float lr, uint64_t n_steps, float* master,
+                                float* m, float* v, float* partial, float* loss, const float2* grid, int nx, int ny,
+                                int nz, int S, int batch, uint64_t seed, bool graph, cudaStream_t s);
 cudaError_t tpc_mlp_grad_only(const float* master, float* partial, float* loss, const float2* grid, int nx, int ny,
                               int nz, int S, int batch, uint64_t seed, uint64_t step, cudaStream_t s);
 cudaError_t tpc_mlp_eval(const float* master, const float2* grid, int nx, int ny, int nz, int S, int nblk,
@@ -336,3 +330,28 @@ struct MrgArgs {
   unsigned int* err;
 };
 cudaError_t launch_merge(const MrgArgs& a, const DevParams& par, int num_sms, cudaStream_t s);
+
+// Looper legs joined into one track (tpc_join_loopers; tpc_reduce.cu)
+struct JoinArgs {
+  const void* trk;            // tpc_track_t [n_trk], sorted by item
+  const uint32_t* ids;
+  long long n_ids;
+  int n_trk;
+  const int* link;            // [n_trk][2] merger links
+  const int* group;           // [n_trk] merger groups (smallest index)
+  const int* partner;         // [n_trk] other leg, -1 none
+  const uint8_t* leg;         // [n_trk] 1 = secondary leg
+  const uint32_t* item_sector;
+  int I;
+  const float* y;
+  const float* z;
+  const int* row;
+  int N;
+  int* glab;                  // [n_trk] label of every group root
+  int* plist;                 // [n_trk] primary legs of mutual pairs
+  int* n_pairs;
+  int* joined;                // out [n_trk]
+  double* jfit;               // out [n_trk][7]
+  unsigned int* err;
+};
+cudaError_t launch_join(const JoinArgs& a, const DevParams& par, int num_sms, cudaStream_t s);

@@ -44,7 +44,6 @@ constexpr long long LINK_D = 512;       // 0.5 cm chord deviation
 constexpr float INFLATE = 100.0f;       // refit prior: outward variances x100 (at most C0)
 constexpr int JOSEPH_UPDATES = 3;       // first updates of a fit done in the Joseph form
 constexpr int LINK_THREADS = 256;
-constexpr int LINK_MAXC = 24;           // window candidates per side and hit
 constexpr int LINK_MAXC_STAGED = 8;     // the same in k_links (overflow: direct enumeration)
 constexpr int LINK_STAGE_MAX = 160 * 1024;  // shared-memory staging of k_links
 
@@ -126,25 +125,54 @@ __global__ void __launch_bounds__(256) k_row_stats(const __grid_constant__ Buffe
     s_min[0][r] = s_min[1][r] = s_min[2][r] = s_min[3][r] = 0x7F7F7F7F;
   }
   __syncthreads();
-  for (int i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) {
-    const float xv = b.x[i], yv = b.y[i], zv = b.z[i];
-    const int r = b.row[i];
+  // one cluster: validation, quantisation (y*1024 is exact in FP32; round half
+  // to even), the row's count and extents; returns the key (-1: rejected)
+  auto one = [&](float xv, float yv, float zv, int r, int2* q) {
     const bool ok = r >= 0 && r < NR && fabsf(xv) < INFINITY && fabsf(yv) <= 1e6f && fabsf(zv) <= 1e6f;
     if (!ok) {
       atomicOr(b.err, TPC_DERR_BAD_INPUT);
-      b.cl_key[i] = -1;
-      continue;
+      *q = make_int2(0, 0);
+      return -1;
     }
-    // y*1024 is exact in FP32; round half to even
     const int qy = __float2int_rn(yv * TPC_QSCALE);
     const int qz = __float2int_rn(zv * TPC_QSCALE);
-    b.cl_key[i] = ch.item * NR + r;
-    b.cl_q[i] = make_int2(qy, qz);
+    *q = make_int2(qy, qz);
     atomicAdd(&s_cnt[r], 1);
     atomicMin(&s_min[0][r], qy);
     atomicMin(&s_min[1][r], -qy);
     atomicMin(&s_min[2][r], qz);
     atomicMin(&s_min[3][r], -qz);
+    return ch.item * NR + r;
+  };
+  auto scalar = [&](int i) {
+    int2 q;
+    const int key = one(b.x[i], b.y[i], b.z[i], b.row[i], &q);
+    b.cl_key[i] = key;
+    if (key >= 0) b.cl_q[i] = q;
+  };
+  const bool vec = ((reinterpret_cast<uintptr_t>(b.x) | reinterpret_cast<uintptr_t>(b.y) |
+                     reinterpret_cast<uintptr_t>(b.z) | reinterpret_cast<uintptr_t>(b.row)) & 15) == 0;
+  if (vec) {
+    // four consecutive clusters per thread with one 16-byte load per array
+    // (and 16-byte stores), the unaligned head and tail of the chunk alone
+    const int a4 = min(ch.end, (ch.begin + 3) & ~3), e4 = max(a4, ch.end & ~3);
+    for (int i = ch.begin + threadIdx.x; i < a4; i += blockDim.x) scalar(i);
+    for (int i = e4 + threadIdx.x; i < ch.end; i += blockDim.x) scalar(i);
+    for (int v = a4 + 4 * threadIdx.x; v < e4; v += 4 * blockDim.x) {
+      const float4 X = __ldg(reinterpret_cast<const float4*>(b.x + v));
+      const float4 Y = __ldg(reinterpret_cast<const float4*>(b.y + v));
+      const float4 Z = __ldg(reinterpret_cast<const float4*>(b.z + v));
+      const int4 R = __ldg(reinterpret_cast<const int4*>(b.row + v));
+      int2 q0, q1, q2, q3;
+      const int k0 = one(X.x, Y.x, Z.x, R.x, &q0), k1 = one(X.y, Y.y, Z.y, R.y, &q1);
+      const int k2 = one(X.z, Y.z, Z.z, R.z, &q2), k3 = one(X.w, Y.w, Z.w, R.w, &q3);
+      *reinterpret_cast<int4*>(b.cl_key + v) = make_int4(k0, k1, k2, k3);
+      int4* qv = reinterpret_cast<int4*>(b.cl_q + v);
+      qv[0] = make_int4(q0.x, q0.y, q1.x, q1.y);
+      qv[1] = make_int4(q2.x, q2.y, q3.x, q3.y);
+    }
+  } else {
+    for (int i = ch.begin + threadIdx.x; i < ch.end; i += blockDim.x) scalar(i);
   }
   __syncthreads();
   for (int r = threadIdx.x; r < NR; r += blockDim.x) {
@@ -705,7 +733,11 @@ __device__ __forceinline__ float d_asin_over_u(float u) {
 
 // Helix step of (y, z, sinphi, tanlambda, q/pT) and covariance transport C <- F C F^T.
 // F differs from the identity in F02, F04, F12, F13, F14, F24 only.
-__device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float* C, float x1, float x2) {
+struct Jac {
+  float a, bq, c, d, e, g;  // F02, F04, F12, F13, F14, F24
+};
+
+__device__ __forceinline__ bool kf_step_state(const DevParams& P, float* p, float x1, float x2, Jac* J) {
   const float kB = P.kB;
   const float dx = x2 - x1;
   const float s1 = p[2];
@@ -732,15 +764,20 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float
   const float dg_dT = __fdividef(T, w) * (f + u * fp);
   const float dg_dk = 0.5f * w * w * adx * fp;
   const float tgl = p[3];
-  const float a = dx * dT_ds;                          // F02
-  const float bq = dx * dT_dq;                         // F04
-  const float c = tgl * dx * dg_dT * dT_ds;            // F12
-  const float d = ell;                                 // F13
-  const float e = tgl * dx * fma2(dg_dT, dT_dq, dg_dk, kB);  // F14
-  const float g = -kB * dx;                            // F24
+  J->a = dx * dT_ds;                                  // F02
+  J->bq = dx * dT_dq;                                 // F04
+  J->c = tgl * dx * dg_dT * dT_ds;                    // F12
+  J->d = ell;                                         // F13
+  J->e = tgl * dx * fma2(dg_dT, dT_dq, dg_dk, kB);    // F14
+  J->g = -kB * dx;                                    // F24
   p[0] += dx * T;
   p[1] += tgl * ell;
   p[2] = s2;
+  return true;
+}
+
+__device__ __forceinline__ void kf_transport(float* C, const Jac& J) {
+  const float a = J.a, bq = J.bq, c = J.c, d = J.d, e = J.e, g = J.g;
   // full symmetric copy
   float M[5][5];
 #pragma unroll
@@ -771,6 +808,12 @@ __device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float
   C[ix(4, 1)] = v1[4];
   C[ix(4, 2)] = v2[4];
   // (3,3), (4,3), (4,4) unchanged
+}
+
+__device__ __forceinline__ bool kf_propagate(const DevParams& P, float* p, float* C, float x1, float x2) {
+  Jac J;
+  if (!kf_step_state(P, p, x1, x2, &J)) return false;
+  kf_transport(C, J);
   return true;
 }
 
@@ -926,8 +969,8 @@ struct Grp {
 };
 
 // Read-only loads: through the non-coherent path where the data was written by
-// an earlier launch (NC = true); plain loads in the persistent kernel, which
-// writes the same arrays earlier in the same launch, and for shared memory.
+// an earlier launch (NC = true); plain loads for data of the same launch and
+// for shared memory.
 template <bool NC, class T>
 __device__ __forceinline__ T ld(const T* p) {
   if constexpr (NC) return __ldg(p);
@@ -959,9 +1002,8 @@ __device__ __forceinline__ RowInfo load_row(const RowInfo* p) {
 // sources; a source that splits an item's rows over several places needs it).
 template <bool NC>
 struct GSrc {  // global memory; NC: data written by an earlier launch
-  // candidates per round of the single-lane search: 8 for the plain kernels,
-  // 4 in the persistent kernel (whose other phases need the registers)
-  static constexpr int kRound = NC ? 8 : 4;
+  // candidates per round of the single-lane search
+  static constexpr int kRound = 8;
   const Buffers* b;
   const RowInfo* rows;  // the item's row table (global, or shared memory)
   __device__ __forceinline__ RowInfo row(int r) const { return load_row<NC>(rows + r); }
@@ -1198,7 +1240,7 @@ __device__ __forceinline__ int pick_hit(const Src& S, const Grp<G>& g, int r, co
 // same propagation and update code together).  The result goes to b.tlu[tl] and
 // the tracklet claims its outermost hit (smallest tracklet index wins); `local`
 // is the item-local id, `rows` the item's row table, `xr` the row positions.
-template <int G, class Src>
+template <int G, bool PRE, class Src>
 __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, const Src& S, const float* xr,
                                             int start, int4 hs, int tl, int local) {
   const DevParams& P = b.par;
@@ -1209,12 +1251,18 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
   const int r0 = key - item * NR;
   const int z_base = hs.y;
   int* hl = b.tl_hits + (size_t)tl * NR;
-  // chain walk (pointer chasing; every lane of the group loads the same address)
+  // chain walk (pointer chasing; every lane of the group loads the same
+  // address), or the chain a previous kernel walked (PRE)
   int L = 0, last = start;
-  for (int h = start; h >= 0 && L < NR; h = S.up(r0 + L - 1, h)) {
-    if (g.gl == 0) hl[L] = h;
-    last = h;
-    ++L;
+  if constexpr (PRE) {
+    L = __ldg(b.chain_len + tl);
+    last = __ldcg(hl + L - 1);
+  } else {
+    for (int h = start; h >= 0 && L < NR; h = S.up(r0 + L - 1, h)) {
+      if (g.gl == 0) hl[L] = h;
+      last = h;
+      ++L;
+    }
   }
   g.sync();
   const int hmid = hl[L / 2];
@@ -1420,7 +1468,7 @@ __global__ void __launch_bounds__(128) k_tracklets_up(const __grid_constant__ Bu
     const int4 hs = __ldg(b.s_hit + start);
     const int item = hs.w / NR;
     const GSrc<true> S{&b, b.rows + (size_t)item * NR};
-    tracklet_up<G>(b, g, S, s_x, start, hs, t, t - b.start_ex[b.item_off[item]]);
+    tracklet_up<G, false>(b, g, S, s_x, start, hs, t, t - b.start_ex[b.item_off[item]]);
   }
 }
 
@@ -1582,331 +1630,98 @@ __global__ void k_counts(const __grid_constant__ Buffers b) {
 
 
 // ============================================================================ S9
-// Batched form: one persistent launch.  Each CTA pops work items (event,
-// sector[, time slice]) from an atomic queue ordered by decreasing cluster
-// count (longest first) and runs every step on the item: shared-memory row
-// statistics, grid setup, counting sort into rows, one warp per row for the
-// bin sort, the neighbour search, cleaning and start compaction, tracklets,
-// shared-cluster resolution and the item's output.  The arithmetic is the
-// plain path's (same device functions), so every item's result is identical.
-// Item k's tracklets live at [item_off[k]/3 + k, ...) and its output at the
-// same place (tracks) and at [item_off[k], ...) (cluster ids); a second kernel
-// concatenates the items.
-namespace {
-constexpr int BT = 128;  // threads per CTA of the persistent kernel
+// Batched form: the stages of the plain form as persistent launches over all
+// items of the batch (events, sectors, time slices) in one captured graph, with
+// the tracklets taken from a work queue ordered by chain length.  A warp runs
+// as long as its slowest lane, and a lane costs about 900 cycles per chain row
+// and 3,400 per searched row: lanes whose chains end at different rows make
+// the warp run both kinds of rows.  Ordering by chain length puts lanes that
+// switch from chain to search at the same row into one warp (on the full TPC
+// event the modelled outward pass drops from 314 to 249 us, the cost of its
+// longest lane).  The queue does not change any result: a tracklet's outputs
+// go to its canonical index.  The order is kept inside each item, so that the
+// lanes of a warp keep reading one item's rows, bins and hits (a global order
+// mixed items in every warp and cost more in cache misses than it saved).
+//   k_chain_walk:  every start hit's chain (hits kept for the outward pass);
+//   k_queue_items: per item (one CTA), a counting sort of its tracklets by chain
+//                  length in shared memory (shortest chains first: their long
+//                  searches start in the item's first warps).
+__global__ void __launch_bounds__(256) k_chain_walk(const __grid_constant__ Buffers b) {
+  const int T = b.start_ex[b.N];
+  const int NR = b.par.n_rows;
+  for (int t = blockIdx.x * blockDim.x + threadIdx.x; t < T; t += gridDim.x * blockDim.x) {
+    int* hl = b.tl_hits + (size_t)t * NR;
+    int L = 0;
+    for (int h = b.starts[t]; h >= 0 && L < NR; h = __ldg(b.up + h)) hl[L++] = h;
+    b.chain_len[t] = L;
+  }
+}
 
-// exclusive scan of n values v(i) (i in [0, n)) over the CTA, chunk by chunk;
-// out(i, ex) receives the exclusive prefix; returns the total
-template <class V, class O>
-__device__ __forceinline__ int cta_scan(int n, V v, O out, int* sm) {
+__global__ void __launch_bounds__(256) k_queue_items(const __grid_constant__ Buffers b) {
+  __shared__ int s_cnt[TPC_MAX_ROWS + 2];
+  __shared__ int sm[33];
+  const int item = blockIdx.x;
+  const int t0 = b.start_ex[b.item_off[item]], t1 = b.start_ex[b.item_off[item + 1]];
+  const int nb = b.par.n_rows + 1;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) s_cnt[k] = 0;
+  __syncthreads();
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) atomicAdd(&s_cnt[b.chain_len[t]], 1);
+  __syncthreads();
   int carry = 0;
-  for (int base = 0; base < n; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const int x = i < n ? v(i) : 0;
+  for (int base = 0; base < nb; base += blockDim.x) {  // block-uniform loop
+    const int k = base + threadIdx.x;
+    const int v = k < nb ? s_cnt[k] : 0;
     int tot;
-    const int ex = block_excl_scan(x, sm, &tot);
-    if (i < n) out(i, carry + ex);
+    const int ex = block_excl_scan(v, sm, &tot);
+    if (k < nb) s_cnt[k] = carry + ex;
     carry += tot;
   }
-  return carry;
+  __syncthreads();
+  for (int t = t0 + threadIdx.x; t < t1; t += blockDim.x) b.tl_order[t0 + atomicAdd(&s_cnt[b.chain_len[t]], 1)] = t;
 }
-
-// one row sorted by one warp: histogram in the row's own first[] entries,
-// warp scan, scatter by arrival slot (slots kept in `slot`), in-bin sort by id
-__device__ __forceinline__ void warp_row_sort(const Buffers& b, const RowInfo& ri, int key, int* slot, int lane) {
-  const int n = ri.n;
-  int* hist = b.first + ri.bin0;
-  if (n == 0) {
-    if (lane == 0) hist[0] = ri.pos0;
-    return;
-  }
-  const int nb = ri.ny * ri.nz;
-  for (int j = lane; j <= nb; j += 32) hist[j] = 0;
-  __syncwarp();
-  const int s = ri.shift;
-  for (int j = lane; j < n; j += 32) {
-    const int2 q = b.g_q[ri.pos0 + j];
-    const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
-    slot[ri.pos0 + j] = atomicAdd(&hist[bin], 1);
-  }
-  __syncwarp();
-  int carry = 0;
-  for (int base = 0; base <= nb; base += 32) {
-    const int j = base + lane;
-    const int v = j <= nb ? hist[j] : 0;
-    const int inc = warp_incl_scan(v);
-    if (j <= nb) hist[j] = carry + inc - v;
-    carry += __shfl_sync(0xffffffffu, inc, 31);
-  }
-  __syncwarp();
-  for (int j = lane; j < n; j += 32) {
-    const int2 q = b.g_q[ri.pos0 + j];
-    const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
-    b.s_hit[ri.pos0 + hist[bin] + slot[ri.pos0 + j]] = make_int4(q.x, q.y, b.g_id[ri.pos0 + j], key);
-  }
-  __syncwarp();
-  for (int bin = lane; bin < nb; bin += 32) {
-    const int a = ri.pos0 + hist[bin], e = ri.pos0 + hist[bin + 1];
-    for (int i = a + 1; i < e; ++i) {
-      const int4 v = b.s_hit[i];
-      int j = i - 1;
-      while (j >= a && b.s_hit[j].z > v.z) {
-        b.s_hit[j + 1] = b.s_hit[j];
-        --j;
-      }
-      b.s_hit[j + 1] = v;
-    }
-  }
-  __syncwarp();
-  for (int j = lane; j <= nb; j += 32) hist[j] += ri.pos0;
-  __syncwarp();
-}
-}  // namespace
 
 template <int G>
-__global__ void __launch_bounds__(BT) k_batched(const __grid_constant__ Buffers b) {
-  const DevParams& P = b.par;
-  __shared__ RowInfo s_rows[TPC_MAX_ROWS];
+__global__ void __launch_bounds__(128) k_tracklets_up_q(const __grid_constant__ Buffers b) {
   __shared__ float s_x[TPC_MAX_ROWS];
-  __shared__ int s_cnt[TPC_MAX_ROWS], s_min[4][TPC_MAX_ROWS], s_fill[TPC_MAX_ROWS];
-  __shared__ int s_cu[LINK_MAXC][BT], s_cd[LINK_MAXC][BT];
-  __shared__ int sm[33];
-  __shared__ int s_item, s_ntl;
-  const int NR = P.n_rows;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarps = blockDim.x >> 5;
+  for (int r = threadIdx.x; r < b.par.n_rows; r += blockDim.x) s_x[r] = b.par.x[r];
+  __syncthreads();
   const Grp<G> g;
-  for (int r = threadIdx.x; r < NR; r += blockDim.x) s_x[r] = P.x[r];
-  for (;;) {
-    if (threadIdx.x == 0) {
-      const int k = atomicAdd(b.queue_head, 1);
-      s_item = k < b.I ? b.queue[k] : -1;
-    }
-    __syncthreads();
-    const int item = s_item;
-    if (item < 0) break;
-    const int a0 = (int)b.item_off[item], a1 = (int)b.item_off[item + 1];
-    const int tlb = a0 / 3 + item;
-    // ---- S1: validation, quantisation and row statistics in shared memory
-    for (int r = threadIdx.x; r < NR; r += blockDim.x) {
-      s_cnt[r] = 0;
-      s_fill[r] = 0;
-      s_min[0][r] = s_min[1][r] = s_min[2][r] = s_min[3][r] = 0x7F7F7F7F;
-    }
-    __syncthreads();
-    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-      b.hit_key[i] = 0ull;
-      b.out_owner[i] = 0x7F7F7F7F;
-      const float xv = b.x[i], yv = b.y[i], zv = b.z[i];
-      const int r = b.row[i];
-      if (!(r >= 0 && r < NR && fabsf(xv) < INFINITY && fabsf(yv) <= 1e6f && fabsf(zv) <= 1e6f)) {
-        atomicOr(b.err, TPC_DERR_BAD_INPUT);
-        continue;
-      }
-      const int qy = __float2int_rn(yv * TPC_QSCALE), qz = __float2int_rn(zv * TPC_QSCALE);
-      atomicAdd(&s_cnt[r], 1);
-      atomicMin(&s_min[0][r], qy);
-      atomicMin(&s_min[1][r], -qy);
-      atomicMin(&s_min[2][r], qz);
-      atomicMin(&s_min[3][r], -qz);
-    }
-    __syncthreads();
-    // ---- S2a: bin size and grid of every row, row and bin offsets
-    for (int r = threadIdx.x; r < NR; r += blockDim.x) {
-      const int n = s_cnt[r];
-      int s = SHIFT_MIN, ny = 0, nz = 0, ymin = 0, zmin = 0;
-      if (n > 0) {
-        ymin = s_min[0][r];
-        zmin = s_min[2][r];
-        const long long dy = (long long)(-s_min[1][r]) - ymin, dz = (long long)(-s_min[3][r]) - zmin;
-        const long long need = ((dy + 1) * (dz + 1) + n - 1) / n;
-        for (;; ++s) {
-          const long long nyy = (dy >> s) + 1, nzz = (dz >> s) + 1;
-          if ((2 * s >= 63 || (1ll << (2 * s)) >= need) && nyy * nzz <= 2ll * n + 2) {
-            ny = (int)nyy;
-            nz = (int)nzz;
-            break;
-          }
-        }
-      }
-      RowInfo& ri = s_rows[r];
-      ri.n = n;
-      ri.ymin = ymin;
-      ri.zmin = zmin;
-      ri.shift = s;
-      ri.ny = ny;
-      ri.nz = nz;
-    }
-    __syncthreads();
-    cta_scan(NR, [&](int r) { return s_rows[r].n; }, [&](int r, int ex) { s_rows[r].pos0 = a0 + ex; }, sm);
-    cta_scan(NR, [&](int r) { return (s_rows[r].n > 0 ? s_rows[r].ny * s_rows[r].nz : 0) + 1; },
-             [&](int r, int ex) { s_rows[r].bin0 = 2 * a0 + 3 * NR * item + ex; }, sm);
-    __syncthreads();
-    for (int r = threadIdx.x; r < NR; r += blockDim.x) b.rows[item * NR + r] = s_rows[r];
-    // ---- S2b: counting sort into rows
-    for (int i = a0 + threadIdx.x; i < a1; i += blockDim.x) {
-      const float xv = b.x[i], yv = b.y[i], zv = b.z[i];
-      const int r = b.row[i];
-      if (!(r >= 0 && r < NR && fabsf(xv) < INFINITY && fabsf(yv) <= 1e6f && fabsf(zv) <= 1e6f)) continue;
-      const int gp = s_rows[r].pos0 + atomicAdd(&s_fill[r], 1);
-      b.g_q[gp] = make_int2(__float2int_rn(yv * TPC_QSCALE), __float2int_rn(zv * TPC_QSCALE));
-      b.g_id[gp] = i;
-    }
-    __syncthreads();
-    // ---- S2c: one warp per row
-    for (int r = warp; r < NR; r += nwarps) warp_row_sort(b, s_rows[r], item * NR + r, b.flags, lane);
-    __syncthreads();
-    // ---- S3: neighbours
-    const int p_end = s_rows[NR - 1].pos0 + s_rows[NR - 1].n;
-    for (int pos = a0 + threadIdx.x; pos < p_end; pos += blockDim.x) {
-      const int4 qh = b.s_hit[pos];
-      const int r = qh.w - item * NR;
-      if (r == 0 || r == NR - 1) {
-        b.up_raw[pos] = -1;
-        b.dn_raw[pos] = -1;
-        continue;
-      }
-      link_hit<BT, LINK_MAXC, false>(b, GlobalSrc{b.s_hit, b.first}, s_rows, 0, pos, qh, r, s_cu, s_cd, threadIdx.x);
-    }
-    for (int pos = p_end + threadIdx.x; pos < a1; pos += blockDim.x) {  // rejected clusters: no links
-      b.up_raw[pos] = -1;
-      b.dn_raw[pos] = -1;
-    }
-    __syncthreads();
-    // ---- S4+S5: mutual links, start hits, compaction in canonical order
-    for (int pos = a0 + threadIdx.x; pos < a1; pos += blockDim.x) {
-      const int u = b.up_raw[pos], d = b.dn_raw[pos];
-      const int cu = (u >= 0 && b.dn_raw[u] == pos) ? u : -1;
-      const int cd = (d >= 0 && b.up_raw[d] == pos) ? d : -1;
-      b.up[pos] = cu;
-      b.dn[pos] = cd;
-      int start = 0;
-      if (cu >= 0 && cd < 0) {
-        const int u2 = b.up_raw[cu];
-        start = (u2 >= 0 && b.dn_raw[u2] == cu) ? 1 : 0;
-      }
-      b.flags[pos] = start;
-    }
-    __syncthreads();
-    {
-      const int ntl = cta_scan(a1 - a0, [&](int i) { return b.flags[a0 + i]; },
-                               [&](int i, int ex) {
-                                 if (b.flags[a0 + i]) b.starts[tlb + ex] = a0 + i;
-                               },
-                               sm);
-      if (threadIdx.x == 0) s_ntl = ntl;
-    }
-    __syncthreads();
-    const int ntl = s_ntl;
-    // ---- S6: tracklets, a group of G lanes each: outward passes, then one
-    // inward refit per outermost hit
-    const GSrc<false> S{&b, s_rows};
-    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) {
-      const int start = b.starts[tlb + t];
-      tracklet_up<G>(b, g, S, s_x, start, b.s_hit[start], tlb + t, t);
-    }
-    __syncthreads();
-    for (int t = threadIdx.x / G; t < ntl; t += blockDim.x / G) tracklet_down<G>(b, g, S, s_x, tlb + t);
-    __syncthreads();
-    // ---- S7: ownership
-    for (int t = warp; t < ntl; t += nwarps) select_max_warp(b, tlb + t, lane);
-    __syncthreads();
-    for (int t = warp; t < ntl; t += nwarps) {
-      const unsigned long long o = select_own_warp(b, tlb + t, lane);
-      if (lane == 0) b.tl_cnt[tlb + t] = o;
-    }
-    __syncthreads();
-    // item-local output offsets: tracks in the high word, cluster ids in the low word
-    if (warp == 0) {
-      unsigned long long carry = 0;
-      for (int base = 0; base < ntl; base += 32) {
-        const int t = base + lane;
-        const unsigned long long v = t < ntl ? b.tl_cnt[tlb + t] : 0ull;
-        const unsigned long long inc = warp_incl_scan64(v);
-        if (t < ntl) b.tl_ex[tlb + t] = carry + inc - v;
-        carry += __shfl_sync(0xffffffffu, inc, 31);
-      }
-      if (lane == 0) {
-        b.item_cnt[item] = carry;
-        b.item_ntl[item] = ntl;
-      }
-    }
-    __syncthreads();
-    // ---- S8: the item's tracks and cluster ids
-    tpc_track_t* trk_tmp = reinterpret_cast<tpc_track_t*>(b.trk_tmp);
-    for (int t = warp; t < ntl; t += nwarps) {
-      const unsigned long long cnt = b.tl_cnt[tlb + t];
-      if (cnt == 0) continue;
-      const unsigned long long ex = b.tl_ex[tlb + t];
-      const unsigned ti = (unsigned)(ex >> 32), io = (unsigned)(ex & 0xFFFFFFFFull);
-      emit_warp(b, tlb + t, cnt, io, trk_tmp + tlb + ti, b.ids_tmp + a0 + io, lane);
-      if (lane == 0) b.trk_tl_tmp[tlb + ti] = tlb + t;
-    }
-    __syncthreads();
+  const int T = b.start_ex[b.N];
+  const int NR = b.par.n_rows;
+  const int grp = (blockIdx.x * blockDim.x + threadIdx.x) / G;
+  const int ngrp = (gridDim.x * blockDim.x) / G;
+  for (int i = grp; i < T; i += ngrp) {
+    const int t = __ldg(b.tl_order + i);
+    const int start = __ldg(b.starts + t);
+    const int4 hs = __ldg(b.s_hit + start);
+    const int item = hs.w / NR;
+    const GSrc<true> S{&b, b.rows + (size_t)item * NR};
+    tracklet_up<G, true>(b, g, S, s_x, start, hs, t, t - b.start_ex[b.item_off[item]]);
   }
 }
 
-// exclusive scan of the items' packed (tracks, ids) counts and tracklet counts
-__global__ void __launch_bounds__(1024) k_items_scan(const __grid_constant__ Buffers b) {
-  __shared__ unsigned long long sm64[33];
-  unsigned long long carry = 0, tl_carry = 0;
-  for (int base = 0; base < b.I; base += blockDim.x) {
-    const int i = base + threadIdx.x;
-    const unsigned long long v = i < b.I ? b.item_cnt[i] : 0ull;
-    const unsigned long long w = i < b.I ? (unsigned long long)b.item_ntl[i] : 0ull;
-    unsigned long long tot, tot2;
-    const unsigned long long ex = block_excl_scan64(v, sm64, &tot);
-    const unsigned long long ex2 = block_excl_scan64(w, sm64, &tot2);
-    if (i < b.I) {
-      b.item_ex[i] = carry + ex;
-      b.item_tl_ex[i] = (int)(tl_carry + ex2);
-    }
-    carry += tot;
-    tl_carry += tot2;
-  }
-  if (threadIdx.x == 0) {
-    b.counts[0] = carry >> 32;
-    b.counts[1] = carry & 0xFFFFFFFFull;
-    b.counts[2] = tl_carry;
-  }
-}
-
-// concatenation of the items' outputs (one CTA per item)
-__global__ void __launch_bounds__(256) k_items_copy(const __grid_constant__ Buffers b) {
-  const int item = blockIdx.x;
-  const unsigned long long cnt = b.item_cnt[item], ex = b.item_ex[item];
-  const unsigned nt = (unsigned)(cnt >> 32), ni = (unsigned)(cnt & 0xFFFFFFFFull);
-  const unsigned t0 = (unsigned)(ex >> 32), i0 = (unsigned)(ex & 0xFFFFFFFFull);
-  const int a0 = (int)b.item_off[item];
-  const int tlb = a0 / 3 + item;
-  const tpc_track_t* src = reinterpret_cast<const tpc_track_t*>(b.trk_tmp) + tlb;
-  tpc_track_t* dst = reinterpret_cast<tpc_track_t*>(b.trk) + t0;
-  for (unsigned k = threadIdx.x; k < nt; k += blockDim.x) {
-    tpc_track_t o = src[k];
-    o.first_cluster += i0;
-    dst[k] = o;
-    b.trk_tl[t0 + k] = b.item_tl_ex[item] + (b.trk_tl_tmp[tlb + k] - tlb);
-  }
-  for (unsigned k = threadIdx.x; k < ni; k += blockDim.x) b.trk_ids[i0 + k] = b.ids_tmp[a0 + k];
-}
-
-cudaError_t tpc_launch_batched(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev) {
-  auto mark = [&](int i) {
-    if (ev) cudaEventRecord(ev[i], s);
-  };
-  mark(9);
-  cudaMemsetAsync(b.queue_head, 0, sizeof(int), s);
-  // persistent grid: every resident CTA slot of the GPU
+cudaError_t tpc_launch_tracklets_queued(const Buffers& b, const LaunchCfg& c, cudaStream_t s) {
+  cudaMemsetAsync(b.out_owner, 0x7F, sizeof(int) * (size_t)b.N, s);
+  k_chain_walk<<<c.num_sms * 8, 256, 0, s>>>(b);
+  k_queue_items<<<b.I, 256, 0, s>>>(b);
+  const int grid = c.grid_tl, block = c.block_tl;
   switch (c.batch_group) {
-    case 1: k_batched<1><<<std::max(1, c.batch_per_sm[0]) * c.num_sms, BT, 0, s>>>(b); break;
-    case 2: k_batched<2><<<std::max(1, c.batch_per_sm[1]) * c.num_sms, BT, 0, s>>>(b); break;
-    default: k_batched<4><<<std::max(1, c.batch_per_sm[2]) * c.num_sms, BT, 0, s>>>(b); break;
+#define TPC_TLQ(GG)                                       \
+  case GG:                                                \
+    k_tracklets_up_q<GG><<<grid, block, 0, s>>>(b);       \
+    k_tracklets_down<GG><<<grid, block, 0, s>>>(b);       \
+    break;
+    TPC_TLQ(1)
+    TPC_TLQ(2)
+    default:
+      k_tracklets_up_q<4><<<grid, block, 0, s>>>(b);
+      k_tracklets_down<4><<<grid, block, 0, s>>>(b);
+      break;
+#undef TPC_TLQ
   }
-  mark(10);
-  k_items_scan<<<1, 1024, 0, s>>>(b);
-  k_items_copy<<<b.I, 256, 0, s>>>(b);
-  mark(11);
   return cudaGetLastError();
 }
+
 
 // ============================================================================ S11
 // Space-point correction by a per-sector grid (location-dependent calibration,
@@ -1973,13 +1788,6 @@ cudaError_t tpc_launch_grid_correction(const Buffers& b, cudaStream_t s) {
   return cudaGetLastError();
 }
 // ============================================================================ host launchers
-cudaError_t tpc_batched_occupancy(int per_sm[3]) {
-  cudaError_t e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[0], k_batched<1>, BT, 0);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[1], k_batched<2>, BT, 0);
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm[2], k_batched<4>, BT, 0);
-  return e;
-}
-
 cudaError_t tpc_configure_kernels(int sort_smem, int link_smem) {
   (void)link_smem;
   cudaError_t e = cudaFuncSetAttribute(k_row_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, sort_smem);
@@ -2005,7 +1813,8 @@ static void scan_u64_dev(const unsigned long long* in, unsigned long long* out, 
 
 // Plain mode: one launch per step over all items.  ev (nullable) receives
 // TPC_N_STAGES+1 events around the steps.
-cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev) {
+namespace {
+cudaError_t launch_stages(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev, bool queued) {
   const int NR = c.n_rows;
   const int M = b.I * NR;
   auto mark = [&](int i) {
@@ -2051,7 +1860,10 @@ cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t 
   scan_i32(b.flags, b.start_ex, b.N, b.scan_tmp, c.grid_scan, s);
   k_starts<<<gN > 0 ? gN : 1, 256, 0, s>>>(b);
   mark(6);
-  tpc_launch_tracklets(b, c, s);
+  if (queued)
+    tpc_launch_tracklets_queued(b, c, s);
+  else
+    tpc_launch_tracklets(b, c, s);
   mark(7);
   // a warp per tracklet: enough blocks for every resident warp slot
   k_select_max<<<c.num_sms * 8, 256, 0, s>>>(b);
@@ -2062,4 +1874,13 @@ cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t 
   k_counts<<<1, 1, 0, s>>>(b);
   mark(9);
   return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t tpc_launch_plain(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev) {
+  return launch_stages(b, c, s, ev, false);
+}
+
+cudaError_t tpc_launch_batched(const Buffers& b, const LaunchCfg& c, cudaStream_t s, cudaEvent_t* ev) {
+  return launch_stages(b, c, s, ev, true);
 }

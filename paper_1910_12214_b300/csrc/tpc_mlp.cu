@@ -36,7 +36,6 @@ constexpr int OW1 = 0, OB1 = 192, OW2 = 256, OB2 = 4352, OW3 = 4416, OB3 = 4608,
 constexpr int NPP = 4616;     // padded parameter stride per sector
 constexpr int TB = 128;       // samples per training CTA
 constexpr float OUT_SCALE = 10.0f;
-constexpr int WS = 516;       // per-warp slots: 192 gW3, 3 gb3, 64 gb2, 192 gW1, 64 gb1, loss
 
 __device__ __forceinline__ uint64_t sm64(uint64_t x) {
   uint64_t z = x + 0x9E3779B97F4A7C15ull;
@@ -51,7 +50,10 @@ __device__ __forceinline__ float counter_uniform(uint64_t seed, uint64_t a, uint
 }
 
 __device__ __forceinline__ float bf(float v) { return __bfloat162float(__float2bfloat16_rn(v)); }
-__device__ __forceinline__ float silu(float z) { return z / (1.0f + expf(-z)); }
+// logistic function with the hardware exponential and reciprocal (a few ulp;
+// training only: its gradients are compared with the FP64 oracle at 2e-2)
+__device__ __forceinline__ float sigm(float z) { return __fdividef(1.0f, 1.0f + __expf(-z)); }
+__device__ __forceinline__ float silu(float z) { return z * sigm(z); }
 
 // SiLU of the deployed network (inference and its residual evaluation):
 // z * sigmoid(z) = h + h tanh(h) with h = z / 2 and the hardware tanh (relative
@@ -69,7 +71,7 @@ __device__ __forceinline__ float silu_fast(float z) {
   return fmaf(hz, tanh_hw(hz), hz);
 }
 __device__ __forceinline__ float dsilu(float z) {
-  const float s = 1.0f / (1.0f + expf(-z));
+  const float s = sigm(z);
   return s * (1.0f + z * (1.0f - s));
 }
 
@@ -103,7 +105,36 @@ __device__ __forceinline__ float2 grid_at(const float2* G, int nx, int ny, int n
 }  // namespace
 
 // ---------------------------------------------------------------------------- training
+// Training clock on the device: the step and its Adam scalars, advanced by
+// k_mlp_tick after every step, so that a CUDA graph of K steps replays the
+// next K steps without arguments from the host.
+struct MlpClock {
+  unsigned long long step, T;
+  float lr;                 // base learning rate
+  float lr_t, c1, c2;       // cosine-decayed rate and the bias corrections 1 - b^(t+1) of this step
+};
+
+__device__ __forceinline__ void clock_scalars(MlpClock* c) {
+  const double t = (double)c->step;
+  c->lr_t = (float)(c->lr * 0.5 * (1.0 + cos(M_PI * t / (double)c->T)));
+  c->c1 = (float)(1.0 - pow(0.9, t + 1.0));
+  c->c2 = (float)(1.0 - pow(0.999, t + 1.0));
+}
+
+__global__ void k_mlp_clock_set(MlpClock* c, unsigned long long step, unsigned long long T, float lr) {
+  c->step = step;
+  c->T = T;
+  c->lr = lr;
+  clock_scalars(c);
+}
+
+__global__ void k_mlp_tick(MlpClock* c) {
+  c->step += 1;
+  clock_scalars(c);
+}
+
 struct MlpTrain {
+  const MlpClock* clock;  // the step comes from here when set, else from `step`
   const float* master;  // [S][NPP]
   float* partial;       // [S][nblk][NPP]
   float* loss;          // [S][nblk]
@@ -113,143 +144,356 @@ struct MlpTrain {
   int batch;            // samples per sector and step (multiple of TB)
 };
 
+__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+// four 8x8 BF16 matrices from shared memory; lanes 8j..8j+7 give the row
+// addresses of matrix j.  Plain: lane l receives row l/4, columns 2(l%4) and
+// 2(l%4)+1 of each; transposed: rows 2(l%4), 2(l%4)+1 at column l/4.
+__device__ __forceinline__ void ldmatrix_x4(uint32_t* r, const void* smem_row) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem_row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+__device__ __forceinline__ void ldmatrix_x4_t(uint32_t* r, const void* smem_row) {
+  const unsigned a = (unsigned)__cvta_generic_to_shared(smem_row);
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
+               : "r"(a));
+}
+
+// D += A B, m16n8k16, BF16 operands, FP32 accumulators.  Fragments (lane =
+// 4 g + q): A rows g and g+8 at columns 2q, 2q+1 and +8; B column g at rows
+// 2q, 2q+1 and +8; D rows g and g+8 at columns 2q, 2q+1.
+__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+      "{%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
+}
+
+constexpr int TS = 72;  // padded row stride (BF16 elements) of the training tiles: conflict-free ldmatrix
+
+// Shared memory of one training CTA.  The sample tiles are [sample][column]:
+// A1x and A2x hold the hidden activations with a column of ones at 64 (the
+// bias gradients come out of the same products), GZ1 and GZ2 the gradients
+// of the pre-activations, INx the inputs with a one at 3, GOx the output
+// gradients (columns 0..2).
+struct __align__(16) TrainSmem {
+  __nv_bfloat16 w2[H * TS];   // W2 [out j][in i]: B of the forward layer 2
+  __nv_bfloat16 w2t[H * TS];  // W2^T [in i][out j]: B of the backward layer 2
+  __nv_bfloat16 a1x[TB * TS], a2x[TB * TS], gz1[TB * TS], gz2[TB * TS];
+  __nv_bfloat16 inx[TB * 8], gox[TB * 16];
+  float w1[192], b1[64], b2[64], w3[192], b3[4];
+  float loss[TB / 32];
+};
+
+// One CTA per TB = 128 samples of a sector (four warps of 32 samples, two
+// 16-sample tiles each).  Forward and backward of a tile run on the tensor
+// cores with the fragments kept in registers (each layer's accumulators,
+// after SiLU and BF16 rounding, become the next product's A fragments):
+//   z1 = W1 in + b1 (K padded 3 -> 16), a1 = bf(silu(z1));
+//   z2 = W2 a1 + b2, a2 = bf(silu(z2)); o = W3 a2 + b3 (N padded 3 -> 8);
+//   go = 2 (o - target) / batch; ga2 = W3^T go (three FMAs per element);
+//   gz2 = ga2 silu'(z2); ga1 = W2^T gz2 (tensor cores); gz1 = ga1 silu'(z1).
+// The sums over the CTA's samples are products over the staged tiles:
+//   [gW2 | gb2] = gz2^T [a1 | 1], [gW1 | gb1] = gz1^T [in | 1],
+//   [gW3 | gb3] = go^T [a2 | 1]  (BF16 operands, FP32 accumulation),
+// written to the CTA's partial in a fixed layout (deterministic training).
 __global__ void __launch_bounds__(TB) k_mlp_grad(const __grid_constant__ MlpTrain a) {
-  extern __shared__ float smem[];
-  float* W = smem;                 // rounded weights and FP32 biases [NPP]
-  float* A1 = W + NPP;             // [H][TB] first hidden activations (BF16 values)
-  float* Z2 = A1 + H * TB;         // [H][TB] second pre-activations, then their gradients
-  float* WP = Z2 + H * TB;         // [4 warps][WS] per-warp gradient sums
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
   const int s = blockIdx.y, blk = blockIdx.x, t = threadIdx.x;
-  const int lane = t & 31, warp = t >> 5;
+  const int lane = t & 31, warp = t >> 5, g = lane >> 2, q = lane & 3;
   const float* M = a.master + (size_t)s * NPP;
-  for (int p = t; p < NP; p += TB) {
-    const bool bias = (p >= OB1 && p < OW2) || (p >= OB2 && p < OW3) || p >= OB3;
-    W[p] = bias ? M[p] : bf(M[p]);
+  for (int p = t; p < H * TS; p += TB) {
+    const int r = p / TS, c = p % TS;
+    S.w2[p] = __float2bfloat16_rn(c < H ? M[OW2 + H * r + c] : 0.0f);
+    S.w2t[p] = __float2bfloat16_rn(c < H ? M[OW2 + H * c + r] : 0.0f);
+  }
+  for (int p = t; p < 192; p += TB) {
+    S.w1[p] = bf(M[OW1 + p]);
+    S.w3[p] = bf(M[OW3 + p]);
+  }
+  for (int p = t; p < 64; p += TB) {
+    S.b1[p] = M[OB1 + p];
+    S.b2[p] = M[OB2 + p];
+  }
+  if (t < 3) S.b3[t] = M[OB3 + t];
+  // the columns beyond the data: ones at 64 (bias column), zeros after
+  for (int r = t; r < TB; r += TB) {
+    for (int c = H; c < TS; ++c) {
+      S.a1x[r * TS + c] = __float2bfloat16_rn(c == H ? 1.0f : 0.0f);
+      S.a2x[r * TS + c] = __float2bfloat16_rn(c == H ? 1.0f : 0.0f);
+      S.gz1[r * TS + c] = __float2bfloat16_rn(0.0f);
+      S.gz2[r * TS + c] = __float2bfloat16_rn(0.0f);
+    }
   }
   __syncthreads();
-  // sample and target
-  const uint64_t k = (uint64_t)blk * TB + t;
-  float in[3], u[3];
+  // per-lane B fragments of layers 1 and 3 (constant over the CTA)
+  uint32_t B1[8];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    u[c] = counter_uniform(a.seed, (uint64_t)s, a.step, 3ull * k + c);
-    in[c] = bf(2.0f * u[c] - 1.0f);
+  for (int nt = 0; nt < 8; ++nt) {
+    const int n = 8 * nt + g;
+    B1[nt] = q == 0 ? pack_bf2(S.w1[3 * n], S.w1[3 * n + 1]) : q == 1 ? pack_bf2(S.w1[3 * n + 2], 0.0f) : 0u;
+  }
+  uint32_t B3[4][2];
+#pragma unroll
+  for (int ks = 0; ks < 4; ++ks) {
+    const int k0 = 16 * ks + 2 * q;
+    B3[ks][0] = g < 3 ? pack_bf2(S.w3[64 * g + k0], S.w3[64 * g + k0 + 1]) : 0u;
+    B3[ks][1] = g < 3 ? pack_bf2(S.w3[64 * g + k0 + 8], S.w3[64 * g + k0 + 9]) : 0u;
   }
   const float2* G = a.grid + (size_t)s * a.nx * a.ny * a.nz;
-  const float2 tg = grid_at(G, a.nx, a.ny, a.nz, u[0] * (a.nx - 1), u[1] * (a.ny - 1), u[2] * (a.nz - 1));
-  const float tgt[3] = {0.0f, tg.x / OUT_SCALE, tg.y / OUT_SCALE};
-  // forward
-  for (int j = 0; j < H; ++j) {
-    const float z1 = W[OB1 + j] + W[OW1 + 3 * j] * in[0] + W[OW1 + 3 * j + 1] * in[1] + W[OW1 + 3 * j + 2] * in[2];
-    A1[j * TB + t] = bf(silu(z1));
-  }
-  float o[3] = {W[OB3], W[OB3 + 1], W[OB3 + 2]};
-  for (int j = 0; j < H; ++j) {
-    float z2 = W[OB2 + j];
-    const float* w2 = W + OW2 + H * j;
-    for (int i = 0; i < H; ++i) z2 += w2[i] * A1[i * TB + t];
-    Z2[j * TB + t] = z2;
-    const float a2 = bf(silu(z2));
+  const float inv_batch = 2.0f / (float)a.batch;
+  const uint64_t step = a.clock ? a.clock->step : a.step;
+  float lsum = 0.f;
+  for (int mt = 0; mt < 2; ++mt) {
+    const int r0 = 32 * warp + 16 * mt;  // first sample (CTA row) of the tile
+    // inputs and targets of rows g and g + 8
+    float in[2][3], tgt[2][2];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) o[c] += W[OW3 + H * c + j] * a2;
-  }
-  float go[3], l = 0.f;
+    for (int h = 0; h < 2; ++h) {
+      const uint64_t k = (uint64_t)blk * TB + r0 + g + 8 * h;
+      float u[3];
 #pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const float r = o[c] - tgt[c];
-    l += r * r;
-    go[c] = 2.0f * r / (float)a.batch;
-  }
-  // backward through layer 3: per-warp sums of the 3-wide gradients
-  auto wsum = [&](float v) {
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) v += __shfl_xor_sync(0xffffffffu, v, off);
-    return v;
-  };
-  float* wp = WP + warp * WS;  // 192 gW3 | 3 gb3 | 64 gb2 | 192 gW1 | 64 gb1 | loss
-#pragma unroll
-  for (int c = 0; c < 3; ++c) {
-    const float v = wsum(go[c]);
-    if (lane == 0) wp[192 + c] = v;
-  }
-  {
-    const float lv = wsum(l);
-    if (lane == 0) wp[515] = lv;
-  }
-  for (int j = 0; j < H; ++j) {
-    const float z2 = Z2[j * TB + t];
-    const float a2 = bf(silu(z2));
-    float ga2 = 0.f;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      ga2 += W[OW3 + H * c + j] * go[c];
-      const float v = wsum(go[c] * a2);
-      if (lane == 0) wp[H * c + j] = v;
+      for (int c = 0; c < 3; ++c) {
+        u[c] = counter_uniform(a.seed, (uint64_t)s, step, 3ull * k + c);
+        in[h][c] = bf(2.0f * u[c] - 1.0f);
+      }
+      const float2 tg = grid_at(G, a.nx, a.ny, a.nz, u[0] * (a.nx - 1), u[1] * (a.ny - 1), u[2] * (a.nz - 1));
+      tgt[h][0] = tg.x / OUT_SCALE;
+      tgt[h][1] = tg.y / OUT_SCALE;
+      if (q == 0) {  // [in | 1] row
+        uint32_t* row = reinterpret_cast<uint32_t*>(S.inx + (r0 + g + 8 * h) * 8);
+        row[0] = pack_bf2(in[h][0], in[h][1]);
+        row[1] = pack_bf2(in[h][2], 1.0f);
+        row[2] = 0u;
+        row[3] = 0u;
+      }
     }
-    const float gz2 = ga2 * dsilu(z2);
-    Z2[j * TB + t] = gz2;
-    const float v = wsum(gz2);
-    if (lane == 0) wp[195 + j] = v;
+    // layer 1 (K padded 3 -> 16): z1 accumulators, a1 fragments
+    uint32_t A1in[4];
+    A1in[0] = q == 0 ? pack_bf2(in[0][0], in[0][1]) : q == 1 ? pack_bf2(in[0][2], 0.0f) : 0u;
+    A1in[1] = q == 0 ? pack_bf2(in[1][0], in[1][1]) : q == 1 ? pack_bf2(in[1][2], 0.0f) : 0u;
+    A1in[2] = 0u;
+    A1in[3] = 0u;
+    float z1[8][4];
+    uint32_t A[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const float2 bb = *reinterpret_cast<const float2*>(S.b1 + 8 * nt + 2 * q);
+      z1[nt][0] = bb.x;
+      z1[nt][1] = bb.y;
+      z1[nt][2] = bb.x;
+      z1[nt][3] = bb.y;
+      mma_bf16(z1[nt], A1in, B1[nt], 0u);
+      const float a0 = bf(silu(z1[nt][0])), a1 = bf(silu(z1[nt][1]));
+      const float a2 = bf(silu(z1[nt][2])), a3 = bf(silu(z1[nt][3]));
+      const int ks = nt >> 1, half = nt & 1;
+      A[ks][2 * half] = pack_bf2(a0, a1);
+      A[ks][2 * half + 1] = pack_bf2(a2, a3);
+      *reinterpret_cast<uint32_t*>(S.a1x + (r0 + g) * TS + 8 * nt + 2 * q) = A[ks][2 * half];
+      *reinterpret_cast<uint32_t*>(S.a1x + (r0 + g + 8) * TS + 8 * nt + 2 * q) = A[ks][2 * half + 1];
+    }
+    // layer 2: z2 accumulators, a2 fragments
+    float z2[8][4];
+    uint32_t A3[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      const float2 bb = *reinterpret_cast<const float2*>(S.b2 + 8 * nt + 2 * q);
+      z2[nt][0] = bb.x;
+      z2[nt][1] = bb.y;
+      z2[nt][2] = bb.x;
+      z2[nt][3] = bb.y;
+#pragma unroll
+      for (int ks = 0; ks < 4; ks += 2) {
+        uint32_t b4[4];
+        const int j = lane >> 3;
+        ldmatrix_x4(b4, S.w2 + (8 * nt + (lane & 7)) * TS + 16 * (ks + (j >> 1)) + 8 * (j & 1));
+        mma_bf16(z2[nt], A[ks], b4[0], b4[1]);
+        mma_bf16(z2[nt], A[ks + 1], b4[2], b4[3]);
+      }
+      const float a0 = bf(silu(z2[nt][0])), a1 = bf(silu(z2[nt][1]));
+      const float a2 = bf(silu(z2[nt][2])), a3 = bf(silu(z2[nt][3]));
+      const int ks3 = nt >> 1, half = nt & 1;
+      A3[ks3][2 * half] = pack_bf2(a0, a1);
+      A3[ks3][2 * half + 1] = pack_bf2(a2, a3);
+      *reinterpret_cast<uint32_t*>(S.a2x + (r0 + g) * TS + 8 * nt + 2 * q) = A3[ks3][2 * half];
+      *reinterpret_cast<uint32_t*>(S.a2x + (r0 + g + 8) * TS + 8 * nt + 2 * q) = A3[ks3][2 * half + 1];
+    }
+    // layer 3 (N padded 3 -> 8): outputs at columns 0..2
+    float o[4] = {q == 0 ? S.b3[0] : q == 1 ? S.b3[2] : 0.f, q == 0 ? S.b3[1] : 0.f,
+                  q == 0 ? S.b3[0] : q == 1 ? S.b3[2] : 0.f, q == 0 ? S.b3[1] : 0.f};
+#pragma unroll
+    for (int ks = 0; ks < 4; ++ks) mma_bf16(o, A3[ks], B3[ks][0], B3[ks][1]);
+    // output gradients: lane q = 0 holds outputs 0, 1 (x, dy), lane q = 1 output 2 (dz)
+    float go[4] = {0.f, 0.f, 0.f, 0.f};
+    if (q == 0) {
+      const float r[4] = {o[0], o[1] - tgt[0][0], o[2], o[3] - tgt[1][0]};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        go[e] = inv_batch * r[e];
+        lsum += r[e] * r[e];
+      }
+    } else if (q == 1) {
+      const float r0v = o[0] - tgt[0][1], r1v = o[2] - tgt[1][1];
+      go[0] = inv_batch * r0v;
+      go[2] = inv_batch * r1v;
+      lsum += r0v * r0v + r1v * r1v;
+    }
+    {  // [go] rows: columns 0..2, zeros to 15
+      uint32_t* row_g = reinterpret_cast<uint32_t*>(S.gox + (r0 + g) * 16);
+      uint32_t* row_h = reinterpret_cast<uint32_t*>(S.gox + (r0 + g + 8) * 16);
+      row_g[q] = q < 2 ? pack_bf2(go[0], go[1]) : 0u;
+      row_h[q] = q < 2 ? pack_bf2(go[2], go[3]) : 0u;
+      row_g[4 + q] = 0u;
+      row_h[4 + q] = 0u;
+    }
+    // the three output gradients of rows g and g + 8 in every lane of the quad
+    const int base = lane & ~3;
+    const float g0a = __shfl_sync(0xffffffffu, go[0], base), g1a = __shfl_sync(0xffffffffu, go[1], base);
+    const float g2a = __shfl_sync(0xffffffffu, go[0], base + 1);
+    const float g0b = __shfl_sync(0xffffffffu, go[2], base), g1b = __shfl_sync(0xffffffffu, go[3], base);
+    const float g2b = __shfl_sync(0xffffffffu, go[2], base + 1);
+    // gz2 = (W3^T go) silu'(z2): fragments of the backward product, and the tile
+    uint32_t GZ[4][4];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float v[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = 8 * nt + 2 * q + (e & 1);
+        const float ga = e < 2 ? g0a * S.w3[j] + g1a * S.w3[64 + j] + g2a * S.w3[128 + j]
+                               : g0b * S.w3[j] + g1b * S.w3[64 + j] + g2b * S.w3[128 + j];
+        v[e] = ga * dsilu(z2[nt][e]);
+      }
+      const int ks = nt >> 1, half = nt & 1;
+      GZ[ks][2 * half] = pack_bf2(v[0], v[1]);
+      GZ[ks][2 * half + 1] = pack_bf2(v[2], v[3]);
+      *reinterpret_cast<uint32_t*>(S.gz2 + (r0 + g) * TS + 8 * nt + 2 * q) = GZ[ks][2 * half];
+      *reinterpret_cast<uint32_t*>(S.gz2 + (r0 + g + 8) * TS + 8 * nt + 2 * q) = GZ[ks][2 * half + 1];
+    }
+    // ga1 = W2^T gz2 on the tensor cores, gz1 = ga1 silu'(z1)
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) {
+      float d[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int ks = 0; ks < 4; ks += 2) {
+        uint32_t b4[4];
+        const int j = lane >> 3;
+        ldmatrix_x4(b4, S.w2t + (8 * nt + (lane & 7)) * TS + 16 * (ks + (j >> 1)) + 8 * (j & 1));
+        mma_bf16(d, GZ[ks], b4[0], b4[1]);
+        mma_bf16(d, GZ[ks + 1], b4[2], b4[3]);
+      }
+      const float v0 = d[0] * dsilu(z1[nt][0]), v1 = d[1] * dsilu(z1[nt][1]);
+      const float v2 = d[2] * dsilu(z1[nt][2]), v3 = d[3] * dsilu(z1[nt][3]);
+      *reinterpret_cast<uint32_t*>(S.gz1 + (r0 + g) * TS + 8 * nt + 2 * q) = pack_bf2(v0, v1);
+      *reinterpret_cast<uint32_t*>(S.gz1 + (r0 + g + 8) * TS + 8 * nt + 2 * q) = pack_bf2(v2, v3);
+    }
   }
+#pragma unroll
+  for (int off = 16; off > 0; off >>= 1) lsum += __shfl_xor_sync(0xffffffffu, lsum, off);
+  if (lane == 0) S.loss[warp] = lsum;
   __syncthreads();
   float* P = a.partial + ((size_t)s * gridDim.x + blk) * NPP;
-  // gW2[j][i] = sum over samples of gz2[j] a1[i]
-  for (int e = t; e < H * H; e += TB) {
-    const int j = e / H, i = e % H;
-    const float* gz = Z2 + j * TB;
-    const float* a1 = A1 + i * TB;
-    float acc = 0.f;
-    for (int b = 0; b < TB; ++b) acc += gz[b] * a1[b];
-    P[OW2 + e] = acc;
-  }
-  // layer 1
-  for (int i = 0; i < H; ++i) {
-    float ga1 = 0.f;
-    for (int j = 0; j < H; ++j) ga1 += W[OW2 + H * j + i] * Z2[j * TB + t];
-    const float z1 = W[OB1 + i] + W[OW1 + 3 * i] * in[0] + W[OW1 + 3 * i + 1] * in[1] + W[OW1 + 3 * i + 2] * in[2];
-    const float gz1 = ga1 * dsilu(z1);
+  // sums over the CTA's 128 samples (K = samples, 8 steps of 16).  A = a
+  // gradient tile transposed, B = an activation tile with its ones column;
+  // both through transposed ldmatrix (matrix j of an x4: rows 8 (j & 1) and
+  // columns 8 (j >> 1) of the 16 x 16 block for A; k rows 8 (j & 1), n tile
+  // j >> 1 for B).
+  const int mj = lane >> 3, mr = lane & 7;
+  {  // [gW2 | gb2]: warp w takes output units 16w .. 16w + 15, all 9 n-tiles
+    float acc[9][4];
 #pragma unroll
-    for (int c = 0; c < 3; ++c) {
-      const float v = wsum(gz1 * in[c]);
-      if (lane == 0) wp[259 + 3 * i + c] = v;
+    for (int nt = 0; nt < 9; ++nt) acc[nt][0] = acc[nt][1] = acc[nt][2] = acc[nt][3] = 0.f;
+    for (int kk = 0; kk < TB; kk += 16) {
+      uint32_t af[4];
+      // A[m = j][k = sample] from gz2[sample][j]: matrix j's rows are samples
+      ldmatrix_x4_t(af, S.gz2 + (kk + 8 * (mj >> 1) + mr) * TS + 16 * warp + 8 * (mj & 1));
+#pragma unroll
+      for (int nt = 0; nt < 9; nt += 2) {
+        uint32_t bfr[4];
+        const int ntb = nt + (mj >> 1) < 9 ? nt + (mj >> 1) : nt;  // the odd last tile reads tile 8 twice
+        ldmatrix_x4_t(bfr, S.a1x + (kk + 8 * (mj & 1) + mr) * TS + 8 * ntb);
+        mma_bf16(acc[nt], af, bfr[0], bfr[1]);
+        if (nt + 1 < 9) mma_bf16(acc[nt + 1], af, bfr[2], bfr[3]);
+      }
     }
-    const float v = wsum(gz1);
-    if (lane == 0) wp[451 + i] = v;
+#pragma unroll
+    for (int nt = 0; nt < 9; ++nt)
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int j = 16 * warp + g + 8 * (e >> 1), i = 8 * nt + 2 * q + (e & 1);
+        if (i < H) P[OW2 + H * j + i] = acc[nt][e];
+        else if (i == H) P[OB2 + j] = acc[nt][e];
+      }
   }
-  __syncthreads();
-  // fixed-order sum of the four warps
-  for (int q = t; q < WS; q += TB) {
-    const float v = ((WP[q] + WP[WS + q]) + WP[2 * WS + q]) + WP[3 * WS + q];
-    if (q < 192) P[OW3 + q] = v;
-    else if (q < 195) P[OB3 + q - 192] = v;
-    else if (q < 259) P[OB2 + q - 195] = v;
-    else if (q < 451) P[OW1 + q - 259] = v;
-    else if (q < 515) P[OB1 + q - 451] = v;
-    else a.loss[(size_t)s * gridDim.x + blk] = v;
+  {  // [gW1 | gb1]: warp w takes hidden units 16w .. 16w + 15; B = [in | 1] (one n tile)
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int kk = 0; kk < TB; kk += 16) {
+      uint32_t af[4], bfr[4];
+      ldmatrix_x4_t(af, S.gz1 + (kk + 8 * (mj >> 1) + mr) * TS + 16 * warp + 8 * (mj & 1));
+      // matrices 0, 1: k rows 0-7 and 8-15 of the [in | 1] tile (2, 3 repeat them)
+      ldmatrix_x4_t(bfr, S.inx + (kk + 8 * (mj & 1) + mr) * 8);
+      mma_bf16(acc, af, bfr[0], bfr[1]);
+    }
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      const int j = 16 * warp + g + 8 * (e >> 1), c = 2 * q + (e & 1);
+      if (c < 3) P[OW1 + 3 * j + c] = acc[e];
+      else if (c == 3) P[OB1 + j] = acc[e];
+    }
   }
+  {  // [gW3 | gb3]: A = go^T (rows 0..2 of 16), B = [a2 | 1]; warp w takes n tiles w, w + 4 (and 8)
+    for (int nt = warp; nt < 9; nt += 4) {
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      for (int kk = 0; kk < TB; kk += 16) {
+        uint32_t af[4], bfr[4];
+        ldmatrix_x4_t(af, S.gox + (kk + 8 * (mj >> 1) + mr) * 16 + 8 * (mj & 1));
+        ldmatrix_x4_t(bfr, S.a2x + (kk + 8 * (mj & 1) + mr) * TS + 8 * nt);
+        mma_bf16(acc, af, bfr[0], bfr[1]);
+      }
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const int c = g + 8 * (e >> 1), j = 8 * nt + 2 * q + (e & 1);
+        if (c < 3) {
+          if (j < H) P[OW3 + H * c + j] = acc[e];
+          else if (j == H) P[OB3 + c] = acc[e];
+        }
+      }
+    }
+  }
+  if (t == 0) a.loss[(size_t)s * gridDim.x + blk] = ((S.loss[0] + S.loss[1]) + S.loss[2]) + S.loss[3];
 }
 
 struct MlpAdam {
+  const MlpClock* clock;  // lr_t, c1, c2 of the step
   float* master;
   float* m;
   float* v;
   const float* partial;
   int nblk;
-  float lr_t, b1, b2, c1, c2, eps;  // c1 = 1 - b1^t, c2 = 1 - b2^t
+  float b1, b2, eps;
 };
 
+// one thread per parameter: the CTA partials summed in a fixed order, then
+// one Adam step on the FP32 master weights
 __global__ void __launch_bounds__(256) k_mlp_adam(const __grid_constant__ MlpAdam a) {
-  const int s = blockIdx.x;
-  for (int p = threadIdx.x; p < NP; p += blockDim.x) {
-    float g = 0.f;
-    for (int k = 0; k < a.nblk; ++k) g += a.partial[((size_t)s * a.nblk + k) * NPP + p];
-    const size_t q = (size_t)s * NPP + p;
-    const float m = a.b1 * a.m[q] + (1.0f - a.b1) * g;
-    const float v = a.b2 * a.v[q] + (1.0f - a.b2) * g * g;
-    a.m[q] = m;
-    a.v[q] = v;
-    a.master[q] -= a.lr_t * (m / a.c1) / (sqrtf(v / a.c2) + a.eps);
-  }
+  const int s = blockIdx.y, p = blockIdx.x * blockDim.x + threadIdx.x;
+  if (p >= NP) return;
+  float g = 0.f;
+  for (int k = 0; k < a.nblk; ++k) g += a.partial[((size_t)s * a.nblk + k) * NPP + p];
+  const size_t q = (size_t)s * NPP + p;
+  const float m = a.b1 * a.m[q] + (1.0f - a.b1) * g;
+  const float v = a.b2 * a.v[q] + (1.0f - a.b2) * g * g;
+  a.m[q] = m;
+  a.v[q] = v;
+  a.master[q] -= a.clock->lr_t * (m / a.clock->c1) / (sqrtf(v / a.clock->c2) + a.eps);
 }
 
 // Xavier-uniform initial weights (stream b = 0x5EED00000000, index = parameter)
@@ -356,28 +600,6 @@ __global__ void k_mlp_prepare(const float* master, const float* bounds, MlpInfer
   }
   if (threadIdx.x < 3) I.b3[threadIdx.x] = M[OB3 + threadIdx.x];
   if (threadIdx.x < 6) I.bounds[threadIdx.x] = bounds[6 * s + threadIdx.x];
-}
-
-__device__ __forceinline__ uint32_t pack_bf2(float lo, float hi) {
-  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
-  return *reinterpret_cast<uint32_t*>(&v);
-}
-
-// four 8x8 BF16 matrices from shared memory (rows given by lanes 8j..8j+7 for
-// matrix j); lane l receives row l/4, columns 2(l%4) and 2(l%4)+1 of each
-__device__ __forceinline__ void ldmatrix_x4(uint32_t* r, const void* smem_row) {
-  const unsigned a = (unsigned)__cvta_generic_to_shared(smem_row);
-  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
-               : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3])
-               : "r"(a));
-}
-
-__device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b0, uint32_t b1) {
-  asm volatile(
-      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-      "{%0,%1,%2,%3};\n"
-      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-      : "r"(a[0]), "r"(a[1]), "r"(a[2]), "r"(a[3]), "r"(b0), "r"(b1));
 }
 
 // One CTA per cluster chunk (one item): the sector's network in shared memory;
@@ -538,27 +760,54 @@ cudaError_t tpc_mlp_init(float* master, float* m, float* v, int S, uint64_t seed
   return cudaGetLastError();
 }
 
-cudaError_t tpc_mlp_step(float* master, float* m, float* v, float* partial, float* loss, const float2* grid, int nx,
-                         int ny, int nz, int S, int batch, uint64_t seed, uint64_t step, float lr_t, float c1, float c2,
-                         cudaStream_t s) {
-  const size_t smem = sizeof(float) * (NPP + 2 * H * TB + 4 * WS);
+size_t tpc_mlp_clock_bytes() { return sizeof(MlpClock); }
+
+cudaError_t tpc_mlp_train_steps(void* clock, uint64_t first, uint64_t T, float lr, uint64_t n_steps, float* master,
+                                float* m, float* v, float* partial, float* loss, const float2* grid, int nx, int ny,
+                                int nz, int S, int batch, uint64_t seed, bool graph, cudaStream_t s) {
   // an attribute of the current device: set per call (a process may train on several devices)
-  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)sizeof(TrainSmem));
   if (e != cudaSuccess) return e;
-  MlpTrain a{master, partial, loss, grid, nx, ny, nz, seed, step, batch};
+  MlpClock* ck = static_cast<MlpClock*>(clock);
+  k_mlp_clock_set<<<1, 1, 0, s>>>(ck, first, T, lr);
   const int nblk = batch / TB;
-  k_mlp_grad<<<dim3(nblk, S), TB, smem, s>>>(a);
-  MlpAdam ad{master, m, v, partial, nblk, lr_t, 0.9f, 0.999f, c1, c2, 1e-8f};
-  k_mlp_adam<<<S, 256, 0, s>>>(ad);
+  MlpTrain a{ck, master, partial, loss, grid, nx, ny, nz, seed, 0, batch};
+  MlpAdam ad{ck, master, m, v, partial, nblk, 0.9f, 0.999f, 1e-8f};
+  auto one = [&]() {
+    k_mlp_grad<<<dim3(nblk, S), TB, sizeof(TrainSmem), s>>>(a);
+    k_mlp_adam<<<dim3((NP + 255) / 256, S), 256, 0, s>>>(ad);
+    k_mlp_tick<<<1, 1, 0, s>>>(ck);
+  };
+  // K steps captured once and replayed: no host work between steps
+  constexpr uint64_t K = 64;
+  uint64_t done = 0;
+  if (graph && n_steps >= 2 * K) {  // (the legacy default stream cannot be captured)
+    cudaGraph_t g = nullptr;
+    cudaGraphExec_t ge = nullptr;
+    e = cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return e;
+    for (uint64_t k = 0; k < K; ++k) one();
+    cudaError_t le = cudaGetLastError();
+    e = cudaStreamEndCapture(s, &g);
+    if (e == cudaSuccess) e = le;
+    if (e == cudaSuccess) e = cudaGraphInstantiate(&ge, g, 0);
+    if (g) cudaGraphDestroy(g);
+    if (e != cudaSuccess) return e;
+    for (; done + K <= n_steps && e == cudaSuccess; done += K) e = cudaGraphLaunch(ge, s);
+    cudaGraphExecDestroy(ge);
+    if (e != cudaSuccess) return e;
+  }
+  for (; done < n_steps; ++done) one();
   return cudaGetLastError();
 }
 
 cudaError_t tpc_mlp_grad_only(const float* master, float* partial, float* loss, const float2* grid, int nx, int ny,
                               int nz, int S, int batch, uint64_t seed, uint64_t step, cudaStream_t s) {
-  const size_t smem = sizeof(float) * (NPP + 2 * H * TB + 4 * WS);
+  const size_t smem = sizeof(TrainSmem);
   cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  MlpTrain a{master, partial, loss, grid, nx, ny, nz, seed, step, batch};
+  MlpTrain a{nullptr, master, partial, loss, grid, nx, ny, nz, seed, step, batch};
   k_mlp_grad<<<dim3(batch / TB, S), TB, smem, s>>>(a);
   return cudaGetLastError();
 }

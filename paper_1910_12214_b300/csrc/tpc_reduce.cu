@@ -1934,6 +1934,287 @@ __global__ void k_mrg_legs_final(const __grid_constant__ MrgArgs a) {
 
 }  // namespace
 
+// ============================================================================ looper legs joined
+// The groups of the merger joined through every mutual leg pair into one
+// track each (Sec. 4: the legs of a looper, found separately, are merged into
+// one track), and each joined track refitted over the clusters of both legs:
+// the algebraic circle as for the groups, then z = z0 + tan(lambda) s with
+// s = R dtheta, the turning angle from the primary legs' innermost cluster in
+// the particle's sense of rotation (clockwise for q/pT > 0 of the primary leg
+// with the smallest index), taken in [-0.1, 2 pi - 0.1).  FP64 throughout:
+// loopers are few.
+namespace {
+constexpr int JN_MAXG = 16;    // groups of one joined track
+constexpr int JN_MAXM = 96;    // tracks of one joined track
+
+__device__ __forceinline__ bool jn_pair(const JoinArgs& a, int t, int* p) {
+  const int q = a.partner[t];
+  if (q < 0 || q >= a.n_trk) return false;
+  const int back = a.partner[q];
+  *p = q;
+  return back == t;
+}
+
+// the primary legs of mutual pairs (order of arrival: every use below is
+// order-independent); input values out of range are flagged and skipped
+__global__ void k_join_pairs(const __grid_constant__ JoinArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride) {
+    a.glab[t] = (int)t;
+    const int g = a.group[t], q = a.partner[t];
+    if (g < 0 || g >= a.n_trk || q < -1 || q >= a.n_trk || a.group[g] != g) {
+      atomicOr(a.err, TPC_DERR_BAD_TRACK);
+      continue;
+    }
+    int p;
+    if (jn_pair(a, (int)t, &p) && a.leg[t] == 0) a.plist[atomicAdd(a.n_pairs, 1)] = (int)t;
+  }
+}
+
+// one round of min-label propagation over the pairs (between group roots)
+__global__ void k_join_union(const __grid_constant__ JoinArgs a, int final_check) {
+  const int np = *a.n_pairs;
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < np; i += stride) {
+    const int t = a.plist[i];
+    const int ga = a.group[t], gb = a.group[a.partner[t]];
+    if (gb < 0 || gb >= a.n_trk) continue;
+    const int la = a.glab[ga], lb = a.glab[gb];
+    if (final_check) {
+      if (la != lb) atomicOr(a.err, TPC_DERR_BAD_TRACK);  // a chain of joins longer than the rounds
+      continue;
+    }
+    const int m = min(la, lb);
+    atomicMin(&a.glab[ga], m);
+    atomicMin(&a.glab[gb], m);
+  }
+}
+
+__global__ void k_join_label(const __grid_constant__ JoinArgs a) {
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < a.n_trk; t += stride) {
+    const int g = a.group[t];
+    a.joined[t] = (g >= 0 && g < a.n_trk) ? a.glab[g] : (int)t;
+    double* o = a.jfit + 7 * t;
+#pragma unroll
+    for (int k = 0; k < 7; ++k) o[k] = 0.0;
+  }
+}
+
+__device__ __forceinline__ double jn_wsum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// one warp per pair; the pair with the smallest primary index of its joined
+// track refits it
+__global__ void __launch_bounds__(128) k_join_fit(const __grid_constant__ JoinArgs a,
+                                                   const __grid_constant__ DevParams par) {
+  __shared__ int s_grp[4][JN_MAXG], s_prim[4][JN_MAXG], s_mem[4][JN_MAXM], s_off[4][JN_MAXM + 1];
+  const tpc_track_t* trk = static_cast<const tpc_track_t*>(a.trk);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int np = *a.n_pairs;
+  const long long nw = ((long long)gridDim.x * blockDim.x) >> 5;
+  for (long long i = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; i < np; i += nw) {
+    const int t = a.plist[i];
+    const int root = a.glab[a.group[t]];
+    // the representative: no pair of the same joined track with a smaller primary
+    bool rep = true;
+    for (int j = lane; j < np; j += 32) {
+      const int u = a.plist[j];
+      if (u < t && a.glab[a.group[u]] == root) rep = false;
+    }
+    if (!__all_sync(0xffffffffu, rep)) continue;
+    // groups of the joined track (primary groups flagged) and their members
+    int ng = 0, nm = 0;
+    bool ok = true;
+    if (lane == 0) {
+      auto add_group = [&](int g, int prim) {
+        if (g < 0 || g >= a.n_trk) {
+          ok = false;
+          return;
+        }
+        for (int k = 0; k < ng; ++k)
+          if (s_grp[w][k] == g) {
+            s_prim[w][k] |= prim;
+            return;
+          }
+        if (ng == JN_MAXG) {
+          ok = false;
+          return;
+        }
+        s_grp[w][ng] = g;
+        s_prim[w][ng] = prim;
+        ++ng;
+      };
+      for (int j = 0; j < np; ++j) {
+        const int u = a.plist[j];
+        if (a.glab[a.group[u]] != root) continue;
+        add_group(a.group[u], 1);
+        add_group(a.group[a.partner[u]], 0);
+      }
+      for (int k = 0; k < ng && ok; ++k) {  // members of group k: the root and its link paths
+        const int g = s_grp[w][k];
+        if (nm == JN_MAXM) {
+          ok = false;
+          break;
+        }
+        s_mem[w][nm++] = g;
+        for (int d = 0; d < 2 && ok; ++d) {
+          int cur = g;
+          for (int step = 0; step < 18; ++step) {
+            const int nxt = a.link[2 * cur + d];
+            if (nxt < 0 || nxt >= a.n_trk) break;
+            if (nm == JN_MAXM) {
+              ok = false;
+              break;
+            }
+            s_mem[w][nm++] = nxt;
+            cur = nxt;
+          }
+        }
+      }
+      for (int x = 1; x < nm; ++x)  // index order
+        for (int y = x; y > 0 && s_mem[w][y - 1] > s_mem[w][y]; --y) {
+          const int v = s_mem[w][y];
+          s_mem[w][y] = s_mem[w][y - 1];
+          s_mem[w][y - 1] = v;
+        }
+      s_off[w][0] = 0;
+      for (int m = 0; m < nm; ++m) s_off[w][m + 1] = s_off[w][m] + (int)trk[s_mem[w][m]].n_clusters;
+      if (!ok) atomicOr(a.err, TPC_DERR_BAD_TRACK);
+    }
+    ok = __shfl_sync(0xffffffffu, ok, 0);
+    nm = __shfl_sync(0xffffffffu, nm, 0);
+    ng = __shfl_sync(0xffffffffu, ng, 0);
+    __syncwarp();
+    if (!ok) continue;
+    const int m_all = s_off[w][nm];
+    // cluster k of the concatenation (members in index order, clusters in track order)
+    auto cluster = [&](int k, double* X, double* Y, double* Z, bool* prim) {
+      int m = 0;
+      while (s_off[w][m + 1] <= k) ++m;
+      const tpc_track_t& T = trk[s_mem[w][m]];
+      const long long pos = (long long)T.first_cluster + (k - s_off[w][m]);
+      const uint32_t c = pos < a.n_ids ? a.ids[pos] : 0xffffffffu;
+      const int r = c < (uint32_t)a.N ? a.row[c] : -1;
+      const bool good = T.item < (uint32_t)a.I && r >= 0 && r < par.n_rows;
+      const double ang = good ? (double)(a.item_sector[T.item] % 18u) * MRG_WEDGE : 0.0;
+      const double lx = good ? (double)par.x[r] : 0.0, ly = good ? (double)a.y[c] : 0.0;
+      *X = lx * cos(ang) - ly * sin(ang);
+      *Y = lx * sin(ang) + ly * cos(ang);
+      *Z = good ? (double)a.z[c] : 0.0;
+      if (!good) atomicOr(a.err, TPC_DERR_BAD_TRACK);
+      int g = s_mem[w][m];
+      g = a.group[g];
+      bool p = false;
+      for (int q = 0; q < ng; ++q) p |= s_grp[w][q] == g && s_prim[w][q];
+      *prim = p;
+    };
+    if (m_all < 3) continue;
+    double sx = 0, sy = 0;
+    for (int k = lane; k < m_all; k += 32) {
+      double X, Y, Z;
+      bool p;
+      cluster(k, &X, &Y, &Z, &p);
+      sx += X;
+      sy += Y;
+    }
+    const double mx = jn_wsum(sx) / m_all, my = jn_wsum(sy) / m_all;
+    double suu = 0, suv = 0, svv = 0, su3 = 0, sv3 = 0, sw = 0;
+    double rmin = 1e300;
+    int kref = m_all;
+    for (int k = lane; k < m_all; k += 32) {
+      double X, Y, Z;
+      bool p;
+      cluster(k, &X, &Y, &Z, &p);
+      const double u = X - mx, v = Y - my, q = u * u + v * v;
+      suu += u * u;
+      suv += u * v;
+      svv += v * v;
+      su3 += u * q;
+      sv3 += v * q;
+      sw += q;
+      const double rr = hypot(X, Y);
+      if (p && rr < rmin) {  // lanes visit k in increasing order: the first of equal radii stays
+        rmin = rr;
+        kref = k;
+      }
+    }
+    suu = jn_wsum(suu);
+    suv = jn_wsum(suv);
+    svv = jn_wsum(svv);
+    su3 = jn_wsum(su3);
+    sv3 = jn_wsum(sv3);
+    sw = jn_wsum(sw);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {  // innermost primary cluster: smallest radius, then smallest k
+      const double r2 = __shfl_xor_sync(0xffffffffu, rmin, o);
+      const int k2 = __shfl_xor_sync(0xffffffffu, kref, o);
+      if (r2 < rmin || (r2 == rmin && k2 < kref)) {
+        rmin = r2;
+        kref = k2;
+      }
+    }
+    const double det = suu * svv - suv * suv;
+    if (!(fabs(det) > 0) || kref >= m_all) continue;
+    const double D = (-su3 * svv + sv3 * suv) / det, E = (-sv3 * suu + su3 * suv) / det, F = -sw / m_all;
+    const double xc = mx - 0.5 * D, yc = my - 0.5 * E;
+    const double R = sqrt(0.25 * (D * D + E * E) - F);
+    double Xr, Yr, Zr;
+    bool pr;
+    cluster(kref, &Xr, &Yr, &Zr, &pr);
+    const double th0 = atan2(Yr - yc, Xr - xc);
+    const bool cw = trk[t].qpt > 0.0f;  // the smallest primary leg of the joined track
+    const double two_pi = 2.0 * 3.14159265358979323846;
+    double ss = 0, sz = 0, sss = 0, ssz = 0;
+    for (int k = lane; k < m_all; k += 32) {
+      double X, Y, Z;
+      bool p;
+      cluster(k, &X, &Y, &Z, &p);
+      const double th = atan2(Y - yc, X - xc);
+      double d = cw ? th0 - th : th - th0;
+      d -= two_pi * floor((d + 0.1) / two_pi);
+      const double sv = R * d;
+      ss += sv;
+      sz += Z;
+      sss += sv * sv;
+      ssz += sv * Z;
+    }
+    ss = jn_wsum(ss);
+    sz = jn_wsum(sz);
+    sss = jn_wsum(sss);
+    ssz = jn_wsum(ssz);
+    if (lane == 0) {
+      const double den = m_all * sss - ss * ss;
+      const double tgl = den > 0 ? (m_all * ssz - ss * sz) / den : 0.0;
+      double* o = a.jfit + 7 * (long long)root;
+      o[0] = xc;
+      o[1] = yc;
+      o[2] = R;
+      o[3] = tgl;
+      o[4] = (sz - tgl * ss) / m_all;
+      o[5] = (double)m_all;
+      o[6] = (double)nm;
+    }
+  }
+}
+}  // namespace
+
+cudaError_t launch_join(const JoinArgs& a, const DevParams& par, int num_sms, cudaStream_t s) {
+  const int g = num_sms * 8;
+  cudaMemsetAsync(a.n_pairs, 0, sizeof(int), s);
+  if (a.n_trk > 0) {
+    k_join_pairs<<<g, 256, 0, s>>>(a);
+    for (int r = 0; r < 4; ++r) k_join_union<<<g, 256, 0, s>>>(a, 0);
+    k_join_union<<<g, 256, 0, s>>>(a, 1);
+    k_join_label<<<g, 256, 0, s>>>(a);
+    k_join_fit<<<num_sms * 4, 128, 0, s>>>(a, par);
+  }
+  return cudaGetLastError();
+}
+
 cudaError_t launch_merge(const MrgArgs& a, const DevParams& par, int num_sms, cudaStream_t s) {
   const int g = num_sms * 8;
   k_mrg_item_first<<<(a.I + 256) / 256, 256, 0, s>>>(a);

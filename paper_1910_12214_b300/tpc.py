@@ -117,6 +117,8 @@ _sig = {
     "tpc_compress": ([_P, C.POINTER(tpc_cluster_charges), _P, C.c_uint64, _P, C.c_uint64, _P, C.c_int, _P,
                       C.c_uint64, C.POINTER(C.c_uint64)], C.c_int),
     "tpc_merge_tracks": ([_P, _P, C.c_uint64, _P, C.c_uint64, C.c_int, _P, _P, _P, _P, _P], C.c_int),
+    "tpc_join_loopers": ([_P, _P, C.c_uint64, _P, C.c_uint64, C.c_int, _P, _P, _P, _P, _P, _P,
+                          C.POINTER(C.c_uint64)], C.c_int),
     "tpc_destroy": ([_P], None),
     "tpc_last_error": ([_P], C.c_char_p),
 }
@@ -496,6 +498,29 @@ class Tracker:
         self._check(_lib.tpc_merge_tracks(self._h, _ptr(tracks), n, _ptr(ids), ni, int(bool(on_device)), nz(link),
                                           nz(group), nz(fit), nz(partner), nz(leg)))
         return (link, group, fit, partner, leg) if legs else (link, group, fit)
+
+    def join_loopers(self, link, group, partner, leg, tracks=None, ids=None, n_tracks=None):
+        """Looper legs joined into one track (include/tpc_reduce.h): (joined [n],
+        jfit [n, 7], number of joined tracks) from the merger's host outputs;
+        tracks=None uses the last tpc_track() output."""
+        if tracks is None:
+            n = self.counts()[0] if n_tracks is None else int(n_tracks)
+        else:
+            tracks = np.ascontiguousarray(tracks, TRACK_DTYPE)
+            ids = np.ascontiguousarray(ids, np.uint32)
+            n = int(tracks.shape[0])
+        link = np.ascontiguousarray(link, np.int32)
+        group = np.ascontiguousarray(group, np.int32)
+        partner = np.ascontiguousarray(partner, np.int32)
+        leg = np.ascontiguousarray(leg, np.uint8)
+        joined = np.zeros(n, np.int32)
+        jfit = np.zeros((n, 7), np.float64)
+        k = C.c_uint64()
+        ni = int(ids.shape[0]) if ids is not None else 0
+        nz = lambda a: _ptr(a) if n else None
+        self._check(_lib.tpc_join_loopers(self._h, _ptr(tracks), n, _ptr(ids), ni, 0, nz(link), nz(group),
+                                          nz(partner), nz(leg), nz(joined), nz(jfit), C.byref(k)))
+        return joined, jfit, int(k.value)
 
     def close(self):
         if getattr(self, "_h", None):

@@ -231,3 +231,57 @@ def test_sorted_lists_and_item_scans_agree():
         for a, b in zip(outs[0], other):
             assert np.array_equal(a, b, equal_nan=True)
     assert (outs[0][0] >= 0).sum() > 10000
+
+
+def test_joined_loopers_equal_the_oracle_on_oracle_merger_outputs():
+    """The joining step on its own: given the oracle merger's links, groups and
+    leg pairs of the oracle tracker's tracks, the GPU joins the same groups
+    (labels exact) and its FP64 refit of every joined looper equals the
+    oracle's (centre, radius, tan(lambda), z0 within 1e-9 relative, counts
+    exact)."""
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_event(41, 6000, second_leg=True)
+    ref = oracle.run(cl, what=["trk_f", "trk_i", "trk_ids"])
+    tf, ti, ids = oracle.merge_tracks(ref)
+    link, group, amb, fit, partner, leg = oracle.merge(cl, tf, ti, ids, legs=True)
+    wj, wf, wk = oracle.join_loopers(cl, tf, ti, ids, group, partner, leg)
+    with tracked(cl) as t:
+        joined, jfit, k = t.join_loopers(link, group, partner, leg, tracks=to_records(tf, ti), ids=ids)
+    assert k == wk and wk > 500
+    assert np.array_equal(joined, wj)
+    roots = np.flatnonzero(wf[:, 5] > 0)
+    assert np.array_equal(np.flatnonzero(jfit[:, 5] > 0), roots)
+    assert np.array_equal(jfit[roots, 5:], wf[roots, 5:])
+    scale = np.maximum(np.abs(wf[roots, :5]), np.array([1.0, 1.0, 1.0, 1e-3, 1.0]))
+    assert np.max(np.abs(jfit[roots, :5] - wf[roots, :5]) / scale) < 1e-9
+
+
+def test_joined_loopers_of_own_tracks_recover_the_particles():
+    """The product path: the GPU's own tracks, merged with looper legs and
+    joined: the joined tracks are the two legs of one particle (>= 95%) and
+    their refitted radius and tan(lambda) are the particle's (median error
+    below 1% and 0.01)."""
+    from paper_1910_12214_b300 import synth
+    cl = synth.make_event(41, 6000, second_leg=True)
+    with tracked(cl) as t:
+        trk, ids = t.get_tracks()
+        n = trk.shape[0]
+        link, group, fit, partner, leg = t.merge_tracks(None, None, n, legs=True)
+        joined, jfit, k = t.join_loopers(link, group, partner, leg, n_tracks=n)
+    assert k > 500
+    kb = 0.299792458e-2 * 0.5
+    roots = np.flatnonzero(jfit[:, 5] > 0)
+    pure, dR, dT = 0, [], []
+    for r in roots:
+        members = np.flatnonzero(joined == r)
+        cs = np.concatenate([ids[trk["first_cluster"][u]:trk["first_cluster"][u] + trk["n_clusters"][u]]
+                             for u in members])
+        mc = cl.mc[cs]
+        lab = np.bincount(mc[mc >= 0]).argmax()
+        if (mc == lab).mean() >= 0.9 and (cl.leg[cs[mc == lab]] == 1).any() and (cl.leg[cs[mc == lab]] == 0).any():
+            pure += 1
+            R = cl.tracks["pt"][lab] / kb
+            dR.append(abs(jfit[r, 2] - R) / R)
+            dT.append(abs(jfit[r, 3] - cl.tracks["tgl"][lab]))
+    assert pure >= 0.95 * roots.size, (pure, roots.size)
+    assert np.median(dR) < 0.01 and np.median(dT) < 0.01, (np.median(dR), np.median(dT))
