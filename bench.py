@@ -588,7 +588,7 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
                 ms = float(np.median(time_steps(t, stream, steps, flush)))
                 trk, ids = t.get_tracks()
                 out[mode] = {"clusters_per_s": n_clusters / (ms * 1e-3), "ms": ms, "tracks": t.counts()[0],
-                             "tuning": tun}
+                             "tuning": tun, "stage_us": {k: round(v, 2) for k, v in stage_profile(t, stream).items()}}
                 if first is None:
                     first = (trk, ids)
                 else:  # every mode must give the first mode's tracks byte for byte
