@@ -709,8 +709,9 @@ def bench_frame(fr, dev, stream, flush, tpc, torch, steps=5):
 def bench_removal_chain(cl, props, dev, stream, tpc, torch):
     """The paper's data-reduction chain (Sec. 4) on one central event whose
     low-pT helices also leave their returning legs: tracking, merger with
-    looper legs, masks with the legs, compression without removal and with
-    strategies A and B (the form of Fig. 6 on synthetic data)."""
+    looper legs, the legs joined into one refitted track, masks with the legs,
+    compression without removal and with strategies A and B (the form of
+    Fig. 6 on synthetic data)."""
     with torch.cuda.stream(stream):
         d = to_device(cl, dev)
         ch = {k: torch.from_numpy(np.ascontiguousarray(props[k])).to(dev)
@@ -725,6 +726,7 @@ def bench_removal_chain(cl, props, dev, stream, tpc, torch):
             t.track()
             n_trk = t.counts()[0]
             link, group, fit, partner, leg = t.merge_tracks(n_tracks=n_trk, legs=True, on_device=True)
+            joined, jfit, n_joined = t.join_loopers(link, group, partner, leg, n_tracks=n_trk, on_device=True)
             m, _ = t.cluster_masks(on_device=True, with_owner=False, leg=leg, n_tracks=n_trk)
             sizes = {}
             for name, bit in (("none", 0), ("A", 4), ("B", 8)):
@@ -732,6 +734,12 @@ def bench_removal_chain(cl, props, dev, stream, tpc, torch):
                 sizes[name] = int(t.compress(ch, on_device=True, keep=keep).shape[0])
             torch.cuda.synchronize()
             wall = time.perf_counter() - w0
+        jw = []  # the join on its own (the call waits for its end)
+        for _ in range(5):
+            torch.cuda.synchronize()
+            w0 = time.perf_counter()
+            t.join_loopers(link, group, partner, leg, n_tracks=n_trk, on_device=True)
+            jw.append(time.perf_counter() - w0)
     mh = m.cpu().numpy()
     partner = partner.cpu().numpy()
     sec = cl.leg == 1
@@ -752,7 +760,8 @@ def bench_removal_chain(cl, props, dev, stream, tpc, torch):
     noise = cl.mc < 0
     res["by_pt"] = by_pt
     res["noise_clusters"] = {"clusters": int(noise.sum()), "removed_by_b": float(((mh[noise] & 8) != 0).mean())}
-    res.update(tracks=n_trk, leg_pairs=int((partner >= 0).sum() // 2), chain_wall_ms=1e3 * wall,
+    res.update(tracks=n_trk, leg_pairs=int((partner >= 0).sum() // 2), joined_loopers=n_joined,
+               join_ms=1e3 * float(np.median(jw)), chain_wall_ms=1e3 * wall,
                removed_by_a=float(((mh & 4) != 0).mean()), removed_by_b=float(((mh & 8) != 0).mean()),
                returning_leg_removed_by_a=float(((mh & 4) != 0)[sec].mean()),
                bytes_per_cluster={k: v / cl.n for k, v in sizes.items()},

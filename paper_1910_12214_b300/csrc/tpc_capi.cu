@@ -241,6 +241,7 @@ tpc_status reserve(tpc_ctx* c, long long N, long long I, long long n_chunks) {
   b.scan_tmp = (unsigned long long*)A(8 * 1040);
   b.chain_len = (int*)A(4 * Tcap);
   b.tl_order = (int*)A(4 * Tcap);
+  b.seg_next = (int*)A(4 * TPC_MAX_SEGS);
   b.cy = (float*)A(4 * N);
   b.cz = (float*)A(4 * N);
   b.T_cap = (int)Tcap;

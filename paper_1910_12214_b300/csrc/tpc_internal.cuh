@@ -40,6 +40,8 @@ struct TrackletRec {
 
 // Result of the outward passes (i)+(ii) of a tracklet, input of the inward
 // refit (iii).
+constexpr int TPC_MAX_SEGS = 1024;  // segments of the batched inward pass (one per SM)
+
 struct TrackletUp {
   int out_hit;   // outermost hit (sorted position), -1 = dropped
   int out_row;
@@ -114,9 +116,12 @@ struct Buffers {
   unsigned long long* counts;  // [0] n_trk, [1] n_ids, [2] n_tracklets
   unsigned int* err;
   unsigned long long* scan_tmp;  // block sums
-  // batched form: tracklets from a work queue ordered by chain length
+  // batched form: tracklets from work queues
   int* chain_len;                 // hits of every start hit's chain [T_cap]
-  int* tl_order;                  // tracklet indices, shortest chains first [T_cap]
+  int* tl_order;                  // tracklet indices in processing order: shortest chains first
+                                  // (outward pass), then highest outermost row first per segment
+                                  // (inward pass) [T_cap]
+  int* seg_next;                  // inward pass: next unclaimed position of every segment [TPC_MAX_SEGS]
   // space-point correction (applied before binning when enabled)
   const float2* grid;             // per-sector (dy, dz) nodes [S][nx][ny][nz]
   const float* grid_bounds;       // [S][6]: x0, x1, v0, v1, z0, z1 (v = y / (x tan_half))

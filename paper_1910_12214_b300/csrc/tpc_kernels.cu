@@ -1356,101 +1356,136 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
   g.sync();
 }
 
-// Inward refit (iii) of tracklet tl by a group of G lanes, only if it is the
-// smallest tracklet that reached its outermost hit (the others are dropped):
-// the record goes to b.tl[tl] and the hit list to b.tl_hits[tl * n_rows ...].
-// `rows` is the row table of the tracklet's item, or null for the global one.
+// Inward refit (iii): the state of one refit and its three steps, shared by the
+// per-tracklet loop below and the refilling kernel of the batched form.
+struct DownFit {
+  float q5[5], C[15];        // running state and covariance
+  float x, chi2sum, in_x;    // current x; chi2 sum; x of the innermost hit
+  float in_p[5], in_C[15];   // state at the innermost hit so far
+  int n, in_z, misses;
+  bool dead;
+};
+
+// Start of the refit of tracklet tl, only if it is the smallest tracklet that
+// reached its outermost hit (the others are dropped): that hit's y, z and the
+// outward direction and curvature with variances inflated 100-fold (capped at
+// the initial ones).
 template <int G, class Src>
-__device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g, const Src& S, const float* xr,
-                                              int tl) {
+__device__ __forceinline__ void down_begin(const Buffers& b, const Grp<G>& g, const Src& S, const float* xr, int tl,
+                                           const TrackletUp& u, int* hl, DownFit& f) {
   const DevParams& P = b.par;
-  const int NR = P.n_rows;
   const float Q = 1.0f / TPC_QSCALE;
-  const TrackletUp u = b.tlu[tl];
-  const int item = u.item, local = u.local, z_base = u.z_base;
-  const int out_hit = u.out_hit, out_row = u.out_row;
   // claims of other threads of the previous launch: read from L2
-  bool dead = out_hit < 0 || __ldcg(b.out_owner + out_hit) != tl;
-  int* hl = b.tl_hits + (size_t)tl * NR;
-  const float out_p[5] = {0.f, 0.f, u.snp, u.tgl, u.qpt};
-  const float ov2 = u.v2, ov3 = u.v3, ov4 = u.v4;
-  float C[15];
-  float x = xr[out_row];
-  int n = 0;
-  float chi2sum = 0.f, in_x = x;
-  float in_p[5] = {0.f, 0.f, 0.f, 0.f, 0.f}, in_C[15];
+  f.dead = u.out_hit < 0 || __ldcg(b.out_owner + u.out_hit) != tl;
+  f.x = xr[u.out_row];
+  f.n = 0;
+  f.chi2sum = 0.f;
+  f.in_x = f.x;
+  f.in_z = 0;
+  f.misses = 0;
 #pragma unroll
-  for (int m = 0; m < 15; ++m) in_C[m] = 0.f;
-  int in_z = 0;
-  if (!dead) {
-    // (iii) inward refit from the outermost hit: its y, z; the outward direction
-    // and curvature with variances inflated 100-fold (capped at the initial ones)
-    const int4 qo = S.hit(out_row, out_hit);
-    float q5[5] = {qo.x * Q, (float)(qo.y - z_base) * Q, out_p[2], out_p[3], out_p[4]};
-    set_c0(P, C);
-    C[ix(2, 2)] = fminf(1.0f, INFLATE * ov2);
-    C[ix(3, 3)] = fminf(1.0f, INFLATE * ov3);
-    C[ix(4, 4)] = fminf(100.0f, INFLATE * ov4);
+  for (int m = 0; m < 5; ++m) f.in_p[m] = 0.f;
+#pragma unroll
+  for (int m = 0; m < 15; ++m) f.in_C[m] = 0.f;
+  if (!f.dead) {
+    const int4 qo = S.hit(u.out_row, u.out_hit);
+    f.q5[0] = qo.x * Q;
+    f.q5[1] = (float)(qo.y - u.z_base) * Q;
+    f.q5[2] = u.snp;
+    f.q5[3] = u.tgl;
+    f.q5[4] = u.qpt;
+    set_c0(P, f.C);
+    f.C[ix(2, 2)] = fminf(1.0f, INFLATE * u.v2);
+    f.C[ix(3, 3)] = fminf(1.0f, INFLATE * u.v3);
+    f.C[ix(4, 4)] = fminf(100.0f, INFLATE * u.v4);
     g.sync();
-    if (g.gl == 0) hl[0] = out_hit;
-    n = 1;
-    in_z = qo.y;
+    if (g.gl == 0) hl[0] = u.out_hit;
+    f.n = 1;
+    f.in_z = qo.y;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) in_p[m] = q5[m];
+    for (int m = 0; m < 5; ++m) f.in_p[m] = f.q5[m];
 #pragma unroll
-    for (int m = 0; m < 15; ++m) in_C[m] = C[m];
-    int misses = 0;
-    for (int r = out_row - 1; r >= 0 && misses < MAX_MISS; --r) {
-      const RowInfo ri = S.row(r);  // independent of the state: in flight during the step
-      const float xn = xr[r];
-      if (!kf_propagate(P, q5, C, x, xn)) break;
-      x = xn;
-      if (!(fabsf(q5[2]) < SIN_MAX) || fabsf(q5[0]) > x * P.tan_half) break;
-      int4 q;
-      const Win w = make_win(P, C);
-      const int h = pick_hit<G>(S, g, r, ri, q5, w, z_base, &q);
-      if (h < 0) {
-        ++misses;
-        continue;
-      }
-      const float e0 = q.x * Q - q5[0], e1 = (float)(q.y - z_base) * Q - q5[1];
-      chi2sum += n <= JOSEPH_UPDATES ? kf_update_joseph(w, P.vy, P.vz, q5, C, e0, e1) : kf_update(w, q5, C, e0, e1);
-      if (!cov_ok(C)) {
-        dead = true;
-        break;
-      }
-      misses = 0;
-      if (g.gl == 0) hl[n] = h;
-      ++n;
-      in_z = q.y;
-      in_x = x;
-#pragma unroll
-      for (int m = 0; m < 5; ++m) in_p[m] = q5[m];
-#pragma unroll
-      for (int m = 0; m < 15; ++m) in_C[m] = C[m];
-    }
+    for (int m = 0; m < 15; ++m) f.in_C[m] = f.C[m];
   }
-  if (dead || n < MIN_HITS) n = 0;
-  // the 112-byte record, fields split over the lanes of the group
+}
+
+// Row r of the refit: propagate, pick the best hit, update.  false ends the
+// pass (f.dead set if the covariance failed); a row without a hit counts a miss.
+template <int G, class Src>
+__device__ __forceinline__ bool down_row(const DevParams& P, const Grp<G>& g, const Src& S, const float* xr, int r,
+                                         int z_base, int* hl, DownFit& f) {
+  const float Q = 1.0f / TPC_QSCALE;
+  const RowInfo ri = S.row(r);  // independent of the state: in flight during the step
+  const float xn = xr[r];
+  if (!kf_propagate(P, f.q5, f.C, f.x, xn)) return false;
+  f.x = xn;
+  if (!(fabsf(f.q5[2]) < SIN_MAX) || fabsf(f.q5[0]) > f.x * P.tan_half) return false;
+  int4 q;
+  const Win w = make_win(P, f.C);
+  const int h = pick_hit<G>(S, g, r, ri, f.q5, w, z_base, &q);
+  if (h < 0) {
+    ++f.misses;
+    return true;
+  }
+  const float e0 = q.x * Q - f.q5[0], e1 = (float)(q.y - z_base) * Q - f.q5[1];
+  f.chi2sum += f.n <= JOSEPH_UPDATES ? kf_update_joseph(w, P.vy, P.vz, f.q5, f.C, e0, e1)
+                                     : kf_update(w, f.q5, f.C, e0, e1);
+  if (!cov_ok(f.C)) {
+    f.dead = true;
+    return false;
+  }
+  f.misses = 0;
+  if (g.gl == 0) hl[f.n] = h;
+  ++f.n;
+  f.in_z = q.y;
+  f.in_x = f.x;
+#pragma unroll
+  for (int m = 0; m < 5; ++m) f.in_p[m] = f.q5[m];
+#pragma unroll
+  for (int m = 0; m < 15; ++m) f.in_C[m] = f.C[m];
+  return true;
+}
+
+// End of the refit: the 112-byte record of tracklet tl (n = 0 if dropped or
+// short), fields split over the lanes of the group.
+template <int G>
+__device__ __forceinline__ void down_end(const Buffers& b, const Grp<G>& g, int tl, int item, int local, int z_base,
+                                         DownFit& f) {
+  if (f.dead || f.n < MIN_HITS) f.n = 0;
   float* rf = reinterpret_cast<float*>(b.tl + tl);
   int* ri_ = reinterpret_cast<int*>(b.tl + tl);
-  const int z_in = n ? in_z : 0;
+  const int z_in = f.n ? f.in_z : 0;
   for (int fld = g.gl; fld < 27; fld += G) {
     float fv = 0.f;
 #pragma unroll
-    for (int m = 0; m < 5; ++m) fv = (fld == m) ? in_p[m] : fv;
+    for (int m = 0; m < 5; ++m) fv = (fld == m) ? f.in_p[m] : fv;
 #pragma unroll
-    for (int m = 0; m < 15; ++m) fv = (fld == 5 + m) ? in_C[m] : fv;
+    for (int m = 0; m < 15; ++m) fv = (fld == 5 + m) ? f.in_C[m] : fv;
     if (fld < 20) rf[fld] = fv;
-    else if (fld == 20) rf[20] = chi2sum;
-    else if (fld == 21) rf[21] = in_x;
-    else if (fld == 22) ri_[22] = n;
+    else if (fld == 20) rf[20] = f.chi2sum;
+    else if (fld == 21) rf[21] = f.in_x;
+    else if (fld == 22) ri_[22] = f.n;
     else if (fld == 23) ri_[23] = z_base;
     else if (fld == 24) ri_[24] = z_in;
     else if (fld == 25) ri_[25] = item;
     else ri_[26] = local;
   }
   g.sync();
+}
+
+// Inward refit (iii) of tracklet tl by a group of G lanes: the record goes to
+// b.tl[tl] and the hit list to b.tl_hits[tl * n_rows ...].
+template <int G, class Src>
+__device__ __forceinline__ void tracklet_down(const Buffers& b, const Grp<G>& g, const Src& S, const float* xr,
+                                              int tl) {
+  const TrackletUp u = b.tlu[tl];
+  int* hl = b.tl_hits + (size_t)tl * b.par.n_rows;
+  DownFit f;
+  down_begin<G>(b, g, S, xr, tl, u, hl, f);
+  if (!f.dead)
+    for (int r = u.out_row - 1; r >= 0 && f.misses < MAX_MISS; --r)
+      if (!down_row<G>(b.par, g, S, xr, r, u.z_base, hl, f)) break;
+  down_end<G>(b, g, tl, u.item, u.local, u.z_base, f);
 }
 
 template <int G>
@@ -1700,6 +1735,125 @@ __global__ void __launch_bounds__(128) k_tracklets_up_q(const __grid_constant__ 
   }
 }
 
+// Inward refits of the batched form.  In a batch the inward pass is bound by
+// how long the lanes of a warp wait for its slowest one: with a tracklet per
+// lane a warp runs as long as its longest refit, and refits run from a few to
+// 150 rows.  Here the tracklets are cut into one contiguous segment per CTA
+// (one CTA per SM, DN_WARPS warps), and a lane takes the next tracklet as soon
+// as it finishes one, so a warp stays full until the work runs out.  A warp
+// takes from its own CTA's segment (its items' rows, bins and hits stay in the
+// SM's L1) and, once that is empty, from the following segments (the segments'
+// work differs by up to 1.5x across a batch of uneven events).  k_down_order
+// sorts every segment by outermost row, highest first (the refit runs from
+// there towards row 0, so that row bounds its length): the long refits start
+// first and a segment ends on short ones; dropped tracklets go last.  The order
+// changes no result: every tracklet writes its own record.
+constexpr int DN_WARPS = 16;
+
+__device__ __forceinline__ int down_key(const Buffers& b, int t, int NR) {
+  const TrackletUp u = b.tlu[t];
+  const bool dropped = u.out_hit < 0 || __ldcg(b.out_owner + u.out_hit) != t;
+  return dropped ? NR : NR - 1 - u.out_row;
+}
+
+// segment c of T tracklets cut into n: [i0, i0 + len)
+__device__ __forceinline__ void down_segment(int T, int n, int c, int* i0, int* len) {
+  const int seg = (T + n - 1) / n;
+  const int a = min(T, c * seg);
+  *i0 = a;
+  *len = min(T, a + seg) - a;
+}
+
+__global__ void __launch_bounds__(256) k_down_order(const __grid_constant__ Buffers b) {
+  __shared__ int s_cnt[TPC_MAX_ROWS + 2];
+  __shared__ int sm[33];
+  const int T = b.start_ex[b.N];
+  int i0, len;
+  down_segment(T, gridDim.x, blockIdx.x, &i0, &len);
+  const int i1 = i0 + len;
+  const int NR = b.par.n_rows, nb = NR + 1;
+  if (threadIdx.x == 0) b.seg_next[blockIdx.x] = 0;
+  for (int k = threadIdx.x; k < nb; k += blockDim.x) s_cnt[k] = 0;
+  __syncthreads();
+  for (int t = i0 + threadIdx.x; t < i1; t += blockDim.x) atomicAdd(&s_cnt[down_key(b, t, NR)], 1);
+  __syncthreads();
+  int carry = 0;
+  for (int base = 0; base < nb; base += blockDim.x) {  // block-uniform loop
+    const int k = base + threadIdx.x;
+    const int v = k < nb ? s_cnt[k] : 0;
+    int tot;
+    const int ex = block_excl_scan(v, sm, &tot);
+    if (k < nb) s_cnt[k] = carry + ex;
+    carry += tot;
+  }
+  __syncthreads();
+  for (int t = i0 + threadIdx.x; t < i1; t += blockDim.x)
+    b.tl_order[i0 + atomicAdd(&s_cnt[down_key(b, t, NR)], 1)] = t;
+}
+
+__global__ void __launch_bounds__(32 * DN_WARPS, 1) k_tracklets_down_p(const __grid_constant__ Buffers b) {
+  __shared__ float s_x[TPC_MAX_ROWS];
+  for (int r = threadIdx.x; r < b.par.n_rows; r += blockDim.x) s_x[r] = b.par.x[r];
+  __syncthreads();
+  const Grp<1> g;
+  const int NR = b.par.n_rows;
+  const int T = b.start_ex[b.N];
+  const int nseg = gridDim.x;
+  const int lane = threadIdx.x & 31;
+  const unsigned lt = (1u << lane) - 1u;
+  int cs = blockIdx.x, tried = 0;  // segment taken from, segments found empty (lane 0's)
+  int tl = -1, r = 0, item = 0, local = 0, z_base = 0;
+  DownFit f;
+  while (true) {
+    // lanes without a tracklet take the next ones: warp-uniform, lane 0 claims
+    // them with one atomic on the segment's counter
+    const unsigned need = __ballot_sync(0xffffffffu, tl < 0);
+    if (need) {
+      int base = -1, i0 = 0, len = 0;
+      if (lane == 0) {
+        while (tried < nseg) {
+          down_segment(T, nseg, cs, &i0, &len);
+          if (__ldcg(b.seg_next + cs) < len) {
+            base = atomicAdd(b.seg_next + cs, __popc(need));
+            if (base < len) break;
+          }
+          cs = cs + 1 == nseg ? 0 : cs + 1;
+          ++tried;
+          base = -1;
+        }
+      }
+      base = __shfl_sync(0xffffffffu, base, 0);
+      i0 = __shfl_sync(0xffffffffu, i0, 0);
+      len = __shfl_sync(0xffffffffu, len, 0);
+      const int k = base + __popc(need & lt);
+      if (tl < 0 && base >= 0 && k < len) {
+        tl = b.tl_order[i0 + k];
+        const TrackletUp u = b.tlu[tl];
+        item = u.item;
+        local = u.local;
+        z_base = u.z_base;
+        r = u.out_row - 1;
+        const GSrc<true> S{&b, b.rows + (size_t)item * NR};
+        down_begin<1>(b, g, S, s_x, tl, u, b.tl_hits + (size_t)tl * NR, f);
+      }
+    }
+    if (!__any_sync(0xffffffffu, tl >= 0)) break;
+    if (tl >= 0) {
+      bool more = !f.dead && r >= 0 && f.misses < MAX_MISS;
+      if (more) {
+        const GSrc<true> S{&b, b.rows + (size_t)item * NR};
+        more = down_row<1>(b.par, g, S, s_x, r, z_base, b.tl_hits + (size_t)tl * NR, f);
+        --r;
+        more = more && r >= 0 && f.misses < MAX_MISS;
+      }
+      if (!more) {
+        down_end<1>(b, g, tl, item, local, z_base, f);
+        tl = -1;
+      }
+    }
+  }
+}
+
 cudaError_t tpc_launch_tracklets_queued(const Buffers& b, const LaunchCfg& c, cudaStream_t s) {
   cudaMemsetAsync(b.out_owner, 0x7F, sizeof(int) * (size_t)b.N, s);
   k_chain_walk<<<c.num_sms * 8, 256, 0, s>>>(b);
@@ -1711,7 +1865,11 @@ cudaError_t tpc_launch_tracklets_queued(const Buffers& b, const LaunchCfg& c, cu
     k_tracklets_up_q<GG><<<grid, block, 0, s>>>(b);       \
     k_tracklets_down<GG><<<grid, block, 0, s>>>(b);       \
     break;
-    TPC_TLQ(1)
+    case 1:
+      k_tracklets_up_q<1><<<grid, block, 0, s>>>(b);
+      k_down_order<<<std::min(c.num_sms, TPC_MAX_SEGS), 256, 0, s>>>(b);
+      k_tracklets_down_p<<<std::min(c.num_sms, TPC_MAX_SEGS), 32 * DN_WARPS, 0, s>>>(b);
+      break;
     TPC_TLQ(2)
     default:
       k_tracklets_up_q<4><<<grid, block, 0, s>>>(b);

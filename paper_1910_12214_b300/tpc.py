@@ -499,27 +499,38 @@ class Tracker:
                                           nz(group), nz(fit), nz(partner), nz(leg)))
         return (link, group, fit, partner, leg) if legs else (link, group, fit)
 
-    def join_loopers(self, link, group, partner, leg, tracks=None, ids=None, n_tracks=None):
+    def join_loopers(self, link, group, partner, leg, tracks=None, ids=None, n_tracks=None, on_device=False):
         """Looper legs joined into one track (include/tpc_reduce.h): (joined [n],
-        jfit [n, 7], number of joined tracks) from the merger's host outputs;
-        tracks=None uses the last tpc_track() output."""
+        jfit [n, 7], number of joined tracks) from the merger's outputs, as
+        numpy arrays, or CUDA tensors with on_device (then link, group,
+        partner, leg are the merger's CUDA tensors); tracks=None uses the last
+        tpc_track() output."""
         if tracks is None:
             n = self.counts()[0] if n_tracks is None else int(n_tracks)
+        elif on_device:
+            n = int(tracks.shape[0])
         else:
             tracks = np.ascontiguousarray(tracks, TRACK_DTYPE)
             ids = np.ascontiguousarray(ids, np.uint32)
             n = int(tracks.shape[0])
-        link = np.ascontiguousarray(link, np.int32)
-        group = np.ascontiguousarray(group, np.int32)
-        partner = np.ascontiguousarray(partner, np.int32)
-        leg = np.ascontiguousarray(leg, np.uint8)
-        joined = np.zeros(n, np.int32)
-        jfit = np.zeros((n, 7), np.float64)
+        if on_device:
+            import torch
+            dev = torch.device("cuda", self.cfg.device)
+            m = max(n, 1)
+            joined = torch.empty(m, dtype=torch.int32, device=dev)[:n]
+            jfit = torch.empty((m, 7), dtype=torch.float64, device=dev)[:n]
+        else:
+            link = np.ascontiguousarray(link, np.int32)
+            group = np.ascontiguousarray(group, np.int32)
+            partner = np.ascontiguousarray(partner, np.int32)
+            leg = np.ascontiguousarray(leg, np.uint8)
+            joined = np.zeros(n, np.int32)
+            jfit = np.zeros((n, 7), np.float64)
         k = C.c_uint64()
         ni = int(ids.shape[0]) if ids is not None else 0
         nz = lambda a: _ptr(a) if n else None
-        self._check(_lib.tpc_join_loopers(self._h, _ptr(tracks), n, _ptr(ids), ni, 0, nz(link), nz(group),
-                                          nz(partner), nz(leg), nz(joined), nz(jfit), C.byref(k)))
+        self._check(_lib.tpc_join_loopers(self._h, _ptr(tracks), n, _ptr(ids), ni, int(bool(on_device)), nz(link),
+                                          nz(group), nz(partner), nz(leg), nz(joined), nz(jfit), C.byref(k)))
         return joined, jfit, int(k.value)
 
     def close(self):

@@ -268,7 +268,11 @@ def test_joined_loopers_of_own_tracks_recover_the_particles():
         n = trk.shape[0]
         link, group, fit, partner, leg = t.merge_tracks(None, None, n, legs=True)
         joined, jfit, k = t.join_loopers(link, group, partner, leg, n_tracks=n)
+        dl, dg, _, dp, dleg = t.merge_tracks(None, None, n, legs=True, on_device=True)
+        dj, df, dk = t.join_loopers(dl, dg, dp, dleg, n_tracks=n, on_device=True)
     assert k > 500
+    # device buffers give the host call's outputs (members are summed in index order)
+    assert dk == k and np.array_equal(dj.cpu().numpy(), joined) and np.array_equal(df.cpu().numpy(), jfit)
     kb = 0.299792458e-2 * 0.5
     roots = np.flatnonzero(jfit[:, 5] > 0)
     pure, dR, dT = 0, [], []
