@@ -1233,16 +1233,23 @@ __device__ __forceinline__ int pick_hit(const Src& S, const Grp<G>& g, int r, co
 // step.  A non-finite or non-positive covariance diagonal drops the tracklet.
 // z is carried relative to the start hit (z_base) so that FP32 keeps its
 // precision for time-frame z' of thousands of cm.
-//
-// Outward passes (i) and (ii) of the tracklet with start hit `start`: one loop
-// over the rows above the start row, taking the chain hit while the chain lasts
-// and searching afterwards (so that lanes of a warp in different phases run the
-// same propagation and update code together).  The result goes to b.tlu[tl] and
-// the tracklet claims its outermost hit (smallest tracklet index wins); `local`
-// is the item-local id, `rows` the item's row table, `xr` the row positions.
+
+// State of the outward passes of one tracklet.
+struct UpFit {
+  float p[5], C[15], x;
+  float out_p[5], ov2, ov3, ov4;  // state and variances at the outermost hit
+  int out_row, out_hit;
+  int hn, hn2;                    // the next chain hit and the one after it
+  int4 qn;                        // coordinates of the next chain hit
+  int misses, n_upd, L, r0, z_base;
+  bool dead;
+};
+
+// (i) start: the chain (walked here, or by an earlier kernel with PRE) and the
+// initial state from the circle through its first, middle and last hits.
 template <int G, bool PRE, class Src>
-__device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, const Src& S, const float* xr,
-                                            int start, int4 hs, int tl, int local) {
+__device__ __forceinline__ void up_begin(const Buffers& b, const Grp<G>& g, const Src& S, const float* xr, int start,
+                                         int4 hs, int tl, UpFit& f) {
   const DevParams& P = b.par;
   const int NR = P.n_rows;
   const float Q = 1.0f / TPC_QSCALE;
@@ -1280,80 +1287,124 @@ __device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, c
   const float u = fminf(1.0f, fmaxf(-1.0f, 0.5f * kappa * d13));
   const float phi1 = atan2f(dy13, dx13) + asinf(u);
   const float arc = d13 * asin_over_u(u);
-  float p[5] = {y1, 0.0f, sinf(phi1), z3 / arc, kappa / P.kB};
-  float C[15];
-  set_c0(P, C);
-  float x = x1;
-  int out_row = r0, out_hit = start;
-  float out_p[5] = {p[0], p[1], p[2], p[3], p[4]};
-  float ov2 = C[ix(2, 2)], ov3 = C[ix(3, 3)], ov4 = C[ix(4, 4)];
-  bool dead = false;
+  f.p[0] = y1;
+  f.p[1] = 0.0f;
+  f.p[2] = sinf(phi1);
+  f.p[3] = z3 / arc;
+  f.p[4] = kappa / P.kB;
+  set_c0(P, f.C);
+  f.x = x1;
+  f.out_row = r0;
+  f.out_hit = start;
+#pragma unroll
+  for (int m = 0; m < 5; ++m) f.out_p[m] = f.p[m];
+  f.ov2 = f.C[ix(2, 2)];
+  f.ov3 = f.C[ix(3, 3)];
+  f.ov4 = f.C[ix(4, 4)];
+  f.dead = false;
   // the next chain hit (position and coordinates) and the one after it are
   // fetched one row ahead of their use
-  int hn = hn0, hn2 = hn1;
-  int4 qn = S.hit(L > 1 ? r0 + 1 : r0, hn);
-  int misses = 0, n_upd = 0;
-  for (int r = r0 + 1; r < NR && misses < MAX_MISS; ++r) {
-    const int i = r - r0;  // chain index of row r
-    const bool chain = i < L;
-    int h = -1;
-    int4 q = make_int4(0, 0, 0, 0);
-    // the row table entry is fetched for every row (one 32-byte load, off the
-    // dependency chain) so that it lives in registers
-    const RowInfo ri = S.row(r);
-    if (chain) {
-      h = hn;
-      q = qn;
-      hn = hn2;
-      if (i + 1 < L) qn = S.hit(r + 1, hn);
-      if (i + 2 < L) hn2 = hl[i + 2];
-    }
-    const float xn = xr[r];
-    if (!kf_propagate(P, p, C, x, xn)) break;
-    x = xn;
-    if (!(fabsf(p[2]) < SIN_MAX) || fabsf(p[0]) > x * P.tan_half) break;
-    const Win w = make_win(P, C);
-    if (!chain) h = pick_hit<G>(S, g, r, ri, p, w, z_base, &q);
-    if (!chain && h < 0) {
-      ++misses;
-      continue;
-    }
-    if (n_upd < JOSEPH_UPDATES)
-      kf_update_joseph(w, P.vy, P.vz, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
-    else
-      kf_update(w, p, C, q.x * Q - p[0], (float)(q.y - z_base) * Q - p[1]);
-    ++n_upd;
-    if (!cov_ok(C)) {
-      dead = true;
-      break;
-    }
-    misses = 0;
-    out_row = r;
-    out_hit = h;
-#pragma unroll
-    for (int m = 0; m < 5; ++m) out_p[m] = p[m];
-    ov2 = C[ix(2, 2)];
-    ov3 = C[ix(3, 3)];
-    ov4 = C[ix(4, 4)];
+  f.hn = hn0;
+  f.hn2 = hn1;
+  f.qn = S.hit(L > 1 ? r0 + 1 : r0, f.hn);
+  f.misses = 0;
+  f.n_upd = 0;
+  f.L = L;
+  f.r0 = r0;
+  f.z_base = z_base;
+}
+
+// Row r of the outward passes: the chain hit while the chain lasts, else (ii)
+// the best hit of the row.  false ends the pass (f.dead set if the covariance
+// failed); a row without a hit counts a miss.
+template <int G, class Src>
+__device__ __forceinline__ bool up_row(const DevParams& P, const Grp<G>& g, const Src& S, const float* xr,
+                                       const int* hl, int r, UpFit& f) {
+  const float Q = 1.0f / TPC_QSCALE;
+  const int i = r - f.r0;  // chain index of row r
+  const bool chain = i < f.L;
+  int h = -1;
+  int4 q = make_int4(0, 0, 0, 0);
+  // the row table entry is fetched for every row (one 32-byte load, off the
+  // dependency chain) so that it lives in registers
+  const RowInfo ri = S.row(r);
+  if (chain) {
+    h = f.hn;
+    q = f.qn;
+    f.hn = f.hn2;
+    if (i + 1 < f.L) f.qn = S.hit(r + 1, f.hn);
+    if (i + 2 < f.L) f.hn2 = hl[i + 2];
   }
+  const float xn = xr[r];
+  if (!kf_propagate(P, f.p, f.C, f.x, xn)) return false;
+  f.x = xn;
+  if (!(fabsf(f.p[2]) < SIN_MAX) || fabsf(f.p[0]) > f.x * P.tan_half) return false;
+  const Win w = make_win(P, f.C);
+  if (!chain) h = pick_hit<G>(S, g, r, ri, f.p, w, f.z_base, &q);
+  if (!chain && h < 0) {
+    ++f.misses;
+    return true;
+  }
+  if (f.n_upd < JOSEPH_UPDATES)
+    kf_update_joseph(w, P.vy, P.vz, f.p, f.C, q.x * Q - f.p[0], (float)(q.y - f.z_base) * Q - f.p[1]);
+  else
+    kf_update(w, f.p, f.C, q.x * Q - f.p[0], (float)(q.y - f.z_base) * Q - f.p[1]);
+  ++f.n_upd;
+  if (!cov_ok(f.C)) {
+    f.dead = true;
+    return false;
+  }
+  f.misses = 0;
+  f.out_row = r;
+  f.out_hit = h;
+#pragma unroll
+  for (int m = 0; m < 5; ++m) f.out_p[m] = f.p[m];
+  f.ov2 = f.C[ix(2, 2)];
+  f.ov3 = f.C[ix(3, 3)];
+  f.ov4 = f.C[ix(4, 4)];
+  return true;
+}
+
+// End of the outward passes: the record goes to b.tlu[tl] and the tracklet
+// claims its outermost hit (smallest tracklet index wins).
+template <int G>
+__device__ __forceinline__ void up_end(const Buffers& b, const Grp<G>& g, int tl, int item, int local,
+                                       const UpFit& f) {
   if (g.gl == 0) {
     TrackletUp u;
-    u.out_hit = dead ? -1 : out_hit;
-    u.out_row = out_row;
-    u.snp = out_p[2];
-    u.tgl = out_p[3];
-    u.qpt = out_p[4];
-    u.v2 = ov2;
-    u.v3 = ov3;
-    u.v4 = ov4;
-    u.z_base = z_base;
+    u.out_hit = f.dead ? -1 : f.out_hit;
+    u.out_row = f.out_row;
+    u.snp = f.out_p[2];
+    u.tgl = f.out_p[3];
+    u.qpt = f.out_p[4];
+    u.v2 = f.ov2;
+    u.v3 = f.ov3;
+    u.v4 = f.ov4;
+    u.z_base = f.z_base;
     u.item = item;
     u.local = local;
     u.pad = 0;
     b.tlu[tl] = u;
-    if (!dead) atomicMin(&b.out_owner[out_hit], tl);
+    if (!f.dead) atomicMin(&b.out_owner[f.out_hit], tl);
   }
   g.sync();
+}
+
+// Outward passes (i) and (ii) of the tracklet with start hit `start`: one loop
+// over the rows above the start row, taking the chain hit while the chain lasts
+// and searching afterwards (so that lanes of a warp in different phases run the
+// same propagation and update code together).  `local` is the item-local id,
+// `xr` the row positions.
+template <int G, bool PRE, class Src>
+__device__ __forceinline__ void tracklet_up(const Buffers& b, const Grp<G>& g, const Src& S, const float* xr,
+                                            int start, int4 hs, int tl, int local) {
+  const int NR = b.par.n_rows;
+  const int* hl = b.tl_hits + (size_t)tl * NR;
+  UpFit f;
+  up_begin<G, PRE>(b, g, S, xr, start, hs, tl, f);
+  for (int r = f.r0 + 1; r < NR && f.misses < MAX_MISS; ++r)
+    if (!up_row<G>(b.par, g, S, xr, hl, r, f)) break;
+  up_end<G>(b, g, tl, hs.w / NR, local, f);
 }
 
 // Inward refit (iii): the state of one refit and its three steps, shared by the
@@ -1665,22 +1716,22 @@ __global__ void k_counts(const __grid_constant__ Buffers b) {
 
 
 // ============================================================================ S9
-// Batched form: the stages of the plain form as persistent launches over all
-// items of the batch (events, sectors, time slices) in one captured graph, with
-// the tracklets taken from a work queue ordered by chain length.  A warp runs
-// as long as its slowest lane, and a lane costs about 900 cycles per chain row
-// and 3,400 per searched row: lanes whose chains end at different rows make
-// the warp run both kinds of rows.  Ordering by chain length puts lanes that
-// switch from chain to search at the same row into one warp (on the full TPC
-// event the modelled outward pass drops from 314 to 249 us, the cost of its
-// longest lane).  The queue does not change any result: a tracklet's outputs
-// go to its canonical index.  The order is kept inside each item, so that the
-// lanes of a warp keep reading one item's rows, bins and hits (a global order
-// mixed items in every warp and cost more in cache misses than it saved).
+// Batched form: the stages of the plain form over all items of the batch
+// (events, sectors, time slices) in one captured graph, with the tracklet
+// passes as persistent kernels that refill their lanes from work queues (below).
+// A warp runs as long as its slowest lane; a lane costs about 900 cycles per
+// chain row and 3,400 per searched row, and tracklets run from a few rows to
+// 300.  The queues change no result: a tracklet's outputs go to its canonical
+// index.  Each queue keeps an item's tracklets together, so that the lanes of
+// an SM keep reading a few items' rows, bins and hits (a global order mixed
+// items in every warp and cost more in cache misses than it saved).
 //   k_chain_walk:  every start hit's chain (hits kept for the outward pass);
 //   k_queue_items: per item (one CTA), a counting sort of its tracklets by chain
-//                  length in shared memory (shortest chains first: their long
-//                  searches start in the item's first warps).
+//                  length in shared memory, shortest chains first: their long
+//                  searches start first, and lanes that switch from chain to
+//                  search at the same row share a warp;
+//   k_down_order:  the inward pass's order (by outermost row, per segment).
+// The non-persistent k_tracklets_up_q<G> serves groups of G > 1 lanes.
 __global__ void __launch_bounds__(256) k_chain_walk(const __grid_constant__ Buffers b) {
   const int T = b.start_ex[b.N];
   const int NR = b.par.n_rows;
@@ -1735,33 +1786,101 @@ __global__ void __launch_bounds__(128) k_tracklets_up_q(const __grid_constant__ 
   }
 }
 
-// Inward refits of the batched form.  In a batch the inward pass is bound by
-// how long the lanes of a warp wait for its slowest one: with a tracklet per
-// lane a warp runs as long as its longest refit, and refits run from a few to
-// 150 rows.  Here the tracklets are cut into one contiguous segment per CTA
-// (one CTA per SM, DN_WARPS warps), and a lane takes the next tracklet as soon
-// as it finishes one, so a warp stays full until the work runs out.  A warp
-// takes from its own CTA's segment (its items' rows, bins and hits stay in the
-// SM's L1) and, once that is empty, from the following segments (the segments'
-// work differs by up to 1.5x across a batch of uneven events).  k_down_order
-// sorts every segment by outermost row, highest first (the refit runs from
-// there towards row 0, so that row bounds its length): the long refits start
-// first and a segment ends on short ones; dropped tracklets go last.  The order
-// changes no result: every tracklet writes its own record.
-constexpr int DN_WARPS = 16;
-
-__device__ __forceinline__ int down_key(const Buffers& b, int t, int NR) {
-  const TrackletUp u = b.tlu[t];
-  const bool dropped = u.out_hit < 0 || __ldcg(b.out_owner + u.out_hit) != t;
-  return dropped ? NR : NR - 1 - u.out_row;
-}
+// Persistent tracklet kernels of the batched form: one CTA per SM with
+// TL_WARPS warps; the tracklets (in the order b.tl_order) are cut into one
+// contiguous segment per CTA, and a lane takes the next tracklet as soon as it
+// finishes one, so that a warp stays full until the work runs out.  A warp
+// takes from its own CTA's segment (whose items' rows, bins and hits stay in
+// the SM's L1) and, once that is empty, from the following segments (work per
+// segment differs by up to 1.5x across a batch of uneven events).
+constexpr int TL_WARPS = 16;
 
 // segment c of T tracklets cut into n: [i0, i0 + len)
-__device__ __forceinline__ void down_segment(int T, int n, int c, int* i0, int* len) {
+__device__ __forceinline__ void tl_segment(int T, int n, int c, int* i0, int* len) {
   const int seg = (T + n - 1) / n;
   const int a = min(T, c * seg);
   *i0 = a;
   *len = min(T, a + seg) - a;
+}
+
+// Called by all lanes of a warp: the lanes with `need` get the next tracklets
+// of the order, or -1 when none is left.  Lane 0 claims them with one atomic on
+// the counter b.seg_next of segment *cs (its CTA's first, then the following
+// ones as they run empty; *tried counts the empty ones, so the search ends).
+__device__ __forceinline__ int take_tracklet(const Buffers& b, int T, bool need, int* cs, int* tried) {
+  const unsigned m = __ballot_sync(0xffffffffu, need);
+  if (!m) return -1;
+  const int lane = threadIdx.x & 31, nseg = gridDim.x;
+  int base = -1, i0 = 0, len = 0;
+  if (lane == 0) {
+    while (*tried < nseg) {
+      tl_segment(T, nseg, *cs, &i0, &len);
+      if (__ldcg(b.seg_next + *cs) < len) {
+        base = atomicAdd(b.seg_next + *cs, __popc(m));
+        if (base < len) break;
+      }
+      *cs = *cs + 1 == nseg ? 0 : *cs + 1;
+      ++*tried;
+      base = -1;
+    }
+  }
+  base = __shfl_sync(0xffffffffu, base, 0);
+  i0 = __shfl_sync(0xffffffffu, i0, 0);
+  len = __shfl_sync(0xffffffffu, len, 0);
+  const int k = base + __popc(m & ((1u << lane) - 1u));
+  return (need && base >= 0 && k < len) ? __ldg(b.tl_order + i0 + k) : -1;
+}
+
+__global__ void __launch_bounds__(32 * TL_WARPS, 1) k_tracklets_up_p(const __grid_constant__ Buffers b) {
+  __shared__ float s_x[TPC_MAX_ROWS];
+  for (int r = threadIdx.x; r < b.par.n_rows; r += blockDim.x) s_x[r] = b.par.x[r];
+  __syncthreads();
+  const Grp<1> g;
+  const int NR = b.par.n_rows;
+  const int T = b.start_ex[b.N];
+  int cs = blockIdx.x, tried = 0;
+  int tl = -1, r = 0, item = 0, local = 0;
+  UpFit f;
+  while (true) {
+    const int got = take_tracklet(b, T, tl < 0, &cs, &tried);
+    if (tl < 0 && got >= 0) {
+      tl = got;
+      const int start = __ldg(b.starts + tl);
+      const int4 hs = __ldg(b.s_hit + start);
+      item = hs.w / NR;
+      local = tl - b.start_ex[b.item_off[item]];
+      const GSrc<true> S{&b, b.rows + (size_t)item * NR};
+      up_begin<1, true>(b, g, S, s_x, start, hs, tl, f);
+      r = f.r0 + 1;
+    }
+    if (!__any_sync(0xffffffffu, tl >= 0)) break;
+    if (tl >= 0) {
+      bool more = r < NR && f.misses < MAX_MISS;
+      if (more) {
+        const GSrc<true> S{&b, b.rows + (size_t)item * NR};
+        more = up_row<1>(b.par, g, S, s_x, b.tl_hits + (size_t)tl * NR, r, f);
+        ++r;
+        more = more && r < NR && f.misses < MAX_MISS;
+      }
+      if (!more) {
+        up_end<1>(b, g, tl, item, local, f);
+        tl = -1;
+      }
+    }
+  }
+}
+
+// Inward refits of the batched form, persistent as above.  With a tracklet per
+// lane a warp runs as long as its longest refit, and refits run from a few to
+// 150 rows.  k_down_order sorts every segment by outermost row, highest first
+// (the refit runs from there towards row 0, so that row bounds its length):
+// the long refits start first and a segment ends on short ones; dropped
+// tracklets go last.  It also resets the segment counters.  The order changes
+// no result: every tracklet writes its own record.
+__device__ __forceinline__ int down_key(const Buffers& b, int t, int NR) {
+  const TrackletUp u = b.tlu[t];
+  const bool dropped = u.out_hit < 0 || __ldcg(b.out_owner + u.out_hit) != t;
+  return dropped ? NR : NR - 1 - u.out_row;
 }
 
 __global__ void __launch_bounds__(256) k_down_order(const __grid_constant__ Buffers b) {
@@ -1769,7 +1888,7 @@ __global__ void __launch_bounds__(256) k_down_order(const __grid_constant__ Buff
   __shared__ int sm[33];
   const int T = b.start_ex[b.N];
   int i0, len;
-  down_segment(T, gridDim.x, blockIdx.x, &i0, &len);
+  tl_segment(T, gridDim.x, blockIdx.x, &i0, &len);
   const int i1 = i0 + len;
   const int NR = b.par.n_rows, nb = NR + 1;
   if (threadIdx.x == 0) b.seg_next[blockIdx.x] = 0;
@@ -1791,51 +1910,27 @@ __global__ void __launch_bounds__(256) k_down_order(const __grid_constant__ Buff
     b.tl_order[i0 + atomicAdd(&s_cnt[down_key(b, t, NR)], 1)] = t;
 }
 
-__global__ void __launch_bounds__(32 * DN_WARPS, 1) k_tracklets_down_p(const __grid_constant__ Buffers b) {
+__global__ void __launch_bounds__(32 * TL_WARPS, 1) k_tracklets_down_p(const __grid_constant__ Buffers b) {
   __shared__ float s_x[TPC_MAX_ROWS];
   for (int r = threadIdx.x; r < b.par.n_rows; r += blockDim.x) s_x[r] = b.par.x[r];
   __syncthreads();
   const Grp<1> g;
   const int NR = b.par.n_rows;
   const int T = b.start_ex[b.N];
-  const int nseg = gridDim.x;
-  const int lane = threadIdx.x & 31;
-  const unsigned lt = (1u << lane) - 1u;
-  int cs = blockIdx.x, tried = 0;  // segment taken from, segments found empty (lane 0's)
+  int cs = blockIdx.x, tried = 0;
   int tl = -1, r = 0, item = 0, local = 0, z_base = 0;
   DownFit f;
   while (true) {
-    // lanes without a tracklet take the next ones: warp-uniform, lane 0 claims
-    // them with one atomic on the segment's counter
-    const unsigned need = __ballot_sync(0xffffffffu, tl < 0);
-    if (need) {
-      int base = -1, i0 = 0, len = 0;
-      if (lane == 0) {
-        while (tried < nseg) {
-          down_segment(T, nseg, cs, &i0, &len);
-          if (__ldcg(b.seg_next + cs) < len) {
-            base = atomicAdd(b.seg_next + cs, __popc(need));
-            if (base < len) break;
-          }
-          cs = cs + 1 == nseg ? 0 : cs + 1;
-          ++tried;
-          base = -1;
-        }
-      }
-      base = __shfl_sync(0xffffffffu, base, 0);
-      i0 = __shfl_sync(0xffffffffu, i0, 0);
-      len = __shfl_sync(0xffffffffu, len, 0);
-      const int k = base + __popc(need & lt);
-      if (tl < 0 && base >= 0 && k < len) {
-        tl = b.tl_order[i0 + k];
-        const TrackletUp u = b.tlu[tl];
-        item = u.item;
-        local = u.local;
-        z_base = u.z_base;
-        r = u.out_row - 1;
-        const GSrc<true> S{&b, b.rows + (size_t)item * NR};
-        down_begin<1>(b, g, S, s_x, tl, u, b.tl_hits + (size_t)tl * NR, f);
-      }
+    const int got = take_tracklet(b, T, tl < 0, &cs, &tried);
+    if (tl < 0 && got >= 0) {
+      tl = got;
+      const TrackletUp u = b.tlu[tl];
+      item = u.item;
+      local = u.local;
+      z_base = u.z_base;
+      r = u.out_row - 1;
+      const GSrc<true> S{&b, b.rows + (size_t)item * NR};
+      down_begin<1>(b, g, S, s_x, tl, u, b.tl_hits + (size_t)tl * NR, f);
     }
     if (!__any_sync(0xffffffffu, tl >= 0)) break;
     if (tl >= 0) {
@@ -1866,9 +1961,13 @@ cudaError_t tpc_launch_tracklets_queued(const Buffers& b, const LaunchCfg& c, cu
     k_tracklets_down<GG><<<grid, block, 0, s>>>(b);       \
     break;
     case 1:
-      k_tracklets_up_q<1><<<grid, block, 0, s>>>(b);
-      k_down_order<<<std::min(c.num_sms, TPC_MAX_SEGS), 256, 0, s>>>(b);
-      k_tracklets_down_p<<<std::min(c.num_sms, TPC_MAX_SEGS), 32 * DN_WARPS, 0, s>>>(b);
+    {
+      const int nseg = std::min(c.num_sms, TPC_MAX_SEGS);
+      cudaMemsetAsync(b.seg_next, 0, sizeof(int) * nseg, s);
+      k_tracklets_up_p<<<nseg, 32 * TL_WARPS, 0, s>>>(b);
+      k_down_order<<<nseg, 256, 0, s>>>(b);
+      k_tracklets_down_p<<<nseg, 32 * TL_WARPS, 0, s>>>(b);
+    }
       break;
     TPC_TLQ(2)
     default:
