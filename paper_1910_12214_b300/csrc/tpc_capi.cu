@@ -89,7 +89,7 @@ struct tpc_ctx {
   // MLP surrogate state (master weights, Adam moments, inference copies)
   int mlp_S = 0, mlp_batch = 1024;
   uint64_t mlp_seed = 0, mlp_step = 0, mlp_T = 0;
-  void* mlp_clock = nullptr;  // device training clock (tpc_mlp.cu)
+  void* mlp_work = nullptr;  // training workspace (tpc_mlp.cu: clock, step counter, staged weights)
   float mlp_lr = 3e-2f;
   float *mlp_master = nullptr, *mlp_m = nullptr, *mlp_v = nullptr, *mlp_partial = nullptr, *mlp_loss = nullptr;
   float* mlp_bounds = nullptr;
@@ -1196,8 +1196,9 @@ const uint32_t kMlpMagic = 0x31504C4D;  // "MLP1"
 
 tpc_status mlp_alloc(tpc_ctx* c, int S) {
   if (c->mlp_master && c->mlp_S == S) return TPC_OK;
+  if (S > 65535) return fail(c, TPC_ERR_INVALID_ARG, "the surrogate takes at most 65535 sectors");
   for (void* p : {(void*)c->mlp_master, (void*)c->mlp_m, (void*)c->mlp_v, (void*)c->mlp_partial,
-                  (void*)c->mlp_loss, (void*)c->mlp_bounds, c->mlp_infer})
+                  (void*)c->mlp_loss, (void*)c->mlp_bounds, c->mlp_infer, c->mlp_work})
     persist_free(c, p);
   const size_t np = (size_t)S * tpc_mlp_stride();
   const int nblk = c->mlp_batch / 128;
@@ -1208,8 +1209,9 @@ tpc_status mlp_alloc(tpc_ctx* c, int S) {
   c->mlp_loss = (float*)persist_alloc(c, 4 * (size_t)S * nblk);
   c->mlp_bounds = (float*)persist_alloc(c, 24 * (size_t)S);
   c->mlp_infer = persist_alloc(c, tpc_mlp_infer_bytes() * S);
+  c->mlp_work = persist_alloc(c, tpc_mlp_work_bytes(S));
   if (!c->mlp_master || !c->mlp_m || !c->mlp_v || !c->mlp_partial || !c->mlp_loss || !c->mlp_bounds ||
-      !c->mlp_infer) {
+      !c->mlp_infer || !c->mlp_work) {
     c->mlp_master = nullptr;
     return fail(c, TPC_ERR_OOM, "surrogate allocation failed");
   }
@@ -1276,9 +1278,7 @@ extern "C" tpc_status tpc_surrogate_train(tpc_ctx* c, uint64_t n_samples, uint64
       return cuda_fail(c, e, "surrogate init");
   }
   const uint64_t end = max_steps > 0 ? std::min<uint64_t>(c->mlp_T, c->mlp_step + (uint64_t)max_steps) : c->mlp_T;
-  if (!c->mlp_clock && !(c->mlp_clock = persist_alloc(c, tpc_mlp_clock_bytes())))
-    return fail(c, TPC_ERR_OOM, "device allocation failed (training clock)");
-  e = tpc_mlp_train_steps(c->mlp_clock, c->mlp_step, c->mlp_T, c->mlp_lr, end - c->mlp_step, c->mlp_master, c->mlp_m,
+  e = tpc_mlp_train_steps(c->mlp_work, c->mlp_step, c->mlp_T, c->mlp_lr, end - c->mlp_step, c->mlp_master, c->mlp_m,
                           c->mlp_v, c->mlp_partial, c->mlp_loss, (const float2*)c->grid_dev, c->b.grid_nx,
                           c->b.grid_ny, c->b.grid_nz, S, c->mlp_batch, seed, capturable(c->stream), c->stream);
   if (e != cudaSuccess) return cuda_fail(c, e, "surrogate steps");
@@ -1335,7 +1335,7 @@ extern "C" tpc_status tpc_surrogate_grad(tpc_ctx* c, int sector, uint64_t seed, 
     return TPC_ERR_INVALID_ARG;
   if (!c->mlp_master || !c->grid_dev || sector < 0 || sector >= c->mlp_S)
     return fail(c, TPC_ERR_STATE, "needs surrogate parameters and the grid");
-  cudaError_t e = tpc_mlp_grad_only(c->mlp_master, c->mlp_partial, c->mlp_loss, (const float2*)c->grid_dev,
+  cudaError_t e = tpc_mlp_grad_only(c->mlp_work, c->mlp_master, c->mlp_partial, c->mlp_loss, (const float2*)c->grid_dev,
                                     c->b.grid_nx, c->b.grid_ny, c->b.grid_nz, c->mlp_S, batch, seed, step, c->stream);
   const int nblk = batch / 128, np = tpc_mlp_nparams(), stride = tpc_mlp_stride();
   std::vector<float> part((size_t)nblk * stride), lv(nblk);
@@ -1404,6 +1404,7 @@ extern "C" tpc_status tpc_surrogate_load(tpc_ctx* c, const char* path) {
   if (!ok) return fail(c, TPC_ERR_INVALID_ARG, "truncated surrogate checkpoint");
   cudaError_t e = cudaSetDevice(c->cfg.device);
   if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+  if (hdr[6] < 128 || hdr[6] > (1u << 20) || hdr[6] % 128) return fail(c, TPC_ERR_INVALID_ARG, "bad batch in checkpoint");
   c->mlp_batch = (int)hdr[6];
   if (c->mlp_S != S) c->mlp_master = nullptr;
   tpc_status st = mlp_alloc(c, S);

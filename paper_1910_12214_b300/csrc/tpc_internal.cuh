@@ -193,14 +193,15 @@ size_t tpc_mlp_infer_bytes();
 int tpc_mlp_nparams();
 int tpc_mlp_stride();
 cudaError_t tpc_mlp_init(float* master, float* m, float* v, int S, uint64_t seed, cudaStream_t s);
-size_t tpc_mlp_clock_bytes();
+// training workspace of S sectors (device clock, step counter, staged weights)
+size_t tpc_mlp_work_bytes(int S);
 // n_steps training steps from step `first` of T (cosine schedule from lr);
-// clock: device block of tpc_mlp_clock_bytes()
-cudaError_t tpc_mlp_train_steps(void* clock, uint64_t first, uint64_t T, float lr, uint64_t n_steps, float* master,
+// work: device block of tpc_mlp_work_bytes(S)
+cudaError_t tpc_mlp_train_steps(void* work, uint64_t first, uint64_t T, float lr, uint64_t n_steps, float* master,
                                 float* m, float* v, float* partial, float* loss, const float2* grid, int nx, int ny,
                                 int nz, int S, int batch, uint64_t seed, bool graph, cudaStream_t s);
-cudaError_t tpc_mlp_grad_only(const float* master, float* partial, float* loss, const float2* grid, int nx, int ny,
-                              int nz, int S, int batch, uint64_t seed, uint64_t step, cudaStream_t s);
+cudaError_t tpc_mlp_grad_only(void* work, const float* master, float* partial, float* loss, const float2* grid,
+                              int nx, int ny, int nz, int S, int batch, uint64_t seed, uint64_t step, cudaStream_t s);
 cudaError_t tpc_mlp_eval(const float* master, const float2* grid, int nx, int ny, int nz, int S, int nblk,
                          uint64_t seed, float* out, cudaStream_t s);
 cudaError_t tpc_mlp_prepare(const float* master, const float* bounds, void* infer, int S, cudaStream_t s);

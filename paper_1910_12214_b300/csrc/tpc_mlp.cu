@@ -105,9 +105,9 @@ __device__ __forceinline__ float2 grid_at(const float2* G, int nx, int ny, int n
 }  // namespace
 
 // ---------------------------------------------------------------------------- training
-// Training clock on the device: the step and its Adam scalars, advanced by
-// k_mlp_tick after every step, so that a CUDA graph of K steps replays the
-// next K steps without arguments from the host.
+// Training clock on the device: the step and its Adam scalars, advanced by the
+// last block of every step's Adam kernel, so that a CUDA graph of K steps
+// replays the next K steps without arguments from the host.
 struct MlpClock {
   unsigned long long step, T;
   float lr;                 // base learning rate
@@ -128,14 +128,11 @@ __global__ void k_mlp_clock_set(MlpClock* c, unsigned long long step, unsigned l
   clock_scalars(c);
 }
 
-__global__ void k_mlp_tick(MlpClock* c) {
-  c->step += 1;
-  clock_scalars(c);
-}
+struct StagedW;
 
 struct MlpTrain {
   const MlpClock* clock;  // the step comes from here when set, else from `step`
-  const float* master;  // [S][NPP]
+  const StagedW* staged;  // [S] the step's weights as the CTAs read them
   float* partial;       // [S][nblk][NPP]
   float* loss;          // [S][nblk]
   const float2* grid;   // [S][nx][ny][nz]
@@ -178,19 +175,61 @@ __device__ __forceinline__ void mma_bf16(float* d, const uint32_t* a, uint32_t b
 
 constexpr int TS = 72;  // padded row stride (BF16 elements) of the training tiles: conflict-free ldmatrix
 
-// Shared memory of one training CTA.  The sample tiles are [sample][column]:
-// A1x and A2x hold the hidden activations with a column of ones at 64 (the
-// bias gradients come out of the same products), GZ1 and GZ2 the gradients
-// of the pre-activations, INx the inputs with a one at 3, GOx the output
-// gradients (columns 0..2).
-struct __align__(16) TrainSmem {
+// The weights of one sector as a training CTA reads them: W2 and W2^T as BF16
+// tiles with padded rows, the 3-wide layers rounded to BF16 (held as floats),
+// the biases FP32.  Staged in global memory once per step (by k_mlp_stage, and
+// by the Adam step for the next step) and copied into shared memory by every
+// CTA with 16-byte loads.
+struct __align__(16) StagedW {
   __nv_bfloat16 w2[H * TS];   // W2 [out j][in i]: B of the forward layer 2
   __nv_bfloat16 w2t[H * TS];  // W2^T [in i][out j]: B of the backward layer 2
+  float w1[192], b1[64], b2[64], w3[192], b3[4];
+};
+static_assert(sizeof(StagedW) % 16 == 0, "staged weights are copied in 16-byte units");
+
+// Shared memory of one training CTA: the staged weights, then the sample tiles
+// [sample][column]: A1x and A2x hold the hidden activations with a column of
+// ones at 64 (the bias gradients come out of the same products), GZ1 and GZ2
+// the gradients of the pre-activations, INx the inputs with a one at 3, GOx the
+// output gradients (columns 0..2).
+struct __align__(16) TrainSmem : StagedW {
   __nv_bfloat16 a1x[TB * TS], a2x[TB * TS], gz1[TB * TS], gz2[TB * TS];
   __nv_bfloat16 inx[TB * 8], gox[TB * 16];
-  float w1[192], b1[64], b2[64], w3[192], b3[4];
   float loss[TB / 32];
 };
+
+// parameter p of a sector with value v, staged
+__device__ __forceinline__ void stage_param(StagedW* W, int p, float v) {
+  if (p < OB1) {
+    W->w1[p - OW1] = bf(v);
+  } else if (p < OW2) {
+    W->b1[p - OB1] = v;
+  } else if (p < OB2) {
+    const int r = (p - OW2) / H, c = (p - OW2) % H;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    W->w2[r * TS + c] = h;
+    W->w2t[c * TS + r] = h;
+  } else if (p < OW3) {
+    W->b2[p - OB2] = v;
+  } else if (p < OB3) {
+    W->w3[p - OW3] = bf(v);
+  } else {
+    W->b3[p - OB3] = v;
+  }
+}
+
+// every weight of a sector staged from its FP32 master M, and the padding
+__global__ void __launch_bounds__(256) k_mlp_stage(const float* master, StagedW* staged) {
+  const float* M = master + (size_t)blockIdx.x * NPP;
+  StagedW* W = staged + blockIdx.x;
+  for (int p = threadIdx.x; p < NP; p += blockDim.x) stage_param(W, p, M[p]);
+  for (int p = threadIdx.x; p < H * (TS - H); p += blockDim.x) {
+    const int r = p / (TS - H), c = H + p % (TS - H);
+    W->w2[r * TS + c] = __float2bfloat16_rn(0.0f);
+    W->w2t[r * TS + c] = __float2bfloat16_rn(0.0f);
+  }
+  if (threadIdx.x == 0) W->b3[3] = 0.0f;
+}
 
 // One CTA per TB = 128 samples of a sector (four warps of 32 samples, two
 // 16-sample tiles each).  Forward and backward of a tile run on the tensor
@@ -209,21 +248,11 @@ __global__ void __launch_bounds__(TB) k_mlp_grad(const __grid_constant__ MlpTrai
   TrainSmem& S = *reinterpret_cast<TrainSmem*>(smem_raw);
   const int s = blockIdx.y, blk = blockIdx.x, t = threadIdx.x;
   const int lane = t & 31, warp = t >> 5, g = lane >> 2, q = lane & 3;
-  const float* M = a.master + (size_t)s * NPP;
-  for (int p = t; p < H * TS; p += TB) {
-    const int r = p / TS, c = p % TS;
-    S.w2[p] = __float2bfloat16_rn(c < H ? M[OW2 + H * r + c] : 0.0f);
-    S.w2t[p] = __float2bfloat16_rn(c < H ? M[OW2 + H * c + r] : 0.0f);
+  {
+    const int4* src = reinterpret_cast<const int4*>(a.staged + s);
+    int4* dst = reinterpret_cast<int4*>(static_cast<StagedW*>(&S));
+    for (int p = t; p < (int)(sizeof(StagedW) / 16); p += TB) dst[p] = __ldg(src + p);
   }
-  for (int p = t; p < 192; p += TB) {
-    S.w1[p] = bf(M[OW1 + p]);
-    S.w3[p] = bf(M[OW3 + p]);
-  }
-  for (int p = t; p < 64; p += TB) {
-    S.b1[p] = M[OB1 + p];
-    S.b2[p] = M[OB2 + p];
-  }
-  if (t < 3) S.b3[t] = M[OB3 + t];
   // the columns beyond the data: ones at 64 (bias column), zeros after
   for (int r = t; r < TB; r += TB) {
     for (int c = H; c < TS; ++c) {
@@ -472,28 +501,43 @@ __global__ void __launch_bounds__(TB) k_mlp_grad(const __grid_constant__ MlpTrai
 }
 
 struct MlpAdam {
-  const MlpClock* clock;  // lr_t, c1, c2 of the step
+  MlpClock* clock;  // lr_t, c1, c2 of the step; advanced by the step's last block
   float* master;
   float* m;
   float* v;
   const float* partial;
+  StagedW* staged;  // the next step's weights
+  unsigned* done;   // blocks finished with the step (zero between steps)
   int nblk;
   float b1, b2, eps;
 };
 
 // one thread per parameter: the CTA partials summed in a fixed order, then
-// one Adam step on the FP32 master weights
+// one Adam step on the FP32 master weights and their staged copy; the last
+// block to finish advances the clock
 __global__ void __launch_bounds__(256) k_mlp_adam(const __grid_constant__ MlpAdam a) {
   const int s = blockIdx.y, p = blockIdx.x * blockDim.x + threadIdx.x;
-  if (p >= NP) return;
-  float g = 0.f;
-  for (int k = 0; k < a.nblk; ++k) g += a.partial[((size_t)s * a.nblk + k) * NPP + p];
-  const size_t q = (size_t)s * NPP + p;
-  const float m = a.b1 * a.m[q] + (1.0f - a.b1) * g;
-  const float v = a.b2 * a.v[q] + (1.0f - a.b2) * g * g;
-  a.m[q] = m;
-  a.v[q] = v;
-  a.master[q] -= a.clock->lr_t * (m / a.clock->c1) / (sqrtf(v / a.clock->c2) + a.eps);
+  if (p < NP) {
+    float g = 0.f;
+    for (int k = 0; k < a.nblk; ++k) g += a.partial[((size_t)s * a.nblk + k) * NPP + p];
+    const size_t q = (size_t)s * NPP + p;
+    const float m = a.b1 * a.m[q] + (1.0f - a.b1) * g;
+    const float v = a.b2 * a.v[q] + (1.0f - a.b2) * g * g;
+    a.m[q] = m;
+    a.v[q] = v;
+    const float w = a.master[q] - a.clock->lr_t * (m / a.clock->c1) / (sqrtf(v / a.clock->c2) + a.eps);
+    a.master[q] = w;
+    stage_param(a.staged + s, p, w);
+  }
+  __syncthreads();  // every thread of the block has read the clock
+  if (threadIdx.x == 0) {
+    __threadfence();
+    if (atomicAdd(a.done, 1u) == gridDim.x * gridDim.y - 1) {
+      *a.done = 0u;
+      a.clock->step += 1;
+      clock_scalars(a.clock);
+    }
+  }
 }
 
 // Xavier-uniform initial weights (stream b = 0x5EED00000000, index = parameter)
@@ -760,24 +804,40 @@ cudaError_t tpc_mlp_init(float* master, float* m, float* v, int S, uint64_t seed
   return cudaGetLastError();
 }
 
-size_t tpc_mlp_clock_bytes() { return sizeof(MlpClock); }
+// Training workspace of S sectors: the clock and the step counter, then the
+// staged weights of every sector.
+namespace {
+struct __align__(16) MlpWorkHead {
+  MlpClock clock;
+  unsigned done;
+};
+StagedW* staged_of(void* work) {
+  return reinterpret_cast<StagedW*>(static_cast<char*>(work) + sizeof(MlpWorkHead));
+}
+}  // namespace
+static_assert(sizeof(MlpWorkHead) % 16 == 0, "staged weights follow at a 16-byte boundary");
 
-cudaError_t tpc_mlp_train_steps(void* clock, uint64_t first, uint64_t T, float lr, uint64_t n_steps, float* master,
+size_t tpc_mlp_work_bytes(int S) { return sizeof(MlpWorkHead) + sizeof(StagedW) * (size_t)S; }
+
+cudaError_t tpc_mlp_train_steps(void* work, uint64_t first, uint64_t T, float lr, uint64_t n_steps, float* master,
                                 float* m, float* v, float* partial, float* loss, const float2* grid, int nx, int ny,
                                 int nz, int S, int batch, uint64_t seed, bool graph, cudaStream_t s) {
   // an attribute of the current device: set per call (a process may train on several devices)
   cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        (int)sizeof(TrainSmem));
   if (e != cudaSuccess) return e;
-  MlpClock* ck = static_cast<MlpClock*>(clock);
+  MlpWorkHead* w = static_cast<MlpWorkHead*>(work);
+  MlpClock* ck = &w->clock;
+  StagedW* staged = staged_of(work);
   k_mlp_clock_set<<<1, 1, 0, s>>>(ck, first, T, lr);
+  if ((e = cudaMemsetAsync(&w->done, 0, sizeof(unsigned), s)) != cudaSuccess) return e;
+  k_mlp_stage<<<S, 256, 0, s>>>(master, staged);
   const int nblk = batch / TB;
-  MlpTrain a{ck, master, partial, loss, grid, nx, ny, nz, seed, 0, batch};
-  MlpAdam ad{ck, master, m, v, partial, nblk, 0.9f, 0.999f, 1e-8f};
+  MlpTrain a{ck, staged, partial, loss, grid, nx, ny, nz, seed, 0, batch};
+  MlpAdam ad{ck, master, m, v, partial, staged, &w->done, nblk, 0.9f, 0.999f, 1e-8f};
   auto one = [&]() {
     k_mlp_grad<<<dim3(nblk, S), TB, sizeof(TrainSmem), s>>>(a);
     k_mlp_adam<<<dim3((NP + 255) / 256, S), 256, 0, s>>>(ad);
-    k_mlp_tick<<<1, 1, 0, s>>>(ck);
   };
   // K steps captured once and replayed: no host work between steps
   constexpr uint64_t K = 64;
@@ -802,12 +862,14 @@ cudaError_t tpc_mlp_train_steps(void* clock, uint64_t first, uint64_t T, float l
   return cudaGetLastError();
 }
 
-cudaError_t tpc_mlp_grad_only(const float* master, float* partial, float* loss, const float2* grid, int nx, int ny,
-                              int nz, int S, int batch, uint64_t seed, uint64_t step, cudaStream_t s) {
+cudaError_t tpc_mlp_grad_only(void* work, const float* master, float* partial, float* loss, const float2* grid,
+                              int nx, int ny, int nz, int S, int batch, uint64_t seed, uint64_t step, cudaStream_t s) {
   const size_t smem = sizeof(TrainSmem);
   cudaError_t e = cudaFuncSetAttribute(k_mlp_grad, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  MlpTrain a{nullptr, master, partial, loss, grid, nx, ny, nz, seed, step, batch};
+  StagedW* staged = staged_of(work);
+  k_mlp_stage<<<S, 256, 0, s>>>(master, staged);
+  MlpTrain a{nullptr, staged, partial, loss, grid, nx, ny, nz, seed, step, batch};
   k_mlp_grad<<<dim3(batch / TB, S), TB, smem, s>>>(a);
   return cudaGetLastError();
 }
