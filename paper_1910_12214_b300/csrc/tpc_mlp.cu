@@ -70,6 +70,8 @@ __device__ __forceinline__ float silu_fast(float z) {
   const float hz = 0.5f * z;
   return fmaf(hz, tanh_hw(hz), hz);
 }
+// the same SiLU from h = z / 2
+__device__ __forceinline__ float silu_of_half(float hz) { return fmaf(hz, tanh_hw(hz), hz); }
 __device__ __forceinline__ float dsilu(float z) {
   const float s = sigm(z);
   return s * (1.0f + z * (1.0f - s));
@@ -617,7 +619,11 @@ __global__ void __launch_bounds__(TB) k_mlp_eval(const __grid_constant__ MlpEval
 // ---------------------------------------------------------------------------- inference
 // Per-sector inference copy: W2 in BF16 with padded rows (16-byte aligned rows
 // for ldmatrix, conflict-free), the other parameters as floats (weights
-// BF16-rounded, biases FP32).
+// BF16-rounded, biases FP32).  Layers 1 and 2 are stored halved (weights and
+// biases x 0.5): their accumulators are then h = z / 2, the argument of the
+// SiLU form h + h tanh(h), with no multiply.  Scaling by a power of two is
+// exact in the BF16 operands, their products and the FP32 sums, so every
+// output equals that of the unscaled network.
 constexpr int W2S = 72;  // padded row stride of W2 in BF16 elements
 struct __align__(16) MlpInfer {
   __nv_bfloat16 w2[H * W2S];
@@ -632,15 +638,15 @@ __global__ void k_mlp_prepare(const float* master, const float* bounds, MlpInfer
   MlpInfer& I = inf[s];
   for (int p = threadIdx.x; p < H * W2S; p += blockDim.x) {
     const int j = p / W2S, i = p % W2S;
-    I.w2[p] = __float2bfloat16_rn(i < H ? M[OW2 + H * j + i] : 0.0f);
+    I.w2[p] = __float2bfloat16_rn(i < H ? 0.5f * bf(M[OW2 + H * j + i]) : 0.0f);
   }
   for (int p = threadIdx.x; p < 192; p += blockDim.x) {
-    I.w1[p] = bf(M[OW1 + p]);
+    I.w1[p] = 0.5f * bf(M[OW1 + p]);
     I.w3[p] = bf(M[OW3 + p]);
   }
   for (int p = threadIdx.x; p < 64; p += blockDim.x) {
-    I.b1[p] = M[OB1 + p];
-    I.b2[p] = M[OB2 + p];
+    I.b1[p] = 0.5f * M[OB1 + p];
+    I.b2[p] = 0.5f * M[OB2 + p];
   }
   if (threadIdx.x < 3) I.b3[threadIdx.x] = M[OB3 + threadIdx.x];
   if (threadIdx.x < 6) I.bounds[threadIdx.x] = bounds[6 * s + threadIdx.x];
@@ -653,8 +659,11 @@ __global__ void k_mlp_prepare(const float* master, const float* bounds, MlpInfer
 // padded from 3 to 8; each layer's accumulators become the next layer's A
 // fragments in registers (after SiLU and BF16 rounding).  Fragment layout
 // (lane = 4 g + q): A rows g and g+8, columns 2q, 2q+1 and +8; B column g, rows
-// 2q, 2q+1 and +8; accumulators rows g and g+8, columns 2q, 2q+1.
-__global__ void __launch_bounds__(128) k_correct_mlp(const __grid_constant__ Buffers b) {
+// 2q, 2q+1 and +8; accumulators rows g and g+8, columns 2q, 2q+1.  The kernel
+// is bound by instruction issue (two per SiLU: tanh and one FMA, on halved
+// layers), so it is held to 80 registers for 6 CTAs per SM (measured 10%
+// faster than 4 CTAs at 98 registers, despite a few spilled values).
+__global__ void __launch_bounds__(128, 6) k_correct_mlp(const __grid_constant__ Buffers b) {
   __shared__ __align__(16) MlpInfer S;
   __shared__ float s_x[TPC_MAX_ROWS];  // row positions (lanes read different rows)
   const DevParams& P = b.par;
@@ -749,8 +758,8 @@ __global__ void __launch_bounds__(128) k_correct_mlp(const __grid_constant__ Buf
       float d[4] = {bb.x, bb.y, bb.x, bb.y};
       mma_bf16(d, A1, B1[t], 0u);
       const int ks = t >> 1, half = t & 1;
-      A[ks][2 * half] = pack_bf2(silu_fast(d[0]), silu_fast(d[1]));      // row g
-      A[ks][2 * half + 1] = pack_bf2(silu_fast(d[2]), silu_fast(d[3]));  // row g + 8
+      A[ks][2 * half] = pack_bf2(silu_of_half(d[0]), silu_of_half(d[1]));      // row g
+      A[ks][2 * half + 1] = pack_bf2(silu_of_half(d[2]), silu_of_half(d[3]));  // row g + 8
     }
     // layer 2: B fragments of two k-steps per ldmatrix (matrix j = lane / 8 is
     // rows 8nt..8nt+7 of W2 at columns 16 (ks + j/2) + 8 (j%2))
@@ -768,8 +777,8 @@ __global__ void __launch_bounds__(128) k_correct_mlp(const __grid_constant__ Buf
         mma_bf16(d, A[ks + 1], bf4[2], bf4[3]);
       }
       const int ks3 = nt >> 1, half = nt & 1;
-      A3[ks3][2 * half] = pack_bf2(silu_fast(d[0]), silu_fast(d[1]));
-      A3[ks3][2 * half + 1] = pack_bf2(silu_fast(d[2]), silu_fast(d[3]));
+      A3[ks3][2 * half] = pack_bf2(silu_of_half(d[0]), silu_of_half(d[1]));
+      A3[ks3][2 * half + 1] = pack_bf2(silu_of_half(d[2]), silu_of_half(d[3]));
     }
     // layer 3: outputs 0..2 in columns 0..2 (column 1 = dy, column 2 = dz)
     float o[4] = {c3a, c3b, c3a, c3b};
