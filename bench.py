@@ -46,7 +46,7 @@ ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12
 # dram__bytes_write.sum); they cannot be measured inside this run.  None: no
 # capture of the kernels as they are now.
 TRAFFIC = {}
-KERNELS_PER_STEP = {"plain": 19, "batched": 3}
+KERNELS_PER_STEP = {"plain": 19, "batched": 22}  # kernels per tracking step, as the launch lists show
 
 METRIC = "TPC clusters/s tracked (sector tracker, full TPC event)"
 WORKLOADS = {
@@ -66,9 +66,9 @@ def make_workload(name: str, rank: int):
 
 
 # ------------------------------------------------------------ input generation (CPU, before CUDA)
-def _gen_batched():
+def _gen_batched(n_events=64):
     from paper_1910_12214_b300 import synth
-    return synth.make_batched(seed=1, n_events=64)
+    return synth.make_batched(seed=1, n_events=n_events)
 
 
 def _gen_frame():
@@ -91,7 +91,7 @@ def _gen_grid():
     return d, g, b
 
 
-def generate_forms(forms):
+def generate_forms(forms, batch_events=64):
     """Generate the form workloads in spawned worker processes (no CUDA yet)."""
     out = {}
     jobs = {}
@@ -100,7 +100,7 @@ def generate_forms(forms):
         if "c10" in forms:
             jobs["c10"] = pool.apply_async(_gen_loopers)
         if any(f in forms for f in ("c3", "c5", "c6", "c7", "c8", "c9")):
-            jobs["c3"] = pool.apply_async(_gen_batched)
+            jobs["c3"] = pool.apply_async(_gen_batched, (batch_events,))
         if "c4" in forms:
             jobs["c4"] = pool.apply_async(_gen_frame)
         if "c5" in forms:
@@ -441,6 +441,9 @@ def main():
     ap.add_argument("--workload", default="c2", choices=sorted(WORKLOADS))
     ap.add_argument("--forms", default="c3,c4,c5,c6,c7,c8,c9,c10", help="extra forms at N=1: c3,...,c10 or none")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--batch-events", type=int, default=64, help="events of the batch forms (c3, c5-c9)")
+    ap.add_argument("--train-samples", type=int, default=40_000_000,
+                    help="surrogate training samples per sector (c5)")
     args = ap.parse_args()
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -448,7 +451,7 @@ def main():
     if args.impl == "reference":
         return run_reference(args, rank, world)
     forms = [] if args.forms == "none" or world > 1 or rank != 0 else [f for f in args.forms.split(",") if f]
-    gen = generate_forms(forms) if forms else {}  # CPU work before CUDA is touched
+    gen = generate_forms(forms, args.batch_events) if forms else {}  # CPU work before CUDA is touched
 
     import torch
     from paper_1910_12214_b300 import shard, tpc
@@ -520,7 +523,7 @@ def main():
 
     form_out = {}
     if rank == 0 and forms:
-        form_out = run_forms(gen, dev, stream, flush, tpc, torch)
+        form_out = run_forms(gen, dev, stream, flush, tpc, torch, args.train_samples, args.batch_events)
 
     if rank == 0:
         dom = max(stages, key=stages.get)
@@ -566,7 +569,7 @@ def main():
         dist.destroy_process_group()
 
 
-def run_forms(gen, dev, stream, flush, tpc, torch):
+def run_forms(gen, dev, stream, flush, tpc, torch, train_samples=40_000_000, batch_events=64):
     """clusters/s of the other forms (device time of tpc_track, L2 flushed)."""
     res = {}
 
@@ -603,7 +606,7 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
 
     if "c3" in gen:
         c3 = gen["c3"]
-        res["batched_64_events"] = {"clusters": c3.n, "items": c3.n_items, **bench_batch(c3, "c3", c3.n)}
+        res[f"batched_{batch_events}_events"] = {"clusters": c3.n, "items": c3.n_items, **bench_batch(c3, "c3", c3.n)}
     if "c4" in gen:
         res["timeframe_50khz_128_collisions"] = bench_frame(gen["c4"], dev, stream, flush, tpc, torch)
     if "c5" in gen:
@@ -613,7 +616,7 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
         def setup(t):
             t.set_grid_correction(grid, bounds)
             t0 = time.perf_counter()
-            mx, rms = t.surrogate_train(40_000_000, seed=1)
+            mx, rms = t.surrogate_train(train_samples, seed=1)
             info.update(train_s=time.perf_counter() - t0, resid_max_cm=mx, resid_rms_cm=rms)
 
         out = {}
@@ -643,15 +646,15 @@ def run_forms(gen, dev, stream, flush, tpc, torch):
         out["grid"]["cpu_baseline"] = cb
         out["mlp"]["parity"] = ("by the GPU tests: the network here is trained on the GPU, and the oracle takes "
                                 "no input from the CUDA path")
-        res["distorted_64_events"] = {"clusters": c5.n, "surrogate": info, **out}
+        res[f"distorted_{batch_events}_events"] = {"clusters": c5.n, "surrogate": info, **out}
     if "c6" in gen:
-        res["codec_64_events"] = bench_codec(gen["c6"], dev, stream, flush, tpc, torch)
+        res[f"codec_{batch_events}_events"] = bench_codec(gen["c6"], dev, stream, flush, tpc, torch)
     if "c7" in gen:
-        res["masks_64_events"] = bench_masks(gen["c7"], dev, stream, flush, tpc, torch)
+        res[f"masks_{batch_events}_events"] = bench_masks(gen["c7"], dev, stream, flush, tpc, torch)
     if "c8" in gen:
-        res["compress_64_events"] = bench_compress(*gen["c8"], dev, stream, flush, tpc, torch)
+        res[f"compress_{batch_events}_events"] = bench_compress(*gen["c8"], dev, stream, flush, tpc, torch)
     if "c9" in gen:
-        res["merge_64_events"] = bench_merge(gen["c9"], dev, stream, flush, tpc, torch)
+        res[f"merge_{batch_events}_events"] = bench_merge(gen["c9"], dev, stream, flush, tpc, torch)
     if "c10" in gen:
         res["removal_chain_loopers"] = bench_removal_chain(*gen["c10"], dev, stream, tpc, torch)
     return res
