@@ -65,8 +65,10 @@ typedef struct {
   float sector_half_angle_deg;/* sector half opening angle (10) */
   float sigma_y, sigma_z;     /* cluster resolution used by the Kalman filter [cm] (0.1) */
   tpc_mode mode;              /* PLAIN: one launch per step over all items; BATCHED: the same
-                                 stages with the tracklets taken from a work queue ordered by
-                                 chain length (identical results) */
+                                 stages, the tracklet passes as persistent kernels whose lanes
+                                 take tracklets from work queues (outward by chain length,
+                                 inward by outermost row) as they finish one; faster on large
+                                 batches, slower on one event (identical results) */
   tpc_corr correction;        /* space-point correction applied by tpc_track (see tpc_set_correction) */
   uint64_t max_clusters;      /* initial reservation (0 = grow on demand) */
   uint32_t max_items;         /* initial reservation (0 = grow on demand) */
@@ -262,8 +264,9 @@ typedef struct {
   int tracklet_blocks_per_sm;
   int sort_smem;
   int link_rows;
-  int mode;          /* 1 = plain, 2 = batched (tracklets from a queue ordered by chain length) */
-  int batch_lanes;   /* lanes per tracklet in the batched form: 1, 2 or 4 */
+  int mode;          /* 1 = plain, 2 = batched (persistent tracklet kernels fed by work queues) */
+  int batch_lanes;   /* lanes per tracklet in the batched form: 1 (persistent refilling kernels),
+                        2 or 4 (queued grid-stride kernels) */
   int use_graph;     /* 1 = launch directly, 2 = capture tpc_track once per load and replay it */
   int merge_sort_cap;
 } tpc_tuning;

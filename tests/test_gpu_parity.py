@@ -220,8 +220,10 @@ def _run_mode(cl, mode, graph, stream=None, lanes=1):
 
 @pytest.mark.parametrize("lanes", [1, 2, 4])
 def test_batched_persistent_kernel_equals_plain_mode(lanes):
-    """The persistent kernel (work queue, longest item first, CUDA graph) gives
-    the plain path's result bit for bit, item by item; so it matches the oracle."""
+    """The batched form (CUDA graph; with one lane per tracklet the persistent
+    tracklet kernels refilling their lanes from the work queues, with groups of
+    2 or 4 lanes the queued grid-stride kernels) gives the plain path's result
+    bit for bit, item by item; so it matches the oracle."""
     import torch
     cl = _with_empty_items(synth.make_batched(seed=7, n_events=6, mult=(5, 3000)))
     s = torch.cuda.Stream()
@@ -235,6 +237,26 @@ def test_batched_persistent_kernel_equals_plain_mode(lanes):
     compare_stages(d_b, ref)
     r = compare_tracks(cl, trk_b, ids_b, ref)
     assert r["ok"], r
+
+
+def test_batched_form_on_batches_smaller_than_the_gpu():
+    """Fewer tracklets than SMs (most segments of the persistent kernels are
+    empty, the warps take work from the following segments), a batch with no
+    tracklet, an empty batch: the batched form equals the plain one."""
+    from paper_1910_12214_b300 import tpc
+    tiny = synth.make_event(3, 4, single_sector=True)  # a few tracks in one sector
+    cases = [tiny, _Cl([100.0, 101.0], [1.0, 1.5], [2.0, 2.1], [14, 15], [0, 2]), _Cl([], [], [], [], [0, 0])]
+    for c in cases:
+        out = []
+        for mode in (1, 2):
+            with tpc.Tracker() as t:
+                t.set_tuning(mode=mode, batch_lanes=1, use_graph=2)
+                t.load(c).track()
+                t.track()  # graph replay
+                trk, ids = t.get_tracks()
+                out.append((trk.tobytes(), ids.tobytes(), t.debug_dump(9).tobytes()))
+        assert out[0] == out[1]
+    assert len(np.frombuffer(out[0][0], np.uint8)) == 0
 
 
 def test_batched_with_rejected_clusters_reports_and_recovers():
