@@ -5,15 +5,18 @@ Headline workload: the full TPC (36 sectors x 152 rows), one central Pb-Pb-like
 event of 6000 primary helices (~0.9M clusters, 5% noise), synthetic and seeded;
 one step = one tpc_track() over the resident batch (every step of the path),
 launch shapes chosen by the library's autotuner, replayed as a CUDA graph.
-Further forms (rank 0, N=1): 64 uneven events (plain vs batched persistent
-kernel), a 50 kHz continuous-readout time frame (128 collisions, sliced), and
+Further forms (rank 0, N=1): 64 uneven events (plain vs the batched form's
+persistent tracklet kernels), a 50 kHz continuous-readout time frame (128
+collisions, sliced on the device inside the timed step), and
 the same 64 events distorted by a space-charge field, corrected by the grid or
 by the trained BF16 network, the cluster codec (float to integer with dynamic
 precision) over the 64 events' clusters, the cluster removal masks
 (attachment, adjacency, protection, strategies A and B) of the 64 events,
 their compression (delta and track-model coding, rANS), the merger of their
-sector tracks with refit and looper legs, and the whole reduction chain (legs,
-masks, removal, compression) on an event whose low-pT helices loop.
+sector tracks with refit and looper legs, and the whole reduction chain (legs
+and their join, masks, removal, compression) on an event whose low-pT helices
+loop.  Every batch form checks its tracks against the oracle on a sample of its
+items in the same run.
 
 Prints ONE JSON line (rank 0).  --impl reference times the FP64 CPU oracle on a
 bounded sample of the same workload instead.

@@ -49,7 +49,7 @@ struct tpc_ctx {
   bool mrg_tab_built = false;
   const void* mrg_tab_dev = nullptr;  // the device copy they were uploaded to
   bool have_events = false;
-  // host copies used by the debug dump and the work queue
+  // host copies of the item tables (debug dump, merger tables, frames)
   std::vector<uint64_t> h_item_off;
   std::vector<uint32_t> h_item_sector, h_item_event;  // empty if the batch has none
   // execution mode and CUDA graph of tpc_track
