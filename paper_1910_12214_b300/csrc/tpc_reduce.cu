@@ -662,23 +662,82 @@ __global__ void k_cmp_unatt(const __grid_constant__ CmpArgs a) {
   }
 }
 
-__global__ void k_cmp_rowcounts(const __grid_constant__ CmpArgs a, int n_rows) {
+// Statistics of the symbol values, gathered by the kernels that produce them
+// (so that no pass reads the values back): per block, the histograms of byte
+// planes 0 and 1 of every stream in shared memory, flushed to a.hist, and per
+// thread the largest value of each stream it writes, reduced per warp into
+// a.vmax.  Planes 2..7 follow in k_cmp_hist_high where the largest value
+// needs them.
+constexpr int CMP_STAT_WORDS = TPC_CMP_STREAMS * 512;
+
+__device__ __forceinline__ void stats_clear(unsigned* h) {
+  for (int i = threadIdx.x; i < CMP_STAT_WORDS; i += blockDim.x) h[i] = 0u;
+  __syncthreads();
+}
+
+__device__ __forceinline__ void stats_add(unsigned* h, int s, unsigned long long x, unsigned long long* mx) {
+  atomicAdd(&h[s * 512 + (int)(x & 255u)], 1u);
+  atomicAdd(&h[s * 512 + 256 + (int)((x >> 8) & 255u)], 1u);
+  *mx = x > *mx ? x : *mx;
+}
+
+// every thread of the block calls it once, after its last value
+template <int K>
+__device__ __forceinline__ void stats_flush(const CmpArgs& a, const unsigned* h, const int (&streams)[K],
+                                            unsigned long long (&mx)[K]) {
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    unsigned long long m = mx[k];
+    for (int o = 16; o; o >>= 1) {
+      const unsigned long long u = __shfl_xor_sync(0xffffffffu, m, o);
+      m = u > m ? u : m;
+    }
+    if ((threadIdx.x & 31) == 0 && m) atomicMax(a.vmax + streams[k], m);
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < CMP_STAT_WORDS; i += blockDim.x) {
+    const unsigned c = h[i];
+    if (c) atomicAdd(a.hist + (long long)(i >> 9) * 2048 + (i & 511), (unsigned long long)c);
+  }
+}
+
+__global__ void __launch_bounds__(256) k_cmp_rowcounts(const __grid_constant__ CmpArgs a, int n_rows) {
+  __shared__ unsigned h[CMP_STAT_WORDS];
+  stats_clear(h);
+  const int st[1] = {C_UNATT_N};
+  unsigned long long mx[1] = {0ull};
   const long long G = (long long)a.I * n_rows;
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long g = (long long)blockIdx.x * blockDim.x + threadIdx.x; g < G; g += stride) {
     const RowInfo ri = a.rows[g];
-    a.val[C_UNATT_N][g] = ri.n > 0 ? (unsigned long long)(a.kpos[ri.pos0 + ri.n] - a.kpos[ri.pos0]) : 0ull;
+    const unsigned long long v = ri.n > 0 ? (unsigned long long)(a.kpos[ri.pos0 + ri.n] - a.kpos[ri.pos0]) : 0ull;
+    a.val[C_UNATT_N][g] = v;
+    stats_add(h, C_UNATT_N, v, &mx[0]);
   }
+  stats_flush(a, h, st, mx);
 }
 
-__device__ __forceinline__ void put_props(const CmpArgs& a, long long k, const int4& q) {
-  a.val[C_QT][k] = (unsigned long long)((unsigned)q.y >> 16);
-  a.val[C_QM][k] = (unsigned long long)((unsigned)q.z & 0xffffu);
-  a.val[C_SY][k] = (unsigned long long)((unsigned)q.w & 0xffu);
-  a.val[C_SZ][k] = (unsigned long long)(((unsigned)q.w >> 8) & 0xffu);
+// the four property codes of a stored cluster (record q) at position k of the
+// property streams; mx[0..3] are their running maxima
+__device__ __forceinline__ void put_props(const CmpArgs& a, long long k, const int4& q, unsigned* h,
+                                          unsigned long long* mx) {
+  const unsigned long long qt = (unsigned)q.y >> 16, qm = (unsigned)q.z & 0xffffu;
+  const unsigned long long sy = (unsigned)q.w & 0xffu, sz = ((unsigned)q.w >> 8) & 0xffu;
+  a.val[C_QT][k] = qt;
+  a.val[C_QM][k] = qm;
+  a.val[C_SY][k] = sy;
+  a.val[C_SZ][k] = sz;
+  stats_add(h, C_QT, qt, mx + 0);
+  stats_add(h, C_QM, qm, mx + 1);
+  stats_add(h, C_SY, sy, mx + 2);
+  stats_add(h, C_SZ, sz, mx + 3);
 }
 
-__global__ void k_cmp_unatt_symbols(const __grid_constant__ CmpArgs a) {
+__global__ void __launch_bounds__(256) k_cmp_unatt_symbols(const __grid_constant__ CmpArgs a) {
+  __shared__ unsigned h[CMP_STAT_WORDS];
+  stats_clear(h);
+  const int st[6] = {C_QT, C_QM, C_SY, C_SZ, C_DY, C_DZ};
+  unsigned long long mx[6] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
   const long long n_un = a.kpos[a.P];
   const long long stride = (long long)gridDim.x * blockDim.x;
   for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n_un; k += stride) {
@@ -689,14 +748,23 @@ __global__ void k_cmp_unatt_symbols(const __grid_constant__ CmpArgs a) {
       yp = rec_y(b);
       zp = b.x;
     }
-    a.val[C_DY][k] = zigzag((long long)rec_y(q) - yp);
-    a.val[C_DZ][k] = zigzag((long long)q.x - zp);
-    put_props(a, k, q);
+    const unsigned long long dy = zigzag((long long)rec_y(q) - yp), dz = zigzag((long long)q.x - zp);
+    a.val[C_DY][k] = dy;
+    a.val[C_DZ][k] = dz;
+    stats_add(h, C_DY, dy, &mx[4]);
+    stats_add(h, C_DZ, dz, &mx[5]);
+    put_props(a, k, q, h, mx);
   }
+  stats_flush(a, h, st, mx);
 }
 
 // one warp per track: row increments, residuals to the prediction, charges
-__global__ void k_cmp_track_symbols(const __grid_constant__ CmpArgs a, const __grid_constant__ DevParams par) {
+__global__ void __launch_bounds__(256) k_cmp_track_symbols(const __grid_constant__ CmpArgs a,
+                                                            const __grid_constant__ DevParams par) {
+  __shared__ unsigned h[CMP_STAT_WORDS];
+  stats_clear(h);
+  const int st[8] = {C_QT, C_QM, C_SY, C_SZ, C_DROW, C_RY, C_RZ, C_TRK_N};
+  unsigned long long mx[8] = {0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull, 0ull};
   const int lane = threadIdx.x & 31;
   const long long n_trk = n_tracks_of(a);
   const long long n_un = a.kpos[a.P];
@@ -707,7 +775,10 @@ __global__ void k_cmp_track_symbols(const __grid_constant__ CmpArgs a, const __g
     const long long base = a.trk_n[t], stored = a.trk_n[t + 1] - base;
     // the track's clusters (all of them when it stores any; a bad track stores none)
     const long long cnt = stored > 0 ? (long long)T.n_clusters : 0;
-    if (lane == 0) a.val[C_TRK_N][t] = (unsigned long long)stored;
+    if (lane == 0) {
+      a.val[C_TRK_N][t] = (unsigned long long)stored;
+      stats_add(h, C_TRK_N, (unsigned long long)stored, &mx[7]);
+    }
     int carry = 0;        // row of the previous stored cluster (0 before the first)
     long long done = 0;   // stored clusters of the previous rounds
     for (long long j0 = 0; j0 < cnt; j0 += 32) {
@@ -734,12 +805,18 @@ __global__ void k_cmp_track_symbols(const __grid_constant__ CmpArgs a, const __g
       }
       long long py, pz;
       predict_codes(T, par.kB, par.x[r], &py, &pz);
-      a.val[C_DROW][base + pos] = zigzag((long long)(r - rp));
-      a.val[C_RY][base + pos] = zigzag((long long)rec_y(q) - py);
-      a.val[C_RZ][base + pos] = zigzag((long long)q.x - pz);
-      put_props(a, n_un + base + pos, q);
+      const unsigned long long drow = zigzag((long long)(r - rp));
+      const unsigned long long ry = zigzag((long long)rec_y(q) - py), rz = zigzag((long long)q.x - pz);
+      a.val[C_DROW][base + pos] = drow;
+      a.val[C_RY][base + pos] = ry;
+      a.val[C_RZ][base + pos] = rz;
+      stats_add(h, C_DROW, drow, &mx[4]);
+      stats_add(h, C_RY, ry, &mx[5]);
+      stats_add(h, C_RZ, rz, &mx[6]);
+      put_props(a, n_un + base + pos, q, h, mx);
     }
   }
+  stats_flush(a, h, st, mx);
 }
 
 // length of stream s from the device-side totals
@@ -751,35 +828,6 @@ __device__ __forceinline__ long long stream_len(const CmpArgs& a, int s, int n_r
     case C_DROW: case C_RY: case C_RZ: return n_att;
     case C_TRK_N: return n_tracks_of(a);
     default: return n_un + n_att;
-  }
-}
-
-// largest value and the histograms of byte planes 0 and 1 of every stream
-// (blockIdx.y = stream); planes 2..7 only where the largest value needs them
-// (k_cmp_hist_high)
-__global__ void __launch_bounds__(256) k_cmp_stats(const __grid_constant__ CmpArgs a, int n_rows) {
-  __shared__ unsigned int h[2][256];
-  const int s = blockIdx.y;
-  const long long n = stream_len(a, s, n_rows);
-  for (int i = threadIdx.x; i < 512; i += blockDim.x) (&h[0][0])[i] = 0;
-  __syncthreads();
-  unsigned long long mx = 0;
-  const unsigned long long* v = a.val[s];
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x) {
-    const unsigned long long x = v[i];
-    mx = x > mx ? x : mx;
-    atomicAdd(&h[0][x & 255], 1u);
-    atomicAdd(&h[1][(x >> 8) & 255], 1u);
-  }
-  for (int o = 16; o; o >>= 1) {
-    const unsigned long long u = __shfl_xor_sync(0xffffffffu, mx, o);
-    mx = u > mx ? u : mx;
-  }
-  if ((threadIdx.x & 31) == 0 && mx) atomicMax(a.vmax + s, mx);
-  __syncthreads();
-  for (int i = threadIdx.x; i < 512; i += blockDim.x) {
-    const unsigned int c = (&h[0][0])[i];
-    if (c) atomicAdd(a.hist + (long long)s * 2048 + i, (unsigned long long)c);
   }
 }
 
@@ -1059,7 +1107,6 @@ cudaError_t cmp_symbols(const CmpArgs& a, const DevParams& par, int num_sms, cud
   k_cmp_rowcounts<<<g, 256, 0, s>>>(a, par.n_rows);
   k_cmp_unatt_symbols<<<g, 256, 0, s>>>(a);
   k_cmp_track_symbols<<<g, 256, 0, s>>>(a, par);
-  k_cmp_stats<<<dim3(num_sms * 2, TPC_CMP_STREAMS), 256, 0, s>>>(a, par.n_rows);
   return cudaGetLastError();
 }
 
