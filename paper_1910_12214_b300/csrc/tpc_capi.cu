@@ -214,6 +214,7 @@ tpc_status reserve(tpc_ctx* c, long long N, long long I, long long n_chunks) {
   b.rs_cnt = (int*)A(4 * M);
   b.rs_min = (int*)A(16 * M);
   b.row_fill = (int*)A(4 * M);
+  b.rs_big = (int*)A(4 * (M + 1));
   b.rows = (RowInfo*)A(sizeof(RowInfo) * M);
   b.g_q = (int2*)A(8 * N);
   b.g_id = (int*)A(4 * N);

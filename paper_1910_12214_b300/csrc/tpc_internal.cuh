@@ -86,6 +86,7 @@ struct Buffers {
   int* rs_cnt;    // [I*NR]
   int* rs_min;    // [4][I*NR]: ymin, -ymax, zmin, -zmax
   int* row_fill;  // [I*NR]
+  int* rs_big;    // rows too large for the warp sort, then their count [I*NR + 1]
   RowInfo* rows;  // [I*NR]
   // grouped (row-major, unsorted) and sorted hits
   int2* g_q;

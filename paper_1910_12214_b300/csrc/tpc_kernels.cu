@@ -5,7 +5,8 @@
 //                    and extents (global atomics)
 //   k_row_setup      bin size, grid dims, row and bin offsets (block scans)
 //   k_group_scatter  counting sort of clusters into row-contiguous order
-//   k_row_sort       per row: bin histogram, scan, scatter, in-bin sort by id
+//   k_row_sort_warp  per row (a warp each): bin histogram, scan, scatter, in-bin sort by id
+//   k_row_sort       the same per CTA for the rows too large for a warp's shared memory
 //                    (canonical order row, bin, original id) and first[] starts
 //   k_links          per hit of an inner row: best (up, down) pair (integer metric)
 //   k_clean_start    mutual-link cleaning and start-hit flags
@@ -276,63 +277,68 @@ __global__ void __launch_bounds__(256) k_group_scatter(const __grid_constant__ B
 // One CTA per (item,row).  Rows that fit the dynamic shared-memory budget are
 // sorted in shared memory; larger rows use the same code on global scratch
 // (tq/tid/tslot) with the row's own first[] entries as the histogram.
-__global__ void __launch_bounds__(128) k_row_sort(const __grid_constant__ Buffers b, int smem_bytes, int2* tq, int* tid_buf, int* tslot) {
+// Rows sorted by one warp each (8 rows per CTA, no block barriers): the counting
+// sort of k_row_sort below, hits by bin and, inside a bin, by original id, for
+// rows whose scratch fits the warp's slice of shared memory (RS_WARP_BYTES);
+// larger rows are listed in b.rs_big for k_row_sort.  Empty rows get their one
+// bin start here.
+constexpr int RS_WARPS = 8;
+constexpr int RS_WARP_BYTES = 8192;
+
+__device__ __forceinline__ bool rs_fits_warp(int n, int nb) { return 16ll * n + 4ll * (nb + 1) <= RS_WARP_BYTES; }
+
+__global__ void __launch_bounds__(32 * RS_WARPS) k_row_sort_warp(const __grid_constant__ Buffers b, int M) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  __shared__ int sm[33];
-  const int k = blockIdx.x;
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int k = blockIdx.x * RS_WARPS + w;
+  if (k >= M) return;  // warp-uniform
   const RowInfo ri = b.rows[k];
   const int n = ri.n;
   if (n == 0) {
-    if (threadIdx.x == 0) b.first[ri.bin0] = ri.pos0;
+    if (lane == 0) b.first[ri.bin0] = ri.pos0;
     return;
   }
   const int nb = ri.ny * ri.nz;
-  const long long need = 12ll * n + 4ll * n + 4ll * (nb + 1);
-  int2* q2;
-  int* id2;
-  int* slot;
-  int* hist;
-  if (need <= smem_bytes) {
-    q2 = reinterpret_cast<int2*>(smem_raw);
-    id2 = reinterpret_cast<int*>(q2 + n);
-    slot = id2 + n;
-    hist = slot + n;
-  } else {
-    q2 = tq + ri.pos0;
-    id2 = tid_buf + ri.pos0;
-    slot = tslot + ri.pos0;
-    hist = b.first + ri.bin0;
+  if (!rs_fits_warp(n, nb)) {
+    if (lane == 0) b.rs_big[atomicAdd(b.rs_big + M, 1)] = k;
+    return;
   }
-  for (int j = threadIdx.x; j <= nb; j += blockDim.x) hist[j] = 0;
-  __syncthreads();
+  int2* q2 = reinterpret_cast<int2*>(smem_raw + (size_t)w * RS_WARP_BYTES);
+  int* id2 = reinterpret_cast<int*>(q2 + n);
+  int* slot = id2 + n;
+  int* hist = slot + n;
+  for (int j = lane; j <= nb; j += 32) hist[j] = 0;
+  __syncwarp();
   const int s = ri.shift;
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+  for (int j = lane; j < n; j += 32) {
     const int2 q = b.g_q[ri.pos0 + j];
     const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
     slot[j] = atomicAdd(&hist[bin], 1);
   }
-  __syncthreads();
-  // exclusive scan of hist[0..nb] in place, chunk by chunk
-  int carry = 0;
-  for (int base = 0; base <= nb; base += blockDim.x) {
-    const int j = base + threadIdx.x;
+  __syncwarp();
+  int carry = 0;  // exclusive scan of hist[0..nb], 32 entries at a time
+  for (int j0 = 0; j0 <= nb; j0 += 32) {
+    const int j = j0 + lane;
     const int v = j <= nb ? hist[j] : 0;
-    int tot;
-    const int ex = block_excl_scan(v, sm, &tot);
-    if (j <= nb) hist[j] = carry + ex;
-    carry += tot;
-    __syncthreads();
+    int inc = v;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int u = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc += u;
+    }
+    if (j <= nb) hist[j] = carry + inc - v;
+    carry += __shfl_sync(0xffffffffu, inc, 31);
   }
-  for (int j = threadIdx.x; j < n; j += blockDim.x) {
+  __syncwarp();
+  for (int j = lane; j < n; j += 32) {
     const int2 q = b.g_q[ri.pos0 + j];
     const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
     const int p = hist[bin] + slot[j];
     q2[p] = q;
     id2[p] = b.g_id[ri.pos0 + j];
   }
-  __syncthreads();
-  // canonical order inside a bin: original id (insertion sort; bins hold a few hits)
-  for (int bin = threadIdx.x; bin < nb; bin += blockDim.x) {
+  __syncwarp();
+  for (int bin = lane; bin < nb; bin += 32) {  // inside a bin: original id (bins hold a few hits)
     const int a = hist[bin], e = hist[bin + 1];
     for (int i = a + 1; i < e; ++i) {
       const int2 qv = q2[i];
@@ -347,13 +353,92 @@ __global__ void __launch_bounds__(128) k_row_sort(const __grid_constant__ Buffer
       id2[j + 1] = iv;
     }
   }
-  __syncthreads();
-  for (int j = threadIdx.x; j < n; j += blockDim.x) b.s_hit[ri.pos0 + j] = make_int4(q2[j].x, q2[j].y, id2[j], k);
-  if (hist != b.first + ri.bin0) {
-    for (int j = threadIdx.x; j <= nb; j += blockDim.x) b.first[ri.bin0 + j] = ri.pos0 + hist[j];
-  } else {
+  __syncwarp();
+  for (int j = lane; j < n; j += 32) b.s_hit[ri.pos0 + j] = make_int4(q2[j].x, q2[j].y, id2[j], k);
+  for (int j = lane; j <= nb; j += 32) b.first[ri.bin0 + j] = ri.pos0 + hist[j];
+}
+
+// The rows listed by k_row_sort_warp, one CTA at a time per row (a grid-stride
+// loop over the list): scratch in shared memory when it fits `smem_bytes`,
+// else in the global scratch arrays tq, tid_buf, tslot at the row's positions.
+__global__ void __launch_bounds__(128) k_row_sort(const __grid_constant__ Buffers b, int smem_bytes, int2* tq, int* tid_buf, int* tslot, int M) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ int sm[33];
+  const int n_big = b.rs_big[M];
+  for (int ib = blockIdx.x; ib < n_big; ib += gridDim.x) {  // block-uniform loop
+    const int k = b.rs_big[ib];
+    const RowInfo ri = b.rows[k];
+    const int n = ri.n;
+    const int nb = ri.ny * ri.nz;
+    const long long need = 12ll * n + 4ll * n + 4ll * (nb + 1);
+    int2* q2;
+    int* id2;
+    int* slot;
+    int* hist;
+    if (need <= smem_bytes) {
+      q2 = reinterpret_cast<int2*>(smem_raw);
+      id2 = reinterpret_cast<int*>(q2 + n);
+      slot = id2 + n;
+      hist = slot + n;
+    } else {
+      q2 = tq + ri.pos0;
+      id2 = tid_buf + ri.pos0;
+      slot = tslot + ri.pos0;
+      hist = b.first + ri.bin0;
+    }
+    for (int j = threadIdx.x; j <= nb; j += blockDim.x) hist[j] = 0;
     __syncthreads();
-    for (int j = threadIdx.x; j <= nb; j += blockDim.x) b.first[ri.bin0 + j] += ri.pos0;
+    const int s = ri.shift;
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const int2 q = b.g_q[ri.pos0 + j];
+      const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
+      slot[j] = atomicAdd(&hist[bin], 1);
+    }
+    __syncthreads();
+    // exclusive scan of hist[0..nb] in place, chunk by chunk
+    int carry = 0;
+    for (int base = 0; base <= nb; base += blockDim.x) {
+      const int j = base + threadIdx.x;
+      const int v = j <= nb ? hist[j] : 0;
+      int tot;
+      const int ex = block_excl_scan(v, sm, &tot);
+      if (j <= nb) hist[j] = carry + ex;
+      carry += tot;
+      __syncthreads();
+    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) {
+      const int2 q = b.g_q[ri.pos0 + j];
+      const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
+      const int p = hist[bin] + slot[j];
+      q2[p] = q;
+      id2[p] = b.g_id[ri.pos0 + j];
+    }
+    __syncthreads();
+    // canonical order inside a bin: original id (insertion sort; bins hold a few hits)
+    for (int bin = threadIdx.x; bin < nb; bin += blockDim.x) {
+      const int a = hist[bin], e = hist[bin + 1];
+      for (int i = a + 1; i < e; ++i) {
+        const int2 qv = q2[i];
+        const int iv = id2[i];
+        int j = i - 1;
+        while (j >= a && id2[j] > iv) {
+          q2[j + 1] = q2[j];
+          id2[j + 1] = id2[j];
+          --j;
+        }
+        q2[j + 1] = qv;
+        id2[j + 1] = iv;
+      }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < n; j += blockDim.x) b.s_hit[ri.pos0 + j] = make_int4(q2[j].x, q2[j].y, id2[j], k);
+    if (hist != b.first + ri.bin0) {
+      for (int j = threadIdx.x; j <= nb; j += blockDim.x) b.first[ri.bin0 + j] = ri.pos0 + hist[j];
+    } else {
+      __syncthreads();
+      for (int j = threadIdx.x; j <= nb; j += blockDim.x) b.first[ri.bin0 + j] += ri.pos0;
+    }
+    __syncthreads();  // the scratch is reused by the next listed row
   }
 }
 
@@ -2049,6 +2134,8 @@ cudaError_t tpc_configure_kernels(int sort_smem, int link_smem) {
   (void)link_smem;
   cudaError_t e = cudaFuncSetAttribute(k_row_sort, cudaFuncAttributeMaxDynamicSharedMemorySize, sort_smem);
   if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_row_sort_warp, cudaFuncAttributeMaxDynamicSharedMemorySize, RS_WARPS * RS_WARP_BYTES);
+  if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_links<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, LINK_STAGE_MAX);
   if (e == cudaSuccess)
     e = cudaFuncSetAttribute(k_links<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, LINK_STAGE_MAX);
@@ -2088,7 +2175,9 @@ cudaError_t launch_stages(const Buffers& b, const LaunchCfg& c, cudaStream_t s, 
   mark(2);
   k_group_scatter<<<b.n_chunks, 256, 0, s>>>(b);
   mark(3);
-  k_row_sort<<<M, 128, c.sort_smem, s>>>(b, c.sort_smem, b.cl_q, b.cl_key, b.up_raw);
+  cudaMemsetAsync(b.rs_big + M, 0, sizeof(int), s);
+  if (M) k_row_sort_warp<<<(M + RS_WARPS - 1) / RS_WARPS, 32 * RS_WARPS, RS_WARPS * RS_WARP_BYTES, s>>>(b, M);
+  k_row_sort<<<c.num_sms * 4, 128, c.sort_smem, s>>>(b, c.sort_smem, b.cl_q, b.cl_key, b.up_raw, M);
   mark(4);
   // positions left unwritten by rejected clusters must read as "no link"
   cudaMemsetAsync(b.up_raw, 0xFF, sizeof(int) * (size_t)b.N, s);
