@@ -283,7 +283,7 @@ __global__ void __launch_bounds__(256) k_group_scatter(const __grid_constant__ B
 // larger rows are listed in b.rs_big for k_row_sort.  Empty rows get their one
 // bin start here.
 constexpr int RS_WARPS = 8;
-constexpr int RS_WARP_BYTES = 8192;
+constexpr int RS_WARP_BYTES = 4096;
 
 __device__ __forceinline__ bool rs_fits_warp(int n, int nb) { return 16ll * n + 4ll * (nb + 1) <= RS_WARP_BYTES; }
 
