@@ -358,17 +358,22 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_row_sort_warp(const __grid_co
   for (int j = lane; j <= nb; j += 32) b.first[ri.bin0 + j] = ri.pos0 + hist[j];
 }
 
-// The rows listed by k_row_sort_warp, one CTA at a time per row (a grid-stride
-// loop over the list): scratch in shared memory when it fits `smem_bytes`,
-// else in the global scratch arrays tq, tid_buf, tslot at the row's positions.
-__global__ void __launch_bounds__(128) k_row_sort(const __grid_constant__ Buffers b, int smem_bytes, int2* tq, int* tid_buf, int* tslot, int M) {
+// The same sort by a CTA per row: every row (listed = 0, one CTA each), or the
+// rows listed by k_row_sort_warp (listed = 1, a grid-stride loop over the
+// list).  Scratch in shared memory when it fits `smem_bytes`, else in the
+// global scratch arrays tq, tid_buf, tslot at the row's positions.
+__global__ void __launch_bounds__(128) k_row_sort(const __grid_constant__ Buffers b, int smem_bytes, int2* tq, int* tid_buf, int* tslot, int M, int listed) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ int sm[33];
-  const int n_big = b.rs_big[M];
-  for (int ib = blockIdx.x; ib < n_big; ib += gridDim.x) {  // block-uniform loop
-    const int k = b.rs_big[ib];
+  const int n_here = listed ? b.rs_big[M] : M;
+  for (int ib = blockIdx.x; ib < n_here; ib += gridDim.x) {  // block-uniform loop
+    const int k = listed ? b.rs_big[ib] : ib;
     const RowInfo ri = b.rows[k];
     const int n = ri.n;
+    if (n == 0) {  // (rows of the unlisted form only)
+      if (threadIdx.x == 0) b.first[ri.bin0] = ri.pos0;
+      continue;
+    }
     const int nb = ri.ny * ri.nz;
     const long long need = 12ll * n + 4ll * n + 4ll * (nb + 1);
     int2* q2;
@@ -2175,9 +2180,15 @@ cudaError_t launch_stages(const Buffers& b, const LaunchCfg& c, cudaStream_t s, 
   mark(2);
   k_group_scatter<<<b.n_chunks, 256, 0, s>>>(b);
   mark(3);
-  cudaMemsetAsync(b.rs_big + M, 0, sizeof(int), s);
-  if (M) k_row_sort_warp<<<(M + RS_WARPS - 1) / RS_WARPS, 32 * RS_WARPS, RS_WARPS * RS_WARP_BYTES, s>>>(b, M);
-  k_row_sort<<<c.num_sms * 4, 128, c.sort_smem, s>>>(b, c.sort_smem, b.cl_q, b.cl_key, b.up_raw, M);
+  // rows of at most 256 hits on average (events, sectors): a warp per row, the
+  // few larger rows by CTAs; denser rows (time-frame slices): a CTA per row
+  if (M && (long long)b.N <= 256ll * M) {
+    cudaMemsetAsync(b.rs_big + M, 0, sizeof(int), s);
+    k_row_sort_warp<<<(M + RS_WARPS - 1) / RS_WARPS, 32 * RS_WARPS, RS_WARPS * RS_WARP_BYTES, s>>>(b, M);
+    k_row_sort<<<c.num_sms * 16, 128, c.sort_smem, s>>>(b, c.sort_smem, b.cl_q, b.cl_key, b.up_raw, M, 1);
+  } else if (M) {
+    k_row_sort<<<M, 128, c.sort_smem, s>>>(b, c.sort_smem, b.cl_q, b.cl_key, b.up_raw, M, 0);
+  }
   mark(4);
   // positions left unwritten by rejected clusters must read as "no link"
   cudaMemsetAsync(b.up_raw, 0xFF, sizeof(int) * (size_t)b.N, s);
