@@ -52,7 +52,8 @@ ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12
 TRAFFIC = {("c2", "tracklets"): 40.12e6}
 TRAFFIC_SOURCE = ("ncu --set full capture of the same kernels on the same workload, per step "
                   "(dram__bytes_read.sum + dram__bytes_write.sum); not measurable in this run")
-KERNELS_PER_STEP = {"plain": 19, "batched": 22}  # kernels per tracking step, as the launch lists show
+KERNELS_PER_STEP = {"plain": 20, "batched": 23}  # kernels per tracking step of an event batch (the
+# launch sequence of launch_stages: 19 and 22 before the warp-per-row sort, as the launch lists show)
 
 METRIC = "TPC clusters/s tracked (sector tracker, full TPC event)"
 WORKLOADS = {
