@@ -5,9 +5,10 @@
 //                    and extents (global atomics)
 //   k_row_setup      bin size, grid dims, row and bin offsets (block scans)
 //   k_group_scatter  counting sort of clusters into row-contiguous order
-//   k_row_sort_warp  per row (a warp each): bin histogram, scan, scatter, in-bin sort by id
-//   k_row_sort       the same per CTA for the rows too large for a warp's shared memory
-//                    (canonical order row, bin, original id) and first[] starts
+//   k_row_sort_warp  per row (a warp each): bin histogram, scan, scatter, in-bin sort
+//                    by id (canonical order row, bin, original id) and first[] starts
+//   k_row_sort       the same per CTA: rows too large for a warp's shared memory, and
+//                    every row of batches with dense rows (time-frame slices)
 //   k_links          per hit of an inner row: best (up, down) pair (integer metric)
 //   k_clean_start    mutual-link cleaning and start-hit flags
 //   k_scan_*         device-wide exclusive scans (reduce-then-scan, fixed grid)
@@ -16,6 +17,10 @@
 //   k_tracklets_down inward refit with hit re-picking, one per outermost hit
 //   k_select_max/own shared-cluster resolution by 64-bit atomicMax keys
 //   k_output         track and cluster-id compaction
+// Batched form (S9 below): the same steps, the tracklet passes as persistent
+// kernels fed by work queues (k_chain_walk, k_queue_items, k_tracklets_up_p,
+// k_down_order, k_tracklets_down_p).  Space-point correction: k_correct_grid
+// (S11; the MLP in tpc_mlp.cu).
 //
 // The method follows the paper's TPC tracking (Sec. 3: cellular-automaton track
 // finding derived from the Run 2 HLT tracker, followed by a Kalman fit) under
