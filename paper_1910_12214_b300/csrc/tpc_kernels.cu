@@ -287,6 +287,27 @@ __global__ void __launch_bounds__(256) k_group_scatter(const __grid_constant__ B
 // rows whose scratch fits the warp's slice of shared memory (RS_WARP_BYTES);
 // larger rows are listed in b.rs_big for k_row_sort.  Empty rows get their one
 // bin start here.
+// bin of quantised hit q in row ri (y-major cells of 2^shift quanta)
+__device__ __forceinline__ int rs_bin(const int2& q, const RowInfo& ri) {
+  return ((q.x - ri.ymin) >> ri.shift) * ri.nz + ((q.y - ri.zmin) >> ri.shift);
+}
+
+// hits [a, e) of one bin put in original-id order (insertion sort: bins hold a few hits)
+__device__ __forceinline__ void rs_bin_sort(int2* q2, int* id2, int a, int e) {
+  for (int i = a + 1; i < e; ++i) {
+    const int2 qv = q2[i];
+    const int iv = id2[i];
+    int j = i - 1;
+    while (j >= a && id2[j] > iv) {
+      q2[j + 1] = q2[j];
+      id2[j + 1] = id2[j];
+      --j;
+    }
+    q2[j + 1] = qv;
+    id2[j + 1] = iv;
+  }
+}
+
 constexpr int RS_WARPS = 8;
 constexpr int RS_WARP_BYTES = 4096;
 
@@ -314,12 +335,7 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_row_sort_warp(const __grid_co
   int* hist = slot + n;
   for (int j = lane; j <= nb; j += 32) hist[j] = 0;
   __syncwarp();
-  const int s = ri.shift;
-  for (int j = lane; j < n; j += 32) {
-    const int2 q = b.g_q[ri.pos0 + j];
-    const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
-    slot[j] = atomicAdd(&hist[bin], 1);
-  }
+  for (int j = lane; j < n; j += 32) slot[j] = atomicAdd(&hist[rs_bin(b.g_q[ri.pos0 + j], ri)], 1);
   __syncwarp();
   int carry = 0;  // exclusive scan of hist[0..nb], 32 entries at a time
   for (int j0 = 0; j0 <= nb; j0 += 32) {
@@ -337,27 +353,12 @@ __global__ void __launch_bounds__(32 * RS_WARPS) k_row_sort_warp(const __grid_co
   __syncwarp();
   for (int j = lane; j < n; j += 32) {
     const int2 q = b.g_q[ri.pos0 + j];
-    const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
-    const int p = hist[bin] + slot[j];
+    const int p = hist[rs_bin(q, ri)] + slot[j];
     q2[p] = q;
     id2[p] = b.g_id[ri.pos0 + j];
   }
   __syncwarp();
-  for (int bin = lane; bin < nb; bin += 32) {  // inside a bin: original id (bins hold a few hits)
-    const int a = hist[bin], e = hist[bin + 1];
-    for (int i = a + 1; i < e; ++i) {
-      const int2 qv = q2[i];
-      const int iv = id2[i];
-      int j = i - 1;
-      while (j >= a && id2[j] > iv) {
-        q2[j + 1] = q2[j];
-        id2[j + 1] = id2[j];
-        --j;
-      }
-      q2[j + 1] = qv;
-      id2[j + 1] = iv;
-    }
-  }
+  for (int bin = lane; bin < nb; bin += 32) rs_bin_sort(q2, id2, hist[bin], hist[bin + 1]);
   __syncwarp();
   for (int j = lane; j < n; j += 32) b.s_hit[ri.pos0 + j] = make_int4(q2[j].x, q2[j].y, id2[j], k);
   for (int j = lane; j <= nb; j += 32) b.first[ri.bin0 + j] = ri.pos0 + hist[j];
@@ -398,12 +399,7 @@ __global__ void __launch_bounds__(128) k_row_sort(const __grid_constant__ Buffer
     }
     for (int j = threadIdx.x; j <= nb; j += blockDim.x) hist[j] = 0;
     __syncthreads();
-    const int s = ri.shift;
-    for (int j = threadIdx.x; j < n; j += blockDim.x) {
-      const int2 q = b.g_q[ri.pos0 + j];
-      const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
-      slot[j] = atomicAdd(&hist[bin], 1);
-    }
+    for (int j = threadIdx.x; j < n; j += blockDim.x) slot[j] = atomicAdd(&hist[rs_bin(b.g_q[ri.pos0 + j], ri)], 1);
     __syncthreads();
     // exclusive scan of hist[0..nb] in place, chunk by chunk
     int carry = 0;
@@ -418,28 +414,13 @@ __global__ void __launch_bounds__(128) k_row_sort(const __grid_constant__ Buffer
     }
     for (int j = threadIdx.x; j < n; j += blockDim.x) {
       const int2 q = b.g_q[ri.pos0 + j];
-      const int bin = ((q.x - ri.ymin) >> s) * ri.nz + ((q.y - ri.zmin) >> s);
-      const int p = hist[bin] + slot[j];
+      const int p = hist[rs_bin(q, ri)] + slot[j];
       q2[p] = q;
       id2[p] = b.g_id[ri.pos0 + j];
     }
     __syncthreads();
-    // canonical order inside a bin: original id (insertion sort; bins hold a few hits)
-    for (int bin = threadIdx.x; bin < nb; bin += blockDim.x) {
-      const int a = hist[bin], e = hist[bin + 1];
-      for (int i = a + 1; i < e; ++i) {
-        const int2 qv = q2[i];
-        const int iv = id2[i];
-        int j = i - 1;
-        while (j >= a && id2[j] > iv) {
-          q2[j + 1] = q2[j];
-          id2[j + 1] = id2[j];
-          --j;
-        }
-        q2[j + 1] = qv;
-        id2[j + 1] = iv;
-      }
-    }
+    // canonical order inside a bin: original id
+    for (int bin = threadIdx.x; bin < nb; bin += blockDim.x) rs_bin_sort(q2, id2, hist[bin], hist[bin + 1]);
     __syncthreads();
     for (int j = threadIdx.x; j < n; j += blockDim.x) b.s_hit[ri.pos0 + j] = make_int4(q2[j].x, q2[j].y, id2[j], k);
     if (hist != b.first + ri.bin0) {
