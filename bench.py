@@ -42,8 +42,7 @@ sys.path.insert(0, ROOT)
 # words 4 B each; the tracklets read about two passes of 8 B of coordinates and
 # 4 B of bin lookup per hit and write a 4 B hit slot).
 ALGO_BYTES = {"quantise+row_stats": 16 + 12, "row_setup": 0, "group_scatter": 12 + 12, "row_sort": 12 + 16 + 8,
-              "links": 16 + 8, "clean+starts": 8 + 8 + 4, "tracklets": 28, "selection": 20, "output": 8,
-              "batched_items": 150, "batched_concat": 4}
+              "links": 16 + 8, "clean+starts": 8 + 8 + 4, "tracklets": 28, "selection": 20, "output": 8}
 # DRAM bytes (read + write) of the dominant step per tracking step, as one ncu
 # capture of the current kernels measured them (dram__bytes_read.sum +
 # dram__bytes_write.sum of k_tracklets_up<1> and k_tracklets_down<1> on the

@@ -174,8 +174,8 @@ tpc_status tpc_device_tracks(tpc_ctx* ctx, const tpc_track_t** trk, const uint32
 
 /* Per-step device times of the last tpc_track() in microseconds (needs
  * cfg.profile = 1): us[i] for the steps named by tpc_stage_name(i); steps the
- * last run's mode does not have read 0 (both modes: 0..8; 9..10 are no longer
- * used).
+ * last run's mode does not have read 0 (both modes: 0..8; 9..10, named
+ * "unused_9" and "unused_10", are no longer used and read 0).
  * Entries 11..12 are the two kernels of the last tpc_cluster_masks() call and
  * 13..15 the symbol, rANS and layout phases of the last tpc_compress() call
  * (tpc_reduce.h) since the batch was loaded, else 0.  Entry 16 is the

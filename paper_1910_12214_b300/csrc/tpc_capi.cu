@@ -763,7 +763,7 @@ extern "C" tpc_status tpc_device_tracks(tpc_ctx* c, const tpc_track_t** trk, con
 
 static const char* kStageNames[TPC_N_REPORTED_STAGES] = {
     "quantise+row_stats", "row_setup", "group_scatter", "row_sort", "links", "clean+starts", "tracklets",
-    "selection", "output", "batched_items", "batched_concat", "mask_assoc", "mask_final", "compress_symbols",
+    "selection", "output", "unused_9", "unused_10", "mask_assoc", "mask_final", "compress_symbols",
     "compress_rans", "compress_layout", "correction"};
 
 extern "C" const char* tpc_stage_name(int i) { return (i >= 0 && i < TPC_N_REPORTED_STAGES) ? kStageNames[i] : ""; }

@@ -133,7 +133,7 @@ struct Buffers {
   float* cz;
 };
 
-#define TPC_N_STAGES 11  // 9 plain-mode steps, then the batched kernel and its compaction
+#define TPC_N_STAGES 11  // the 9 steps of tpc_track, then two slots no longer used (indices kept stable)
 #define TPC_N_REPORTED_STAGES 17  // ... then the two kernels of tpc_cluster_masks, the 3 phases of
                                   // tpc_compress, and the space-point correction of tpc_track
 
